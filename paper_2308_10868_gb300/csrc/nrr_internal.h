@@ -1,0 +1,74 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nrr.h"
+
+namespace nrr {
+
+// ---- host-side error reporting -------------------------------------------
+nrr_status fail(nrr_status s, const char *fmt, ...);
+nrr_status cuda_fail(cudaError_t e, const char *what);
+void clear_error();
+
+#define NRR_CUDA_TRY(call)                                  \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return nrr::cuda_fail(e_, #call); \
+    } while (0)
+
+// Device word the kernels set on a bounded-wait timeout or failed check.
+// Returns its device address for the current device (no allocation: it is a
+// file-scope __device__ variable of the library).
+nrr_status device_error_word(unsigned int **ptr);
+
+// Bits of the device error word.
+enum : unsigned int { DEV_ERR_TIMEOUT = 1u, DEV_ERR_INTERNAL = 2u };
+
+// Encode a 3-D tiled tensor map over a [nz][ny][nx] volume of `dtype` with a
+// box of (bx, by, bz) elements; out-of-bounds reads fill zeros.
+nrr_status encode_volume_map(CUtensorMap *map, const void *base, nrr_dtype dtype, nrr_dims dims, int bx, int by,
+                             int bz);
+
+int sm_count();
+
+// Common argument checks.
+nrr_status check_dims(nrr_dims dims, nrr_dtype dtype, int32_t block);
+inline size_t elem_size(nrr_dtype t) { return t == NRR_F32 ? 4 : 2; }
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Box sums: number of bytes and the two sub-arrays of a box-sum buffer.
+size_t boxsum_bytes(nrr_dims dims, nrr_dtype dtype);
+inline size_t boxsum_s2_offset(nrr_dims dims, nrr_dtype dtype)
+{
+    size_t v = (size_t)dims.nx * dims.ny * dims.nz;
+    (void)dtype;
+    return align_up(v * 4, 256);  // S1 is int32 or float: 4 bytes each
+}
+nrr_status launch_boxsums(const void *d_intraop, nrr_dtype dtype, nrr_dims dims, int32_t block, void *d_boxsums,
+                          cudaStream_t stream);
+
+// Match kernel launch (box sums already computed).
+struct MatchLaunch {
+    const void *preop;
+    const void *intraop;
+    const void *s1;
+    const void *s2;
+    nrr_dtype dtype;
+    nrr_dims dims;
+    const int32_t *centers;
+    int32_t n_blocks;
+    const int32_t *d_n_blocks;
+    int32_t block;
+    int32_t radius[3];
+    int32_t *disp;
+    double *ncc;
+    uint8_t *valid;
+    unsigned int *err;
+};
+nrr_status launch_match(const MatchLaunch &a, cudaStream_t stream);
+
+}  // namespace nrr

@@ -1,0 +1,671 @@
+// NCC block-matching kernel (Sec. 3 NCC equation and O(B x W) bound;
+// Sec. 4.3 block-matching loop), written for sm_103a.
+//
+// One CTA processes one registration block at a time (persistent loop over
+// blocks).  Per block:
+//   1. One thread issues a TMA tiled load of the block's search window of
+//      the reference image, [c-h-R, c+h+R] per axis, into shared memory
+//      (x start rounded down to a 16-byte boundary; out-of-volume voxels
+//      arrive as zeros and are excluded below by coordinates).
+//   2. Meanwhile the CTA loads the floating block, reduces its sums and
+//      stores it mean-shifted (T_k = I_k - m) in shared memory.
+//   3. The window is converted to float, shifted by a per-block constant c
+//      (J'_k = J_k - c).
+//   4. Search: thread t owns one (dz, dy) line of the window and all
+//      2*rx+1 shifts along x; for every template row it loads one window row
+//      (vectorised 16-byte shared loads, conflict-free row pitch) and
+//      accumulates A(d) = sum_k T_k J'_{k+d} with FP32 FFMA, fully unrolled
+//      over the row and the x shifts.
+//   5. Every shift gets an approximate NCC from A(d) and the box sums S_J,
+//      S_JJ (precomputed, exact for uint16) together with a rigorous bound on
+//      its error (FFMA recursive-summation bound gamma_N * sum|T||J'|, with
+//      Cauchy-Schwarz sum|T||J'| <= sqrt(sum T^2 * sum J'^2), plus the
+//      rounding of the final operations; doubled for margin).
+//   6. Shifts whose upper bound reaches the best lower bound survive (about
+//      one per block on the phantoms) and are rescored by a warp each:
+//      uint16 -> exact int64 sum, then the canonical FP64 ratio
+//      num / sqrt(vI * vJ); float32 -> FP64 Pearson.  The best survivor
+//      under the tie-break rule is the block's answer.
+// The exhaustive maximum is therefore found exactly: the true arg-max can
+// never be filtered out, because its upper bound is at least its value,
+// which is at least every other shift's value, hence at least every lower
+// bound.
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "nrr_internal.h"
+#include "nrr_ptx.cuh"
+
+namespace nrr {
+
+struct MatchParams {
+    const void *preop;
+    const void *intraop;
+    const void *s1;
+    const void *s2;
+    int nx, ny, nz;
+    const int32_t *centers;
+    int32_t n_blocks;
+    const int32_t *d_n_blocks;
+    int ry, rz;
+    int bx;  // TMA box extent along x (elements)
+    int pf;  // row pitch of the float window (floats)
+    int32_t *disp;
+    double *ncc;
+    uint8_t *valid;
+    unsigned int *err;
+};
+
+constexpr int MATCH_MAX_THREADS = 256;
+constexpr int MATCH_MAX_WARPS = MATCH_MAX_THREADS / 32;
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s
+
+struct MatchScratch {
+    float wlb[MATCH_MAX_WARPS];
+    long long wsi[MATCH_MAX_WARPS];
+    unsigned long long wsii[MATCH_MAX_WARPS];
+    double wd1[MATCH_MAX_WARPS];
+    double wd2[MATCH_MAX_WARPS];
+    float wmin[MATCH_MAX_WARPS];
+    float wmax[MATCH_MAX_WARPS];
+    double bs[MATCH_MAX_WARPS];
+    int bn2[MATCH_MAX_WARPS];
+    int bcode[MATCH_MAX_WARPS];
+    int bok[MATCH_MAX_WARPS];
+    int nsurv;
+};
+
+struct MatchLayout {
+    int u, f, t, iraw, surv, sc, bar, total;
+};
+
+__host__ __device__ inline int round_up_i(int v, int a) { return (v + a - 1) / a * a; }
+
+// Shared-memory carve-up of one CTA (all offsets 128-byte aligned).
+__host__ __device__ inline MatchLayout match_layout(int elem, int B, int P, int bx, int pf, int wy, int wz, int py,
+                                                   int pz, bool f32)
+{
+    MatchLayout L;
+    int pt = round_up_i(B, 4);
+    int o = 0;
+    L.u = o;
+    o += round_up_i(bx * wy * wz * elem, 128);
+    L.f = o;
+    o += round_up_i(pf * wy * wz * 4, 128);
+    L.t = o;
+    o += round_up_i(B * B * pt * 4, 128);
+    L.iraw = o;
+    o += f32 ? round_up_i(B * B * B * 4, 128) : 0;
+    L.surv = o;
+    o += round_up_i(P * py * pz * 2, 128);
+    L.sc = o;
+    o += round_up_i((int)sizeof(MatchScratch), 128);
+    L.bar = o;
+    o += 128;
+    L.total = o;
+    return L;
+}
+
+// Row pitch of the float window: a multiple of 4 floats with an odd number
+// of 16-byte chunks, so 8 consecutive rows fall in distinct bank groups.
+__host__ __device__ inline int match_pitch(int wx)
+{
+    int q = (wx + 3) / 4;
+    if ((q & 1) == 0) ++q;
+    return 4 * q;
+}
+
+struct Cand {
+    double s;
+    int n2;
+    int code;
+    int ok;
+};
+
+// NCC descending, then |d|^2 ascending, then (dz, dy, dx) lexicographic
+// ascending; `code` increases with (dz, dy, dx) lexicographically.
+__device__ __forceinline__ bool cand_better(const Cand &a, const Cand &b)
+{
+    if (!a.ok) return false;
+    if (!b.ok) return true;
+    if (a.s != b.s) return a.s > b.s;
+    if (a.n2 != b.n2) return a.n2 < b.n2;
+    return a.code < b.code;
+}
+
+__device__ __forceinline__ float warp_max_f(float v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_min_f(float v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+template <typename V>
+__device__ __forceinline__ V warp_sum(V v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void write_result(const MatchParams &a, int blk, const Cand &b, int P, int py, int rx,
+                                             int ry, int rz)
+{
+    if (b.ok) {
+        int dxi = b.code % P, dyi = (b.code / P) % py, dzi = b.code / (P * py);
+        a.disp[3 * blk + 0] = dxi - rx;
+        a.disp[3 * blk + 1] = dyi - ry;
+        a.disp[3 * blk + 2] = dzi - rz;
+        a.ncc[blk] = b.s;
+        a.valid[blk] = 1;
+    } else {
+        a.disp[3 * blk + 0] = 0;
+        a.disp[3 * blk + 1] = 0;
+        a.disp[3 * blk + 2] = 0;
+        a.ncc[blk] = __longlong_as_double(0x7ff8000000000000ll);
+        a.valid[blk] = 0;
+    }
+}
+
+template <typename T, int B, int P>
+__global__ void __launch_bounds__(MATCH_MAX_THREADS) match_kernel(const MatchParams a,
+                                                                  const __grid_constant__ CUtensorMap tmap)
+{
+    constexpr bool F32 = std::is_same<T, float>::value;
+    constexpr int H = (B - 1) / 2;
+    constexpr int N = B * B * B;
+    constexpr int PT = (B + 3) / 4 * 4;
+    constexpr int RX = (P - 1) / 2;
+    constexpr int WX = B + P - 1;
+    constexpr int NJ4 = (WX + 3) / 4;
+    constexpr int ALIGN = 16 / (int)sizeof(T);
+    constexpr float U32 = 5.9604644775390625e-08f;  // 2^-24, unit roundoff of binary32
+    constexpr double GAMMA_N = (double)N * 5.9604644775390625e-08 / (1.0 - (double)N * 5.9604644775390625e-08);
+
+    const int ry = a.ry, rz = a.rz, py = 2 * ry + 1, pz = 2 * rz + 1, lines = py * pz;
+    const int wy = B + 2 * ry, wz = B + 2 * rz, bx = a.bx, pf = a.pf;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    const MatchLayout L = match_layout((int)sizeof(T), B, P, bx, pf, wy, wz, py, pz, F32);
+    T *U = reinterpret_cast<T *>(smem + L.u);
+    float *Fw = reinterpret_cast<float *>(smem + L.f);
+    float *Tm = reinterpret_cast<float *>(smem + L.t);
+    float *Iraw = reinterpret_cast<float *>(smem + L.iraw);
+    uint16_t *surv = reinterpret_cast<uint16_t *>(smem + L.surv);
+    MatchScratch *sc = reinterpret_cast<MatchScratch *>(smem + L.sc);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nthr = blockDim.x, nwarp = nthr >> 5;
+    int n = a.n_blocks;
+    if (a.d_n_blocks) {
+        int m = *a.d_n_blocks;
+        n = m < 0 ? 0 : (m < n ? m : n);
+    }
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+
+    for (int blk = blockIdx.x; blk < n; blk += gridDim.x) {
+        const int cx = a.centers[3 * blk + 0], cy = a.centers[3 * blk + 1], cz = a.centers[3 * blk + 2];
+        const bool inside = cx >= H && cy >= H && cz >= H && cx <= nx - 1 - H && cy <= ny - 1 - H && cz <= nz - 1 - H;
+        if (!inside) {
+            if (tid == 0) write_result(a, blk, Cand{0.0, 0, 0, 0}, P, py, RX, ry, rz);
+            continue;
+        }
+        const int x0 = cx - H - RX, y0 = cy - H - ry, z0 = cz - H - rz;
+        const int xs = x0 & ~(ALIGN - 1);  // floor to a 16-byte boundary (also for negative x0)
+        const int xo = x0 - xs;
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bar, (uint32_t)(bx * wy * wz * (int)sizeof(T)));
+            tma_load_3d(U, &tmap, bar, xs, y0, z0);
+            sc->nsurv = 0;
+        }
+
+        // ---- floating block: sums, mean shift, template in shared memory --
+        const T *pre = reinterpret_cast<const T *>(a.preop);
+        long long si_p = 0;
+        unsigned long long sii_p = 0;
+        double dsi_p = 0.0;
+        float mn = INFINITY, mx = -INFINITY;
+        for (int k = tid; k < B * B * PT; k += nthr) {
+            int kx = k % PT, kzy = k / PT, ky = kzy % B, kz = kzy / B;
+            float v = 0.f;
+            if (kx < B) {
+                T raw = pre[((size_t)(cz - H + kz) * ny + (cy - H + ky)) * nx + (cx - H + kx)];
+                if constexpr (F32) {
+                    v = raw;
+                    dsi_p += (double)raw;
+                    mn = fminf(mn, raw);
+                    mx = fmaxf(mx, raw);
+                    Iraw[(kz * B + ky) * B + kx] = raw;
+                } else {
+                    v = (float)raw;
+                    si_p += raw;
+                    sii_p += (unsigned long long)((uint32_t)raw * (uint32_t)raw);
+                }
+            }
+            Tm[k] = v;
+        }
+        if constexpr (F32) {
+            dsi_p = warp_sum(dsi_p);
+            mn = warp_min_f(mn);
+            mx = warp_max_f(mx);
+            if (lane == 0) {
+                sc->wd1[warp] = dsi_p;
+                sc->wmin[warp] = mn;
+                sc->wmax[warp] = mx;
+            }
+        } else {
+            si_p = warp_sum(si_p);
+            sii_p = warp_sum(sii_p);
+            if (lane == 0) {
+                sc->wsi[warp] = si_p;
+                sc->wsii[warp] = sii_p;
+            }
+        }
+        __syncthreads();
+
+        // per-block constants of the filter
+        float fvI, kq, c_f = 0.f, emu = 0.f, mu = 0.f;
+        long long vI = 0, rr = 0;
+        int c_i = 0;
+        double Ibar = 0.0, dvI = 0.0;
+        bool flatI;
+        const size_t cidx = ((size_t)cz * ny + cy) * nx + cx;
+        if constexpr (F32) {
+            double s = 0.0;
+            float lo = INFINITY, hi = -INFINITY;
+            for (int w = 0; w < nwarp; ++w) {
+                s += sc->wd1[w];
+                lo = fminf(lo, sc->wmin[w]);
+                hi = fmaxf(hi, sc->wmax[w]);
+            }
+            flatI = !(lo < hi);
+            Ibar = s / (double)N;
+            mu = (float)Ibar;
+            emu = (float)(Ibar - (double)mu);
+            c_f = __fdiv_rn(reinterpret_cast<const float *>(a.s1)[cidx], (float)N);
+        } else {
+            long long s = 0;
+            unsigned long long q = 0;
+            for (int w = 0; w < nwarp; ++w) {
+                s += sc->wsi[w];
+                q += sc->wsii[w];
+            }
+            vI = (long long)N * (long long)q - s * s;
+            flatI = vI == 0;
+            long long m = (2 * s + N) / (2 * N);  // nearest integer to the block mean
+            rr = (long long)N * m - s;
+            long long qt = (long long)q - 2 * m * s + (long long)N * m * m;  // sum (I - m)^2, exact
+            fvI = (float)vI;
+            kq = (float)((double)N * GAMMA_N * sqrt((double)qt) * (1.0 + 1e-6));
+            long long s1c = reinterpret_cast<const int32_t *>(a.s1)[cidx];
+            c_i = (int)((2 * s1c + N) / (2 * N));
+            // shift the template by m (exact small integers in float)
+            for (int k = tid; k < B * B * PT; k += nthr)
+                if (k % PT < B) Tm[k] = Tm[k] - (float)m;
+        }
+        if constexpr (F32) {
+            double dq_p = 0.0, dv_p = 0.0;
+            for (int k = tid; k < B * B * PT; k += nthr) {
+                if (k % PT < B) {
+                    float raw = Tm[k];
+                    float t = __fsub_rn(raw, mu);
+                    Tm[k] = t;
+                    dq_p += (double)t * (double)t;
+                    double dv = (double)raw - Ibar;
+                    dv_p += dv * dv;
+                }
+            }
+            dq_p = warp_sum(dq_p);
+            dv_p = warp_sum(dv_p);
+            __syncthreads();  // every thread has read wd1 above
+            if (lane == 0) {
+                sc->wd1[warp] = dq_p;
+                sc->wd2[warp] = dv_p;
+            }
+        }
+
+        // ---- wait for the window ----------------------------------------
+        bool got = mbar_wait_bounded(bar, phase, WAIT_LIMIT_NS);
+        if (!__syncthreads_and(got)) {
+            if (tid == 0) {
+                atomicOr(a.err, DEV_ERR_TIMEOUT);
+                write_result(a, blk, Cand{0.0, 0, 0, 0}, P, py, RX, ry, rz);
+            }
+            mbar_wait_bounded(bar, phase, WAIT_LIMIT_NS);  // let an in-flight copy land before exiting
+            return;
+        }
+        phase ^= 1u;
+        if constexpr (F32) {
+            double q = 0.0, v = 0.0;
+            for (int w = 0; w < nwarp; ++w) {
+                q += sc->wd1[w];
+                v += sc->wd2[w];
+            }
+            dvI = v;
+            fvI = (float)v;
+            kq = (float)(sqrt(q) * (1.0 + 1e-6));  // sqrt(sum T^2), rounded up
+        }
+        if (flatI) {  // flat floating block: NCC undefined for every shift
+            if (tid == 0) write_result(a, blk, Cand{0.0, 0, 0, 0}, P, py, RX, ry, rz);
+            __syncthreads();
+            continue;
+        }
+
+        // ---- window -> float, shifted by c --------------------------------
+        for (int i = tid; i < wz * wy * pf; i += nthr) {
+            int x = i % pf, zy = i / pf;
+            float v = 0.f;
+            if (x < WX) {
+                T u = U[zy * bx + xo + x];
+                if constexpr (F32)
+                    v = __fsub_rn(u, c_f);
+                else
+                    v = (float)((int)u - c_i);
+            }
+            Fw[i] = v;
+        }
+        __syncthreads();
+
+        // ---- search: FP32 accumulation of A(d) over the whole window ------
+        float ub[P];
+        float lbm = -INFINITY;
+        const int dyi = tid % py, dzi = tid / py;
+        if (tid < lines) {
+            float acc[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) acc[p] = 0.f;
+            for (int kz = 0; kz < B; ++kz) {
+                const float *frow = Fw + ((dzi + kz) * wy + dyi) * pf;
+                const float *trow = Tm + kz * B * PT;
+#pragma unroll 1
+                for (int ky = 0; ky < B; ++ky) {
+                    float j[4 * NJ4];
+                    float t[PT];
+#pragma unroll
+                    for (int q = 0; q < NJ4; ++q) {
+                        float4 v = *reinterpret_cast<const float4 *>(frow + ky * pf + 4 * q);
+                        j[4 * q + 0] = v.x;
+                        j[4 * q + 1] = v.y;
+                        j[4 * q + 2] = v.z;
+                        j[4 * q + 3] = v.w;
+                    }
+#pragma unroll
+                    for (int q = 0; q < PT / 4; ++q) {
+                        float4 v = *reinterpret_cast<const float4 *>(trow + ky * PT + 4 * q);
+                        t[4 * q + 0] = v.x;
+                        t[4 * q + 1] = v.y;
+                        t[4 * q + 2] = v.z;
+                        t[4 * q + 3] = v.w;
+                    }
+#pragma unroll
+                    for (int kx = 0; kx < B; ++kx)
+#pragma unroll
+                        for (int p = 0; p < P; ++p) acc[p] = __fmaf_rn(t[kx], j[kx + p], acc[p]);
+                }
+            }
+
+            // ---- approximate NCC and its error bound per shift -----------
+            const int dy = dyi - ry, dz = dzi - rz, Y = cy + dy, Z = cz + dz;
+            const bool yz_ok = Y >= H && Y <= ny - 1 - H && Z >= H && Z <= nz - 1 - H;
+            const float fN = (float)N;
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const int X = cx + p - RX;
+                ub[p] = -INFINITY;
+                if (!(yz_ok && X >= H && X <= nx - 1 - H)) continue;
+                const size_t idx = ((size_t)Z * ny + Y) * nx + X;
+                if constexpr (!F32) {
+                    const long long s1 = reinterpret_cast<const int32_t *>(a.s1)[idx];
+                    const long long s2 = reinterpret_cast<const long long *>(a.s2)[idx];
+                    const long long vJ = (long long)N * s2 - s1 * s1;
+                    if (vJ <= 0) continue;  // flat reference block
+                    const long long s1p = s1 - (long long)N * c_i;
+                    const long long s2p = s2 - 2ll * c_i * s1 + (long long)N * c_i * c_i;  // sum (J-c)^2
+                    const float inv = __frsqrt_rn(__fmul_rn(fvI, (float)vJ));
+                    const float na = __fmul_rn(fN, acc[p]);
+                    const float rs = (float)(rr * s1p);
+                    const float v = __fmul_rn(__fadd_rn(na, rs), inv);
+                    float e = kq * __fsqrt_rn((float)s2p) * inv + 3.f * U32 * (fabsf(na) + fabsf(rs)) * inv +
+                              6.f * U32 * fabsf(v);
+                    e = 2.f * e + 1e-9f;
+                    ub[p] = v + e;
+                    lbm = fmaxf(lbm, v - e);
+                } else {
+                    constexpr float GS = (float)(3.0 * B * 5.9604644775390625e-08 /
+                                                 (1.0 - 3.0 * B * 5.9604644775390625e-08));  // box-sum depth
+                    constexpr float GN = (float)GAMMA_N;
+                    const float s1 = reinterpret_cast<const float *>(a.s1)[idx];
+                    const float s2 = fmaxf(reinterpret_cast<const float *>(a.s2)[idx], 0.f);
+                    const float d1 = GS * __fsqrt_rn(fN * s2) * 1.01f;  // |S1 err| bound
+                    const float s1sq_n = __fmul_rn(__fmul_rn(s1, s1), 1.0f / fN);
+                    const float vJa = __fsub_rn(s2, s1sq_n);
+                    const float dv = GS * s2 + (2.f * fabsf(s1) + d1) * d1 / fN + 4.f * U32 * (s2 + s1sq_n);
+                    const float s1p = __fsub_rn(s1, __fmul_rn(fN, c_f));  // ~ sum (J - c)
+                    const float m2 = s2 + 2.f * fabsf(c_f) * fabsf(s1) + fN * c_f * c_f;
+                    const float e2 = __fadd_rn(__fsub_rn(s2, 2.f * c_f * s1), fN * c_f * c_f);
+                    const float sj2 = (fmaxf(e2, 0.f) + (GS + 8.f * U32) * m2 * 1.01f) * (1.f + 4.f * U32);
+                    if (!(vJa - dv > 0.f)) {  // spread of the reference block not resolved: rescore
+                        ub[p] = INFINITY;
+                        continue;
+                    }
+                    const float rho = dv / (vJa - dv);
+                    if (!(rho <= 0.25f)) {
+                        ub[p] = INFINITY;
+                        continue;
+                    }
+                    const float inv = __frsqrt_rn(__fmul_rn(fvI, vJa));
+                    const float A = acc[p];
+                    const float es = __fmul_rn(emu, s1p);
+                    const float num = __fsub_rn(A, es);
+                    const float v = __fmul_rn(num, inv);
+                    const float enum_ = (GN + 3.f * U32) * kq * __fsqrt_rn(sj2) +
+                                        fabsf(emu) * (fabsf(s1p) + d1 + 2.f * U32 * fN * fabsf(c_f)) * 1.01f +
+                                        U32 * (fabsf(A) + fabsf(es));
+                    float e = enum_ * inv * (1.f + 0.7f * rho + 4.f * U32) + fabsf(num) * inv * (0.7f * rho + 6.f * U32) +
+                              3.f * U32 * fabsf(v);
+                    e = 2.f * e + 1e-9f;
+                    ub[p] = v + e;
+                    lbm = fmaxf(lbm, v - e);
+                }
+            }
+        }
+
+        // ---- best lower bound over the window; survivors ------------------
+        lbm = warp_max_f(lbm);
+        if (lane == 0) sc->wlb[warp] = lbm;
+        __syncthreads();
+        float LB = -INFINITY;
+        for (int w = 0; w < nwarp; ++w) LB = fmaxf(LB, sc->wlb[w]);
+        if (tid < lines) {
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                if (ub[p] > -INFINITY && ub[p] >= LB) {
+                    int s = atomicAdd(&sc->nsurv, 1);
+                    surv[s] = (uint16_t)((dzi * py + dyi) * P + p);
+                }
+            }
+        }
+        __syncthreads();
+        const int nsurv = sc->nsurv;
+
+        // ---- exact rescoring of the survivors, one warp each -------------
+        Cand wb{0.0, 0, 0, 0};
+        for (int s = warp; s < nsurv; s += nwarp) {
+            const int code = surv[s];
+            const int sxi = code % P, syi = (code / P) % py, szi = code / (P * py);
+            const int dx = sxi - RX, dy = syi - ry, dz = szi - rz;
+            const size_t idx = ((size_t)(cz + dz) * ny + (cy + dy)) * nx + (cx + dx);
+            Cand c{0.0, dx * dx + dy * dy + dz * dz, code, 0};
+            if constexpr (!F32) {
+                long long e = 0;
+                for (int k = lane; k < N; k += 32) {
+                    const int kz = k / (B * B), rem = k - kz * B * B, ky = rem / B, kx = rem - ky * B;
+                    const int t = (int)Tm[(kz * B + ky) * PT + kx];
+                    const int jv = (int)Fw[((szi + kz) * wy + (syi + ky)) * pf + sxi + kx];
+                    e += (long long)t * jv;
+                }
+                e = warp_sum(e);
+                if (lane == 0) {
+                    const long long s1 = reinterpret_cast<const int32_t *>(a.s1)[idx];
+                    const long long s2 = reinterpret_cast<const long long *>(a.s2)[idx];
+                    const long long vJ = (long long)N * s2 - s1 * s1;
+                    const long long num = (long long)N * e + rr * (s1 - (long long)N * c_i);
+                    if (vJ > 0) {
+                        const double den = __dsqrt_rn(__dmul_rn((double)vI, (double)vJ));
+                        c.s = __ddiv_rn((double)num, den);
+                        c.ok = 1;
+                    }
+                }
+            } else {
+                double sij = 0.0, sj = 0.0, sjj = 0.0;
+                float lo = INFINITY, hi = -INFINITY;
+                for (int k = lane; k < N; k += 32) {
+                    const int kz = k / (B * B), rem = k - kz * B * B, ky = rem / B, kx = rem - ky * B;
+                    const double di = (double)Iraw[k] - Ibar;
+                    const float jf = U[((szi + kz) * wy + (syi + ky)) * bx + xo + sxi + kx];
+                    const double jd = (double)jf;
+                    sij = fma(di, jd, sij);
+                    sj += jd;
+                    sjj = fma(jd, jd, sjj);
+                    lo = fminf(lo, jf);
+                    hi = fmaxf(hi, jf);
+                }
+                sij = warp_sum(sij);
+                sj = warp_sum(sj);
+                sjj = warp_sum(sjj);
+                lo = warp_min_f(lo);
+                hi = warp_max_f(hi);
+                if (lane == 0 && lo < hi) {
+                    const double vJ = sjj - sj * sj / (double)N;
+                    if (vJ > 0.0) {
+                        c.s = sij / sqrt(dvI * vJ);
+                        c.ok = 1;
+                    }
+                }
+            }
+            if (lane == 0 && cand_better(c, wb)) wb = c;
+        }
+        if (lane == 0) {
+            sc->bs[warp] = wb.s;
+            sc->bn2[warp] = wb.n2;
+            sc->bcode[warp] = wb.code;
+            sc->bok[warp] = wb.ok;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            Cand best{0.0, 0, 0, 0};
+            for (int w = 0; w < nwarp; ++w) {
+                Cand c{sc->bs[w], sc->bn2[w], sc->bcode[w], sc->bok[w]};
+                if (cand_better(c, best)) best = c;
+            }
+            write_result(a, blk, best, P, py, RX, ry, rz);
+        }
+        __syncthreads();
+    }
+}
+
+// Host side: launch one (element type, block size, x-shift count) variant.
+template <typename T, int B, int P>
+nrr_status launch_match_variant(const MatchLaunch &m, cudaStream_t stream)
+{
+    constexpr bool F32 = std::is_same<T, float>::value;
+    constexpr int ALIGN = 16 / (int)sizeof(T);
+    constexpr int WX = B + P - 1;
+    const int ry = m.radius[1], rz = m.radius[2], py = 2 * ry + 1, pz = 2 * rz + 1;
+    const int wy = B + 2 * ry, wz = B + 2 * rz;
+    const int bx = round_up_i(WX + ALIGN - 1, ALIGN);
+    const int pf = match_pitch(WX);
+    const MatchLayout L = match_layout((int)sizeof(T), B, P, bx, pf, wy, wz, py, pz, F32);
+    const int lines = py * pz;
+    const int threads = round_up_i(lines, 32);
+    if (threads > MATCH_MAX_THREADS) return fail(NRR_E_INVALID, "search window too large");
+
+    CUtensorMap map;
+    nrr_status st = encode_volume_map(&map, m.intraop, m.dtype, m.dims, bx, wy, wz);
+    if (st != NRR_OK) return st;
+
+    auto kern = match_kernel<T, B, P>;
+    static int smem_set = 0;  // largest dynamic shared memory opted in so far
+    if (L.total > smem_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(match_kernel)");
+        smem_set = L.total;
+    }
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, L.total);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (occ < 1) return fail(NRR_E_INVALID, "match kernel does not fit on an SM (%d B shared)", L.total);
+    long long grid = (long long)occ * sm_count();
+    if (grid > m.n_blocks) grid = m.n_blocks;
+
+    MatchParams p;
+    p.preop = m.preop;
+    p.intraop = m.intraop;
+    p.s1 = m.s1;
+    p.s2 = m.s2;
+    p.nx = m.dims.nx;
+    p.ny = m.dims.ny;
+    p.nz = m.dims.nz;
+    p.centers = m.centers;
+    p.n_blocks = m.n_blocks;
+    p.d_n_blocks = m.d_n_blocks;
+    p.ry = ry;
+    p.rz = rz;
+    p.bx = bx;
+    p.pf = pf;
+    p.disp = m.disp;
+    p.ncc = m.ncc;
+    p.valid = m.valid;
+    p.err = m.err;
+    kern<<<(unsigned)grid, threads, L.total, stream>>>(p, map);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "match kernel launch");
+    return NRR_OK;
+}
+
+template <typename T, int B>
+nrr_status launch_match_b(const MatchLaunch &m, cudaStream_t stream)
+{
+    switch (m.radius[0]) {
+    case 0: return launch_match_variant<T, B, 1>(m, stream);
+    case 1: return launch_match_variant<T, B, 3>(m, stream);
+    case 2: return launch_match_variant<T, B, 5>(m, stream);
+    case 3: return launch_match_variant<T, B, 7>(m, stream);
+    case 4: return launch_match_variant<T, B, 9>(m, stream);
+    case 5: return launch_match_variant<T, B, 11>(m, stream);
+    case 6: return launch_match_variant<T, B, 13>(m, stream);
+    case 7: return launch_match_variant<T, B, 15>(m, stream);
+    }
+    return fail(NRR_E_INVALID, "radius x %d outside 0..7", m.radius[0]);
+}
+
+// One entry per (element type, block size); defined in the instantiation
+// translation units.
+nrr_status launch_match_u16_b3(const MatchLaunch &, cudaStream_t);
+nrr_status launch_match_u16_b5(const MatchLaunch &, cudaStream_t);
+nrr_status launch_match_u16_b7(const MatchLaunch &, cudaStream_t);
+nrr_status launch_match_u16_b9(const MatchLaunch &, cudaStream_t);
+nrr_status launch_match_u16_b11(const MatchLaunch &, cudaStream_t);
+nrr_status launch_match_f32_b3(const MatchLaunch &, cudaStream_t);
+nrr_status launch_match_f32_b5(const MatchLaunch &, cudaStream_t);
+nrr_status launch_match_f32_b7(const MatchLaunch &, cudaStream_t);
+nrr_status launch_match_f32_b9(const MatchLaunch &, cudaStream_t);
+nrr_status launch_match_f32_b11(const MatchLaunch &, cudaStream_t);
+
+}  // namespace nrr

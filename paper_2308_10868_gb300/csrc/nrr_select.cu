@@ -1,0 +1,412 @@
+// Variance-based block selection (Sec. 4.1, "Parallel feature selection").
+//
+// The paper partitions the image among threads, computes a variance and an
+// index per candidate, sorts the pairs in parallel, merges them and keeps
+// 0.5 + N_c * F_s blocks.  Here that becomes:
+//   K1 grid_keys     one thread per stride grid point: exact variance key
+//                    N*sum(I^2) - (sum I)^2 of its b^3 block if it is a
+//                    candidate (centre in mask, block in volume), else -1;
+//                    counts N_c and the number of keys > 0.
+//   K2 radix select  five histogram passes over 11/11/11/11/9-bit digits of
+//                    the (< 2^53) keys find the n_sel-th largest key K* and
+//                    how many keys equal to K* are needed; no full sort.
+//   K3 compaction    an order-preserving compaction writes every centre
+//                    with key > K*, plus the first `need` with key == K*
+//                    in raster order, to the output in raster order.
+// Ties are therefore ranked by raster index and the result is
+// deterministic.
+#include <math.h>
+
+#include "nrr_internal.h"
+
+namespace nrr {
+namespace {
+
+constexpr int KEY_THREADS = 256;
+constexpr int HIST_BINS = 2048;
+constexpr int HIST_THREADS = 512;
+constexpr int PICK_THREADS = 1024;
+constexpr int CMP_THREADS = 1024;
+constexpr int CMP_ITEMS = 4;
+constexpr int CMP_CHUNK = CMP_THREADS * CMP_ITEMS;
+constexpr int NPASS = 5;
+__constant__ int c_shift[NPASS] = {42, 31, 20, 9, 0};
+__constant__ int c_width[NPASS] = {11, 11, 11, 11, 9};
+
+struct SelState {
+    unsigned long long nc;    // candidates
+    unsigned long long npos;  // candidates with key > 0
+    long long prefix;         // digits fixed so far
+    long long kth;            // rank still to find inside the current bucket (1-based)
+    long long nsel;           // number selected
+    long long thresh;         // key of the nsel-th largest (K*)
+    long long need_ties;      // how many keys equal to K* are selected
+    int done;                 // nothing (more) to select
+};
+
+template <int B>
+__global__ void __launch_bounds__(KEY_THREADS) grid_keys_kernel(const uint16_t *__restrict__ preop,
+                                                                const uint8_t *__restrict__ mask, int nx, int ny,
+                                                                int nz, int stride, int gx, int gy, long long ng,
+                                                                long long *__restrict__ keys, SelState *st)
+{
+    constexpr int H = (B - 1) / 2;
+    constexpr long long N = (long long)B * B * B;
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int cand = 0, pos = 0;
+    if (g < ng) {
+        const int i = (int)(g % gx), j = (int)((g / gx) % gy), k = (int)(g / ((long long)gx * gy));
+        const int x = i * stride, y = j * stride, z = k * stride;
+        long long key = -1;
+        if (x >= H && y >= H && z >= H && x <= nx - 1 - H && y <= ny - 1 - H && z <= nz - 1 - H &&
+            mask[((size_t)z * ny + y) * nx + x] != 0) {
+            unsigned int s = 0;
+            unsigned long long q = 0;
+            for (int kz = -H; kz <= H; ++kz)
+                for (int ky = -H; ky <= H; ++ky) {
+                    const uint16_t *row = preop + ((size_t)(z + kz) * ny + (y + ky)) * nx + (x - H);
+                    unsigned int rs = 0;
+                    unsigned long long rq = 0;
+#pragma unroll
+                    for (int kx = 0; kx < B; ++kx) {
+                        unsigned int v = __ldg(row + kx);
+                        rs += v;
+                        rq += (unsigned long long)(v * v);
+                    }
+                    s += rs;
+                    q += rq;
+                }
+            key = N * (long long)q - (long long)s * (long long)s;
+            cand = 1;
+            pos = key > 0;
+        }
+        keys[g] = key;
+    }
+    // block reduction of the two counts
+    __shared__ int ws[KEY_THREADS / 32][2];
+    unsigned m = 0xffffffffu;
+    for (int o = 16; o; o >>= 1) {
+        cand += __shfl_xor_sync(m, cand, o);
+        pos += __shfl_xor_sync(m, pos, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        ws[threadIdx.x >> 5][0] = cand;
+        ws[threadIdx.x >> 5][1] = pos;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int c = 0, p = 0;
+        for (int w = 0; w < KEY_THREADS / 32; ++w) {
+            c += ws[w][0];
+            p += ws[w][1];
+        }
+        if (c) atomicAdd(&st->nc, (unsigned long long)c);
+        if (p) atomicAdd(&st->npos, (unsigned long long)p);
+    }
+}
+
+// Histogram of digit `pass` over the keys that match the prefix fixed so far.
+__global__ void __launch_bounds__(HIST_THREADS) radix_hist_kernel(const long long *__restrict__ keys, long long ng,
+                                                                  int pass, const SelState *st,
+                                                                  unsigned int *__restrict__ hist)
+{
+    __shared__ unsigned int h[HIST_BINS];
+    if (st->done) return;
+    for (int i = threadIdx.x; i < HIST_BINS; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const int sh = c_shift[pass], w = c_width[pass];
+    const long long hi = st->prefix >> (sh + w);
+    const long long dmask = (1ll << w) - 1;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += (long long)gridDim.x * blockDim.x) {
+        const long long k = keys[g];
+        if (k > 0 && (k >> (sh + w)) == hi) atomicAdd(&h[(k >> sh) & dmask], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < HIST_BINS; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[pass * HIST_BINS + i], h[i]);
+}
+
+// Pick the bucket holding the kth largest key; fix its digit.
+__global__ void __launch_bounds__(PICK_THREADS) radix_pick_kernel(int pass, double frac, SelState *st,
+                                                                  const unsigned int *__restrict__ hist)
+{
+    __shared__ long long wsum[PICK_THREADS / 32];
+    __shared__ long long s_kth;
+    if (threadIdx.x == 0) {
+        if (pass == 0) {
+            // n_sel = floor(0.5 + N_c * F_s), capped at the keys > 0 (Sec. 4.1)
+            long long ns = (long long)floor(__dadd_rn(0.5, __dmul_rn((double)st->nc, frac)));
+            if (ns > (long long)st->npos) ns = (long long)st->npos;
+            if (ns < 0) ns = 0;
+            st->nsel = ns;
+            st->kth = ns;
+            st->prefix = 0;
+            if (ns == 0) {
+                st->done = 1;
+                st->thresh = 0x7fffffffffffffffll;
+                st->need_ties = 0;
+            }
+        }
+        s_kth = st->kth;
+    }
+    __syncthreads();
+    if (st->done) return;
+    const long long kth = s_kth;
+    const int w = c_width[pass], nb = 1 << w;
+    // thread t owns reversed bins r = 2t, 2t+1 (bin b = nb-1-r): inclusive
+    // scan over r gives the number of keys in bins >= b.
+    const int t = threadIdx.x;
+    long long c0 = 0, c1 = 0;
+    int b0 = nb - 1 - 2 * t, b1 = nb - 2 - 2 * t;
+    if (b0 >= 0) c0 = hist[pass * HIST_BINS + b0];
+    if (b1 >= 0) c1 = hist[pass * HIST_BINS + b1];
+    long long v = c0 + c1, incl = v;
+    const int lane = t & 31, wp = t >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        long long n = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += n;
+    }
+    if (lane == 31) wsum[wp] = incl;
+    __syncthreads();
+    long long before = 0;
+    for (int i = 0; i < wp; ++i) before += wsum[i];
+    const long long excl = before + incl - v;  // keys in bins > b0
+    const long long ge0 = excl + c0, ge1 = ge0 + c1;
+    int pick = -1;
+    long long above = 0;
+    if (b0 >= 0 && excl < kth && ge0 >= kth) {
+        pick = b0;
+        above = excl;
+    } else if (b1 >= 0 && ge0 < kth && ge1 >= kth) {
+        pick = b1;
+        above = ge0;
+    }
+    if (pick >= 0) {
+        const int sh = c_shift[pass];
+        const long long pre = st->prefix | ((long long)pick << sh);
+        st->prefix = pre;
+        st->kth = kth - above;
+        if (pass == NPASS - 1) {
+            st->thresh = pre;
+            st->need_ties = kth - above;
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned long long block_excl_scan_u64(unsigned long long v, unsigned long long *tot)
+{
+    __shared__ unsigned long long ws[CMP_THREADS / 32];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    unsigned long long incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long n = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += n;
+    }
+    if (lane == 31) ws[wp] = incl;
+    __syncthreads();
+    unsigned long long before = 0, all = 0;
+    for (int i = 0; i < CMP_THREADS / 32; ++i) {
+        if (i < wp) before += ws[i];
+        all += ws[i];
+    }
+    if (tot) *tot = all;
+    return before + incl - v;
+}
+
+// Per-chunk counts of keys > K* (high word) and == K* (low word).
+__global__ void __launch_bounds__(CMP_THREADS) compact_count_kernel(const long long *__restrict__ keys, long long ng,
+                                                                    const SelState *st,
+                                                                    unsigned long long *__restrict__ cnt)
+{
+    const long long th = st->thresh;
+    const long long base = (long long)blockIdx.x * CMP_CHUNK + (long long)threadIdx.x * CMP_ITEMS;
+    unsigned long long v = 0;
+#pragma unroll
+    for (int i = 0; i < CMP_ITEMS; ++i) {
+        const long long g = base + i;
+        if (g < ng) {
+            const long long k = keys[g];
+            if (k > th) v += 1ull << 32;
+            else if (k == th) v += 1ull;
+        }
+    }
+    unsigned long long tot;
+    block_excl_scan_u64(v, &tot);
+    if (threadIdx.x == 0) cnt[blockIdx.x] = tot;
+}
+
+// Exclusive scan of the per-chunk counts (one CTA, any number of chunks).
+__global__ void __launch_bounds__(CMP_THREADS) compact_scan_kernel(unsigned long long *cnt, int nchunks)
+{
+    __shared__ unsigned long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b = 0; b < nchunks; b += CMP_THREADS) {
+        const int i = b + threadIdx.x;
+        const unsigned long long v = i < nchunks ? cnt[i] : 0ull;
+        unsigned long long tot;
+        const unsigned long long ex = block_excl_scan_u64(v, &tot);
+        const unsigned long long c = carry;
+        if (i < nchunks) cnt[i] = c + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry = c + tot;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(CMP_THREADS) compact_write_kernel(const long long *__restrict__ keys, long long ng,
+                                                                    int gx, int gy, int stride, const SelState *st,
+                                                                    const unsigned long long *__restrict__ off,
+                                                                    int32_t *__restrict__ centers, int max_blocks,
+                                                                    int32_t *d_n_selected)
+{
+    const long long th = st->thresh, need = st->need_ties;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && d_n_selected) *d_n_selected = (int32_t)st->nsel;
+    const long long base = (long long)blockIdx.x * CMP_CHUNK + (long long)threadIdx.x * CMP_ITEMS;
+    long long k[CMP_ITEMS];
+    unsigned long long v = 0;
+#pragma unroll
+    for (int i = 0; i < CMP_ITEMS; ++i) {
+        const long long g = base + i;
+        k[i] = g < ng ? keys[g] : -1;
+        if (k[i] > th) v += 1ull << 32;
+        else if (k[i] == th) v += 1ull;
+    }
+    const unsigned long long ex = block_excl_scan_u64(v, nullptr) + off[blockIdx.x];
+    long long sb = (long long)(ex >> 32), tb = (long long)(ex & 0xffffffffull);
+#pragma unroll
+    for (int i = 0; i < CMP_ITEMS; ++i) {
+        const long long g = base + i;
+        bool sel = false;
+        long long pos = 0;
+        if (k[i] > th) {
+            sel = true;
+            pos = sb + (tb < need ? tb : need);
+            ++sb;
+        } else if (k[i] == th) {
+            if (tb < need) {
+                sel = true;
+                pos = sb + tb;
+            }
+            ++tb;
+        }
+        if (sel && pos < max_blocks) {
+            const int x = (int)(g % gx), y = (int)((g / gx) % gy), z = (int)(g / ((long long)gx * gy));
+            centers[3 * pos + 0] = x * stride;
+            centers[3 * pos + 1] = y * stride;
+            centers[3 * pos + 2] = z * stride;
+        }
+    }
+}
+
+template <int B>
+void launch_keys(const uint16_t *preop, const uint8_t *mask, nrr_dims d, int stride, int gx, int gy, long long ng,
+                 long long *keys, SelState *st, cudaStream_t s)
+{
+    const unsigned grid = (unsigned)((ng + KEY_THREADS - 1) / KEY_THREADS);
+    grid_keys_kernel<B><<<grid, KEY_THREADS, 0, s>>>(preop, mask, d.nx, d.ny, d.nz, stride, gx, gy, ng, keys, st);
+}
+
+}  // namespace
+
+struct SelectPlan {
+    int gx, gy, gz;
+    long long ng;
+    int nchunks;
+    size_t off_keys, off_hist, off_state, off_cnt, bytes;
+};
+
+static SelectPlan select_plan(nrr_dims d, int stride)
+{
+    SelectPlan p;
+    p.gx = (d.nx + stride - 1) / stride;
+    p.gy = (d.ny + stride - 1) / stride;
+    p.gz = (d.nz + stride - 1) / stride;
+    p.ng = (long long)p.gx * p.gy * p.gz;
+    p.nchunks = (int)((p.ng + CMP_CHUNK - 1) / CMP_CHUNK);
+    size_t o = 0;
+    p.off_keys = o;
+    o += align_up((size_t)p.ng * 8, 256);
+    p.off_hist = o;
+    o += align_up(sizeof(unsigned int) * HIST_BINS * NPASS, 256);
+    p.off_state = o;
+    o += align_up(sizeof(SelState), 256);
+    p.off_cnt = o;
+    o += align_up((size_t)p.nchunks * 8, 256);
+    p.bytes = o;
+    return p;
+}
+
+// Enqueue the whole selection on `s` using the scratch buffer `ws` (at least
+// select_plan().bytes, 256-byte aligned).  Reads nothing back.
+static nrr_status enqueue_select(const uint16_t *preop, const uint8_t *mask, nrr_dims d, int block, int stride,
+                                 double frac, int32_t *centers, int32_t max_blocks, int32_t *d_n_selected,
+                                 unsigned char *ws, const SelectPlan &p, cudaStream_t s)
+{
+    long long *keys = (long long *)(ws + p.off_keys);
+    unsigned int *hist = (unsigned int *)(ws + p.off_hist);
+    SelState *st = (SelState *)(ws + p.off_state);
+    unsigned long long *cnt = (unsigned long long *)(ws + p.off_cnt);
+    NRR_CUDA_TRY(cudaMemsetAsync(ws + p.off_hist, 0, p.off_cnt - p.off_hist, s));
+    switch (block) {
+    case 3: launch_keys<3>(preop, mask, d, stride, p.gx, p.gy, p.ng, keys, st, s); break;
+    case 5: launch_keys<5>(preop, mask, d, stride, p.gx, p.gy, p.ng, keys, st, s); break;
+    case 7: launch_keys<7>(preop, mask, d, stride, p.gx, p.gy, p.ng, keys, st, s); break;
+    case 9: launch_keys<9>(preop, mask, d, stride, p.gx, p.gy, p.ng, keys, st, s); break;
+    default: launch_keys<11>(preop, mask, d, stride, p.gx, p.gy, p.ng, keys, st, s); break;
+    }
+    long long hgrid = (p.ng + HIST_THREADS * 8 - 1) / (HIST_THREADS * 8);
+    if (hgrid > 4 * sm_count()) hgrid = 4 * sm_count();
+    if (hgrid < 1) hgrid = 1;
+    for (int pass = 0; pass < NPASS; ++pass) {
+        radix_hist_kernel<<<(unsigned)hgrid, HIST_THREADS, 0, s>>>(keys, p.ng, pass, st, hist);
+        radix_pick_kernel<<<1, PICK_THREADS, 0, s>>>(pass, frac, st, hist);
+    }
+    compact_count_kernel<<<p.nchunks, CMP_THREADS, 0, s>>>(keys, p.ng, st, cnt);
+    compact_scan_kernel<<<1, CMP_THREADS, 0, s>>>(cnt, p.nchunks);
+    compact_write_kernel<<<p.nchunks, CMP_THREADS, 0, s>>>(keys, p.ng, p.gx, p.gy, stride, st, cnt, centers,
+                                                          max_blocks, d_n_selected);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "selection kernel launch");
+    return NRR_OK;
+}
+
+}  // namespace nrr
+
+using namespace nrr;
+
+extern "C" nrr_status nrr_select_blocks(const uint16_t *d_preop, const uint8_t *d_mask, nrr_dims dims, int32_t block,
+                                        int32_t stride, double frac, int32_t *d_centers, int32_t max_blocks,
+                                        int32_t *d_n_selected, int32_t *h_n_selected, void *stream)
+{
+    clear_error();
+    nrr_status st = check_dims(dims, NRR_U16, block);
+    if (st != NRR_OK) return st;
+    if (stride < 1 || stride > 64) return fail(NRR_E_INVALID, "stride %d outside 1..64", stride);
+    if (!(frac > 0.0 && frac <= 1.0)) return fail(NRR_E_INVALID, "frac must be in (0, 1]");
+    if (max_blocks < 0) return fail(NRR_E_INVALID, "max_blocks < 0");
+    if (!d_preop || !d_mask) return fail(NRR_E_INVALID, "NULL volume or mask");
+    if (max_blocks > 0 && !d_centers) return fail(NRR_E_INVALID, "NULL centre buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    const SelectPlan p = select_plan(dims, stride);
+    void *ws = nullptr;
+    NRR_CUDA_TRY(cudaMallocAsync(&ws, p.bytes, s));
+    st = enqueue_select(d_preop, d_mask, dims, block, stride, frac, d_centers, max_blocks, d_n_selected,
+                        (unsigned char *)ws, p, s);
+    long long nsel = 0;
+    if (st == NRR_OK && h_n_selected) {
+        cudaError_t e = cudaMemcpyAsync(&nsel, (unsigned char *)ws + p.off_state + offsetof(SelState, nsel),
+                                        sizeof(nsel), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_fail(e, "reading the selection count");
+    }
+    cudaError_t e = cudaFreeAsync(ws, s);
+    if (st != NRR_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync");
+    if (h_n_selected) {
+        *h_n_selected = (int32_t)nsel;
+        if (nsel > max_blocks)
+            return fail(NRR_E_CAPACITY, "%lld blocks selected but max_blocks is %d", nsel, max_blocks);
+    }
+    return NRR_OK;
+}

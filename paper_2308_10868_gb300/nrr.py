@@ -1,0 +1,210 @@
+"""Python binding of ``libnrr.so`` (the C ABI in include/nrr.h).
+
+Argument marshalling only: every step of selection and matching runs in the
+library's CUDA kernels.  PyTorch supplies device memory and the current
+stream.  There is no CPU fallback: if the library has not been built, or a
+call is made without a CUDA device, the call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libnrr.so")
+
+NRR_OK, NRR_PENDING = 0, 1
+NRR_U16, NRR_F32 = 0, 1
+
+# Every entry point declared in include/nrr.h, with its ctypes signature.
+_P = C.c_void_p
+_I32 = C.c_int32
+
+
+class Dims(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32)]
+
+
+SIGNATURES = {
+    "nrr_status_string": (C.c_char_p, [C.c_int]),
+    "nrr_last_error": (C.c_char_p, []),
+    "nrr_version": (_I32, []),
+    "nrr_select_blocks": (C.c_int, [_P, _P, Dims, _I32, _I32, C.c_double, _P, _I32, _P, _P, _P]),
+    "nrr_boxsum_bytes": (C.c_int, [Dims, C.c_int, C.POINTER(C.c_size_t)]),
+    "nrr_boxsums": (C.c_int, [_P, C.c_int, Dims, _I32, _P, _P]),
+    "nrr_block_match": (C.c_int, [_P, _P, C.c_int, Dims, _P, _I32, _P, _I32, _P, _P, _P, _P, _P]),
+    "nrr_block_match_bs": (C.c_int, [_P, _P, _P, C.c_int, Dims, _P, _I32, _P, _I32, _P, _P, _P, _P, _P]),
+    "nrr_device_status": (C.c_int, [_P]),
+}
+
+_lib = None
+
+
+class NrrError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: status {status} ({detail})")
+        self.status = status
+
+
+def lib():
+    """Load libnrr.so; raise if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2308_10868_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status < 0:
+        L = lib()
+        detail = L.nrr_last_error().decode() or L.nrr_status_string(status).decode()
+        raise NrrError(status, where, detail)
+    return status
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _dims(vol: torch.Tensor) -> Dims:
+    nz, ny, nx = vol.shape
+    return Dims(nx, ny, nz)
+
+
+def _dtype_code(vol: torch.Tensor) -> int:
+    if vol.dtype == torch.float32:
+        return NRR_F32
+    if vol.dtype in (torch.uint16, torch.int16):  # int16 = same bits, reinterpreted
+        return NRR_U16
+    raise TypeError(f"volumes must be uint16 (or int16 bit-views) or float32, got {vol.dtype}")
+
+
+def _cuda_contig(t: torch.Tensor, name: str):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def radius3(radius):
+    if isinstance(radius, int):
+        return (radius, radius, radius)
+    r = tuple(int(v) for v in radius)
+    if len(r) != 3:
+        raise ValueError("radius must be an int or 3 ints")
+    return r
+
+
+def max_selected(dims, stride: int, frac: float) -> int:
+    """Upper bound on the number of blocks selection can return."""
+    nx, ny, nz = dims
+    ng = math.ceil(nx / stride) * math.ceil(ny / stride) * math.ceil(nz / stride)
+    return int(math.floor(0.5 + ng * frac))
+
+
+def select_blocks(preop: torch.Tensor, mask: torch.Tensor, block: int, stride: int, frac: float,
+                  max_blocks: int | None = None, centers: torch.Tensor | None = None,
+                  n_selected: torch.Tensor | None = None, sync: bool = True, stream=None):
+    """Variance-based block selection.  Returns the (n, 3) int32 centres
+    (x, y, z) in raster order.  With ``sync=False`` nothing is read back:
+    the full ``centers`` buffer and the device count ``n_selected`` are
+    returned instead."""
+    _cuda_contig(preop, "preop")
+    _cuda_contig(mask, "mask")
+    if _dtype_code(preop) != NRR_U16:
+        raise TypeError("selection takes a uint16 volume")
+    if mask.dtype not in (torch.uint8, torch.bool) or mask.shape != preop.shape:
+        raise ValueError("mask must be uint8/bool with the volume's shape")
+    dims = _dims(preop)
+    if max_blocks is None:
+        max_blocks = max_selected((dims.nx, dims.ny, dims.nz), stride, frac)
+    if centers is None:
+        centers = torch.empty((max(1, max_blocks), 3), dtype=torch.int32, device=preop.device)
+    if n_selected is None:
+        n_selected = torch.zeros(1, dtype=torch.int32, device=preop.device)
+    h = C.c_int32(0)
+    st = lib().nrr_select_blocks(_ptr(preop), _ptr(mask), dims, block, stride, float(frac), _ptr(centers),
+                                 max_blocks, _ptr(n_selected), C.byref(h) if sync else None, _stream(stream))
+    _check(st, "nrr_select_blocks")
+    if sync:
+        return centers[:h.value]
+    return centers, n_selected
+
+
+def boxsum_bytes(vol: torch.Tensor) -> int:
+    n = C.c_size_t(0)
+    _check(lib().nrr_boxsum_bytes(_dims(vol), _dtype_code(vol), C.byref(n)), "nrr_boxsum_bytes")
+    return int(n.value)
+
+
+def boxsums(intraop: torch.Tensor, block: int, out: torch.Tensor | None = None, stream=None):
+    """Box sums S_J, S_JJ of the reference volume for one block size (an
+    opaque uint8 device buffer for :func:`block_match`)."""
+    _cuda_contig(intraop, "intraop")
+    nbytes = boxsum_bytes(intraop)
+    if out is None:
+        out = torch.empty(nbytes + 256, dtype=torch.uint8, device=intraop.device)
+    off = (-out.data_ptr()) % 256
+    buf = out[off:off + nbytes]
+    _check(lib().nrr_boxsums(_ptr(intraop), _dtype_code(intraop), _dims(intraop), block, _ptr(buf),
+                             _stream(stream)), "nrr_boxsums")
+    return buf
+
+
+def block_match(preop: torch.Tensor, intraop: torch.Tensor, centers: torch.Tensor, block: int, radius,
+                n_blocks: torch.Tensor | None = None, box: torch.Tensor | None = None, out=None, stream=None):
+    """Exhaustive NCC block matching.  Returns (disp int32 (n,3), ncc f64 (n,),
+    valid uint8 (n,)).  ``n_blocks`` is an optional device int32 count
+    (<= len(centers)); ``box`` optional precomputed box sums."""
+    for t, nm in ((preop, "preop"), (intraop, "intraop"), (centers, "centers")):
+        _cuda_contig(t, nm)
+    if preop.shape != intraop.shape or preop.dtype != intraop.dtype:
+        raise ValueError("preop and intraop must have the same shape and dtype")
+    if centers.dtype != torch.int32 or centers.dim() != 2 or centers.shape[1] != 3:
+        raise ValueError("centers must be int32 (n, 3)")
+    n = centers.shape[0]
+    dev = preop.device
+    if out is None:
+        out = (torch.empty((n, 3), dtype=torch.int32, device=dev), torch.empty(n, dtype=torch.float64, device=dev),
+               torch.empty(n, dtype=torch.uint8, device=dev))
+    disp, ncc, valid = out
+    r = (C.c_int32 * 3)(*radius3(radius))
+    L = lib()
+    if box is None:
+        st = L.nrr_block_match(_ptr(preop), _ptr(intraop), _dtype_code(preop), _dims(preop), _ptr(centers), n,
+                               _ptr(n_blocks), block, r, _ptr(disp), _ptr(ncc), _ptr(valid), _stream(stream))
+    else:
+        st = L.nrr_block_match_bs(_ptr(preop), _ptr(intraop), _ptr(box), _dtype_code(preop), _dims(preop),
+                                  _ptr(centers), n, _ptr(n_blocks), block, r, _ptr(disp), _ptr(ncc), _ptr(valid),
+                                  _stream(stream))
+    _check(st, "nrr_block_match")
+    return disp, ncc, valid
+
+
+def device_status(stream=None) -> int:
+    """Wait for the stream; raise if a kernel reported a timeout or failed
+    check since the last call."""
+    return _check(lib().nrr_device_status(_stream(stream)), "nrr_device_status")
+
+
+def to_device_u16(a, device="cuda") -> torch.Tensor:
+    """uint16 numpy array -> CUDA tensor holding the same bits."""
+    import numpy as np
+
+    a = np.ascontiguousarray(a, dtype=np.uint16)
+    return torch.from_numpy(a.view(np.int16)).to(device)

@@ -1,0 +1,82 @@
+"""The C-ABI library builds, loads without a GPU, exports every entry point
+declared in include/nrr.h and rejects bad arguments before touching the
+device (CPU only: no compute call is made)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2308_10868_gb300 import build as nbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    nbuild.build()
+    from paper_2308_10868_gb300 import nrr
+
+    return nrr.lib()
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(nrr_[a-z0-9_]+)\s*\(", text))
+    return names
+
+
+def test_every_declared_symbol_is_exported(L):
+    from paper_2308_10868_gb300 import nrr
+
+    names = _declared()
+    assert {"nrr_select_blocks", "nrr_block_match", "nrr_status_string"} <= names
+    for n in sorted(names):
+        assert hasattr(L, n), f"{n} not exported"
+    # the binding declares a signature for every entry point
+    assert names <= set(nrr.SIGNATURES), sorted(names - set(nrr.SIGNATURES))
+
+
+def test_status_strings_and_version(L):
+    assert L.nrr_status_string(0) == b"ok"
+    assert L.nrr_status_string(-1) == b"invalid argument"
+    assert L.nrr_status_string(12345) == b"unknown status"
+    assert L.nrr_version() >= 100
+
+
+def test_argument_checks_need_no_device(L):
+    from paper_2308_10868_gb300 import nrr
+
+    d = nrr.Dims(64, 64, 48)
+    n = C.c_size_t(0)
+    assert L.nrr_boxsum_bytes(d, 0, C.byref(n)) == 0 and n.value >= 64 * 64 * 48 * 12
+    assert L.nrr_boxsum_bytes(nrr.Dims(63, 64, 48), 0, C.byref(n)) == -1  # nx*2 not a multiple of 16
+    assert b"multiple of 16" in L.nrr_last_error()
+    assert L.nrr_boxsum_bytes(nrr.Dims(64, 64, 48), 7, C.byref(n)) == -1  # bad dtype
+    fake = C.c_void_p(1 << 20)
+    # even block size, radius out of range, bad fraction, bad stride
+    assert L.nrr_select_blocks(fake, fake, d, 6, 2, 0.1, fake, 10, None, None, None) == -1
+    assert L.nrr_select_blocks(fake, fake, d, 7, 0, 0.1, fake, 10, None, None, None) == -1
+    assert L.nrr_select_blocks(fake, fake, d, 7, 2, 0.0, fake, 10, None, None, None) == -1
+    assert L.nrr_select_blocks(fake, fake, d, 7, 2, 1.5, fake, 10, None, None, None) == -1
+    r = (C.c_int32 * 3)(4, 8, 4)
+    assert L.nrr_block_match(fake, fake, 0, d, fake, 5, None, 7, r, fake, fake, fake, None) == -1
+    assert b"radius" in L.nrr_last_error()
+    r = (C.c_int32 * 3)(4, 4, 4)
+    assert L.nrr_block_match(fake, fake, 0, d, fake, 5, None, 13, r, fake, fake, fake, None) == -1
+    assert L.nrr_block_match(None, fake, 0, d, fake, 5, None, 7, r, fake, fake, fake, None) == -1
+    assert L.nrr_block_match(fake, fake, 0, nrr.Dims(64, 64, 4), fake, 5, None, 7, r, fake, fake, fake, None) == -1
+
+
+def test_binding_refuses_cpu_tensors():
+    import torch
+
+    from paper_2308_10868_gb300 import nrr
+
+    v = torch.zeros((8, 8, 8), dtype=torch.int16)
+    with pytest.raises(ValueError):
+        nrr.select_blocks(v, torch.zeros((8, 8, 8), dtype=torch.uint8), 3, 2, 0.1)
