@@ -86,6 +86,10 @@ const char *nrr_last_error(void);
 /* Library ABI version (major * 100 + minor). */
 int32_t nrr_version(void);
 
+/* Number of CUDA kernels this library has launched in this process so far
+ * (instrumentation for benchmarks and tests). */
+int64_t nrr_kernel_launches(void);
+
 /* ------------------------------------------------------------------------
  * Block selection (Sec. 4.1, "Parallel feature selection").
  *

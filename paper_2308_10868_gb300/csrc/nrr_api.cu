@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "nrr_internal.h"
@@ -49,6 +50,10 @@ nrr_status device_error_word(unsigned int **ptr)
     *ptr = addr[dev];
     return NRR_OK;
 }
+
+static std::atomic<long long> g_launches{0};
+
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 int sm_count()
 {
@@ -148,6 +153,8 @@ const char *nrr_status_string(nrr_status s)
 const char *nrr_last_error(void) { return g_last_error; }
 
 int32_t nrr_version(void) { return 100; }
+
+int64_t nrr_kernel_launches(void) { return nrr::g_launches.load(std::memory_order_relaxed); }
 
 nrr_status nrr_device_status(void *stream)
 {

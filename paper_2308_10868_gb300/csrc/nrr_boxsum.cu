@@ -156,6 +156,7 @@ nrr_status launch_boxsums(const void *d_intraop, nrr_dtype dtype, nrr_dims dims,
         launch_t<uint16_t>(d_intraop, dims, block, d_boxsums, off2, stream);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "boxsum kernel launch");
+    count_launches(1);
     return NRR_OK;
 }
 

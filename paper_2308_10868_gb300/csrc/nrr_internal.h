@@ -35,6 +35,9 @@ nrr_status encode_volume_map(CUtensorMap *map, const void *base, nrr_dtype dtype
 
 int sm_count();
 
+// Running count of kernel launches made by the library in this process.
+void count_launches(int n);
+
 // Common argument checks.
 nrr_status check_dims(nrr_dims dims, nrr_dtype dtype, int32_t block);
 inline size_t elem_size(nrr_dtype t) { return t == NRR_F32 ? 4 : 2; }

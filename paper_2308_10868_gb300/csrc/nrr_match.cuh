@@ -636,6 +636,7 @@ nrr_status launch_match_variant(const MatchLaunch &m, cudaStream_t stream)
     kern<<<(unsigned)grid, threads, L.total, stream>>>(p, map);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "match kernel launch");
+    count_launches(1);
     return NRR_OK;
 }
 

@@ -368,6 +368,7 @@ static nrr_status enqueue_select(const uint16_t *preop, const uint8_t *mask, nrr
                                                           max_blocks, d_n_selected);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "selection kernel launch");
+    count_launches(2 + 2 * NPASS + 2);
     return NRR_OK;
 }
 

@@ -32,6 +32,7 @@ SIGNATURES = {
     "nrr_status_string": (C.c_char_p, [C.c_int]),
     "nrr_last_error": (C.c_char_p, []),
     "nrr_version": (_I32, []),
+    "nrr_kernel_launches": (C.c_int64, []),
     "nrr_select_blocks": (C.c_int, [_P, _P, Dims, _I32, _I32, C.c_double, _P, _I32, _P, _P, _P]),
     "nrr_boxsum_bytes": (C.c_int, [Dims, C.c_int, C.POINTER(C.c_size_t)]),
     "nrr_boxsums": (C.c_int, [_P, C.c_int, Dims, _I32, _P, _P]),
@@ -194,6 +195,11 @@ def block_match(preop: torch.Tensor, intraop: torch.Tensor, centers: torch.Tenso
                                   _stream(stream))
     _check(st, "nrr_block_match")
     return disp, ncc, valid
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(lib().nrr_kernel_launches())
 
 
 def device_status(stream=None) -> int:
