@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark of the block-selection + NCC block-matching path on GB300.
+
+One step = the whole hot path on one synthetic volume pair already resident
+in device memory: variance block selection (keys, radix select, compaction),
+box sums of the reference volume, and exhaustive NCC block matching of every
+selected block.  Metric: NCC evaluations per second, one evaluation being
+one (block, shift) pair of the search (nominal count: selected blocks x
+(2R+1)^3).
+
+Default workload: the clinical-size single registration, 256x256x124 uint16
+phantom pair (40 Gaussians, smooth field max 8 voxels, noise sigma 30),
+ellipsoidal mask, blocks 7^3 on a stride-2 grid, top 5% by variance
+(~19.4k blocks), search radius 5 (1331 shifts).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torchrun) every rank runs an independent replica of
+the workload on its own GPU (the path has no exchange step); the reported
+value is all ranks' evaluations over the slowest rank's time.
+``--impl reference`` times the CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "NCC evals/s (block x shift)"
+UNIT = "evals/s"
+FP32_LANES_PER_SM = 128  # FFMA lanes per Blackwell SM
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="clinical")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _config(w, n_blocks=None, extra=None):
+    c = {"workload": w.name, "volume": "x".join(map(str, w.dims)) + " uint16", "block": w.block,
+         "stride": w.stride, "frac": w.frac, "radius": w.radius, "shifts": (2 * w.radius + 1) ** 3,
+         "phantom": f"40 Gaussians, field max {w.umax:g} vox, noise sigma {w.noise:g}, seed-fixed",
+         "l2": "flushed between timed steps (512 MiB write)"}
+    if n_blocks is not None:
+        c["n_blocks"] = int(n_blocks)
+    if extra:
+        c.update(extra)
+    return c
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "50"], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t_start: float, t_end: float):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = sorted(float(r[1]) for r in rows)
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": float(rows[0][2]), "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit()),
+                "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------
+# recorded ncu traffic of the match kernel (valid only for the same source)
+# --------------------------------------------------------------------------
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("nrr_match.cuh", "nrr_ptx.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2308_10868_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _recorded_traffic():
+    path = os.path.join(ROOT, "profiles", "match_kernel_clinical.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m1 = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+    m2 = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not (m1 and m2) or m1.group(1) != _kernel_source_hash():
+        return None
+    return float(m2.group(1))
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            return json.load(open(path))
+        except ValueError:
+            pass
+    return {}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timings (baseline only)
+# --------------------------------------------------------------------------
+def _oracle_step(w, pre, intra, mask, sample_every=1):
+    import oracle
+
+    t0 = time.perf_counter()
+    centers, _ = oracle.select_blocks(pre, mask, w.block, w.stride, w.frac)
+    sub = centers[::sample_every]
+    oracle.match(pre, intra, sub, w.block, w.radius)
+    dt = time.perf_counter() - t0
+    return len(sub) * (2 * w.radius + 1) ** 3, dt, len(centers)
+
+
+def _cpu_baseline(w, pre, intra, mask):
+    import oracle
+
+    oracle.build()
+    ev, dt, n = _oracle_step(w, pre, intra, mask)
+    return {"value": ev / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"whole workload: selection of {n} blocks + matching all of them ({ev} evals), "
+                      f"{dt:.2f} s, FP64 C oracle, OpenMP over blocks"}
+
+
+def run_reference(a):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2308_10868_gb300 import synth
+
+    oracle.build()
+    w = synth.WORKLOADS[a.workload]
+    pre, intra, mask = synth.workload_pair(a.workload)
+    for _ in range(a.warmup):
+        _oracle_step(w, pre, intra, mask, sample_every=4)
+    evs, tot, n = 0, 0.0, 0
+    for _ in range(a.steps):
+        ev, dt, n = _oracle_step(w, pre, intra, mask, sample_every=4)
+        evs += ev
+        tot += dt
+    v = evs / tot
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+            "config": _config(w, n, {"sample": "selection of all blocks + matching every 4th selected block"}),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "per step: full selection + matching every 4th selected block"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# the GPU path
+# --------------------------------------------------------------------------
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    from paper_2308_10868_gb300 import build as nbuild
+
+    nbuild.build()
+    from paper_2308_10868_gb300 import nrr, synth
+
+    w = synth.WORKLOADS[a.workload]
+    pre, intra, mask = synth.workload_pair(a.workload)
+    d_pre, d_intra = nrr.to_device_u16(pre, dev), nrr.to_device_u16(intra, dev)
+    d_mask = torch.from_numpy(mask).to(dev)
+    cap = nrr.max_selected(w.dims, w.stride, w.frac)
+    centers = torch.empty((cap, 3), dtype=torch.int32, device=dev)
+    n_sel = torch.zeros(1, dtype=torch.int32, device=dev)
+    out = (torch.empty((cap, 3), dtype=torch.int32, device=dev), torch.empty(cap, dtype=torch.float64, device=dev),
+           torch.empty(cap, dtype=torch.uint8, device=dev))
+    box_raw = torch.empty(nrr.boxsum_bytes(d_intra) + 256, dtype=torch.uint8, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(p, i, m, ev_match=None):
+        nrr.select_blocks(p, m, w.block, w.stride, w.frac, max_blocks=cap, centers=centers, n_selected=n_sel,
+                          sync=False)
+        box = nrr.boxsums(i, w.block, out=box_raw)
+        if ev_match is not None:
+            ev_match[0].record(stream)
+        nrr.block_match(p, i, centers, w.block, w.radius, n_blocks=n_sel, box=box, out=out)
+        if ev_match is not None:
+            ev_match[1].record(stream)
+
+    for _ in range(max(3, a.warmup)):
+        flush.fill_(1)
+        step(d_pre, d_intra, d_mask)
+    nrr.device_status()
+    n_blocks = int(n_sel.item())
+    evals = n_blocks * (2 * w.radius + 1) ** 3
+    valid_count = int(out[2][:n_blocks].sum().item())
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    evm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    l0 = nrr.kernel_launches()
+    with ClockSampler(local) as clk:
+        t_start = time.time()
+        for k in range(a.steps):
+            flush.fill_(k & 0xFF)
+            evs[k][0].record(stream)
+            step(d_pre, d_intra, d_mask, evm[k])
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        t_end = time.time()
+    launches = nrr.kernel_launches() - l0
+    nrr.device_status()
+    if pg:
+        pg.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in evs]
+    match_ms = [s.elapsed_time(e) for s, e in evm]
+    total_s = sum(step_ms) / 1e3
+    tmax = torch.tensor([total_s], dtype=torch.float64, device=dev)
+    if pg:
+        pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
+    total_s = float(tmax.item())
+    value = world * a.steps * evals / total_s
+
+    # ---- end to end through the public API with host buffers --------------
+    h_pre = torch.from_numpy(np.ascontiguousarray(pre).view(np.int16)).pin_memory()
+    h_intra = torch.from_numpy(np.ascontiguousarray(intra).view(np.int16)).pin_memory()
+    h_mask = torch.from_numpy(np.ascontiguousarray(mask)).pin_memory()
+    e_pre, e_intra, e_mask = torch.empty_like(d_pre), torch.empty_like(d_intra), torch.empty_like(d_mask)
+    h_out = (torch.empty((cap, 3), dtype=torch.int32).pin_memory(), torch.empty(cap, dtype=torch.float64).pin_memory(),
+             torch.empty(cap, dtype=torch.uint8).pin_memory(), torch.empty(1, dtype=torch.int32).pin_memory())
+    bi = h_pre.numel() * 2 + h_intra.numel() * 2 + h_mask.numel()
+    bo = sum(t.numel() * t.element_size() for t in h_out)
+    ke = max(10, min(a.steps, 100))
+    e2e_ms = []
+    for k in range(ke + 3):
+        flush.fill_(k & 0xFF)
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        e_pre.copy_(h_pre, non_blocking=True)
+        e_intra.copy_(h_intra, non_blocking=True)
+        e_mask.copy_(h_mask, non_blocking=True)
+        step(e_pre, e_intra, e_mask)
+        for h, d in zip(h_out, out + (n_sel,)):
+            h.copy_(d, non_blocking=True)
+        s1.record(stream)
+        s1.synchronize()
+        if k >= 3:
+            e2e_ms.append(s0.elapsed_time(s1))
+    assert int(h_out[3].item()) == n_blocks
+    e2e_value = world * evals / (sum(e2e_ms) / len(e2e_ms) / 1e3)
+
+    if rank != 0:
+        return 0
+
+    # ---- roofline of the dominant kernel (the match kernel) ---------------
+    peaks = _peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    match_s = sum(match_ms) / len(match_ms) / 1e3
+    flops = 2.0 * evals * w.block ** 3
+    achieved = flops / match_s / 1e12
+    traffic = _recorded_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1e3 * total_s / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u16", "data": "synthetic", "config": _config(w, n_blocks, {"parallelism": f"replicas x{world}"}),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": traffic,
+                     "kernel": "match_kernel (FP32 FFMA search + exact rescoring)",
+                     "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
+                                   f"{sm_max:.0f} MHz (max SM clock)",
+                     "match_ms": 1e3 * match_s},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
+        "gpu_launches": launches,
+        "gpu_launches_per_step": launches / a.steps,
+        "registrations_per_s": world * a.steps / total_s,
+        "valid_blocks": valid_count,
+        "clocks": clk.summary(t_start, t_end),
+    }
+    if world == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = _cpu_baseline(w, pre, intra, mask)
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
