@@ -1,27 +1,26 @@
 // NCC block-matching kernel (Sec. 3 NCC equation and O(B x W) bound;
 // Sec. 4.3 block-matching loop), written for sm_103a.
 //
-// One CTA processes one registration block at a time (persistent loop over
-// blocks).  Per block:
-//   1. One thread issues a TMA tiled load of the block's search window of
-//      the reference image, [c-h-R, c+h+R] per axis, into shared memory
-//      (x start rounded down to a 16-byte boundary; out-of-volume voxels
-//      arrive as zeros and are excluded below by coordinates).
-//   2. Meanwhile the CTA loads the floating block, reduces its sums and
-//      stores it mean-shifted (T_k = I_k - m) in shared memory.
-//   3. The window is converted to float, shifted by a per-block constant c
-//      (J'_k = J_k - c).
-//   4. Search: thread t owns one (dz, dy) line of the window and all
-//      2*rx+1 shifts along x; for every template row it loads one window row
-//      (vectorised 16-byte shared loads, conflict-free row pitch) and
-//      accumulates A(d) = sum_k T_k J'_{k+d} with FP32 FFMA, fully unrolled
-//      over the row and the x shifts.
-//   5. Every shift gets an approximate NCC from A(d) and the box sums S_J,
-//      S_JJ (precomputed, exact for uint16) together with a rigorous bound on
-//      its error (FFMA recursive-summation bound gamma_N * sum|T||J'|, with
+// A persistent CTA walks its share of the registration blocks.  Per block:
+//   1. TMA tiled loads bring the block's search window of the reference
+//      image, [c-h-R, c+h+R] per axis, and the floating block [c-h, c+h]^3
+//      into shared memory (x start rounded down to a 16-byte boundary;
+//      out-of-volume voxels arrive as zeros and are excluded by coordinates).
+//      The copy for the next block is issued as soon as the current one has
+//      been unpacked, so it lands while the current block is searched.
+//   2. Warp 0 reduces the floating block's sums; the other warps unpack the
+//      window to float, shifted by a per-block constant c (J'_k = J_k - c).
+//      The floating block is stored mean-shifted (T_k = I_k - m).
+//   3. Search: thread t owns one (dz, dy) line of the window and all 2*rx+1
+//      shifts along x; for every template row it loads one window row
+//      (16-byte shared loads, conflict-free row pitch) and accumulates
+//      A(d) = sum_k T_k J'_{k+d} with FP32 FFMA, fully unrolled over the row
+//      and the x shifts.
+//   4. Every shift gets an approximate NCC and a rigorous bound on its error
+//      (recursive-summation bound gamma_N * sum|T||J'| for the FFMA chain,
 //      Cauchy-Schwarz sum|T||J'| <= sqrt(sum T^2 * sum J'^2), plus the
 //      rounding of the final operations; doubled for margin).
-//   6. Shifts whose upper bound reaches the best lower bound survive (about
+//   5. Shifts whose upper bound reaches the best lower bound survive (about
 //      one per block on the phantoms) and are rescored by a warp each:
 //      uint16 -> exact int64 sum, then the canonical FP64 ratio
 //      num / sqrt(vI * vJ); float32 -> FP64 Pearson.  The best survivor
@@ -52,8 +51,9 @@ struct MatchParams {
     int32_t n_blocks;
     const int32_t *d_n_blocks;
     int ry, rz;
-    int bx;  // TMA box extent along x (elements)
-    int pf;  // row pitch of the float window (floats)
+    int bx;   // TMA box extent along x of the window (elements)
+    int btx;  // TMA box extent along x of the floating block (elements)
+    int pf;   // row pitch of the float window (floats)
     int32_t *disp;
     double *ncc;
     uint8_t *valid;
@@ -64,14 +64,23 @@ constexpr int MATCH_MAX_THREADS = 256;
 constexpr int MATCH_MAX_WARPS = MATCH_MAX_THREADS / 32;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s
 
+// Per-block constants produced by warp 0 and read by the whole CTA.
+struct BlockConst {
+    long long vI;   // uint16: N*S_II - S_I^2 (exact)
+    long long rr;   // uint16: N*m - S_I
+    double dvI;     // float32: sum (I - Ibar)^2
+    double ibar;    // float32: mean of I
+    float fvI;      // vI as float
+    float kq;       // uint16: N*gamma_N*sqrt(sum T^2); float32: sqrt(sum T^2) (rounded up)
+    float mu;       // float32: float mean used for T
+    float emu;      // float32: Ibar - mu
+    int m;          // uint16: integer mean used for T
+    int flat;       // floating block has zero variance
+};
+
 struct MatchScratch {
+    BlockConst bc;
     float wlb[MATCH_MAX_WARPS];
-    long long wsi[MATCH_MAX_WARPS];
-    unsigned long long wsii[MATCH_MAX_WARPS];
-    double wd1[MATCH_MAX_WARPS];
-    double wd2[MATCH_MAX_WARPS];
-    float wmin[MATCH_MAX_WARPS];
-    float wmax[MATCH_MAX_WARPS];
     double bs[MATCH_MAX_WARPS];
     int bn2[MATCH_MAX_WARPS];
     int bcode[MATCH_MAX_WARPS];
@@ -80,26 +89,26 @@ struct MatchScratch {
 };
 
 struct MatchLayout {
-    int u, f, t, iraw, surv, sc, bar, total;
+    int u, ut, f, t, surv, sc, bar, total;
 };
 
 __host__ __device__ inline int round_up_i(int v, int a) { return (v + a - 1) / a * a; }
 
 // Shared-memory carve-up of one CTA (all offsets 128-byte aligned).
-__host__ __device__ inline MatchLayout match_layout(int elem, int B, int P, int bx, int pf, int wy, int wz, int py,
-                                                   int pz, bool f32)
+__host__ __device__ inline MatchLayout match_layout(int elem, int B, int P, int bx, int btx, int pf, int wy, int wz,
+                                                   int py, int pz)
 {
     MatchLayout L;
     int pt = round_up_i(B, 4);
     int o = 0;
     L.u = o;
     o += round_up_i(bx * wy * wz * elem, 128);
+    L.ut = o;
+    o += round_up_i(btx * B * B * elem, 128);
     L.f = o;
     o += round_up_i(pf * wy * wz * 4, 128);
     L.t = o;
     o += round_up_i(B * B * pt * 4, 128);
-    L.iraw = o;
-    o += f32 ? round_up_i(B * B * B * 4, 128) : 0;
     L.surv = o;
     o += round_up_i(P * py * pz * 2, 128);
     L.sc = o;
@@ -157,6 +166,13 @@ __device__ __forceinline__ V warp_sum(V v)
     return v;
 }
 
+// Exact uint16 -> float of (u - c) for u, c < 2^16: 0x4B000000|u is the float
+// 2^23 + u, so one integer OR and one float subtraction suffice.
+__device__ __forceinline__ float u16_minus(uint32_t u, float c_plus_2p23)
+{
+    return __fsub_rn(__uint_as_float(0x4B000000u | u), c_plus_2p23);
+}
+
 __device__ __forceinline__ void write_result(const MatchParams &a, int blk, const Cand &b, int P, int py, int rx,
                                              int ry, int rz)
 {
@@ -176,9 +192,23 @@ __device__ __forceinline__ void write_result(const MatchParams &a, int blk, cons
     }
 }
 
+template <int H>
+__device__ __forceinline__ bool center_inside(int cx, int cy, int cz, int nx, int ny, int nz)
+{
+    return cx >= H && cy >= H && cz >= H && cx <= nx - 1 - H && cy <= ny - 1 - H && cz <= nz - 1 - H;
+}
+
+// Register budget: at most 80 registers per thread for blocks up to 7^3 and
+// up to 11 x-shifts (5-6 search CTAs of <= 128 threads per SM), 128 above.
+template <int B, int P>
+struct MatchMinBlocks {
+    static constexpr int value = (P <= 11 && B <= 7) ? 3 : 2;
+};
+
 template <typename T, int B, int P>
-__global__ void __launch_bounds__(MATCH_MAX_THREADS) match_kernel(const MatchParams a,
-                                                                  const __grid_constant__ CUtensorMap tmap)
+__global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value) match_kernel(const MatchParams a,
+                                                                  const __grid_constant__ CUtensorMap tmapJ,
+                                                                  const __grid_constant__ CUtensorMap tmapI)
 {
     constexpr bool F32 = std::is_same<T, float>::value;
     constexpr int H = (B - 1) / 2;
@@ -192,15 +222,15 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS) match_kernel(const MatchPar
     constexpr double GAMMA_N = (double)N * 5.9604644775390625e-08 / (1.0 - (double)N * 5.9604644775390625e-08);
 
     const int ry = a.ry, rz = a.rz, py = 2 * ry + 1, pz = 2 * rz + 1, lines = py * pz;
-    const int wy = B + 2 * ry, wz = B + 2 * rz, bx = a.bx, pf = a.pf;
+    const int wy = B + 2 * ry, wz = B + 2 * rz, bx = a.bx, btx = a.btx, pf = a.pf;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
 
     extern __shared__ __align__(128) unsigned char smem[];
-    const MatchLayout L = match_layout((int)sizeof(T), B, P, bx, pf, wy, wz, py, pz, F32);
+    const MatchLayout L = match_layout((int)sizeof(T), B, P, bx, btx, pf, wy, wz, py, pz);
     T *U = reinterpret_cast<T *>(smem + L.u);
+    T *Ut = reinterpret_cast<T *>(smem + L.ut);
     float *Fw = reinterpret_cast<float *>(smem + L.f);
     float *Tm = reinterpret_cast<float *>(smem + L.t);
-    float *Iraw = reinterpret_cast<float *>(smem + L.iraw);
     uint16_t *surv = reinterpret_cast<uint16_t *>(smem + L.surv);
     MatchScratch *sc = reinterpret_cast<MatchScratch *>(smem + L.sc);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);
@@ -211,137 +241,53 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS) match_kernel(const MatchPar
         int m = *a.d_n_blocks;
         n = m < 0 ? 0 : (m < n ? m : n);
     }
+    const uint32_t tx_bytes = (uint32_t)((bx * wy * wz + btx * B * B) * (int)sizeof(T));
+    // Thread 0 issues both copies of block b (its centre must be inside).
+    auto issue = [&](int b) {
+        const int cx = a.centers[3 * b + 0], cy = a.centers[3 * b + 1], cz = a.centers[3 * b + 2];
+        const int x0 = cx - H - RX, xt = cx - H;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar, tx_bytes);
+        tma_load_3d(U, &tmapJ, bar, x0 & ~(ALIGN - 1), cy - H - ry, cz - H - rz);
+        tma_load_3d(Ut, &tmapI, bar, xt & ~(ALIGN - 1), cy - H, cz - H);
+    };
     if (tid == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
     }
     __syncthreads();
     uint32_t phase = 0;
+    int inflight = -1;  // block whose copies are in flight (same value in every thread)
 
     for (int blk = blockIdx.x; blk < n; blk += gridDim.x) {
         const int cx = a.centers[3 * blk + 0], cy = a.centers[3 * blk + 1], cz = a.centers[3 * blk + 2];
-        const bool inside = cx >= H && cy >= H && cz >= H && cx <= nx - 1 - H && cy <= ny - 1 - H && cz <= nz - 1 - H;
-        if (!inside) {
+        if (!center_inside<H>(cx, cy, cz, nx, ny, nz)) {
             if (tid == 0) write_result(a, blk, Cand{0.0, 0, 0, 0}, P, py, RX, ry, rz);
             continue;
         }
-        const int x0 = cx - H - RX, y0 = cy - H - ry, z0 = cz - H - rz;
-        const int xs = x0 & ~(ALIGN - 1);  // floor to a 16-byte boundary (also for negative x0)
-        const int xo = x0 - xs;
-        if (tid == 0) {
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(bar, (uint32_t)(bx * wy * wz * (int)sizeof(T)));
-            tma_load_3d(U, &tmap, bar, xs, y0, z0);
-            sc->nsurv = 0;
+        if (inflight != blk) {
+            if (tid == 0) issue(blk);
+            inflight = blk;
         }
-
-        // ---- floating block: sums, mean shift, template in shared memory --
-        const T *pre = reinterpret_cast<const T *>(a.preop);
-        long long si_p = 0;
-        unsigned long long sii_p = 0;
-        double dsi_p = 0.0;
-        float mn = INFINITY, mx = -INFINITY;
-        for (int k = tid; k < B * B * PT; k += nthr) {
-            int kx = k % PT, kzy = k / PT, ky = kzy % B, kz = kzy / B;
-            float v = 0.f;
-            if (kx < B) {
-                T raw = pre[((size_t)(cz - H + kz) * ny + (cy - H + ky)) * nx + (cx - H + kx)];
-                if constexpr (F32) {
-                    v = raw;
-                    dsi_p += (double)raw;
-                    mn = fminf(mn, raw);
-                    mx = fmaxf(mx, raw);
-                    Iraw[(kz * B + ky) * B + kx] = raw;
-                } else {
-                    v = (float)raw;
-                    si_p += raw;
-                    sii_p += (unsigned long long)((uint32_t)raw * (uint32_t)raw);
-                }
-            }
-            Tm[k] = v;
-        }
-        if constexpr (F32) {
-            dsi_p = warp_sum(dsi_p);
-            mn = warp_min_f(mn);
-            mx = warp_max_f(mx);
-            if (lane == 0) {
-                sc->wd1[warp] = dsi_p;
-                sc->wmin[warp] = mn;
-                sc->wmax[warp] = mx;
-            }
-        } else {
-            si_p = warp_sum(si_p);
-            sii_p = warp_sum(sii_p);
-            if (lane == 0) {
-                sc->wsi[warp] = si_p;
-                sc->wsii[warp] = sii_p;
-            }
-        }
-        __syncthreads();
-
-        // per-block constants of the filter
-        float fvI, kq, c_f = 0.f, emu = 0.f, mu = 0.f;
-        long long vI = 0, rr = 0;
-        int c_i = 0;
-        double Ibar = 0.0, dvI = 0.0;
-        bool flatI;
+        const int x0 = cx - H - RX, xo = x0 - (x0 & ~(ALIGN - 1));
+        const int xt = cx - H, xot = xt - (xt & ~(ALIGN - 1));
         const size_t cidx = ((size_t)cz * ny + cy) * nx + cx;
+        // window centring constant from the box sum at the centre
+        float cshift;  // value subtracted (with 2^23 folded in for uint16)
+        int c_i = 0;
+        float c_f = 0.f;
         if constexpr (F32) {
-            double s = 0.0;
-            float lo = INFINITY, hi = -INFINITY;
-            for (int w = 0; w < nwarp; ++w) {
-                s += sc->wd1[w];
-                lo = fminf(lo, sc->wmin[w]);
-                hi = fmaxf(hi, sc->wmax[w]);
-            }
-            flatI = !(lo < hi);
-            Ibar = s / (double)N;
-            mu = (float)Ibar;
-            emu = (float)(Ibar - (double)mu);
             c_f = __fdiv_rn(reinterpret_cast<const float *>(a.s1)[cidx], (float)N);
+            cshift = c_f;
         } else {
-            long long s = 0;
-            unsigned long long q = 0;
-            for (int w = 0; w < nwarp; ++w) {
-                s += sc->wsi[w];
-                q += sc->wsii[w];
-            }
-            vI = (long long)N * (long long)q - s * s;
-            flatI = vI == 0;
-            long long m = (2 * s + N) / (2 * N);  // nearest integer to the block mean
-            rr = (long long)N * m - s;
-            long long qt = (long long)q - 2 * m * s + (long long)N * m * m;  // sum (I - m)^2, exact
-            fvI = (float)vI;
-            kq = (float)((double)N * GAMMA_N * sqrt((double)qt) * (1.0 + 1e-6));
-            long long s1c = reinterpret_cast<const int32_t *>(a.s1)[cidx];
+            const long long s1c = reinterpret_cast<const int32_t *>(a.s1)[cidx];
             c_i = (int)((2 * s1c + N) / (2 * N));
-            // shift the template by m (exact small integers in float)
-            for (int k = tid; k < B * B * PT; k += nthr)
-                if (k % PT < B) Tm[k] = Tm[k] - (float)m;
+            cshift = 8388608.0f + (float)c_i;
         }
-        if constexpr (F32) {
-            double dq_p = 0.0, dv_p = 0.0;
-            for (int k = tid; k < B * B * PT; k += nthr) {
-                if (k % PT < B) {
-                    float raw = Tm[k];
-                    float t = __fsub_rn(raw, mu);
-                    Tm[k] = t;
-                    dq_p += (double)t * (double)t;
-                    double dv = (double)raw - Ibar;
-                    dv_p += dv * dv;
-                }
-            }
-            dq_p = warp_sum(dq_p);
-            dv_p = warp_sum(dv_p);
-            __syncthreads();  // every thread has read wd1 above
-            if (lane == 0) {
-                sc->wd1[warp] = dq_p;
-                sc->wd2[warp] = dv_p;
-            }
-        }
+        if (tid == 0) sc->nsurv = 0;
 
-        // ---- wait for the window ----------------------------------------
-        bool got = mbar_wait_bounded(bar, phase, WAIT_LIMIT_NS);
+        // ---- wait for the window and the floating block ------------------
+        const bool got = mbar_wait_bounded(bar, phase, WAIT_LIMIT_NS);
         if (!__syncthreads_and(got)) {
             if (tid == 0) {
                 atomicOr(a.err, DEV_ERR_TIMEOUT);
@@ -351,55 +297,211 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS) match_kernel(const MatchPar
             return;
         }
         phase ^= 1u;
-        if constexpr (F32) {
-            double q = 0.0, v = 0.0;
-            for (int w = 0; w < nwarp; ++w) {
-                q += sc->wd1[w];
-                v += sc->wd2[w];
+
+        // ---- phase A: warp 0 reduces the floating block, the rest unpack ---
+        if (warp == 0) {
+            if constexpr (F32) {
+                constexpr int KPL = (N + 31) / 32;  // values per lane
+                constexpr int CH = KPL < 6 ? KPL : 6;   // loads in flight per lane
+                double s = 0.0;
+                float lo = INFINITY, hi = -INFINITY;
+#pragma unroll 1
+                for (int i0 = 0; i0 < KPL; i0 += CH) {
+                    float vals[CH];
+#pragma unroll
+                    for (int i = 0; i < CH; ++i) {
+                        const int k = lane + 32 * (i0 + i);
+                        const int kzy = k / B, kx = k - kzy * B;
+                        vals[i] = k < N ? Ut[kzy * btx + xot + kx] : NAN;
+                    }
+#pragma unroll
+                    for (int i = 0; i < CH; ++i) {
+                        if (lane + 32 * (i0 + i) < N) {
+                            s += (double)vals[i];
+                            lo = fminf(lo, vals[i]);
+                            hi = fmaxf(hi, vals[i]);
+                        }
+                    }
+                }
+                s = warp_sum(s);
+                lo = warp_min_f(lo);
+                hi = warp_max_f(hi);
+                const double ibar = s / (double)N;
+                const float mu = (float)ibar;
+                double q = 0.0, dv = 0.0;
+#pragma unroll 1
+                for (int i0 = 0; i0 < KPL; i0 += CH) {
+                    float vals[CH];
+#pragma unroll
+                    for (int i = 0; i < CH; ++i) {
+                        const int k = lane + 32 * (i0 + i);
+                        const int kzy = k / B, kx = k - kzy * B;
+                        vals[i] = k < N ? Ut[kzy * btx + xot + kx] : 0.f;
+                    }
+#pragma unroll
+                    for (int i = 0; i < CH; ++i) {
+                        if (lane + 32 * (i0 + i) < N) {
+                            const double t = (double)__fsub_rn(vals[i], mu);
+                            q = fma(t, t, q);
+                            const double d = (double)vals[i] - ibar;
+                            dv = fma(d, d, dv);
+                        }
+                    }
+                }
+                q = warp_sum(q);
+                dv = warp_sum(dv);
+                if (lane == 0) {
+                    BlockConst &c = sc->bc;
+                    c.flat = !(lo < hi);
+                    c.ibar = ibar;
+                    c.mu = mu;
+                    c.emu = (float)(ibar - (double)mu);
+                    c.dvI = dv;
+                    c.fvI = (float)dv;
+                    c.kq = (float)(sqrt(q) * (1.0 + 1e-6));
+                }
+            } else {
+                constexpr int KPL = (N + 31) / 32;  // values per lane
+                constexpr int CH = KPL < 6 ? KPL : 6;   // loads in flight per lane
+                long long s = 0;
+                unsigned long long q = 0;
+#pragma unroll 1
+                for (int i0 = 0; i0 < KPL; i0 += CH) {
+                    uint32_t vals[CH];
+#pragma unroll
+                    for (int i = 0; i < CH; ++i) {
+                        const int k = lane + 32 * (i0 + i);
+                        const int kzy = k / B, kx = k - kzy * B;
+                        vals[i] = k < N ? (uint32_t)Ut[kzy * btx + xot + kx] : 0u;
+                    }
+#pragma unroll
+                    for (int i = 0; i < CH; ++i) {
+                        s += vals[i];
+                        q += (unsigned long long)(vals[i] * vals[i]);
+                    }
+                }
+                s = warp_sum(s);
+                q = warp_sum(q);
+                if (lane == 0) {
+                    BlockConst &c = sc->bc;
+                    const long long vI = (long long)N * (long long)q - s * s;
+                    const long long m = (2 * s + N) / (2 * N);  // nearest integer to the block mean
+                    const long long qt = (long long)q - 2 * m * s + (long long)N * m * m;  // sum (I-m)^2, exact
+                    c.vI = vI;
+                    c.flat = vI == 0;
+                    c.m = (int)m;
+                    c.rr = (long long)N * m - s;
+                    c.fvI = (float)vI;
+                    c.kq = (float)((double)N * GAMMA_N * sqrt((double)qt) * (1.0 + 1e-6));
+                }
             }
-            dvI = v;
-            fvI = (float)v;
-            kq = (float)(sqrt(q) * (1.0 + 1e-6));  // sqrt(sum T^2), rounded up
         }
-        if (flatI) {  // flat floating block: NCC undefined for every shift
+        {
+            // Window rows: lanes along x, a warp takes RB rows at a time and
+            // issues all their loads before any store, so the shared-memory
+            // latency is paid once per batch rather than once per row.
+            constexpr int RB = 8;
+            const int rows = wz * wy;
+            for (int r0 = warp * RB; r0 < rows; r0 += nwarp * RB) {
+                float v[RB];
+#pragma unroll
+                for (int j = 0; j < RB; ++j) {
+                    const int r = r0 + j;
+                    v[j] = 0.f;
+                    if (r < rows && lane < WX) {
+                        const T u = U[r * bx + xo + lane];
+                        if constexpr (F32)
+                            v[j] = __fsub_rn(u, cshift);
+                        else
+                            v[j] = u16_minus(u, cshift);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < RB; ++j) {
+                    const int r = r0 + j;
+                    if (r < rows && lane < pf) Fw[r * pf + lane] = v[j];
+                }
+            }
+        }
+        __syncthreads();
+        const BlockConst bc = sc->bc;
+        if (bc.flat) {  // flat floating block: NCC undefined for every shift
             if (tid == 0) write_result(a, blk, Cand{0.0, 0, 0, 0}, P, py, RX, ry, rz);
             __syncthreads();
             continue;
         }
-
-        // ---- window -> float, shifted by c --------------------------------
-        for (int i = tid; i < wz * wy * pf; i += nthr) {
-            int x = i % pf, zy = i / pf;
-            float v = 0.f;
-            if (x < WX) {
-                T u = U[zy * bx + xo + x];
-                if constexpr (F32)
-                    v = __fsub_rn(u, c_f);
-                else
-                    v = (float)((int)u - c_i);
+        // ---- phase B: mean-shifted template ---------------------------------
+        {
+            const float tsh = F32 ? bc.mu : 8388608.0f + (float)bc.m;
+            constexpr int TB = B * B * PT;
+            constexpr int TPT = (TB + 63) / 64;  // items per thread at 64+ threads
+            float v[TPT];
+#pragma unroll
+            for (int j = 0; j < TPT; ++j) {
+                const int k = tid + j * nthr;
+                const int kzy = k / PT, kx = k - kzy * PT;
+                v[j] = 0.f;
+                if (k < TB && kx < B) {
+                    if constexpr (F32)
+                        v[j] = __fsub_rn(Ut[kzy * btx + xot + kx], tsh);
+                    else
+                        v[j] = u16_minus(Ut[kzy * btx + xot + kx], tsh);
+                }
             }
-            Fw[i] = v;
+#pragma unroll
+            for (int j = 0; j < TPT; ++j) {
+                const int k = tid + j * nthr;
+                if (k < TB) Tm[k] = v[j];
+            }
+            for (int k = tid + TPT * nthr; k < TB; k += nthr) {  // fewer than 64 threads
+                const int kzy = k / PT, kx = k - kzy * PT;
+                float w = 0.f;
+                if (kx < B) {
+                    if constexpr (F32)
+                        w = __fsub_rn(Ut[kzy * btx + xot + kx], tsh);
+                    else
+                        w = u16_minus(Ut[kzy * btx + xot + kx], tsh);
+                }
+                Tm[k] = w;
+            }
         }
         __syncthreads();
+        // both staging buffers are free: start the next block's copies
+        {
+            int nb = blk + gridDim.x;
+            if (nb < n) {
+                const int ncx = a.centers[3 * nb + 0], ncy = a.centers[3 * nb + 1], ncz = a.centers[3 * nb + 2];
+                if (center_inside<H>(ncx, ncy, ncz, nx, ny, nz)) {
+                    if (tid == 0) issue(nb);
+                    inflight = nb;
+                }
+            }
+        }
 
         // ---- search: FP32 accumulation of A(d) over the whole window ------
         float ub[P];
         float lbm = -INFINITY;
         const int dyi = tid % py, dzi = tid / py;
         if (tid < lines) {
+            const int dy = dyi - ry, dz = dzi - rz, Y = cy + dy, Z = cz + dz;
+            const bool yz_ok = Y >= H && Y <= ny - 1 - H && Z >= H && Z <= nz - 1 - H;
+            typedef typename std::conditional<F32, float, int32_t>::type S1T;
+            typedef typename std::conditional<F32, float, long long>::type S2T;
+
+            const float *fbase = Fw + (dzi * wy + dyi) * pf;
             float acc[P];
 #pragma unroll
             for (int p = 0; p < P; ++p) acc[p] = 0.f;
+#pragma unroll 1
             for (int kz = 0; kz < B; ++kz) {
-                const float *frow = Fw + ((dzi + kz) * wy + dyi) * pf;
-                const float *trow = Tm + kz * B * PT;
 #pragma unroll 1
                 for (int ky = 0; ky < B; ++ky) {
-                    float j[4 * NJ4];
-                    float t[PT];
+                    const float *fr = fbase + (kz * wy + ky) * pf;
+                    const float *tr = Tm + (kz * B + ky) * PT;
+                    float j[4 * NJ4], t[PT];
 #pragma unroll
                     for (int q = 0; q < NJ4; ++q) {
-                        float4 v = *reinterpret_cast<const float4 *>(frow + ky * pf + 4 * q);
+                        const float4 v = *reinterpret_cast<const float4 *>(fr + 4 * q);
                         j[4 * q + 0] = v.x;
                         j[4 * q + 1] = v.y;
                         j[4 * q + 2] = v.z;
@@ -407,7 +509,7 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS) match_kernel(const MatchPar
                     }
 #pragma unroll
                     for (int q = 0; q < PT / 4; ++q) {
-                        float4 v = *reinterpret_cast<const float4 *>(trow + ky * PT + 4 * q);
+                        const float4 v = *reinterpret_cast<const float4 *>(tr + 4 * q);
                         t[4 * q + 0] = v.x;
                         t[4 * q + 1] = v.y;
                         t[4 * q + 2] = v.z;
@@ -420,28 +522,41 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS) match_kernel(const MatchPar
                 }
             }
 
-            // ---- approximate NCC and its error bound per shift -----------
-            const int dy = dyi - ry, dz = dzi - rz, Y = cy + dy, Z = cz + dz;
-            const bool yz_ok = Y >= H && Y <= ny - 1 - H && Z >= H && Z <= nz - 1 - H;
-            const float fN = (float)N;
+            // box sums of this thread's shifts (independent loads, issued together)
+            S1T ps1[P];
+            S2T ps2[P];
+            uint32_t vmask = 0;
+            const size_t rowbase = ((size_t)Z * ny + Y) * nx;
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 const int X = cx + p - RX;
+                ps1[p] = 0;
+                ps2[p] = 0;
+                if (yz_ok && X >= H && X <= nx - 1 - H) {
+                    vmask |= 1u << p;
+                    ps1[p] = reinterpret_cast<const S1T *>(a.s1)[rowbase + X];
+                    ps2[p] = reinterpret_cast<const S2T *>(a.s2)[rowbase + X];
+                }
+            }
+
+            // ---- approximate NCC and its error bound per shift -----------
+            const float fN = (float)N;
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
                 ub[p] = -INFINITY;
-                if (!(yz_ok && X >= H && X <= nx - 1 - H)) continue;
-                const size_t idx = ((size_t)Z * ny + Y) * nx + X;
+                if (!((vmask >> p) & 1u)) continue;
                 if constexpr (!F32) {
-                    const long long s1 = reinterpret_cast<const int32_t *>(a.s1)[idx];
-                    const long long s2 = reinterpret_cast<const long long *>(a.s2)[idx];
+                    const long long s1 = ps1[p];
+                    const long long s2 = ps2[p];
                     const long long vJ = (long long)N * s2 - s1 * s1;
                     if (vJ <= 0) continue;  // flat reference block
                     const long long s1p = s1 - (long long)N * c_i;
                     const long long s2p = s2 - 2ll * c_i * s1 + (long long)N * c_i * c_i;  // sum (J-c)^2
-                    const float inv = __frsqrt_rn(__fmul_rn(fvI, (float)vJ));
+                    const float inv = __frsqrt_rn(__fmul_rn(bc.fvI, (float)vJ));
                     const float na = __fmul_rn(fN, acc[p]);
-                    const float rs = (float)(rr * s1p);
+                    const float rs = (float)(bc.rr * s1p);
                     const float v = __fmul_rn(__fadd_rn(na, rs), inv);
-                    float e = kq * __fsqrt_rn((float)s2p) * inv + 3.f * U32 * (fabsf(na) + fabsf(rs)) * inv +
+                    float e = bc.kq * __fsqrt_rn((float)s2p) * inv + 3.f * U32 * (fabsf(na) + fabsf(rs)) * inv +
                               6.f * U32 * fabsf(v);
                     e = 2.f * e + 1e-9f;
                     ub[p] = v + e;
@@ -450,8 +565,8 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS) match_kernel(const MatchPar
                     constexpr float GS = (float)(3.0 * B * 5.9604644775390625e-08 /
                                                  (1.0 - 3.0 * B * 5.9604644775390625e-08));  // box-sum depth
                     constexpr float GN = (float)GAMMA_N;
-                    const float s1 = reinterpret_cast<const float *>(a.s1)[idx];
-                    const float s2 = fmaxf(reinterpret_cast<const float *>(a.s2)[idx], 0.f);
+                    const float s1 = ps1[p];
+                    const float s2 = fmaxf(ps2[p], 0.f);
                     const float d1 = GS * __fsqrt_rn(fN * s2) * 1.01f;  // |S1 err| bound
                     const float s1sq_n = __fmul_rn(__fmul_rn(s1, s1), 1.0f / fN);
                     const float vJa = __fsub_rn(s2, s1sq_n);
@@ -469,16 +584,16 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS) match_kernel(const MatchPar
                         ub[p] = INFINITY;
                         continue;
                     }
-                    const float inv = __frsqrt_rn(__fmul_rn(fvI, vJa));
+                    const float inv = __frsqrt_rn(__fmul_rn(bc.fvI, vJa));
                     const float A = acc[p];
-                    const float es = __fmul_rn(emu, s1p);
+                    const float es = __fmul_rn(bc.emu, s1p);
                     const float num = __fsub_rn(A, es);
                     const float v = __fmul_rn(num, inv);
-                    const float enum_ = (GN + 3.f * U32) * kq * __fsqrt_rn(sj2) +
-                                        fabsf(emu) * (fabsf(s1p) + d1 + 2.f * U32 * fN * fabsf(c_f)) * 1.01f +
+                    const float enum_ = (GN + 3.f * U32) * bc.kq * __fsqrt_rn(sj2) +
+                                        fabsf(bc.emu) * (fabsf(s1p) + d1 + 2.f * U32 * fN * fabsf(c_f)) * 1.01f +
                                         U32 * (fabsf(A) + fabsf(es));
-                    float e = enum_ * inv * (1.f + 0.7f * rho + 4.f * U32) + fabsf(num) * inv * (0.7f * rho + 6.f * U32) +
-                              3.f * U32 * fabsf(v);
+                    float e = enum_ * inv * (1.f + 0.7f * rho + 4.f * U32) +
+                              fabsf(num) * inv * (0.7f * rho + 6.f * U32) + 3.f * U32 * fabsf(v);
                     e = 2.f * e + 1e-9f;
                     ub[p] = v + e;
                     lbm = fmaxf(lbm, v - e);
@@ -513,32 +628,51 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS) match_kernel(const MatchPar
             const size_t idx = ((size_t)(cz + dz) * ny + (cy + dy)) * nx + (cx + dx);
             Cand c{0.0, dx * dx + dy * dy + dz * dz, code, 0};
             if constexpr (!F32) {
+                long long s1 = 0, s2 = 0;
+                if (lane == 0) {  // issued first, consumed after the warp sum
+                    s1 = reinterpret_cast<const int32_t *>(a.s1)[idx];
+                    s2 = reinterpret_cast<const long long *>(a.s2)[idx];
+                }
+                constexpr int KPL = (N + 31) / 32;
+                constexpr int CH = KPL < 6 ? KPL : 6;
                 long long e = 0;
-                for (int k = lane; k < N; k += 32) {
-                    const int kz = k / (B * B), rem = k - kz * B * B, ky = rem / B, kx = rem - ky * B;
-                    const int t = (int)Tm[(kz * B + ky) * PT + kx];
-                    const int jv = (int)Fw[((szi + kz) * wy + (syi + ky)) * pf + sxi + kx];
-                    e += (long long)t * jv;
+#pragma unroll 1
+                for (int i0 = 0; i0 < KPL; i0 += CH) {
+                    int tv[CH], jv[CH];
+#pragma unroll
+                    for (int i = 0; i < CH; ++i) {
+                        const int k = lane + 32 * (i0 + i);
+                        const int kz = k / (B * B), rem = k - kz * B * B, ky = rem / B, kx = rem - ky * B;
+                        tv[i] = 0;
+                        jv[i] = 0;
+                        if (k < N) {
+                            tv[i] = (int)Tm[(kz * B + ky) * PT + kx];
+                            jv[i] = (int)Fw[((szi + kz) * wy + (syi + ky)) * pf + sxi + kx];
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < CH; ++i) e += (long long)tv[i] * jv[i];
                 }
                 e = warp_sum(e);
                 if (lane == 0) {
-                    const long long s1 = reinterpret_cast<const int32_t *>(a.s1)[idx];
-                    const long long s2 = reinterpret_cast<const long long *>(a.s2)[idx];
                     const long long vJ = (long long)N * s2 - s1 * s1;
-                    const long long num = (long long)N * e + rr * (s1 - (long long)N * c_i);
+                    const long long num = (long long)N * e + bc.rr * (s1 - (long long)N * c_i);
                     if (vJ > 0) {
-                        const double den = __dsqrt_rn(__dmul_rn((double)vI, (double)vJ));
+                        const double den = __dsqrt_rn(__dmul_rn((double)bc.vI, (double)vJ));
                         c.s = __ddiv_rn((double)num, den);
                         c.ok = 1;
                     }
                 }
             } else {
+                const float *pre = reinterpret_cast<const float *>(a.preop);
+                const float *intra = reinterpret_cast<const float *>(a.intraop);
                 double sij = 0.0, sj = 0.0, sjj = 0.0;
                 float lo = INFINITY, hi = -INFINITY;
                 for (int k = lane; k < N; k += 32) {
                     const int kz = k / (B * B), rem = k - kz * B * B, ky = rem / B, kx = rem - ky * B;
-                    const double di = (double)Iraw[k] - Ibar;
-                    const float jf = U[((szi + kz) * wy + (syi + ky)) * bx + xo + sxi + kx];
+                    const double di =
+                        (double)pre[((size_t)(cz - H + kz) * ny + (cy - H + ky)) * nx + (cx - H + kx)] - bc.ibar;
+                    const float jf = intra[((size_t)(cz + dz - H + kz) * ny + (cy + dy - H + ky)) * nx + (cx + dx - H + kx)];
                     const double jd = (double)jf;
                     sij = fma(di, jd, sij);
                     sj += jd;
@@ -554,7 +688,7 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS) match_kernel(const MatchPar
                 if (lane == 0 && lo < hi) {
                     const double vJ = sjj - sj * sj / (double)N;
                     if (vJ > 0.0) {
-                        c.s = sij / sqrt(dvI * vJ);
+                        c.s = sij / sqrt(bc.dvI * vJ);
                         c.ok = 1;
                     }
                 }
@@ -578,32 +712,38 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS) match_kernel(const MatchPar
         }
         __syncthreads();
     }
+    // a copy issued for a block this CTA never reached cannot exist: copies
+    // are only issued for blocks < n that the loop visits next.
 }
 
 // Host side: launch one (element type, block size, x-shift count) variant.
 template <typename T, int B, int P>
 nrr_status launch_match_variant(const MatchLaunch &m, cudaStream_t stream)
 {
-    constexpr bool F32 = std::is_same<T, float>::value;
     constexpr int ALIGN = 16 / (int)sizeof(T);
     constexpr int WX = B + P - 1;
     const int ry = m.radius[1], rz = m.radius[2], py = 2 * ry + 1, pz = 2 * rz + 1;
     const int wy = B + 2 * ry, wz = B + 2 * rz;
     const int bx = round_up_i(WX + ALIGN - 1, ALIGN);
+    const int btx = round_up_i(B + ALIGN - 1, ALIGN);
     const int pf = match_pitch(WX);
-    const MatchLayout L = match_layout((int)sizeof(T), B, P, bx, pf, wy, wz, py, pz, F32);
+    const MatchLayout L = match_layout((int)sizeof(T), B, P, bx, btx, pf, wy, wz, py, pz);
     const int lines = py * pz;
     const int threads = round_up_i(lines, 32);
     if (threads > MATCH_MAX_THREADS) return fail(NRR_E_INVALID, "search window too large");
 
-    CUtensorMap map;
-    nrr_status st = encode_volume_map(&map, m.intraop, m.dtype, m.dims, bx, wy, wz);
+    CUtensorMap mapJ, mapI;
+    nrr_status st = encode_volume_map(&mapJ, m.intraop, m.dtype, m.dims, bx, wy, wz);
+    if (st != NRR_OK) return st;
+    st = encode_volume_map(&mapI, m.preop, m.dtype, m.dims, btx, B, B);
     if (st != NRR_OK) return st;
 
     auto kern = match_kernel<T, B, P>;
     static int smem_set = 0;  // largest dynamic shared memory opted in so far
     if (L.total > smem_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(match_kernel)");
         smem_set = L.total;
     }
@@ -628,12 +768,13 @@ nrr_status launch_match_variant(const MatchLaunch &m, cudaStream_t stream)
     p.ry = ry;
     p.rz = rz;
     p.bx = bx;
+    p.btx = btx;
     p.pf = pf;
     p.disp = m.disp;
     p.ncc = m.ncc;
     p.valid = m.valid;
     p.err = m.err;
-    kern<<<(unsigned)grid, threads, L.total, stream>>>(p, map);
+    kern<<<(unsigned)grid, threads, L.total, stream>>>(p, mapJ, mapI);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "match kernel launch");
     count_launches(1);
