@@ -49,7 +49,27 @@ def _args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="clinical")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--batched-reps", type=int, default=5)
+    p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--serve-open-requests", type=int, default=200)
+    p.add_argument("--serve-closed-requests", type=int, default=300)
     return p.parse_args()
+
+
+def aggregate_replicas(local_s: float, world: int, units_per_rank: int, pg=None):
+    """Replicas only: every rank processed `units_per_rank` independently;
+    the job's time is the slowest rank's.  Returns (max seconds, whole-job
+    units per second)."""
+    import torch
+
+    t = local_s
+    if pg is not None and world > 1:
+        dev = torch.device("cuda", torch.cuda.current_device()) if pg.get_backend() == "nccl" else torch.device("cpu")
+        x = torch.tensor([local_s], dtype=torch.float64, device=dev)
+        pg.all_reduce(x, op=pg.ReduceOp.MAX)
+        t = float(x.item())
+    return t, world * units_per_rank / t
 
 
 def _dist():
@@ -215,6 +235,127 @@ def run_reference(a):
 # --------------------------------------------------------------------------
 # the GPU path
 # --------------------------------------------------------------------------
+def _batched_search(a, nrr, synth, d_pre, d_intra, d_mask, w, flush):
+    """The batched parameter search: 64 settings on the clinical pair, one
+    graph-captured plan (autotuned) against 64 sequential plain calls."""
+    import torch
+
+    settings = synth.parameter_settings(64)
+    stream = torch.cuda.current_stream()
+
+    def evals_of(counts):
+        return sum(n * (2 * r + 1) ** 3 for n, (b, r, f) in zip(counts, settings))
+
+    # plain: one select (host count) + one match (own box sums) per setting
+    def plain():
+        counts = []
+        for b, r, f in settings:
+            c = nrr.select_blocks(d_pre, d_mask, b, 2, f)
+            nrr.block_match(d_pre, d_intra, c, b, r)
+            counts.append(c.shape[0])
+        return counts
+
+    plain()
+    torch.cuda.synchronize()
+    t_plain = []
+    for _ in range(max(2, a.batched_reps // 2)):
+        flush.fill_(3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        counts = plain()
+        torch.cuda.synchronize()
+        t_plain.append(time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    plan = nrr.BatchPlan(d_pre, d_intra, d_mask, [(b, 2, r, f) for b, r, f in settings], graph=True, autotune=True)
+    t_create = time.perf_counter() - t0
+    for _ in range(2):
+        plan.run()
+    torch.cuda.synchronize()
+    t_batch = []
+    for _ in range(a.batched_reps):
+        flush.fill_(5)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.run()
+        e1.record(stream)
+        e1.synchronize()
+        t_batch.append(e0.elapsed_time(e1) / 1e3)
+    nrr.device_status()
+    bcounts = [int(plan.view(i)[0].item()) for i in range(len(settings))]
+    assert bcounts == counts, "batched and plain selections differ"
+    plan.close()
+    ev = evals_of(counts)
+    tp, tb = min(t_plain), min(t_batch)
+    return {"workload": "clinical pair x 64 settings (block 5/7/9, radius 3..7, fraction 2..10%, stride 2)",
+            "settings": len(settings), "evals": ev,
+            "plain_ms": 1e3 * tp, "batched_ms": 1e3 * tb, "plan_create_s": t_create,
+            "plain_registrations_per_s": len(settings) / tp, "batched_registrations_per_s": len(settings) / tb,
+            "plain_evals_per_s": ev / tp, "batched_evals_per_s": ev / tb, "speedup": tp / tb,
+            "timing": "plain: host wall clock incl. its per-setting host syncs; batched: CUDA events around one "
+                      "graph launch; best of repeats, L2 flushed before each"}
+
+
+def _serving(a, nrr, synth, dev):
+    """The served stream: Poisson arrivals (mean 20 requests/s) of
+    registrations of three volume sizes with random (block, radius,
+    fraction); volumes resident on the device.  Reports p50/p99 latency
+    (submission to completion on the device) and registrations/s, plus a
+    saturation run (all requests queued at once) served with 8 slots against
+    one-at-a-time FIFO service (1 slot)."""
+    import numpy as np
+    import torch
+
+    pool = []
+    for si in range(len(synth.SERVE_SIZES)):
+        pre, intra, mask = synth.serve_pair(si, 0)
+        pool.append((nrr.to_device_u16(pre, dev), nrr.to_device_u16(intra, dev), torch.from_numpy(mask).to(dev)))
+    torch.cuda.synchronize()
+
+    def run(reqs, slots, open_loop):
+        srv = nrr.Server(slots=slots, reserve_bytes=2 << 30)
+        try:
+            # warm the kernels of every variant used, outside the measurement
+            t0 = time.perf_counter()
+            tickets = []
+            for t_arr, si, b, r, f in reqs:
+                if open_loop:
+                    dt = t_arr - (time.perf_counter() - t0)
+                    if dt > 0:
+                        time.sleep(dt)
+                p, i, m = pool[si]
+                tickets.append(srv.submit(p, i, m, b, 2, r, f))
+            done = {}
+            while len(done) < len(tickets):
+                for t in tickets:
+                    if t not in done:
+                        res = srv.poll(t)
+                        if res is not None:
+                            done[t] = (res["latency_s"], res["n"])
+                            srv.release(t)
+            wall = time.perf_counter() - t0
+        finally:
+            srv.stop()
+        lat = np.array([done[t][0] for t in tickets])
+        return {"requests": len(tickets), "slots": slots, "wall_s": wall, "registrations_per_s": len(tickets) / wall,
+                "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                "mean_ms": 1e3 * float(lat.mean())}
+
+    reqs_open = synth.poisson_arrivals(a.serve_open_requests, 20.0)
+    warm = [(0.0, si, b, r, f) for (si, b, r, f) in {(q[1], q[2], q[3], q[4]) for q in reqs_open}]
+    run(warm, 8, False)
+    out = {"workload": "Poisson 20 req/s, volumes 128x128x64 / 192x192x96 / 256x256x160 uint16, block 5/7/9, "
+                       "radius 3..7, fraction 2..10%, stride 2, volumes resident on the device",
+           "latency": "submission to completion on the device (host callback timestamp)"}
+    out["open_loop_20rps"] = run(reqs_open, 8, True)
+    reqs_closed = [(0.0, si, b, r, f) for (_, si, b, r, f) in synth.poisson_arrivals(a.serve_closed_requests, 20.0,
+                                                                                      seed=synth.SEED_BASE + 11)]
+    out["saturated_served_8_slots"] = run(reqs_closed, 8, False)
+    out["saturated_fifo_1_slot"] = run(reqs_closed, 1, False)
+    out["saturated_speedup"] = (out["saturated_served_8_slots"]["registrations_per_s"] /
+                                out["saturated_fifo_1_slot"]["registrations_per_s"])
+    return out
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -286,12 +427,7 @@ def run_ours(a):
         pg.barrier()
     step_ms = [s.elapsed_time(e) for s, e in evs]
     match_ms = [s.elapsed_time(e) for s, e in evm]
-    total_s = sum(step_ms) / 1e3
-    tmax = torch.tensor([total_s], dtype=torch.float64, device=dev)
-    if pg:
-        pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
-    total_s = float(tmax.item())
-    value = world * a.steps * evals / total_s
+    total_s, value = aggregate_replicas(sum(step_ms) / 1e3, world, a.steps * evals, pg)
 
     # ---- end to end through the public API with host buffers --------------
     h_pre = torch.from_numpy(np.ascontiguousarray(pre).view(np.int16)).pin_memory()
@@ -350,6 +486,10 @@ def run_ours(a):
         "valid_blocks": valid_count,
         "clocks": clk.summary(t_start, t_end),
     }
+    if not a.no_batched:
+        line["batched"] = _batched_search(a, nrr, synth, d_pre, d_intra, d_mask, w, flush)
+    if not a.no_serving:
+        line["serving"] = _serving(a, nrr, synth, dev)
     if world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(w, pre, intra, mask)
     print(json.dumps(line), flush=True)

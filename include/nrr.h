@@ -184,6 +184,136 @@ nrr_status nrr_block_match_bs(const void *d_preop, const void *d_intraop, const 
                               int32_t block, const int32_t radius[3],
                               int32_t *d_disp, double *d_ncc, uint8_t *d_valid, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Execution-configuration autotuning (Sec. 4.3: the paper tunes its GPU
+ * block-matching kernel by an empirical search over thread configurations).
+ *
+ * nrr_autotune_match times the match kernel for one (dtype, block, radius)
+ * at every feasible number of persistent CTAs per SM on the given inputs
+ * (arguments as nrr_block_match_bs, with a host block count) and stores the
+ * fastest in a per-process table that every later match launch of that
+ * variant uses.  It waits for `stream`.  best_ctas_per_sm and best_ms may
+ * be NULL.  nrr_tuning_get/set read and write one table entry (0 = as many
+ * CTAs as fit); nrr_tuning_save/load write and read the whole table as text.
+ * ---------------------------------------------------------------------- */
+nrr_status nrr_autotune_match(const void *d_preop, const void *d_intraop, const void *d_boxsums,
+                              nrr_dtype dtype, nrr_dims dims, const int32_t *d_centers, int32_t n_blocks,
+                              int32_t block, const int32_t radius[3],
+                              int32_t *d_disp, double *d_ncc, uint8_t *d_valid,
+                              int32_t *best_ctas_per_sm, float *best_ms, void *stream);
+nrr_status nrr_tuning_get(nrr_dtype dtype, int32_t block, const int32_t radius[3], int32_t *ctas_per_sm);
+nrr_status nrr_tuning_set(nrr_dtype dtype, int32_t block, const int32_t radius[3], int32_t ctas_per_sm);
+nrr_status nrr_tuning_save(const char *path);
+nrr_status nrr_tuning_load(const char *path);
+
+/* ------------------------------------------------------------------------
+ * Batched parameter search (the paper's sweep over registration parameters,
+ * Sec. 4.2 speculative runs with many parameter values and Sec. 5 the
+ * parameter pool of the learned predictor, both run there as separate
+ * registrations).
+ *
+ * A plan binds one uint16 volume pair and mask (device pointers that must
+ * stay valid and unchanged in place for the plan's life) and n_settings
+ * settings; each setting is a full registration's hot path: selection with
+ * (block, stride, frac), then matching with (block, radius).  The plan owns
+ * all scratch and result memory (allocated at creation, nothing is
+ * allocated when it runs).  Work shared between settings is done once: box
+ * sums per distinct block size, selection per distinct (block, stride,
+ * frac); matching runs as one persistent launch per distinct (block,
+ * radius) holding all of that variant's settings.
+ *
+ * flags: NRR_BATCH_GRAPH captures the whole sweep into one CUDA graph at
+ * creation, so nrr_batch_run is a single graph launch with no host round
+ * trip; NRR_BATCH_AUTOTUNE runs the sweep once at creation and autotunes
+ * every match variant on it (creation then waits for the device).
+ * nrr_batch_run enqueues one sweep on `stream` (asynchronous).  After it
+ * completes, nrr_batch_view_get gives setting s's device arrays: the count
+ * (device int32), centres, displacements, NCC and valid flags, each with
+ * `capacity` entries of which the first count are meaningful.
+ * Errors: NRR_E_INVALID (arguments), NRR_E_NOMEM, NRR_E_CUDA.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int32_t block;      /* odd 3..11 */
+    int32_t stride;     /* 1..64 */
+    int32_t radius[3];  /* 0..7 each */
+    double frac;        /* (0, 1] */
+} nrr_setting;
+
+typedef struct nrr_batch_s *nrr_batch;
+
+typedef struct {
+    const int32_t *centers;   /* device [capacity][3] */
+    const int32_t *n_blocks;  /* device, one int32 */
+    const int32_t *disp;      /* device [capacity][3] */
+    const double *ncc;        /* device [capacity] */
+    const uint8_t *valid;     /* device [capacity] */
+    int32_t capacity;
+} nrr_batch_view;
+
+enum { NRR_BATCH_GRAPH = 1, NRR_BATCH_AUTOTUNE = 2 };
+
+nrr_status nrr_batch_create(const uint16_t *d_preop, const uint16_t *d_intraop, const uint8_t *d_mask,
+                            nrr_dims dims, const nrr_setting *settings, int32_t n_settings, int32_t flags,
+                            nrr_batch *plan);
+nrr_status nrr_batch_run(nrr_batch plan, void *stream);
+nrr_status nrr_batch_view_get(nrr_batch plan, int32_t setting, nrr_batch_view *view);
+nrr_status nrr_batch_destroy(nrr_batch plan);
+
+/* ------------------------------------------------------------------------
+ * Serving with continuous batching (the paper's client/server registration
+ * service, Sec. 4.1 "Ease-of-use", on one GPU).
+ *
+ * nrr_server_start starts a scheduler thread on the current device with
+ * `slots` CUDA streams.  nrr_submit queues one registration and returns a
+ * ticket at once.  Queued requests are admitted in arrival order whenever
+ * a slot is free and the device's free memory, less reserve_bytes, covers
+ * the request's scratch and result buffers; admitted requests run
+ * concurrently (their kernels overlap on the device) and a new one starts
+ * as soon as an earlier one finishes.  Each request runs selection (on
+ * d_select), box sums and matching exactly as the synchronous calls do, so
+ * its result equals a lone call's bit for bit whatever else is running.
+ *
+ * The caller keeps the request's volumes and mask valid and unchanged until
+ * nrr_poll has returned NRR_OK (or an error) for it.  nrr_poll returns
+ * NRR_PENDING while the request is queued or running; afterwards it fills
+ * `out` with the block count, device pointers to the results (owned by the
+ * library until nrr_release), the time from submission to admission and
+ * from submission to completion on the device.  nrr_release frees a
+ * finished (or still queued) request's buffers and forgets its ticket.
+ * A request whose allocation or launch fails is reported by nrr_poll with
+ * that status; the server keeps serving the others.  nrr_server_stop waits
+ * for running work and frees everything.  Only one server per process.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    const void *d_preop;       /* floating volume, `dtype` */
+    const void *d_intraop;     /* reference volume, `dtype` */
+    const uint16_t *d_select;  /* uint16 floating volume used for selection
+                                  (d_preop itself when dtype is NRR_U16) */
+    const uint8_t *d_mask;
+    nrr_dims dims;
+    nrr_dtype dtype;
+    int32_t block;
+    int32_t stride;
+    int32_t radius[3];
+    double frac;
+} nrr_request;
+
+typedef struct {
+    int32_t n_blocks;
+    const int32_t *centers;  /* device [n_blocks][3] */
+    const int32_t *disp;     /* device [n_blocks][3] */
+    const double *ncc;       /* device [n_blocks] */
+    const uint8_t *valid;    /* device [n_blocks] */
+    double queued_s;         /* submission -> admission */
+    double latency_s;        /* submission -> completion on the device */
+} nrr_result;
+
+nrr_status nrr_server_start(int32_t slots, size_t reserve_bytes);
+nrr_status nrr_server_stop(void);
+nrr_status nrr_submit(const nrr_request *req, uint64_t *ticket);
+nrr_status nrr_poll(uint64_t ticket, nrr_result *out);
+nrr_status nrr_release(uint64_t ticket);
+
 /* Waits for `stream`, then reports and clears the device error word that
  * the kernels set when a bounded wait gives up (NRR_E_TIMEOUT) or an
  * internal check fails (NRR_E_INTERNAL).  NRR_OK if neither happened. */

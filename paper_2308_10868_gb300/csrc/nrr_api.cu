@@ -224,21 +224,18 @@ nrr_status nrr_block_match_bs(const void *d_preop, const void *d_intraop, const 
     if (!d_boxsums || ((uintptr_t)d_boxsums & 255u) != 0)
         return fail(NRR_E_INVALID, "box-sum buffer NULL or not 256-byte aligned");
     if (n_blocks == 0) return NRR_OK;
-    MatchLaunch a;
+    MatchLaunch a{};
     a.preop = d_preop;
     a.intraop = d_intraop;
     a.s1 = d_boxsums;
     a.s2 = (const char *)d_boxsums + boxsum_s2_offset(dims, dtype);
     a.dtype = dtype;
     a.dims = dims;
-    a.centers = d_centers;
-    a.n_blocks = n_blocks;
-    a.d_n_blocks = d_n_blocks;
     a.block = block;
     for (int i = 0; i < 3; ++i) a.radius[i] = radius[i];
-    a.disp = d_disp;
-    a.ncc = d_ncc;
-    a.valid = d_valid;
+    a.n_jobs = 1;
+    a.jobs[0] = MatchJob{d_centers, d_n_blocks, n_blocks, d_disp, d_ncc, d_valid};
+    a.ctas_per_sm = tuned_ctas_per_sm(dtype, block, radius);
     st = device_error_word(&a.err);
     if (st != NRR_OK) return st;
     return launch_match(a, (cudaStream_t)stream);

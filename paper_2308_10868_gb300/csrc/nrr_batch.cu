@@ -1,0 +1,377 @@
+// Batched parameter search: many (block size, search radius, selection
+// fraction) settings of the registration run on one volume pair as one unit
+// of GPU work.
+//
+// The paper runs such sweeps as separate registrations spread over grid or
+// cloud resources (Sec. 4.2, speculative execution with many parameter
+// values; Sec. 5, the parameter pool of the learned predictor).  On one GPU
+// the same sweep becomes a plan built once and replayed:
+//   - box sums of the reference volume, once per distinct block size;
+//   - one selection per distinct (block, stride, fraction), each on its own
+//     preallocated scratch;
+//   - one persistent match launch per distinct (block, radius), whose job
+//     table holds every setting of that variant (up to 16 per launch);
+//   - all of it forked over internal streams with event dependencies and
+//     captured as a single CUDA graph, so a run is one graph launch with no
+//     host round trip.
+// Results stay on the device; every setting's count, centres, displacements,
+// NCC and valid flags are reachable through nrr_batch_view_get.
+#include <stdio.h>
+
+#include <algorithm>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "nrr_internal.h"
+
+namespace nrr {
+
+namespace {
+constexpr int NSTREAMS = 8;
+
+struct SelEntry {
+    int block, stride;
+    double frac;
+    SelectPlan plan;
+    unsigned char *ws;
+    int32_t *centers;
+    int32_t *d_n;
+    int32_t cap;
+    cudaEvent_t done;
+};
+struct BoxEntry {
+    int block;
+    void *buf;
+    cudaEvent_t done;
+};
+struct SettingOut {
+    int sel;
+    int32_t *disp;
+    double *ncc;
+    uint8_t *valid;
+};
+struct Group {
+    int block;
+    int radius[3];
+    std::vector<int> settings;
+};
+}  // namespace
+
+}  // namespace nrr
+
+struct nrr_batch_s {
+    int device = 0;
+    const uint16_t *preop = nullptr, *intraop = nullptr;
+    const uint8_t *mask = nullptr;
+    nrr_dims dims{};
+    int flags = 0;
+    std::vector<nrr_setting> settings;
+    std::vector<nrr::SelEntry> sels;
+    std::vector<nrr::BoxEntry> boxes;
+    std::vector<nrr::SettingOut> outs;
+    std::vector<nrr::Group> groups;
+    cudaStream_t streams[nrr::NSTREAMS] = {};
+    cudaStream_t launch = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, fork = nullptr, join[nrr::NSTREAMS] = {};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<void *> allocs;
+    unsigned int *err = nullptr;
+};
+
+namespace nrr {
+
+static nrr_status batch_alloc(nrr_batch_s *b, size_t bytes, void **p)
+{
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (batch plan)");
+    b->allocs.push_back(*p);
+    return NRR_OK;
+}
+
+// Enqueue the whole sweep on the plan's streams, ordered after `in` and
+// joined back into `out` (the same stream in practice).
+static nrr_status batch_enqueue(nrr_batch_s *b, cudaStream_t s)
+{
+    NRR_CUDA_TRY(cudaEventRecord(b->fork, s));
+    for (int k = 0; k < NSTREAMS; ++k) NRR_CUDA_TRY(cudaStreamWaitEvent(b->streams[k], b->fork, 0));
+    int rr = 0;
+    for (auto &bx : b->boxes) {
+        cudaStream_t st = b->streams[rr++ % NSTREAMS];
+        nrr_status r = launch_boxsums(b->intraop, NRR_U16, b->dims, bx.block, bx.buf, st);
+        if (r != NRR_OK) return r;
+        NRR_CUDA_TRY(cudaEventRecord(bx.done, st));
+    }
+    for (auto &se : b->sels) {
+        cudaStream_t st = b->streams[rr++ % NSTREAMS];
+        nrr_status r = enqueue_select(b->preop, b->mask, b->dims, se.block, se.stride, se.frac, se.centers, se.cap,
+                                      se.d_n, se.ws, se.plan, st);
+        if (r != NRR_OK) return r;
+        NRR_CUDA_TRY(cudaEventRecord(se.done, st));
+    }
+    // match launches, largest groups first so they start early
+    std::vector<int> order(b->groups.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::sort(order.begin(), order.end(), [&](int x, int y) {
+        auto work = [&](int g) {
+            const Group &G = b->groups[g];
+            long long w = 0;
+            for (int s_ : G.settings) w += (long long)b->sels[b->outs[s_].sel].cap;
+            return w * (2 * G.radius[0] + 1) * (2 * G.radius[1] + 1) * (2 * G.radius[2] + 1) * G.block * G.block *
+                   G.block;
+        };
+        return work(x) > work(y);
+    });
+    for (int gi : order) {
+        const Group &G = b->groups[gi];
+        const BoxEntry *bx = nullptr;
+        for (auto &e : b->boxes)
+            if (e.block == G.block) bx = &e;
+        for (size_t c0 = 0; c0 < G.settings.size(); c0 += MATCH_MAX_JOBS) {
+            cudaStream_t st = b->streams[rr++ % NSTREAMS];
+            NRR_CUDA_TRY(cudaStreamWaitEvent(st, bx->done, 0));
+            MatchLaunch a{};
+            a.preop = b->preop;
+            a.intraop = b->intraop;
+            a.s1 = bx->buf;
+            a.s2 = (const char *)bx->buf + boxsum_s2_offset(b->dims, NRR_U16);
+            a.dtype = NRR_U16;
+            a.dims = b->dims;
+            a.block = G.block;
+            for (int i = 0; i < 3; ++i) a.radius[i] = G.radius[i];
+            a.err = b->err;
+            a.ctas_per_sm = tuned_ctas_per_sm(NRR_U16, G.block, G.radius);
+            for (size_t c = c0; c < G.settings.size() && c < c0 + MATCH_MAX_JOBS; ++c) {
+                const SettingOut &o = b->outs[G.settings[c]];
+                const SelEntry &se = b->sels[o.sel];
+                NRR_CUDA_TRY(cudaStreamWaitEvent(st, se.done, 0));
+                a.jobs[a.n_jobs++] = MatchJob{se.centers, se.d_n, se.cap, o.disp, o.ncc, o.valid};
+            }
+            nrr_status r = launch_match(a, st);
+            if (r != NRR_OK) return r;
+        }
+    }
+    for (int k = 0; k < NSTREAMS; ++k) {
+        NRR_CUDA_TRY(cudaEventRecord(b->join[k], b->streams[k]));
+        NRR_CUDA_TRY(cudaStreamWaitEvent(s, b->join[k], 0));
+    }
+    return NRR_OK;
+}
+
+static void batch_free(nrr_batch_s *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto &e : b->sels)
+        if (e.done) cudaEventDestroy(e.done);
+    for (auto &e : b->boxes)
+        if (e.done) cudaEventDestroy(e.done);
+    for (int k = 0; k < NSTREAMS; ++k) {
+        if (b->join[k]) cudaEventDestroy(b->join[k]);
+        if (b->streams[k]) cudaStreamDestroy(b->streams[k]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->launch) cudaStreamDestroy(b->launch);
+    for (void *p : b->allocs) cudaFree(p);
+    delete b;
+}
+
+}  // namespace nrr
+
+using namespace nrr;
+
+extern "C" {
+
+nrr_status nrr_batch_create(const uint16_t *d_preop, const uint16_t *d_intraop, const uint8_t *d_mask, nrr_dims dims,
+                            const nrr_setting *settings, int32_t n_settings, int32_t flags, nrr_batch *out)
+{
+    clear_error();
+    if (!out) return fail(NRR_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!d_preop || !d_intraop || !d_mask || !settings || n_settings < 1)
+        return fail(NRR_E_INVALID, "NULL volume/mask/settings or no settings");
+    if (((uintptr_t)d_preop & 15u) || ((uintptr_t)d_intraop & 15u))
+        return fail(NRR_E_INVALID, "volumes must be 16-byte aligned");
+    for (int i = 0; i < n_settings; ++i) {
+        const nrr_setting &s = settings[i];
+        nrr_status st = check_select_args(dims, s.block, s.stride, s.frac);
+        if (st != NRR_OK) {
+            char why[256];
+            snprintf(why, sizeof why, "%s", nrr_last_error());
+            return fail(st, "setting %d: %s", i, why);
+        }
+        for (int k = 0; k < 3; ++k)
+            if (s.radius[k] < 0 || s.radius[k] > 7) return fail(NRR_E_INVALID, "setting %d: radius outside 0..7", i);
+    }
+    nrr_batch_s *b = new nrr_batch_s();
+    b->preop = d_preop;
+    b->intraop = d_intraop;
+    b->mask = d_mask;
+    b->dims = dims;
+    b->flags = flags;
+    b->settings.assign(settings, settings + n_settings);
+    cudaGetDevice(&b->device);
+    nrr_status st = device_error_word(&b->err);
+    auto bail = [&](nrr_status r) {
+        batch_free(b);
+        return r;
+    };
+    if (st != NRR_OK) return bail(st);
+    // distinct box-sum block sizes, selections and match variants
+    std::map<int, int> box_of;
+    std::map<std::tuple<int, int, double>, int> sel_of;
+    std::map<std::tuple<int, int, int, int>, int> grp_of;
+    for (int i = 0; i < n_settings; ++i) {
+        const nrr_setting &s = settings[i];
+        if (!box_of.count(s.block)) {
+            box_of[s.block] = (int)b->boxes.size();
+            BoxEntry e{s.block, nullptr, nullptr};
+            if ((st = batch_alloc(b, boxsum_bytes(dims, NRR_U16), &e.buf)) != NRR_OK) return bail(st);
+            if (cudaEventCreateWithFlags(&e.done, cudaEventDisableTiming) != cudaSuccess)
+                return bail(fail(NRR_E_CUDA, "event"));
+            b->boxes.push_back(e);
+        }
+        auto sk = std::make_tuple(s.block, s.stride, s.frac);
+        if (!sel_of.count(sk)) {
+            sel_of[sk] = (int)b->sels.size();
+            SelEntry e{};
+            e.block = s.block;
+            e.stride = s.stride;
+            e.frac = s.frac;
+            e.plan = select_plan(dims, s.stride);
+            const long long ng = e.plan.ng;
+            long long cap = (long long)(0.5 + (double)ng * s.frac) + 1;
+            if (cap > ng) cap = ng;
+            e.cap = (int32_t)(cap < 1 ? 1 : cap);
+            void *p;
+            if ((st = batch_alloc(b, e.plan.bytes, &p)) != NRR_OK) return bail(st);
+            e.ws = (unsigned char *)p;
+            if ((st = batch_alloc(b, sizeof(int32_t) * 3 * (size_t)e.cap, &p)) != NRR_OK) return bail(st);
+            e.centers = (int32_t *)p;
+            if ((st = batch_alloc(b, 256, &p)) != NRR_OK) return bail(st);
+            e.d_n = (int32_t *)p;
+            if (cudaEventCreateWithFlags(&e.done, cudaEventDisableTiming) != cudaSuccess)
+                return bail(fail(NRR_E_CUDA, "event"));
+            b->sels.push_back(e);
+        }
+        SettingOut o{};
+        o.sel = sel_of[sk];
+        const int32_t cap = b->sels[o.sel].cap;
+        void *p;
+        if ((st = batch_alloc(b, (size_t)cap * (12 + 8 + 1) + 512, &p)) != NRR_OK) return bail(st);
+        o.ncc = (double *)p;
+        o.disp = (int32_t *)((char *)p + align_up((size_t)cap * 8, 256));
+        o.valid = (uint8_t *)((char *)o.disp + align_up((size_t)cap * 12, 256));
+        b->outs.push_back(o);
+        auto gk = std::make_tuple(s.block, s.radius[0], s.radius[1], s.radius[2]);
+        if (!grp_of.count(gk)) {
+            grp_of[gk] = (int)b->groups.size();
+            Group g;
+            g.block = s.block;
+            for (int k = 0; k < 3; ++k) g.radius[k] = s.radius[k];
+            b->groups.push_back(g);
+        }
+        b->groups[grp_of[gk]].settings.push_back(i);
+    }
+    for (int k = 0; k < NSTREAMS; ++k) {
+        if (cudaStreamCreateWithFlags(&b->streams[k], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming) != cudaSuccess)
+            return bail(fail(NRR_E_CUDA, "stream/event creation"));
+    }
+    if (cudaStreamCreateWithFlags(&b->launch, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(NRR_E_CUDA, "stream/event creation"));
+
+    if (flags & NRR_BATCH_AUTOTUNE) {
+        // one eager run for real inputs, then tune every match variant on its
+        // largest setting
+        if ((st = batch_enqueue(b, b->launch)) != NRR_OK) return bail(st);
+        if (cudaStreamSynchronize(b->launch) != cudaSuccess) return bail(fail(NRR_E_CUDA, "sync"));
+        for (auto &G : b->groups) {
+            int best_s = G.settings[0];
+            for (int s_ : G.settings)
+                if (b->sels[b->outs[s_].sel].cap > b->sels[b->outs[best_s].sel].cap) best_s = s_;
+            const SettingOut &o = b->outs[best_s];
+            const SelEntry &se = b->sels[o.sel];
+            int32_t n = 0;
+            if (cudaMemcpy(&n, se.d_n, sizeof(n), cudaMemcpyDeviceToHost) != cudaSuccess)
+                return bail(fail(NRR_E_CUDA, "count copy"));
+            if (n < 1) continue;
+            const BoxEntry *bx = nullptr;
+            for (auto &e : b->boxes)
+                if (e.block == G.block) bx = &e;
+            st = nrr_autotune_match(b->preop, b->intraop, bx->buf, NRR_U16, dims, se.centers, n, G.block, G.radius,
+                                    o.disp, o.ncc, o.valid, nullptr, nullptr, b->launch);
+            if (st != NRR_OK) return bail(st);
+        }
+    }
+    if (flags & NRR_BATCH_GRAPH) {
+        if (cudaStreamBeginCapture(b->launch, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+            return bail(fail(NRR_E_CUDA, "cudaStreamBeginCapture"));
+        st = batch_enqueue(b, b->launch);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->launch, &g);
+        if (st != NRR_OK) {
+            if (g) cudaGraphDestroy(g);
+            return bail(st);
+        }
+        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamEndCapture"));
+        b->graph = g;
+        e = cudaGraphInstantiate(&b->exec, g, 0);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaGraphInstantiate"));
+    }
+    *out = b;
+    return NRR_OK;
+}
+
+nrr_status nrr_batch_run(nrr_batch b, void *stream)
+{
+    clear_error();
+    if (!b) return fail(NRR_E_INVALID, "NULL plan");
+    cudaStream_t s = (cudaStream_t)stream;
+    NRR_CUDA_TRY(cudaEventRecord(b->ev_in, s));
+    NRR_CUDA_TRY(cudaStreamWaitEvent(b->launch, b->ev_in, 0));
+    if (b->exec) {
+        NRR_CUDA_TRY(cudaGraphLaunch(b->exec, b->launch));
+        count_launches((int)(b->boxes.size() + b->sels.size() * 14));
+        for (auto &G : b->groups) count_launches((int)((G.settings.size() + MATCH_MAX_JOBS - 1) / MATCH_MAX_JOBS));
+    } else {
+        nrr_status st = batch_enqueue(b, b->launch);
+        if (st != NRR_OK) return st;
+    }
+    NRR_CUDA_TRY(cudaEventRecord(b->ev_out, b->launch));
+    NRR_CUDA_TRY(cudaStreamWaitEvent(s, b->ev_out, 0));
+    return NRR_OK;
+}
+
+nrr_status nrr_batch_view_get(nrr_batch b, int32_t setting, nrr_batch_view *view)
+{
+    clear_error();
+    if (!b || !view || setting < 0 || setting >= (int32_t)b->outs.size())
+        return fail(NRR_E_INVALID, "bad plan, setting index or view");
+    const SettingOut &o = b->outs[setting];
+    const SelEntry &se = b->sels[o.sel];
+    view->centers = se.centers;
+    view->n_blocks = se.d_n;
+    view->disp = o.disp;
+    view->ncc = o.ncc;
+    view->valid = o.valid;
+    view->capacity = se.cap;
+    return NRR_OK;
+}
+
+nrr_status nrr_batch_destroy(nrr_batch b)
+{
+    clear_error();
+    if (!b) return NRR_OK;
+    cudaStreamSynchronize(b->launch);
+    batch_free(b);
+    return NRR_OK;
+}
+
+}  // extern "C"

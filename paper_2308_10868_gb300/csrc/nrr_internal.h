@@ -54,7 +54,18 @@ inline size_t boxsum_s2_offset(nrr_dims dims, nrr_dtype dtype)
 nrr_status launch_boxsums(const void *d_intraop, nrr_dtype dtype, nrr_dims dims, int32_t block, void *d_boxsums,
                           cudaStream_t stream);
 
-// Match kernel launch (box sums already computed).
+// Match kernel launch (box sums already computed).  One launch serves up to
+// MATCH_MAX_JOBS lists of blocks that share the volume pair, block size and
+// search radius (one job per registration or per parameter setting).
+constexpr int MATCH_MAX_JOBS = 16;
+struct MatchJob {
+    const int32_t *centers;  // [cap][3]
+    const int32_t *d_n;      // optional device count (<= cap)
+    int32_t cap;
+    int32_t *disp;
+    double *ncc;
+    uint8_t *valid;
+};
 struct MatchLaunch {
     const void *preop;
     const void *intraop;
@@ -62,16 +73,35 @@ struct MatchLaunch {
     const void *s2;
     nrr_dtype dtype;
     nrr_dims dims;
-    const int32_t *centers;
-    int32_t n_blocks;
-    const int32_t *d_n_blocks;
     int32_t block;
     int32_t radius[3];
-    int32_t *disp;
-    double *ncc;
-    uint8_t *valid;
+    int n_jobs;
+    MatchJob jobs[MATCH_MAX_JOBS];
+    int ctas_per_sm;  // persistent CTAs per SM; 0 = as many as fit
     unsigned int *err;
 };
 nrr_status launch_match(const MatchLaunch &a, cudaStream_t stream);
+
+// Upper bound on resident match CTAs per SM for this launch's variant.
+nrr_status match_occupancy(const MatchLaunch &a, int *ctas_per_sm);
+
+// Autotuned persistent CTAs per SM for a match variant (0 = as many as fit).
+int tuned_ctas_per_sm(nrr_dtype dtype, int block, const int32_t *radius);
+
+// Autotuner entry used by the batch plan (C ABI function).
+// Block selection on caller-provided scratch (no allocation, no host sync).
+struct SelectPlan {
+    int gx, gy, gz;
+    long long ng;
+    int nchunks;
+    size_t off_keys, off_hist, off_state, off_cnt, bytes;
+};
+SelectPlan select_plan(nrr_dims d, int stride);
+nrr_status enqueue_select(const uint16_t *preop, const uint8_t *mask, nrr_dims d, int block, int stride, double frac,
+                          int32_t *centers, int32_t max_blocks, int32_t *d_n_selected, unsigned char *ws,
+                          const SelectPlan &p, cudaStream_t s);
+// Offset of the selected count (int64) inside the selection scratch.
+size_t select_count_offset(const SelectPlan &p);
+nrr_status check_select_args(nrr_dims dims, int32_t block, int32_t stride, double frac);
 
 }  // namespace nrr

@@ -47,16 +47,12 @@ struct MatchParams {
     const void *s1;
     const void *s2;
     int nx, ny, nz;
-    const int32_t *centers;
-    int32_t n_blocks;
-    const int32_t *d_n_blocks;
     int ry, rz;
     int bx;   // TMA box extent along x of the window (elements)
     int btx;  // TMA box extent along x of the floating block (elements)
     int pf;   // row pitch of the float window (floats)
-    int32_t *disp;
-    double *ncc;
-    uint8_t *valid;
+    int n_jobs;
+    MatchJob jobs[MATCH_MAX_JOBS];
     unsigned int *err;
 };
 
@@ -86,6 +82,7 @@ struct MatchScratch {
     int bcode[MATCH_MAX_WARPS];
     int bok[MATCH_MAX_WARPS];
     int nsurv;
+    int jstart[MATCH_MAX_JOBS + 1];  // first work item of each job
 };
 
 struct MatchLayout {
@@ -173,8 +170,8 @@ __device__ __forceinline__ float u16_minus(uint32_t u, float c_plus_2p23)
     return __fsub_rn(__uint_as_float(0x4B000000u | u), c_plus_2p23);
 }
 
-__device__ __forceinline__ void write_result(const MatchParams &a, int blk, const Cand &b, int P, int py, int rx,
-                                             int ry, int rz)
+__device__ __forceinline__ void write_result(const MatchJob &a, int blk, const Cand &b, int P, int py, int rx, int ry,
+                                             int rz)
 {
     if (b.ok) {
         int dxi = b.code % P, dyi = (b.code / P) % py, dzi = b.code / (P * py);
@@ -236,15 +233,34 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nthr = blockDim.x, nwarp = nthr >> 5;
-    int n = a.n_blocks;
-    if (a.d_n_blocks) {
-        int m = *a.d_n_blocks;
-        n = m < 0 ? 0 : (m < n ? m : n);
+    if (tid == 0) {
+        int w = 0;
+        for (int j = 0; j < a.n_jobs; ++j) {
+            sc->jstart[j] = w;
+            int m = a.jobs[j].cap;
+            if (a.jobs[j].d_n) {
+                const int d = *a.jobs[j].d_n;
+                m = d < 0 ? 0 : (d < m ? d : m);
+            }
+            w += m;
+        }
+        sc->jstart[a.n_jobs] = w;
     }
+    __syncthreads();
+    const int n = sc->jstart[a.n_jobs];  // work items over all jobs
+    // work item -> (job, index within the job)
+    auto locate = [&](int w, int &j, int &i) {
+        j = 0;
+        while (j + 1 < a.n_jobs && w >= sc->jstart[j + 1]) ++j;
+        i = w - sc->jstart[j];
+    };
     const uint32_t tx_bytes = (uint32_t)((bx * wy * wz + btx * B * B) * (int)sizeof(T));
     // Thread 0 issues both copies of block b (its centre must be inside).
     auto issue = [&](int b) {
-        const int cx = a.centers[3 * b + 0], cy = a.centers[3 * b + 1], cz = a.centers[3 * b + 2];
+        int j, i;
+        locate(b, j, i);
+        const int32_t *cc = a.jobs[j].centers + 3 * i;
+        const int cx = cc[0], cy = cc[1], cz = cc[2];
         const int x0 = cx - H - RX, xt = cx - H;
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(bar, tx_bytes);
@@ -260,9 +276,12 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
     int inflight = -1;  // block whose copies are in flight (same value in every thread)
 
     for (int blk = blockIdx.x; blk < n; blk += gridDim.x) {
-        const int cx = a.centers[3 * blk + 0], cy = a.centers[3 * blk + 1], cz = a.centers[3 * blk + 2];
+        int job, bi;
+        locate(blk, job, bi);
+        const MatchJob &J = a.jobs[job];
+        const int cx = J.centers[3 * bi + 0], cy = J.centers[3 * bi + 1], cz = J.centers[3 * bi + 2];
         if (!center_inside<H>(cx, cy, cz, nx, ny, nz)) {
-            if (tid == 0) write_result(a, blk, Cand{0.0, 0, 0, 0}, P, py, RX, ry, rz);
+            if (tid == 0) write_result(J, bi, Cand{0.0, 0, 0, 0}, P, py, RX, ry, rz);
             continue;
         }
         if (inflight != blk) {
@@ -291,7 +310,7 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
         if (!__syncthreads_and(got)) {
             if (tid == 0) {
                 atomicOr(a.err, DEV_ERR_TIMEOUT);
-                write_result(a, blk, Cand{0.0, 0, 0, 0}, P, py, RX, ry, rz);
+                write_result(J, bi, Cand{0.0, 0, 0, 0}, P, py, RX, ry, rz);
             }
             mbar_wait_bounded(bar, phase, WAIT_LIMIT_NS);  // let an in-flight copy land before exiting
             return;
@@ -426,7 +445,7 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
         __syncthreads();
         const BlockConst bc = sc->bc;
         if (bc.flat) {  // flat floating block: NCC undefined for every shift
-            if (tid == 0) write_result(a, blk, Cand{0.0, 0, 0, 0}, P, py, RX, ry, rz);
+            if (tid == 0) write_result(J, bi, Cand{0.0, 0, 0, 0}, P, py, RX, ry, rz);
             __syncthreads();
             continue;
         }
@@ -470,7 +489,10 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
         {
             int nb = blk + gridDim.x;
             if (nb < n) {
-                const int ncx = a.centers[3 * nb + 0], ncy = a.centers[3 * nb + 1], ncz = a.centers[3 * nb + 2];
+                int nj, ni;
+                locate(nb, nj, ni);
+                const int32_t *nc = a.jobs[nj].centers + 3 * ni;
+                const int ncx = nc[0], ncy = nc[1], ncz = nc[2];
                 if (center_inside<H>(ncx, ncy, ncz, nx, ny, nz)) {
                     if (tid == 0) issue(nb);
                     inflight = nb;
@@ -708,7 +730,7 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
                 Cand c{sc->bs[w], sc->bn2[w], sc->bcode[w], sc->bok[w]};
                 if (cand_better(c, best)) best = c;
             }
-            write_result(a, blk, best, P, py, RX, ry, rz);
+            write_result(J, bi, best, P, py, RX, ry, rz);
         }
         __syncthreads();
     }
@@ -751,8 +773,12 @@ nrr_status launch_match_variant(const MatchLaunch &m, cudaStream_t stream)
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, L.total);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (occ < 1) return fail(NRR_E_INVALID, "match kernel does not fit on an SM (%d B shared)", L.total);
+    if (m.ctas_per_sm > 0 && m.ctas_per_sm < occ) occ = m.ctas_per_sm;
+    long long cap = 0;
+    for (int j = 0; j < m.n_jobs; ++j) cap += m.jobs[j].cap;
     long long grid = (long long)occ * sm_count();
-    if (grid > m.n_blocks) grid = m.n_blocks;
+    if (grid > cap) grid = cap;
+    if (grid < 1) return NRR_OK;
 
     MatchParams p;
     p.preop = m.preop;
@@ -762,17 +788,13 @@ nrr_status launch_match_variant(const MatchLaunch &m, cudaStream_t stream)
     p.nx = m.dims.nx;
     p.ny = m.dims.ny;
     p.nz = m.dims.nz;
-    p.centers = m.centers;
-    p.n_blocks = m.n_blocks;
-    p.d_n_blocks = m.d_n_blocks;
     p.ry = ry;
     p.rz = rz;
     p.bx = bx;
     p.btx = btx;
     p.pf = pf;
-    p.disp = m.disp;
-    p.ncc = m.ncc;
-    p.valid = m.valid;
+    p.n_jobs = m.n_jobs;
+    for (int j = 0; j < MATCH_MAX_JOBS; ++j) p.jobs[j] = j < m.n_jobs ? m.jobs[j] : MatchJob{};
     p.err = m.err;
     kern<<<(unsigned)grid, threads, L.total, stream>>>(p, mapJ, mapI);
     e = cudaGetLastError();
@@ -781,33 +803,54 @@ nrr_status launch_match_variant(const MatchLaunch &m, cudaStream_t stream)
     return NRR_OK;
 }
 
+template <typename T, int B, int P>
+nrr_status occupancy_variant(const MatchLaunch &m, int *occ)
+{
+    constexpr int ALIGN = 16 / (int)sizeof(T);
+    constexpr int WX = B + P - 1;
+    const int ry = m.radius[1], rz = m.radius[2], py = 2 * ry + 1, pz = 2 * rz + 1;
+    const int bx = round_up_i(WX + ALIGN - 1, ALIGN), btx = round_up_i(B + ALIGN - 1, ALIGN);
+    const MatchLayout L = match_layout((int)sizeof(T), B, P, bx, btx, match_pitch(WX), B + 2 * ry, B + 2 * rz, py, pz);
+    auto kern = match_kernel<T, B, P>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, round_up_i(py * pz, 32), L.total);
+    if (e != cudaSuccess) return cuda_fail(e, "match occupancy query");
+    return NRR_OK;
+}
+
 template <typename T, int B>
-nrr_status launch_match_b(const MatchLaunch &m, cudaStream_t stream)
+nrr_status launch_match_b(const MatchLaunch &m, cudaStream_t stream, int *occ)
 {
     switch (m.radius[0]) {
-    case 0: return launch_match_variant<T, B, 1>(m, stream);
-    case 1: return launch_match_variant<T, B, 3>(m, stream);
-    case 2: return launch_match_variant<T, B, 5>(m, stream);
-    case 3: return launch_match_variant<T, B, 7>(m, stream);
-    case 4: return launch_match_variant<T, B, 9>(m, stream);
-    case 5: return launch_match_variant<T, B, 11>(m, stream);
-    case 6: return launch_match_variant<T, B, 13>(m, stream);
-    case 7: return launch_match_variant<T, B, 15>(m, stream);
+#define NRR_CASE(r, p) \
+    case r: return occ ? occupancy_variant<T, B, p>(m, occ) : launch_match_variant<T, B, p>(m, stream);
+        NRR_CASE(0, 1)
+        NRR_CASE(1, 3)
+        NRR_CASE(2, 5)
+        NRR_CASE(3, 7)
+        NRR_CASE(4, 9)
+        NRR_CASE(5, 11)
+        NRR_CASE(6, 13)
+        NRR_CASE(7, 15)
+#undef NRR_CASE
     }
     return fail(NRR_E_INVALID, "radius x %d outside 0..7", m.radius[0]);
 }
 
 // One entry per (element type, block size); defined in the instantiation
 // translation units.
-nrr_status launch_match_u16_b3(const MatchLaunch &, cudaStream_t);
-nrr_status launch_match_u16_b5(const MatchLaunch &, cudaStream_t);
-nrr_status launch_match_u16_b7(const MatchLaunch &, cudaStream_t);
-nrr_status launch_match_u16_b9(const MatchLaunch &, cudaStream_t);
-nrr_status launch_match_u16_b11(const MatchLaunch &, cudaStream_t);
-nrr_status launch_match_f32_b3(const MatchLaunch &, cudaStream_t);
-nrr_status launch_match_f32_b5(const MatchLaunch &, cudaStream_t);
-nrr_status launch_match_f32_b7(const MatchLaunch &, cudaStream_t);
-nrr_status launch_match_f32_b9(const MatchLaunch &, cudaStream_t);
-nrr_status launch_match_f32_b11(const MatchLaunch &, cudaStream_t);
+nrr_status launch_match_u16_b3(const MatchLaunch &, cudaStream_t, int *);
+nrr_status launch_match_u16_b5(const MatchLaunch &, cudaStream_t, int *);
+nrr_status launch_match_u16_b7(const MatchLaunch &, cudaStream_t, int *);
+nrr_status launch_match_u16_b9(const MatchLaunch &, cudaStream_t, int *);
+nrr_status launch_match_u16_b11(const MatchLaunch &, cudaStream_t, int *);
+nrr_status launch_match_f32_b3(const MatchLaunch &, cudaStream_t, int *);
+nrr_status launch_match_f32_b5(const MatchLaunch &, cudaStream_t, int *);
+nrr_status launch_match_f32_b7(const MatchLaunch &, cudaStream_t, int *);
+nrr_status launch_match_f32_b9(const MatchLaunch &, cudaStream_t, int *);
+nrr_status launch_match_f32_b11(const MatchLaunch &, cudaStream_t, int *);
 
 }  // namespace nrr

@@ -19,5 +19,8 @@
 #endif
 
 namespace nrr {
-nrr_status NRR_FN(const MatchLaunch &m, cudaStream_t stream) { return launch_match_b<NRR_T, NRR_INST_B>(m, stream); }
+nrr_status NRR_FN(const MatchLaunch &m, cudaStream_t stream, int *occ)
+{
+    return launch_match_b<NRR_T, NRR_INST_B>(m, stream, occ);
+}
 }  // namespace nrr

@@ -309,14 +309,7 @@ void launch_keys(const uint16_t *preop, const uint8_t *mask, nrr_dims d, int str
 
 }  // namespace
 
-struct SelectPlan {
-    int gx, gy, gz;
-    long long ng;
-    int nchunks;
-    size_t off_keys, off_hist, off_state, off_cnt, bytes;
-};
-
-static SelectPlan select_plan(nrr_dims d, int stride)
+SelectPlan select_plan(nrr_dims d, int stride)
 {
     SelectPlan p;
     p.gx = (d.nx + stride - 1) / stride;
@@ -339,7 +332,7 @@ static SelectPlan select_plan(nrr_dims d, int stride)
 
 // Enqueue the whole selection on `s` using the scratch buffer `ws` (at least
 // select_plan().bytes, 256-byte aligned).  Reads nothing back.
-static nrr_status enqueue_select(const uint16_t *preop, const uint8_t *mask, nrr_dims d, int block, int stride,
+nrr_status enqueue_select(const uint16_t *preop, const uint8_t *mask, nrr_dims d, int block, int stride,
                                  double frac, int32_t *centers, int32_t max_blocks, int32_t *d_n_selected,
                                  unsigned char *ws, const SelectPlan &p, cudaStream_t s)
 {
@@ -372,6 +365,17 @@ static nrr_status enqueue_select(const uint16_t *preop, const uint8_t *mask, nrr
     return NRR_OK;
 }
 
+size_t select_count_offset(const SelectPlan &p) { return p.off_state + offsetof(SelState, nsel); }
+
+nrr_status check_select_args(nrr_dims dims, int32_t block, int32_t stride, double frac)
+{
+    nrr_status st = check_dims(dims, NRR_U16, block);
+    if (st != NRR_OK) return st;
+    if (stride < 1 || stride > 64) return fail(NRR_E_INVALID, "stride %d outside 1..64", stride);
+    if (!(frac > 0.0 && frac <= 1.0)) return fail(NRR_E_INVALID, "frac must be in (0, 1]");
+    return NRR_OK;
+}
+
 }  // namespace nrr
 
 using namespace nrr;
@@ -381,10 +385,8 @@ extern "C" nrr_status nrr_select_blocks(const uint16_t *d_preop, const uint8_t *
                                         int32_t *d_n_selected, int32_t *h_n_selected, void *stream)
 {
     clear_error();
-    nrr_status st = check_dims(dims, NRR_U16, block);
+    nrr_status st = check_select_args(dims, block, stride, frac);
     if (st != NRR_OK) return st;
-    if (stride < 1 || stride > 64) return fail(NRR_E_INVALID, "stride %d outside 1..64", stride);
-    if (!(frac > 0.0 && frac <= 1.0)) return fail(NRR_E_INVALID, "frac must be in (0, 1]");
     if (max_blocks < 0) return fail(NRR_E_INVALID, "max_blocks < 0");
     if (!d_preop || !d_mask) return fail(NRR_E_INVALID, "NULL volume or mask");
     if (max_blocks > 0 && !d_centers) return fail(NRR_E_INVALID, "NULL centre buffer");
@@ -396,7 +398,7 @@ extern "C" nrr_status nrr_select_blocks(const uint16_t *d_preop, const uint8_t *
                         (unsigned char *)ws, p, s);
     long long nsel = 0;
     if (st == NRR_OK && h_n_selected) {
-        cudaError_t e = cudaMemcpyAsync(&nsel, (unsigned char *)ws + p.off_state + offsetof(SelState, nsel),
+        cudaError_t e = cudaMemcpyAsync(&nsel, (unsigned char *)ws + select_count_offset(p),
                                         sizeof(nsel), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = cuda_fail(e, "reading the selection count");

@@ -1,0 +1,398 @@
+// Serving: registrations submitted one by one and run with continuous
+// batching on one GPU.
+//
+// The paper serves the operating room from a client/server setup whose
+// server spreads each registration over remote clusters, with a work pool
+// that tolerates failures (Sec. 4.1 "Ease-of-use", "Multi-Level Fault
+// Tolerance").  On one GB300 a server is a scheduler thread in front of a
+// set of CUDA streams ("slots"):
+//   - nrr_submit queues a request (device-resident volumes, parameters) and
+//     returns a ticket at once;
+//   - the scheduler admits queued requests in arrival order whenever a slot
+//     is free and the free device memory, less a reserve, covers the
+//     request's scratch and result buffers; several admitted requests run
+//     at the same time on different streams, so their kernels overlap on the
+//     device, and a new request starts as soon as any earlier one finishes;
+//   - each request runs the whole path (selection with a device-side count,
+//     box sums, matching) on its slot stream, then a host callback stamps
+//     its completion time;
+//   - nrr_poll reports NRR_PENDING or the result (device pointers owned by
+//     the library until nrr_release, the block count and the latencies).
+// Failures are contained per request: an allocation or launch error marks
+// that request failed (nrr_poll returns the status) and the server goes on.
+// Host-side fault injection for tests: NRR_FAULT=alloc makes every
+// admission's allocation fail; NRR_FAULT=alloc_once fails the next one only.
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "nrr_internal.h"
+
+namespace nrr {
+namespace {
+
+double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+enum ReqState { QUEUED, RUNNING, DONE, FAILED };
+
+struct Req {
+    uint64_t ticket;
+    nrr_request r;
+    ReqState state = QUEUED;
+    nrr_status status = NRR_OK;
+    int slot = -1;
+    void *mem = nullptr;
+    size_t bytes = 0;
+    int32_t cap = 0;
+    int32_t *centers = nullptr, *d_n = nullptr, *disp = nullptr;
+    double *ncc = nullptr;
+    uint8_t *valid = nullptr;
+    int32_t n_host = -1;  // count, read once at the first poll after completion
+    std::atomic<int> finished{0};
+    double t_submit = 0, t_admit = 0;
+    std::atomic<double> t_done{0};
+};
+
+struct Server {
+    int device = 0;
+    int nslots = 0;
+    size_t reserve = 0;
+    size_t max_queue = 65536;
+    std::vector<cudaStream_t> slots;
+    std::vector<uint64_t> slot_req;  // 0 = free
+    std::deque<uint64_t> queue;
+    std::unordered_map<uint64_t, Req *> reqs;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::thread worker;
+    bool stop = false;
+    uint64_t next = 1;
+    unsigned int *err = nullptr;
+};
+
+std::mutex g_server_mu;
+Server *g_server = nullptr;
+
+struct Layout {
+    SelectPlan sp;
+    size_t off_ws, off_box, off_centers, off_n, off_disp, off_ncc, off_valid, total;
+    int32_t cap;
+};
+
+Layout layout_of(const nrr_request &r)
+{
+    Layout L;
+    L.sp = select_plan(r.dims, r.stride);
+    long long cap = (long long)(0.5 + (double)L.sp.ng * r.frac) + 1;
+    if (cap > L.sp.ng) cap = L.sp.ng;
+    L.cap = (int32_t)(cap < 1 ? 1 : cap);
+    size_t o = 0;
+    L.off_ws = o;
+    o += align_up(L.sp.bytes, 256);
+    L.off_box = o;
+    o += align_up(boxsum_bytes(r.dims, r.dtype), 256);
+    L.off_centers = o;
+    o += align_up((size_t)L.cap * 12, 256);
+    L.off_n = o;
+    o += 256;
+    L.off_disp = o;
+    o += align_up((size_t)L.cap * 12, 256);
+    L.off_ncc = o;
+    o += align_up((size_t)L.cap * 8, 256);
+    L.off_valid = o;
+    o += align_up((size_t)L.cap, 256);
+    L.total = o;
+    return L;
+}
+
+bool fault(const char *what)
+{
+    static std::atomic<int> once_used{0};
+    const char *f = getenv("NRR_FAULT");
+    if (!f) return false;
+    if (!strcmp(f, what)) return true;
+    if (!strncmp(f, what, strlen(what)) && !strcmp(f + strlen(what), "_once")) return once_used.exchange(1) == 0;
+    return false;
+}
+
+void CUDART_CB on_done(void *p)
+{
+    Req *q = (Req *)p;
+    q->t_done.store(now_s());
+    q->finished.store(1);
+}
+
+// Admit request q on slot k (server lock held).  Returns false if memory is
+// short right now (q stays queued).
+bool admit(Server *S, Req *q, int k)
+{
+    const nrr_request &r = q->r;
+    const Layout L = layout_of(r);
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && fr < L.total + S->reserve) {
+        bool busy = false;
+        for (uint64_t t : S->slot_req) busy |= t != 0;
+        if (busy) return false;  // wait for running requests to free memory
+        q->status = fail(NRR_E_NOMEM, "request needs %zu bytes, %zu free", L.total, fr);
+        q->state = FAILED;  // would never fit
+        return true;
+    }
+    cudaStream_t s = S->slots[k];
+    q->slot = k;
+    q->t_admit = now_s();
+    q->state = RUNNING;
+    S->slot_req[k] = q->ticket;
+    cudaError_t e = fault("alloc") ? cudaErrorMemoryAllocation : cudaMallocAsync(&q->mem, L.total, s);
+    if (e != cudaSuccess) {
+        q->mem = nullptr;
+        q->status = cuda_fail(e, "request allocation");
+        q->state = FAILED;
+        S->slot_req[k] = 0;
+        return true;
+    }
+    unsigned char *m = (unsigned char *)q->mem;
+    q->bytes = L.total;
+    q->cap = L.cap;
+    q->centers = (int32_t *)(m + L.off_centers);
+    q->d_n = (int32_t *)(m + L.off_n);
+    q->disp = (int32_t *)(m + L.off_disp);
+    q->ncc = (double *)(m + L.off_ncc);
+    q->valid = (uint8_t *)(m + L.off_valid);
+    nrr_status st = enqueue_select(r.d_select, r.d_mask, r.dims, r.block, r.stride, r.frac,
+                                   q->centers, q->cap, q->d_n, m + L.off_ws, L.sp, s);
+    if (st == NRR_OK) st = launch_boxsums(r.d_intraop, r.dtype, r.dims, r.block, m + L.off_box, s);
+    if (st == NRR_OK) {
+        MatchLaunch a{};
+        a.preop = r.d_preop;
+        a.intraop = r.d_intraop;
+        a.s1 = m + L.off_box;
+        a.s2 = m + L.off_box + boxsum_s2_offset(r.dims, r.dtype);
+        a.dtype = r.dtype;
+        a.dims = r.dims;
+        a.block = r.block;
+        for (int i = 0; i < 3; ++i) a.radius[i] = r.radius[i];
+        a.n_jobs = 1;
+        a.jobs[0] = MatchJob{q->centers, q->d_n, q->cap, q->disp, q->ncc, q->valid};
+        a.ctas_per_sm = tuned_ctas_per_sm(r.dtype, r.block, r.radius);
+        a.err = S->err;
+        st = launch_match(a, s);
+    }
+    if (st == NRR_OK && cudaLaunchHostFunc(s, on_done, q) != cudaSuccess) st = fail(NRR_E_CUDA, "host callback");
+    if (st != NRR_OK) {
+        q->status = st;
+        q->state = FAILED;
+        cudaStreamSynchronize(s);  // nothing of this request may still run
+        cudaFreeAsync(q->mem, s);
+        q->mem = nullptr;
+        S->slot_req[k] = 0;
+    }
+    return true;
+}
+
+void worker_main(Server *S)
+{
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (!S->stop) {
+        // retire finished requests, freeing their slots
+        for (int k = 0; k < S->nslots; ++k) {
+            uint64_t t = S->slot_req[k];
+            if (!t) continue;
+            auto it = S->reqs.find(t);
+            if (it == S->reqs.end()) {
+                S->slot_req[k] = 0;
+                continue;
+            }
+            Req *q = it->second;
+            if (q->finished.load()) {
+                q->state = DONE;
+                S->slot_req[k] = 0;
+                S->cv.notify_all();
+            }
+        }
+        // admit in arrival order while slots and memory allow
+        bool progressed = false;
+        while (!S->queue.empty()) {
+            int k = -1;
+            for (int i = 0; i < S->nslots; ++i)
+                if (!S->slot_req[i]) {
+                    k = i;
+                    break;
+                }
+            if (k < 0) break;
+            const uint64_t t = S->queue.front();
+            auto it = S->reqs.find(t);
+            if (it == S->reqs.end()) {  // released while queued
+                S->queue.pop_front();
+                continue;
+            }
+            if (!admit(S, it->second, k)) break;
+            S->queue.pop_front();
+            progressed = true;
+        }
+        if (progressed) S->cv.notify_all();
+        S->cv.wait_for(lk, std::chrono::microseconds(50));
+    }
+}
+
+}  // namespace
+}  // namespace nrr
+
+using namespace nrr;
+
+extern "C" {
+
+nrr_status nrr_server_start(int32_t slots, size_t reserve_bytes)
+{
+    clear_error();
+    if (slots < 1 || slots > 64) return fail(NRR_E_INVALID, "slots must be 1..64");
+    std::lock_guard<std::mutex> g(g_server_mu);
+    if (g_server) return fail(NRR_E_INVALID, "server already running");
+    Server *S = new Server();
+    if (cudaGetDevice(&S->device) != cudaSuccess) {
+        delete S;
+        return fail(NRR_E_CUDA, "cudaGetDevice");
+    }
+    nrr_status st = device_error_word(&S->err);
+    if (st != NRR_OK) {
+        delete S;
+        return st;
+    }
+    S->nslots = slots;
+    S->reserve = reserve_bytes;
+    S->slots.resize(slots);
+    S->slot_req.assign(slots, 0);
+    for (int k = 0; k < slots; ++k) {
+        if (cudaStreamCreateWithFlags(&S->slots[k], cudaStreamNonBlocking) != cudaSuccess) {
+            for (int j = 0; j < k; ++j) cudaStreamDestroy(S->slots[j]);
+            delete S;
+            return fail(NRR_E_CUDA, "stream creation");
+        }
+    }
+    S->worker = std::thread(worker_main, S);
+    g_server = S;
+    return NRR_OK;
+}
+
+nrr_status nrr_server_stop(void)
+{
+    clear_error();
+    Server *S;
+    {
+        std::lock_guard<std::mutex> g(g_server_mu);
+        S = g_server;
+        g_server = nullptr;
+    }
+    if (!S) return NRR_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv.notify_all();
+    S->worker.join();
+    for (auto &st : S->slots) cudaStreamSynchronize(st);
+    for (auto &kv : S->reqs) {
+        Req *q = kv.second;
+        if (q->mem) cudaFree(q->mem);
+        delete q;
+    }
+    for (auto &st : S->slots) cudaStreamDestroy(st);
+    delete S;
+    return NRR_OK;
+}
+
+nrr_status nrr_submit(const nrr_request *req, uint64_t *ticket)
+{
+    clear_error();
+    if (!req || !ticket) return fail(NRR_E_INVALID, "NULL request or ticket");
+    if (req->dtype != NRR_U16 && req->dtype != NRR_F32) return fail(NRR_E_INVALID, "unknown dtype");
+    nrr_status st = check_select_args(req->dims, req->block, req->stride, req->frac);
+    if (st != NRR_OK) return st;
+    st = check_dims(req->dims, req->dtype, req->block);
+    if (st != NRR_OK) return st;
+    for (int i = 0; i < 3; ++i)
+        if (req->radius[i] < 0 || req->radius[i] > 7) return fail(NRR_E_INVALID, "radius outside 0..7");
+    if (!req->d_preop || !req->d_intraop || !req->d_mask || !req->d_select)
+        return fail(NRR_E_INVALID, "NULL volume, mask or selection volume");
+    std::lock_guard<std::mutex> g(g_server_mu);
+    Server *S = g_server;
+    if (!S) return fail(NRR_E_INVALID, "no server running (nrr_server_start)");
+    Req *q = new Req();
+    q->r = *req;
+    q->t_submit = now_s();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->queue.size() >= S->max_queue) {
+            delete q;
+            return fail(NRR_E_CAPACITY, "request queue full");
+        }
+        q->ticket = S->next++;
+        S->reqs[q->ticket] = q;
+        S->queue.push_back(q->ticket);
+        *ticket = q->ticket;
+    }
+    S->cv.notify_all();
+    return NRR_OK;
+}
+
+nrr_status nrr_poll(uint64_t ticket, nrr_result *out)
+{
+    clear_error();
+    std::lock_guard<std::mutex> g(g_server_mu);
+    Server *S = g_server;
+    if (!S) return fail(NRR_E_INVALID, "no server running");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return fail(NRR_E_NOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    Req *q = it->second;
+    if (q->state == RUNNING && q->finished.load()) q->state = DONE;
+    if (q->state == FAILED) return fail(q->status, "request %llu failed", (unsigned long long)ticket);
+    if (q->state != DONE) return NRR_PENDING;
+    if (q->n_host < 0) {
+        int32_t n = 0;
+        cudaError_t e = cudaMemcpy(&n, q->d_n, sizeof(n), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "reading the block count");
+        q->n_host = n;
+    }
+    if (out) {
+        out->n_blocks = q->n_host;
+        out->centers = q->centers;
+        out->disp = q->disp;
+        out->ncc = q->ncc;
+        out->valid = q->valid;
+        out->queued_s = q->t_admit - q->t_submit;
+        out->latency_s = q->t_done.load() - q->t_submit;
+    }
+    return NRR_OK;
+}
+
+nrr_status nrr_release(uint64_t ticket)
+{
+    clear_error();
+    std::lock_guard<std::mutex> g(g_server_mu);
+    Server *S = g_server;
+    if (!S) return fail(NRR_E_INVALID, "no server running");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return fail(NRR_E_NOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    Req *q = it->second;
+    if (q->state == RUNNING && !q->finished.load())
+        return fail(NRR_E_INVALID, "request %llu still running", (unsigned long long)ticket);
+    if (q->mem) cudaFreeAsync(q->mem, S->slots[q->slot >= 0 ? q->slot : 0]);
+    S->reqs.erase(it);  // a queued request is simply dropped from the queue later
+    delete q;
+    return NRR_OK;
+}
+
+}  // extern "C"

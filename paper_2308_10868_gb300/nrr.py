@@ -28,6 +28,28 @@ class Dims(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32)]
 
 
+class Setting(C.Structure):
+    _fields_ = [("block", C.c_int32), ("stride", C.c_int32), ("radius", C.c_int32 * 3), ("frac", C.c_double)]
+
+
+class BatchView(C.Structure):
+    _fields_ = [("centers", C.c_void_p), ("n_blocks", C.c_void_p), ("disp", C.c_void_p), ("ncc", C.c_void_p),
+                ("valid", C.c_void_p), ("capacity", C.c_int32)]
+
+
+NRR_BATCH_GRAPH, NRR_BATCH_AUTOTUNE = 1, 2
+
+
+class Request(C.Structure):
+    _fields_ = [("d_preop", C.c_void_p), ("d_intraop", C.c_void_p), ("d_select", C.c_void_p),
+                ("d_mask", C.c_void_p), ("dims", Dims), ("dtype", C.c_int), ("block", C.c_int32),
+                ("stride", C.c_int32), ("radius", C.c_int32 * 3), ("frac", C.c_double)]
+
+
+class Result(C.Structure):
+    _fields_ = [("n_blocks", C.c_int32), ("centers", C.c_void_p), ("disp", C.c_void_p), ("ncc", C.c_void_p),
+                ("valid", C.c_void_p), ("queued_s", C.c_double), ("latency_s", C.c_double)]
+
 SIGNATURES = {
     "nrr_status_string": (C.c_char_p, [C.c_int]),
     "nrr_last_error": (C.c_char_p, []),
@@ -39,6 +61,20 @@ SIGNATURES = {
     "nrr_block_match": (C.c_int, [_P, _P, C.c_int, Dims, _P, _I32, _P, _I32, _P, _P, _P, _P, _P]),
     "nrr_block_match_bs": (C.c_int, [_P, _P, _P, C.c_int, Dims, _P, _I32, _P, _I32, _P, _P, _P, _P, _P]),
     "nrr_device_status": (C.c_int, [_P]),
+    "nrr_autotune_match": (C.c_int, [_P, _P, _P, C.c_int, Dims, _P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P]),
+    "nrr_tuning_get": (C.c_int, [C.c_int, _I32, _P, _P]),
+    "nrr_tuning_set": (C.c_int, [C.c_int, _I32, _P, _I32]),
+    "nrr_tuning_save": (C.c_int, [C.c_char_p]),
+    "nrr_tuning_load": (C.c_int, [C.c_char_p]),
+    "nrr_batch_create": (C.c_int, [_P, _P, _P, Dims, _P, _I32, _I32, _P]),
+    "nrr_batch_run": (C.c_int, [_P, _P]),
+    "nrr_batch_view_get": (C.c_int, [_P, _I32, _P]),
+    "nrr_batch_destroy": (C.c_int, [_P]),
+    "nrr_server_start": (C.c_int, [_I32, C.c_size_t]),
+    "nrr_server_stop": (C.c_int, []),
+    "nrr_submit": (C.c_int, [_P, _P]),
+    "nrr_poll": (C.c_int, [C.c_uint64, _P]),
+    "nrr_release": (C.c_int, [C.c_uint64]),
 }
 
 _lib = None
@@ -200,6 +236,145 @@ def block_match(preop: torch.Tensor, intraop: torch.Tensor, centers: torch.Tenso
 def kernel_launches() -> int:
     """Kernels launched by the library so far in this process."""
     return int(lib().nrr_kernel_launches())
+
+
+class _DeviceArray:
+    """A raw device pointer seen through __cuda_array_interface__ (no copy)."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+def _wrap(ptr, shape, typestr, device):
+    return torch.as_tensor(_DeviceArray(ptr, shape, typestr), device=device)
+
+
+def autotune_match(preop, intraop, box, centers, block: int, radius, stream=None):
+    """Time the match kernel at every feasible CTAs-per-SM on these inputs and
+    keep the fastest for this (dtype, block, radius).  Returns (ctas, ms)."""
+    n = centers.shape[0]
+    out = (torch.empty((n, 3), dtype=torch.int32, device=preop.device),
+           torch.empty(n, dtype=torch.float64, device=preop.device),
+           torch.empty(n, dtype=torch.uint8, device=preop.device))
+    r = (C.c_int32 * 3)(*radius3(radius))
+    k, ms = C.c_int32(0), C.c_float(0)
+    _check(lib().nrr_autotune_match(_ptr(preop), _ptr(intraop), _ptr(box), _dtype_code(preop), _dims(preop),
+                                    _ptr(centers), n, block, r, _ptr(out[0]), _ptr(out[1]), _ptr(out[2]),
+                                    C.byref(k), C.byref(ms), _stream(stream)), "nrr_autotune_match")
+    return int(k.value), float(ms.value)
+
+
+def tuning_get(dtype_code: int, block: int, radius) -> int:
+    r = (C.c_int32 * 3)(*radius3(radius))
+    v = C.c_int32(0)
+    _check(lib().nrr_tuning_get(dtype_code, block, r, C.byref(v)), "nrr_tuning_get")
+    return int(v.value)
+
+
+def tuning_set(dtype_code: int, block: int, radius, ctas_per_sm: int):
+    r = (C.c_int32 * 3)(*radius3(radius))
+    _check(lib().nrr_tuning_set(dtype_code, block, r, ctas_per_sm), "nrr_tuning_set")
+
+
+class BatchPlan:
+    """A batched parameter search over one uint16 volume pair (see
+    nrr_batch_create).  ``settings`` is a list of (block, stride, radius,
+    frac) with radius an int or 3 ints."""
+
+    def __init__(self, preop, intraop, mask, settings, graph: bool = True, autotune: bool = False):
+        for t, nm in ((preop, "preop"), (intraop, "intraop"), (mask, "mask")):
+            _cuda_contig(t, nm)
+        self._keep = (preop, intraop, mask)  # the plan holds their addresses
+        self.device = preop.device
+        arr = (Setting * len(settings))()
+        for i, (b, st, r, f) in enumerate(settings):
+            arr[i].block, arr[i].stride, arr[i].frac = b, st, float(f)
+            arr[i].radius[:] = list(radius3(r))
+        self.settings = list(settings)
+        flags = (NRR_BATCH_GRAPH if graph else 0) | (NRR_BATCH_AUTOTUNE if autotune else 0)
+        h = C.c_void_p(0)
+        _check(lib().nrr_batch_create(_ptr(preop), _ptr(intraop), _ptr(mask), _dims(preop), arr, len(settings),
+                                      flags, C.byref(h)), "nrr_batch_create")
+        self._h = h
+
+    def run(self, stream=None):
+        _check(lib().nrr_batch_run(self._h, _stream(stream)), "nrr_batch_run")
+
+    def view(self, s: int):
+        """Device tensors (no copy) of setting s: n (1,), centres, disp, ncc,
+        valid, each with the plan's capacity."""
+        v = BatchView()
+        _check(lib().nrr_batch_view_get(self._h, s, C.byref(v)), "nrr_batch_view_get")
+        cap, dev = v.capacity, self.device
+        return (_wrap(v.n_blocks, (1,), "<i4", dev), _wrap(v.centers, (cap, 3), "<i4", dev),
+                _wrap(v.disp, (cap, 3), "<i4", dev), _wrap(v.ncc, (cap,), "<f8", dev), _wrap(v.valid, (cap,), "|u1", dev))
+
+    def result(self, s: int):
+        """Copies of setting s's results, trimmed to its count (synchronises)."""
+        n, c, d, x, v = self.view(s)
+        k = int(n.item())
+        return c[:k].clone(), d[:k].clone(), x[:k].clone(), v[:k].clone()
+
+    def close(self):
+        if self._h:
+            lib().nrr_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Registration server with continuous batching (see nrr_server_start).
+    Volumes passed to submit() must stay alive until the request is done."""
+
+    def __init__(self, slots: int = 8, reserve_bytes: int = 1 << 30):
+        _check(lib().nrr_server_start(slots, reserve_bytes), "nrr_server_start")
+        self._live = {}
+
+    def submit(self, preop, intraop, mask, block: int, stride: int, radius, frac: float, select=None) -> int:
+        for t, nm in ((preop, "preop"), (intraop, "intraop"), (mask, "mask")):
+            _cuda_contig(t, nm)
+        sel = preop if select is None else select
+        if _dtype_code(sel) != NRR_U16:
+            raise TypeError("selection needs a uint16 volume (pass select= for float32 requests)")
+        r = Request()
+        r.d_preop, r.d_intraop, r.d_select, r.d_mask = (preop.data_ptr(), intraop.data_ptr(), sel.data_ptr(),
+                                                         mask.data_ptr())
+        r.dims, r.dtype, r.block, r.stride, r.frac = _dims(preop), _dtype_code(preop), block, stride, float(frac)
+        r.radius[:] = list(radius3(radius))
+        t = C.c_uint64(0)
+        _check(lib().nrr_submit(C.byref(r), C.byref(t)), "nrr_submit")
+        self._live[t.value] = (preop, intraop, mask, sel)
+        return int(t.value)
+
+    def poll(self, ticket: int):
+        """None while pending; else dict with device tensors (views, valid
+        until release) and latencies.  Raises NrrError if the request failed."""
+        res = Result()
+        st = lib().nrr_poll(ticket, C.byref(res))
+        if st == NRR_PENDING:
+            return None
+        _check(st, "nrr_poll")
+        n = res.n_blocks
+        dev = self._live[ticket][0].device if ticket in self._live else torch.device("cuda")
+        wrap = (lambda p, sh, ty: _wrap(p, sh, ty, dev)) if n > 0 else (lambda p, sh, ty: torch.empty(
+            sh, dtype={"<i4": torch.int32, "<f8": torch.float64, "|u1": torch.uint8}[ty], device=dev))
+        return {"n": n, "centers": wrap(res.centers, (n, 3), "<i4"), "disp": wrap(res.disp, (n, 3), "<i4"),
+                "ncc": wrap(res.ncc, (n,), "<f8"), "valid": wrap(res.valid, (n,), "|u1"),
+                "queued_s": res.queued_s, "latency_s": res.latency_s}
+
+    def release(self, ticket: int):
+        _check(lib().nrr_release(ticket), "nrr_release")
+        self._live.pop(ticket, None)
+
+    def stop(self):
+        lib().nrr_server_stop()
+        self._live.clear()
 
 
 def device_status(stream=None) -> int:

@@ -80,3 +80,26 @@ def test_binding_refuses_cpu_tensors():
     v = torch.zeros((8, 8, 8), dtype=torch.int16)
     with pytest.raises(ValueError):
         nrr.select_blocks(v, torch.zeros((8, 8, 8), dtype=torch.uint8), 3, 2, 0.1)
+
+
+def test_serving_and_batch_arguments_need_no_device(L):
+    import ctypes as C
+
+    from paper_2308_10868_gb300 import nrr
+
+    r = nrr.Request()
+    t = C.c_uint64(0)
+    assert L.nrr_submit(C.byref(r), C.byref(t)) == -1  # block 0 is invalid
+    r.d_preop = r.d_intraop = r.d_select = r.d_mask = 1 << 20
+    r.dims, r.dtype, r.block, r.stride, r.frac = nrr.Dims(64, 64, 48), 0, 7, 2, 0.1
+    r.radius[:] = [3, 3, 3]
+    assert L.nrr_submit(C.byref(r), C.byref(t)) == -1  # no server running
+    assert b"no server" in L.nrr_last_error()
+    assert L.nrr_poll(1, None) == -1 and L.nrr_release(1) == -1
+    assert L.nrr_server_start(0, 0) == -1
+    s = (nrr.Setting * 1)()
+    s[0].block, s[0].stride, s[0].frac = 6, 2, 0.1
+    h = C.c_void_p(0)
+    assert L.nrr_batch_create(1 << 20, 1 << 20, 1 << 20, nrr.Dims(64, 64, 48), s, 1, 0, C.byref(h)) == -1
+    assert b"setting 0" in L.nrr_last_error()
+    assert L.nrr_batch_run(None, None) == -1

@@ -1,0 +1,104 @@
+"""Batched parameter search and autotuning (GPU).
+
+Every setting of a batch plan must give exactly what the single-registration
+path gives for that setting (and that path is checked against the oracle
+elsewhere); two settings per plan are also checked against the oracle
+directly.  Graph replay, eager runs and autotuned launch shapes must not
+change any bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2308_10868_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nrr():
+    from paper_2308_10868_gb300 import build as nbuild
+
+    nbuild.build()
+    from paper_2308_10868_gb300 import nrr as m
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return m
+
+
+@pytest.fixture(scope="module")
+def pair(nrr):
+    pre, intra, mask = synth.workload_pair("small")
+    return pre, intra, mask, nrr.to_device_u16(pre), nrr.to_device_u16(intra), torch.from_numpy(mask).cuda()
+
+
+SETTINGS = [(5, 2, 2, 0.05), (5, 2, 3, 0.05), (7, 2, 3, 0.10), (7, 2, 3, 0.04), (5, 3, (3, 1, 2), 0.08),
+            (9, 2, 4, 0.02), (7, 2, 3, 0.10), (5, 2, 2, 0.10)]
+
+
+def _single(nrr, dpre, dintra, dmask, s):
+    b, st, r, f = s
+    c = nrr.select_blocks(dpre, dmask, b, st, f)
+    d, n, v = nrr.block_match(dpre, dintra, c, b, r)
+    return [t.cpu().numpy() for t in (c, d, n, v)]
+
+
+def _same(a, b):
+    return all(np.array_equal(x.view(np.uint8), y.view(np.uint8)) for x, y in zip(a, b))
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_batch_equals_single_calls(nrr, pair, graph):
+    pre, intra, mask, dpre, dintra, dmask = pair
+    plan = nrr.BatchPlan(dpre, dintra, dmask, SETTINGS, graph=graph)
+    for rep in range(2):
+        plan.run()
+        torch.cuda.synchronize()
+        nrr.device_status()
+        for i, s in enumerate(SETTINGS):
+            got = [t.cpu().numpy() for t in plan.result(i)]
+            assert _same(got, _single(nrr, dpre, dintra, dmask, s)), (rep, i, s)
+    for i in (2, 4):
+        b, st, r, f = SETTINGS[i]
+        rc, _ = oracle.select_blocks(pre, mask, b, st, f)
+        rd, rn, rv = oracle.match(pre, intra, rc, b, r)
+        c, d, n, v = [t.cpu().numpy() for t in plan.result(i)]
+        assert np.array_equal(c, rc) and np.array_equal(d, rd) and np.array_equal(v, rv)
+        assert np.array_equal(n[~np.isnan(n)].view(np.int64), rn[~np.isnan(rn)].view(np.int64))
+    plan.close()
+
+
+def test_batch_more_jobs_than_one_launch_holds(nrr, pair):
+    pre, intra, mask, dpre, dintra, dmask = pair
+    fr = [0.02 + 0.005 * k for k in range(18)]  # 18 selections of one (b, R) variant: two launches
+    settings = [(5, 2, 2, f) for f in fr]
+    plan = nrr.BatchPlan(dpre, dintra, dmask, settings, graph=True)
+    plan.run()
+    torch.cuda.synchronize()
+    for i in (0, 15, 16, 17):
+        got = [t.cpu().numpy() for t in plan.result(i)]
+        assert _same(got, _single(nrr, dpre, dintra, dmask, settings[i]))
+    plan.close()
+
+
+def test_autotune_keeps_results(nrr, pair):
+    pre, intra, mask, dpre, dintra, dmask = pair
+    c = nrr.select_blocks(dpre, dmask, 7, 2, 0.1)
+    ref = [t.cpu().numpy() for t in nrr.block_match(dpre, dintra, c, 7, 4)]
+    box = nrr.boxsums(dintra, 7)
+    k, ms = nrr.autotune_match(dpre, dintra, box, c, 7, 4)
+    assert k >= 1 and ms > 0
+    assert nrr.tuning_get(0, 7, 4) in (0, k)
+    for forced in (1, 2):
+        nrr.tuning_set(0, 7, 4, forced)
+        got = [t.cpu().numpy() for t in nrr.block_match(dpre, dintra, c, 7, 4)]
+        assert _same(got, ref)
+    nrr.tuning_set(0, 7, 4, 0)
+    plan = nrr.BatchPlan(dpre, dintra, dmask, SETTINGS[:3], graph=True, autotune=True)
+    plan.run()
+    torch.cuda.synchronize()
+    for i, s in enumerate(SETTINGS[:3]):
+        assert _same([t.cpu().numpy() for t in plan.result(i)], _single(nrr, dpre, dintra, dmask, s))
+    plan.close()
