@@ -128,6 +128,42 @@ nrr_status nrr_select_blocks(const uint16_t *d_preop, const uint8_t *d_mask, nrr
                              int32_t *d_n_selected, int32_t *h_n_selected, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Block selection that allocates nothing.
+ *
+ * Some callers cannot allocate device memory when they call in: systems
+ * whose whole device-memory budget is reserved at start-up (an
+ * intra-operative workstation whose memory use must be fixed and verified in
+ * advance), code that runs where an allocation is not allowed (a host
+ * callback, a real-time thread that must not block in the allocator), or a
+ * host application whose own pool owns all device memory.
+ * nrr_select_blocks_noalloc does exactly what nrr_select_blocks does, with
+ * the same arguments, results and errors, but takes its scratch from a
+ * fixed array of NRR_SELECT_STATIC_SCRATCH_BYTES (32 MiB) built into the
+ * library instead of from an allocator: it calls no cudaMalloc, cudaFree or
+ * other allocating routine.  Every GPU that loads the library holds that
+ * array until the process exits.
+ *
+ *  - Limit: the scratch needs about 8 bytes per candidate grid point
+ *    (ceil(nx/stride) * ceil(ny/stride) * ceil(nz/stride)), so up to about
+ *    4 million grid points; a larger grid returns NRR_E_CAPACITY and writes
+ *    nothing.
+ *  - The first call on each device looks up the array's device address
+ *    (a one-time set-up, no allocation); make that first call before any
+ *    stream capture.
+ *  - All calls share the one array and each leaves its contents there (each
+ *    call clears what it needs zeroed before use).  Calls whose work could
+ *    overlap on the GPU (different streams without ordering between them,
+ *    or several host threads) race on it: order them on one stream or
+ *    serialise them.
+ *  - The paper has no counterpart of this entry point.
+ * ---------------------------------------------------------------------- */
+#define NRR_SELECT_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+nrr_status nrr_select_blocks_noalloc(const uint16_t *d_preop, const uint8_t *d_mask, nrr_dims dims,
+                                     int32_t block, int32_t stride, double frac,
+                                     int32_t *d_centers, int32_t max_blocks,
+                                     int32_t *d_n_selected, int32_t *h_n_selected, void *stream);
+
+/* ------------------------------------------------------------------------
  * Box sums of the reference image, the per-shift sums S_J and S_JJ of the
  * NCC (Sec. 3): for every voxel v whose b^3 block lies in the volume,
  *   S1[v] = sum of J over the block centred at v,

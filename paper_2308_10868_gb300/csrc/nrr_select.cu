@@ -17,6 +17,8 @@
 // deterministic.
 #include <math.h>
 
+#include <mutex>
+
 #include "nrr_internal.h"
 
 namespace nrr {
@@ -407,6 +409,77 @@ extern "C" nrr_status nrr_select_blocks(const uint16_t *d_preop, const uint8_t *
     if (st != NRR_OK) return st;
     if (e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync");
     if (h_n_selected) {
+        *h_n_selected = (int32_t)nsel;
+        if (nsel > max_blocks)
+            return fail(NRR_E_CAPACITY, "%lld blocks selected but max_blocks is %d", nsel, max_blocks);
+    }
+    return NRR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Selection without any allocation at call time.
+//
+// The scratch lives in one file-scope device array of fixed size, so every
+// GPU that loads the library holds it until the process exits.  Host code
+// cannot use the array's name as a device address (it only stands in for
+// the symbol on the host), so the address is looked up once per device with
+// cudaGetSymbolAddress, with that device current.
+// ---------------------------------------------------------------------------
+namespace nrr {
+namespace {
+constexpr size_t SELECT_STATIC_SCRATCH_BYTES = (size_t)NRR_SELECT_STATIC_SCRATCH_BYTES;
+__device__ __align__(256) unsigned char g_select_scratch[SELECT_STATIC_SCRATCH_BYTES];
+
+nrr_status static_select_scratch(unsigned char **ptr)
+{
+    static std::mutex mu;
+    static unsigned char *addr[64] = {};
+    int dev = 0;
+    NRR_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(NRR_E_INTERNAL, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_select_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(selection scratch)");
+        addr[dev] = (unsigned char *)p;
+    }
+    *ptr = addr[dev];
+    return NRR_OK;
+}
+}  // namespace
+}  // namespace nrr
+
+extern "C" nrr_status nrr_select_blocks_noalloc(const uint16_t *d_preop, const uint8_t *d_mask, nrr_dims dims,
+                                                int32_t block, int32_t stride, double frac, int32_t *d_centers,
+                                                int32_t max_blocks, int32_t *d_n_selected, int32_t *h_n_selected,
+                                                void *stream)
+{
+    clear_error();
+    nrr_status st = check_select_args(dims, block, stride, frac);
+    if (st != NRR_OK) return st;
+    if (max_blocks < 0) return fail(NRR_E_INVALID, "max_blocks < 0");
+    if (!d_preop || !d_mask) return fail(NRR_E_INVALID, "NULL volume or mask");
+    if (max_blocks > 0 && !d_centers) return fail(NRR_E_INVALID, "NULL centre buffer");
+    const SelectPlan p = select_plan(dims, stride);
+    if (p.bytes > SELECT_STATIC_SCRATCH_BYTES)
+        return fail(NRR_E_CAPACITY,
+                    "%lld candidate grid points need %zu scratch bytes; the allocation-free selection holds %zu "
+                    "(use nrr_select_blocks or a larger stride)",
+                    p.ng, p.bytes, SELECT_STATIC_SCRATCH_BYTES);
+    unsigned char *ws = nullptr;
+    st = static_select_scratch(&ws);
+    if (st != NRR_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // enqueue_select zeroes the histograms and counters it accumulates into
+    // (the array keeps whatever the previous call left there).
+    st = enqueue_select(d_preop, d_mask, dims, block, stride, frac, d_centers, max_blocks, d_n_selected, ws, p, s);
+    if (st != NRR_OK) return st;
+    if (h_n_selected) {
+        long long nsel = 0;
+        cudaError_t e = cudaMemcpyAsync(&nsel, ws + select_count_offset(p), sizeof(nsel), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "reading the selection count");
         *h_n_selected = (int32_t)nsel;
         if (nsel > max_blocks)
             return fail(NRR_E_CAPACITY, "%lld blocks selected but max_blocks is %d", nsel, max_blocks);

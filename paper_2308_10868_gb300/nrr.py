@@ -56,6 +56,7 @@ SIGNATURES = {
     "nrr_version": (_I32, []),
     "nrr_kernel_launches": (C.c_int64, []),
     "nrr_select_blocks": (C.c_int, [_P, _P, Dims, _I32, _I32, C.c_double, _P, _I32, _P, _P, _P]),
+    "nrr_select_blocks_noalloc": (C.c_int, [_P, _P, Dims, _I32, _I32, C.c_double, _P, _I32, _P, _P, _P]),
     "nrr_boxsum_bytes": (C.c_int, [Dims, C.c_int, C.POINTER(C.c_size_t)]),
     "nrr_boxsums": (C.c_int, [_P, C.c_int, Dims, _I32, _P, _P]),
     "nrr_block_match": (C.c_int, [_P, _P, C.c_int, Dims, _P, _I32, _P, _I32, _P, _P, _P, _P, _P]),
