@@ -52,6 +52,7 @@ def _args():
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--batched-reps", type=int, default=5)
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--no-highres", action="store_true")
     p.add_argument("--serve-open-requests", type=int, default=200)
     p.add_argument("--serve-closed-requests", type=int, default=300)
     return p.parse_args()
@@ -356,6 +357,59 @@ def _serving(a, nrr, synth, dev):
     return out
 
 
+def _highres(a, nrr, synth, dev, flush):
+    """The high-resolution variant: 512x512x256, block 9^3, stride 3, top 5%,
+    radius 7 (3375 shifts), as uint16 (exact path) and as float32 u/65535
+    (FP32 search, FP64 rescoring); NCC error of float32 against the FP64
+    oracle on a sample of blocks."""
+    import numpy as np
+    import torch
+
+    import oracle
+
+    w = synth.WORKLOADS["highres"]
+    pre, intra, mask = synth.workload_pair("highres")
+    dpre, dintra = nrr.to_device_u16(pre, dev), nrr.to_device_u16(intra, dev)
+    dmask = torch.from_numpy(mask).to(dev)
+    p32, i32 = synth.as_f32(pre), synth.as_f32(intra)
+    fpre, fintra = torch.from_numpy(p32).to(dev), torch.from_numpy(i32).to(dev)
+    stream = torch.cuda.current_stream()
+    centers = nrr.select_blocks(dpre, dmask, w.block, w.stride, w.frac)
+    n = centers.shape[0]
+    evals = n * (2 * w.radius + 1) ** 3
+    out = {"workload": w.name, "n_blocks": n, "shifts": (2 * w.radius + 1) ** 3, "evals": evals}
+    for name, (p, i) in (("u16", (dpre, dintra)), ("f32", (fpre, fintra))):
+        box = nrr.boxsums(i, w.block)
+        res = nrr.block_match(p, i, centers, w.block, w.radius, box=box)
+        ts = []
+        for _ in range(3):
+            flush.fill_(7)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            nrr.block_match(p, i, centers, w.block, w.radius, box=box, out=res)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        nrr.device_status()
+        t = min(ts)
+        out[name] = {"match_ms": 1e3 * t, "evals_per_s": evals / t,
+                     "roofline_frac": 2.0 * evals * w.block ** 3 / t / 1e12 / (
+                         torch.cuda.get_device_properties(dev).multi_processor_count * FP32_LANES_PER_SM * 2 *
+                         float(_peaks().get("sm_max_mhz", 2070.0)) * 1e6 / 1e12)}
+        if name == "f32":
+            c = centers.cpu().numpy()
+            idx = np.arange(0, n, max(1, n // 400))
+            gd, gn = res[0].cpu().numpy()[idx], res[1].cpu().numpy()[idx]
+            rd, rn, rv = oracle.match(p32, i32, c[idx], w.block, w.radius)
+            at = np.array([oracle.pearson_f32(p32, i32, w.block, c[k], gd[j]) if rv[j] else np.nan
+                           for j, k in enumerate(idx)])
+            ok = rv == 1
+            out["f32"]["ncc_max_abs_err_vs_fp64_oracle"] = float(np.abs(gn[ok] - at[ok]).max())
+            out["f32"]["disp_mismatch_frac"] = float(((gd != rd).any(axis=1) & ok).mean())
+            out["f32"]["sample_blocks"] = int(len(idx))
+    return out
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -490,6 +544,8 @@ def run_ours(a):
         line["batched"] = _batched_search(a, nrr, synth, d_pre, d_intra, d_mask, w, flush)
     if not a.no_serving:
         line["serving"] = _serving(a, nrr, synth, dev)
+    if not a.no_highres:
+        line["highres"] = _highres(a, nrr, synth, dev, flush)
     if world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(w, pre, intra, mask)
     print(json.dumps(line), flush=True)
