@@ -1,24 +1,30 @@
 // NCC block-matching kernel (Sec. 3 NCC equation and O(B x W) bound;
 // Sec. 4.3 block-matching loop), written for sm_103a.
 //
-// A persistent CTA walks its share of the registration blocks.  Per block:
+// A persistent CTA walks its share of the registration blocks, two blocks in
+// flight: while block i is processed, the TMA copies of block i+1 land in
+// the other half of a double buffer.  Per block:
 //   1. TMA tiled loads bring the block's search window of the reference
 //      image, [c-h-R, c+h+R] per axis, and the floating block [c-h, c+h]^3
-//      into shared memory (x start rounded down to a 16-byte boundary;
-//      out-of-volume voxels arrive as zeros and are excluded by coordinates).
-//      The copy for the next block is issued as soon as the current one has
-//      been unpacked, so it lands while the current block is searched.
-//   2. Warp 0 reduces the floating block's sums; the other warps unpack the
-//      window to float, shifted by a per-block constant c (J'_k = J_k - c).
-//      The floating block is stored mean-shifted (T_k = I_k - m).
+//      into shared memory.  The x start is rounded down to a 16-byte
+//      boundary (offset xo); the box is widened so that its row and plane
+//      pitches make every 16-byte load of 8 consecutive threads hit 8
+//      distinct bank groups.  Out-of-volume voxels arrive as zeros and are
+//      excluded by coordinates.
+//   2. Warp 0 reduces the floating block's sums; the CTA stores it
+//      mean-shifted (T_k = I_k - m) as float.
 //   3. Search: thread t owns one (dz, dy) line of the window and all 2*rx+1
-//      shifts along x; for every template row it loads one window row
-//      (16-byte shared loads, conflict-free row pitch) and accumulates
-//      A(d) = sum_k T_k J'_{k+d} with FP32 FFMA, fully unrolled over the row
-//      and the x shifts.
-//   4. Every shift gets an approximate NCC and a rigorous bound on its error
-//      (recursive-summation bound gamma_N * sum|T||J'| for the FFMA chain,
-//      Cauchy-Schwarz sum|T||J'| <= sqrt(sum T^2 * sum J'^2), plus the
+//      shifts along x.  For every template row it reads the window row
+//      straight from the TMA buffer with 16-byte loads, turns the values it
+//      needs into floats shifted by a per-block constant c (J'_k = J_k - c;
+//      for uint16 one byte-permute and one subtraction, exact), and
+//      accumulates A(d) = sum_k T_k J'_{k+d} with FP32 FFMA, fully unrolled
+//      over the row and the x shifts.  The offset xo is a compile-time
+//      parameter of the loop, so every register index is static.
+//   4. Every shift gets an approximate NCC from A(d) and the box sums S_J,
+//      S_JJ (precomputed, exact for uint16) together with a rigorous bound on
+//      its error (recursive-summation bound gamma_N * sum|T||J'| for the FFMA
+//      chain, Cauchy-Schwarz sum|T||J'| <= sqrt(sum T^2 * sum J'^2), plus the
 //      rounding of the final operations; doubled for margin).
 //   5. Shifts whose upper bound reaches the best lower bound survive (about
 //      one per block on the phantoms) and are rescored by a warp each:
@@ -48,9 +54,7 @@ struct MatchParams {
     const void *s2;
     int nx, ny, nz;
     int ry, rz;
-    int bx;   // TMA box extent along x of the window (elements)
-    int btx;  // TMA box extent along x of the floating block (elements)
-    int pf;   // row pitch of the float window (floats)
+    int wyp;  // rows per plane of the window box (>= window height)
     int n_jobs;
     MatchJob jobs[MATCH_MAX_JOBS];
     unsigned int *err;
@@ -85,25 +89,49 @@ struct MatchScratch {
     int jstart[MATCH_MAX_JOBS + 1];  // first work item of each job
 };
 
-struct MatchLayout {
-    int u, ut, f, t, surv, sc, bar, total;
-};
-
+__host__ __device__ constexpr int round_up_c(int v, int a) { return (v + a - 1) / a * a; }
 __host__ __device__ inline int round_up_i(int v, int a) { return (v + a - 1) / a * a; }
 
+// Row pitch (elements) of the window box: covers the WX needed values from
+// any start offset below one 16-byte chunk, and is an odd number of 16-byte
+// chunks, so 8 consecutive rows start in 8 distinct bank groups.
+template <typename T, int B, int P>
+__host__ __device__ constexpr int match_bx()
+{
+    constexpr int EPC = 16 / (int)sizeof(T);
+    constexpr int c = (B + P - 1 + EPC - 1 + EPC - 1) / EPC;  // chunks
+    return EPC * (c % 2 ? c : c + 1);
+}
+
+// Rows per plane of the window box.  Consecutive threads own consecutive
+// (dz, dy) lines; their rows are 1 apart except at the wrap from dy = py-1
+// to the next dz, where they are wyp - py + 1 apart.  With an odd number of
+// chunks per row, both steps map to the same bank-group step iff
+// wyp == py (mod 8).
+__host__ __device__ inline int match_wyp(int wy, int py)
+{
+    int w = wy;
+    while ((w - py) % 8 != 0) ++w;
+    return w;
+}
+
+struct MatchLayout {
+    int u[2], ut[2], t, surv, sc, bar, total;
+};
+
 // Shared-memory carve-up of one CTA (all offsets 128-byte aligned).
-__host__ __device__ inline MatchLayout match_layout(int elem, int B, int P, int bx, int btx, int pf, int wy, int wz,
-                                                   int py, int pz)
+__host__ __device__ inline MatchLayout match_layout(int elem, int B, int P, int bx, int btx, int wyp, int wz, int py,
+                                                   int pz)
 {
     MatchLayout L;
-    int pt = round_up_i(B, 4);
+    const int pt = round_up_i(B, 4);
     int o = 0;
-    L.u = o;
-    o += round_up_i(bx * wy * wz * elem, 128);
-    L.ut = o;
-    o += round_up_i(btx * B * B * elem, 128);
-    L.f = o;
-    o += round_up_i(pf * wy * wz * 4, 128);
+    for (int b = 0; b < 2; ++b) {
+        L.u[b] = o;
+        o += round_up_i(bx * wyp * wz * elem, 128);
+        L.ut[b] = o;
+        o += round_up_i(btx * B * B * elem, 128);
+    }
     L.t = o;
     o += round_up_i(B * B * pt * 4, 128);
     L.surv = o;
@@ -114,15 +142,6 @@ __host__ __device__ inline MatchLayout match_layout(int elem, int B, int P, int 
     o += 128;
     L.total = o;
     return L;
-}
-
-// Row pitch of the float window: a multiple of 4 floats with an odd number
-// of 16-byte chunks, so 8 consecutive rows fall in distinct bank groups.
-__host__ __device__ inline int match_pitch(int wx)
-{
-    int q = (wx + 3) / 4;
-    if ((q & 1) == 0) ++q;
-    return 4 * q;
 }
 
 struct Cand {
@@ -195,6 +214,65 @@ __device__ __forceinline__ bool center_inside(int cx, int cy, int cz, int nx, in
     return cx >= H && cy >= H && cz >= H && cx <= nx - 1 - H && cy <= ny - 1 - H && cz <= nz - 1 - H;
 }
 
+// The search of one thread's line for a window whose row data starts XO
+// elements into each row of the box.  `row0` points at the thread's first
+// row; rows of the next template row are one box row apart, template planes
+// `zstride` elements apart.
+template <typename T, int B, int P, int XO>
+__device__ __forceinline__ void search_line(const T *row0, int zstride, const float *Tm, float csh, float (&acc)[P])
+{
+    constexpr bool F32 = std::is_same<T, float>::value;
+    constexpr int WX = B + P - 1;
+    constexpr int EPC = 16 / (int)sizeof(T);
+    constexpr int NC = (XO + WX - 1) / EPC + 1;  // 16-byte chunks covering [XO, XO + WX)
+    constexpr int PT = (B + 3) / 4 * 4;
+    constexpr int BX = match_bx<T, B, P>();
+#pragma unroll 1
+    for (int kz = 0; kz < B; ++kz) {
+#pragma unroll 1
+        for (int ky = 0; ky < B; ++ky) {
+            const T *row = row0 + kz * zstride + ky * BX;
+            const float *tr = Tm + (kz * B + ky) * PT;
+            uint4 ch[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) ch[c] = *reinterpret_cast<const uint4 *>(row + c * EPC);
+            float t[PT];
+#pragma unroll
+            for (int q = 0; q < PT / 4; ++q) {
+                const float4 v = *reinterpret_cast<const float4 *>(tr + 4 * q);
+                t[4 * q + 0] = v.x;
+                t[4 * q + 1] = v.y;
+                t[4 * q + 2] = v.z;
+                t[4 * q + 3] = v.w;
+            }
+            float j[WX];
+#pragma unroll
+            for (int e = 0; e < WX; ++e) {
+                constexpr int dummy = 0;
+                (void)dummy;
+                const int E = XO + e;  // element within the loaded chunks (compile-time after unrolling)
+                const uint4 &q = ch[E / EPC];
+                if constexpr (F32) {
+                    const int w = E % 4;
+                    const uint32_t bits = w == 0 ? q.x : w == 1 ? q.y : w == 2 ? q.z : q.w;
+                    j[e] = __fsub_rn(__uint_as_float(bits), csh);
+                } else {
+                    const int w = (E % 8) / 2;
+                    const uint32_t word = w == 0 ? q.x : w == 1 ? q.y : w == 2 ? q.z : q.w;
+                    // 0x4B00|u is the float 2^23 + u: one byte-permute, then
+                    // subtracting 2^23 + c gives u - c exactly
+                    const uint32_t bits = (E & 1) ? __byte_perm(word, 0x4B00u, 0x5432) : __byte_perm(word, 0x4B00u, 0x5410);
+                    j[e] = __fsub_rn(__uint_as_float(bits), csh);
+                }
+            }
+#pragma unroll
+            for (int kx = 0; kx < B; ++kx)
+#pragma unroll
+                for (int p = 0; p < P; ++p) acc[p] = __fmaf_rn(t[kx], j[kx + p], acc[p]);
+        }
+    }
+}
+
 // Register budget: at most 80 registers per thread for blocks up to 7^3 and
 // up to 11 x-shifts (5-6 search CTAs of <= 128 threads per SM), 128 above.
 template <int B, int P>
@@ -203,34 +281,30 @@ struct MatchMinBlocks {
 };
 
 template <typename T, int B, int P>
-__global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value) match_kernel(const MatchParams a,
-                                                                  const __grid_constant__ CUtensorMap tmapJ,
-                                                                  const __grid_constant__ CUtensorMap tmapI)
+__global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value) match_kernel(
+    const MatchParams a, const __grid_constant__ CUtensorMap tmapJ, const __grid_constant__ CUtensorMap tmapI)
 {
     constexpr bool F32 = std::is_same<T, float>::value;
     constexpr int H = (B - 1) / 2;
     constexpr int N = B * B * B;
     constexpr int PT = (B + 3) / 4 * 4;
     constexpr int RX = (P - 1) / 2;
-    constexpr int WX = B + P - 1;
-    constexpr int NJ4 = (WX + 3) / 4;
     constexpr int ALIGN = 16 / (int)sizeof(T);
+    constexpr int BX = match_bx<T, B, P>();
+    constexpr int BTX = round_up_c(B + ALIGN - 1, ALIGN);
     constexpr float U32 = 5.9604644775390625e-08f;  // 2^-24, unit roundoff of binary32
     constexpr double GAMMA_N = (double)N * 5.9604644775390625e-08 / (1.0 - (double)N * 5.9604644775390625e-08);
 
     const int ry = a.ry, rz = a.rz, py = 2 * ry + 1, pz = 2 * rz + 1, lines = py * pz;
-    const int wy = B + 2 * ry, wz = B + 2 * rz, bx = a.bx, btx = a.btx, pf = a.pf;
+    const int wz = B + 2 * rz, wyp = a.wyp;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
 
     extern __shared__ __align__(128) unsigned char smem[];
-    const MatchLayout L = match_layout((int)sizeof(T), B, P, bx, btx, pf, wy, wz, py, pz);
-    T *U = reinterpret_cast<T *>(smem + L.u);
-    T *Ut = reinterpret_cast<T *>(smem + L.ut);
-    float *Fw = reinterpret_cast<float *>(smem + L.f);
+    const MatchLayout L = match_layout((int)sizeof(T), B, P, BX, BTX, wyp, wz, py, pz);
     float *Tm = reinterpret_cast<float *>(smem + L.t);
     uint16_t *surv = reinterpret_cast<uint16_t *>(smem + L.surv);
     MatchScratch *sc = reinterpret_cast<MatchScratch *>(smem + L.sc);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);  // [2]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nthr = blockDim.x, nwarp = nthr >> 5;
     if (tid == 0) {
@@ -245,54 +319,69 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
             w += m;
         }
         sc->jstart[a.n_jobs] = w;
+        mbar_init(bar + 0, 1);
+        mbar_init(bar + 1, 1);
+        fence_mbar_init();
     }
     __syncthreads();
     const int n = sc->jstart[a.n_jobs];  // work items over all jobs
-    // work item -> (job, index within the job)
     auto locate = [&](int w, int &j, int &i) {
         j = 0;
         while (j + 1 < a.n_jobs && w >= sc->jstart[j + 1]) ++j;
         i = w - sc->jstart[j];
     };
-    const uint32_t tx_bytes = (uint32_t)((bx * wy * wz + btx * B * B) * (int)sizeof(T));
-    // Thread 0 issues both copies of block b (its centre must be inside).
-    auto issue = [&](int b) {
+    auto centre = [&](int w, int &cx, int &cy, int &cz) {
         int j, i;
-        locate(b, j, i);
-        const int32_t *cc = a.jobs[j].centers + 3 * i;
-        const int cx = cc[0], cy = cc[1], cz = cc[2];
+        locate(w, j, i);
+        const int32_t *c = a.jobs[j].centers + 3 * i;
+        cx = c[0];
+        cy = c[1];
+        cz = c[2];
+    };
+    // next work item of this CTA at or after w whose centre is inside;
+    // thread 0 reports the skipped ones as invalid
+    auto next_inside = [&](int w) {
+        for (; w < n; w += gridDim.x) {
+            int cx, cy, cz;
+            centre(w, cx, cy, cz);
+            if (center_inside<H>(cx, cy, cz, nx, ny, nz)) return w;
+            if (tid == 0) {
+                int j, i;
+                locate(w, j, i);
+                write_result(a.jobs[j], i, Cand{0.0, 0, 0, 0}, P, py, RX, ry, rz);
+            }
+        }
+        return n;
+    };
+    const uint32_t tx_bytes = (uint32_t)((BX * wyp * wz + BTX * B * B) * (int)sizeof(T));
+    // thread 0: both copies of block w into buffer b
+    auto issue = [&](int w, int b) {
+        int cx, cy, cz;
+        centre(w, cx, cy, cz);
         const int x0 = cx - H - RX, xt = cx - H;
         fence_proxy_async_smem();
-        mbar_arrive_expect_tx(bar, tx_bytes);
-        tma_load_3d(U, &tmapJ, bar, x0 & ~(ALIGN - 1), cy - H - ry, cz - H - rz);
-        tma_load_3d(Ut, &tmapI, bar, xt & ~(ALIGN - 1), cy - H, cz - H);
+        mbar_arrive_expect_tx(bar + b, tx_bytes);
+        tma_load_3d(smem + L.u[b], &tmapJ, bar + b, x0 & ~(ALIGN - 1), cy - H - ry, cz - H - rz);
+        tma_load_3d(smem + L.ut[b], &tmapI, bar + b, xt & ~(ALIGN - 1), cy - H, cz - H);
     };
-    if (tid == 0) {
-        mbar_init(bar, 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    uint32_t phase = 0;
-    int inflight = -1;  // block whose copies are in flight (same value in every thread)
 
-    for (int blk = blockIdx.x; blk < n; blk += gridDim.x) {
+    uint32_t phase[2] = {0u, 0u};
+    int i = 0;
+    int blk = next_inside(blockIdx.x);
+    if (blk < n && tid == 0) issue(blk, 0);
+    while (blk < n) {
+        const int b = i & 1;
+        const T *U = reinterpret_cast<const T *>(smem + L.u[b]);
+        const T *Ut = reinterpret_cast<const T *>(smem + L.ut[b]);
         int job, bi;
         locate(blk, job, bi);
         const MatchJob &J = a.jobs[job];
         const int cx = J.centers[3 * bi + 0], cy = J.centers[3 * bi + 1], cz = J.centers[3 * bi + 2];
-        if (!center_inside<H>(cx, cy, cz, nx, ny, nz)) {
-            if (tid == 0) write_result(J, bi, Cand{0.0, 0, 0, 0}, P, py, RX, ry, rz);
-            continue;
-        }
-        if (inflight != blk) {
-            if (tid == 0) issue(blk);
-            inflight = blk;
-        }
         const int x0 = cx - H - RX, xo = x0 - (x0 & ~(ALIGN - 1));
         const int xt = cx - H, xot = xt - (xt & ~(ALIGN - 1));
         const size_t cidx = ((size_t)cz * ny + cy) * nx + cx;
         // window centring constant from the box sum at the centre
-        float cshift;  // value subtracted (with 2^23 folded in for uint16)
+        float cshift;  // subtracted from the float of each window value (2^23 folded in for uint16)
         int c_i = 0;
         float c_f = 0.f;
         if constexpr (F32) {
@@ -305,69 +394,69 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
         }
         if (tid == 0) sc->nsurv = 0;
 
-        // ---- wait for the window and the floating block ------------------
-        const bool got = mbar_wait_bounded(bar, phase, WAIT_LIMIT_NS);
+        // ---- wait for this block's copies; start the next block's --------
+        const bool got = mbar_wait_bounded(bar + b, phase[b], WAIT_LIMIT_NS);
         if (!__syncthreads_and(got)) {
             if (tid == 0) {
                 atomicOr(a.err, DEV_ERR_TIMEOUT);
                 write_result(J, bi, Cand{0.0, 0, 0, 0}, P, py, RX, ry, rz);
             }
-            mbar_wait_bounded(bar, phase, WAIT_LIMIT_NS);  // let an in-flight copy land before exiting
+            mbar_wait_bounded(bar + b, phase[b], WAIT_LIMIT_NS);  // let an in-flight copy land before exiting
             return;
         }
-        phase ^= 1u;
+        phase[b] ^= 1u;
+        const int nb = next_inside(blk + gridDim.x);
+        if (nb < n && tid == 0) issue(nb, b ^ 1);  // buffer b^1 was released by the previous block's last barrier
 
-        // ---- phase A: warp 0 reduces the floating block, the rest unpack ---
+        // ---- warp 0: floating block statistics ------------------------------
         if (warp == 0) {
+            constexpr int KPL = (N + 31) / 32;
+            constexpr int CH = KPL < 6 ? KPL : 6;
             if constexpr (F32) {
-                constexpr int KPL = (N + 31) / 32;  // values per lane
-                constexpr int CH = KPL < 6 ? KPL : 6;   // loads in flight per lane
                 double s = 0.0;
                 float lo = INFINITY, hi = -INFINITY;
 #pragma unroll 1
                 for (int i0 = 0; i0 < KPL; i0 += CH) {
                     float vals[CH];
 #pragma unroll
-                    for (int i = 0; i < CH; ++i) {
-                        const int k = lane + 32 * (i0 + i);
+                    for (int q = 0; q < CH; ++q) {
+                        const int k = lane + 32 * (i0 + q);
                         const int kzy = k / B, kx = k - kzy * B;
-                        vals[i] = k < N ? Ut[kzy * btx + xot + kx] : NAN;
+                        vals[q] = k < N ? Ut[kzy * BTX + xot + kx] : 0.f;
                     }
 #pragma unroll
-                    for (int i = 0; i < CH; ++i) {
-                        if (lane + 32 * (i0 + i) < N) {
-                            s += (double)vals[i];
-                            lo = fminf(lo, vals[i]);
-                            hi = fmaxf(hi, vals[i]);
+                    for (int q = 0; q < CH; ++q)
+                        if (lane + 32 * (i0 + q) < N) {
+                            s += (double)vals[q];
+                            lo = fminf(lo, vals[q]);
+                            hi = fmaxf(hi, vals[q]);
                         }
-                    }
                 }
                 s = warp_sum(s);
                 lo = warp_min_f(lo);
                 hi = warp_max_f(hi);
                 const double ibar = s / (double)N;
                 const float mu = (float)ibar;
-                double q = 0.0, dv = 0.0;
+                double qq = 0.0, dv = 0.0;
 #pragma unroll 1
                 for (int i0 = 0; i0 < KPL; i0 += CH) {
                     float vals[CH];
 #pragma unroll
-                    for (int i = 0; i < CH; ++i) {
-                        const int k = lane + 32 * (i0 + i);
+                    for (int q = 0; q < CH; ++q) {
+                        const int k = lane + 32 * (i0 + q);
                         const int kzy = k / B, kx = k - kzy * B;
-                        vals[i] = k < N ? Ut[kzy * btx + xot + kx] : 0.f;
+                        vals[q] = k < N ? Ut[kzy * BTX + xot + kx] : 0.f;
                     }
 #pragma unroll
-                    for (int i = 0; i < CH; ++i) {
-                        if (lane + 32 * (i0 + i) < N) {
-                            const double t = (double)__fsub_rn(vals[i], mu);
-                            q = fma(t, t, q);
-                            const double d = (double)vals[i] - ibar;
+                    for (int q = 0; q < CH; ++q)
+                        if (lane + 32 * (i0 + q) < N) {
+                            const double t = (double)__fsub_rn(vals[q], mu);
+                            qq = fma(t, t, qq);
+                            const double d = (double)vals[q] - ibar;
                             dv = fma(d, d, dv);
                         }
-                    }
                 }
-                q = warp_sum(q);
+                qq = warp_sum(qq);
                 dv = warp_sum(dv);
                 if (lane == 0) {
                     BlockConst &c = sc->bc;
@@ -377,35 +466,33 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
                     c.emu = (float)(ibar - (double)mu);
                     c.dvI = dv;
                     c.fvI = (float)dv;
-                    c.kq = (float)(sqrt(q) * (1.0 + 1e-6));
+                    c.kq = (float)(sqrt(qq) * (1.0 + 1e-6));
                 }
             } else {
-                constexpr int KPL = (N + 31) / 32;  // values per lane
-                constexpr int CH = KPL < 6 ? KPL : 6;   // loads in flight per lane
                 long long s = 0;
-                unsigned long long q = 0;
+                unsigned long long q2 = 0;
 #pragma unroll 1
                 for (int i0 = 0; i0 < KPL; i0 += CH) {
                     uint32_t vals[CH];
 #pragma unroll
-                    for (int i = 0; i < CH; ++i) {
-                        const int k = lane + 32 * (i0 + i);
+                    for (int q = 0; q < CH; ++q) {
+                        const int k = lane + 32 * (i0 + q);
                         const int kzy = k / B, kx = k - kzy * B;
-                        vals[i] = k < N ? (uint32_t)Ut[kzy * btx + xot + kx] : 0u;
+                        vals[q] = k < N ? (uint32_t)Ut[kzy * BTX + xot + kx] : 0u;
                     }
 #pragma unroll
-                    for (int i = 0; i < CH; ++i) {
-                        s += vals[i];
-                        q += (unsigned long long)(vals[i] * vals[i]);
+                    for (int q = 0; q < CH; ++q) {
+                        s += vals[q];
+                        q2 += (unsigned long long)(vals[q] * vals[q]);
                     }
                 }
                 s = warp_sum(s);
-                q = warp_sum(q);
+                q2 = warp_sum(q2);
                 if (lane == 0) {
                     BlockConst &c = sc->bc;
-                    const long long vI = (long long)N * (long long)q - s * s;
+                    const long long vI = (long long)N * (long long)q2 - s * s;
                     const long long m = (2 * s + N) / (2 * N);  // nearest integer to the block mean
-                    const long long qt = (long long)q - 2 * m * s + (long long)N * m * m;  // sum (I-m)^2, exact
+                    const long long qt = (long long)q2 - 2 * m * s + (long long)N * m * m;  // sum (I-m)^2, exact
                     c.vI = vI;
                     c.flat = vI == 0;
                     c.m = (int)m;
@@ -415,41 +502,16 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
                 }
             }
         }
-        {
-            // Window rows: lanes along x, a warp takes RB rows at a time and
-            // issues all their loads before any store, so the shared-memory
-            // latency is paid once per batch rather than once per row.
-            constexpr int RB = 8;
-            const int rows = wz * wy;
-            for (int r0 = warp * RB; r0 < rows; r0 += nwarp * RB) {
-                float v[RB];
-#pragma unroll
-                for (int j = 0; j < RB; ++j) {
-                    const int r = r0 + j;
-                    v[j] = 0.f;
-                    if (r < rows && lane < WX) {
-                        const T u = U[r * bx + xo + lane];
-                        if constexpr (F32)
-                            v[j] = __fsub_rn(u, cshift);
-                        else
-                            v[j] = u16_minus(u, cshift);
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < RB; ++j) {
-                    const int r = r0 + j;
-                    if (r < rows && lane < pf) Fw[r * pf + lane] = v[j];
-                }
-            }
-        }
         __syncthreads();
         const BlockConst bc = sc->bc;
         if (bc.flat) {  // flat floating block: NCC undefined for every shift
             if (tid == 0) write_result(J, bi, Cand{0.0, 0, 0, 0}, P, py, RX, ry, rz);
             __syncthreads();
+            blk = nb;
+            ++i;
             continue;
         }
-        // ---- phase B: mean-shifted template ---------------------------------
+        // ---- mean-shifted template (loads batched before stores) -----------
         {
             const float tsh = F32 ? bc.mu : 8388608.0f + (float)bc.m;
             constexpr int TB = B * B * PT;
@@ -462,9 +524,9 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
                 v[j] = 0.f;
                 if (k < TB && kx < B) {
                     if constexpr (F32)
-                        v[j] = __fsub_rn(Ut[kzy * btx + xot + kx], tsh);
+                        v[j] = __fsub_rn(Ut[kzy * BTX + xot + kx], tsh);
                     else
-                        v[j] = u16_minus(Ut[kzy * btx + xot + kx], tsh);
+                        v[j] = u16_minus(Ut[kzy * BTX + xot + kx], tsh);
                 }
             }
 #pragma unroll
@@ -477,28 +539,14 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
                 float w = 0.f;
                 if (kx < B) {
                     if constexpr (F32)
-                        w = __fsub_rn(Ut[kzy * btx + xot + kx], tsh);
+                        w = __fsub_rn(Ut[kzy * BTX + xot + kx], tsh);
                     else
-                        w = u16_minus(Ut[kzy * btx + xot + kx], tsh);
+                        w = u16_minus(Ut[kzy * BTX + xot + kx], tsh);
                 }
                 Tm[k] = w;
             }
         }
         __syncthreads();
-        // both staging buffers are free: start the next block's copies
-        {
-            int nb = blk + gridDim.x;
-            if (nb < n) {
-                int nj, ni;
-                locate(nb, nj, ni);
-                const int32_t *nc = a.jobs[nj].centers + 3 * ni;
-                const int ncx = nc[0], ncy = nc[1], ncz = nc[2];
-                if (center_inside<H>(ncx, ncy, ncz, nx, ny, nz)) {
-                    if (tid == 0) issue(nb);
-                    inflight = nb;
-                }
-            }
-        }
 
         // ---- search: FP32 accumulation of A(d) over the whole window ------
         float ub[P];
@@ -509,39 +557,25 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
             const bool yz_ok = Y >= H && Y <= ny - 1 - H && Z >= H && Z <= nz - 1 - H;
             typedef typename std::conditional<F32, float, int32_t>::type S1T;
             typedef typename std::conditional<F32, float, long long>::type S2T;
-
-            const float *fbase = Fw + (dzi * wy + dyi) * pf;
             float acc[P];
 #pragma unroll
             for (int p = 0; p < P; ++p) acc[p] = 0.f;
-#pragma unroll 1
-            for (int kz = 0; kz < B; ++kz) {
-#pragma unroll 1
-                for (int ky = 0; ky < B; ++ky) {
-                    const float *fr = fbase + (kz * wy + ky) * pf;
-                    const float *tr = Tm + (kz * B + ky) * PT;
-                    float j[4 * NJ4], t[PT];
-#pragma unroll
-                    for (int q = 0; q < NJ4; ++q) {
-                        const float4 v = *reinterpret_cast<const float4 *>(fr + 4 * q);
-                        j[4 * q + 0] = v.x;
-                        j[4 * q + 1] = v.y;
-                        j[4 * q + 2] = v.z;
-                        j[4 * q + 3] = v.w;
-                    }
-#pragma unroll
-                    for (int q = 0; q < PT / 4; ++q) {
-                        const float4 v = *reinterpret_cast<const float4 *>(tr + 4 * q);
-                        t[4 * q + 0] = v.x;
-                        t[4 * q + 1] = v.y;
-                        t[4 * q + 2] = v.z;
-                        t[4 * q + 3] = v.w;
-                    }
-#pragma unroll
-                    for (int kx = 0; kx < B; ++kx)
-#pragma unroll
-                        for (int p = 0; p < P; ++p) acc[p] = __fmaf_rn(t[kx], j[kx + p], acc[p]);
-                }
+            const T *row0 = U + (dzi * wyp + dyi) * BX;
+            const int zs = wyp * BX;
+            switch (xo) {
+#define NRR_XO(k) \
+    case k:       \
+        if constexpr (k < ALIGN) search_line<T, B, P, k>(row0, zs, Tm, cshift, acc); \
+        break;
+                NRR_XO(0)
+                NRR_XO(1)
+                NRR_XO(2)
+                NRR_XO(3)
+                NRR_XO(4)
+                NRR_XO(5)
+                NRR_XO(6)
+                NRR_XO(7)
+#undef NRR_XO
             }
 
             // box sums of this thread's shifts (independent loads, issued together)
@@ -560,7 +594,6 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
                     ps2[p] = reinterpret_cast<const S2T *>(a.s2)[rowbase + X];
                 }
             }
-
             // ---- approximate NCC and its error bound per shift -----------
             const float fN = (float)N;
 #pragma unroll
@@ -669,7 +702,7 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
                         jv[i] = 0;
                         if (k < N) {
                             tv[i] = (int)Tm[(kz * B + ky) * PT + kx];
-                            jv[i] = (int)Fw[((szi + kz) * wy + (syi + ky)) * pf + sxi + kx];
+                            jv[i] = (int)U[((szi + kz) * wyp + (syi + ky)) * BX + xo + sxi + kx] - c_i;
                         }
                     }
 #pragma unroll
@@ -732,10 +765,12 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
             }
             write_result(J, bi, best, P, py, RX, ry, rz);
         }
-        __syncthreads();
+        __syncthreads();  // releases buffer b for the copies of the block after next
+        blk = nb;
+        ++i;
     }
-    // a copy issued for a block this CTA never reached cannot exist: copies
-    // are only issued for blocks < n that the loop visits next.
+    // every copy issued was waited for: a block's copies are issued only
+    // when the loop is certain to visit it next
 }
 
 // Host side: launch one (element type, block size, x-shift count) variant.
@@ -743,21 +778,19 @@ template <typename T, int B, int P>
 nrr_status launch_match_variant(const MatchLaunch &m, cudaStream_t stream)
 {
     constexpr int ALIGN = 16 / (int)sizeof(T);
-    constexpr int WX = B + P - 1;
+    constexpr int BX = match_bx<T, B, P>();
+    constexpr int BTX = round_up_c(B + ALIGN - 1, ALIGN);
     const int ry = m.radius[1], rz = m.radius[2], py = 2 * ry + 1, pz = 2 * rz + 1;
-    const int wy = B + 2 * ry, wz = B + 2 * rz;
-    const int bx = round_up_i(WX + ALIGN - 1, ALIGN);
-    const int btx = round_up_i(B + ALIGN - 1, ALIGN);
-    const int pf = match_pitch(WX);
-    const MatchLayout L = match_layout((int)sizeof(T), B, P, bx, btx, pf, wy, wz, py, pz);
-    const int lines = py * pz;
-    const int threads = round_up_i(lines, 32);
+    const int wy = B + 2 * ry, wz = B + 2 * rz, wyp = match_wyp(wy, py);
+    const MatchLayout L = match_layout((int)sizeof(T), B, P, BX, BTX, wyp, wz, py, pz);
+    const int threads = round_up_i(py * pz, 32);
     if (threads > MATCH_MAX_THREADS) return fail(NRR_E_INVALID, "search window too large");
+    if (wyp > 256) return fail(NRR_E_INVALID, "search window too large");
 
     CUtensorMap mapJ, mapI;
-    nrr_status st = encode_volume_map(&mapJ, m.intraop, m.dtype, m.dims, bx, wy, wz);
+    nrr_status st = encode_volume_map(&mapJ, m.intraop, m.dtype, m.dims, BX, wyp, wz);
     if (st != NRR_OK) return st;
-    st = encode_volume_map(&mapI, m.preop, m.dtype, m.dims, btx, B, B);
+    st = encode_volume_map(&mapI, m.preop, m.dtype, m.dims, BTX, B, B);
     if (st != NRR_OK) return st;
 
     auto kern = match_kernel<T, B, P>;
@@ -790,9 +823,7 @@ nrr_status launch_match_variant(const MatchLaunch &m, cudaStream_t stream)
     p.nz = m.dims.nz;
     p.ry = ry;
     p.rz = rz;
-    p.bx = bx;
-    p.btx = btx;
-    p.pf = pf;
+    p.wyp = wyp;
     p.n_jobs = m.n_jobs;
     for (int j = 0; j < MATCH_MAX_JOBS; ++j) p.jobs[j] = j < m.n_jobs ? m.jobs[j] : MatchJob{};
     p.err = m.err;
@@ -807,16 +838,15 @@ template <typename T, int B, int P>
 nrr_status occupancy_variant(const MatchLaunch &m, int *occ)
 {
     constexpr int ALIGN = 16 / (int)sizeof(T);
-    constexpr int WX = B + P - 1;
     const int ry = m.radius[1], rz = m.radius[2], py = 2 * ry + 1, pz = 2 * rz + 1;
-    const int bx = round_up_i(WX + ALIGN - 1, ALIGN), btx = round_up_i(B + ALIGN - 1, ALIGN);
-    const MatchLayout L = match_layout((int)sizeof(T), B, P, bx, btx, match_pitch(WX), B + 2 * ry, B + 2 * rz, py, pz);
+    const int wyp = match_wyp(B + 2 * ry, py);
+    const MatchLayout L = match_layout((int)sizeof(T), B, P, match_bx<T, B, P>(), round_up_c(B + ALIGN - 1, ALIGN),
+                                       wyp, B + 2 * rz, py, pz);
     auto kern = match_kernel<T, B, P>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, round_up_i(py * pz, 32), L.total);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, round_up_i(py * pz, 32), L.total);
     if (e != cudaSuccess) return cuda_fail(e, "match occupancy query");
     return NRR_OK;
 }

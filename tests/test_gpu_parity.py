@@ -220,3 +220,4 @@ def test_f32_integer_valued_equals_u16(nrr):
                                     torch.from_numpy(intra.astype(np.float32)).cuda(), dc, 7, 4)
     assert torch.equal(v16, v32)
     assert (n16 - n32).abs().max().item() < 1e-12
+
