@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
             cshift = c_f;
         } else {
             const long long s1c = reinterpret_cast<const int32_t *>(a.s1)[cidx];
-            c_i = (int)((2 * s1c + N) / (2 * N));
+            c_i = (int)((2u * (uint32_t)s1c + (uint32_t)N) / (2u * (uint32_t)N));
             cshift = 8388608.0f + (float)c_i;
         }
         if (tid == 0) sc->nsurv = 0;
@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
                 if (lane == 0) {
                     BlockConst &c = sc->bc;
                     const long long vI = (long long)N * (long long)q2 - s * s;
-                    const long long m = (2 * s + N) / (2 * N);  // nearest integer to the block mean
+                    const long long m = (long long)((2u * (uint32_t)s + (uint32_t)N) / (2u * (uint32_t)N));  // nearest integer to the mean
                     const long long qt = (long long)q2 - 2 * m * s + (long long)N * m * m;  // sum (I-m)^2, exact
                     c.vI = vI;
                     c.flat = vI == 0;
