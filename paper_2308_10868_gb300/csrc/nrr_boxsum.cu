@@ -1,146 +1,309 @@
-// Box sums of the reference image: the per-shift sums S_J = sum J and
-// S_JJ = sum J^2 over the b^3 block at every voxel (Sec. 3, NCC equation:
-// the mean and spread of the reference block change with every shift).
+// Sums over b^3 blocks, for both steps of the path:
+//  * matching (Sec. 3, NCC equation): S_J = sum J and S_JJ = sum J^2 of the
+//    reference block at every voxel -- the reference block's mean and spread
+//    change with every shift -- computed once per (volume, block size)
+//    because neighbouring blocks' search windows overlap heavily;
+//  * selection (Sec. 4.1, "Parallel feature selection"): the variance key
+//    N*sum I^2 - (sum I)^2 of the floating block at every stride grid point
+//    whose centre lies in the mask and whose block lies in the volume.
 //
-// Computed once per (volume, block size) instead of once per registration
-// block: neighbouring blocks' search windows overlap heavily, so the match
-// kernel reads these sums rather than re-deriving them from its window.
-//
-// One CTA owns a 32 x 8 column of outputs and streams through z: for every
-// input plane it stages the (32+b-1) x (8+b-1) tile in shared memory, sums
-// rows of b along x, then b row sums along y (the plane sum of that
-// column), keeps the last b plane sums in registers and emits their sum.
-// uint16: int32 / uint64 arithmetic, exact.  float32: float32 arithmetic
-// with every output formed by three levels of b-term sums (the match
-// kernel's error bound relies on that shape).
+// Both are separable box sums.  One CTA owns TX x TY x ZC outputs (spaced
+// `stride` voxels apart; stride 1 for matching).  Its input brick, with the
+// b-1 halo, is brought into shared memory by TMA in z-chunks of CZ planes,
+// each completing its own mbarrier, so the first planes are summed while the
+// later ones are still in flight.  Per input plane: sums of b along x at the
+// output columns, for every row of the plane (double-buffered, so one barrier
+// per plane suffices); then sums of b of those along y at the output rows,
+// one thread per output column; the last b plane sums stay in registers and
+// at every output plane their sum is the result.
+//   uint16: exact (32-bit sums of J, 64-bit sums of J^2, running z sums).
+//   float32: float sums whose every output is three levels of b-term sums;
+//            the match kernel's error bound relies on that shape.
+#include <stddef.h>
+
 #include "nrr_internal.h"
+#include "nrr_ptx.cuh"
 
 namespace nrr {
 namespace {
 
-constexpr int TX = 32, TY = 8, ZCHUNK = 32;
+constexpr int TX = 32, MAX_TY = 8, MAX_NT = TX * MAX_TY;
+constexpr int CZ = 4;          // planes per TMA chunk
+constexpr int MAX_CHUNKS = 8;  // so at most 32 input planes per CTA
+constexpr uint64_t BOX_WAIT_NS = 2000000000ull;
+constexpr size_t BOX_SMEM_TARGET = 110 * 1024;  // keeps two CTAs per SM
 
+// Per-element quantities summed: uint16 -> J (32-bit) and J^2 (64-bit,
+// exact); float32 -> J and J^2 in float.
 template <typename T>
-struct Acc;
+struct BoxQ;
 template <>
-struct Acc<uint16_t> {
-    typedef int32_t A1;
+struct BoxQ<uint16_t> {
+    typedef uint32_t A1;
     typedef unsigned long long A2;
-    static __device__ __forceinline__ A1 v1(uint16_t v) { return (A1)v; }
-    static __device__ __forceinline__ A2 v2(uint16_t v) { return (A2)((uint32_t)v * (uint32_t)v); }
+    static constexpr bool exact = true;
 };
 template <>
-struct Acc<float> {
+struct BoxQ<float> {
     typedef float A1;
     typedef float A2;
-    static __device__ __forceinline__ A1 v1(float v) { return v; }
-    static __device__ __forceinline__ A2 v2(float v) { return __fmul_rn(v, v); }
+    static constexpr bool exact = false;
 };
 
-template <typename T, int B>
-__global__ void __launch_bounds__(TX *TY) boxsum_kernel(const T *__restrict__ vol, int nx, int ny, int nz,
-                                                        typename Acc<T>::A1 *__restrict__ s1,
-                                                        typename Acc<T>::A2 *__restrict__ s2)
+// Geometry of one CTA's brick; the same on host and device.
+struct BoxGeom {
+    int S, TY, ZC;         // output spacing, output rows and planes per CTA
+    int xoff;              // x of the brick's first needed voxel inside the TMA box
+    int bw, ih, iz;        // TMA box width (x), rows, input planes
+    int nchunk;            // TMA chunks of CZ planes
+    size_t chunk_pitch;    // bytes between chunks (128-byte multiple)
+    size_t r_off;          // byte offset of the x-sum buffers
+    size_t smem;           // dynamic shared memory
+};
+
+__host__ __device__ inline BoxGeom box_geom(int B, int S, int TY, int ZC, int es)
 {
-    typedef typename Acc<T>::A1 A1;
-    typedef typename Acc<T>::A2 A2;
+    BoxGeom g;
+    const int H = (B - 1) / 2, A = 16 / es;  // TMA x coordinates are multiples of A elements
+    g.S = S;
+    g.TY = TY;
+    g.ZC = ZC;
+    g.xoff = (A - H % A) % A;
+    const int iw = (TX - 1) * S + B;
+    g.bw = (g.xoff + iw + A - 1) / A * A;
+    g.ih = (TY - 1) * S + B;
+    g.iz = (ZC - 1) * S + B;
+    g.nchunk = (g.iz + CZ - 1) / CZ;
+    g.chunk_pitch = ((size_t)g.bw * g.ih * CZ * es + 127) / 128 * 128;
+    g.r_off = g.chunk_pitch * g.nchunk;
+    const size_t a12 = es == 2 ? 12 : 8;  // bytes of (A1, A2) per x sum
+    g.smem = g.r_off + 2 * (size_t)g.ih * TX * a12;
+    return g;
+}
+
+struct BoxArgs {
+    BoxGeom g;
+    int nx, ny, nz;
+    int gx, gy, gz;  // outputs per axis (grid points for keys, voxels for box sums)
+    // box sums
+    void *out1, *out2;
+    // keys
+    const uint8_t *mask;
+    long long *keys;
+    unsigned long long *nc, *npos, *maxkey;
+    unsigned int *err;
+};
+
+template <typename T, int B, bool KEYS>
+__global__ void __launch_bounds__(MAX_NT) box_kernel(const __grid_constant__ CUtensorMap map, const BoxArgs a)
+{
+    typedef typename BoxQ<T>::A1 A1;
+    typedef typename BoxQ<T>::A2 A2;
     constexpr int H = (B - 1) / 2;
-    constexpr int IW = TX + B - 1, IH = TY + B - 1;
-    __shared__ T tile[IH][IW];
-    __shared__ A1 r1[IH][TX];
-    __shared__ A2 r2[IH][TX];
+    constexpr long long N = (long long)B * B * B;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar[MAX_CHUNKS];
+    const BoxGeom &g = a.g;
+    const int S = g.S, IH = g.ih, IZ = g.iz, BW = g.bw, NT = TX * g.TY;
+    A2 *rb2 = reinterpret_cast<A2 *>(smem + g.r_off);                              // [2][IH][TX]
+    A1 *rb1 = reinterpret_cast<A1 *>(smem + g.r_off + 2 * sizeof(A2) * IH * TX);  // [2][IH][TX]
 
-    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int zo0 = blockIdx.z * ZCHUNK, zo1 = min(nz, zo0 + ZCHUNK);
-    const int x = x0 + tx, y = y0 + ty;
-    const bool xy_ok = x < nx && y < ny;
-    const bool xy_in = x >= H && x <= nx - 1 - H && y >= H && y <= ny - 1 - H;
+    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * g.TY, k0 = blockIdx.z * g.ZC;
+    if (tid == 0) {
+        for (int c = 0; c < g.nchunk; ++c) mbar_init(bar + c, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const uint32_t bytes = (uint32_t)((size_t)BW * IH * CZ * sizeof(T));
+        const int xa = i0 * S - H - g.xoff, ya = j0 * S - H, za = k0 * S - H;
+        for (int c = 0; c < g.nchunk; ++c) {
+            mbar_arrive_expect_tx(bar + c, bytes);
+            tma_load_3d(smem + c * g.chunk_pitch, &map, bar + c, xa, ya, za + c * CZ);
+        }
+    }
 
+    const int i = i0 + tx, j = j0 + ty;  // this thread's output column
     A1 ring1[B];
     A2 ring2[B];
+    A1 run1 = 0;  // exact path: running sums of the ring
+    A2 run2 = 0;
 #pragma unroll
-    for (int i = 0; i < B; ++i) {
-        ring1[i] = 0;
-        ring2[i] = 0;
+    for (int k = 0; k < B; ++k) {
+        ring1[k] = 0;
+        ring2[k] = 0;
     }
-    // input planes zo0-H .. zo1-1+H; output plane z-H emitted after plane z
-    for (int z = zo0 - H; z < zo1 + H; ++z) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < IH * IW; i += TX * TY) {
-            int iy = i / IW, ix = i % IW;
-            int gx = x0 - H + ix, gy = y0 - H + iy;
-            T v = 0;
-            if (z >= 0 && z < nz && gx >= 0 && gx < nx && gy >= 0 && gy < ny)
-                v = vol[((size_t)z * ny + gy) * nx + gx];
-            tile[iy][ix] = v;
+    int cand = 0, pos = 0;
+    unsigned long long kmax = 0;
+
+    for (int iz = 0; iz < IZ; ++iz) {
+        if (iz % CZ == 0) {
+            const bool got = mbar_wait_bounded(bar + iz / CZ, 0, BOX_WAIT_NS);
+            if (!__syncthreads_and(got)) {
+                if (tid == 0) {
+                    atomicOr(a.err, DEV_ERR_TIMEOUT);
+                    for (int c = iz / CZ; c < g.nchunk; ++c)  // let copies in flight land before exiting
+                        mbar_wait_bounded(bar + c, 0, BOX_WAIT_NS);
+                }
+                __syncthreads();
+                return;
+            }
         }
-        __syncthreads();
-        for (int i = threadIdx.x; i < IH * TX; i += TX * TY) {
-            int iy = i / TX, ix = i % TX;
-            A1 a = 0;
-            A2 q = 0;
+        const T *plane = reinterpret_cast<const T *>(smem + (iz / CZ) * g.chunk_pitch) + (iz % CZ) * IH * BW;
+        A1 *r1 = rb1 + (iz & 1) * IH * TX;
+        A2 *r2 = rb2 + (iz & 1) * IH * TX;
+        // x sums at the output columns of every row of plane iz
+        for (int it = tid; it < IH * TX; it += NT) {
+            const int ox = it % TX, iy = it / TX;
+            const T *src = plane + iy * BW + g.xoff + ox * S;
+            A1 a1 = 0;
+            A2 a2 = 0;
 #pragma unroll
             for (int k = 0; k < B; ++k) {
-                T v = tile[iy][ix + k];
-                a += Acc<T>::v1(v);
-                q += Acc<T>::v2(v);
+                const T v = src[k];
+                if constexpr (BoxQ<T>::exact) {
+                    a1 += (uint32_t)v;
+                    a2 += (unsigned long long)((uint32_t)v) * (uint32_t)v;
+                } else {
+                    a1 += v;
+                    a2 += __fmul_rn(v, v);
+                }
             }
-            r1[iy][ix] = a;
-            r2[iy][ix] = q;
+            r1[iy * TX + ox] = a1;
+            r2[iy * TX + ox] = a2;
         }
-        __syncthreads();
+        __syncthreads();  // x sums of plane iz ready (and plane iz-2's buffer is free)
         A1 p1 = 0;
         A2 p2 = 0;
 #pragma unroll
         for (int k = 0; k < B; ++k) {
-            p1 += r1[ty + k][tx];
-            p2 += r2[ty + k][tx];
+            p1 += r1[(ty * S + k) * TX + tx];
+            p2 += r2[(ty * S + k) * TX + tx];
+        }
+        if constexpr (BoxQ<T>::exact) {
+            run1 += p1 - ring1[0];
+            run2 += p2 - ring2[0];
         }
 #pragma unroll
-        for (int i = 0; i < B - 1; ++i) {
-            ring1[i] = ring1[i + 1];
-            ring2[i] = ring2[i + 1];
+        for (int k = 0; k < B - 1; ++k) {
+            ring1[k] = ring1[k + 1];
+            ring2[k] = ring2[k + 1];
         }
         ring1[B - 1] = p1;
         ring2[B - 1] = p2;
-        const int zo = z - H;  // output plane whose block spans planes zo-H..zo+H == z-2H..z
-        if (zo >= zo0 && zo < zo1 && xy_ok) {
-            A1 o1 = 0;
-            A2 o2 = 0;
-            if (xy_in && zo >= H && zo <= nz - 1 - H) {
+        // the ring now holds input planes iz-B+1..iz: an output plane when
+        // they are the planes of local output kk
+        const int q = iz - (B - 1);
+        if (q < 0 || q % S) continue;
+        const int kk = q / S, k = k0 + kk;
+        if (kk >= g.ZC || k >= a.gz || i >= a.gx || j >= a.gy) continue;
+        A1 o1;
+        A2 o2;
+        if constexpr (BoxQ<T>::exact) {
+            o1 = run1;
+            o2 = run2;
+        } else {  // a direct sum of the b plane sums (fixed depth)
+            o1 = 0;
+            o2 = 0;
 #pragma unroll
-                for (int i = 0; i < B; ++i) {
-                    o1 += ring1[i];
-                    o2 += ring2[i];
-                }
+            for (int t = 0; t < B; ++t) {
+                o1 += ring1[t];
+                o2 += ring2[t];
             }
-            size_t idx = ((size_t)zo * ny + y) * nx + x;
-            s1[idx] = o1;
-            s2[idx] = o2;
+        }
+        const int x = i * S, y = j * S, z = k * S;
+        const bool in = x >= H && x <= a.nx - 1 - H && y >= H && y <= a.ny - 1 - H && z >= H && z <= a.nz - 1 - H;
+        if constexpr (KEYS) {
+            long long key = -1;
+            if (in && a.mask[((size_t)z * a.ny + y) * a.nx + x] != 0) {
+                key = N * (long long)o2 - (long long)o1 * (long long)o1;
+                cand += 1;
+                pos += key > 0;
+                kmax = (unsigned long long)key > kmax ? (unsigned long long)key : kmax;
+            }
+            a.keys[((long long)k * a.gy + j) * a.gx + i] = key;
+        } else {
+            const size_t idx = ((size_t)z * a.ny + y) * a.nx + x;
+            if constexpr (BoxQ<T>::exact) {
+                reinterpret_cast<int32_t *>(a.out1)[idx] = in ? (int32_t)o1 : 0;
+                reinterpret_cast<unsigned long long *>(a.out2)[idx] = in ? (unsigned long long)o2 : 0ull;
+            } else {
+                reinterpret_cast<float *>(a.out1)[idx] = in ? (float)o1 : 0.f;
+                reinterpret_cast<float *>(a.out2)[idx] = in ? (float)o2 : 0.f;
+            }
+        }
+    }
+
+    if constexpr (KEYS) {  // candidate counts and the largest key of this CTA
+        __shared__ int ws[MAX_NT / 32][2];
+        __shared__ unsigned long long wmax[MAX_NT / 32];
+        for (int o = 16; o; o >>= 1) {
+            cand += __shfl_xor_sync(0xffffffffu, cand, o);
+            pos += __shfl_xor_sync(0xffffffffu, pos, o);
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, kmax, o);
+            kmax = other > kmax ? other : kmax;
+        }
+        if ((tid & 31) == 0) {
+            ws[tid >> 5][0] = cand;
+            ws[tid >> 5][1] = pos;
+            wmax[tid >> 5] = kmax;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int c = 0, p = 0;
+            unsigned long long mx = 0;
+            for (int w = 0; w < NT / 32; ++w) {
+                c += ws[w][0];
+                p += ws[w][1];
+                mx = wmax[w] > mx ? wmax[w] : mx;
+            }
+            if (c) atomicAdd(a.nc, (unsigned long long)c);
+            if (p) atomicAdd(a.npos, (unsigned long long)p);
+            if (mx) atomicMax(a.maxkey, mx);
         }
     }
 }
 
-template <typename T, int B>
-void launch_one(const void *vol, nrr_dims d, void *bs, size_t off2, cudaStream_t st)
+// The largest CTA tile (TY in {8, 4}, then ZC in {16, 8, 4}) whose brick fits
+// the shared-memory target and the chunk count; ok = false if none does.
+inline bool pick_geom(int B, int S, int es, BoxGeom *out)
 {
-    typedef typename Acc<T>::A1 A1;
-    typedef typename Acc<T>::A2 A2;
-    dim3 grid((d.nx + TX - 1) / TX, (d.ny + TY - 1) / TY, (d.nz + ZCHUNK - 1) / ZCHUNK);
-    boxsum_kernel<T, B><<<grid, TX * TY, 0, st>>>((const T *)vol, d.nx, d.ny, d.nz, (A1 *)bs,
-                                                  (A2 *)((char *)bs + off2));
+    for (int ty = MAX_TY; ty >= 4; ty /= 2)
+        for (int zc = 16; zc >= 4; zc /= 2) {
+            const BoxGeom g = box_geom(B, S, ty, zc, es);
+            if (g.nchunk <= MAX_CHUNKS && g.bw <= 256 && g.ih <= 256 && g.smem <= BOX_SMEM_TARGET) {
+                *out = g;
+                return true;
+            }
+        }
+    return false;
 }
 
-template <typename T>
-void launch_t(const void *vol, nrr_dims d, int b, void *bs, size_t off2, cudaStream_t st)
+template <typename T, int B, bool KEYS>
+cudaError_t launch_box(const CUtensorMap &map, BoxArgs &a, cudaStream_t st)
+{
+    auto kern = box_kernel<T, B, KEYS>;
+    static size_t attr = 0;  // largest dynamic shared memory opted in so far
+    if (a.g.smem > attr) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.g.smem);
+        if (e != cudaSuccess) return e;
+        attr = a.g.smem;
+    }
+    dim3 grid((a.gx + TX - 1) / TX, (a.gy + a.g.TY - 1) / a.g.TY, (a.gz + a.g.ZC - 1) / a.g.ZC);
+    kern<<<grid, TX * a.g.TY, a.g.smem, st>>>(map, a);
+    return cudaGetLastError();
+}
+
+template <typename T, bool KEYS>
+cudaError_t launch_box_b(int b, const CUtensorMap &map, BoxArgs &a, cudaStream_t st)
 {
     switch (b) {
-    case 3: launch_one<T, 3>(vol, d, bs, off2, st); break;
-    case 5: launch_one<T, 5>(vol, d, bs, off2, st); break;
-    case 7: launch_one<T, 7>(vol, d, bs, off2, st); break;
-    case 9: launch_one<T, 9>(vol, d, bs, off2, st); break;
-    default: launch_one<T, 11>(vol, d, bs, off2, st); break;
+    case 3: return launch_box<T, 3, KEYS>(map, a, st);
+    case 5: return launch_box<T, 5, KEYS>(map, a, st);
+    case 7: return launch_box<T, 7, KEYS>(map, a, st);
+    case 9: return launch_box<T, 9, KEYS>(map, a, st);
+    default: return launch_box<T, 11, KEYS>(map, a, st);
     }
 }
 
@@ -149,14 +312,57 @@ void launch_t(const void *vol, nrr_dims d, int b, void *bs, size_t off2, cudaStr
 nrr_status launch_boxsums(const void *d_intraop, nrr_dtype dtype, nrr_dims dims, int32_t block, void *d_boxsums,
                           cudaStream_t stream)
 {
-    size_t off2 = boxsum_s2_offset(dims, dtype);
-    if (dtype == NRR_F32)
-        launch_t<float>(d_intraop, dims, block, d_boxsums, off2, stream);
-    else
-        launch_t<uint16_t>(d_intraop, dims, block, d_boxsums, off2, stream);
-    cudaError_t e = cudaGetLastError();
+    const int es = (int)elem_size(dtype);
+    BoxArgs a{};
+    if (!pick_geom(block, 1, es, &a.g)) return fail(NRR_E_INTERNAL, "box-sum brick does not fit shared memory");
+    a.nx = a.gx = dims.nx;
+    a.ny = a.gy = dims.ny;
+    a.nz = a.gz = dims.nz;
+    a.out1 = d_boxsums;
+    a.out2 = (char *)d_boxsums + boxsum_s2_offset(dims, dtype);
+    nrr_status s = device_error_word(&a.err);
+    if (s != NRR_OK) return s;
+    CUtensorMap map;
+    s = encode_volume_map(&map, d_intraop, dtype, dims, a.g.bw, a.g.ih, CZ);
+    if (s != NRR_OK) return s;
+    cudaError_t e = dtype == NRR_F32 ? launch_box_b<float, false>(block, map, a, stream)
+                                     : launch_box_b<uint16_t, false>(block, map, a, stream);
     if (e != cudaSuccess) return cuda_fail(e, "boxsum kernel launch");
     count_launches(1);
+    return NRR_OK;
+}
+
+bool keys_box_supported(int32_t block, int32_t stride)
+{
+    BoxGeom g;
+    return stride <= 3 && pick_geom(block, stride, 2, &g);
+}
+
+nrr_status launch_keys_box(const uint16_t *d_preop, const uint8_t *d_mask, nrr_dims dims, int32_t block,
+                           int32_t stride, int gx, int gy, int gz, long long *keys, unsigned long long *nc,
+                           unsigned long long *npos, unsigned long long *maxkey, cudaStream_t stream)
+{
+    BoxArgs a{};
+    if (stride > 3 || !pick_geom(block, stride, 2, &a.g))
+        return fail(NRR_E_INTERNAL, "key brick does not fit shared memory");
+    a.nx = dims.nx;
+    a.ny = dims.ny;
+    a.nz = dims.nz;
+    a.gx = gx;
+    a.gy = gy;
+    a.gz = gz;
+    a.mask = d_mask;
+    a.keys = keys;
+    a.nc = nc;
+    a.npos = npos;
+    a.maxkey = maxkey;
+    nrr_status s = device_error_word(&a.err);
+    if (s != NRR_OK) return s;
+    CUtensorMap map;
+    s = encode_volume_map(&map, d_preop, NRR_U16, dims, a.g.bw, a.g.ih, CZ);
+    if (s != NRR_OK) return s;
+    cudaError_t e = launch_box_b<uint16_t, true>(block, map, a, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "key kernel launch");
     return NRR_OK;
 }
 

@@ -54,6 +54,15 @@ inline size_t boxsum_s2_offset(nrr_dims dims, nrr_dtype dtype)
 nrr_status launch_boxsums(const void *d_intraop, nrr_dtype dtype, nrr_dims dims, int32_t block, void *d_boxsums,
                           cudaStream_t stream);
 
+// Selection keys N*sum(I^2) - (sum I)^2 at the stride grid points through the
+// box-sum kernel (strides up to 3): keys[(k*gy + j)*gx + i] for the point
+// (i, j, k)*stride, -1 for non-candidates; adds the candidate count, the count
+// of keys > 0 and the largest key into *nc, *npos, *maxkey.
+bool keys_box_supported(int32_t block, int32_t stride);
+nrr_status launch_keys_box(const uint16_t *d_preop, const uint8_t *d_mask, nrr_dims dims, int32_t block,
+                           int32_t stride, int gx, int gy, int gz, long long *keys, unsigned long long *nc,
+                           unsigned long long *npos, unsigned long long *maxkey, cudaStream_t stream);
+
 // Match kernel launch (box sums already computed).  One launch serves up to
 // MATCH_MAX_JOBS lists of blocks that share the volume pair, block size and
 // search radius (one job per registration or per parameter setting).

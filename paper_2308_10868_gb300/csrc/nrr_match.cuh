@@ -11,8 +11,11 @@
 //      pitches make every 16-byte load of 8 consecutive threads hit 8
 //      distinct bank groups.  Out-of-volume voxels arrive as zeros and are
 //      excluded by coordinates.
-//   2. Warp 0 reduces the floating block's sums; the CTA stores it
-//      mean-shifted (T_k = I_k - m) as float.
+//   2. Every warp sums a share of the floating block; each thread combines
+//      the partials into the shift m (cheap, identical everywhere) and
+//      thread 0 alone derives the FP64 block constants (FP64 issue is
+//      scarce on this part).  The CTA stores the block mean-shifted
+//      (T_k = I_k - m) as float.
 //   3. Search: thread t owns one (dz, dy) line of the window and all 2*rx+1
 //      shifts along x.  For every template row it reads the window row
 //      straight from the TMA buffer with 16-byte loads, turns the values it
@@ -27,10 +30,11 @@
 //      chain, Cauchy-Schwarz sum|T||J'| <= sqrt(sum T^2 * sum J'^2), plus the
 //      rounding of the final operations; doubled for margin).
 //   5. Shifts whose upper bound reaches the best lower bound survive (about
-//      one per block on the phantoms) and are rescored by a warp each:
-//      uint16 -> exact int64 sum, then the canonical FP64 ratio
-//      num / sqrt(vI * vJ); float32 -> FP64 Pearson.  The best survivor
-//      under the tie-break rule is the block's answer.
+//      one per block on the phantoms) and are rescored: a warp per survivor,
+//      or, with fewer survivors than warps, each survivor's terms split over
+//      several warps.  uint16 -> exact int64 sum, then the canonical FP64
+//      ratio num / sqrt(vI * vJ); float32 -> FP64 Pearson.  The best
+//      survivor under the tie-break rule is the block's answer.
 // The exhaustive maximum is therefore found exactly: the true arg-max can
 // never be filtered out, because its upper bound is at least its value,
 // which is at least every other shift's value, hence at least every lower
@@ -75,7 +79,6 @@ struct BlockConst {
     float mu;       // float32: float mean used for T
     float emu;      // float32: Ibar - mu
     int m;          // uint16: integer mean used for T
-    int flat;       // floating block has zero variance
 };
 
 struct MatchScratch {
@@ -87,6 +90,15 @@ struct MatchScratch {
     int bok[MATCH_MAX_WARPS];
     int nsurv;
     int jstart[MATCH_MAX_JOBS + 1];  // first work item of each job
+    // per-warp partial statistics of the floating block
+    double pd1[MATCH_MAX_WARPS], pd2[MATCH_MAX_WARPS];
+    long long pi1[MATCH_MAX_WARPS];
+    unsigned long long pi2[MATCH_MAX_WARPS];
+    float plo[MATCH_MAX_WARPS], phi[MATCH_MAX_WARPS];
+    // per-warp partial sums when few survivors are split across warps
+    long long re[MATCH_MAX_WARPS], rs1[MATCH_MAX_WARPS], rs2[MATCH_MAX_WARPS];
+    double rf[MATCH_MAX_WARPS][3];
+    float rlo[MATCH_MAX_WARPS], rhi[MATCH_MAX_WARPS];
 };
 
 __host__ __device__ constexpr int round_up_c(int v, int a) { return (v + a - 1) / a * a; }
@@ -273,15 +285,16 @@ __device__ __forceinline__ void search_line(const T *row0, int zstride, const fl
     }
 }
 
-// Register budget: at most 80 registers per thread for blocks up to 7^3 and
-// up to 11 x-shifts (5-6 search CTAs of <= 128 threads per SM), 128 above.
+// Register budget per thread: 96 for blocks up to 7^3 with up to 11
+// x-shifts (5 search CTAs per SM are limited by shared memory there anyway),
+// 128 above.
 template <int B, int P>
-struct MatchMinBlocks {
-    static constexpr int value = (P <= 11 && B <= 7) ? 3 : 2;
+struct MatchRegs {
+    static constexpr int value = (P <= 11 && B <= 7) ? 96 : 128;
 };
 
 template <typename T, int B, int P>
-__global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value) match_kernel(
+__global__ void __maxnreg__((MatchRegs<B, P>::value)) match_kernel(
     const MatchParams a, const __grid_constant__ CUtensorMap tmapJ, const __grid_constant__ CUtensorMap tmapI)
 {
     constexpr bool F32 = std::is_same<T, float>::value;
@@ -408,103 +421,127 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
         const int nb = next_inside(blk + gridDim.x);
         if (nb < n && tid == 0) issue(nb, b ^ 1);  // buffer b^1 was released by the previous block's last barrier
 
-        // ---- warp 0: floating block statistics ------------------------------
-        if (warp == 0) {
-            constexpr int KPL = (N + 31) / 32;
-            constexpr int CH = KPL < 6 ? KPL : 6;
+        // ---- floating block statistics: every warp sums a share, then every
+        // thread combines the per-warp partials (one pass, one barrier) ----
+        {
+            constexpr int IPT = (N + 63) / 64;  // values per thread at 64+ threads
             if constexpr (F32) {
-                double s = 0.0;
+                double s1 = 0.0, s2 = 0.0;
                 float lo = INFINITY, hi = -INFINITY;
-#pragma unroll 1
-                for (int i0 = 0; i0 < KPL; i0 += CH) {
-                    float vals[CH];
+                for (int k0 = tid; k0 < N; k0 += IPT * nthr) {
+                    float vals[IPT];
 #pragma unroll
-                    for (int q = 0; q < CH; ++q) {
-                        const int k = lane + 32 * (i0 + q);
+                    for (int q = 0; q < IPT; ++q) {
+                        const int k = k0 + q * nthr;
                         const int kzy = k / B, kx = k - kzy * B;
                         vals[q] = k < N ? Ut[kzy * BTX + xot + kx] : 0.f;
                     }
 #pragma unroll
-                    for (int q = 0; q < CH; ++q)
-                        if (lane + 32 * (i0 + q) < N) {
-                            s += (double)vals[q];
+                    for (int q = 0; q < IPT; ++q)
+                        if (k0 + q * nthr < N) {
+                            const double d = (double)vals[q];
+                            s1 += d;
+                            s2 = fma(d, d, s2);
                             lo = fminf(lo, vals[q]);
                             hi = fmaxf(hi, vals[q]);
                         }
                 }
-                s = warp_sum(s);
+                s1 = warp_sum(s1);
+                s2 = warp_sum(s2);
                 lo = warp_min_f(lo);
                 hi = warp_max_f(hi);
-                const double ibar = s / (double)N;
-                const float mu = (float)ibar;
-                double qq = 0.0, dv = 0.0;
-#pragma unroll 1
-                for (int i0 = 0; i0 < KPL; i0 += CH) {
-                    float vals[CH];
-#pragma unroll
-                    for (int q = 0; q < CH; ++q) {
-                        const int k = lane + 32 * (i0 + q);
-                        const int kzy = k / B, kx = k - kzy * B;
-                        vals[q] = k < N ? Ut[kzy * BTX + xot + kx] : 0.f;
-                    }
-#pragma unroll
-                    for (int q = 0; q < CH; ++q)
-                        if (lane + 32 * (i0 + q) < N) {
-                            const double t = (double)__fsub_rn(vals[q], mu);
-                            qq = fma(t, t, qq);
-                            const double d = (double)vals[q] - ibar;
-                            dv = fma(d, d, dv);
-                        }
-                }
-                qq = warp_sum(qq);
-                dv = warp_sum(dv);
                 if (lane == 0) {
-                    BlockConst &c = sc->bc;
-                    c.flat = !(lo < hi);
-                    c.ibar = ibar;
-                    c.mu = mu;
-                    c.emu = (float)(ibar - (double)mu);
-                    c.dvI = dv;
-                    c.fvI = (float)dv;
-                    c.kq = (float)(sqrt(qq) * (1.0 + 1e-6));
+                    sc->pd1[warp] = s1;
+                    sc->pd2[warp] = s2;
+                    sc->plo[warp] = lo;
+                    sc->phi[warp] = hi;
                 }
             } else {
-                long long s = 0;
-                unsigned long long q2 = 0;
-#pragma unroll 1
-                for (int i0 = 0; i0 < KPL; i0 += CH) {
-                    uint32_t vals[CH];
+                unsigned int s1 = 0;
+                unsigned long long s2 = 0;
+                for (int k0 = tid; k0 < N; k0 += IPT * nthr) {
+                    uint32_t vals[IPT];
 #pragma unroll
-                    for (int q = 0; q < CH; ++q) {
-                        const int k = lane + 32 * (i0 + q);
+                    for (int q = 0; q < IPT; ++q) {
+                        const int k = k0 + q * nthr;
                         const int kzy = k / B, kx = k - kzy * B;
                         vals[q] = k < N ? (uint32_t)Ut[kzy * BTX + xot + kx] : 0u;
                     }
 #pragma unroll
-                    for (int q = 0; q < CH; ++q) {
-                        s += vals[q];
-                        q2 += (unsigned long long)(vals[q] * vals[q]);
+                    for (int q = 0; q < IPT; ++q) {
+                        s1 += vals[q];
+                        s2 += (unsigned long long)vals[q] * vals[q];
                     }
                 }
-                s = warp_sum(s);
-                q2 = warp_sum(q2);
+                const long long s1w = warp_sum((long long)s1);
+                s2 = warp_sum(s2);
                 if (lane == 0) {
-                    BlockConst &c = sc->bc;
-                    const long long vI = (long long)N * (long long)q2 - s * s;
-                    const long long m = (long long)((2u * (uint32_t)s + (uint32_t)N) / (2u * (uint32_t)N));  // nearest integer to the mean
-                    const long long qt = (long long)q2 - 2 * m * s + (long long)N * m * m;  // sum (I-m)^2, exact
-                    c.vI = vI;
-                    c.flat = vI == 0;
-                    c.m = (int)m;
-                    c.rr = (long long)N * m - s;
-                    c.fvI = (float)vI;
-                    c.kq = (float)((double)N * GAMMA_N * sqrt((double)qt) * (1.0 + 1e-6));
+                    sc->pi1[warp] = s1w;
+                    sc->pi2[warp] = s2;
                 }
             }
         }
         __syncthreads();
-        const BlockConst bc = sc->bc;
-        if (bc.flat) {  // flat floating block: NCC undefined for every shift
+        // Every thread needs only the template shift and the flat test, both
+        // cheap and computed identically everywhere; thread 0 alone derives
+        // the FP64 block constants (FP64 units are scarce on this part), read
+        // by all threads from shared memory after the next barrier.
+        float tsh;
+        bool flat;
+        if constexpr (F32) {
+            float sf = 0.f, lo = INFINITY, hi = -INFINITY;
+            for (int w = 0; w < nwarp; ++w) {
+                sf += (float)sc->pd1[w];
+                lo = fminf(lo, sc->plo[w]);
+                hi = fmaxf(hi, sc->phi[w]);
+            }
+            tsh = __fmul_rn(sf, 1.0f / (float)N);  // any float near the mean serves as the shift mu
+            flat = !(lo < hi);
+            if (tid == 0 && !flat) {
+                double s1 = 0.0, s2 = 0.0;
+                for (int w = 0; w < nwarp; ++w) {
+                    s1 += sc->pd1[w];
+                    s2 += sc->pd2[w];
+                }
+                const double ibar = s1 / (double)N;
+                double dv = s2 - s1 * ibar;  // sum (I - Ibar)^2
+                if (dv < 0.0) dv = 0.0;
+                const double em = ibar - (double)tsh;
+                BlockConst &c = sc->bc;
+                c.ibar = ibar;
+                c.mu = tsh;
+                c.emu = (float)em;
+                c.dvI = dv;
+                c.fvI = (float)dv;
+                // sum of T^2 with T = fl(I - mu): at most (1+u)^2 sum (I - mu)^2
+                // = (1+u)^2 (sum (I - Ibar)^2 + N (Ibar - mu)^2); the FP64
+                // one-pass spread is inexact by at most a few ulp of s2
+                c.kq = (float)(sqrt((dv + 64.0 * 1.1102230246251565e-16 * s2 + (double)N * em * em) * (1.0 + 2.4e-7)) *
+                               (1.0 + 1e-6));
+            }
+        } else {
+            long long s1 = 0;
+            unsigned long long s2 = 0;
+            for (int w = 0; w < nwarp; ++w) {
+                s1 += sc->pi1[w];
+                s2 += sc->pi2[w];
+            }
+            const long long vI = (long long)N * (long long)s2 - s1 * s1;
+            const uint32_t m = (2u * (uint32_t)s1 + (uint32_t)N) / (2u * (uint32_t)N);  // nearest integer to the mean
+            tsh = 8388608.0f + (float)m;
+            flat = vI == 0;
+            if (tid == 0 && !flat) {
+                const long long mm = (long long)m;
+                const long long qt = (long long)s2 - 2 * mm * s1 + (long long)N * mm * mm;  // sum (I-m)^2, exact
+                BlockConst &c = sc->bc;
+                c.vI = vI;
+                c.m = (int)m;
+                c.rr = (long long)N * mm - s1;
+                c.fvI = (float)vI;
+                c.kq = (float)((double)N * GAMMA_N * sqrt((double)qt) * (1.0 + 1e-6));
+            }
+        }
+        if (flat) {  // flat floating block: NCC undefined for every shift
             if (tid == 0) write_result(J, bi, Cand{0.0, 0, 0, 0}, P, py, RX, ry, rz);
             __syncthreads();
             blk = nb;
@@ -513,7 +550,6 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
         }
         // ---- mean-shifted template (loads batched before stores) -----------
         {
-            const float tsh = F32 ? bc.mu : 8388608.0f + (float)bc.m;
             constexpr int TB = B * B * PT;
             constexpr int TPT = (TB + 63) / 64;  // items per thread at 64+ threads
             float v[TPT];
@@ -547,6 +583,7 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
             }
         }
         __syncthreads();
+        const BlockConst &bc = sc->bc;
 
         // ---- search: FP32 accumulation of A(d) over the whole window ------
         float ub[P];
@@ -674,48 +711,64 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
         __syncthreads();
         const int nsurv = sc->nsurv;
 
-        // ---- exact rescoring of the survivors, one warp each -------------
+        // ---- exact rescoring of the survivors ---------------------------------
+        // With at least as many survivors as warps, each warp rescores whole
+        // survivors; with fewer, each survivor's terms are split over
+        // nwarp/nsurv warps whose partial sums thread 0 adds up.
+        const int parts = nsurv >= nwarp ? 1 : (nsurv > 0 ? nwarp / nsurv : 1);
+        constexpr int KS1 = N;  // terms of a whole survivor
         Cand wb{0.0, 0, 0, 0};
-        for (int s = warp; s < nsurv; s += nwarp) {
-            const int code = surv[s];
+        const int ntask = parts == 1 ? nsurv : nsurv * parts;
+        for (int task = warp; task < ntask; task += nwarp) {
+            const int sidx = task / parts, part = task - sidx * parts;
+            const int ks = (KS1 + parts - 1) / parts;
+            const int kbeg = part * ks, kend = kbeg + ks < N ? kbeg + ks : N;
+            const int code = surv[sidx];
             const int sxi = code % P, syi = (code / P) % py, szi = code / (P * py);
             const int dx = sxi - RX, dy = syi - ry, dz = szi - rz;
             const size_t idx = ((size_t)(cz + dz) * ny + (cy + dy)) * nx + (cx + dx);
             Cand c{0.0, dx * dx + dy * dy + dz * dz, code, 0};
             if constexpr (!F32) {
                 long long s1 = 0, s2 = 0;
-                if (lane == 0) {  // issued first, consumed after the warp sum
+                if (lane == 0 && part == 0) {  // issued first, consumed after the warp sum
                     s1 = reinterpret_cast<const int32_t *>(a.s1)[idx];
                     s2 = reinterpret_cast<const long long *>(a.s2)[idx];
                 }
-                constexpr int KPL = (N + 31) / 32;
-                constexpr int CH = KPL < 6 ? KPL : 6;
+                constexpr int CH = 4;
                 long long e = 0;
 #pragma unroll 1
-                for (int i0 = 0; i0 < KPL; i0 += CH) {
+                for (int k0 = kbeg + lane; k0 < kend; k0 += 32 * CH) {
                     int tv[CH], jv[CH];
 #pragma unroll
-                    for (int i = 0; i < CH; ++i) {
-                        const int k = lane + 32 * (i0 + i);
+                    for (int q = 0; q < CH; ++q) {
+                        const int k = k0 + 32 * q;
                         const int kz = k / (B * B), rem = k - kz * B * B, ky = rem / B, kx = rem - ky * B;
-                        tv[i] = 0;
-                        jv[i] = 0;
-                        if (k < N) {
-                            tv[i] = (int)Tm[(kz * B + ky) * PT + kx];
-                            jv[i] = (int)U[((szi + kz) * wyp + (syi + ky)) * BX + xo + sxi + kx] - c_i;
+                        tv[q] = 0;
+                        jv[q] = 0;
+                        if (k < kend) {
+                            tv[q] = (int)Tm[(kz * B + ky) * PT + kx];
+                            jv[q] = (int)U[((szi + kz) * wyp + (syi + ky)) * BX + xo + sxi + kx] - c_i;
                         }
                     }
 #pragma unroll
-                    for (int i = 0; i < CH; ++i) e += (long long)tv[i] * jv[i];
+                    for (int q = 0; q < CH; ++q) e += (long long)tv[q] * jv[q];
                 }
                 e = warp_sum(e);
                 if (lane == 0) {
-                    const long long vJ = (long long)N * s2 - s1 * s1;
-                    const long long num = (long long)N * e + bc.rr * (s1 - (long long)N * c_i);
-                    if (vJ > 0) {
-                        const double den = __dsqrt_rn(__dmul_rn((double)bc.vI, (double)vJ));
-                        c.s = __ddiv_rn((double)num, den);
-                        c.ok = 1;
+                    if (parts == 1) {
+                        const long long vJ = (long long)N * s2 - s1 * s1;
+                        const long long num = (long long)N * e + bc.rr * (s1 - (long long)N * c_i);
+                        if (vJ > 0) {
+                            const double den = __dsqrt_rn(__dmul_rn((double)bc.vI, (double)vJ));
+                            c.s = __ddiv_rn((double)num, den);
+                            c.ok = 1;
+                        }
+                    } else {
+                        sc->re[task] = e;
+                        if (part == 0) {
+                            sc->rs1[task] = s1;
+                            sc->rs2[task] = s2;
+                        }
                     }
                 }
             } else {
@@ -723,7 +776,7 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
                 const float *intra = reinterpret_cast<const float *>(a.intraop);
                 double sij = 0.0, sj = 0.0, sjj = 0.0;
                 float lo = INFINITY, hi = -INFINITY;
-                for (int k = lane; k < N; k += 32) {
+                for (int k = kbeg + lane; k < kend; k += 32) {
                     const int kz = k / (B * B), rem = k - kz * B * B, ky = rem / B, kx = rem - ky * B;
                     const double di =
                         (double)pre[((size_t)(cz - H + kz) * ny + (cy - H + ky)) * nx + (cx - H + kx)] - bc.ibar;
@@ -740,15 +793,25 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
                 sjj = warp_sum(sjj);
                 lo = warp_min_f(lo);
                 hi = warp_max_f(hi);
-                if (lane == 0 && lo < hi) {
-                    const double vJ = sjj - sj * sj / (double)N;
-                    if (vJ > 0.0) {
-                        c.s = sij / sqrt(bc.dvI * vJ);
-                        c.ok = 1;
+                if (lane == 0) {
+                    if (parts == 1) {
+                        if (lo < hi) {
+                            const double vJ = sjj - sj * sj / (double)N;
+                            if (vJ > 0.0) {
+                                c.s = sij / sqrt(bc.dvI * vJ);
+                                c.ok = 1;
+                            }
+                        }
+                    } else {
+                        sc->rf[task][0] = sij;
+                        sc->rf[task][1] = sj;
+                        sc->rf[task][2] = sjj;
+                        sc->rlo[task] = lo;
+                        sc->rhi[task] = hi;
                     }
                 }
             }
-            if (lane == 0 && cand_better(c, wb)) wb = c;
+            if (lane == 0 && parts == 1 && cand_better(c, wb)) wb = c;
         }
         if (lane == 0) {
             sc->bs[warp] = wb.s;
@@ -762,6 +825,44 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
             for (int w = 0; w < nwarp; ++w) {
                 Cand c{sc->bs[w], sc->bn2[w], sc->bcode[w], sc->bok[w]};
                 if (cand_better(c, best)) best = c;
+            }
+            if (parts > 1) {
+                for (int si = 0; si < nsurv; ++si) {
+                    const int code = surv[si];
+                    const int sxi = code % P, syi = (code / P) % py, szi = code / (P * py);
+                    const int dx = sxi - RX, dy = syi - ry, dz = szi - rz;
+                    Cand c{0.0, dx * dx + dy * dy + dz * dz, code, 0};
+                    if constexpr (!F32) {
+                        long long e = 0;
+                        for (int q = 0; q < parts; ++q) e += sc->re[si * parts + q];
+                        const long long s1 = sc->rs1[si * parts], s2 = sc->rs2[si * parts];
+                        const long long vJ = (long long)N * s2 - s1 * s1;
+                        const long long num = (long long)N * e + bc.rr * (s1 - (long long)N * c_i);
+                        if (vJ > 0) {
+                            const double den = __dsqrt_rn(__dmul_rn((double)bc.vI, (double)vJ));
+                            c.s = __ddiv_rn((double)num, den);
+                            c.ok = 1;
+                        }
+                    } else {
+                        double sij = 0.0, sj = 0.0, sjj = 0.0;
+                        float lo = INFINITY, hi = -INFINITY;
+                        for (int q = 0; q < parts; ++q) {
+                            sij += sc->rf[si * parts + q][0];
+                            sj += sc->rf[si * parts + q][1];
+                            sjj += sc->rf[si * parts + q][2];
+                            lo = fminf(lo, sc->rlo[si * parts + q]);
+                            hi = fmaxf(hi, sc->rhi[si * parts + q]);
+                        }
+                        if (lo < hi) {
+                            const double vJ = sjj - sj * sj / (double)N;
+                            if (vJ > 0.0) {
+                                c.s = sij / sqrt(bc.dvI * vJ);
+                                c.ok = 1;
+                            }
+                        }
+                    }
+                    if (cand_better(c, best)) best = c;
+                }
             }
             write_result(J, bi, best, P, py, RX, ry, rz);
         }

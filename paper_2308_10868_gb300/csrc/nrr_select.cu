@@ -3,13 +3,17 @@
 // The paper partitions the image among threads, computes a variance and an
 // index per candidate, sorts the pairs in parallel, merges them and keeps
 // 0.5 + N_c * F_s blocks.  Here that becomes:
-//   K1 grid_keys     one thread per stride grid point: exact variance key
-//                    N*sum(I^2) - (sum I)^2 of its b^3 block if it is a
-//                    candidate (centre in mask, block in volume), else -1;
-//                    counts N_c and the number of keys > 0.
-//   K2 radix select  five histogram passes over 11/11/11/11/9-bit digits of
-//                    the (< 2^53) keys find the n_sel-th largest key K* and
-//                    how many keys equal to K* are needed; no full sort.
+//   K1 keys          exact key N*sum(I^2) - (sum I)^2 of the b^3 block at
+//                    every stride grid point that is a candidate (centre in
+//                    mask, block in volume), else -1; counts N_c and the
+//                    number of keys > 0.  Strides up to 3 use the TMA-fed
+//                    separable box-sum kernel (nrr_boxsum.cu); larger ones one
+//                    thread per grid point.
+//   K2 radix select  up to five histogram passes over 11-bit digits of the
+//                    keys, starting at the top bit of the largest key, find
+//                    the n_sel-th largest key K* and how many keys equal to
+//                    K* are needed; no full sort.  The CTA that finishes a
+//                    pass last picks the digit, so a pass is one launch.
 //   K3 compaction    an order-preserving compaction writes every centre
 //                    with key > K*, plus the first `need` with key == K*
 //                    in raster order, to the output in raster order.
@@ -27,13 +31,10 @@ namespace {
 constexpr int KEY_THREADS = 256;
 constexpr int HIST_BINS = 2048;
 constexpr int HIST_THREADS = 512;
-constexpr int PICK_THREADS = 1024;
 constexpr int CMP_THREADS = 1024;
 constexpr int CMP_ITEMS = 4;
 constexpr int CMP_CHUNK = CMP_THREADS * CMP_ITEMS;
 constexpr int NPASS = 5;
-__constant__ int c_shift[NPASS] = {42, 31, 20, 9, 0};
-__constant__ int c_width[NPASS] = {11, 11, 11, 11, 9};
 
 struct SelState {
     unsigned long long nc;    // candidates
@@ -43,6 +44,8 @@ struct SelState {
     long long nsel;           // number selected
     long long thresh;         // key of the nsel-th largest (K*)
     long long need_ties;      // how many keys equal to K* are selected
+    unsigned long long maxkey;  // largest key (sets the first digit)
+    unsigned int arrived[NPASS + 1];  // CTAs finished per histogram pass / count pass
     int done;                 // nothing (more) to select
 };
 
@@ -56,6 +59,7 @@ __global__ void __launch_bounds__(KEY_THREADS) grid_keys_kernel(const uint16_t *
     constexpr long long N = (long long)B * B * B;
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int cand = 0, pos = 0;
+    unsigned long long kmax = 0;
     if (g < ng) {
         const int i = (int)(g % gx), j = (int)((g / gx) % gy), k = (int)(g / ((long long)gx * gy));
         const int x = i * stride, y = j * stride, z = k * stride;
@@ -81,59 +85,96 @@ __global__ void __launch_bounds__(KEY_THREADS) grid_keys_kernel(const uint16_t *
             key = N * (long long)q - (long long)s * (long long)s;
             cand = 1;
             pos = key > 0;
+            kmax = (unsigned long long)key;
         }
         keys[g] = key;
     }
     // block reduction of the two counts
     __shared__ int ws[KEY_THREADS / 32][2];
+    __shared__ unsigned long long wmax[KEY_THREADS / 32];
     unsigned m = 0xffffffffu;
     for (int o = 16; o; o >>= 1) {
         cand += __shfl_xor_sync(m, cand, o);
         pos += __shfl_xor_sync(m, pos, o);
+        const unsigned long long other = __shfl_xor_sync(m, kmax, o);
+        kmax = other > kmax ? other : kmax;
     }
     if ((threadIdx.x & 31) == 0) {
         ws[threadIdx.x >> 5][0] = cand;
         ws[threadIdx.x >> 5][1] = pos;
+        wmax[threadIdx.x >> 5] = kmax;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         int c = 0, p = 0;
+        unsigned long long mx = 0;
         for (int w = 0; w < KEY_THREADS / 32; ++w) {
             c += ws[w][0];
             p += ws[w][1];
+            mx = wmax[w] > mx ? wmax[w] : mx;
         }
         if (c) atomicAdd(&st->nc, (unsigned long long)c);
         if (p) atomicAdd(&st->npos, (unsigned long long)p);
+        if (mx) atomicMax(&st->maxkey, mx);
     }
 }
 
-// Histogram of digit `pass` over the keys that match the prefix fixed so far.
-__global__ void __launch_bounds__(HIST_THREADS) radix_hist_kernel(const long long *__restrict__ keys, long long ng,
-                                                                  int pass, const SelState *st,
+// Digit of pass `pass`: 11-bit digits from the top bit of the largest key
+// down; the last one may be narrower.  Returns false if the pass is unused.
+__device__ __forceinline__ bool digit_of_pass(const SelState *st, int pass, int *shift, int *width)
+{
+    const unsigned long long mx = st->maxkey;
+    if (!mx) return false;
+    const int top = 64 - __clzll((long long)mx);  // bits in the largest key
+    int sh = top - 11 * (pass + 1), w = 11;
+    if (sh < 0) {
+        w += sh;
+        sh = 0;
+    }
+    if (w <= 0) return false;
+    *shift = sh;
+    *width = w;
+    return true;
+}
+
+// One radix pass: histogram of this pass's digit over the keys that match
+// the digits fixed so far; the CTA that finishes last then finds the bucket
+// holding the kth largest key and fixes its digit (the counts of the other
+// CTAs are visible to it through the arrival counter).
+__global__ void __launch_bounds__(HIST_THREADS) radix_pass_kernel(const long long *__restrict__ keys, long long ng,
+                                                                  int pass, double frac, SelState *st,
                                                                   unsigned int *__restrict__ hist)
 {
     __shared__ unsigned int h[HIST_BINS];
+    __shared__ long long wsum[HIST_THREADS / 32];
+    __shared__ long long s_kth;
+    __shared__ int s_last;
     if (st->done) return;
+    int sh, w;
+    if (!digit_of_pass(st, pass, &sh, &w)) return;
     for (int i = threadIdx.x; i < HIST_BINS; i += blockDim.x) h[i] = 0;
     __syncthreads();
-    const int sh = c_shift[pass], w = c_width[pass];
     const long long hi = st->prefix >> (sh + w);
     const long long dmask = (1ll << w) - 1;
     for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += (long long)gridDim.x * blockDim.x) {
         const long long k = keys[g];
-        if (k > 0 && (k >> (sh + w)) == hi) atomicAdd(&h[(k >> sh) & dmask], 1u);
+        if (k > 0 && (k >> (sh + w)) == hi) {
+            const unsigned bin = (unsigned)((k >> sh) & dmask);
+            // lanes of a warp with the same bin add once
+            const unsigned peers = __match_any_sync(__activemask(), bin);
+            if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[bin], (unsigned)__popc(peers));
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < HIST_BINS; i += blockDim.x)
         if (h[i]) atomicAdd(&hist[pass * HIST_BINS + i], h[i]);
-}
-
-// Pick the bucket holding the kth largest key; fix its digit.
-__global__ void __launch_bounds__(PICK_THREADS) radix_pick_kernel(int pass, double frac, SelState *st,
-                                                                  const unsigned int *__restrict__ hist)
-{
-    __shared__ long long wsum[PICK_THREADS / 32];
-    __shared__ long long s_kth;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&st->arrived[pass], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // ---- the last CTA picks the bucket --------------------------------------
     if (threadIdx.x == 0) {
         if (pass == 0) {
             // n_sel = floor(0.5 + N_c * F_s), capped at the keys > 0 (Sec. 4.1)
@@ -154,44 +195,41 @@ __global__ void __launch_bounds__(PICK_THREADS) radix_pick_kernel(int pass, doub
     __syncthreads();
     if (st->done) return;
     const long long kth = s_kth;
-    const int w = c_width[pass], nb = 1 << w;
-    // thread t owns reversed bins r = 2t, 2t+1 (bin b = nb-1-r): inclusive
-    // scan over r gives the number of keys in bins >= b.
+    const int nb = 1 << w;
+    constexpr int PER = HIST_BINS / HIST_THREADS;  // bins per thread
+    // thread t owns reversed bins r = PER*t .. PER*t+PER-1 (bin b = nb-1-r);
+    // an inclusive scan over r counts the keys in bins >= b
     const int t = threadIdx.x;
-    long long c0 = 0, c1 = 0;
-    int b0 = nb - 1 - 2 * t, b1 = nb - 2 - 2 * t;
-    if (b0 >= 0) c0 = hist[pass * HIST_BINS + b0];
-    if (b1 >= 0) c1 = hist[pass * HIST_BINS + b1];
-    long long v = c0 + c1, incl = v;
+    long long c[PER], v = 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int bin = nb - 1 - (PER * t + q);
+        c[q] = bin >= 0 ? (long long)hist[pass * HIST_BINS + bin] : 0;
+        v += c[q];
+    }
+    long long incl = v;
     const int lane = t & 31, wp = t >> 5;
     for (int o = 1; o < 32; o <<= 1) {
-        long long n = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += n;
+        const long long n2 = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += n2;
     }
     if (lane == 31) wsum[wp] = incl;
     __syncthreads();
-    long long before = 0;
-    for (int i = 0; i < wp; ++i) before += wsum[i];
-    const long long excl = before + incl - v;  // keys in bins > b0
-    const long long ge0 = excl + c0, ge1 = ge0 + c1;
-    int pick = -1;
-    long long above = 0;
-    if (b0 >= 0 && excl < kth && ge0 >= kth) {
-        pick = b0;
-        above = excl;
-    } else if (b1 >= 0 && ge0 < kth && ge1 >= kth) {
-        pick = b1;
-        above = ge0;
-    }
-    if (pick >= 0) {
-        const int sh = c_shift[pass];
-        const long long pre = st->prefix | ((long long)pick << sh);
-        st->prefix = pre;
-        st->kth = kth - above;
-        if (pass == NPASS - 1) {
-            st->thresh = pre;
-            st->need_ties = kth - above;
+    long long above = incl - v;  // keys in bins above this thread's first bin
+    for (int i = 0; i < wp; ++i) above += wsum[i];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int bin = nb - 1 - (PER * t + q);
+        if (bin >= 0 && above < kth && above + c[q] >= kth) {
+            const long long pre = st->prefix | ((long long)bin << sh);
+            st->prefix = pre;
+            st->kth = kth - above;
+            if (sh == 0) {
+                st->thresh = pre;
+                st->need_ties = kth - above;
+            }
         }
+        above += c[q];
     }
 }
 
@@ -215,11 +253,14 @@ __device__ __forceinline__ unsigned long long block_excl_scan_u64(unsigned long 
     return before + incl - v;
 }
 
-// Per-chunk counts of keys > K* (high word) and == K* (low word).
+// Per-chunk counts of keys > K* (high word) and == K* (low word); the CTA
+// that finishes last turns them into exclusive prefix offsets.
 __global__ void __launch_bounds__(CMP_THREADS) compact_count_kernel(const long long *__restrict__ keys, long long ng,
-                                                                    const SelState *st,
-                                                                    unsigned long long *__restrict__ cnt)
+                                                                    SelState *st, unsigned long long *__restrict__ cnt,
+                                                                    int nchunks)
 {
+    __shared__ int s_last;
+    __shared__ unsigned long long carry;
     const long long th = st->thresh;
     const long long base = (long long)blockIdx.x * CMP_CHUNK + (long long)threadIdx.x * CMP_ITEMS;
     unsigned long long v = 0;
@@ -235,23 +276,23 @@ __global__ void __launch_bounds__(CMP_THREADS) compact_count_kernel(const long l
     unsigned long long tot;
     block_excl_scan_u64(v, &tot);
     if (threadIdx.x == 0) cnt[blockIdx.x] = tot;
-}
-
-// Exclusive scan of the per-chunk counts (one CTA, any number of chunks).
-__global__ void __launch_bounds__(CMP_THREADS) compact_scan_kernel(unsigned long long *cnt, int nchunks)
-{
-    __shared__ unsigned long long carry;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&st->arrived[NPASS], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     for (int b = 0; b < nchunks; b += CMP_THREADS) {
         const int i = b + threadIdx.x;
-        const unsigned long long v = i < nchunks ? cnt[i] : 0ull;
-        unsigned long long tot;
-        const unsigned long long ex = block_excl_scan_u64(v, &tot);
-        const unsigned long long c = carry;
-        if (i < nchunks) cnt[i] = c + ex;
+        const unsigned long long x = i < nchunks ? cnt[i] : 0ull;
+        unsigned long long t2;
+        const unsigned long long ex = block_excl_scan_u64(x, &t2);
+        const unsigned long long c0 = carry;
+        if (i < nchunks) cnt[i] = c0 + ex;
         __syncthreads();
-        if (threadIdx.x == 0) carry = c + tot;
+        if (threadIdx.x == 0) carry = c0 + t2;
         __syncthreads();
     }
 }
@@ -343,27 +384,30 @@ nrr_status enqueue_select(const uint16_t *preop, const uint8_t *mask, nrr_dims d
     SelState *st = (SelState *)(ws + p.off_state);
     unsigned long long *cnt = (unsigned long long *)(ws + p.off_cnt);
     NRR_CUDA_TRY(cudaMemsetAsync(ws + p.off_hist, 0, p.off_cnt - p.off_hist, s));
-    switch (block) {
-    case 3: launch_keys<3>(preop, mask, d, stride, p.gx, p.gy, p.ng, keys, st, s); break;
-    case 5: launch_keys<5>(preop, mask, d, stride, p.gx, p.gy, p.ng, keys, st, s); break;
-    case 7: launch_keys<7>(preop, mask, d, stride, p.gx, p.gy, p.ng, keys, st, s); break;
-    case 9: launch_keys<9>(preop, mask, d, stride, p.gx, p.gy, p.ng, keys, st, s); break;
-    default: launch_keys<11>(preop, mask, d, stride, p.gx, p.gy, p.ng, keys, st, s); break;
+    if (keys_box_supported(block, stride)) {
+        nrr_status ks = launch_keys_box(preop, mask, d, block, stride, p.gx, p.gy, p.gz, keys, &st->nc, &st->npos,
+                                        &st->maxkey, s);
+        if (ks != NRR_OK) return ks;
+    } else {
+        switch (block) {
+        case 3: launch_keys<3>(preop, mask, d, stride, p.gx, p.gy, p.ng, keys, st, s); break;
+        case 5: launch_keys<5>(preop, mask, d, stride, p.gx, p.gy, p.ng, keys, st, s); break;
+        case 7: launch_keys<7>(preop, mask, d, stride, p.gx, p.gy, p.ng, keys, st, s); break;
+        case 9: launch_keys<9>(preop, mask, d, stride, p.gx, p.gy, p.ng, keys, st, s); break;
+        default: launch_keys<11>(preop, mask, d, stride, p.gx, p.gy, p.ng, keys, st, s); break;
+        }
     }
     long long hgrid = (p.ng + HIST_THREADS * 8 - 1) / (HIST_THREADS * 8);
     if (hgrid > 4 * sm_count()) hgrid = 4 * sm_count();
     if (hgrid < 1) hgrid = 1;
-    for (int pass = 0; pass < NPASS; ++pass) {
-        radix_hist_kernel<<<(unsigned)hgrid, HIST_THREADS, 0, s>>>(keys, p.ng, pass, st, hist);
-        radix_pick_kernel<<<1, PICK_THREADS, 0, s>>>(pass, frac, st, hist);
-    }
-    compact_count_kernel<<<p.nchunks, CMP_THREADS, 0, s>>>(keys, p.ng, st, cnt);
-    compact_scan_kernel<<<1, CMP_THREADS, 0, s>>>(cnt, p.nchunks);
+    for (int pass = 0; pass < NPASS; ++pass)
+        radix_pass_kernel<<<(unsigned)hgrid, HIST_THREADS, 0, s>>>(keys, p.ng, pass, frac, st, hist);
+    compact_count_kernel<<<p.nchunks, CMP_THREADS, 0, s>>>(keys, p.ng, st, cnt, p.nchunks);
     compact_write_kernel<<<p.nchunks, CMP_THREADS, 0, s>>>(keys, p.ng, p.gx, p.gy, stride, st, cnt, centers,
                                                           max_blocks, d_n_selected);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "selection kernel launch");
-    count_launches(2 + 2 * NPASS + 2);
+    count_launches(1 + NPASS + 2);
     return NRR_OK;
 }
 
