@@ -92,11 +92,8 @@ struct MatchScratch {
     int jstart[MATCH_MAX_JOBS + 1];  // first work item of each job
     // per-warp partial statistics of the floating block
     double pd1[MATCH_MAX_WARPS], pd2[MATCH_MAX_WARPS];
-    long long pi1[MATCH_MAX_WARPS];
-    unsigned long long pi2[MATCH_MAX_WARPS];
     float plo[MATCH_MAX_WARPS], phi[MATCH_MAX_WARPS];
-    // per-warp partial sums when few survivors are split across warps
-    long long re[MATCH_MAX_WARPS], rs1[MATCH_MAX_WARPS], rs2[MATCH_MAX_WARPS];
+    // float32: per-warp partial sums when few survivors are split across warps
     double rf[MATCH_MAX_WARPS][3];
     float rlo[MATCH_MAX_WARPS], rhi[MATCH_MAX_WARPS];
 };
@@ -285,17 +282,10 @@ __device__ __forceinline__ void search_line(const T *row0, int zstride, const fl
     }
 }
 
-// Register budget per thread: 96 for blocks up to 7^3 with up to 11
-// x-shifts (5 search CTAs per SM are limited by shared memory there anyway),
-// 128 above.
-template <int B, int P>
-struct MatchRegs {
-    static constexpr int value = (P <= 11 && B <= 7) ? 96 : 128;
-};
-
+// The kernel body; the two __global__ entries below differ only in their
+// register budget.  `a`, `tmapJ` and `tmapI` live in kernel-parameter space.
 template <typename T, int B, int P>
-__global__ void __maxnreg__((MatchRegs<B, P>::value)) match_kernel(
-    const MatchParams a, const __grid_constant__ CUtensorMap tmapJ, const __grid_constant__ CUtensorMap tmapI)
+__device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorMap *tmapJ, const CUtensorMap *tmapI)
 {
     constexpr bool F32 = std::is_same<T, float>::value;
     constexpr int H = (B - 1) / 2;
@@ -374,8 +364,8 @@ __global__ void __maxnreg__((MatchRegs<B, P>::value)) match_kernel(
         const int x0 = cx - H - RX, xt = cx - H;
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(bar + b, tx_bytes);
-        tma_load_3d(smem + L.u[b], &tmapJ, bar + b, x0 & ~(ALIGN - 1), cy - H - ry, cz - H - rz);
-        tma_load_3d(smem + L.ut[b], &tmapI, bar + b, xt & ~(ALIGN - 1), cy - H, cz - H);
+        tma_load_3d(smem + L.u[b], tmapJ, bar + b, x0 & ~(ALIGN - 1), cy - H - ry, cz - H - rz);
+        tma_load_3d(smem + L.ut[b], tmapI, bar + b, xt & ~(ALIGN - 1), cy - H, cz - H);
     };
 
     uint32_t phase[2] = {0u, 0u};
@@ -421,8 +411,9 @@ __global__ void __maxnreg__((MatchRegs<B, P>::value)) match_kernel(
         const int nb = next_inside(blk + gridDim.x);
         if (nb < n && tid == 0) issue(nb, b ^ 1);  // buffer b^1 was released by the previous block's last barrier
 
-        // ---- floating block statistics: every warp sums a share, then every
-        // thread combines the per-warp partials (one pass, one barrier) ----
+        // ---- floating block statistics.  float32: every warp sums a share in
+        // FP64 and every thread combines the per-warp partials; uint16: warp 0
+        // alone (exact integer sums, cheap) writes the block constants ----
         {
             constexpr int IPT = (N + 63) / 64;  // values per thread at 64+ threads
             if constexpr (F32) {
@@ -456,36 +447,46 @@ __global__ void __maxnreg__((MatchRegs<B, P>::value)) match_kernel(
                     sc->plo[warp] = lo;
                     sc->phi[warp] = hi;
                 }
-            } else {
-                unsigned int s1 = 0;
+            } else if (warp == 0) {  // uint16: one warp, exact integer sums
+                constexpr int KPL = (N + 31) / 32;
+                constexpr int CH = KPL < 6 ? KPL : 6;
+                long long s1 = 0;
                 unsigned long long s2 = 0;
-                for (int k0 = tid; k0 < N; k0 += IPT * nthr) {
-                    uint32_t vals[IPT];
+#pragma unroll 1
+                for (int i0 = 0; i0 < KPL; i0 += CH) {
+                    uint32_t vals[CH];
 #pragma unroll
-                    for (int q = 0; q < IPT; ++q) {
-                        const int k = k0 + q * nthr;
+                    for (int q = 0; q < CH; ++q) {
+                        const int k = lane + 32 * (i0 + q);
                         const int kzy = k / B, kx = k - kzy * B;
                         vals[q] = k < N ? (uint32_t)Ut[kzy * BTX + xot + kx] : 0u;
                     }
 #pragma unroll
-                    for (int q = 0; q < IPT; ++q) {
+                    for (int q = 0; q < CH; ++q) {
                         s1 += vals[q];
-                        s2 += (unsigned long long)vals[q] * vals[q];
+                        s2 += (unsigned long long)(vals[q] * vals[q]);
                     }
                 }
-                const long long s1w = warp_sum((long long)s1);
+                s1 = warp_sum(s1);
                 s2 = warp_sum(s2);
                 if (lane == 0) {
-                    sc->pi1[warp] = s1w;
-                    sc->pi2[warp] = s2;
+                    BlockConst &c = sc->bc;
+                    const long long vI = (long long)N * (long long)s2 - s1 * s1;
+                    const long long m = (long long)((2u * (uint32_t)s1 + (uint32_t)N) / (2u * (uint32_t)N));  // nearest integer to the mean
+                    const long long qt = (long long)s2 - 2 * m * s1 + (long long)N * m * m;  // sum (I-m)^2, exact
+                    c.vI = vI;
+                    c.m = (int)m;
+                    c.rr = (long long)N * m - s1;
+                    c.fvI = (float)vI;
+                    c.kq = (float)((double)N * GAMMA_N * sqrt((double)qt) * (1.0 + 1e-6));
                 }
             }
         }
         __syncthreads();
-        // Every thread needs only the template shift and the flat test, both
-        // cheap and computed identically everywhere; thread 0 alone derives
-        // the FP64 block constants (FP64 units are scarce on this part), read
-        // by all threads from shared memory after the next barrier.
+        // float32: every thread needs only the template shift and the flat
+        // test, both cheap and computed identically everywhere; thread 0
+        // alone derives the FP64 block constants (FP64 issue is scarce on
+        // this part), read by all threads after the next barrier.
         float tsh;
         bool flat;
         if constexpr (F32) {
@@ -520,26 +521,8 @@ __global__ void __maxnreg__((MatchRegs<B, P>::value)) match_kernel(
                                (1.0 + 1e-6));
             }
         } else {
-            long long s1 = 0;
-            unsigned long long s2 = 0;
-            for (int w = 0; w < nwarp; ++w) {
-                s1 += sc->pi1[w];
-                s2 += sc->pi2[w];
-            }
-            const long long vI = (long long)N * (long long)s2 - s1 * s1;
-            const uint32_t m = (2u * (uint32_t)s1 + (uint32_t)N) / (2u * (uint32_t)N);  // nearest integer to the mean
-            tsh = 8388608.0f + (float)m;
-            flat = vI == 0;
-            if (tid == 0 && !flat) {
-                const long long mm = (long long)m;
-                const long long qt = (long long)s2 - 2 * mm * s1 + (long long)N * mm * mm;  // sum (I-m)^2, exact
-                BlockConst &c = sc->bc;
-                c.vI = vI;
-                c.m = (int)m;
-                c.rr = (long long)N * mm - s1;
-                c.fvI = (float)vI;
-                c.kq = (float)((double)N * GAMMA_N * sqrt((double)qt) * (1.0 + 1e-6));
-            }
+            flat = sc->bc.vI == 0;
+            tsh = 8388608.0f + (float)sc->bc.m;
         }
         if (flat) {  // flat floating block: NCC undefined for every shift
             if (tid == 0) write_result(J, bi, Cand{0.0, 0, 0, 0}, P, py, RX, ry, rz);
@@ -583,7 +566,7 @@ __global__ void __maxnreg__((MatchRegs<B, P>::value)) match_kernel(
             }
         }
         __syncthreads();
-        const BlockConst &bc = sc->bc;
+        const BlockConst bc = sc->bc;
 
         // ---- search: FP32 accumulation of A(d) over the whole window ------
         float ub[P];
@@ -712,10 +695,10 @@ __global__ void __maxnreg__((MatchRegs<B, P>::value)) match_kernel(
         const int nsurv = sc->nsurv;
 
         // ---- exact rescoring of the survivors ---------------------------------
-        // With at least as many survivors as warps, each warp rescores whole
-        // survivors; with fewer, each survivor's terms are split over
-        // nwarp/nsurv warps whose partial sums thread 0 adds up.
-        const int parts = nsurv >= nwarp ? 1 : (nsurv > 0 ? nwarp / nsurv : 1);
+        // A warp rescores a whole survivor.  float32 (FP64 sums, slow on this
+        // part): with fewer survivors than warps, each survivor's terms are
+        // split over nwarp/nsurv warps whose partial sums thread 0 adds up.
+        const int parts = (!F32 || nsurv >= nwarp) ? 1 : (nsurv > 0 ? nwarp / nsurv : 1);
         constexpr int KS1 = N;  // terms of a whole survivor
         Cand wb{0.0, 0, 0, 0};
         const int ntask = parts == 1 ? nsurv : nsurv * parts;
@@ -728,24 +711,25 @@ __global__ void __maxnreg__((MatchRegs<B, P>::value)) match_kernel(
             const int dx = sxi - RX, dy = syi - ry, dz = szi - rz;
             const size_t idx = ((size_t)(cz + dz) * ny + (cy + dy)) * nx + (cx + dx);
             Cand c{0.0, dx * dx + dy * dy + dz * dz, code, 0};
-            if constexpr (!F32) {
+            if constexpr (!F32) {  // one warp per survivor: parts == 1
                 long long s1 = 0, s2 = 0;
-                if (lane == 0 && part == 0) {  // issued first, consumed after the warp sum
+                if (lane == 0) {  // issued first, consumed after the warp sum
                     s1 = reinterpret_cast<const int32_t *>(a.s1)[idx];
                     s2 = reinterpret_cast<const long long *>(a.s2)[idx];
                 }
-                constexpr int CH = 4;
+                constexpr int KPL = (N + 31) / 32;
+                constexpr int CH = KPL < 6 ? KPL : 6;
                 long long e = 0;
 #pragma unroll 1
-                for (int k0 = kbeg + lane; k0 < kend; k0 += 32 * CH) {
+                for (int i0 = 0; i0 < KPL; i0 += CH) {
                     int tv[CH], jv[CH];
 #pragma unroll
                     for (int q = 0; q < CH; ++q) {
-                        const int k = k0 + 32 * q;
+                        const int k = lane + 32 * (i0 + q);
                         const int kz = k / (B * B), rem = k - kz * B * B, ky = rem / B, kx = rem - ky * B;
                         tv[q] = 0;
                         jv[q] = 0;
-                        if (k < kend) {
+                        if (k < N) {
                             tv[q] = (int)Tm[(kz * B + ky) * PT + kx];
                             jv[q] = (int)U[((szi + kz) * wyp + (syi + ky)) * BX + xo + sxi + kx] - c_i;
                         }
@@ -755,20 +739,12 @@ __global__ void __maxnreg__((MatchRegs<B, P>::value)) match_kernel(
                 }
                 e = warp_sum(e);
                 if (lane == 0) {
-                    if (parts == 1) {
-                        const long long vJ = (long long)N * s2 - s1 * s1;
-                        const long long num = (long long)N * e + bc.rr * (s1 - (long long)N * c_i);
-                        if (vJ > 0) {
-                            const double den = __dsqrt_rn(__dmul_rn((double)bc.vI, (double)vJ));
-                            c.s = __ddiv_rn((double)num, den);
-                            c.ok = 1;
-                        }
-                    } else {
-                        sc->re[task] = e;
-                        if (part == 0) {
-                            sc->rs1[task] = s1;
-                            sc->rs2[task] = s2;
-                        }
+                    const long long vJ = (long long)N * s2 - s1 * s1;
+                    const long long num = (long long)N * e + bc.rr * (s1 - (long long)N * c_i);
+                    if (vJ > 0) {
+                        const double den = __dsqrt_rn(__dmul_rn((double)bc.vI, (double)vJ));
+                        c.s = __ddiv_rn((double)num, den);
+                        c.ok = 1;
                     }
                 }
             } else {
@@ -832,18 +808,7 @@ __global__ void __maxnreg__((MatchRegs<B, P>::value)) match_kernel(
                     const int sxi = code % P, syi = (code / P) % py, szi = code / (P * py);
                     const int dx = sxi - RX, dy = syi - ry, dz = szi - rz;
                     Cand c{0.0, dx * dx + dy * dy + dz * dz, code, 0};
-                    if constexpr (!F32) {
-                        long long e = 0;
-                        for (int q = 0; q < parts; ++q) e += sc->re[si * parts + q];
-                        const long long s1 = sc->rs1[si * parts], s2 = sc->rs2[si * parts];
-                        const long long vJ = (long long)N * s2 - s1 * s1;
-                        const long long num = (long long)N * e + bc.rr * (s1 - (long long)N * c_i);
-                        if (vJ > 0) {
-                            const double den = __dsqrt_rn(__dmul_rn((double)bc.vI, (double)vJ));
-                            c.s = __ddiv_rn((double)num, den);
-                            c.ok = 1;
-                        }
-                    } else {
+                    if constexpr (F32) {
                         double sij = 0.0, sj = 0.0, sjj = 0.0;
                         float lo = INFINITY, hi = -INFINITY;
                         for (int q = 0; q < parts; ++q) {
@@ -875,6 +840,43 @@ __global__ void __maxnreg__((MatchRegs<B, P>::value)) match_kernel(
 }
 
 // Host side: launch one (element type, block size, x-shift count) variant.
+// Register budgets.  uint16: 96 per thread for blocks up to 7^3 with up to
+// 11 x-shifts (5 CTAs per SM are limited by shared memory there anyway), 128
+// above.  float32: the same limits expressed as resident CTAs per SM.
+template <int B, int P>
+struct MatchRegs {
+    static constexpr int value = (P <= 11 && B <= 7) ? 96 : 128;
+};
+template <int B, int P>
+struct MatchMinBlocks {
+    static constexpr int value = (P <= 11 && B <= 7) ? 3 : 2;
+};
+
+template <int B, int P>
+__global__ void __maxnreg__((MatchRegs<B, P>::value))
+    match_kernel_u16(const __grid_constant__ MatchParams a, const __grid_constant__ CUtensorMap tmapJ,
+                     const __grid_constant__ CUtensorMap tmapI)
+{
+    match_body<uint16_t, B, P>(a, &tmapJ, &tmapI);
+}
+
+template <int B, int P>
+__global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value)
+    match_kernel_f32(const __grid_constant__ MatchParams a, const __grid_constant__ CUtensorMap tmapJ,
+                     const __grid_constant__ CUtensorMap tmapI)
+{
+    match_body<float, B, P>(a, &tmapJ, &tmapI);
+}
+
+template <typename T, int B, int P>
+constexpr auto match_kernel_ptr()
+{
+    if constexpr (std::is_same<T, float>::value)
+        return match_kernel_f32<B, P>;
+    else
+        return match_kernel_u16<B, P>;
+}
+
 template <typename T, int B, int P>
 nrr_status launch_match_variant(const MatchLaunch &m, cudaStream_t stream)
 {
@@ -894,7 +896,7 @@ nrr_status launch_match_variant(const MatchLaunch &m, cudaStream_t stream)
     st = encode_volume_map(&mapI, m.preop, m.dtype, m.dims, BTX, B, B);
     if (st != NRR_OK) return st;
 
-    auto kern = match_kernel<T, B, P>;
+    auto kern = match_kernel_ptr<T, B, P>();
     static int smem_set = 0;  // largest dynamic shared memory opted in so far
     if (L.total > smem_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
@@ -943,7 +945,7 @@ nrr_status occupancy_variant(const MatchLaunch &m, int *occ)
     const int wyp = match_wyp(B + 2 * ry, py);
     const MatchLayout L = match_layout((int)sizeof(T), B, P, match_bx<T, B, P>(), round_up_c(B + ALIGN - 1, ALIGN),
                                        wyp, B + 2 * rz, py, pz);
-    auto kern = match_kernel<T, B, P>;
+    auto kern = match_kernel_ptr<T, B, P>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
