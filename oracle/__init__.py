@@ -51,6 +51,8 @@ def lib():
         L.oracle_n_select.argtypes = [i64, dbl]
         L.oracle_select_blocks.restype = i64
         L.oracle_select_blocks.argtypes = [P, P, i32, i32, i32, i32, i32, dbl, P, i64, P]
+        L.oracle_select_blocks_spaced.restype = i64
+        L.oracle_select_blocks_spaced.argtypes = [P, P, i32, i32, i32, i32, i32, dbl, i32, P, i64, P]
         for name in ("oracle_ncc_u16", "oracle_pearson_u16", "oracle_pearson_f32"):
             f = getattr(L, name)
             f.restype = i32
@@ -110,6 +112,21 @@ def select_blocks(preop, mask, b, stride, frac):
     nc = C.c_int64(0)
     n = lib().oracle_select_blocks(_p(preop), _p(mask), nx, ny, nz, b, stride, float(frac), _p(out), cap,
                                    C.byref(nc))
+    return out[:n].copy(), int(nc.value)
+
+
+def select_blocks_spaced(preop, mask, b, stride, frac, conn):
+    """Selection with a connectivity pattern conn in {0, 6, 18, 26} (Sec.
+    4.1).  Returns (centers int32[n][3] in raster order, n_candidates)."""
+    preop = np.ascontiguousarray(preop, dtype=np.uint16)
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    nx, ny, nz = _dims(preop)
+    ng = (-(-nx // stride)) * (-(-ny // stride)) * (-(-nz // stride))
+    cap = max(1, ng)
+    out = np.empty((cap, 3), dtype=np.int32)
+    nc = C.c_int64(0)
+    n = lib().oracle_select_blocks_spaced(_p(preop), _p(mask), nx, ny, nz, b, stride, float(frac), int(conn),
+                                          _p(out), cap, C.byref(nc))
     return out[:n].copy(), int(nc.value)
 
 

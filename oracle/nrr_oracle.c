@@ -37,6 +37,10 @@
  *     candidates (Sec. 4.1), capped at the number of candidates with a
  *     nonzero key.  Order is key descending, raster index ascending; the
  *     selected centres are returned in raster order.
+ *   - Connectivity pattern (Sec. 4.1, optional): greedy in selection order;
+ *     a candidate is skipped if an already accepted candidate is its 6-, 18-
+ *     or 26-neighbour on the candidate grid (offsets in {-1,0,1}^3 of L1
+ *     norm at most 1, 2 or 3).
  *
  * Layout: volumes are C-contiguous [nz][ny][nx]; centres and displacements
  * are int32 triples (x, y, z).
@@ -177,6 +181,67 @@ int64_t oracle_select_blocks(const uint16_t *preop, const uint8_t *mask, int nx,
         centers[3 * s + 2] = (int32_t)(k * stride);
     }
     if (n_candidates) *n_candidates = nc;
+    free(pos);
+    free(keys);
+    return nsel;
+}
+
+/* Variance-based selection with a connectivity pattern (Sec. 4.1: blocks
+ * that are too close are not both selected; the "face", "edge" and "vertex"
+ * simplex patterns mean 6-, 18- and 26-connectivity).  Reading: the
+ * candidates are visited in selection order (key descending, raster index
+ * ascending; flat blocks never); a candidate is accepted unless a candidate
+ * accepted before it is its neighbour on the candidate grid, i.e. its grid
+ * offset (di,dj,dk) lies in {-1,0,1}^3 with |di|+|dj|+|dk| at most 1 (6),
+ * 2 (18) or 3 (26); the walk stops after floor(0.5 + N_c * F_s) accepted.
+ * conn = 0 is selection without a pattern.  Writes up to `cap` centres in
+ * raster order; returns the number selected. */
+int64_t oracle_select_blocks_spaced(const uint16_t *preop, const uint8_t *mask, int nx, int ny, int nz,
+                                    int b, int stride, double frac, int conn, int32_t *centers, int64_t cap,
+                                    int64_t *n_candidates)
+{
+    int order = conn == 6 ? 1 : conn == 18 ? 2 : conn == 26 ? 3 : 0;
+    int64_t gx = (nx + stride - 1) / stride, gy = (ny + stride - 1) / stride,
+            gz = (nz + stride - 1) / stride, ng = gx * gy * gz;
+    int64_t *keys = (int64_t *)malloc(sizeof(int64_t) * (size_t)(ng > 0 ? ng : 1));
+    int64_t nc = oracle_grid_keys(preop, mask, nx, ny, nz, b, stride, keys);
+    keyed *pos = (keyed *)malloc(sizeof(keyed) * (size_t)(ng > 0 ? ng : 1));
+    unsigned char *taken = (unsigned char *)calloc((size_t)(ng > 0 ? ng : 1), 1);
+    int64_t npos = 0;
+    for (int64_t g = 0; g < ng; ++g)
+        if (keys[g] > 0) {
+            pos[npos].key = keys[g];
+            pos[npos].idx = g;
+            ++npos;
+        }
+    qsort(pos, (size_t)npos, sizeof(keyed), by_key_desc_idx_asc);
+    int64_t want = oracle_n_select(nc, frac), nsel = 0;
+    for (int64_t r = 0; r < npos && nsel < want; ++r) {
+        int64_t g = pos[r].idx, i = g % gx, j = (g / gx) % gy, k = g / (gx * gy);
+        int blocked = 0;
+        for (int dk = -1; dk <= 1 && !blocked; ++dk)
+            for (int dj = -1; dj <= 1 && !blocked; ++dj)
+                for (int di = -1; di <= 1 && !blocked; ++di) {
+                    int l1 = abs(di) + abs(dj) + abs(dk);
+                    if (l1 == 0 || l1 > order) continue;
+                    int64_t ii = i + di, jj = j + dj, kk = k + dk;
+                    if (ii < 0 || jj < 0 || kk < 0 || ii >= gx || jj >= gy || kk >= gz) continue;
+                    if (taken[(kk * gy + jj) * gx + ii]) blocked = 1;
+                }
+        if (!blocked) {
+            taken[g] = 1;
+            pos[nsel++] = pos[r];  /* accepted ones move to the front (r >= nsel) */
+        }
+    }
+    qsort(pos, (size_t)nsel, sizeof(keyed), by_idx_asc);
+    for (int64_t s = 0; s < nsel && s < cap; ++s) {
+        int64_t g = pos[s].idx, i = g % gx, j = (g / gx) % gy, k = g / (gx * gy);
+        centers[3 * s + 0] = (int32_t)(i * stride);
+        centers[3 * s + 1] = (int32_t)(j * stride);
+        centers[3 * s + 2] = (int32_t)(k * stride);
+    }
+    if (n_candidates) *n_candidates = nc;
+    free(taken);
     free(pos);
     free(keys);
     return nsel;

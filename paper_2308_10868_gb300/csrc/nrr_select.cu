@@ -31,6 +31,7 @@ namespace {
 constexpr int KEY_THREADS = 256;
 constexpr int HIST_BINS = 2048;
 constexpr int HIST_THREADS = 512;
+constexpr int HIST_KPT = 8;  // keys per thread per sweep of a histogram pass
 constexpr int CMP_THREADS = 1024;
 constexpr int CMP_ITEMS = 4;
 constexpr int CMP_CHUNK = CMP_THREADS * CMP_ITEMS;
@@ -156,13 +157,24 @@ __global__ void __launch_bounds__(HIST_THREADS) radix_pass_kernel(const long lon
     __syncthreads();
     const long long hi = st->prefix >> (sh + w);
     const long long dmask = (1ll << w) - 1;
-    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += (long long)gridDim.x * blockDim.x) {
-        const long long k = keys[g];
-        if (k > 0 && (k >> (sh + w)) == hi) {
-            const unsigned bin = (unsigned)((k >> sh) & dmask);
-            // lanes of a warp with the same bin add once
-            const unsigned peers = __match_any_sync(__activemask(), bin);
-            if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[bin], (unsigned)__popc(peers));
+    // HIST_KPT keys per thread per sweep, all loads issued before any is used
+    const long long sweep = (long long)gridDim.x * blockDim.x * HIST_KPT;
+    for (long long g0 = (long long)blockIdx.x * blockDim.x * HIST_KPT + threadIdx.x; g0 < ng; g0 += sweep) {
+        long long kv[HIST_KPT];
+#pragma unroll
+        for (int q = 0; q < HIST_KPT; ++q) {
+            const long long g = g0 + (long long)q * blockDim.x;
+            kv[q] = g < ng ? keys[g] : -1;
+        }
+#pragma unroll
+        for (int q = 0; q < HIST_KPT; ++q) {
+            const long long k = kv[q];
+            if (k > 0 && (k >> (sh + w)) == hi) {
+                const unsigned bin = (unsigned)((k >> sh) & dmask);
+                // lanes of a warp with the same bin add once
+                const unsigned peers = __match_any_sync(__activemask(), bin);
+                if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[bin], (unsigned)__popc(peers));
+            }
         }
     }
     __syncthreads();
@@ -397,7 +409,7 @@ nrr_status enqueue_select(const uint16_t *preop, const uint8_t *mask, nrr_dims d
         default: launch_keys<11>(preop, mask, d, stride, p.gx, p.gy, p.ng, keys, st, s); break;
         }
     }
-    long long hgrid = (p.ng + HIST_THREADS * 8 - 1) / (HIST_THREADS * 8);
+    long long hgrid = (p.ng + HIST_THREADS * HIST_KPT - 1) / (HIST_THREADS * HIST_KPT);
     if (hgrid > 4 * sm_count()) hgrid = 4 * sm_count();
     if (hgrid < 1) hgrid = 1;
     for (int pass = 0; pass < NPASS; ++pass)

@@ -285,3 +285,121 @@ def test_f32_path_agrees_with_integer_path():
     ds, ns, vs = oracle.match(synth.as_f32(pre), synth.as_f32(intra), centers, 7, 2)
     assert (vs == v16).all()
     np.testing.assert_allclose(ns, n16, rtol=0, atol=1e-5)
+
+
+# ---------------------------------------------------------------------------
+# Selection with a connectivity pattern (Sec. 4.1: face / edge / vertex
+# simplex patterns = 6 / 18 / 26 connectivity; greedy in selection order)
+# ---------------------------------------------------------------------------
+_ORDER = {6: 1, 18: 2, 26: 3}
+
+
+def _phantom(dims, seed):
+    """Smooth Gaussian-blob volume (dims = (nx, ny, nz)) plus a little noise,
+    so that block variances vary smoothly with long monotone runs."""
+    rng = synth.rng_for(seed, salt=17)
+    v = synth.phantom_f64(dims, rng, n_gauss=12, sigma=(2.0, 6.0))
+    return synth.to_u16(v + rng.normal(0.0, 3.0, v.shape))
+
+
+def _pattern_offsets(conn):
+    return [o for o in itertools.product((-1, 0, 1), repeat=3) if 0 < sum(map(abs, o)) <= _ORDER[conn]]
+
+
+@pytest.mark.parametrize("b,stride,frac", [(3, 1, 0.2), (5, 2, 0.5), (3, 3, 1.0)])
+def test_spaced_selection_without_pattern_is_plain_selection(b, stride, frac):
+    pre = _phantom((26, 24, 22), seed=7)
+    mask = np.ones(pre.shape, np.uint8)
+    mask[:, :, :4] = 0
+    plain, nc = oracle.select_blocks(pre, mask, b, stride, frac)
+    spaced, nc2 = oracle.select_blocks_spaced(pre, mask, b, stride, frac, 0)
+    assert nc == nc2 and np.array_equal(plain, spaced)
+
+
+@pytest.mark.parametrize("stride", [1, 2])
+@pytest.mark.parametrize("conn", [6, 18, 26])
+def test_spaced_selection_equal_keys_gives_the_closed_form_lattice(conn, stride):
+    # I = 1000 + 300*(x mod 3): every 3^3 block holds the same multiset of
+    # values, so every candidate has the same positive key and the selection
+    # order is the raster order.  Greedy exclusion in raster order then keeps,
+    # in grid coordinates relative to the first candidate (a, a, a):
+    #   face (6):    (u+v+w) even
+    #   edge (18):   u = v = w (mod 2)
+    #   vertex (26): u, v, w all even
+    # (densities 1/2, 1/4, 1/8: the face pattern is the densest).
+    nz, ny, nx = 13, 14, 15
+    x = np.arange(nx)
+    pre = np.broadcast_to(1000 + 300 * (x % 3), (nz, ny, nx)).astype(np.uint16).copy()
+    mask = np.ones((nz, ny, nx), np.uint8)
+    got, nc = oracle.select_blocks_spaced(pre, mask, 3, stride, 1.0, conn)
+    keys, _ = oracle.grid_keys(pre, mask, 3, stride)
+    cand = np.argwhere(keys >= 0)  # (k, j, i)
+    assert len(cand) == nc and len(np.unique(keys[keys >= 0])) == 1 and keys.max() > 0
+    a = cand.min(axis=0)
+    u, v, w = (cand - a).T
+    keep = {6: (u + v + w) % 2 == 0, 18: ((u % 2) == (v % 2)) & ((v % 2) == (w % 2)),
+            26: (u % 2 == 0) & (v % 2 == 0) & (w % 2 == 0)}[conn]
+    kji = cand[keep]
+    expect = np.stack([kji[:, 2], kji[:, 1], kji[:, 0]], axis=1) * stride
+    order = np.lexsort((expect[:, 0], expect[:, 1], expect[:, 2]))
+    assert np.array_equal(got, expect[order].astype(np.int32))
+    # a smaller fraction keeps the first n_sel lattice points in raster order
+    frac = 0.1
+    part, _ = oracle.select_blocks_spaced(pre, mask, 3, stride, frac, conn)
+    assert np.array_equal(part, expect[order][:oracle.n_select(nc, frac)].astype(np.int32))
+
+
+@pytest.mark.parametrize("conn", [6, 18, 26])
+@pytest.mark.parametrize("b,stride,frac", [(3, 1, 0.08), (3, 2, 0.3), (5, 1, 1.0), (5, 3, 0.2)])
+def test_spaced_selection_is_the_greedy_independent_set(conn, b, stride, frac):
+    # The greedy result S is characterised by: (1) no two members of S are
+    # pattern neighbours; (2) |S| = min(n_sel, size of the full greedy set);
+    # (3) every unselected candidate with a positive key that precedes the
+    # last member of S in selection order (or any, if |S| < n_sel) has a
+    # member of S among its neighbours that precedes it.  Any set with these
+    # properties equals the greedy one (a first difference contradicts (1)).
+    pre = _phantom((30, 27, 25), seed=11 + conn)
+    mask = np.zeros(pre.shape, np.uint8)
+    mask[3:-3, 2:-2, 4:-1] = 1
+    got, nc = oracle.select_blocks_spaced(pre, mask, b, stride, frac, conn)
+    keys, _ = oracle.grid_keys(pre, mask, b, stride)
+    gz, gy, gx = keys.shape
+    rank = {}
+    flat = [(int(keys[k, j, i]), (k * gy + j) * gx + i, (k, j, i)) for k, j, i in np.argwhere(keys > 0)]
+    flat.sort(key=lambda t: (-t[0], t[1]))
+    for r, (_, _, kji) in enumerate(flat):
+        rank[tuple(int(q) for q in kji)] = r
+    S = {(int(c[2]) // stride, int(c[1]) // stride, int(c[0]) // stride) for c in got}
+    assert len(S) == len(got)
+    offs = _pattern_offsets(conn)
+
+    def nbrs(p):
+        for o in offs:
+            q = (p[0] + o[2], p[1] + o[1], p[2] + o[0])
+            if q in rank:
+                yield q
+
+    for p in S:  # (1)
+        assert p in rank
+        assert not any(q in S for q in nbrs(p))
+    want = oracle.n_select(nc, frac)
+    assert len(S) <= want
+    last = max(rank[p] for p in S) if S else -1
+    for p, r in rank.items():  # (3)
+        if p in S or (len(S) == want and r > last):
+            continue
+        assert any(q in S and rank[q] < r for q in nbrs(p)), p
+    if len(S) < want:  # (2): the walk ran out of candidates, nothing is left to add
+        assert all(p in S or any(q in S for q in nbrs(p)) for p in rank)
+
+
+@pytest.mark.parametrize("conn", [6, 26])
+def test_spaced_selection_fractions_are_nested(conn):
+    pre = _phantom((28, 26, 24), seed=5)
+    mask = np.ones(pre.shape, np.uint8)
+    prev = set()
+    for frac in (0.01, 0.03, 0.07, 0.2):
+        s, _ = oracle.select_blocks_spaced(pre, mask, 3, 1, frac, conn)
+        cur = {tuple(c) for c in s.tolist()}
+        assert prev <= cur
+        prev = cur
