@@ -128,6 +128,39 @@ nrr_status nrr_select_blocks(const uint16_t *d_preop, const uint8_t *d_mask, nrr
                              int32_t *d_n_selected, int32_t *h_n_selected, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Block selection with a connectivity pattern (Sec. 4.1, "Parallel feature
+ * selection": a connectivity pattern keeps selected blocks from being too
+ * close to each other; its "face", "edge" and "vertex" simplex patterns are
+ * 6-, 18- and 26-connectivity, the face pattern giving the densest
+ * selection).
+ *
+ * Same candidates, keys, count n_sel = floor(0.5 + N_c * frac) and order
+ * (key descending, raster index ascending) as nrr_select_blocks.  The
+ * candidates are taken greedily in that order: one is skipped when a
+ * candidate taken before it is its neighbour on the candidate grid, i.e. its
+ * grid offset (di, dj, dk) lies in {-1,0,1}^3 with |di|+|dj|+|dk| at most 1
+ * (connectivity 6), 2 (18) or 3 (26); the walk stops after n_sel have been
+ * taken, or earlier when the candidates run out.  Centres are written in
+ * raster order.
+ *
+ *   connectivity  0 (no pattern: exactly nrr_select_blocks), 6, 18 or 26
+ *   other arguments as nrr_select_blocks
+ *
+ * Scratch: as nrr_select_blocks plus 5 bytes per candidate grid point, from
+ * the stream-ordered pool.  The pattern runs as one cooperative kernel (all
+ * of its CTAs resident at once) whose rounds are separated by grid-wide
+ * barriers; a barrier that waits longer than 2 s gives up and sets the
+ * device error word (nrr_device_status then returns NRR_E_TIMEOUT).  Not for
+ * use inside stream capture.
+ * Errors: NRR_E_INVALID (arguments, connectivity), NRR_E_NOMEM, NRR_E_CUDA,
+ * NRR_E_CAPACITY as nrr_select_blocks.
+ * ---------------------------------------------------------------------- */
+nrr_status nrr_select_blocks_spaced(const uint16_t *d_preop, const uint8_t *d_mask, nrr_dims dims,
+                                    int32_t block, int32_t stride, double frac, int32_t connectivity,
+                                    int32_t *d_centers, int32_t max_blocks,
+                                    int32_t *d_n_selected, int32_t *h_n_selected, void *stream);
+
+/* ------------------------------------------------------------------------
  * Block selection that allocates nothing.
  *
  * Some callers cannot allocate device memory when they call in: systems

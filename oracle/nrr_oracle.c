@@ -23,7 +23,7 @@
  *     block (Sec. 3, the NCC equation).  The signed value is maximised.
  *   - Block edge b is odd, h = (b-1)/2; the search radius is given per axis
  *     and the shifts are d in [-R,R]^3 (Sec. 3, complexity bound; Sec. 5
- *     "half window size ... axial, coronal, sagittal").
+ *     gives the half window size per anatomical axis).
  *   - A shift whose block leaves the volume, or whose reference block is
  *     flat (zero variance), is not a candidate.
  *   - Ties in NCC are broken by smaller |d|^2, then by (dz,dy,dx)

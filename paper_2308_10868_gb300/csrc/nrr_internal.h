@@ -103,12 +103,26 @@ struct SelectPlan {
     int gx, gy, gz;
     long long ng;
     int nchunks;
-    size_t off_keys, off_hist, off_state, off_cnt, bytes;
+    int connectivity;  // 0, 6, 18 or 26
+    size_t off_keys, off_hist, off_state, off_sync, off_cnt, off_sp_state, off_sp_mask, bytes;
 };
-SelectPlan select_plan(nrr_dims d, int stride);
+SelectPlan select_plan(nrr_dims d, int stride, int connectivity = 0);
 nrr_status enqueue_select(const uint16_t *preop, const uint8_t *mask, nrr_dims d, int block, int stride, double frac,
                           int32_t *centers, int32_t max_blocks, int32_t *d_n_selected, unsigned char *ws,
                           const SelectPlan &p, cudaStream_t s);
+
+// Connectivity pattern of the selection (6, 18 or 26 neighbours on the
+// candidate grid): keeps only the greedy independent set of the candidates
+// in selection order selectable (other keys become 0) and sets *npos to its
+// size.  `sync` must be zero on entry; state and hmask hold ng bytes and ng
+// 32-bit words.
+struct SpacingSync {
+    unsigned int arrive;
+    unsigned int pad;
+    unsigned long long undecided[3];
+};
+nrr_status launch_spacing(int connectivity, long long *keys, int gx, int gy, long long ng, unsigned char *state,
+                          unsigned int *hmask, SpacingSync *sync, unsigned long long *npos, cudaStream_t s);
 // Offset of the selected count (int64) inside the selection scratch.
 size_t select_count_offset(const SelectPlan &p);
 nrr_status check_select_args(nrr_dims dims, int32_t block, int32_t stride, double frac);

@@ -364,9 +364,10 @@ void launch_keys(const uint16_t *preop, const uint8_t *mask, nrr_dims d, int str
 
 }  // namespace
 
-SelectPlan select_plan(nrr_dims d, int stride)
+SelectPlan select_plan(nrr_dims d, int stride, int connectivity)
 {
     SelectPlan p;
+    p.connectivity = connectivity;
     p.gx = (d.nx + stride - 1) / stride;
     p.gy = (d.ny + stride - 1) / stride;
     p.gz = (d.nz + stride - 1) / stride;
@@ -379,8 +380,16 @@ SelectPlan select_plan(nrr_dims d, int stride)
     o += align_up(sizeof(unsigned int) * HIST_BINS * NPASS, 256);
     p.off_state = o;
     o += align_up(sizeof(SelState), 256);
+    p.off_sync = o;  // zeroed together with the histograms and the state
+    o += align_up(sizeof(SpacingSync), 256);
     p.off_cnt = o;
     o += align_up((size_t)p.nchunks * 8, 256);
+    p.off_sp_state = p.off_sp_mask = o;
+    if (connectivity) {
+        o += align_up((size_t)p.ng, 256);
+        p.off_sp_mask = o;
+        o += align_up((size_t)p.ng * 4, 256);
+    }
     p.bytes = o;
     return p;
 }
@@ -408,6 +417,12 @@ nrr_status enqueue_select(const uint16_t *preop, const uint8_t *mask, nrr_dims d
         case 9: launch_keys<9>(preop, mask, d, stride, p.gx, p.gy, p.ng, keys, st, s); break;
         default: launch_keys<11>(preop, mask, d, stride, p.gx, p.gy, p.ng, keys, st, s); break;
         }
+    }
+    if (p.connectivity) {
+        nrr_status ss = launch_spacing(p.connectivity, keys, p.gx, p.gy, p.ng, ws + p.off_sp_state,
+                                       (unsigned int *)(ws + p.off_sp_mask), (SpacingSync *)(ws + p.off_sync),
+                                       &st->npos, s);
+        if (ss != NRR_OK) return ss;
     }
     long long hgrid = (p.ng + HIST_THREADS * HIST_KPT - 1) / (HIST_THREADS * HIST_KPT);
     if (hgrid > 4 * sm_count()) hgrid = 4 * sm_count();
@@ -450,6 +465,43 @@ extern "C" nrr_status nrr_select_blocks(const uint16_t *d_preop, const uint8_t *
     if (max_blocks > 0 && !d_centers) return fail(NRR_E_INVALID, "NULL centre buffer");
     cudaStream_t s = (cudaStream_t)stream;
     const SelectPlan p = select_plan(dims, stride);
+    void *ws = nullptr;
+    NRR_CUDA_TRY(cudaMallocAsync(&ws, p.bytes, s));
+    st = enqueue_select(d_preop, d_mask, dims, block, stride, frac, d_centers, max_blocks, d_n_selected,
+                        (unsigned char *)ws, p, s);
+    long long nsel = 0;
+    if (st == NRR_OK && h_n_selected) {
+        cudaError_t e = cudaMemcpyAsync(&nsel, (unsigned char *)ws + select_count_offset(p),
+                                        sizeof(nsel), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_fail(e, "reading the selection count");
+    }
+    cudaError_t e = cudaFreeAsync(ws, s);
+    if (st != NRR_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync");
+    if (h_n_selected) {
+        *h_n_selected = (int32_t)nsel;
+        if (nsel > max_blocks)
+            return fail(NRR_E_CAPACITY, "%lld blocks selected but max_blocks is %d", nsel, max_blocks);
+    }
+    return NRR_OK;
+}
+
+extern "C" nrr_status nrr_select_blocks_spaced(const uint16_t *d_preop, const uint8_t *d_mask, nrr_dims dims,
+                                               int32_t block, int32_t stride, double frac, int32_t connectivity,
+                                               int32_t *d_centers, int32_t max_blocks, int32_t *d_n_selected,
+                                               int32_t *h_n_selected, void *stream)
+{
+    clear_error();
+    nrr_status st = check_select_args(dims, block, stride, frac);
+    if (st != NRR_OK) return st;
+    if (connectivity != 0 && connectivity != 6 && connectivity != 18 && connectivity != 26)
+        return fail(NRR_E_INVALID, "connectivity %d is not 0, 6, 18 or 26", connectivity);
+    if (max_blocks < 0) return fail(NRR_E_INVALID, "max_blocks < 0");
+    if (!d_preop || !d_mask) return fail(NRR_E_INVALID, "NULL volume or mask");
+    if (max_blocks > 0 && !d_centers) return fail(NRR_E_INVALID, "NULL centre buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    const SelectPlan p = select_plan(dims, stride, connectivity);
     void *ws = nullptr;
     NRR_CUDA_TRY(cudaMallocAsync(&ws, p.bytes, s));
     st = enqueue_select(d_preop, d_mask, dims, block, stride, frac, d_centers, max_blocks, d_n_selected,

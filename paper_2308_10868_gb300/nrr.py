@@ -57,6 +57,7 @@ SIGNATURES = {
     "nrr_kernel_launches": (C.c_int64, []),
     "nrr_select_blocks": (C.c_int, [_P, _P, Dims, _I32, _I32, C.c_double, _P, _I32, _P, _P, _P]),
     "nrr_select_blocks_noalloc": (C.c_int, [_P, _P, Dims, _I32, _I32, C.c_double, _P, _I32, _P, _P, _P]),
+    "nrr_select_blocks_spaced": (C.c_int, [_P, _P, Dims, _I32, _I32, C.c_double, _I32, _P, _I32, _P, _P, _P]),
     "nrr_boxsum_bytes": (C.c_int, [Dims, C.c_int, C.POINTER(C.c_size_t)]),
     "nrr_boxsums": (C.c_int, [_P, C.c_int, Dims, _I32, _P, _P]),
     "nrr_block_match": (C.c_int, [_P, _P, C.c_int, Dims, _P, _I32, _P, _I32, _P, _P, _P, _P, _P]),
@@ -157,11 +158,13 @@ def max_selected(dims, stride: int, frac: float) -> int:
 
 def select_blocks(preop: torch.Tensor, mask: torch.Tensor, block: int, stride: int, frac: float,
                   max_blocks: int | None = None, centers: torch.Tensor | None = None,
-                  n_selected: torch.Tensor | None = None, sync: bool = True, stream=None):
+                  n_selected: torch.Tensor | None = None, sync: bool = True, stream=None,
+                  connectivity: int = 0):
     """Variance-based block selection.  Returns the (n, 3) int32 centres
     (x, y, z) in raster order.  With ``sync=False`` nothing is read back:
     the full ``centers`` buffer and the device count ``n_selected`` are
-    returned instead."""
+    returned instead.  ``connectivity`` 6, 18 or 26 applies the face, edge
+    or vertex spacing pattern (nrr_select_blocks_spaced)."""
     _cuda_contig(preop, "preop")
     _cuda_contig(mask, "mask")
     if _dtype_code(preop) != NRR_U16:
@@ -176,9 +179,15 @@ def select_blocks(preop: torch.Tensor, mask: torch.Tensor, block: int, stride: i
     if n_selected is None:
         n_selected = torch.zeros(1, dtype=torch.int32, device=preop.device)
     h = C.c_int32(0)
-    st = lib().nrr_select_blocks(_ptr(preop), _ptr(mask), dims, block, stride, float(frac), _ptr(centers),
-                                 max_blocks, _ptr(n_selected), C.byref(h) if sync else None, _stream(stream))
-    _check(st, "nrr_select_blocks")
+    if connectivity:
+        st = lib().nrr_select_blocks_spaced(_ptr(preop), _ptr(mask), dims, block, stride, float(frac),
+                                            int(connectivity), _ptr(centers), max_blocks, _ptr(n_selected),
+                                            C.byref(h) if sync else None, _stream(stream))
+        _check(st, "nrr_select_blocks_spaced")
+    else:
+        st = lib().nrr_select_blocks(_ptr(preop), _ptr(mask), dims, block, stride, float(frac), _ptr(centers),
+                                     max_blocks, _ptr(n_selected), C.byref(h) if sync else None, _stream(stream))
+        _check(st, "nrr_select_blocks")
     if sync:
         return centers[:h.value]
     return centers, n_selected

@@ -63,6 +63,11 @@ def test_argument_checks_need_no_device(L):
     assert L.nrr_select_blocks(fake, fake, d, 7, 0, 0.1, fake, 10, None, None, None) == -1
     assert L.nrr_select_blocks(fake, fake, d, 7, 2, 0.0, fake, 10, None, None, None) == -1
     assert L.nrr_select_blocks(fake, fake, d, 7, 2, 1.5, fake, 10, None, None, None) == -1
+    # connectivity pattern must be 0, 6, 18 or 26
+    for conn in (1, 8, 27, -6):
+        assert L.nrr_select_blocks_spaced(fake, fake, d, 7, 2, 0.1, conn, fake, 10, None, None, None) == -1
+        assert b"connectivity" in L.nrr_last_error()
+    assert L.nrr_select_blocks_spaced(fake, fake, d, 6, 2, 0.1, 6, fake, 10, None, None, None) == -1
     r = (C.c_int32 * 3)(4, 8, 4)
     assert L.nrr_block_match(fake, fake, 0, d, fake, 5, None, 7, r, fake, fake, fake, None) == -1
     assert b"radius" in L.nrr_last_error()
