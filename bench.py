@@ -53,6 +53,7 @@ def _args():
     p.add_argument("--batched-reps", type=int, default=5)
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-highres", action="store_true")
+    p.add_argument("--no-spacing", action="store_true")
     p.add_argument("--serve-open-requests", type=int, default=200)
     p.add_argument("--serve-closed-requests", type=int, default=300)
     return p.parse_args()
@@ -360,12 +361,9 @@ def _serving(a, nrr, synth, dev):
 def _highres(a, nrr, synth, dev, flush):
     """The high-resolution variant: 512x512x256, block 9^3, stride 3, top 5%,
     radius 7 (3375 shifts), as uint16 (exact path) and as float32 u/65535
-    (FP32 search, FP64 rescoring); NCC error of float32 against the FP64
-    oracle on a sample of blocks."""
-    import numpy as np
+    (FP32 search, FP64 rescoring).  Their agreement with the oracle is checked
+    by tests/test_gpu_highres.py, not here."""
     import torch
-
-    import oracle
 
     w = synth.WORKLOADS["highres"]
     pre, intra, mask = synth.workload_pair("highres")
@@ -396,17 +394,30 @@ def _highres(a, nrr, synth, dev, flush):
                      "roofline_frac": 2.0 * evals * w.block ** 3 / t / 1e12 / (
                          torch.cuda.get_device_properties(dev).multi_processor_count * FP32_LANES_PER_SM * 2 *
                          float(_peaks().get("sm_max_mhz", 2070.0)) * 1e6 / 1e12)}
-        if name == "f32":
-            c = centers.cpu().numpy()
-            idx = np.arange(0, n, max(1, n // 400))
-            gd, gn = res[0].cpu().numpy()[idx], res[1].cpu().numpy()[idx]
-            rd, rn, rv = oracle.match(p32, i32, c[idx], w.block, w.radius)
-            at = np.array([oracle.pearson_f32(p32, i32, w.block, c[k], gd[j]) if rv[j] else np.nan
-                           for j, k in enumerate(idx)])
-            ok = rv == 1
-            out["f32"]["ncc_max_abs_err_vs_fp64_oracle"] = float(np.abs(gn[ok] - at[ok]).max())
-            out["f32"]["disp_mismatch_frac"] = float(((gd != rd).any(axis=1) & ok).mean())
-            out["f32"]["sample_blocks"] = int(len(idx))
+    return out
+
+
+def _spacing(a, nrr, synth, d_pre, d_mask, w, flush):
+    """Selection with the face / edge / vertex connectivity patterns (6 / 18 /
+    26 neighbours on the candidate grid) on the step's volume, against the
+    plain selection: device time per selection (CUDA events, L2 flushed
+    before each) and the number selected."""
+    import torch
+
+    stream = torch.cuda.current_stream()
+    out = {"workload": w.name, "timing": "CUDA events around one selection, best of 5, L2 flushed before each"}
+    for conn in (0, 6, 18, 26):
+        ts = []
+        for _ in range(6):
+            flush.fill_(3)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c, n = nrr.select_blocks(d_pre, d_mask, w.block, w.stride, w.frac, connectivity=conn, sync=False)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        nrr.device_status()
+        out[f"conn{conn}"] = {"select_ms": min(ts[1:]), "n_selected": int(n.item())}
     return out
 
 
@@ -546,6 +557,8 @@ def run_ours(a):
         line["serving"] = _serving(a, nrr, synth, dev)
     if not a.no_highres:
         line["highres"] = _highres(a, nrr, synth, dev, flush)
+    if not a.no_spacing:
+        line["spacing"] = _spacing(a, nrr, synth, d_pre, d_mask, w, flush)
     if world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(w, pre, intra, mask)
     print(json.dumps(line), flush=True)

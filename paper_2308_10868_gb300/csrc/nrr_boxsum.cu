@@ -94,8 +94,15 @@ struct BoxArgs {
     unsigned int *err;
 };
 
+// Resident CTAs per SM to keep registers for, without spills (the keys
+// epilogue's stride-spaced brick allows only two by shared memory).
+template <int B, bool KEYS>
+struct BoxMinBlocks {
+    static constexpr int value = KEYS ? 2 : B <= 5 ? 6 : B <= 7 ? 4 : B <= 9 ? 3 : 2;
+};
+
 template <typename T, int B, bool KEYS>
-__global__ void __launch_bounds__(MAX_NT) box_kernel(const __grid_constant__ CUtensorMap map, const BoxArgs a)
+__global__ void __launch_bounds__(MAX_NT, (BoxMinBlocks<B, KEYS>::value)) box_kernel(const __grid_constant__ CUtensorMap map, const BoxArgs a)
 {
     typedef typename BoxQ<T>::A1 A1;
     typedef typename BoxQ<T>::A2 A2;
@@ -136,8 +143,27 @@ __global__ void __launch_bounds__(MAX_NT) box_kernel(const __grid_constant__ CUt
     }
     int cand = 0, pos = 0;
     unsigned long long kmax = 0;
+    // keys: this column's mask bits, fetched while the brick is in flight
+    uint32_t mbits = 0;
+    if constexpr (KEYS) {
+        const int x = i * S, y = j * S;
+        if (i < a.gx && j < a.gy && x >= H && x <= a.nx - 1 - H && y >= H && y <= a.ny - 1 - H) {
+#pragma unroll
+            for (int kk = 0; kk < 16; ++kk) {
+                const int z = (k0 + kk) * S;
+                if (kk < g.ZC && z >= H && z <= a.nz - 1 - H && a.mask[((size_t)z * a.ny + y) * a.nx + x] != 0)
+                    mbits |= 1u << kk;
+            }
+        }
+    }
 
-    for (int iz = 0; iz < IZ; ++iz) {
+    // planes in groups of B, so that ring slot u always holds the plane
+    // sums of the planes congruent to u modulo B (static register indices)
+    for (int iz0 = 0; iz0 < IZ; iz0 += B) {
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+        const int iz = iz0 + u;
+        if (iz >= IZ) break;
         if (iz % CZ == 0) {
             const bool got = mbar_wait_bounded(bar + iz / CZ, 0, BOX_WAIT_NS);
             if (!__syncthreads_and(got)) {
@@ -181,17 +207,12 @@ __global__ void __launch_bounds__(MAX_NT) box_kernel(const __grid_constant__ CUt
             p1 += r1[(ty * S + k) * TX + tx];
             p2 += r2[(ty * S + k) * TX + tx];
         }
-        if constexpr (BoxQ<T>::exact) {
-            run1 += p1 - ring1[0];
-            run2 += p2 - ring2[0];
+        if constexpr (BoxQ<T>::exact) {  // slot u held plane iz - B
+            run1 += p1 - ring1[u];
+            run2 += p2 - ring2[u];
         }
-#pragma unroll
-        for (int k = 0; k < B - 1; ++k) {
-            ring1[k] = ring1[k + 1];
-            ring2[k] = ring2[k + 1];
-        }
-        ring1[B - 1] = p1;
-        ring2[B - 1] = p2;
+        ring1[u] = p1;
+        ring2[u] = p2;
         // the ring now holds input planes iz-B+1..iz: an output plane when
         // they are the planes of local output kk
         const int q = iz - (B - 1);
@@ -203,7 +224,7 @@ __global__ void __launch_bounds__(MAX_NT) box_kernel(const __grid_constant__ CUt
         if constexpr (BoxQ<T>::exact) {
             o1 = run1;
             o2 = run2;
-        } else {  // a direct sum of the b plane sums (fixed depth)
+        } else {  // a direct sum of the b plane sums (fixed depth b)
             o1 = 0;
             o2 = 0;
 #pragma unroll
@@ -216,7 +237,7 @@ __global__ void __launch_bounds__(MAX_NT) box_kernel(const __grid_constant__ CUt
         const bool in = x >= H && x <= a.nx - 1 - H && y >= H && y <= a.ny - 1 - H && z >= H && z <= a.nz - 1 - H;
         if constexpr (KEYS) {
             long long key = -1;
-            if (in && a.mask[((size_t)z * a.ny + y) * a.nx + x] != 0) {
+            if (in && ((mbits >> kk) & 1u)) {
                 key = N * (long long)o2 - (long long)o1 * (long long)o1;
                 cand += 1;
                 pos += key > 0;
@@ -233,6 +254,7 @@ __global__ void __launch_bounds__(MAX_NT) box_kernel(const __grid_constant__ CUt
                 reinterpret_cast<float *>(a.out2)[idx] = in ? (float)o2 : 0.f;
             }
         }
+    }
     }
 
     if constexpr (KEYS) {  // candidate counts and the largest key of this CTA

@@ -112,17 +112,21 @@ nrr_status enqueue_select(const uint16_t *preop, const uint8_t *mask, nrr_dims d
                           const SelectPlan &p, cudaStream_t s);
 
 // Connectivity pattern of the selection (6, 18 or 26 neighbours on the
-// candidate grid): keeps only the greedy independent set of the candidates
-// in selection order selectable (other keys become 0) and sets *npos to its
-// size.  `sync` must be zero on entry; state and hmask hold ng bytes and ng
-// 32-bit words.
+// candidate grid): keeps selectable (key > 0) only the members of the greedy
+// independent set, in selection order, of a prefix of the candidates that
+// holds at least n_sel = floor(0.5 + *nc * frac) members if the whole set
+// does, and sets *npos to the number kept.  `sync` must be zero on entry;
+// state and hmask hold ng bytes and ng 32-bit words.
 struct SpacingSync {
     unsigned int arrive;
     unsigned int pad;
     unsigned long long undecided[3];
+    unsigned int hist[2048];
 };
-nrr_status launch_spacing(int connectivity, long long *keys, int gx, int gy, long long ng, unsigned char *state,
-                          unsigned int *hmask, SpacingSync *sync, unsigned long long *npos, cudaStream_t s);
+nrr_status launch_spacing(int connectivity, long long *keys, int gx, int gy, long long ng, double frac,
+                          unsigned char *state, unsigned int *hmask, SpacingSync *sync,
+                          const unsigned long long *nc, const unsigned long long *maxkey, unsigned long long *npos,
+                          cudaStream_t s);
 // Offset of the selected count (int64) inside the selection scratch.
 size_t select_count_offset(const SelectPlan &p);
 nrr_status check_select_args(nrr_dims dims, int32_t block, int32_t stride, double frac);

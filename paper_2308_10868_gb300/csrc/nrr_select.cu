@@ -419,9 +419,9 @@ nrr_status enqueue_select(const uint16_t *preop, const uint8_t *mask, nrr_dims d
         }
     }
     if (p.connectivity) {
-        nrr_status ss = launch_spacing(p.connectivity, keys, p.gx, p.gy, p.ng, ws + p.off_sp_state,
+        nrr_status ss = launch_spacing(p.connectivity, keys, p.gx, p.gy, p.ng, frac, ws + p.off_sp_state,
                                        (unsigned int *)(ws + p.off_sp_mask), (SpacingSync *)(ws + p.off_sync),
-                                       &st->npos, s);
+                                       &st->nc, &st->maxkey, &st->npos, s);
         if (ss != NRR_OK) return ss;
     }
     long long hgrid = (p.ng + HIST_THREADS * HIST_KPT - 1) / (HIST_THREADS * HIST_KPT);
