@@ -226,7 +226,8 @@ def run_reference(a):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u16", "data": "synthetic",
-            "config": _config(w, n, {"sample": "selection of all blocks + matching every 4th selected block"}),
+            "config": _config(w, n, {"sample": "selection of all blocks + matching every 4th selected block",
+                                     "l2": "not applicable (host CPU run)"}),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": "per step: full selection + matching every 4th selected block"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
