@@ -197,14 +197,18 @@ nrr_status nrr_select_blocks_noalloc(const uint16_t *d_preop, const uint8_t *d_m
                                      int32_t *d_n_selected, int32_t *h_n_selected, void *stream);
 
 /* ------------------------------------------------------------------------
- * Box sums of the reference image, the per-shift sums S_J and S_JJ of the
- * NCC (Sec. 3): for every voxel v whose b^3 block lies in the volume,
+ * Box sums of the reference image, from the per-shift sums S_J and S_JJ of
+ * the NCC (Sec. 3): for every voxel v whose b^3 block lies in the volume,
  *   S1[v] = sum of J over the block centred at v,
- *   S2[v] = sum of J^2 over the same block.
- * uint16: S1 is int32 and S2 int64, both exact.  float32: both float32.
- * Layout of d_boxsums: S1 as [nz][ny][nx] elements, then S2 as
- * [nz][ny][nx] elements starting at the next 256-byte boundary; size from
- * nrr_boxsum_bytes.  Voxels whose block leaves the volume hold 0.
+ *   A2[v] = uint16:  N * (sum of J^2) - S1[v]^2  (N = b^3; exact in 64 bits,
+ *                    then rounded once to float32: N^2 times the block's
+ *                    variance),
+ *           float32: sum of J^2 over the block.
+ * uint16: S1 is int32 (exact), A2 float32.  float32: both float32.
+ * Layout of d_boxsums: S1 as [nz][ny][nx] elements, then A2 as [nz][ny][nx]
+ * elements starting at the next 256-byte boundary (8 bytes per voxel in
+ * all); size from nrr_boxsum_bytes.  Voxels whose block leaves the volume
+ * hold 0.
  * ---------------------------------------------------------------------- */
 nrr_status nrr_boxsum_bytes(nrr_dims dims, nrr_dtype dtype, size_t *bytes);
 nrr_status nrr_boxsums(const void *d_intraop, nrr_dtype dtype, nrr_dims dims, int32_t block,

@@ -123,7 +123,8 @@ nrr_status check_dims(nrr_dims d, nrr_dtype dtype, int32_t block)
 size_t boxsum_bytes(nrr_dims dims, nrr_dtype dtype)
 {
     size_t v = (size_t)dims.nx * dims.ny * dims.nz;
-    return boxsum_s2_offset(dims, dtype) + align_up(v * (dtype == NRR_F32 ? 4 : 8), 256);
+    (void)dtype;
+    return boxsum_s2_offset(dims, dtype) + align_up(v * 4, 256);  // second array: 4-byte elements
 }
 
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }

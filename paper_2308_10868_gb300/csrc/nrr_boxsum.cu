@@ -1,8 +1,8 @@
 // Sums over b^3 blocks, for both steps of the path:
-//  * matching (Sec. 3, NCC equation): S_J = sum J and S_JJ = sum J^2 of the
-//    reference block at every voxel -- the reference block's mean and spread
-//    change with every shift -- computed once per (volume, block size)
-//    because neighbouring blocks' search windows overlap heavily;
+//  * matching (Sec. 3, NCC equation): S_J = sum J of the reference block at
+//    every voxel and its spread, from S_JJ = sum J^2 -- the reference block's
+//    mean and spread change with every shift -- computed once per (volume,
+//    block size) because neighbouring blocks' search windows overlap heavily;
 //  * selection (Sec. 4.1, "Parallel feature selection"): the variance key
 //    N*sum I^2 - (sum I)^2 of the floating block at every stride grid point
 //    whose centre lies in the mask and whose block lies in the volume.
@@ -16,7 +16,10 @@
 // per plane suffices); then sums of b of those along y at the output rows,
 // one thread per output column; the last b plane sums stay in registers and
 // at every output plane their sum is the result.
-//   uint16: exact (32-bit sums of J, 64-bit sums of J^2, running z sums).
+//   uint16: exact (32-bit sums of J, 64-bit sums of J^2, running z sums);
+//           stored as S_J (int32) and v_J = N*S_JJ - S_J^2 rounded once to
+//           float (the match kernel's filter needs only an approximation
+//           of v_J, and its exact rescoring recomputes the sums).
 //   float32: float sums whose every output is three levels of b-term sums;
 //            the match kernel's error bound relies on that shape.
 #include <stddef.h>
@@ -248,7 +251,9 @@ __global__ void __launch_bounds__(MAX_NT, (BoxMinBlocks<B, KEYS>::value)) box_ke
             const size_t idx = ((size_t)z * a.ny + y) * a.nx + x;
             if constexpr (BoxQ<T>::exact) {
                 reinterpret_cast<int32_t *>(a.out1)[idx] = in ? (int32_t)o1 : 0;
-                reinterpret_cast<unsigned long long *>(a.out2)[idx] = in ? (unsigned long long)o2 : 0ull;
+                // v_J = N*S_JJ - S_J^2 (exact in 64 bits), rounded once to float
+                reinterpret_cast<float *>(a.out2)[idx] =
+                    in ? __ll2float_rn(N * (long long)o2 - (long long)o1 * (long long)o1) : 0.f;
             } else {
                 reinterpret_cast<float *>(a.out1)[idx] = in ? (float)o1 : 0.f;
                 reinterpret_cast<float *>(a.out2)[idx] = in ? (float)o2 : 0.f;

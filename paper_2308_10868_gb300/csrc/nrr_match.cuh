@@ -75,6 +75,7 @@ struct BlockConst {
     double dvI;     // float32: sum (I - Ibar)^2
     double ibar;    // float32: mean of I
     float fvI;      // vI as float
+    float frr;      // uint16: rr as float (exact: |rr| <= N/2)
     float kq;       // uint16: N*gamma_N*sqrt(sum T^2); float32: sqrt(sum T^2) (rounded up)
     float mu;       // float32: float mean used for T
     float emu;      // float32: Ibar - mu
@@ -477,6 +478,7 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                     c.vI = vI;
                     c.m = (int)m;
                     c.rr = (long long)N * m - s1;
+                    c.frr = (float)c.rr;
                     c.fvI = (float)vI;
                     c.kq = (float)((double)N * GAMMA_N * sqrt((double)qt) * (1.0 + 1e-6));
                 }
@@ -576,7 +578,7 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
             const int dy = dyi - ry, dz = dzi - rz, Y = cy + dy, Z = cz + dz;
             const bool yz_ok = Y >= H && Y <= ny - 1 - H && Z >= H && Z <= nz - 1 - H;
             typedef typename std::conditional<F32, float, int32_t>::type S1T;
-            typedef typename std::conditional<F32, float, long long>::type S2T;
+            typedef float S2T;  // uint16: v_J = N S_JJ - S_J^2 rounded to float; float32: S_JJ
             float acc[P];
 #pragma unroll
             for (int p = 0; p < P; ++p) acc[p] = 0.f;
@@ -621,17 +623,22 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                 ub[p] = -INFINITY;
                 if (!((vmask >> p) & 1u)) continue;
                 if constexpr (!F32) {
-                    const long long s1 = ps1[p];
-                    const long long s2 = ps2[p];
-                    const long long vJ = (long long)N * s2 - s1 * s1;
-                    if (vJ <= 0) continue;  // flat reference block
-                    const long long s1p = s1 - (long long)N * c_i;
-                    const long long s2p = s2 - 2ll * c_i * s1 + (long long)N * c_i * c_i;  // sum (J-c)^2
-                    const float inv = __frsqrt_rn(__fmul_rn(bc.fvI, (float)vJ));
+                    // 32-bit integer and float arithmetic only: a 64-bit
+                    // integer to float conversion issues on the FP64 pipe,
+                    // which is narrow on this part.  v_J arrives rounded once
+                    // (zero only for a flat block); S'_J = S_J - N c is exact.
+                    const float vjf = ps2[p];
+                    if (!(vjf > 0.f)) continue;  // flat reference block
+                    const int s1p = ps1[p] - N * c_i;
+                    const float s1pf = (float)s1p;
+                    // sum (J - c)^2 = (v_J + S'_J^2) / N, rounded up: the
+                    // rounded v_J and S'_J and three operations stay below 6u
+                    const float s2p = __fmul_rn(__fmul_rn(__fmaf_rn(s1pf, s1pf, vjf), 1.0f / fN), 1.f + 16.f * U32);
+                    const float inv = __frsqrt_rn(__fmul_rn(bc.fvI, vjf));
                     const float na = __fmul_rn(fN, acc[p]);
-                    const float rs = (float)(bc.rr * s1p);
+                    const float rs = __fmul_rn(bc.frr, s1pf);  // rr exact in float (|rr| <= N/2)
                     const float v = __fmul_rn(__fadd_rn(na, rs), inv);
-                    float e = bc.kq * __fsqrt_rn((float)s2p) * inv + 3.f * U32 * (fabsf(na) + fabsf(rs)) * inv +
+                    float e = bc.kq * __fsqrt_rn(s2p) * inv + 4.f * U32 * (fabsf(na) + fabsf(rs)) * inv +
                               6.f * U32 * fabsf(v);
                     e = 2.f * e + 1e-9f;
                     ub[p] = v + e;
@@ -712,14 +719,11 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
             const size_t idx = ((size_t)(cz + dz) * ny + (cy + dy)) * nx + (cx + dx);
             Cand c{0.0, dx * dx + dy * dy + dz * dz, code, 0};
             if constexpr (!F32) {  // one warp per survivor: parts == 1
-                long long s1 = 0, s2 = 0;
-                if (lane == 0) {  // issued first, consumed after the warp sum
-                    s1 = reinterpret_cast<const int32_t *>(a.s1)[idx];
-                    s2 = reinterpret_cast<const long long *>(a.s2)[idx];
-                }
+                long long s1 = 0;
+                if (lane == 0) s1 = reinterpret_cast<const int32_t *>(a.s1)[idx];  // issued first, used after the warp sums
                 constexpr int KPL = (N + 31) / 32;
                 constexpr int CH = KPL < 6 ? KPL : 6;
-                long long e = 0;
+                long long e = 0, q2 = 0;  // sum T (J - c), sum (J - c)^2: exact
 #pragma unroll 1
                 for (int i0 = 0; i0 < KPL; i0 += CH) {
                     int tv[CH], jv[CH];
@@ -735,12 +739,17 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                         }
                     }
 #pragma unroll
-                    for (int q = 0; q < CH; ++q) e += (long long)tv[q] * jv[q];
+                    for (int q = 0; q < CH; ++q) {
+                        e += (long long)tv[q] * jv[q];
+                        q2 += (long long)jv[q] * jv[q];
+                    }
                 }
                 e = warp_sum(e);
+                q2 = warp_sum(q2);
                 if (lane == 0) {
-                    const long long vJ = (long long)N * s2 - s1 * s1;
-                    const long long num = (long long)N * e + bc.rr * (s1 - (long long)N * c_i);
+                    const long long s1p = s1 - (long long)N * c_i;  // sum (J - c)
+                    const long long vJ = (long long)N * q2 - s1p * s1p;  // = N S_JJ - S_J^2, exact
+                    const long long num = (long long)N * e + bc.rr * s1p;
                     if (vJ > 0) {
                         const double den = __dsqrt_rn(__dmul_rn((double)bc.vI, (double)vJ));
                         c.s = __ddiv_rn((double)num, den);

@@ -221,3 +221,41 @@ def test_f32_integer_valued_equals_u16(nrr):
     assert torch.equal(v16, v32)
     assert (n16 - n32).abs().max().item() < 1e-12
 
+
+
+def _box_ref(vol, b):
+    """Exact block sums of J and J^2 by integral volumes (int64), 0 where the
+    block leaves the volume."""
+    v = vol.astype(np.int64)
+    h = (b - 1) // 2
+
+    def boxsum(a):
+        c = np.zeros(tuple(s + 1 for s in a.shape), np.int64)
+        c[1:, 1:, 1:] = a.cumsum(0).cumsum(1).cumsum(2)
+        nz, ny, nx = a.shape
+        out = np.zeros(a.shape, np.int64)
+        z0, y0, x0 = np.arange(nz - b + 1), np.arange(ny - b + 1), np.arange(nx - b + 1)
+        Z, Y, X = np.ix_(z0, y0, x0)
+        s = (c[Z + b, Y + b, X + b] - c[Z, Y + b, X + b] - c[Z + b, Y, X + b] - c[Z + b, Y + b, X]
+             + c[Z, Y, X + b] + c[Z, Y + b, X] + c[Z + b, Y, X] - c[Z, Y, X])
+        out[h:nz - h, h:ny - h, h:nx - h] = s
+        return out
+
+    return boxsum(v), boxsum(v * v)
+
+
+@pytest.mark.parametrize("b", [3, 7, 11])
+def test_box_sums_contents(nrr, b):
+    # uint16 box sums: S1 exact int32; A2 = N*S2 - S1^2 rounded once to float32
+    dims = (48, 26, 21)
+    vol = synth.random_u16(dims, 5)  # full 16-bit range
+    buf = nrr.boxsums(_dev_u16(nrr, vol), b).cpu().numpy()
+    nz, ny, nx = vol.shape
+    nv = nx * ny * nz
+    s1 = buf[:4 * nv].view(np.int32).reshape(nz, ny, nx)
+    off = (4 * nv + 255) // 256 * 256
+    a2 = buf[off:off + 4 * nv].view(np.float32).reshape(nz, ny, nx)
+    r1, r2 = _box_ref(vol, b)
+    assert np.array_equal(s1.astype(np.int64), r1)
+    ref_a2 = (b ** 3 * r2 - r1 * r1).astype(np.float32)
+    assert np.array_equal(a2.view(np.uint32), ref_a2.view(np.uint32))
