@@ -101,10 +101,10 @@ struct BoxArgs {
 // epilogue's stride-spaced brick allows only two by shared memory).
 template <int B, bool KEYS>
 struct BoxMinBlocks {
-    static constexpr int value = KEYS ? 2 : B <= 5 ? 6 : B <= 7 ? 4 : B <= 9 ? 3 : 2;
+    static constexpr int value = KEYS ? 2 : B <= 3 ? 6 : B <= 5 ? 5 : B <= 7 ? 4 : B <= 9 ? 3 : 2;
 };
 
-template <typename T, int B, bool KEYS>
+template <typename T, int B, bool KEYS, int S>
 __global__ void __launch_bounds__(MAX_NT, (BoxMinBlocks<B, KEYS>::value)) box_kernel(const __grid_constant__ CUtensorMap map, const BoxArgs a)
 {
     typedef typename BoxQ<T>::A1 A1;
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(MAX_NT, (BoxMinBlocks<B, KEYS>::value)) box_ke
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar[MAX_CHUNKS];
     const BoxGeom &g = a.g;
-    const int S = g.S, IH = g.ih, IZ = g.iz, BW = g.bw, NT = TX * g.TY;
+    const int IH = g.ih, IZ = g.iz, BW = g.bw, NT = TX * g.TY;
     A2 *rb2 = reinterpret_cast<A2 *>(smem + g.r_off);                              // [2][IH][TX]
     A1 *rb1 = reinterpret_cast<A1 *>(smem + g.r_off + 2 * sizeof(A2) * IH * TX);  // [2][IH][TX]
 
@@ -183,24 +183,61 @@ __global__ void __launch_bounds__(MAX_NT, (BoxMinBlocks<B, KEYS>::value)) box_ke
         A1 *r1 = rb1 + (iz & 1) * IH * TX;
         A2 *r2 = rb2 + (iz & 1) * IH * TX;
         // x sums at the output columns of every row of plane iz
-        for (int it = tid; it < IH * TX; it += NT) {
-            const int ox = it % TX, iy = it / TX;
-            const T *src = plane + iy * BW + g.xoff + ox * S;
-            A1 a1 = 0;
-            A2 a2 = 0;
+        if constexpr (BoxQ<T>::exact) {
+            // a thread slides along 8 consecutive outputs of a row: the next
+            // sum adds the S entering values and drops the S leaving ones
+            // (modular 32/64-bit arithmetic, exact since the true sums fit)
+            constexpr int SEG = 8, NSEG = TX / SEG, NV = (SEG - 1) * S + B;
+            for (int it = tid; it < IH * NSEG; it += NT) {
+                const int seg = it % NSEG, iy = it / NSEG;
+                const T *src = plane + iy * BW + g.xoff + seg * SEG * S;
+                uint32_t v[NV], sq[NV];
 #pragma unroll
-            for (int k = 0; k < B; ++k) {
-                const T v = src[k];
-                if constexpr (BoxQ<T>::exact) {
-                    a1 += (uint32_t)v;
-                    a2 += (unsigned long long)((uint32_t)v) * (uint32_t)v;
-                } else {
+                for (int k = 0; k < NV; ++k) {
+                    v[k] = src[k];
+                    sq[k] = v[k] * v[k];  // < 2^32
+                }
+                uint32_t a1 = 0, o1[SEG];
+                unsigned long long a2 = 0, o2[SEG];
+#pragma unroll
+                for (int k = 0; k < B; ++k) {
+                    a1 += v[k];
+                    a2 += sq[k];
+                }
+                o1[0] = a1;
+                o2[0] = a2;
+#pragma unroll
+                for (int i = 1; i < SEG; ++i) {
+#pragma unroll
+                    for (int k = 0; k < S; ++k) {
+                        a1 += v[(i - 1) * S + B + k] - v[(i - 1) * S + k];
+                        a2 += (unsigned long long)sq[(i - 1) * S + B + k] - sq[(i - 1) * S + k];
+                    }
+                    o1[i] = a1;
+                    o2[i] = a2;
+                }
+                uint4 *d1 = reinterpret_cast<uint4 *>(r1 + iy * TX + seg * SEG);  // 16-byte aligned
+                d1[0] = make_uint4(o1[0], o1[1], o1[2], o1[3]);
+                d1[1] = make_uint4(o1[4], o1[5], o1[6], o1[7]);
+                ulonglong2 *d2 = reinterpret_cast<ulonglong2 *>(r2 + iy * TX + seg * SEG);
+#pragma unroll
+                for (int q = 0; q < SEG / 2; ++q) d2[q] = make_ulonglong2(o2[2 * q], o2[2 * q + 1]);
+            }
+        } else {  // float: every x sum a direct b-term sum (fixed depth)
+            for (int it = tid; it < IH * TX; it += NT) {
+                const int ox = it % TX, iy = it / TX;
+                const T *src = plane + iy * BW + g.xoff + ox * S;
+                A1 a1 = 0;
+                A2 a2 = 0;
+#pragma unroll
+                for (int k = 0; k < B; ++k) {
+                    const T v = src[k];
                     a1 += v;
                     a2 += __fmul_rn(v, v);
                 }
+                r1[iy * TX + ox] = a1;
+                r2[iy * TX + ox] = a2;
             }
-            r1[iy * TX + ox] = a1;
-            r2[iy * TX + ox] = a2;
         }
         __syncthreads();  // x sums of plane iz ready (and plane iz-2's buffer is free)
         A1 p1 = 0;
@@ -307,10 +344,10 @@ inline bool pick_geom(int B, int S, int es, BoxGeom *out)
     return false;
 }
 
-template <typename T, int B, bool KEYS>
-cudaError_t launch_box(const CUtensorMap &map, BoxArgs &a, cudaStream_t st)
+template <typename T, int B, bool KEYS, int S>
+cudaError_t launch_box_s(const CUtensorMap &map, BoxArgs &a, cudaStream_t st)
 {
-    auto kern = box_kernel<T, B, KEYS>;
+    auto kern = box_kernel<T, B, KEYS, S>;
     static size_t attr = 0;  // largest dynamic shared memory opted in so far
     if (a.g.smem > attr) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.g.smem);
@@ -320,6 +357,20 @@ cudaError_t launch_box(const CUtensorMap &map, BoxArgs &a, cudaStream_t st)
     dim3 grid((a.gx + TX - 1) / TX, (a.gy + a.g.TY - 1) / a.g.TY, (a.gz + a.g.ZC - 1) / a.g.ZC);
     kern<<<grid, TX * a.g.TY, a.g.smem, st>>>(map, a);
     return cudaGetLastError();
+}
+
+template <typename T, int B, bool KEYS>
+cudaError_t launch_box(const CUtensorMap &map, BoxArgs &a, cudaStream_t st)
+{
+    if constexpr (!KEYS) {
+        return launch_box_s<T, B, KEYS, 1>(map, a, st);
+    } else {
+        switch (a.g.S) {
+        case 1: return launch_box_s<T, B, KEYS, 1>(map, a, st);
+        case 2: return launch_box_s<T, B, KEYS, 2>(map, a, st);
+        default: return launch_box_s<T, B, KEYS, 3>(map, a, st);
+        }
+    }
 }
 
 template <typename T, bool KEYS>
