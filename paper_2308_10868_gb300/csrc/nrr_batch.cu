@@ -9,8 +9,15 @@
 //   - box sums of the reference volume, once per distinct block size;
 //   - one selection per distinct (block, stride, fraction), each on its own
 //     preallocated scratch;
+//   - settings that share (block, stride, radius) and differ only in the
+//     fraction select nested sets of blocks (a smaller fraction takes a
+//     prefix of the same selection order), and a block's match does not
+//     depend on the fraction: only the largest fraction's blocks are
+//     matched, and every other setting of that unit gathers its blocks'
+//     results from them;
 //   - one persistent match launch per distinct (block, radius), whose job
-//     table holds every setting of that variant (up to 16 per launch);
+//     table holds the matched selection of every unit of that variant (up
+//     to 16 per launch);
 //   - all of it forked over internal streams with event dependencies and
 //     captured as a single CUDA graph, so a run is one graph launch with no
 //     host round trip.
@@ -47,10 +54,49 @@ struct BoxEntry {
 };
 struct SettingOut {
     int sel;
+    int src;  // setting whose matched blocks hold this one's results (itself if matched)
     int32_t *disp;
     double *ncc;
     uint8_t *valid;
 };
+
+// Results of a nested selection from those of the larger one it is part of:
+// both centre lists are in raster order, so each centre is found by binary
+// search on its raster index.
+__global__ void gather_nested_kernel(const int32_t *__restrict__ centers, const int32_t *__restrict__ d_n,
+                                     int32_t cap, const int32_t *__restrict__ big_centers,
+                                     const int32_t *__restrict__ big_n, int32_t big_cap, int nx, int ny,
+                                     const int32_t *__restrict__ big_disp, const double *__restrict__ big_ncc,
+                                     const uint8_t *__restrict__ big_valid, int32_t *__restrict__ disp,
+                                     double *__restrict__ ncc, uint8_t *__restrict__ valid, unsigned int *err)
+{
+    const int n = *d_n < cap ? *d_n : cap;
+    const int nb = *big_n < big_cap ? *big_n : big_cap;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const long long key = ((long long)centers[3 * i + 2] * ny + centers[3 * i + 1]) * nx + centers[3 * i];
+        int lo = 0, hi = nb;  // first index whose raster key is >= key
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            const long long mk =
+                ((long long)big_centers[3 * mid + 2] * ny + big_centers[3 * mid + 1]) * nx + big_centers[3 * mid];
+            if (mk < key) lo = mid + 1;
+            else hi = mid;
+        }
+        if (lo < nb && big_centers[3 * lo] == centers[3 * i] && big_centers[3 * lo + 1] == centers[3 * i + 1] &&
+            big_centers[3 * lo + 2] == centers[3 * i + 2]) {
+            disp[3 * i + 0] = big_disp[3 * lo + 0];
+            disp[3 * i + 1] = big_disp[3 * lo + 1];
+            disp[3 * i + 2] = big_disp[3 * lo + 2];
+            ncc[i] = big_ncc[lo];
+            valid[i] = big_valid[lo];
+        } else {  // cannot happen for nested selections; reported, never silent
+            disp[3 * i + 0] = disp[3 * i + 1] = disp[3 * i + 2] = 0;
+            ncc[i] = 0.0;
+            valid[i] = 0;
+            atomicOr(err, DEV_ERR_INTERNAL);
+        }
+    }
+}
 struct Group {
     int block;
     int radius[3];
@@ -117,7 +163,8 @@ static nrr_status batch_enqueue(nrr_batch_s *b, cudaStream_t s)
         auto work = [&](int g) {
             const Group &G = b->groups[g];
             long long w = 0;
-            for (int s_ : G.settings) w += (long long)b->sels[b->outs[s_].sel].cap;
+            for (int s_ : G.settings)
+                if (b->outs[s_].src == s_) w += (long long)b->sels[b->outs[s_].sel].cap;
             return w * (2 * G.radius[0] + 1) * (2 * G.radius[1] + 1) * (2 * G.radius[2] + 1) * G.block * G.block *
                    G.block;
         };
@@ -128,9 +175,12 @@ static nrr_status batch_enqueue(nrr_batch_s *b, cudaStream_t s)
         const BoxEntry *bx = nullptr;
         for (auto &e : b->boxes)
             if (e.block == G.block) bx = &e;
-        for (size_t c0 = 0; c0 < G.settings.size(); c0 += MATCH_MAX_JOBS) {
-            cudaStream_t st = b->streams[rr++ % NSTREAMS];
-            NRR_CUDA_TRY(cudaStreamWaitEvent(st, bx->done, 0));
+        std::vector<int> matched;
+        for (int s_ : G.settings)
+            if (b->outs[s_].src == s_) matched.push_back(s_);
+        cudaStream_t st = b->streams[rr++ % NSTREAMS];  // the group's launches, then its gathers
+        NRR_CUDA_TRY(cudaStreamWaitEvent(st, bx->done, 0));
+        for (size_t c0 = 0; c0 < matched.size(); c0 += MATCH_MAX_JOBS) {
             MatchLaunch a{};
             a.preop = b->preop;
             a.intraop = b->intraop;
@@ -142,14 +192,27 @@ static nrr_status batch_enqueue(nrr_batch_s *b, cudaStream_t s)
             for (int i = 0; i < 3; ++i) a.radius[i] = G.radius[i];
             a.err = b->err;
             a.ctas_per_sm = tuned_ctas_per_sm(NRR_U16, G.block, G.radius);
-            for (size_t c = c0; c < G.settings.size() && c < c0 + MATCH_MAX_JOBS; ++c) {
-                const SettingOut &o = b->outs[G.settings[c]];
+            for (size_t c = c0; c < matched.size() && c < c0 + MATCH_MAX_JOBS; ++c) {
+                const SettingOut &o = b->outs[matched[c]];
                 const SelEntry &se = b->sels[o.sel];
                 NRR_CUDA_TRY(cudaStreamWaitEvent(st, se.done, 0));
                 a.jobs[a.n_jobs++] = MatchJob{se.centers, se.d_n, se.cap, o.disp, o.ncc, o.valid};
             }
             nrr_status r = launch_match(a, st);
             if (r != NRR_OK) return r;
+        }
+        for (int s_ : G.settings) {
+            const SettingOut &o = b->outs[s_];
+            if (o.src == s_) continue;
+            const SettingOut &m = b->outs[o.src];
+            const SelEntry &se = b->sels[o.sel], &sm = b->sels[m.sel];
+            NRR_CUDA_TRY(cudaStreamWaitEvent(st, se.done, 0));
+            const int grid = (se.cap + 255) / 256;
+            gather_nested_kernel<<<grid < 1 ? 1 : grid, 256, 0, st>>>(
+                se.centers, se.d_n, se.cap, sm.centers, sm.d_n, sm.cap, b->dims.nx, b->dims.ny, m.disp, m.ncc,
+                m.valid, o.disp, o.ncc, o.valid, b->err);
+            NRR_CUDA_TRY(cudaGetLastError());
+            count_launches(1);
         }
     }
     for (int k = 0; k < NSTREAMS; ++k) {
@@ -275,6 +338,19 @@ nrr_status nrr_batch_create(const uint16_t *d_preop, const uint16_t *d_intraop, 
             b->groups.push_back(g);
         }
         b->groups[grp_of[gk]].settings.push_back(i);
+    }
+    // per (block, stride, radius): the setting with the largest fraction is
+    // matched, the others gather from it (their selections are nested in it)
+    std::map<std::tuple<int, int, int, int, int>, int> unit_of;
+    for (int i = 0; i < n_settings; ++i) {
+        const nrr_setting &s = settings[i];
+        auto uk = std::make_tuple(s.block, s.stride, s.radius[0], s.radius[1], s.radius[2]);
+        auto it = unit_of.find(uk);
+        if (it == unit_of.end() || settings[it->second].frac < s.frac) unit_of[uk] = i;
+    }
+    for (int i = 0; i < n_settings; ++i) {
+        const nrr_setting &s = settings[i];
+        b->outs[i].src = unit_of[std::make_tuple(s.block, s.stride, s.radius[0], s.radius[1], s.radius[2])];
     }
     for (int k = 0; k < NSTREAMS; ++k) {
         if (cudaStreamCreateWithFlags(&b->streams[k], cudaStreamNonBlocking) != cudaSuccess ||
