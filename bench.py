@@ -54,7 +54,8 @@ def _args():
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-highres", action="store_true")
     p.add_argument("--no-spacing", action="store_true")
-    p.add_argument("--serve-open-requests", type=int, default=200)
+    p.add_argument("--serve-open-requests", type=int, default=400)
+    p.add_argument("--serve-sweep-requests", type=int, default=300)
     p.add_argument("--serve-closed-requests", type=int, default=300)
     return p.parse_args()
 
@@ -310,9 +311,10 @@ def _serving(a, nrr, synth, dev):
     """The served stream: Poisson arrivals (mean 20 requests/s) of
     registrations of three volume sizes with random (block, radius,
     fraction); volumes resident on the device.  Reports p50/p99 latency
-    (submission to completion on the device) and registrations/s, plus a
-    saturation run (all requests queued at once) served with 8 slots against
-    one-at-a-time FIFO service (1 slot)."""
+    (submission to completion on the device) and registrations/s, the same
+    for arrival rates from 100 to 1600 requests/s, and a saturation run (all
+    requests queued at once) served with 8 slots against one-at-a-time FIFO
+    service (1 slot)."""
     import numpy as np
     import torch
 
@@ -358,6 +360,12 @@ def _serving(a, nrr, synth, dev):
                        "radius 3..7, fraction 2..10%, stride 2, volumes resident on the device",
            "latency": "submission to completion on the device (host callback timestamp)"}
     out["open_loop_20rps"] = run(reqs_open, 8, True)
+    # arrival-rate sweep up to saturation (same request mix, fresh arrivals)
+    sweep = {}
+    for rate in (100.0, 200.0, 400.0, 800.0, 1600.0):
+        reqs = synth.poisson_arrivals(a.serve_sweep_requests, rate, seed=synth.SEED_BASE + 20 + int(rate))
+        sweep[f"{rate:g}rps"] = run(reqs, 8, True)
+    out["open_loop_rate_sweep"] = sweep
     reqs_closed = [(0.0, si, b, r, f) for (_, si, b, r, f) in synth.poisson_arrivals(a.serve_closed_requests, 20.0,
                                                                                       seed=synth.SEED_BASE + 11)]
     out["saturated_served_8_slots"] = run(reqs_closed, 8, False)
