@@ -438,6 +438,29 @@ def _spacing(a, nrr, synth, d_pre, d_mask, w, flush):
     return out
 
 
+def _phases(w, select_ms, box_ms, match_ms, peaks):
+    """Device time of the three phases of a step (CUDA events on the launching
+    stream, averaged over the timed steps) and, for the two HBM-type phases,
+    algorithmic bytes over time against the measured copy bandwidth:
+    selection reads the volume (2 B/voxel) and the mask (1 B/voxel) and
+    writes one 8-byte key per grid point (plus passes over the keys, not
+    counted); box sums read 2 B and write 8 B per voxel."""
+    nv = w.dims[0] * w.dims[1] * w.dims[2]
+    ng = 1
+    for d in w.dims:
+        ng *= -(-d // w.stride)
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    sel_s = sum(select_ms) / len(select_ms) / 1e3
+    box_s = sum(box_ms) / len(box_ms) / 1e3
+    sel_b, box_b = 3 * nv + 8 * ng, 10 * nv
+    return {"selection_ms": 1e3 * sel_s, "box_sums_ms": 1e3 * box_s,
+            "match_ms": 1e3 * sum(match_ms) / len(match_ms),
+            "selection_hbm": {"algorithmic_bytes": sel_b, "achieved_gbs": sel_b / sel_s / 1e9,
+                              "frac_of_measured_hbm": sel_b / sel_s / 1e9 / hbm},
+            "box_sums_hbm": {"algorithmic_bytes": box_b, "achieved_gbs": box_b / box_s / 1e9,
+                             "frac_of_measured_hbm": box_b / box_s / 1e9 / hbm}}
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -470,15 +493,18 @@ def run_ours(a):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(p, i, m, ev_match=None):
+    def step(p, i, m, ev_phase=None):
+        # ev_phase: events after selection, after box sums, after matching
         nrr.select_blocks(p, m, w.block, w.stride, w.frac, max_blocks=cap, centers=centers, n_selected=n_sel,
                           sync=False)
+        if ev_phase is not None:
+            ev_phase[0].record(stream)
         box = nrr.boxsums(i, w.block, out=box_raw)
-        if ev_match is not None:
-            ev_match[0].record(stream)
+        if ev_phase is not None:
+            ev_phase[1].record(stream)
         nrr.block_match(p, i, centers, w.block, w.radius, n_blocks=n_sel, box=box, out=out)
-        if ev_match is not None:
-            ev_match[1].record(stream)
+        if ev_phase is not None:
+            ev_phase[2].record(stream)
 
     for _ in range(max(3, a.warmup)):
         flush.fill_(1)
@@ -489,7 +515,7 @@ def run_ours(a):
     valid_count = int(out[2][:n_blocks].sum().item())
 
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
-    evm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    evm = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(a.steps)]
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
@@ -508,7 +534,9 @@ def run_ours(a):
     if pg:
         pg.barrier()
     step_ms = [s.elapsed_time(e) for s, e in evs]
-    match_ms = [s.elapsed_time(e) for s, e in evm]
+    select_ms = [s.elapsed_time(p[0]) for (s, _), p in zip(evs, evm)]
+    box_ms = [p[0].elapsed_time(p[1]) for p in evm]
+    match_ms = [p[1].elapsed_time(p[2]) for p in evm]
     total_s, value = aggregate_replicas(sum(step_ms) / 1e3, world, a.steps * evals, pg)
 
     # ---- end to end through the public API with host buffers --------------
@@ -616,6 +644,7 @@ def run_ours(a):
                      "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
                                    f"{sm_max:.0f} MHz (max SM clock)",
                      "match_ms": 1e3 * match_s},
+        "phases": _phases(w, select_ms, box_ms, match_ms, peaks),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
                 "pipelining": "each step's inputs copied from pinned host memory and results copied back inside "
                               "the timed region, overlapped with the neighbouring steps' compute (3 streams)",
