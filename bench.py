@@ -454,7 +454,7 @@ def _phases(w, select_ms, box_ms, match_ms, peaks):
     box_s = sum(box_ms) / len(box_ms) / 1e3
     sel_b, box_b = 3 * nv + 8 * ng, 10 * nv
     return {"selection_ms": 1e3 * sel_s, "box_sums_ms": 1e3 * box_s,
-            "match_ms": 1e3 * sum(match_ms) / len(match_ms),
+            "match_ms": sum(match_ms) / len(match_ms),
             "selection_hbm": {"algorithmic_bytes": sel_b, "achieved_gbs": sel_b / sel_s / 1e9,
                               "frac_of_measured_hbm": sel_b / sel_s / 1e9 / hbm},
             "box_sums_hbm": {"algorithmic_bytes": box_b, "achieved_gbs": box_b / box_s / 1e9,

@@ -72,14 +72,31 @@ def test_batch_equals_single_calls(nrr, pair, graph):
 
 def test_batch_more_jobs_than_one_launch_holds(nrr, pair):
     pre, intra, mask, dpre, dintra, dmask = pair
-    fr = [0.02 + 0.005 * k for k in range(18)]  # 18 selections of one (b, R) variant: two launches
-    settings = [(5, 2, 2, f) for f in fr]
+    # 18 strides: 18 matched selections of one (b, R) variant, so two launches
+    settings = [(5, st, 2, 0.3) for st in range(1, 19)]
     plan = nrr.BatchPlan(dpre, dintra, dmask, settings, graph=True)
     plan.run()
     torch.cuda.synchronize()
-    for i in (0, 15, 16, 17):
+    nrr.device_status()
+    for i in (0, 1, 15, 16, 17):
         got = [t.cpu().numpy() for t in plan.result(i)]
         assert _same(got, _single(nrr, dpre, dintra, dmask, settings[i]))
+    plan.close()
+
+
+def test_batch_nested_fractions_share_one_match(nrr, pair):
+    # fractions of one (b, stride, R) unit are matched once (the largest) and
+    # the others gathered from it: every one must equal its own single call
+    pre, intra, mask, dpre, dintra, dmask = pair
+    fr = [0.01, 0.02 + 0.005, 0.05, 0.05, 0.07, 0.02, 0.13]
+    settings = [(7, 2, (2, 3, 1), f) for f in fr] + [(7, 3, (2, 3, 1), f) for f in fr[:3]]
+    plan = nrr.BatchPlan(dpre, dintra, dmask, settings, graph=True)
+    plan.run()
+    torch.cuda.synchronize()
+    nrr.device_status()
+    for i, s in enumerate(settings):
+        got = [t.cpu().numpy() for t in plan.result(i)]
+        assert _same(got, _single(nrr, dpre, dintra, dmask, s)), (i, s)
     plan.close()
 
 
