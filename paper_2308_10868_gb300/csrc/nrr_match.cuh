@@ -60,6 +60,7 @@ struct MatchParams {
     int ry, rz;
     int wyp;  // rows per plane of the window box (>= window height)
     int n_jobs;
+    int single_window;  // one window buffer: the next block's copy is issued once this block's window is read
     MatchJob jobs[MATCH_MAX_JOBS];
     unsigned int *err;
 };
@@ -129,16 +130,22 @@ struct MatchLayout {
     int u[2], ut[2], t, surv, sc, bar, total;
 };
 
-// Shared-memory carve-up of one CTA (all offsets 128-byte aligned).
+// Shared-memory carve-up of one CTA (all offsets 128-byte aligned).  With
+// single_window the two blocks in flight share one window buffer (their
+// floating blocks stay double-buffered).
 __host__ __device__ inline MatchLayout match_layout(int elem, int B, int P, int bx, int btx, int wyp, int wz, int py,
-                                                   int pz)
+                                                   int pz, bool single_window = false)
 {
     MatchLayout L;
     const int pt = round_up_i(B, 4);
     int o = 0;
     for (int b = 0; b < 2; ++b) {
-        L.u[b] = o;
-        o += round_up_i(bx * wyp * wz * elem, 128);
+        if (single_window && b == 1) {
+            L.u[1] = L.u[0];
+        } else {
+            L.u[b] = o;
+            o += round_up_i(bx * wyp * wz * elem, 128);
+        }
         L.ut[b] = o;
         o += round_up_i(btx * B * B * elem, 128);
     }
@@ -304,7 +311,8 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
     const int nx = a.nx, ny = a.ny, nz = a.nz;
 
     extern __shared__ __align__(128) unsigned char smem[];
-    const MatchLayout L = match_layout((int)sizeof(T), B, P, BX, BTX, wyp, wz, py, pz);
+    const MatchLayout L = match_layout((int)sizeof(T), B, P, BX, BTX, wyp, wz, py, pz, a.single_window != 0);
+    const bool single = a.single_window != 0;
     float *Tm = reinterpret_cast<float *>(smem + L.t);
     uint16_t *surv = reinterpret_cast<uint16_t *>(smem + L.surv);
     MatchScratch *sc = reinterpret_cast<MatchScratch *>(smem + L.sc);
@@ -410,7 +418,9 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         }
         phase[b] ^= 1u;
         const int nb = next_inside(blk + gridDim.x);
-        if (nb < n && tid == 0) issue(nb, b ^ 1);  // buffer b^1 was released by the previous block's last barrier
+        // buffer b^1 was released by the previous block's last barrier; a
+        // shared window buffer is refilled only once this block has read it
+        if (!single && nb < n && tid == 0) issue(nb, b ^ 1);
 
         // ---- floating block statistics.  float32: every warp sums a share in
         // FP64 and every thread combines the per-warp partials; uint16: warp 0
@@ -527,6 +537,7 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
             tsh = 8388608.0f + (float)sc->bc.m;
         }
         if (flat) {  // flat floating block: NCC undefined for every shift
+            if (single && nb < n && tid == 0) issue(nb, b ^ 1);  // the window is not read
             if (tid == 0) write_result(J, bi, Cand{0.0, 0, 0, 0}, P, py, RX, ry, rz);
             __syncthreads();
             blk = nb;
@@ -687,6 +698,10 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         lbm = warp_max_f(lbm);
         if (lane == 0) sc->wlb[warp] = lbm;
         __syncthreads();
+        // float32 reads the window only in the search (its rescoring reads
+        // global memory): a shared window buffer is refilled from here
+        if constexpr (F32)
+            if (single && nb < n && tid == 0) issue(nb, b ^ 1);
         float LB = -INFINITY;
         for (int w = 0; w < nwarp; ++w) LB = fmaxf(LB, sc->wlb[w]);
         if (tid < lines) {
@@ -805,6 +820,8 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
             sc->bok[warp] = wb.ok;
         }
         __syncthreads();
+        if constexpr (!F32)  // uint16 rescoring read the window up to here
+            if (single && nb < n && tid == 0) issue(nb, b ^ 1);
         if (tid == 0) {
             Cand best{0.0, 0, 0, 0};
             for (int w = 0; w < nwarp; ++w) {
@@ -886,6 +903,40 @@ constexpr auto match_kernel_ptr()
         return match_kernel_u16<B, P>;
 }
 
+// Shared-memory layout of a launch: double-buffered windows, unless that
+// leaves three or fewer CTAs per SM and a single window buffer gives more
+// (the other CTAs then hide the exposed copy latency; measured on float32
+// windows: b = 9, R = 7 from 1 to 2 CTAs, 23% faster; b = 7, R = 5 from 3 to
+// 6 CTAs, 16% faster).
+template <typename T, int B, int P>
+nrr_status choose_layout(const MatchLaunch &m, MatchLayout *L, bool *single, int *occ)
+{
+    constexpr int ALIGN = 16 / (int)sizeof(T);
+    const int ry = m.radius[1], rz = m.radius[2], py = 2 * ry + 1, pz = 2 * rz + 1;
+    const int wyp = match_wyp(B + 2 * ry, py), threads = round_up_i(py * pz, 32);
+    const MatchLayout L2 = match_layout((int)sizeof(T), B, P, match_bx<T, B, P>(), round_up_c(B + ALIGN - 1, ALIGN),
+                                        wyp, B + 2 * rz, py, pz, false);
+    const MatchLayout L1 = match_layout((int)sizeof(T), B, P, match_bx<T, B, P>(), round_up_c(B + ALIGN - 1, ALIGN),
+                                        wyp, B + 2 * rz, py, pz, true);
+    auto kern = match_kernel_ptr<T, B, P>();
+    static int smem_set = 0;  // largest dynamic shared memory opted in so far
+    if (L2.total > smem_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L2.total);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(match_kernel)");
+        smem_set = L2.total;
+    }
+    int o2 = 0, o1 = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, kern, threads, L2.total);
+    if (e == cudaSuccess && o2 <= 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, kern, threads, L1.total);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    *single = o2 <= 3 && o1 > o2;
+    *L = *single ? L1 : L2;
+    *occ = *single ? o1 : o2;
+    return NRR_OK;
+}
+
 template <typename T, int B, int P>
 nrr_status launch_match_variant(const MatchLaunch &m, cudaStream_t stream)
 {
@@ -894,7 +945,6 @@ nrr_status launch_match_variant(const MatchLaunch &m, cudaStream_t stream)
     constexpr int BTX = round_up_c(B + ALIGN - 1, ALIGN);
     const int ry = m.radius[1], rz = m.radius[2], py = 2 * ry + 1, pz = 2 * rz + 1;
     const int wy = B + 2 * ry, wz = B + 2 * rz, wyp = match_wyp(wy, py);
-    const MatchLayout L = match_layout((int)sizeof(T), B, P, BX, BTX, wyp, wz, py, pz);
     const int threads = round_up_i(py * pz, 32);
     if (threads > MATCH_MAX_THREADS) return fail(NRR_E_INVALID, "search window too large");
     if (wyp > 256) return fail(NRR_E_INVALID, "search window too large");
@@ -906,17 +956,11 @@ nrr_status launch_match_variant(const MatchLaunch &m, cudaStream_t stream)
     if (st != NRR_OK) return st;
 
     auto kern = match_kernel_ptr<T, B, P>();
-    static int smem_set = 0;  // largest dynamic shared memory opted in so far
-    if (L.total > smem_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(match_kernel)");
-        smem_set = L.total;
-    }
+    MatchLayout L;
+    bool single = false;
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, L.total);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    st = choose_layout<T, B, P>(m, &L, &single, &occ);
+    if (st != NRR_OK) return st;
     if (occ < 1) return fail(NRR_E_INVALID, "match kernel does not fit on an SM (%d B shared)", L.total);
     if (m.ctas_per_sm > 0 && m.ctas_per_sm < occ) occ = m.ctas_per_sm;
     long long cap = 0;
@@ -937,10 +981,11 @@ nrr_status launch_match_variant(const MatchLaunch &m, cudaStream_t stream)
     p.rz = rz;
     p.wyp = wyp;
     p.n_jobs = m.n_jobs;
+    p.single_window = single ? 1 : 0;
     for (int j = 0; j < MATCH_MAX_JOBS; ++j) p.jobs[j] = j < m.n_jobs ? m.jobs[j] : MatchJob{};
     p.err = m.err;
     kern<<<(unsigned)grid, threads, L.total, stream>>>(p, mapJ, mapI);
-    e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "match kernel launch");
     count_launches(1);
     return NRR_OK;
@@ -949,18 +994,9 @@ nrr_status launch_match_variant(const MatchLaunch &m, cudaStream_t stream)
 template <typename T, int B, int P>
 nrr_status occupancy_variant(const MatchLaunch &m, int *occ)
 {
-    constexpr int ALIGN = 16 / (int)sizeof(T);
-    const int ry = m.radius[1], rz = m.radius[2], py = 2 * ry + 1, pz = 2 * rz + 1;
-    const int wyp = match_wyp(B + 2 * ry, py);
-    const MatchLayout L = match_layout((int)sizeof(T), B, P, match_bx<T, B, P>(), round_up_c(B + ALIGN - 1, ALIGN),
-                                       wyp, B + 2 * rz, py, pz);
-    auto kern = match_kernel_ptr<T, B, P>();
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, round_up_i(py * pz, 32), L.total);
-    if (e != cudaSuccess) return cuda_fail(e, "match occupancy query");
-    return NRR_OK;
+    MatchLayout L;
+    bool single = false;
+    return choose_layout<T, B, P>(m, &L, &single, occ);
 }
 
 template <typename T, int B>
