@@ -75,6 +75,7 @@ struct BlockConst {
     long long rr;   // uint16: N*m - S_I
     double dvI;     // float32: sum (I - Ibar)^2
     double ibar;    // float32: mean of I
+    float ibh, ibl; // float32: the mean as a float pair (ibh + ibl)
     float fvI;      // vI as float
     float frr;      // uint16: rr as float (exact: |rr| <= N/2)
     float kq;       // uint16: N*gamma_N*sqrt(sum T^2); float32: sqrt(sum T^2) (rounded up)
@@ -198,6 +199,61 @@ __device__ __forceinline__ V warp_sum(V v)
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+
+// Float-float sums (a value h + l with |l| <= ulp(h)/2): the float32 path's
+// statistics and rescoring accumulate in pairs of floats on the FP32 pipe
+// instead of in FP64 (narrow on this part).  Products of two floats are exact
+// as p + fma(x, y, -p); a sum is Knuth's branch-free two-sum of the high
+// parts, the low terms added, then renormalised (Dekker's fast two-sum), so
+// each step errs by about 2^-48 relative and sums of integers below 2^48 are
+// exact -- far below the 1e-6 NCC tolerance.
+struct FF {
+    float h, l;
+};
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ FF ff_norm(float s, float e)  // |s| >= |e|
+{
+    const float h = __fadd_rn(s, e);
+    return FF{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ FF ff_add(FF a, float b)
+{
+    float s, e;
+    two_sum(a.h, b, s, e);
+    return ff_norm(s, __fadd_rn(e, a.l));
+}
+__device__ __forceinline__ FF ff_add2(FF a, float b, float c)  // a + b + c, |c| tiny next to b
+{
+    float s, e;
+    two_sum(a.h, b, s, e);
+    return ff_norm(s, __fadd_rn(__fadd_rn(e, a.l), c));
+}
+__device__ __forceinline__ FF ff_add_prod(FF a, float x, float y)  // a + x*y
+{
+    const float p = __fmul_rn(x, y);
+    return ff_add2(a, p, __fmaf_rn(x, y, -p));
+}
+__device__ __forceinline__ FF ff_add_ff(FF a, FF b)
+{
+    float s, e;
+    two_sum(a.h, b.h, s, e);
+    return ff_norm(s, __fadd_rn(__fadd_rn(e, a.l), b.l));
+}
+__device__ __forceinline__ FF warp_sum_ff(FF v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        FF w{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
+        v = ff_add_ff(v, w);
+    }
+    return v;
+}
+__device__ __forceinline__ double ff_to_double(FF v) { return (double)v.h + (double)v.l; }
 
 // Exact uint16 -> float of (u - c) for u, c < 2^16: 0x4B000000|u is the float
 // 2^23 + u, so one integer OR and one float subtraction suffice.
@@ -428,7 +484,11 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         {
             constexpr int IPT = (N + 63) / 64;  // values per thread at 64+ threads
             if constexpr (F32) {
-                double s1 = 0.0, s2 = 0.0;
+                // sums of (I - I0) and (I - I0)^2 with I0 the block's first
+                // value (shifted data: the spread loses no digits to
+                // cancellation), in float-float; I - I0 is exact as dh + de
+                const float i0 = Ut[xot];
+                FF s1{0.f, 0.f}, s2{0.f, 0.f};
                 float lo = INFINITY, hi = -INFINITY;
                 for (int k0 = tid; k0 < N; k0 += IPT * nthr) {
                     float vals[IPT];
@@ -441,20 +501,22 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
 #pragma unroll
                     for (int q = 0; q < IPT; ++q)
                         if (k0 + q * nthr < N) {
-                            const double d = (double)vals[q];
-                            s1 += d;
-                            s2 = fma(d, d, s2);
+                            float dh, de;
+                            two_sum(vals[q], -i0, dh, de);
+                            s1 = ff_add2(s1, dh, de);
+                            const float p = __fmul_rn(dh, dh);  // (dh + de)^2; de^2 is below the pair's precision
+                            s2 = ff_add2(s2, p, __fmaf_rn(2.f * dh, de, __fmaf_rn(dh, dh, -p)));
                             lo = fminf(lo, vals[q]);
                             hi = fmaxf(hi, vals[q]);
                         }
                 }
-                s1 = warp_sum(s1);
-                s2 = warp_sum(s2);
+                s1 = warp_sum_ff(s1);
+                s2 = warp_sum_ff(s2);
                 lo = warp_min_f(lo);
                 hi = warp_max_f(hi);
                 if (lane == 0) {
-                    sc->pd1[warp] = s1;
-                    sc->pd2[warp] = s2;
+                    sc->pd1[warp] = ff_to_double(s1);
+                    sc->pd2[warp] = ff_to_double(s2);
                     sc->plo[warp] = lo;
                     sc->phi[warp] = hi;
                 }
@@ -508,17 +570,22 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                 lo = fminf(lo, sc->plo[w]);
                 hi = fmaxf(hi, sc->phi[w]);
             }
-            tsh = __fmul_rn(sf, 1.0f / (float)N);  // any float near the mean serves as the shift mu
+            // any float near the mean serves as the shift mu (the partials
+            // are sums of I - I0)
+            tsh = __fadd_rn(Ut[xot], __fmul_rn(sf, 1.0f / (float)N));
             flat = !(lo < hi);
             if (tid == 0 && !flat) {
-                double s1 = 0.0, s2 = 0.0;
+                double s1 = 0.0, s2 = 0.0;  // sums of (I - I0) and (I - I0)^2
                 for (int w = 0; w < nwarp; ++w) {
                     s1 += sc->pd1[w];
                     s2 += sc->pd2[w];
                 }
-                const double ibar = s1 / (double)N;
-                double dv = s2 - s1 * ibar;  // sum (I - Ibar)^2
+                const double i0 = (double)Ut[xot];
+                const double ibar = i0 + s1 / (double)N;
+                double dv = s2 - s1 * (s1 / (double)N);  // sum (I - Ibar)^2
                 if (dv < 0.0) dv = 0.0;
+                sc->bc.ibh = (float)ibar;
+                sc->bc.ibl = (float)(ibar - (double)sc->bc.ibh);
                 const double em = ibar - (double)tsh;
                 BlockConst &c = sc->bc;
                 c.ibar = ibar;
@@ -527,9 +594,10 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                 c.dvI = dv;
                 c.fvI = (float)dv;
                 // sum of T^2 with T = fl(I - mu): at most (1+u)^2 sum (I - mu)^2
-                // = (1+u)^2 (sum (I - Ibar)^2 + N (Ibar - mu)^2); the FP64
-                // one-pass spread is inexact by at most a few ulp of s2
-                c.kq = (float)(sqrt((dv + 64.0 * 1.1102230246251565e-16 * s2 + (double)N * em * em) * (1.0 + 2.4e-7)) *
+                // = (1+u)^2 (sum (I - Ibar)^2 + N (Ibar - mu)^2); the
+                // float-float sums (about 2^-48 relative per step, tens of
+                // steps) leave the spread inexact by well under 2048 ulp of s2
+                c.kq = (float)(sqrt((dv + 2048.0 * 1.1102230246251565e-16 * s2 + (double)N * em * em) * (1.0 + 2.4e-7)) *
                                (1.0 + 1e-6));
             }
         } else {
@@ -774,23 +842,27 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
             } else {
                 const float *pre = reinterpret_cast<const float *>(a.preop);
                 const float *intra = reinterpret_cast<const float *>(a.intraop);
-                double sij = 0.0, sj = 0.0, sjj = 0.0;
+                // float-float sums of (I - Ibar) J, J and J^2 (FP32 pipe)
+                FF fij{0.f, 0.f}, fj{0.f, 0.f}, fjj{0.f, 0.f};
                 float lo = INFINITY, hi = -INFINITY;
                 for (int k = kbeg + lane; k < kend; k += 32) {
                     const int kz = k / (B * B), rem = k - kz * B * B, ky = rem / B, kx = rem - ky * B;
-                    const double di =
-                        (double)pre[((size_t)(cz - H + kz) * ny + (cy - H + ky)) * nx + (cx - H + kx)] - bc.ibar;
+                    const float iv = pre[((size_t)(cz - H + kz) * ny + (cy - H + ky)) * nx + (cx - H + kx)];
                     const float jf = intra[((size_t)(cz + dz - H + kz) * ny + (cy + dy - H + ky)) * nx + (cx + dx - H + kx)];
-                    const double jd = (double)jf;
-                    sij = fma(di, jd, sij);
-                    sj += jd;
-                    sjj = fma(jd, jd, sjj);
+                    float dh, de;
+                    two_sum(iv, -bc.ibh, dh, de);  // I - Ibar = dh + dl, nearly exact
+                    const float dl = __fsub_rn(de, bc.ibl);
+                    const float p = __fmul_rn(dh, jf);
+                    fij = ff_add2(fij, p, __fmaf_rn(dl, jf, __fmaf_rn(dh, jf, -p)));
+                    fj = ff_add(fj, jf);
+                    fjj = ff_add_prod(fjj, jf, jf);
                     lo = fminf(lo, jf);
                     hi = fmaxf(hi, jf);
                 }
-                sij = warp_sum(sij);
-                sj = warp_sum(sj);
-                sjj = warp_sum(sjj);
+                fij = warp_sum_ff(fij);
+                fj = warp_sum_ff(fj);
+                fjj = warp_sum_ff(fjj);
+                const double sij = ff_to_double(fij), sj = ff_to_double(fj), sjj = ff_to_double(fjj);
                 lo = warp_min_f(lo);
                 hi = warp_max_f(hi);
                 if (lane == 0) {
