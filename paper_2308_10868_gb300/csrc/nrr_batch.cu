@@ -15,6 +15,11 @@
 //     depend on the fraction: only the largest fraction's blocks are
 //     matched, and every other setting of that unit gathers its blocks'
 //     results from them;
+//   - per (block, stride), a unit whose search box lies inside a matched
+//     unit's box and whose fraction is not larger is not matched either: the
+//     larger unit's job reports the best shift within the smaller box too
+//     (an extra radius level of the same search), and its settings gather
+//     from those results;
 //   - one persistent match launch per distinct (block, radius), whose job
 //     table holds the matched selection of every unit of that variant (up
 //     to 16 per launch);
@@ -52,12 +57,20 @@ struct BoxEntry {
     void *buf;
     cudaEvent_t done;
 };
-struct SettingOut {
-    int sel;
-    int src;  // setting whose matched blocks hold this one's results (itself if matched)
+struct LevelOut {  // an extra radius a matched setting's job reports
+    int r[3];
     int32_t *disp;
     double *ncc;
     uint8_t *valid;
+};
+struct SettingOut {
+    int sel;
+    int src;  // setting whose job holds this one's results (itself if matched)
+    int lvl;  // -1: src's own radius; else src's extra radius level
+    int32_t *disp;
+    double *ncc;
+    uint8_t *valid;
+    std::vector<LevelOut> levels;  // matched settings only
 };
 
 // Results of a nested selection from those of the larger one it is part of:
@@ -196,21 +209,30 @@ static nrr_status batch_enqueue(nrr_batch_s *b, cudaStream_t s)
                 const SettingOut &o = b->outs[matched[c]];
                 const SelEntry &se = b->sels[o.sel];
                 NRR_CUDA_TRY(cudaStreamWaitEvent(st, se.done, 0));
-                a.jobs[a.n_jobs++] = MatchJob{se.centers, se.d_n, se.cap, o.disp, o.ncc, o.valid};
+                MatchJob jb{se.centers, se.d_n, se.cap, o.disp, o.ncc, o.valid};
+                jb.n_levels = (int32_t)o.levels.size();
+                for (size_t l = 0; l < o.levels.size(); ++l)
+                    jb.levels[l] = MatchLevel{{o.levels[l].r[0], o.levels[l].r[1], o.levels[l].r[2]}, o.levels[l].disp,
+                                              o.levels[l].ncc, o.levels[l].valid};
+                a.jobs[a.n_jobs++] = jb;
             }
             nrr_status r = launch_match(a, st);
             if (r != NRR_OK) return r;
         }
-        for (int s_ : G.settings) {
+        // settings served by this group's jobs: gathered after the launches
+        for (size_t s_ = 0; s_ < b->outs.size(); ++s_) {
             const SettingOut &o = b->outs[s_];
-            if (o.src == s_) continue;
+            if (o.src == (int)s_ || std::find(matched.begin(), matched.end(), o.src) == matched.end()) continue;
             const SettingOut &m = b->outs[o.src];
             const SelEntry &se = b->sels[o.sel], &sm = b->sels[m.sel];
+            const int32_t *md = o.lvl < 0 ? m.disp : m.levels[o.lvl].disp;
+            const double *mn = o.lvl < 0 ? m.ncc : m.levels[o.lvl].ncc;
+            const uint8_t *mv = o.lvl < 0 ? m.valid : m.levels[o.lvl].valid;
             NRR_CUDA_TRY(cudaStreamWaitEvent(st, se.done, 0));
             const int grid = (se.cap + 255) / 256;
             gather_nested_kernel<<<grid < 1 ? 1 : grid, 256, 0, st>>>(
-                se.centers, se.d_n, se.cap, sm.centers, sm.d_n, sm.cap, b->dims.nx, b->dims.ny, m.disp, m.ncc,
-                m.valid, o.disp, o.ncc, o.valid, b->err);
+                se.centers, se.d_n, se.cap, sm.centers, sm.d_n, sm.cap, b->dims.nx, b->dims.ny, md, mn, mv, o.disp,
+                o.ncc, o.valid, b->err);
             NRR_CUDA_TRY(cudaGetLastError());
             count_launches(1);
         }
@@ -348,9 +370,57 @@ nrr_status nrr_batch_create(const uint16_t *d_preop, const uint16_t *d_intraop, 
         auto it = unit_of.find(uk);
         if (it == unit_of.end() || settings[it->second].frac < s.frac) unit_of[uk] = i;
     }
+    // per (block, stride): a unit whose radius box lies in a matched unit's
+    // box and whose fraction is not larger is served by that unit's job as an
+    // extra radius level (its blocks are among the larger unit's, and the
+    // search over the larger box contains the smaller one); units are taken
+    // largest box first
+    std::vector<int> prim;
+    for (auto &kv : unit_of) prim.push_back(kv.second);
+    auto vol = [&](int i) {
+        const nrr_setting &s = settings[i];
+        return (2 * s.radius[0] + 1) * (2 * s.radius[1] + 1) * (2 * s.radius[2] + 1);
+    };
+    std::sort(prim.begin(), prim.end(), [&](int x, int y) {
+        if (vol(x) != vol(y)) return vol(x) > vol(y);
+        if (settings[x].frac != settings[y].frac) return settings[x].frac > settings[y].frac;
+        return x < y;
+    });
+    std::map<int, std::pair<int, int>> served;  // unit primary -> (matched primary, level)
+    std::vector<int> launched;
+    for (int u : prim) {
+        const nrr_setting &su = settings[u];
+        int host = -1;
+        for (int a_ : launched) {
+            const nrr_setting &sa = settings[a_];
+            if (sa.block == su.block && sa.stride == su.stride && sa.frac >= su.frac &&
+                sa.radius[0] >= su.radius[0] && sa.radius[1] >= su.radius[1] && sa.radius[2] >= su.radius[2] &&
+                (int)b->outs[a_].levels.size() < MATCH_MAX_LEVELS) {
+                host = a_;
+                break;
+            }
+        }
+        if (host < 0) {
+            launched.push_back(u);
+            continue;
+        }
+        LevelOut lv{};
+        for (int k = 0; k < 3; ++k) lv.r[k] = su.radius[k];
+        const int32_t hcap = b->sels[b->outs[host].sel].cap;
+        void *p;
+        if ((st = batch_alloc(b, (size_t)hcap * (12 + 8 + 1) + 512, &p)) != NRR_OK) return bail(st);
+        lv.ncc = (double *)p;
+        lv.disp = (int32_t *)((char *)p + align_up((size_t)hcap * 8, 256));
+        lv.valid = (uint8_t *)((char *)lv.disp + align_up((size_t)hcap * 12, 256));
+        b->outs[host].levels.push_back(lv);
+        served[u] = std::make_pair(host, (int)b->outs[host].levels.size() - 1);
+    }
     for (int i = 0; i < n_settings; ++i) {
         const nrr_setting &s = settings[i];
-        b->outs[i].src = unit_of[std::make_tuple(s.block, s.stride, s.radius[0], s.radius[1], s.radius[2])];
+        const int u = unit_of[std::make_tuple(s.block, s.stride, s.radius[0], s.radius[1], s.radius[2])];
+        auto it = served.find(u);
+        b->outs[i].src = it == served.end() ? u : it->second.first;
+        b->outs[i].lvl = it == served.end() ? -1 : it->second.second;
     }
     for (int k = 0; k < NSTREAMS; ++k) {
         if (cudaStreamCreateWithFlags(&b->streams[k], cudaStreamNonBlocking) != cudaSuccess ||

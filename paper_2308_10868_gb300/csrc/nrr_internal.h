@@ -67,6 +67,15 @@ nrr_status launch_keys_box(const uint16_t *d_preop, const uint8_t *d_mask, nrr_d
 // MATCH_MAX_JOBS lists of blocks that share the volume pair, block size and
 // search radius (one job per registration or per parameter setting).
 constexpr int MATCH_MAX_JOBS = 16;
+// Extra search radii a job reports besides its own (batched search): the
+// best shift within a smaller box [-r, r] per axis, from the same search.
+constexpr int MATCH_MAX_LEVELS = 4;
+struct MatchLevel {
+    int32_t r[3];
+    int32_t *disp;
+    double *ncc;
+    uint8_t *valid;
+};
 struct MatchJob {
     const int32_t *centers;  // [cap][3]
     const int32_t *d_n;      // optional device count (<= cap)
@@ -74,6 +83,8 @@ struct MatchJob {
     int32_t *disp;
     double *ncc;
     uint8_t *valid;
+    int32_t n_levels;  // 0 .. MATCH_MAX_LEVELS
+    MatchLevel levels[MATCH_MAX_LEVELS];
 };
 struct MatchLaunch {
     const void *preop;

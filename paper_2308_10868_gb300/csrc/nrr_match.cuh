@@ -101,6 +101,15 @@ struct MatchScratch {
     float rlo[MATCH_MAX_WARPS], rhi[MATCH_MAX_WARPS];
 };
 
+// Extra radius levels (level-aware kernel only): per-warp lower bounds and
+// per-warp best survivors of each level.
+struct MatchLevelScratch {
+    float wlbl[MATCH_MAX_LEVELS][MATCH_MAX_WARPS];
+    double lbs[MATCH_MAX_LEVELS][MATCH_MAX_WARPS];
+    int lbn2[MATCH_MAX_LEVELS][MATCH_MAX_WARPS], lbcode[MATCH_MAX_LEVELS][MATCH_MAX_WARPS],
+        lbok[MATCH_MAX_LEVELS][MATCH_MAX_WARPS];
+};
+
 __host__ __device__ constexpr int round_up_c(int v, int a) { return (v + a - 1) / a * a; }
 __host__ __device__ inline int round_up_i(int v, int a) { return (v + a - 1) / a * a; }
 
@@ -128,14 +137,14 @@ __host__ __device__ inline int match_wyp(int wy, int py)
 }
 
 struct MatchLayout {
-    int u[2], ut[2], t, surv, sc, bar, total;
+    int u[2], ut[2], t, surv, sc, lsc, bar, total;
 };
 
 // Shared-memory carve-up of one CTA (all offsets 128-byte aligned).  With
 // single_window the two blocks in flight share one window buffer (their
-// floating blocks stay double-buffered).
+// floating blocks stay double-buffered); `levels` adds the level scratch.
 __host__ __device__ inline MatchLayout match_layout(int elem, int B, int P, int bx, int btx, int wyp, int wz, int py,
-                                                   int pz, bool single_window = false)
+                                                   int pz, bool single_window, bool levels)
 {
     MatchLayout L;
     const int pt = round_up_i(B, 4);
@@ -156,6 +165,8 @@ __host__ __device__ inline MatchLayout match_layout(int elem, int B, int P, int 
     o += round_up_i(P * py * pz * 2, 128);
     L.sc = o;
     o += round_up_i((int)sizeof(MatchScratch), 128);
+    L.lsc = o;
+    if (levels) o += round_up_i((int)sizeof(MatchLevelScratch), 128);
     L.bar = o;
     o += 128;
     L.total = o;
@@ -262,23 +273,42 @@ __device__ __forceinline__ float u16_minus(uint32_t u, float c_plus_2p23)
     return __fsub_rn(__uint_as_float(0x4B000000u | u), c_plus_2p23);
 }
 
-__device__ __forceinline__ void write_result(const MatchJob &a, int blk, const Cand &b, int P, int py, int rx, int ry,
-                                             int rz)
+__device__ __forceinline__ void write_out(int32_t *disp, double *ncc, uint8_t *valid, int blk, const Cand &b, int P,
+                                          int py, int rx, int ry, int rz)
 {
     if (b.ok) {
         int dxi = b.code % P, dyi = (b.code / P) % py, dzi = b.code / (P * py);
-        a.disp[3 * blk + 0] = dxi - rx;
-        a.disp[3 * blk + 1] = dyi - ry;
-        a.disp[3 * blk + 2] = dzi - rz;
-        a.ncc[blk] = b.s;
-        a.valid[blk] = 1;
+        disp[3 * blk + 0] = dxi - rx;
+        disp[3 * blk + 1] = dyi - ry;
+        disp[3 * blk + 2] = dzi - rz;
+        ncc[blk] = b.s;
+        valid[blk] = 1;
     } else {
-        a.disp[3 * blk + 0] = 0;
-        a.disp[3 * blk + 1] = 0;
-        a.disp[3 * blk + 2] = 0;
-        a.ncc[blk] = __longlong_as_double(0x7ff8000000000000ll);
-        a.valid[blk] = 0;
+        disp[3 * blk + 0] = 0;
+        disp[3 * blk + 1] = 0;
+        disp[3 * blk + 2] = 0;
+        ncc[blk] = __longlong_as_double(0x7ff8000000000000ll);
+        valid[blk] = 0;
     }
+}
+__device__ __forceinline__ void write_result(const MatchJob &a, int blk, const Cand &b, int P, int py, int rx, int ry,
+                                             int rz)
+{
+    write_out(a.disp, a.ncc, a.valid, blk, b, P, py, rx, ry, rz);
+}
+// A block with no candidate shift: invalid in its own radius and every level.
+__device__ __forceinline__ void write_invalid(const MatchJob &a, int blk, int P, int py, int rx, int ry, int rz)
+{
+    const Cand none{0.0, 0, 0, 0};
+    write_out(a.disp, a.ncc, a.valid, blk, none, P, py, rx, ry, rz);
+    for (int l = 0; l < a.n_levels; ++l)
+        write_out(a.levels[l].disp, a.levels[l].ncc, a.levels[l].valid, blk, none, P, py, rx, ry, rz);
+}
+// Shift `code` (x fastest, P x-shifts, py y-shifts) lies in level box r.
+__device__ __forceinline__ bool in_level(int code, const int32_t (&r)[3], int P, int py, int rx, int ry, int rz)
+{
+    const int dx = code % P - rx, dy = (code / P) % py - ry, dz = code / (P * py) - rz;
+    return abs(dx) <= r[0] && abs(dy) <= r[1] && abs(dz) <= r[2];
 }
 
 template <int H>
@@ -346,9 +376,11 @@ __device__ __forceinline__ void search_line(const T *row0, int zstride, const fl
     }
 }
 
-// The kernel body; the two __global__ entries below differ only in their
+// The kernel body; the __global__ entries below differ only in their
 // register budget.  `a`, `tmapJ` and `tmapI` live in kernel-parameter space.
-template <typename T, int B, int P>
+// LEV: the jobs may report extra radius levels (batched search); without it
+// that code is compiled out of the search's per-shift loops.
+template <typename T, int B, int P, bool LEV>
 __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorMap *tmapJ, const CUtensorMap *tmapI)
 {
     constexpr bool F32 = std::is_same<T, float>::value;
@@ -367,11 +399,12 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
     const int nx = a.nx, ny = a.ny, nz = a.nz;
 
     extern __shared__ __align__(128) unsigned char smem[];
-    const MatchLayout L = match_layout((int)sizeof(T), B, P, BX, BTX, wyp, wz, py, pz, a.single_window != 0);
+    const MatchLayout L = match_layout((int)sizeof(T), B, P, BX, BTX, wyp, wz, py, pz, a.single_window != 0, LEV);
     const bool single = a.single_window != 0;
     float *Tm = reinterpret_cast<float *>(smem + L.t);
     uint16_t *surv = reinterpret_cast<uint16_t *>(smem + L.surv);
     MatchScratch *sc = reinterpret_cast<MatchScratch *>(smem + L.sc);
+    MatchLevelScratch *ls = reinterpret_cast<MatchLevelScratch *>(smem + L.lsc);  // LEV only
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);  // [2]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nthr = blockDim.x, nwarp = nthr >> 5;
@@ -416,7 +449,7 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
             if (tid == 0) {
                 int j, i;
                 locate(w, j, i);
-                write_result(a.jobs[j], i, Cand{0.0, 0, 0, 0}, P, py, RX, ry, rz);
+                write_invalid(a.jobs[j], i, P, py, RX, ry, rz);
             }
         }
         return n;
@@ -467,7 +500,7 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         if (!__syncthreads_and(got)) {
             if (tid == 0) {
                 atomicOr(a.err, DEV_ERR_TIMEOUT);
-                write_result(J, bi, Cand{0.0, 0, 0, 0}, P, py, RX, ry, rz);
+                write_invalid(J, bi, P, py, RX, ry, rz);
             }
             mbar_wait_bounded(bar + b, phase[b], WAIT_LIMIT_NS);  // let an in-flight copy land before exiting
             return;
@@ -606,7 +639,7 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         }
         if (flat) {  // flat floating block: NCC undefined for every shift
             if (single && nb < n && tid == 0) issue(nb, b ^ 1);  // the window is not read
-            if (tid == 0) write_result(J, bi, Cand{0.0, 0, 0, 0}, P, py, RX, ry, rz);
+            if (tid == 0) write_invalid(J, bi, P, py, RX, ry, rz);
             __syncthreads();
             blk = nb;
             ++i;
@@ -653,6 +686,17 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         float ub[P];
         float lbm = -INFINITY;
         const int dyi = tid % py, dzi = tid / py;
+        const int nl = LEV ? J.n_levels : 0;  // extra radius levels of this block's job
+        float lbl[MATCH_MAX_LEVELS];
+        unsigned int lvl_line = 0;  // bit l: this thread's (dz, dy) line lies in level l
+        if constexpr (LEV) {
+#pragma unroll
+            for (int l = 0; l < MATCH_MAX_LEVELS; ++l) {
+                lbl[l] = -INFINITY;
+                if (l < nl && tid < lines && abs(dyi - ry) <= J.levels[l].r[1] && abs(dzi - rz) <= J.levels[l].r[2])
+                    lvl_line |= 1u << l;
+            }
+        }
         if (tid < lines) {
             const int dy = dyi - ry, dz = dzi - rz, Y = cy + dy, Z = cz + dz;
             const bool yz_ok = Y >= H && Y <= ny - 1 - H && Z >= H && Z <= nz - 1 - H;
@@ -722,6 +766,11 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                     e = 2.f * e + 1e-9f;
                     ub[p] = v + e;
                     lbm = fmaxf(lbm, v - e);
+                    if (LEV && lvl_line) {
+#pragma unroll
+                        for (int l = 0; l < MATCH_MAX_LEVELS; ++l)
+                            if (((lvl_line >> l) & 1u) && abs(p - RX) <= J.levels[l].r[0]) lbl[l] = fmaxf(lbl[l], v - e);
+                    }
                 } else {
                     constexpr float GS = (float)(3.0 * B * 5.9604644775390625e-08 /
                                                  (1.0 - 3.0 * B * 5.9604644775390625e-08));  // box-sum depth
@@ -758,6 +807,11 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                     e = 2.f * e + 1e-9f;
                     ub[p] = v + e;
                     lbm = fmaxf(lbm, v - e);
+                    if (LEV && lvl_line) {
+#pragma unroll
+                        for (int l = 0; l < MATCH_MAX_LEVELS; ++l)
+                            if (((lvl_line >> l) & 1u) && abs(p - RX) <= J.levels[l].r[0]) lbl[l] = fmaxf(lbl[l], v - e);
+                    }
                 }
             }
         }
@@ -765,6 +819,16 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         // ---- best lower bound over the window; survivors ------------------
         lbm = warp_max_f(lbm);
         if (lane == 0) sc->wlb[warp] = lbm;
+        if (LEV && nl) {
+#pragma unroll
+            for (int l = 0; l < MATCH_MAX_LEVELS; ++l) {
+                const float v = warp_max_f(lbl[l]);
+                if (lane == 0) {
+                    ls->wlbl[l][warp] = v;
+                    ls->lbok[l][warp] = 0;  // this warp's best survivor in level l: none yet
+                }
+            }
+        }
         __syncthreads();
         // float32 reads the window only in the search (its rescoring reads
         // global memory): a shared window buffer is refilled from here
@@ -772,10 +836,29 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
             if (single && nb < n && tid == 0) issue(nb, b ^ 1);
         float LB = -INFINITY;
         for (int w = 0; w < nwarp; ++w) LB = fmaxf(LB, sc->wlb[w]);
+        // a shift survives if it can be the best of the whole window or of
+        // a level box holding it
+        float LBl[MATCH_MAX_LEVELS];
+        if constexpr (LEV) {
+#pragma unroll
+            for (int l = 0; l < MATCH_MAX_LEVELS; ++l) {
+                LBl[l] = INFINITY;
+                if (l < nl) {
+                    LBl[l] = -INFINITY;
+                    for (int w = 0; w < nwarp; ++w) LBl[l] = fmaxf(LBl[l], ls->wlbl[l][w]);
+                }
+            }
+        }
         if (tid < lines) {
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                if (ub[p] > -INFINITY && ub[p] >= LB) {
+                bool lv = false;
+                if (LEV && lvl_line) {
+#pragma unroll
+                    for (int l = 0; l < MATCH_MAX_LEVELS; ++l)
+                        lv |= ((lvl_line >> l) & 1u) && abs(p - RX) <= J.levels[l].r[0] && ub[p] >= LBl[l];
+                }
+                if (ub[p] > -INFINITY && (ub[p] >= LB || lv)) {
                     int s = atomicAdd(&sc->nsurv, 1);
                     surv[s] = (uint16_t)((dzi * py + dyi) * P + p);
                 }
@@ -883,7 +966,20 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                     }
                 }
             }
-            if (lane == 0 && parts == 1 && cand_better(c, wb)) wb = c;
+            if (lane == 0 && parts == 1) {
+                if (cand_better(c, wb)) wb = c;
+                if constexpr (LEV)
+                    for (int l = 0; l < nl; ++l)
+                    if (in_level(code, J.levels[l].r, P, py, RX, ry, rz)) {
+                        const Cand cur{ls->lbs[l][warp], ls->lbn2[l][warp], ls->lbcode[l][warp], ls->lbok[l][warp]};
+                        if (cand_better(c, cur)) {
+                            ls->lbs[l][warp] = c.s;
+                            ls->lbn2[l][warp] = c.n2;
+                            ls->lbcode[l][warp] = c.code;
+                            ls->lbok[l][warp] = c.ok;
+                        }
+                    }
+            }
         }
         if (lane == 0) {
             sc->bs[warp] = wb.s;
@@ -896,9 +992,17 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
             if (single && nb < n && tid == 0) issue(nb, b ^ 1);
         if (tid == 0) {
             Cand best{0.0, 0, 0, 0};
+            Cand bestl[MATCH_MAX_LEVELS];
             for (int w = 0; w < nwarp; ++w) {
                 Cand c{sc->bs[w], sc->bn2[w], sc->bcode[w], sc->bok[w]};
                 if (cand_better(c, best)) best = c;
+            }
+            for (int l = 0; l < nl; ++l) {
+                bestl[l] = Cand{0.0, 0, 0, 0};
+                for (int w = 0; w < nwarp; ++w) {
+                    Cand c{ls->lbs[l][w], ls->lbn2[l][w], ls->lbcode[l][w], ls->lbok[l][w]};
+                    if (cand_better(c, bestl[l])) bestl[l] = c;
+                }
             }
             if (parts > 1) {
                 for (int si = 0; si < nsurv; ++si) {
@@ -925,9 +1029,13 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                         }
                     }
                     if (cand_better(c, best)) best = c;
+                    for (int l = 0; l < nl; ++l)
+                        if (in_level(code, J.levels[l].r, P, py, RX, ry, rz) && cand_better(c, bestl[l])) bestl[l] = c;
                 }
             }
             write_result(J, bi, best, P, py, RX, ry, rz);
+            for (int l = 0; l < nl; ++l)
+                write_out(J.levels[l].disp, J.levels[l].ncc, J.levels[l].valid, bi, bestl[l], P, py, RX, ry, rz);
         }
         __syncthreads();  // releases buffer b for the copies of the block after next
         blk = nb;
@@ -950,12 +1058,12 @@ struct MatchMinBlocks {
     static constexpr int value = (P <= 11 && B <= 7) ? 3 : 2;
 };
 
-template <int B, int P>
+template <int B, int P, bool LEV>
 __global__ void __maxnreg__((MatchRegs<B, P>::value))
     match_kernel_u16(const __grid_constant__ MatchParams a, const __grid_constant__ CUtensorMap tmapJ,
                      const __grid_constant__ CUtensorMap tmapI)
 {
-    match_body<uint16_t, B, P>(a, &tmapJ, &tmapI);
+    match_body<uint16_t, B, P, LEV>(a, &tmapJ, &tmapI);
 }
 
 template <int B, int P>
@@ -963,16 +1071,16 @@ __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value
     match_kernel_f32(const __grid_constant__ MatchParams a, const __grid_constant__ CUtensorMap tmapJ,
                      const __grid_constant__ CUtensorMap tmapI)
 {
-    match_body<float, B, P>(a, &tmapJ, &tmapI);
+    match_body<float, B, P, false>(a, &tmapJ, &tmapI);
 }
 
-template <typename T, int B, int P>
+template <typename T, int B, int P, bool LEV>
 constexpr auto match_kernel_ptr()
 {
     if constexpr (std::is_same<T, float>::value)
-        return match_kernel_f32<B, P>;
+        return match_kernel_f32<B, P>;  // float32 jobs report no extra levels
     else
-        return match_kernel_u16<B, P>;
+        return match_kernel_u16<B, P, LEV>;
 }
 
 // Shared-memory layout of a launch: double-buffered windows, unless that
@@ -980,17 +1088,17 @@ constexpr auto match_kernel_ptr()
 // (the other CTAs then hide the exposed copy latency; measured on float32
 // windows: b = 9, R = 7 from 1 to 2 CTAs, 23% faster; b = 7, R = 5 from 3 to
 // 6 CTAs, 16% faster).
-template <typename T, int B, int P>
+template <typename T, int B, int P, bool LEV>
 nrr_status choose_layout(const MatchLaunch &m, MatchLayout *L, bool *single, int *occ)
 {
     constexpr int ALIGN = 16 / (int)sizeof(T);
     const int ry = m.radius[1], rz = m.radius[2], py = 2 * ry + 1, pz = 2 * rz + 1;
     const int wyp = match_wyp(B + 2 * ry, py), threads = round_up_i(py * pz, 32);
     const MatchLayout L2 = match_layout((int)sizeof(T), B, P, match_bx<T, B, P>(), round_up_c(B + ALIGN - 1, ALIGN),
-                                        wyp, B + 2 * rz, py, pz, false);
+                                        wyp, B + 2 * rz, py, pz, false, LEV);
     const MatchLayout L1 = match_layout((int)sizeof(T), B, P, match_bx<T, B, P>(), round_up_c(B + ALIGN - 1, ALIGN),
-                                        wyp, B + 2 * rz, py, pz, true);
-    auto kern = match_kernel_ptr<T, B, P>();
+                                        wyp, B + 2 * rz, py, pz, true, LEV);
+    auto kern = match_kernel_ptr<T, B, P, LEV>();
     static int smem_set = 0;  // largest dynamic shared memory opted in so far
     if (L2.total > smem_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L2.total);
@@ -1009,8 +1117,8 @@ nrr_status choose_layout(const MatchLaunch &m, MatchLayout *L, bool *single, int
     return NRR_OK;
 }
 
-template <typename T, int B, int P>
-nrr_status launch_match_variant(const MatchLaunch &m, cudaStream_t stream)
+template <typename T, int B, int P, bool LEV>
+nrr_status launch_match_variant_l(const MatchLaunch &m, cudaStream_t stream)
 {
     constexpr int ALIGN = 16 / (int)sizeof(T);
     constexpr int BX = match_bx<T, B, P>();
@@ -1027,11 +1135,11 @@ nrr_status launch_match_variant(const MatchLaunch &m, cudaStream_t stream)
     st = encode_volume_map(&mapI, m.preop, m.dtype, m.dims, BTX, B, B);
     if (st != NRR_OK) return st;
 
-    auto kern = match_kernel_ptr<T, B, P>();
+    auto kern = match_kernel_ptr<T, B, P, LEV>();
     MatchLayout L;
     bool single = false;
     int occ = 0;
-    st = choose_layout<T, B, P>(m, &L, &single, &occ);
+    st = choose_layout<T, B, P, LEV>(m, &L, &single, &occ);
     if (st != NRR_OK) return st;
     if (occ < 1) return fail(NRR_E_INVALID, "match kernel does not fit on an SM (%d B shared)", L.total);
     if (m.ctas_per_sm > 0 && m.ctas_per_sm < occ) occ = m.ctas_per_sm;
@@ -1063,12 +1171,26 @@ nrr_status launch_match_variant(const MatchLaunch &m, cudaStream_t stream)
     return NRR_OK;
 }
 
+// Launches whose jobs report extra radius levels use the level-aware kernel
+// (uint16 only: the batched search runs on uint16 volumes).
+template <typename T, int B, int P>
+nrr_status launch_match_variant(const MatchLaunch &m, cudaStream_t stream)
+{
+    bool lev = false;
+    for (int j = 0; j < m.n_jobs; ++j) lev |= m.jobs[j].n_levels > 0;
+    if (!lev) return launch_match_variant_l<T, B, P, false>(m, stream);
+    if constexpr (std::is_same<T, float>::value)
+        return fail(NRR_E_INTERNAL, "extra radius levels are not supported for float32 volumes");
+    else
+        return launch_match_variant_l<T, B, P, true>(m, stream);
+}
+
 template <typename T, int B, int P>
 nrr_status occupancy_variant(const MatchLaunch &m, int *occ)
 {
     MatchLayout L;
     bool single = false;
-    return choose_layout<T, B, P>(m, &L, &single, occ);
+    return choose_layout<T, B, P, false>(m, &L, &single, occ);
 }
 
 template <typename T, int B>

@@ -119,3 +119,27 @@ def test_autotune_keeps_results(nrr, pair):
     for i, s in enumerate(SETTINGS[:3]):
         assert _same([t.cpu().numpy() for t in plan.result(i)], _single(nrr, dpre, dintra, dmask, s))
     plan.close()
+
+
+def test_batch_smaller_radii_reported_by_the_larger_search(nrr, pair):
+    # units of one (b, stride) whose boxes nest: the largest box's job also
+    # reports the best shift within each smaller box (up to 4 extra levels;
+    # a fifth is matched by itself); every setting must equal its own call
+    pre, intra, mask, dpre, dintra, dmask = pair
+    radii = [(4, 4, 4), (3, 3, 3), (2, 2, 2), (1, 1, 1), (0, 0, 0), (3, 1, 2)]
+    settings = [(5, 2, r, 0.1) for r in radii] + [(5, 2, (2, 2, 2), 0.05), (5, 2, (4, 4, 4), 0.03)]
+    plan = nrr.BatchPlan(dpre, dintra, dmask, settings, graph=True)
+    for rep in range(2):
+        plan.run()
+        torch.cuda.synchronize()
+        nrr.device_status()
+        for i, s in enumerate(settings):
+            got = [t.cpu().numpy() for t in plan.result(i)]
+            assert _same(got, _single(nrr, dpre, dintra, dmask, s)), (rep, i, s)
+    # and directly against the oracle for one served level
+    b, st, r, f = settings[2]
+    rc, _ = oracle.select_blocks(pre, mask, b, st, f)
+    rd, rn, rv = oracle.match(pre, intra, rc, b, r)
+    c, d, n, v = [t.cpu().numpy() for t in plan.result(2)]
+    assert np.array_equal(c, rc) and np.array_equal(d, rd) and np.array_equal(v, rv)
+    plan.close()
