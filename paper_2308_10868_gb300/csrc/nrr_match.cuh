@@ -511,9 +511,9 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         // shared window buffer is refilled only once this block has read it
         if (!single && nb < n && tid == 0) issue(nb, b ^ 1);
 
-        // ---- floating block statistics.  float32: every warp sums a share in
-        // FP64 and every thread combines the per-warp partials; uint16: warp 0
-        // alone (exact integer sums, cheap) writes the block constants ----
+        // ---- floating block statistics.  Every warp sums a share (float32 in
+        // float-float, uint16 in exact integers) and every thread combines the
+        // per-warp partials after the barrier ----
         {
             constexpr int IPT = (N + 63) / 64;  // values per thread at 64+ threads
             if constexpr (F32) {
@@ -553,39 +553,29 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                     sc->plo[warp] = lo;
                     sc->phi[warp] = hi;
                 }
-            } else if (warp == 0) {  // uint16: one warp, exact integer sums
-                constexpr int KPL = (N + 31) / 32;
-                constexpr int CH = KPL < 6 ? KPL : 6;
+            } else {  // uint16: every warp sums a share (exact integer sums)
+                constexpr int KPT = (N + 63) / 64;
                 long long s1 = 0;
                 unsigned long long s2 = 0;
-#pragma unroll 1
-                for (int i0 = 0; i0 < KPL; i0 += CH) {
-                    uint32_t vals[CH];
 #pragma unroll
-                    for (int q = 0; q < CH; ++q) {
-                        const int k = lane + 32 * (i0 + q);
-                        const int kzy = k / B, kx = k - kzy * B;
-                        vals[q] = k < N ? (uint32_t)Ut[kzy * BTX + xot + kx] : 0u;
-                    }
-#pragma unroll
-                    for (int q = 0; q < CH; ++q) {
-                        s1 += vals[q];
-                        s2 += (unsigned long long)(vals[q] * vals[q]);
-                    }
+                for (int q = 0; q < KPT; ++q) {
+                    const int k = tid + q * nthr;
+                    const int kzy = k / B, kx = k - kzy * B;
+                    const uint32_t v = k < N ? (uint32_t)Ut[kzy * BTX + xot + kx] : 0u;
+                    s1 += v;
+                    s2 += (unsigned long long)(v * v);
+                }
+                for (int k = tid + KPT * nthr; k < N; k += nthr) {  // fewer than 64 threads
+                    const int kzy = k / B, kx = k - kzy * B;
+                    const uint32_t v = (uint32_t)Ut[kzy * BTX + xot + kx];
+                    s1 += v;
+                    s2 += (unsigned long long)(v * v);
                 }
                 s1 = warp_sum(s1);
                 s2 = warp_sum(s2);
                 if (lane == 0) {
-                    BlockConst &c = sc->bc;
-                    const long long vI = (long long)N * (long long)s2 - s1 * s1;
-                    const long long m = (long long)((2u * (uint32_t)s1 + (uint32_t)N) / (2u * (uint32_t)N));  // nearest integer to the mean
-                    const long long qt = (long long)s2 - 2 * m * s1 + (long long)N * m * m;  // sum (I-m)^2, exact
-                    c.vI = vI;
-                    c.m = (int)m;
-                    c.rr = (long long)N * m - s1;
-                    c.frr = (float)c.rr;
-                    c.fvI = (float)vI;
-                    c.kq = (float)((double)N * GAMMA_N * sqrt((double)qt) * (1.0 + 1e-6));
+                    reinterpret_cast<long long *>(sc->pd1)[warp] = s1;
+                    reinterpret_cast<long long *>(sc->pd2)[warp] = (long long)s2;
                 }
             }
         }
@@ -634,8 +624,32 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                                (1.0 + 1e-6));
             }
         } else {
-            flat = sc->bc.vI == 0;
-            tsh = 8388608.0f + (float)sc->bc.m;
+            // uint16: every thread adds the per-warp partials (exact) and
+            // derives the integer mean; thread 0 writes the block constants
+            long long s1 = 0, s2 = 0;
+            for (int w = 0; w < nwarp; ++w) {
+                s1 += reinterpret_cast<const long long *>(sc->pd1)[w];
+                s2 += reinterpret_cast<const long long *>(sc->pd2)[w];
+            }
+            const long long vI = (long long)N * s2 - s1 * s1;
+            const long long m = (long long)((2u * (uint32_t)s1 + (uint32_t)N) / (2u * (uint32_t)N));  // nearest integer to the mean
+            flat = vI == 0;
+            tsh = 8388608.0f + (float)(int)m;
+            if (tid == 0) {
+                BlockConst &c = sc->bc;
+                const long long qt = s2 - 2 * m * s1 + (long long)N * m * m;  // sum (I-m)^2, exact, below 2^48
+                c.vI = vI;
+                c.m = (int)m;
+                c.rr = (long long)N * m - s1;
+                c.frr = (float)(int)c.rr;
+                c.fvI = (float)vI;
+                // kq = N gamma_N sqrt(qt), rounded up in float (no FP64 on this
+                // path): qt < 2^48 becomes a float through two exact 24-bit
+                // halves and one rounding; the factor 1 + 4e-6 covers that
+                // rounding and the rounding of N gamma_N
+                const float qf = __fmaf_rn((float)(int)(qt >> 24), 16777216.f, (float)(int)(qt & 0xFFFFFF));
+                c.kq = __fmul_ru(__fmul_ru((float)((double)N * GAMMA_N), __fsqrt_ru(qf)), 1.000004f);
+            }
         }
         if (flat) {  // flat floating block: NCC undefined for every shift
             if (single && nb < n && tid == 0) issue(nb, b ^ 1);  // the window is not read
@@ -757,12 +771,19 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                     // sum (J - c)^2 = (v_J + S'_J^2) / N, rounded up: the
                     // rounded v_J and S'_J and three operations stay below 6u
                     const float s2p = __fmul_rn(__fmul_rn(__fmaf_rn(s1pf, s1pf, vjf), 1.0f / fN), 1.f + 16.f * U32);
-                    const float inv = __frsqrt_rn(__fmul_rn(bc.fvI, vjf));
+                    // rsqrt.approx and sqrt.approx (relative error below 2^-22
+                    // over the whole range) instead of the correctly rounded
+                    // forms: the factor 1 + 64u on the error terms and 40u|v|
+                    // for the centre value absorb their error
+                    float inv;
+                    asm("rsqrt.approx.f32 %0, %1;" : "=f"(inv) : "f"(__fmul_rn(bc.fvI, vjf)));
                     const float na = __fmul_rn(fN, acc[p]);
                     const float rs = __fmul_rn(bc.frr, s1pf);  // rr exact in float (|rr| <= N/2)
                     const float v = __fmul_rn(__fadd_rn(na, rs), inv);
-                    float e = bc.kq * __fsqrt_rn(s2p) * inv + 4.f * U32 * (fabsf(na) + fabsf(rs)) * inv +
-                              6.f * U32 * fabsf(v);
+                    float sq;
+                    asm("sqrt.approx.f32 %0, %1;" : "=f"(sq) : "f"(s2p));
+                    float e = (bc.kq * sq * inv + 4.f * U32 * (fabsf(na) + fabsf(rs)) * inv) * (1.f + 64.f * U32) +
+                              40.f * U32 * fabsf(v);
                     e = 2.f * e + 1e-9f;
                     ub[p] = v + e;
                     lbm = fmaxf(lbm, v - e);
