@@ -798,7 +798,9 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                     constexpr float GN = (float)GAMMA_N;
                     const float s1 = ps1[p];
                     const float s2 = fmaxf(ps2[p], 0.f);
-                    const float d1 = GS * __fsqrt_rn(fN * s2) * 1.01f;  // |S1 err| bound
+                    float d1;  // |S1 err| bound (the factor 1.01 covers sqrt.approx)
+                    asm("sqrt.approx.f32 %0, %1;" : "=f"(d1) : "f"(fN * s2));
+                    d1 = GS * d1 * 1.01f;
                     const float s1sq_n = __fmul_rn(__fmul_rn(s1, s1), 1.0f / fN);
                     const float vJa = __fsub_rn(s2, s1sq_n);
                     const float dv = GS * s2 + (2.f * fabsf(s1) + d1) * d1 / fN + 4.f * U32 * (s2 + s1sq_n);
@@ -815,16 +817,21 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                         ub[p] = INFINITY;
                         continue;
                     }
-                    const float inv = __frsqrt_rn(__fmul_rn(bc.fvI, vJa));
+                    // approximate rsqrt / sqrt as for uint16: 1 + 64u on the
+                    // error terms and 40u|v| absorb their error
+                    float inv, sq;
+                    asm("rsqrt.approx.f32 %0, %1;" : "=f"(inv) : "f"(__fmul_rn(bc.fvI, vJa)));
+                    asm("sqrt.approx.f32 %0, %1;" : "=f"(sq) : "f"(sj2));
                     const float A = acc[p];
                     const float es = __fmul_rn(bc.emu, s1p);
                     const float num = __fsub_rn(A, es);
                     const float v = __fmul_rn(num, inv);
-                    const float enum_ = (GN + 3.f * U32) * bc.kq * __fsqrt_rn(sj2) +
+                    const float enum_ = (GN + 3.f * U32) * bc.kq * sq +
                                         fabsf(bc.emu) * (fabsf(s1p) + d1 + 2.f * U32 * fN * fabsf(c_f)) * 1.01f +
                                         U32 * (fabsf(A) + fabsf(es));
-                    float e = enum_ * inv * (1.f + 0.7f * rho + 4.f * U32) +
-                              fabsf(num) * inv * (0.7f * rho + 6.f * U32) + 3.f * U32 * fabsf(v);
+                    float e = (enum_ * inv * (1.f + 0.7f * rho + 4.f * U32) + fabsf(num) * inv * (0.7f * rho + 6.f * U32)) *
+                                  (1.f + 64.f * U32) +
+                              43.f * U32 * fabsf(v);
                     e = 2.f * e + 1e-9f;
                     ub[p] = v + e;
                     lbm = fmaxf(lbm, v - e);
