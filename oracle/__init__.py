@@ -45,22 +45,34 @@ def lib():
         L.oracle_set_threads.argtypes = [i32]
         L.oracle_block_key.restype = i64
         L.oracle_block_key.argtypes = [P, i32, i32, i32, i32, i32, i32, i32]
+        L.oracle_block_key_3.restype = i64
+        L.oracle_block_key_3.argtypes = [P, i32, i32, i32, i32, i32, i32, i32, i32, i32]
         L.oracle_grid_keys.restype = i64
         L.oracle_grid_keys.argtypes = [P, P, i32, i32, i32, i32, i32, P]
+        L.oracle_grid_keys_3.restype = i64
+        L.oracle_grid_keys_3.argtypes = [P, P, i32, i32, i32, i32, i32, i32, i32, P]
         L.oracle_n_select.restype = i64
         L.oracle_n_select.argtypes = [i64, dbl]
         L.oracle_select_blocks.restype = i64
         L.oracle_select_blocks.argtypes = [P, P, i32, i32, i32, i32, i32, dbl, P, i64, P]
+        L.oracle_select_blocks_3.restype = i64
+        L.oracle_select_blocks_3.argtypes = [P, P, i32, i32, i32, i32, i32, i32, i32, dbl, P, i64, P]
         L.oracle_select_blocks_spaced.restype = i64
         L.oracle_select_blocks_spaced.argtypes = [P, P, i32, i32, i32, i32, i32, dbl, i32, P, i64, P]
         for name in ("oracle_ncc_u16", "oracle_pearson_u16", "oracle_pearson_f32"):
             f = getattr(L, name)
             f.restype = i32
             f.argtypes = [P, P, i32, i32, i32, i32, i32, i32, i32, i32, i32, i32, P]
+            f = getattr(L, name + "_3")
+            f.restype = i32
+            f.argtypes = [P, P, i32, i32, i32, i32, i32, i32, i32, i32, i32, i32, i32, i32, P]
         for name in ("oracle_match_u16", "oracle_match_f32"):
             f = getattr(L, name)
             f.restype = None
             f.argtypes = [P, P, i32, i32, i32, P, i64, i32, P, P, P, P]
+            f = getattr(L, name + "_3")
+            f.restype = None
+            f.argtypes = [P, P, i32, i32, i32, P, i64, P, P, P, P, P]
         _lib = L
     return _lib
 
@@ -74,6 +86,14 @@ def _dims(vol: np.ndarray):
     return nx, ny, nz
 
 
+def _block3(b):
+    """Block edges (bx, by, bz) from an int (cubic block) or a triple."""
+    if np.isscalar(b):
+        return (int(b),) * 3
+    bx, by, bz = (int(v) for v in b)
+    return bx, by, bz
+
+
 def num_threads() -> int:
     return int(lib().oracle_num_threads())
 
@@ -83,8 +103,11 @@ def set_threads(n: int) -> None:
 
 
 def block_key(vol, b, x, y, z) -> int:
+    """b: block edge, or (bx, by, bz)."""
     vol = np.ascontiguousarray(vol, dtype=np.uint16)
-    return int(lib().oracle_block_key(_p(vol), *_dims(vol), b, x, y, z))
+    if np.isscalar(b):
+        return int(lib().oracle_block_key(_p(vol), *_dims(vol), b, x, y, z))
+    return int(lib().oracle_block_key_3(_p(vol), *_dims(vol), *_block3(b), x, y, z))
 
 
 def grid_keys(preop, mask, b, stride):
@@ -93,7 +116,10 @@ def grid_keys(preop, mask, b, stride):
     nx, ny, nz = _dims(preop)
     g = (-(-nx // stride), -(-ny // stride), -(-nz // stride))
     keys = np.empty(g[2] * g[1] * g[0], dtype=np.int64)
-    nc = lib().oracle_grid_keys(_p(preop), _p(mask), nx, ny, nz, b, stride, _p(keys))
+    if np.isscalar(b):
+        nc = lib().oracle_grid_keys(_p(preop), _p(mask), nx, ny, nz, b, stride, _p(keys))
+    else:
+        nc = lib().oracle_grid_keys_3(_p(preop), _p(mask), nx, ny, nz, *_block3(b), stride, _p(keys))
     return keys.reshape(g[2], g[1], g[0]), int(nc)
 
 
@@ -102,7 +128,8 @@ def n_select(n_candidates: int, frac: float) -> int:
 
 
 def select_blocks(preop, mask, b, stride, frac):
-    """Returns (centers int32[n][3] (x,y,z) in raster order, n_candidates)."""
+    """b: block edge, or (bx, by, bz).  Returns (centers int32[n][3] (x,y,z)
+    in raster order, n_candidates)."""
     preop = np.ascontiguousarray(preop, dtype=np.uint16)
     mask = np.ascontiguousarray(mask, dtype=np.uint8)
     nx, ny, nz = _dims(preop)
@@ -110,8 +137,12 @@ def select_blocks(preop, mask, b, stride, frac):
     cap = max(1, ng)
     out = np.empty((cap, 3), dtype=np.int32)
     nc = C.c_int64(0)
-    n = lib().oracle_select_blocks(_p(preop), _p(mask), nx, ny, nz, b, stride, float(frac), _p(out), cap,
-                                   C.byref(nc))
+    if np.isscalar(b):
+        n = lib().oracle_select_blocks(_p(preop), _p(mask), nx, ny, nz, b, stride, float(frac), _p(out), cap,
+                                       C.byref(nc))
+    else:
+        n = lib().oracle_select_blocks_3(_p(preop), _p(mask), nx, ny, nz, *_block3(b), stride, float(frac),
+                                         _p(out), cap, C.byref(nc))
     return out[:n].copy(), int(nc.value)
 
 
@@ -133,8 +164,13 @@ def select_blocks_spaced(preop, mask, b, stride, frac, conn):
 def _ncc_at(fn, preop, intraop, b, c, d):
     nx, ny, nz = _dims(preop)
     v = C.c_double(0.0)
-    ok = fn(_p(preop), _p(intraop), nx, ny, nz, b, int(c[0]), int(c[1]), int(c[2]), int(d[0]), int(d[1]),
-            int(d[2]), C.byref(v))
+    if np.isscalar(b):
+        ok = fn(_p(preop), _p(intraop), nx, ny, nz, b, int(c[0]), int(c[1]), int(c[2]), int(d[0]), int(d[1]),
+                int(d[2]), C.byref(v))
+    else:
+        fn3 = getattr(lib(), fn.__name__ + "_3")
+        ok = fn3(_p(preop), _p(intraop), nx, ny, nz, *_block3(b), int(c[0]), int(c[1]), int(c[2]), int(d[0]),
+                 int(d[1]), int(d[2]), C.byref(v))
     return float(v.value) if ok else None
 
 
@@ -165,8 +201,8 @@ def _radius3(radius):
 
 def match(preop, intraop, centers, b, radius):
     """Exhaustive block matching.  uint16 volumes use the exact integer path,
-    float32 volumes the FP64 two-pass path.  Returns (disp int32[n][3],
-    ncc f64[n], valid u8[n])."""
+    float32 volumes the FP64 two-pass path; b is the block edge or (bx, by,
+    bz).  Returns (disp int32[n][3], ncc f64[n], valid u8[n])."""
     f32 = preop.dtype == np.float32
     dt = np.float32 if f32 else np.uint16
     preop = np.ascontiguousarray(preop, dtype=dt)
@@ -177,7 +213,12 @@ def match(preop, intraop, centers, b, radius):
     ncc = np.zeros(n, dtype=np.float64)
     valid = np.zeros(n, dtype=np.uint8)
     r = _radius3(radius)
-    fn = lib().oracle_match_f32 if f32 else lib().oracle_match_u16
     nx, ny, nz = _dims(preop)
-    fn(_p(preop), _p(intraop), nx, ny, nz, _p(centers), n, b, _p(r), _p(disp), _p(ncc), _p(valid))
+    if np.isscalar(b):
+        fn = lib().oracle_match_f32 if f32 else lib().oracle_match_u16
+        fn(_p(preop), _p(intraop), nx, ny, nz, _p(centers), n, b, _p(r), _p(disp), _p(ncc), _p(valid))
+    else:
+        fn = lib().oracle_match_f32_3 if f32 else lib().oracle_match_u16_3
+        bl = np.array(_block3(b), dtype=np.int32)
+        fn(_p(preop), _p(intraop), nx, ny, nz, _p(centers), n, _p(bl), _p(r), _p(disp), _p(ncc), _p(valid))
     return disp, ncc, valid

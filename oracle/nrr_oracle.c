@@ -23,7 +23,10 @@
  *     block (Sec. 3, the NCC equation).  The signed value is maximised.
  *   - Block edge b is odd, h = (b-1)/2; the search radius is given per axis
  *     and the shifts are d in [-R,R]^3 (Sec. 3, complexity bound; Sec. 5
- *     gives the half window size per anatomical axis).
+ *     gives the half window size per anatomical axis).  Sec. 5 counts twelve
+ *     tunable parameters, which holds only if the half block size is also
+ *     given per axis: the *_3 functions take the block edges (bx, by, bz),
+ *     each odd, N = bx*by*bz; the cubic functions are the case bx=by=bz=b.
  *   - A shift whose block leaves the volume, or whose reference block is
  *     flat (zero variance), is not a candidate.
  *   - Ties in NCC are broken by smaller |d|^2, then by (dz,dy,dx)
@@ -76,24 +79,26 @@ void oracle_set_threads(int n)
 #endif
 }
 
-/* Block of edge b centred at (x,y,z) lies inside the volume. */
-static int block_inside(int nx, int ny, int nz, int b, int64_t x, int64_t y, int64_t z)
+/* Block of edges (bx,by,bz) centred at (x,y,z) lies inside the volume. */
+static int block_inside(int nx, int ny, int nz, const int bl[3], int64_t x, int64_t y, int64_t z)
 {
-    int h = (b - 1) / 2;
-    return x - h >= 0 && y - h >= 0 && z - h >= 0 &&
-           x + h <= nx - 1 && y + h <= ny - 1 && z + h <= nz - 1;
+    int hx = (bl[0] - 1) / 2, hy = (bl[1] - 1) / 2, hz = (bl[2] - 1) / 2;
+    return x - hx >= 0 && y - hy >= 0 && z - hz >= 0 &&
+           x + hx <= nx - 1 && y + hy <= ny - 1 && z + hz <= nz - 1;
 }
 
-/* Exact variance key of the b^3 block at (x,y,z): N*sum(I^2) - (sum I)^2,
- * which equals N^2 times the population variance (Sec. 4.1). */
-int64_t oracle_block_key(const uint16_t *vol, int nx, int ny, int nz, int b, int x, int y, int z)
+/* Exact variance key of the bx*by*bz block at (x,y,z):
+ * N*sum(I^2) - (sum I)^2, which equals N^2 times the population variance
+ * (Sec. 4.1). */
+int64_t oracle_block_key_3(const uint16_t *vol, int nx, int ny, int nz, int bx, int by, int bz, int x, int y,
+                           int z)
 {
-    int h = (b - 1) / 2;
-    int64_t n = (int64_t)b * b * b, s = 0, q = 0;
+    int hx = (bx - 1) / 2, hy = (by - 1) / 2, hz = (bz - 1) / 2;
+    int64_t n = (int64_t)bx * by * bz, s = 0, q = 0;
     (void)nz;
-    for (int k = -h; k <= h; ++k)
-        for (int j = -h; j <= h; ++j)
-            for (int i = -h; i <= h; ++i) {
+    for (int k = -hz; k <= hz; ++k)
+        for (int j = -hy; j <= hy; ++j)
+            for (int i = -hx; i <= hx; ++i) {
                 int64_t v = vol[lin(x + i, y + j, z + k, nx, ny)];
                 s += v;
                 q += v * v;
@@ -101,11 +106,17 @@ int64_t oracle_block_key(const uint16_t *vol, int nx, int ny, int nz, int b, int
     return n * q - s * s;
 }
 
+int64_t oracle_block_key(const uint16_t *vol, int nx, int ny, int nz, int b, int x, int y, int z)
+{
+    return oracle_block_key_3(vol, nx, ny, nz, b, b, b, x, y, z);
+}
+
 /* Keys of every stride grid point, in raster order of the grid
  * (gz, gy, gx ascending).  Non-candidates get -1.  Returns N_c. */
-int64_t oracle_grid_keys(const uint16_t *preop, const uint8_t *mask, int nx, int ny, int nz,
-                         int b, int stride, int64_t *keys)
+int64_t oracle_grid_keys_3(const uint16_t *preop, const uint8_t *mask, int nx, int ny, int nz, int bx, int by,
+                           int bz, int stride, int64_t *keys)
 {
+    const int bl[3] = {bx, by, bz};
     int64_t gx = (nx + stride - 1) / stride, gy = (ny + stride - 1) / stride,
             gz = (nz + stride - 1) / stride, nc = 0;
 #pragma omp parallel for reduction(+ : nc) schedule(static)
@@ -113,14 +124,20 @@ int64_t oracle_grid_keys(const uint16_t *preop, const uint8_t *mask, int nx, int
         for (int64_t j = 0; j < gy; ++j)
             for (int64_t i = 0; i < gx; ++i) {
                 int64_t x = i * stride, y = j * stride, z = k * stride, g = (k * gy + j) * gx + i;
-                if (block_inside(nx, ny, nz, b, x, y, z) && mask[lin(x, y, z, nx, ny)] != 0) {
-                    keys[g] = oracle_block_key(preop, nx, ny, nz, b, (int)x, (int)y, (int)z);
+                if (block_inside(nx, ny, nz, bl, x, y, z) && mask[lin(x, y, z, nx, ny)] != 0) {
+                    keys[g] = oracle_block_key_3(preop, nx, ny, nz, bx, by, bz, (int)x, (int)y, (int)z);
                     nc += 1;
                 } else {
                     keys[g] = -1;
                 }
             }
     return nc;
+}
+
+int64_t oracle_grid_keys(const uint16_t *preop, const uint8_t *mask, int nx, int ny, int nz,
+                         int b, int stride, int64_t *keys)
+{
+    return oracle_grid_keys_3(preop, mask, nx, ny, nz, b, b, b, stride, keys);
 }
 
 typedef struct {
@@ -153,14 +170,14 @@ int64_t oracle_n_select(int64_t n_candidates, double frac)
 /* Variance-based block selection (Sec. 4.1).  Writes up to `cap` centres
  * (x,y,z) in raster order; returns the number selected (may exceed cap).
  * *n_candidates receives N_c. */
-int64_t oracle_select_blocks(const uint16_t *preop, const uint8_t *mask, int nx, int ny, int nz,
-                             int b, int stride, double frac, int32_t *centers, int64_t cap,
-                             int64_t *n_candidates)
+int64_t oracle_select_blocks_3(const uint16_t *preop, const uint8_t *mask, int nx, int ny, int nz, int bx,
+                               int by, int bz, int stride, double frac, int32_t *centers, int64_t cap,
+                               int64_t *n_candidates)
 {
     int64_t gx = (nx + stride - 1) / stride, gy = (ny + stride - 1) / stride,
             gz = (nz + stride - 1) / stride, ng = gx * gy * gz;
     int64_t *keys = (int64_t *)malloc(sizeof(int64_t) * (size_t)(ng > 0 ? ng : 1));
-    int64_t nc = oracle_grid_keys(preop, mask, nx, ny, nz, b, stride, keys);
+    int64_t nc = oracle_grid_keys_3(preop, mask, nx, ny, nz, bx, by, bz, stride, keys);
     keyed *pos = (keyed *)malloc(sizeof(keyed) * (size_t)(ng > 0 ? ng : 1));
     int64_t npos = 0;
     for (int64_t g = 0; g < ng; ++g)
@@ -184,6 +201,13 @@ int64_t oracle_select_blocks(const uint16_t *preop, const uint8_t *mask, int nx,
     free(pos);
     free(keys);
     return nsel;
+}
+
+int64_t oracle_select_blocks(const uint16_t *preop, const uint8_t *mask, int nx, int ny, int nz,
+                             int b, int stride, double frac, int32_t *centers, int64_t cap,
+                             int64_t *n_candidates)
+{
+    return oracle_select_blocks_3(preop, mask, nx, ny, nz, b, b, b, stride, frac, centers, cap, n_candidates);
 }
 
 /* Variance-based selection with a connectivity pattern (Sec. 4.1: blocks
@@ -256,16 +280,17 @@ int64_t oracle_select_blocks_spaced(const uint16_t *preop, const uint8_t *mask, 
  * (N^2 times covariance and variances: the common factor cancels) and the
  * single rounded expression  num / sqrt(vI * vJ).  Returns 0 and leaves
  * *ncc untouched when the shift is not a candidate. */
-int oracle_ncc_u16(const uint16_t *preop, const uint16_t *intraop, int nx, int ny, int nz, int b,
-                   int cx, int cy, int cz, int dx, int dy, int dz, double *ncc)
+int oracle_ncc_u16_3(const uint16_t *preop, const uint16_t *intraop, int nx, int ny, int nz, int bx, int by,
+                     int bz, int cx, int cy, int cz, int dx, int dy, int dz, double *ncc)
 {
-    if (!block_inside(nx, ny, nz, b, cx, cy, cz)) return 0;
-    if (!block_inside(nx, ny, nz, b, (int64_t)cx + dx, (int64_t)cy + dy, (int64_t)cz + dz)) return 0;
-    int h = (b - 1) / 2;
-    int64_t n = (int64_t)b * b * b, si = 0, sj = 0, sii = 0, sjj = 0, sij = 0;
-    for (int k = -h; k <= h; ++k)
-        for (int j = -h; j <= h; ++j)
-            for (int i = -h; i <= h; ++i) {
+    const int bl[3] = {bx, by, bz};
+    if (!block_inside(nx, ny, nz, bl, cx, cy, cz)) return 0;
+    if (!block_inside(nx, ny, nz, bl, (int64_t)cx + dx, (int64_t)cy + dy, (int64_t)cz + dz)) return 0;
+    int hx = (bx - 1) / 2, hy = (by - 1) / 2, hz = (bz - 1) / 2;
+    int64_t n = (int64_t)bx * by * bz, si = 0, sj = 0, sii = 0, sjj = 0, sij = 0;
+    for (int k = -hz; k <= hz; ++k)
+        for (int j = -hy; j <= hy; ++j)
+            for (int i = -hx; i <= hx; ++i) {
                 int64_t a = preop[lin(cx + i, cy + j, cz + k, nx, ny)];
                 int64_t c = intraop[lin(cx + dx + i, cy + dy + j, cz + dz + k, nx, ny)];
                 si += a;
@@ -281,30 +306,36 @@ int oracle_ncc_u16(const uint16_t *preop, const uint16_t *intraop, int nx, int n
     return 1;
 }
 
+int oracle_ncc_u16(const uint16_t *preop, const uint16_t *intraop, int nx, int ny, int nz, int b,
+                   int cx, int cy, int cz, int dx, int dy, int dz, double *ncc)
+{
+    return oracle_ncc_u16_3(preop, intraop, nx, ny, nz, b, b, b, cx, cy, cz, dx, dy, dz, ncc);
+}
+
 /* Definition path (Sec. 3 NCC equation, read as Pearson): means first, then
  * the centred cross and squared sums, all in FP64.  Inputs widened from the
  * given element type.  Used for float32 intensities and as a check of the
  * integer path. */
 static int pearson_generic(const void *preop, const void *intraop, int is_f32, int nx, int ny, int nz,
-                           int b, int cx, int cy, int cz, int dx, int dy, int dz, double *ncc)
+                           const int bl[3], int cx, int cy, int cz, int dx, int dy, int dz, double *ncc)
 {
-    if (!block_inside(nx, ny, nz, b, cx, cy, cz)) return 0;
-    if (!block_inside(nx, ny, nz, b, (int64_t)cx + dx, (int64_t)cy + dy, (int64_t)cz + dz)) return 0;
-    int h = (b - 1) / 2;
-    double n = (double)b * b * b, mi = 0.0, mj = 0.0;
+    if (!block_inside(nx, ny, nz, bl, cx, cy, cz)) return 0;
+    if (!block_inside(nx, ny, nz, bl, (int64_t)cx + dx, (int64_t)cy + dy, (int64_t)cz + dz)) return 0;
+    int hx = (bl[0] - 1) / 2, hy = (bl[1] - 1) / 2, hz = (bl[2] - 1) / 2;
+    double n = (double)bl[0] * bl[1] * bl[2], mi = 0.0, mj = 0.0;
 #define VAL(p, idx) (is_f32 ? (double)((const float *)(p))[idx] : (double)((const uint16_t *)(p))[idx])
-    for (int k = -h; k <= h; ++k)
-        for (int j = -h; j <= h; ++j)
-            for (int i = -h; i <= h; ++i) {
+    for (int k = -hz; k <= hz; ++k)
+        for (int j = -hy; j <= hy; ++j)
+            for (int i = -hx; i <= hx; ++i) {
                 mi += VAL(preop, lin(cx + i, cy + j, cz + k, nx, ny));
                 mj += VAL(intraop, lin(cx + dx + i, cy + dy + j, cz + dz + k, nx, ny));
             }
     mi /= n;
     mj /= n;
     double cov = 0.0, vi = 0.0, vj = 0.0;
-    for (int k = -h; k <= h; ++k)
-        for (int j = -h; j <= h; ++j)
-            for (int i = -h; i <= h; ++i) {
+    for (int k = -hz; k <= hz; ++k)
+        for (int j = -hy; j <= hy; ++j)
+            for (int i = -hx; i <= hx; ++i) {
                 double a = VAL(preop, lin(cx + i, cy + j, cz + k, nx, ny)) - mi;
                 double c = VAL(intraop, lin(cx + dx + i, cy + dy + j, cz + dz + k, nx, ny)) - mj;
                 cov += a * c;
@@ -317,16 +348,30 @@ static int pearson_generic(const void *preop, const void *intraop, int is_f32, i
     return 1;
 }
 
+int oracle_pearson_u16_3(const uint16_t *preop, const uint16_t *intraop, int nx, int ny, int nz, int bx, int by,
+                         int bz, int cx, int cy, int cz, int dx, int dy, int dz, double *ncc)
+{
+    const int bl[3] = {bx, by, bz};
+    return pearson_generic(preop, intraop, 0, nx, ny, nz, bl, cx, cy, cz, dx, dy, dz, ncc);
+}
+
+int oracle_pearson_f32_3(const float *preop, const float *intraop, int nx, int ny, int nz, int bx, int by, int bz,
+                         int cx, int cy, int cz, int dx, int dy, int dz, double *ncc)
+{
+    const int bl[3] = {bx, by, bz};
+    return pearson_generic(preop, intraop, 1, nx, ny, nz, bl, cx, cy, cz, dx, dy, dz, ncc);
+}
+
 int oracle_pearson_u16(const uint16_t *preop, const uint16_t *intraop, int nx, int ny, int nz, int b,
                        int cx, int cy, int cz, int dx, int dy, int dz, double *ncc)
 {
-    return pearson_generic(preop, intraop, 0, nx, ny, nz, b, cx, cy, cz, dx, dy, dz, ncc);
+    return oracle_pearson_u16_3(preop, intraop, nx, ny, nz, b, b, b, cx, cy, cz, dx, dy, dz, ncc);
 }
 
 int oracle_pearson_f32(const float *preop, const float *intraop, int nx, int ny, int nz, int b,
                        int cx, int cy, int cz, int dx, int dy, int dz, double *ncc)
 {
-    return pearson_generic(preop, intraop, 1, nx, ny, nz, b, cx, cy, cz, dx, dy, dz, ncc);
+    return oracle_pearson_f32_3(preop, intraop, nx, ny, nz, b, b, b, cx, cy, cz, dx, dy, dz, ncc);
 }
 
 /* ---------------------------------------------------------------------
@@ -349,9 +394,10 @@ static int better(double s, const int d[3], double bs, const int bd[3])
 }
 
 static void match_generic(const void *preop, const void *intraop, int is_f32, int nx, int ny, int nz,
-                          const int32_t *centers, int64_t n_blocks, int b, const int32_t radius[3],
+                          const int32_t *centers, int64_t n_blocks, const int32_t block[3], const int32_t radius[3],
                           int32_t *disp, double *ncc_out, uint8_t *valid)
 {
+    int bx = block[0], by = block[1], bz = block[2];
     int rx = radius[0], ry = radius[1], rz = radius[2];
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t blk = 0; blk < n_blocks; ++blk) {
@@ -362,10 +408,10 @@ static void match_generic(const void *preop, const void *intraop, int is_f32, in
             for (int dy = -ry; dy <= ry; ++dy)
                 for (int dx = -rx; dx <= rx; ++dx) {
                     double s;
-                    int ok = is_f32 ? oracle_pearson_f32((const float *)preop, (const float *)intraop, nx, ny,
-                                                         nz, b, cx, cy, cz, dx, dy, dz, &s)
-                                    : oracle_ncc_u16((const uint16_t *)preop, (const uint16_t *)intraop, nx, ny,
-                                                     nz, b, cx, cy, cz, dx, dy, dz, &s);
+                    int ok = is_f32 ? oracle_pearson_f32_3((const float *)preop, (const float *)intraop, nx, ny,
+                                                           nz, bx, by, bz, cx, cy, cz, dx, dy, dz, &s)
+                                    : oracle_ncc_u16_3((const uint16_t *)preop, (const uint16_t *)intraop, nx, ny,
+                                                       nz, bx, by, bz, cx, cy, cz, dx, dy, dz, &s);
                     if (!ok) continue;
                     int d[3] = {dx, dy, dz};
                     if (!found || better(s, d, best, best_d)) {
@@ -384,18 +430,35 @@ static void match_generic(const void *preop, const void *intraop, int is_f32, in
     }
 }
 
-/* uint16 intensities: exact integer sums, FP64 ratio (see oracle_ncc_u16). */
+/* uint16 intensities: exact integer sums, FP64 ratio (see oracle_ncc_u16);
+ * block edges (bx, by, bz). */
+void oracle_match_u16_3(const uint16_t *preop, const uint16_t *intraop, int nx, int ny, int nz,
+                        const int32_t *centers, int64_t n_blocks, const int32_t block[3], const int32_t radius[3],
+                        int32_t *disp, double *ncc, uint8_t *valid)
+{
+    match_generic(preop, intraop, 0, nx, ny, nz, centers, n_blocks, block, radius, disp, ncc, valid);
+}
+
+/* float32 intensities: FP64 two-pass Pearson (see pearson_generic). */
+void oracle_match_f32_3(const float *preop, const float *intraop, int nx, int ny, int nz,
+                        const int32_t *centers, int64_t n_blocks, const int32_t block[3], const int32_t radius[3],
+                        int32_t *disp, double *ncc, uint8_t *valid)
+{
+    match_generic(preop, intraop, 1, nx, ny, nz, centers, n_blocks, block, radius, disp, ncc, valid);
+}
+
 void oracle_match_u16(const uint16_t *preop, const uint16_t *intraop, int nx, int ny, int nz,
                       const int32_t *centers, int64_t n_blocks, int b, const int32_t radius[3],
                       int32_t *disp, double *ncc, uint8_t *valid)
 {
-    match_generic(preop, intraop, 0, nx, ny, nz, centers, n_blocks, b, radius, disp, ncc, valid);
+    const int32_t block[3] = {b, b, b};
+    oracle_match_u16_3(preop, intraop, nx, ny, nz, centers, n_blocks, block, radius, disp, ncc, valid);
 }
 
-/* float32 intensities: FP64 two-pass Pearson (see pearson_generic). */
 void oracle_match_f32(const float *preop, const float *intraop, int nx, int ny, int nz,
                       const int32_t *centers, int64_t n_blocks, int b, const int32_t radius[3],
                       int32_t *disp, double *ncc, uint8_t *valid)
 {
-    match_generic(preop, intraop, 1, nx, ny, nz, centers, n_blocks, b, radius, disp, ncc, valid);
+    const int32_t block[3] = {b, b, b};
+    oracle_match_f32_3(preop, intraop, nx, ny, nz, centers, n_blocks, block, radius, disp, ncc, valid);
 }
