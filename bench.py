@@ -53,6 +53,7 @@ def _args():
     p.add_argument("--batched-reps", type=int, default=5)
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-highres", action="store_true")
+    p.add_argument("--no-aniso", action="store_true")
     p.add_argument("--no-spacing", action="store_true")
     p.add_argument("--serve-open-requests", type=int, default=400)
     p.add_argument("--serve-sweep-requests", type=int, default=300)
@@ -425,6 +426,57 @@ def _highres(a, nrr, synth, dev, flush):
     return out
 
 
+ANISO_BLOCK = (9, 9, 5)   # edges along x, y, z: thick slices along z
+ANISO_RADIUS = (5, 5, 3)
+
+
+def _aniso(a, nrr, synth, d_pre, d_intra, d_mask, w, flush):
+    """Blocks with a different edge per axis on the step's clinical pair:
+    block 9x9x5, radius 5x5x3 (847 shifts), stride 2, top 5%: selection, box
+    sums (three separable passes) and matching, each timed on its own with
+    CUDA events (best of 3, L2 flushed before each).  Agreement with the
+    oracle is checked by tests/test_gpu_aniso.py."""
+    import torch
+
+    stream = torch.cuda.current_stream()
+    bl, r = ANISO_BLOCK, ANISO_RADIUS
+    shifts = (2 * r[0] + 1) * (2 * r[1] + 1) * (2 * r[2] + 1)
+    nblk = bl[0] * bl[1] * bl[2]
+
+    def timed(fn):
+        ts = []
+        for _ in range(3):
+            flush.fill_(7)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        return min(ts)
+
+    centers = nrr.select_blocks(d_pre, d_mask, bl, w.stride, w.frac)
+    n = centers.shape[0]
+    cbuf, cnt = nrr.select_blocks(d_pre, d_mask, bl, w.stride, w.frac, sync=False)
+    t_sel = timed(lambda: nrr.select_blocks(d_pre, d_mask, bl, w.stride, w.frac, centers=cbuf, n_selected=cnt,
+                                            sync=False))
+    box = nrr.boxsums(d_intra, bl)
+    t_box = timed(lambda: nrr.boxsums(d_intra, bl, out=box))
+    box = nrr.boxsums(d_intra, bl)
+    res = nrr.block_match(d_pre, d_intra, centers, bl, r, box=box)
+    t_match = timed(lambda: nrr.block_match(d_pre, d_intra, centers, bl, r, box=box, out=res))
+    nrr.device_status()
+    evals = n * shifts
+    peak = (torch.cuda.get_device_properties(d_pre.device).multi_processor_count * FP32_LANES_PER_SM * 2 *
+            float(_peaks().get("sm_max_mhz", 2070.0)) * 1e6)
+    return {"workload": f"clinical pair, block {bl[0]}x{bl[1]}x{bl[2]}, radius {r[0]}x{r[1]}x{r[2]}, "
+                        f"stride {w.stride}, top {w.frac:.0%}",
+            "n_blocks": n, "shifts": shifts, "evals": evals,
+            "select_ms": 1e3 * t_sel, "box_sums_ms": 1e3 * t_box, "match_ms": 1e3 * t_match,
+            "evals_per_s": evals / (t_sel + t_box + t_match), "match_evals_per_s": evals / t_match,
+            "match_roofline_frac": 2.0 * evals * nblk / t_match / peak}
+
+
 def _spacing(a, nrr, synth, d_pre, d_mask, w, flush):
     """Selection with the face / edge / vertex connectivity patterns (6 / 18 /
     26 neighbours on the candidate grid) on the step's volume, against the
@@ -525,26 +577,64 @@ def run_ours(a):
     evals = n_blocks * (2 * w.radius + 1) ** 3
     valid_count = int(out[2][:n_blocks].sum().item())
 
+    # one step captured as a CUDA graph (the step's launches are short and
+    # many: replaying them from a graph keeps host launch latency out of the
+    # device timeline); the graph's results are checked against the eager step
+    graph, graph_note = None, "one step captured as a CUDA graph and replayed"
+    ref = [t.clone() for t in out] + [n_sel.clone()]
+    try:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, capture_error_mode="thread_local"):
+            step(d_pre, d_intra, d_mask)
+        for t in out:
+            t.zero_()
+        for _ in range(max(3, a.warmup)):
+            flush.fill_(1)
+            graph.replay()
+        torch.cuda.synchronize()
+        nrr.device_status()
+        same = all(torch.equal(x.view(torch.uint8), y.view(torch.uint8)) for x, y in zip(list(out) + [n_sel], ref))
+        if not same:
+            graph, graph_note = None, "graph replay differed from the eager step; eager steps timed"
+    except Exception as ex:  # capture not available: time the eager steps
+        graph, graph_note = None, f"graph capture failed ({type(ex).__name__}); eager steps timed"
+        torch.cuda.synchronize()
+
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
     evm = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(a.steps)]
+    evg = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
     l0 = nrr.kernel_launches()
     with ClockSampler(local) as clk:
         t_start = time.time()
+        # eager steps through the public calls, with per-phase events
         for k in range(a.steps):
             flush.fill_(k & 0xFF)
             evs[k][0].record(stream)
             step(d_pre, d_intra, d_mask, evm[k])
             evs[k][1].record(stream)
         torch.cuda.synchronize()
+        launches = nrr.kernel_launches() - l0
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        # the timed steps of the headline: graph replays of the same step
+        if graph is not None:
+            for k in range(a.steps):
+                flush.fill_(k & 0xFF)
+                evg[k][0].record(stream)
+                graph.replay()
+                evg[k][1].record(stream)
+            torch.cuda.synchronize()
         t_end = time.time()
-    launches = nrr.kernel_launches() - l0
     nrr.device_status()
     if pg:
         pg.barrier()
-    step_ms = [s.elapsed_time(e) for s, e in evs]
+    eager_ms = [s.elapsed_time(e) for s, e in evs]
+    step_ms = [s.elapsed_time(e) for s, e in evg] if graph is not None else eager_ms
+    # the graph replays launch the same kernels per step as the eager steps
     select_ms = [s.elapsed_time(p[0]) for (s, _), p in zip(evs, evm)]
     box_ms = [p[0].elapsed_time(p[1]) for p in evm]
     match_ms = [p[1].elapsed_time(p[2]) for p in evm]
@@ -662,6 +752,8 @@ def run_ours(a):
                 "serial_value": e2e_serial},
         "gpu_launches": launches,
         "gpu_launches_per_step": launches / a.steps,
+        "step_timing": graph_note,
+        "eager_ms_per_step": sum(eager_ms) / len(eager_ms),
         "registrations_per_s": world * a.steps / total_s,
         "valid_blocks": valid_count,
         "clocks": clk.summary(t_start, t_end),
@@ -674,6 +766,8 @@ def run_ours(a):
         line["highres"] = _highres(a, nrr, synth, dev, flush)
     if not a.no_spacing:
         line["spacing"] = _spacing(a, nrr, synth, d_pre, d_mask, w, flush)
+    if not a.no_aniso:
+        line["aniso"] = _aniso(a, nrr, synth, d_pre, d_intra, d_mask, w, flush)
     if world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(w, pre, intra, mask)
     print(json.dumps(line), flush=True)

@@ -258,6 +258,42 @@ nrr_status nrr_block_match_bs(const void *d_preop, const void *d_intraop, const 
                               int32_t *d_disp, double *d_ncc, uint8_t *d_valid, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Blocks with a different edge per axis (Sec. 5 lists the half block size,
+ * like the half window size, per anatomical axis).  block = {bx, by, bz},
+ * host int32[3], each odd in 3..11; N = bx*by*bz; the block centred at c
+ * covers c +- (bx-1)/2 along x, (by-1)/2 along y, (bz-1)/2 along z.
+ * Otherwise each call is its cubic counterpart above, with the same
+ * arguments, results, exactness, ownership and errors:
+ *
+ *   nrr_select_blocks_aniso  = nrr_select_blocks (keys over the bx*by*bz
+ *                              block; a candidate's block must lie in the
+ *                              volume along every axis)
+ *   nrr_boxsums_aniso        = nrr_boxsums (for a non-cubic block the sums
+ *                              run in three separable passes through a
+ *                              scratch buffer from the stream-ordered pool,
+ *                              12 bytes per voxel for uint16, 8 for float32)
+ *   nrr_block_match_aniso    = nrr_block_match
+ *   nrr_block_match_bs_aniso = nrr_block_match_bs, with box sums from
+ *                              nrr_boxsums_aniso for the same block
+ * A cubic triple {b, b, b} takes exactly the cubic path.
+ * ---------------------------------------------------------------------- */
+nrr_status nrr_select_blocks_aniso(const uint16_t *d_preop, const uint8_t *d_mask, nrr_dims dims,
+                                   const int32_t block[3], int32_t stride, double frac,
+                                   int32_t *d_centers, int32_t max_blocks,
+                                   int32_t *d_n_selected, int32_t *h_n_selected, void *stream);
+nrr_status nrr_boxsums_aniso(const void *d_intraop, nrr_dtype dtype, nrr_dims dims, const int32_t block[3],
+                             void *d_boxsums, void *stream);
+nrr_status nrr_block_match_aniso(const void *d_preop, const void *d_intraop, nrr_dtype dtype, nrr_dims dims,
+                                 const int32_t *d_centers, int32_t n_blocks, const int32_t *d_n_blocks,
+                                 const int32_t block[3], const int32_t radius[3],
+                                 int32_t *d_disp, double *d_ncc, uint8_t *d_valid, void *stream);
+nrr_status nrr_block_match_bs_aniso(const void *d_preop, const void *d_intraop, const void *d_boxsums,
+                                    nrr_dtype dtype, nrr_dims dims,
+                                    const int32_t *d_centers, int32_t n_blocks, const int32_t *d_n_blocks,
+                                    const int32_t block[3], const int32_t radius[3],
+                                    int32_t *d_disp, double *d_ncc, uint8_t *d_valid, void *stream);
+
+/* ------------------------------------------------------------------------
  * Execution-configuration autotuning (Sec. 4.3: the paper tunes its GPU
  * block-matching kernel by an empirical search over thread configurations).
  *

@@ -26,7 +26,7 @@ LIB = os.path.join(OUT_DIR, "libnrr.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 
-PLAIN_UNITS = ["nrr_api.cu", "nrr_select.cu", "nrr_spacing.cu", "nrr_boxsum.cu", "nrr_match_dispatch.cu", "nrr_tune.cu", "nrr_batch.cu", "nrr_serve.cu"]
+PLAIN_UNITS = ["nrr_api.cu", "nrr_select.cu", "nrr_spacing.cu", "nrr_boxsum.cu", "nrr_boxsum3.cu", "nrr_match_dispatch.cu", "nrr_tune.cu", "nrr_batch.cu", "nrr_serve.cu"]
 MATCH_VARIANTS = [(f32, b) for f32 in (0, 1) for b in (3, 5, 7, 9, 11)]
 
 

@@ -120,6 +120,20 @@ nrr_status check_dims(nrr_dims d, nrr_dtype dtype, int32_t block)
     return NRR_OK;
 }
 
+nrr_status check_dims3(nrr_dims d, nrr_dtype dtype, const int32_t *block)
+{
+    if (!block) return fail(NRR_E_INVALID, "block is NULL");
+    nrr_status st = check_dims(d, dtype, 3);  // dtype, size and pitch rules
+    if (st != NRR_OK) return st;
+    for (int i = 0; i < 3; ++i)
+        if (block[i] < 3 || block[i] > 11 || (block[i] & 1) == 0)
+            return fail(NRR_E_INVALID, "block[%d] must be odd and in 3..11 (got %d)", i, block[i]);
+    if (d.nx < block[0] || d.ny < block[1] || d.nz < block[2])
+        return fail(NRR_E_INVALID, "volume %dx%dx%d smaller than block %dx%dx%d", d.nx, d.ny, d.nz, block[0], block[1],
+                    block[2]);
+    return NRR_OK;
+}
+
 size_t boxsum_bytes(nrr_dims dims, nrr_dtype dtype)
 {
     size_t v = (size_t)dims.nx * dims.ny * dims.nz;
@@ -197,10 +211,10 @@ nrr_status nrr_boxsums(const void *d_intraop, nrr_dtype dtype, nrr_dims dims, in
 }
 
 static nrr_status check_match_args(const void *d_preop, const void *d_intraop, nrr_dtype dtype, nrr_dims dims,
-                                   const int32_t *d_centers, int32_t n_blocks, int32_t block, const int32_t *radius,
-                                   int32_t *d_disp, double *d_ncc, uint8_t *d_valid)
+                                   const int32_t *d_centers, int32_t n_blocks, const int32_t *block3,
+                                   const int32_t *radius, int32_t *d_disp, double *d_ncc, uint8_t *d_valid)
 {
-    nrr_status st = check_dims(dims, dtype, block);
+    nrr_status st = check_dims3(dims, dtype, block3);
     if (st != NRR_OK) return st;
     if (!radius) return fail(NRR_E_INVALID, "radius is NULL");
     for (int i = 0; i < 3; ++i)
@@ -213,10 +227,10 @@ static nrr_status check_match_args(const void *d_preop, const void *d_intraop, n
     return NRR_OK;
 }
 
-nrr_status nrr_block_match_bs(const void *d_preop, const void *d_intraop, const void *d_boxsums, nrr_dtype dtype,
-                              nrr_dims dims, const int32_t *d_centers, int32_t n_blocks, const int32_t *d_n_blocks,
-                              int32_t block, const int32_t radius[3], int32_t *d_disp, double *d_ncc,
-                              uint8_t *d_valid, void *stream)
+nrr_status nrr_block_match_bs_aniso(const void *d_preop, const void *d_intraop, const void *d_boxsums,
+                                    nrr_dtype dtype, nrr_dims dims, const int32_t *d_centers, int32_t n_blocks,
+                                    const int32_t *d_n_blocks, const int32_t block[3], const int32_t radius[3],
+                                    int32_t *d_disp, double *d_ncc, uint8_t *d_valid, void *stream)
 {
     clear_error();
     nrr_status st = check_match_args(d_preop, d_intraop, dtype, dims, d_centers, n_blocks, block, radius, d_disp,
@@ -232,19 +246,52 @@ nrr_status nrr_block_match_bs(const void *d_preop, const void *d_intraop, const 
     a.s2 = (const char *)d_boxsums + boxsum_s2_offset(dims, dtype);
     a.dtype = dtype;
     a.dims = dims;
-    a.block = block;
+    a.block = block[0];
+    const bool cubic = block[1] == block[0] && block[2] == block[0];
+    a.block_y = cubic ? 0 : block[1];
+    a.block_z = cubic ? 0 : block[2];
     for (int i = 0; i < 3; ++i) a.radius[i] = radius[i];
     a.n_jobs = 1;
     a.jobs[0] = MatchJob{d_centers, d_n_blocks, n_blocks, d_disp, d_ncc, d_valid};
-    a.ctas_per_sm = tuned_ctas_per_sm(dtype, block, radius);
+    a.ctas_per_sm = cubic ? tuned_ctas_per_sm(dtype, block[0], radius) : 0;
     st = device_error_word(&a.err);
     if (st != NRR_OK) return st;
     return launch_match(a, (cudaStream_t)stream);
 }
 
-nrr_status nrr_block_match(const void *d_preop, const void *d_intraop, nrr_dtype dtype, nrr_dims dims,
-                           const int32_t *d_centers, int32_t n_blocks, const int32_t *d_n_blocks, int32_t block,
-                           const int32_t radius[3], int32_t *d_disp, double *d_ncc, uint8_t *d_valid, void *stream)
+nrr_status nrr_block_match_bs(const void *d_preop, const void *d_intraop, const void *d_boxsums, nrr_dtype dtype,
+                              nrr_dims dims, const int32_t *d_centers, int32_t n_blocks, const int32_t *d_n_blocks,
+                              int32_t block, const int32_t radius[3], int32_t *d_disp, double *d_ncc,
+                              uint8_t *d_valid, void *stream)
+{
+    const int32_t b3[3] = {block, block, block};
+    return nrr_block_match_bs_aniso(d_preop, d_intraop, d_boxsums, dtype, dims, d_centers, n_blocks, d_n_blocks, b3,
+                                    radius, d_disp, d_ncc, d_valid, stream);
+}
+
+nrr_status nrr_boxsums_aniso(const void *d_intraop, nrr_dtype dtype, nrr_dims dims, const int32_t block[3],
+                             void *d_boxsums, void *stream)
+{
+    clear_error();
+    nrr_status st = check_dims3(dims, dtype, block);
+    if (st != NRR_OK) return st;
+    if (!d_intraop || !d_boxsums) return fail(NRR_E_INVALID, "NULL volume or box-sum buffer");
+    if (((uintptr_t)d_boxsums & 255u) != 0) return fail(NRR_E_INVALID, "box-sum buffer must be 256-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (block[1] == block[0] && block[2] == block[0])
+        return launch_boxsums(d_intraop, dtype, dims, block[0], d_boxsums, s);
+    void *scratch = nullptr;
+    NRR_CUDA_TRY(cudaMallocAsync(&scratch, boxsum3_scratch_bytes(dims, dtype), s));
+    st = launch_boxsums3(d_intraop, dtype, dims, block, d_boxsums, scratch, s);
+    cudaError_t e = cudaFreeAsync(scratch, s);
+    if (st == NRR_OK && e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync");
+    return st;
+}
+
+nrr_status nrr_block_match_aniso(const void *d_preop, const void *d_intraop, nrr_dtype dtype, nrr_dims dims,
+                                 const int32_t *d_centers, int32_t n_blocks, const int32_t *d_n_blocks,
+                                 const int32_t block[3], const int32_t radius[3], int32_t *d_disp, double *d_ncc,
+                                 uint8_t *d_valid, void *stream)
 {
     clear_error();
     nrr_status st = check_match_args(d_preop, d_intraop, dtype, dims, d_centers, n_blocks, block, radius, d_disp,
@@ -254,13 +301,22 @@ nrr_status nrr_block_match(const void *d_preop, const void *d_intraop, nrr_dtype
     cudaStream_t s = (cudaStream_t)stream;
     void *bs = nullptr;
     NRR_CUDA_TRY(cudaMallocAsync(&bs, boxsum_bytes(dims, dtype), s));
-    st = launch_boxsums(d_intraop, dtype, dims, block, bs, s);
+    st = nrr_boxsums_aniso(d_intraop, dtype, dims, block, bs, stream);
     if (st == NRR_OK)
-        st = nrr_block_match_bs(d_preop, d_intraop, bs, dtype, dims, d_centers, n_blocks, d_n_blocks, block, radius,
-                                d_disp, d_ncc, d_valid, stream);
+        st = nrr_block_match_bs_aniso(d_preop, d_intraop, bs, dtype, dims, d_centers, n_blocks, d_n_blocks, block,
+                                      radius, d_disp, d_ncc, d_valid, stream);
     cudaError_t e = cudaFreeAsync(bs, s);
     if (st == NRR_OK && e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync");
     return st;
+}
+
+nrr_status nrr_block_match(const void *d_preop, const void *d_intraop, nrr_dtype dtype, nrr_dims dims,
+                           const int32_t *d_centers, int32_t n_blocks, const int32_t *d_n_blocks, int32_t block,
+                           const int32_t radius[3], int32_t *d_disp, double *d_ncc, uint8_t *d_valid, void *stream)
+{
+    const int32_t b3[3] = {block, block, block};
+    return nrr_block_match_aniso(d_preop, d_intraop, dtype, dims, d_centers, n_blocks, d_n_blocks, b3, radius, d_disp,
+                                 d_ncc, d_valid, stream);
 }
 
 }  // extern "C"

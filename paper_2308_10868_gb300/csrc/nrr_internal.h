@@ -40,6 +40,8 @@ void count_launches(int n);
 
 // Common argument checks.
 nrr_status check_dims(nrr_dims dims, nrr_dtype dtype, int32_t block);
+// Per-axis block edges (x, y, z): each odd in 3..11 and no larger than the volume.
+nrr_status check_dims3(nrr_dims dims, nrr_dtype dtype, const int32_t *block);
 inline size_t elem_size(nrr_dtype t) { return t == NRR_F32 ? 4 : 2; }
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -51,6 +53,11 @@ inline size_t boxsum_s2_offset(nrr_dims dims, nrr_dtype dtype)
     (void)dtype;
     return align_up(v * 4, 256);  // S1 is int32 or float: 4 bytes each
 }
+// Box sums for blocks with per-axis edges (nrr_boxsum3.cu): three separable
+// passes through a scratch buffer of boxsum3_scratch_bytes.
+size_t boxsum3_scratch_bytes(nrr_dims dims, nrr_dtype dtype);
+nrr_status launch_boxsums3(const void *d_intraop, nrr_dtype dtype, nrr_dims dims, const int32_t block[3],
+                           void *d_boxsums, void *d_scratch, cudaStream_t stream);
 nrr_status launch_boxsums(const void *d_intraop, nrr_dtype dtype, nrr_dims dims, int32_t block, void *d_boxsums,
                           cudaStream_t stream);
 
@@ -93,7 +100,8 @@ struct MatchLaunch {
     const void *s2;
     nrr_dtype dtype;
     nrr_dims dims;
-    int32_t block;
+    int32_t block;             // block edge along x
+    int32_t block_y, block_z;  // edges along y and z; 0 = the x edge (cubic block)
     int32_t radius[3];
     int n_jobs;
     MatchJob jobs[MATCH_MAX_JOBS];
@@ -120,7 +128,7 @@ struct SelectPlan {
 SelectPlan select_plan(nrr_dims d, int stride, int connectivity = 0);
 nrr_status enqueue_select(const uint16_t *preop, const uint8_t *mask, nrr_dims d, int block, int stride, double frac,
                           int32_t *centers, int32_t max_blocks, int32_t *d_n_selected, unsigned char *ws,
-                          const SelectPlan &p, cudaStream_t s);
+                          const SelectPlan &p, cudaStream_t s, int block_y = 0, int block_z = 0);
 
 // Connectivity pattern of the selection (6, 18 or 26 neighbours on the
 // candidate grid): keeps selectable (key > 0) only the members of the greedy

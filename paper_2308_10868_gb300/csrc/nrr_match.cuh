@@ -61,6 +61,7 @@ struct MatchParams {
     int wyp;  // rows per plane of the window box (>= window height)
     int n_jobs;
     int single_window;  // one window buffer: the next block's copy is issued once this block's window is read
+    int by, bz;         // block edges along y and z (the x edge is the template parameter B)
     MatchJob jobs[MATCH_MAX_JOBS];
     unsigned int *err;
 };
@@ -144,8 +145,9 @@ struct MatchLayout {
 // single_window the two blocks in flight share one window buffer (their
 // floating blocks stay double-buffered); `levels` adds the level scratch.
 __host__ __device__ inline MatchLayout match_layout(int elem, int B, int P, int bx, int btx, int wyp, int wz, int py,
-                                                   int pz, bool single_window, bool levels)
+                                                   int pz, bool single_window, bool levels, int brows)
 {
+    // brows: rows of the floating block (by * bz)
     MatchLayout L;
     const int pt = round_up_i(B, 4);
     int o = 0;
@@ -157,10 +159,10 @@ __host__ __device__ inline MatchLayout match_layout(int elem, int B, int P, int 
             o += round_up_i(bx * wyp * wz * elem, 128);
         }
         L.ut[b] = o;
-        o += round_up_i(btx * B * B * elem, 128);
+        o += round_up_i(btx * brows * elem, 128);
     }
     L.t = o;
-    o += round_up_i(B * B * pt * 4, 128);
+    o += round_up_i(brows * pt * 4, 128);
     L.surv = o;
     o += round_up_i(P * py * pz * 2, 128);
     L.sc = o;
@@ -311,10 +313,9 @@ __device__ __forceinline__ bool in_level(int code, const int32_t (&r)[3], int P,
     return abs(dx) <= r[0] && abs(dy) <= r[1] && abs(dz) <= r[2];
 }
 
-template <int H>
-__device__ __forceinline__ bool center_inside(int cx, int cy, int cz, int nx, int ny, int nz)
+__device__ __forceinline__ bool center_inside(int cx, int cy, int cz, int nx, int ny, int nz, int hx, int hy, int hz)
 {
-    return cx >= H && cy >= H && cz >= H && cx <= nx - 1 - H && cy <= ny - 1 - H && cz <= nz - 1 - H;
+    return cx >= hx && cy >= hy && cz >= hz && cx <= nx - 1 - hx && cy <= ny - 1 - hy && cz <= nz - 1 - hz;
 }
 
 // The search of one thread's line for a window whose row data starts XO
@@ -322,7 +323,8 @@ __device__ __forceinline__ bool center_inside(int cx, int cy, int cz, int nx, in
 // row; rows of the next template row are one box row apart, template planes
 // `zstride` elements apart.
 template <typename T, int B, int P, int XO>
-__device__ __forceinline__ void search_line(const T *row0, int zstride, const float *Tm, float csh, float (&acc)[P])
+__device__ __forceinline__ void search_line(const T *row0, int zstride, const float *Tm, float csh, float (&acc)[P],
+                                            int by, int bz)
 {
     constexpr bool F32 = std::is_same<T, float>::value;
     constexpr int WX = B + P - 1;
@@ -331,11 +333,11 @@ __device__ __forceinline__ void search_line(const T *row0, int zstride, const fl
     constexpr int PT = (B + 3) / 4 * 4;
     constexpr int BX = match_bx<T, B, P>();
 #pragma unroll 1
-    for (int kz = 0; kz < B; ++kz) {
+    for (int kz = 0; kz < bz; ++kz) {
 #pragma unroll 1
-        for (int ky = 0; ky < B; ++ky) {
+        for (int ky = 0; ky < by; ++ky) {
             const T *row = row0 + kz * zstride + ky * BX;
-            const float *tr = Tm + (kz * B + ky) * PT;
+            const float *tr = Tm + (kz * by + ky) * PT;
             uint4 ch[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) ch[c] = *reinterpret_cast<const uint4 *>(row + c * EPC);
@@ -379,27 +381,33 @@ __device__ __forceinline__ void search_line(const T *row0, int zstride, const fl
 // The kernel body; the __global__ entries below differ only in their
 // register budget.  `a`, `tmapJ` and `tmapI` live in kernel-parameter space.
 // LEV: the jobs may report extra radius levels (batched search); without it
-// that code is compiled out of the search's per-shift loops.
-template <typename T, int B, int P, bool LEV>
+// that code is compiled out of the search's per-shift loops.  ANI: the block
+// edges along y and z (a.by, a.bz) may differ from the x edge B; without it
+// they are B and every size below is a compile-time constant.
+template <typename T, int B, int P, bool LEV, bool ANI>
 __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorMap *tmapJ, const CUtensorMap *tmapI)
 {
     constexpr bool F32 = std::is_same<T, float>::value;
-    constexpr int H = (B - 1) / 2;
-    constexpr int N = B * B * B;
+    constexpr int H = (B - 1) / 2;  // x half edge
+    constexpr int N3 = B * B * B;   // terms of a cubic block
+    const int BY = ANI ? a.by : B, BZ = ANI ? a.bz : B;
+    const int HY = (BY - 1) / 2, HZ = (BZ - 1) / 2;
+    const int N = ANI ? B * BY * BZ : N3;
     constexpr int PT = (B + 3) / 4 * 4;
     constexpr int RX = (P - 1) / 2;
     constexpr int ALIGN = 16 / (int)sizeof(T);
     constexpr int BX = match_bx<T, B, P>();
     constexpr int BTX = round_up_c(B + ALIGN - 1, ALIGN);
     constexpr float U32 = 5.9604644775390625e-08f;  // 2^-24, unit roundoff of binary32
-    constexpr double GAMMA_N = (double)N * 5.9604644775390625e-08 / (1.0 - (double)N * 5.9604644775390625e-08);
+    const double GAMMA_N = (double)N * 5.9604644775390625e-08 / (1.0 - (double)N * 5.9604644775390625e-08);
 
     const int ry = a.ry, rz = a.rz, py = 2 * ry + 1, pz = 2 * rz + 1, lines = py * pz;
-    const int wz = B + 2 * rz, wyp = a.wyp;
+    const int wz = BZ + 2 * rz, wyp = a.wyp;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
 
     extern __shared__ __align__(128) unsigned char smem[];
-    const MatchLayout L = match_layout((int)sizeof(T), B, P, BX, BTX, wyp, wz, py, pz, a.single_window != 0, LEV);
+    const MatchLayout L =
+        match_layout((int)sizeof(T), B, P, BX, BTX, wyp, wz, py, pz, a.single_window != 0, LEV, BY * BZ);
     const bool single = a.single_window != 0;
     float *Tm = reinterpret_cast<float *>(smem + L.t);
     uint16_t *surv = reinterpret_cast<uint16_t *>(smem + L.surv);
@@ -445,7 +453,7 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         for (; w < n; w += gridDim.x) {
             int cx, cy, cz;
             centre(w, cx, cy, cz);
-            if (center_inside<H>(cx, cy, cz, nx, ny, nz)) return w;
+            if (center_inside(cx, cy, cz, nx, ny, nz, H, HY, HZ)) return w;
             if (tid == 0) {
                 int j, i;
                 locate(w, j, i);
@@ -454,7 +462,7 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         }
         return n;
     };
-    const uint32_t tx_bytes = (uint32_t)((BX * wyp * wz + BTX * B * B) * (int)sizeof(T));
+    const uint32_t tx_bytes = (uint32_t)((BX * wyp * wz + BTX * BY * BZ) * (int)sizeof(T));
     // thread 0: both copies of block w into buffer b
     auto issue = [&](int w, int b) {
         int cx, cy, cz;
@@ -462,8 +470,8 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         const int x0 = cx - H - RX, xt = cx - H;
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(bar + b, tx_bytes);
-        tma_load_3d(smem + L.u[b], tmapJ, bar + b, x0 & ~(ALIGN - 1), cy - H - ry, cz - H - rz);
-        tma_load_3d(smem + L.ut[b], tmapI, bar + b, xt & ~(ALIGN - 1), cy - H, cz - H);
+        tma_load_3d(smem + L.u[b], tmapJ, bar + b, x0 & ~(ALIGN - 1), cy - HY - ry, cz - HZ - rz);
+        tma_load_3d(smem + L.ut[b], tmapI, bar + b, xt & ~(ALIGN - 1), cy - HY, cz - HZ);
     };
 
     uint32_t phase[2] = {0u, 0u};
@@ -515,7 +523,7 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         // float-float, uint16 in exact integers) and every thread combines the
         // per-warp partials after the barrier ----
         {
-            constexpr int IPT = (N + 63) / 64;  // values per thread at 64+ threads
+            constexpr int IPT = ANI ? 1 : (N3 + 63) / 64;  // values per thread at 64+ threads
             if constexpr (F32) {
                 // sums of (I - I0) and (I - I0)^2 with I0 the block's first
                 // value (shifted data: the spread loses no digits to
@@ -554,7 +562,7 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                     sc->phi[warp] = hi;
                 }
             } else {  // uint16: every warp sums a share (exact integer sums)
-                constexpr int KPT = (N + 63) / 64;
+                constexpr int KPT = ANI ? 0 : (N3 + 63) / 64;
                 long long s1 = 0;
                 unsigned long long s2 = 0;
 #pragma unroll
@@ -661,9 +669,9 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         }
         // ---- mean-shifted template (loads batched before stores) -----------
         {
-            constexpr int TB = B * B * PT;
-            constexpr int TPT = (TB + 63) / 64;  // items per thread at 64+ threads
-            float v[TPT];
+            const int TB = BY * BZ * PT;
+            constexpr int TPT = ANI ? 0 : (B * B * PT + 63) / 64;  // items per thread at 64+ threads
+            float v[TPT > 0 ? TPT : 1];
 #pragma unroll
             for (int j = 0; j < TPT; ++j) {
                 const int k = tid + j * nthr;
@@ -713,7 +721,7 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         }
         if (tid < lines) {
             const int dy = dyi - ry, dz = dzi - rz, Y = cy + dy, Z = cz + dz;
-            const bool yz_ok = Y >= H && Y <= ny - 1 - H && Z >= H && Z <= nz - 1 - H;
+            const bool yz_ok = Y >= HY && Y <= ny - 1 - HY && Z >= HZ && Z <= nz - 1 - HZ;
             typedef typename std::conditional<F32, float, int32_t>::type S1T;
             typedef float S2T;  // uint16: v_J = N S_JJ - S_J^2 rounded to float; float32: S_JJ
             float acc[P];
@@ -724,7 +732,7 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
             switch (xo) {
 #define NRR_XO(k) \
     case k:       \
-        if constexpr (k < ALIGN) search_line<T, B, P, k>(row0, zs, Tm, cshift, acc); \
+        if constexpr (k < ALIGN) search_line<T, B, P, k>(row0, zs, Tm, cshift, acc, BY, BZ); \
         break;
                 NRR_XO(0)
                 NRR_XO(1)
@@ -793,9 +801,9 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                             if (((lvl_line >> l) & 1u) && abs(p - RX) <= J.levels[l].r[0]) lbl[l] = fmaxf(lbl[l], v - e);
                     }
                 } else {
-                    constexpr float GS = (float)(3.0 * B * 5.9604644775390625e-08 /
-                                                 (1.0 - 3.0 * B * 5.9604644775390625e-08));  // box-sum depth
-                    constexpr float GN = (float)GAMMA_N;
+                    const float GS = (float)((B + BY + BZ) * 5.9604644775390625e-08 /
+                                             (1.0 - (B + BY + BZ) * 5.9604644775390625e-08));  // box-sum depth
+                    const float GN = (float)GAMMA_N;
                     const float s1 = ps1[p];
                     const float s2 = fmaxf(ps2[p], 0.f);
                     float d1;  // |S1 err| bound (the factor 1.01 covers sqrt.approx)
@@ -900,7 +908,7 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         // part): with fewer survivors than warps, each survivor's terms are
         // split over nwarp/nsurv warps whose partial sums thread 0 adds up.
         const int parts = (!F32 || nsurv >= nwarp) ? 1 : (nsurv > 0 ? nwarp / nsurv : 1);
-        constexpr int KS1 = N;  // terms of a whole survivor
+        const int KS1 = N;  // terms of a whole survivor
         Cand wb{0.0, 0, 0, 0};
         const int ntask = parts == 1 ? nsurv : nsurv * parts;
         for (int task = warp; task < ntask; task += nwarp) {
@@ -915,8 +923,8 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
             if constexpr (!F32) {  // one warp per survivor: parts == 1
                 long long s1 = 0;
                 if (lane == 0) s1 = reinterpret_cast<const int32_t *>(a.s1)[idx];  // issued first, used after the warp sums
-                constexpr int KPL = (N + 31) / 32;
-                constexpr int CH = KPL < 6 ? KPL : 6;
+                const int KPL = (N + 31) / 32;
+                constexpr int CH = ANI ? 6 : ((N3 + 31) / 32 < 6 ? (N3 + 31) / 32 : 6);
                 long long e = 0, q2 = 0;  // sum T (J - c), sum (J - c)^2: exact
 #pragma unroll 1
                 for (int i0 = 0; i0 < KPL; i0 += CH) {
@@ -924,11 +932,11 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
 #pragma unroll
                     for (int q = 0; q < CH; ++q) {
                         const int k = lane + 32 * (i0 + q);
-                        const int kz = k / (B * B), rem = k - kz * B * B, ky = rem / B, kx = rem - ky * B;
+                        const int kz = k / (B * BY), rem = k - kz * B * BY, ky = rem / B, kx = rem - ky * B;
                         tv[q] = 0;
                         jv[q] = 0;
                         if (k < N) {
-                            tv[q] = (int)Tm[(kz * B + ky) * PT + kx];
+                            tv[q] = (int)Tm[(kz * BY + ky) * PT + kx];
                             jv[q] = (int)U[((szi + kz) * wyp + (syi + ky)) * BX + xo + sxi + kx] - c_i;
                         }
                     }
@@ -957,9 +965,10 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                 FF fij{0.f, 0.f}, fj{0.f, 0.f}, fjj{0.f, 0.f};
                 float lo = INFINITY, hi = -INFINITY;
                 for (int k = kbeg + lane; k < kend; k += 32) {
-                    const int kz = k / (B * B), rem = k - kz * B * B, ky = rem / B, kx = rem - ky * B;
-                    const float iv = pre[((size_t)(cz - H + kz) * ny + (cy - H + ky)) * nx + (cx - H + kx)];
-                    const float jf = intra[((size_t)(cz + dz - H + kz) * ny + (cy + dy - H + ky)) * nx + (cx + dx - H + kx)];
+                    const int kz = k / (B * BY), rem = k - kz * B * BY, ky = rem / B, kx = rem - ky * B;
+                    const float iv = pre[((size_t)(cz - HZ + kz) * ny + (cy - HY + ky)) * nx + (cx - H + kx)];
+                    const float jf =
+                        intra[((size_t)(cz + dz - HZ + kz) * ny + (cy + dy - HY + ky)) * nx + (cx + dx - H + kx)];
                     float dh, de;
                     two_sum(iv, -bc.ibh, dh, de);  // I - Ibar = dh + dl, nearly exact
                     const float dl = __fsub_rn(de, bc.ibl);
@@ -1086,29 +1095,29 @@ struct MatchMinBlocks {
     static constexpr int value = (P <= 11 && B <= 7) ? 3 : 2;
 };
 
-template <int B, int P, bool LEV>
+template <int B, int P, bool LEV, bool ANI>
 __global__ void __maxnreg__((MatchRegs<B, P>::value))
     match_kernel_u16(const __grid_constant__ MatchParams a, const __grid_constant__ CUtensorMap tmapJ,
                      const __grid_constant__ CUtensorMap tmapI)
 {
-    match_body<uint16_t, B, P, LEV>(a, &tmapJ, &tmapI);
+    match_body<uint16_t, B, P, LEV, ANI>(a, &tmapJ, &tmapI);
 }
 
-template <int B, int P>
+template <int B, int P, bool ANI>
 __global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value)
     match_kernel_f32(const __grid_constant__ MatchParams a, const __grid_constant__ CUtensorMap tmapJ,
                      const __grid_constant__ CUtensorMap tmapI)
 {
-    match_body<float, B, P, false>(a, &tmapJ, &tmapI);
+    match_body<float, B, P, false, ANI>(a, &tmapJ, &tmapI);
 }
 
-template <typename T, int B, int P, bool LEV>
+template <typename T, int B, int P, bool LEV, bool ANI>
 constexpr auto match_kernel_ptr()
 {
     if constexpr (std::is_same<T, float>::value)
-        return match_kernel_f32<B, P>;  // float32 jobs report no extra levels
+        return match_kernel_f32<B, P, ANI>;  // float32 jobs report no extra levels
     else
-        return match_kernel_u16<B, P, LEV>;
+        return match_kernel_u16<B, P, LEV, ANI>;
 }
 
 // Shared-memory layout of a launch: double-buffered windows, unless that
@@ -1116,17 +1125,22 @@ constexpr auto match_kernel_ptr()
 // (the other CTAs then hide the exposed copy latency; measured on float32
 // windows: b = 9, R = 7 from 1 to 2 CTAs, 23% faster; b = 7, R = 5 from 3 to
 // 6 CTAs, 16% faster).
-template <typename T, int B, int P, bool LEV>
+// Block edges along y and z of a launch (0 in MatchLaunch: the x edge).
+inline int launch_by(const MatchLaunch &m) { return m.block_y > 0 ? m.block_y : m.block; }
+inline int launch_bz(const MatchLaunch &m) { return m.block_z > 0 ? m.block_z : m.block; }
+
+template <typename T, int B, int P, bool LEV, bool ANI>
 nrr_status choose_layout(const MatchLaunch &m, MatchLayout *L, bool *single, int *occ)
 {
     constexpr int ALIGN = 16 / (int)sizeof(T);
+    const int by = launch_by(m), bz = launch_bz(m);
     const int ry = m.radius[1], rz = m.radius[2], py = 2 * ry + 1, pz = 2 * rz + 1;
-    const int wyp = match_wyp(B + 2 * ry, py), threads = round_up_i(py * pz, 32);
+    const int wyp = match_wyp(by + 2 * ry, py), threads = round_up_i(py * pz, 32);
     const MatchLayout L2 = match_layout((int)sizeof(T), B, P, match_bx<T, B, P>(), round_up_c(B + ALIGN - 1, ALIGN),
-                                        wyp, B + 2 * rz, py, pz, false, LEV);
+                                        wyp, bz + 2 * rz, py, pz, false, LEV, by * bz);
     const MatchLayout L1 = match_layout((int)sizeof(T), B, P, match_bx<T, B, P>(), round_up_c(B + ALIGN - 1, ALIGN),
-                                        wyp, B + 2 * rz, py, pz, true, LEV);
-    auto kern = match_kernel_ptr<T, B, P, LEV>();
+                                        wyp, bz + 2 * rz, py, pz, true, LEV, by * bz);
+    auto kern = match_kernel_ptr<T, B, P, LEV, ANI>();
     static int smem_set = 0;  // largest dynamic shared memory opted in so far
     if (L2.total > smem_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L2.total);
@@ -1145,14 +1159,15 @@ nrr_status choose_layout(const MatchLaunch &m, MatchLayout *L, bool *single, int
     return NRR_OK;
 }
 
-template <typename T, int B, int P, bool LEV>
+template <typename T, int B, int P, bool LEV, bool ANI>
 nrr_status launch_match_variant_l(const MatchLaunch &m, cudaStream_t stream)
 {
     constexpr int ALIGN = 16 / (int)sizeof(T);
     constexpr int BX = match_bx<T, B, P>();
     constexpr int BTX = round_up_c(B + ALIGN - 1, ALIGN);
+    const int by = launch_by(m), bz = launch_bz(m);
     const int ry = m.radius[1], rz = m.radius[2], py = 2 * ry + 1, pz = 2 * rz + 1;
-    const int wy = B + 2 * ry, wz = B + 2 * rz, wyp = match_wyp(wy, py);
+    const int wy = by + 2 * ry, wz = bz + 2 * rz, wyp = match_wyp(wy, py);
     const int threads = round_up_i(py * pz, 32);
     if (threads > MATCH_MAX_THREADS) return fail(NRR_E_INVALID, "search window too large");
     if (wyp > 256) return fail(NRR_E_INVALID, "search window too large");
@@ -1160,14 +1175,14 @@ nrr_status launch_match_variant_l(const MatchLaunch &m, cudaStream_t stream)
     CUtensorMap mapJ, mapI;
     nrr_status st = encode_volume_map(&mapJ, m.intraop, m.dtype, m.dims, BX, wyp, wz);
     if (st != NRR_OK) return st;
-    st = encode_volume_map(&mapI, m.preop, m.dtype, m.dims, BTX, B, B);
+    st = encode_volume_map(&mapI, m.preop, m.dtype, m.dims, BTX, by, bz);
     if (st != NRR_OK) return st;
 
-    auto kern = match_kernel_ptr<T, B, P, LEV>();
+    auto kern = match_kernel_ptr<T, B, P, LEV, ANI>();
     MatchLayout L;
     bool single = false;
     int occ = 0;
-    st = choose_layout<T, B, P, LEV>(m, &L, &single, &occ);
+    st = choose_layout<T, B, P, LEV, ANI>(m, &L, &single, &occ);
     if (st != NRR_OK) return st;
     if (occ < 1) return fail(NRR_E_INVALID, "match kernel does not fit on an SM (%d B shared)", L.total);
     if (m.ctas_per_sm > 0 && m.ctas_per_sm < occ) occ = m.ctas_per_sm;
@@ -1190,6 +1205,8 @@ nrr_status launch_match_variant_l(const MatchLaunch &m, cudaStream_t stream)
     p.wyp = wyp;
     p.n_jobs = m.n_jobs;
     p.single_window = single ? 1 : 0;
+    p.by = by;
+    p.bz = bz;
     for (int j = 0; j < MATCH_MAX_JOBS; ++j) p.jobs[j] = j < m.n_jobs ? m.jobs[j] : MatchJob{};
     p.err = m.err;
     kern<<<(unsigned)grid, threads, L.total, stream>>>(p, mapJ, mapI);
@@ -1201,16 +1218,23 @@ nrr_status launch_match_variant_l(const MatchLaunch &m, cudaStream_t stream)
 
 // Launches whose jobs report extra radius levels use the level-aware kernel
 // (uint16 only: the batched search runs on uint16 volumes).
+// Launches whose blocks have other edges along y or z than along x use the
+// variant with those edges at run time.
 template <typename T, int B, int P>
 nrr_status launch_match_variant(const MatchLaunch &m, cudaStream_t stream)
 {
     bool lev = false;
     for (int j = 0; j < m.n_jobs; ++j) lev |= m.jobs[j].n_levels > 0;
-    if (!lev) return launch_match_variant_l<T, B, P, false>(m, stream);
+    const bool ani = launch_by(m) != B || launch_bz(m) != B;
+    if (ani) {
+        if (lev) return fail(NRR_E_INTERNAL, "extra radius levels are not supported for anisotropic blocks");
+        return launch_match_variant_l<T, B, P, false, true>(m, stream);
+    }
+    if (!lev) return launch_match_variant_l<T, B, P, false, false>(m, stream);
     if constexpr (std::is_same<T, float>::value)
         return fail(NRR_E_INTERNAL, "extra radius levels are not supported for float32 volumes");
     else
-        return launch_match_variant_l<T, B, P, true>(m, stream);
+        return launch_match_variant_l<T, B, P, true, false>(m, stream);
 }
 
 template <typename T, int B, int P>
@@ -1218,7 +1242,8 @@ nrr_status occupancy_variant(const MatchLaunch &m, int *occ)
 {
     MatchLayout L;
     bool single = false;
-    return choose_layout<T, B, P, false>(m, &L, &single, occ);
+    if (launch_by(m) != B || launch_bz(m) != B) return choose_layout<T, B, P, false, true>(m, &L, &single, occ);
+    return choose_layout<T, B, P, false, false>(m, &L, &single, occ);
 }
 
 template <typename T, int B>

@@ -50,14 +50,17 @@ struct SelState {
     int done;                 // nothing (more) to select
 };
 
+// B: block edge along x; by, bz: edges along y and z
 template <int B>
 __global__ void __launch_bounds__(KEY_THREADS) grid_keys_kernel(const uint16_t *__restrict__ preop,
                                                                 const uint8_t *__restrict__ mask, int nx, int ny,
-                                                                int nz, int stride, int gx, int gy, long long ng,
-                                                                long long *__restrict__ keys, SelState *st)
+                                                                int nz, int by, int bz, int stride, int gx, int gy,
+                                                                long long ng, long long *__restrict__ keys,
+                                                                SelState *st)
 {
     constexpr int H = (B - 1) / 2;
-    constexpr long long N = (long long)B * B * B;
+    const int HY = (by - 1) / 2, HZ = (bz - 1) / 2;
+    const long long N = (long long)B * by * bz;
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int cand = 0, pos = 0;
     unsigned long long kmax = 0;
@@ -65,12 +68,12 @@ __global__ void __launch_bounds__(KEY_THREADS) grid_keys_kernel(const uint16_t *
         const int i = (int)(g % gx), j = (int)((g / gx) % gy), k = (int)(g / ((long long)gx * gy));
         const int x = i * stride, y = j * stride, z = k * stride;
         long long key = -1;
-        if (x >= H && y >= H && z >= H && x <= nx - 1 - H && y <= ny - 1 - H && z <= nz - 1 - H &&
+        if (x >= H && y >= HY && z >= HZ && x <= nx - 1 - H && y <= ny - 1 - HY && z <= nz - 1 - HZ &&
             mask[((size_t)z * ny + y) * nx + x] != 0) {
             unsigned int s = 0;
             unsigned long long q = 0;
-            for (int kz = -H; kz <= H; ++kz)
-                for (int ky = -H; ky <= H; ++ky) {
+            for (int kz = -HZ; kz <= HZ; ++kz)
+                for (int ky = -HY; ky <= HY; ++ky) {
                     const uint16_t *row = preop + ((size_t)(z + kz) * ny + (y + ky)) * nx + (x - H);
                     unsigned int rs = 0;
                     unsigned long long rq = 0;
@@ -355,11 +358,12 @@ __global__ void __launch_bounds__(CMP_THREADS) compact_write_kernel(const long l
 }
 
 template <int B>
-void launch_keys(const uint16_t *preop, const uint8_t *mask, nrr_dims d, int stride, int gx, int gy, long long ng,
-                 long long *keys, SelState *st, cudaStream_t s)
+void launch_keys(const uint16_t *preop, const uint8_t *mask, nrr_dims d, int by, int bz, int stride, int gx, int gy,
+                 long long ng, long long *keys, SelState *st, cudaStream_t s)
 {
     const unsigned grid = (unsigned)((ng + KEY_THREADS - 1) / KEY_THREADS);
-    grid_keys_kernel<B><<<grid, KEY_THREADS, 0, s>>>(preop, mask, d.nx, d.ny, d.nz, stride, gx, gy, ng, keys, st);
+    grid_keys_kernel<B><<<grid, KEY_THREADS, 0, s>>>(preop, mask, d.nx, d.ny, d.nz, by, bz, stride, gx, gy, ng, keys,
+                                                     st);
 }
 
 }  // namespace
@@ -398,24 +402,25 @@ SelectPlan select_plan(nrr_dims d, int stride, int connectivity)
 // select_plan().bytes, 256-byte aligned).  Reads nothing back.
 nrr_status enqueue_select(const uint16_t *preop, const uint8_t *mask, nrr_dims d, int block, int stride,
                                  double frac, int32_t *centers, int32_t max_blocks, int32_t *d_n_selected,
-                                 unsigned char *ws, const SelectPlan &p, cudaStream_t s)
+                                 unsigned char *ws, const SelectPlan &p, cudaStream_t s, int block_y, int block_z)
 {
+    const int by = block_y > 0 ? block_y : block, bz = block_z > 0 ? block_z : block;
     long long *keys = (long long *)(ws + p.off_keys);
     unsigned int *hist = (unsigned int *)(ws + p.off_hist);
     SelState *st = (SelState *)(ws + p.off_state);
     unsigned long long *cnt = (unsigned long long *)(ws + p.off_cnt);
     NRR_CUDA_TRY(cudaMemsetAsync(ws + p.off_hist, 0, p.off_cnt - p.off_hist, s));
-    if (keys_box_supported(block, stride)) {
+    if (by == block && bz == block && keys_box_supported(block, stride)) {
         nrr_status ks = launch_keys_box(preop, mask, d, block, stride, p.gx, p.gy, p.gz, keys, &st->nc, &st->npos,
                                         &st->maxkey, s);
         if (ks != NRR_OK) return ks;
     } else {
         switch (block) {
-        case 3: launch_keys<3>(preop, mask, d, stride, p.gx, p.gy, p.ng, keys, st, s); break;
-        case 5: launch_keys<5>(preop, mask, d, stride, p.gx, p.gy, p.ng, keys, st, s); break;
-        case 7: launch_keys<7>(preop, mask, d, stride, p.gx, p.gy, p.ng, keys, st, s); break;
-        case 9: launch_keys<9>(preop, mask, d, stride, p.gx, p.gy, p.ng, keys, st, s); break;
-        default: launch_keys<11>(preop, mask, d, stride, p.gx, p.gy, p.ng, keys, st, s); break;
+        case 3: launch_keys<3>(preop, mask, d, by, bz, stride, p.gx, p.gy, p.ng, keys, st, s); break;
+        case 5: launch_keys<5>(preop, mask, d, by, bz, stride, p.gx, p.gy, p.ng, keys, st, s); break;
+        case 7: launch_keys<7>(preop, mask, d, by, bz, stride, p.gx, p.gy, p.ng, keys, st, s); break;
+        case 9: launch_keys<9>(preop, mask, d, by, bz, stride, p.gx, p.gy, p.ng, keys, st, s); break;
+        default: launch_keys<11>(preop, mask, d, by, bz, stride, p.gx, p.gy, p.ng, keys, st, s); break;
         }
     }
     if (p.connectivity) {
@@ -453,22 +458,28 @@ nrr_status check_select_args(nrr_dims dims, int32_t block, int32_t stride, doubl
 
 using namespace nrr;
 
-extern "C" nrr_status nrr_select_blocks(const uint16_t *d_preop, const uint8_t *d_mask, nrr_dims dims, int32_t block,
-                                        int32_t stride, double frac, int32_t *d_centers, int32_t max_blocks,
-                                        int32_t *d_n_selected, int32_t *h_n_selected, void *stream)
+// Selection with the scratch from the stream-ordered allocator: block edges
+// (x, y, z) and an optional connectivity pattern.
+static nrr_status select_alloc(const uint16_t *d_preop, const uint8_t *d_mask, nrr_dims dims, const int32_t *block,
+                               int32_t stride, double frac, int32_t connectivity, int32_t *d_centers,
+                               int32_t max_blocks, int32_t *d_n_selected, int32_t *h_n_selected, void *stream)
 {
     clear_error();
-    nrr_status st = check_select_args(dims, block, stride, frac);
+    nrr_status st = check_dims3(dims, NRR_U16, block);
     if (st != NRR_OK) return st;
+    st = check_select_args(dims, block[0], stride, frac);
+    if (st != NRR_OK) return st;
+    if (connectivity != 0 && connectivity != 6 && connectivity != 18 && connectivity != 26)
+        return fail(NRR_E_INVALID, "connectivity %d is not 0, 6, 18 or 26", connectivity);
     if (max_blocks < 0) return fail(NRR_E_INVALID, "max_blocks < 0");
     if (!d_preop || !d_mask) return fail(NRR_E_INVALID, "NULL volume or mask");
     if (max_blocks > 0 && !d_centers) return fail(NRR_E_INVALID, "NULL centre buffer");
     cudaStream_t s = (cudaStream_t)stream;
-    const SelectPlan p = select_plan(dims, stride);
+    const SelectPlan p = select_plan(dims, stride, connectivity);
     void *ws = nullptr;
     NRR_CUDA_TRY(cudaMallocAsync(&ws, p.bytes, s));
-    st = enqueue_select(d_preop, d_mask, dims, block, stride, frac, d_centers, max_blocks, d_n_selected,
-                        (unsigned char *)ws, p, s);
+    st = enqueue_select(d_preop, d_mask, dims, block[0], stride, frac, d_centers, max_blocks, d_n_selected,
+                        (unsigned char *)ws, p, s, block[1], block[2]);
     long long nsel = 0;
     if (st == NRR_OK && h_n_selected) {
         cudaError_t e = cudaMemcpyAsync(&nsel, (unsigned char *)ws + select_count_offset(p),
@@ -487,41 +498,33 @@ extern "C" nrr_status nrr_select_blocks(const uint16_t *d_preop, const uint8_t *
     return NRR_OK;
 }
 
+extern "C" nrr_status nrr_select_blocks(const uint16_t *d_preop, const uint8_t *d_mask, nrr_dims dims, int32_t block,
+                                        int32_t stride, double frac, int32_t *d_centers, int32_t max_blocks,
+                                        int32_t *d_n_selected, int32_t *h_n_selected, void *stream)
+{
+    const int32_t b3[3] = {block, block, block};
+    return select_alloc(d_preop, d_mask, dims, b3, stride, frac, 0, d_centers, max_blocks, d_n_selected,
+                        h_n_selected, stream);
+}
+
 extern "C" nrr_status nrr_select_blocks_spaced(const uint16_t *d_preop, const uint8_t *d_mask, nrr_dims dims,
                                                int32_t block, int32_t stride, double frac, int32_t connectivity,
                                                int32_t *d_centers, int32_t max_blocks, int32_t *d_n_selected,
                                                int32_t *h_n_selected, void *stream)
 {
-    clear_error();
-    nrr_status st = check_select_args(dims, block, stride, frac);
-    if (st != NRR_OK) return st;
-    if (connectivity != 0 && connectivity != 6 && connectivity != 18 && connectivity != 26)
-        return fail(NRR_E_INVALID, "connectivity %d is not 0, 6, 18 or 26", connectivity);
-    if (max_blocks < 0) return fail(NRR_E_INVALID, "max_blocks < 0");
-    if (!d_preop || !d_mask) return fail(NRR_E_INVALID, "NULL volume or mask");
-    if (max_blocks > 0 && !d_centers) return fail(NRR_E_INVALID, "NULL centre buffer");
-    cudaStream_t s = (cudaStream_t)stream;
-    const SelectPlan p = select_plan(dims, stride, connectivity);
-    void *ws = nullptr;
-    NRR_CUDA_TRY(cudaMallocAsync(&ws, p.bytes, s));
-    st = enqueue_select(d_preop, d_mask, dims, block, stride, frac, d_centers, max_blocks, d_n_selected,
-                        (unsigned char *)ws, p, s);
-    long long nsel = 0;
-    if (st == NRR_OK && h_n_selected) {
-        cudaError_t e = cudaMemcpyAsync(&nsel, (unsigned char *)ws + select_count_offset(p),
-                                        sizeof(nsel), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) st = cuda_fail(e, "reading the selection count");
-    }
-    cudaError_t e = cudaFreeAsync(ws, s);
-    if (st != NRR_OK) return st;
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync");
-    if (h_n_selected) {
-        *h_n_selected = (int32_t)nsel;
-        if (nsel > max_blocks)
-            return fail(NRR_E_CAPACITY, "%lld blocks selected but max_blocks is %d", nsel, max_blocks);
-    }
-    return NRR_OK;
+    const int32_t b3[3] = {block, block, block};
+    return select_alloc(d_preop, d_mask, dims, b3, stride, frac, connectivity, d_centers, max_blocks, d_n_selected,
+                        h_n_selected, stream);
+}
+
+extern "C" nrr_status nrr_select_blocks_aniso(const uint16_t *d_preop, const uint8_t *d_mask, nrr_dims dims,
+                                              const int32_t block[3], int32_t stride, double frac,
+                                              int32_t *d_centers, int32_t max_blocks, int32_t *d_n_selected,
+                                              int32_t *h_n_selected, void *stream)
+{
+    if (!block) return fail(NRR_E_INVALID, "block is NULL");
+    return select_alloc(d_preop, d_mask, dims, block, stride, frac, 0, d_centers, max_blocks, d_n_selected,
+                        h_n_selected, stream);
 }
 
 // ---------------------------------------------------------------------------

@@ -62,6 +62,10 @@ SIGNATURES = {
     "nrr_boxsums": (C.c_int, [_P, C.c_int, Dims, _I32, _P, _P]),
     "nrr_block_match": (C.c_int, [_P, _P, C.c_int, Dims, _P, _I32, _P, _I32, _P, _P, _P, _P, _P]),
     "nrr_block_match_bs": (C.c_int, [_P, _P, _P, C.c_int, Dims, _P, _I32, _P, _I32, _P, _P, _P, _P, _P]),
+    "nrr_select_blocks_aniso": (C.c_int, [_P, _P, Dims, _P, _I32, C.c_double, _P, _I32, _P, _P, _P]),
+    "nrr_boxsums_aniso": (C.c_int, [_P, C.c_int, Dims, _P, _P, _P]),
+    "nrr_block_match_aniso": (C.c_int, [_P, _P, C.c_int, Dims, _P, _I32, _P, _P, _P, _P, _P, _P, _P]),
+    "nrr_block_match_bs_aniso": (C.c_int, [_P, _P, _P, C.c_int, Dims, _P, _I32, _P, _P, _P, _P, _P, _P, _P]),
     "nrr_device_status": (C.c_int, [_P]),
     "nrr_autotune_match": (C.c_int, [_P, _P, _P, C.c_int, Dims, _P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P]),
     "nrr_tuning_get": (C.c_int, [C.c_int, _I32, _P, _P]),
@@ -149,6 +153,16 @@ def radius3(radius):
     return r
 
 
+def block3(block):
+    """Block edges (bx, by, bz) as a C int32[3], or None for a cubic block
+    given as one int."""
+    if isinstance(block, (tuple, list)):
+        if len(block) != 3:
+            raise ValueError("block must be an int or (bx, by, bz)")
+        return (C.c_int32 * 3)(*(int(b) for b in block))
+    return None
+
+
 def max_selected(dims, stride: int, frac: float) -> int:
     """Upper bound on the number of blocks selection can return."""
     nx, ny, nz = dims
@@ -156,7 +170,7 @@ def max_selected(dims, stride: int, frac: float) -> int:
     return int(math.floor(0.5 + ng * frac))
 
 
-def select_blocks(preop: torch.Tensor, mask: torch.Tensor, block: int, stride: int, frac: float,
+def select_blocks(preop: torch.Tensor, mask: torch.Tensor, block, stride: int, frac: float,
                   max_blocks: int | None = None, centers: torch.Tensor | None = None,
                   n_selected: torch.Tensor | None = None, sync: bool = True, stream=None,
                   connectivity: int = 0):
@@ -164,7 +178,8 @@ def select_blocks(preop: torch.Tensor, mask: torch.Tensor, block: int, stride: i
     (x, y, z) in raster order.  With ``sync=False`` nothing is read back:
     the full ``centers`` buffer and the device count ``n_selected`` are
     returned instead.  ``connectivity`` 6, 18 or 26 applies the face, edge
-    or vertex spacing pattern (nrr_select_blocks_spaced)."""
+    or vertex spacing pattern (nrr_select_blocks_spaced).  ``block`` is the
+    block edge, or (bx, by, bz) for nrr_select_blocks_aniso."""
     _cuda_contig(preop, "preop")
     _cuda_contig(mask, "mask")
     if _dtype_code(preop) != NRR_U16:
@@ -179,7 +194,15 @@ def select_blocks(preop: torch.Tensor, mask: torch.Tensor, block: int, stride: i
     if n_selected is None:
         n_selected = torch.zeros(1, dtype=torch.int32, device=preop.device)
     h = C.c_int32(0)
-    if connectivity:
+    b3 = block3(block)
+    if b3 is not None:
+        if connectivity:
+            raise ValueError("the connectivity pattern takes a cubic block")
+        st = lib().nrr_select_blocks_aniso(_ptr(preop), _ptr(mask), dims, b3, stride, float(frac), _ptr(centers),
+                                           max_blocks, _ptr(n_selected), C.byref(h) if sync else None,
+                                           _stream(stream))
+        _check(st, "nrr_select_blocks_aniso")
+    elif connectivity:
         st = lib().nrr_select_blocks_spaced(_ptr(preop), _ptr(mask), dims, block, stride, float(frac),
                                             int(connectivity), _ptr(centers), max_blocks, _ptr(n_selected),
                                             C.byref(h) if sync else None, _stream(stream))
@@ -199,25 +222,32 @@ def boxsum_bytes(vol: torch.Tensor) -> int:
     return int(n.value)
 
 
-def boxsums(intraop: torch.Tensor, block: int, out: torch.Tensor | None = None, stream=None):
+def boxsums(intraop: torch.Tensor, block, out: torch.Tensor | None = None, stream=None):
     """Box sums S_J, S_JJ of the reference volume for one block size (an
-    opaque uint8 device buffer for :func:`block_match`)."""
+    opaque uint8 device buffer for :func:`block_match`); ``block`` is the
+    edge or (bx, by, bz)."""
     _cuda_contig(intraop, "intraop")
     nbytes = boxsum_bytes(intraop)
     if out is None:
         out = torch.empty(nbytes + 256, dtype=torch.uint8, device=intraop.device)
     off = (-out.data_ptr()) % 256
     buf = out[off:off + nbytes]
-    _check(lib().nrr_boxsums(_ptr(intraop), _dtype_code(intraop), _dims(intraop), block, _ptr(buf),
-                             _stream(stream)), "nrr_boxsums")
+    b3 = block3(block)
+    if b3 is not None:
+        _check(lib().nrr_boxsums_aniso(_ptr(intraop), _dtype_code(intraop), _dims(intraop), b3, _ptr(buf),
+                                       _stream(stream)), "nrr_boxsums_aniso")
+    else:
+        _check(lib().nrr_boxsums(_ptr(intraop), _dtype_code(intraop), _dims(intraop), block, _ptr(buf),
+                                 _stream(stream)), "nrr_boxsums")
     return buf
 
 
-def block_match(preop: torch.Tensor, intraop: torch.Tensor, centers: torch.Tensor, block: int, radius,
+def block_match(preop: torch.Tensor, intraop: torch.Tensor, centers: torch.Tensor, block, radius,
                 n_blocks: torch.Tensor | None = None, box: torch.Tensor | None = None, out=None, stream=None):
     """Exhaustive NCC block matching.  Returns (disp int32 (n,3), ncc f64 (n,),
     valid uint8 (n,)).  ``n_blocks`` is an optional device int32 count
-    (<= len(centers)); ``box`` optional precomputed box sums."""
+    (<= len(centers)); ``box`` optional precomputed box sums; ``block`` the
+    block edge or (bx, by, bz)."""
     for t, nm in ((preop, "preop"), (intraop, "intraop"), (centers, "centers")):
         _cuda_contig(t, nm)
     if preop.shape != intraop.shape or preop.dtype != intraop.dtype:
@@ -232,7 +262,16 @@ def block_match(preop: torch.Tensor, intraop: torch.Tensor, centers: torch.Tenso
     disp, ncc, valid = out
     r = (C.c_int32 * 3)(*radius3(radius))
     L = lib()
-    if box is None:
+    b3 = block3(block)
+    if b3 is not None:
+        if box is None:
+            st = L.nrr_block_match_aniso(_ptr(preop), _ptr(intraop), _dtype_code(preop), _dims(preop), _ptr(centers),
+                                         n, _ptr(n_blocks), b3, r, _ptr(disp), _ptr(ncc), _ptr(valid), _stream(stream))
+        else:
+            st = L.nrr_block_match_bs_aniso(_ptr(preop), _ptr(intraop), _ptr(box), _dtype_code(preop), _dims(preop),
+                                            _ptr(centers), n, _ptr(n_blocks), b3, r, _ptr(disp), _ptr(ncc),
+                                            _ptr(valid), _stream(stream))
+    elif box is None:
         st = L.nrr_block_match(_ptr(preop), _ptr(intraop), _dtype_code(preop), _dims(preop), _ptr(centers), n,
                                _ptr(n_blocks), block, r, _ptr(disp), _ptr(ncc), _ptr(valid), _stream(stream))
     else:
