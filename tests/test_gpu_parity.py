@@ -104,8 +104,11 @@ def test_match_clinical_workload_bit_exact(nrr):
     assert gv.all() and np.nanmedian(gn) > 0.9
 
 
+# windows whose (dy, dz) line grid pairs along z only, along y only (rz = 0),
+# with a line left over along y or along z (ry = 0), or is a single line
 @pytest.mark.parametrize("b,r", [(3, (1, 1, 1)), (5, (3, 2, 1)), (7, (0, 2, 3)), (9, (7, 7, 7)),
-                                 (11, (2, 5, 4)), (5, (6, 0, 0)), (3, (7, 1, 6))])
+                                 (11, (2, 5, 4)), (5, (6, 0, 0)), (3, (7, 1, 6)), (5, (2, 0, 3)),
+                                 (7, (1, 4, 0)), (3, (0, 0, 1)), (9, (3, 6, 7))])
 def test_match_block_sizes_and_anisotropic_windows(nrr, b, r):
     pre, intra, mask = synth.workload_pair("small")
     centers, _ = oracle.select_blocks(pre, mask, b, 2, 0.05)
