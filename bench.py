@@ -55,6 +55,7 @@ def _args():
     p.add_argument("--no-highres", action="store_true")
     p.add_argument("--no-aniso", action="store_true")
     p.add_argument("--no-spacing", action="store_true")
+    p.add_argument("--no-plain", action="store_true")
     p.add_argument("--serve-open-requests", type=int, default=400)
     p.add_argument("--serve-sweep-requests", type=int, default=300)
     p.add_argument("--serve-closed-requests", type=int, default=300)
@@ -524,6 +525,40 @@ def _phases(w, select_ms, box_ms, match_ms, peaks):
                              "frac_of_measured_hbm": box_b / box_s / 1e9 / hbm}}
 
 
+def _plain_vs_persistent(a, nrr, d_pre, d_intra, centers, n_sel, box_raw, w, flush, cap, dev):
+    """Matching alone on the clinical blocks, in the plain launch form (one CTA
+    per block, nrr_block_match_plain) and in the persistent form the step
+    uses; CUDA events on the launching stream, L2 flushed before each launch,
+    results compared bit for bit."""
+    import torch
+
+    stream = torch.cuda.current_stream()
+    box = nrr.boxsums(d_intra, w.block, out=box_raw)
+    outs = {}
+    times = {}
+    reps = max(10, min(a.steps, 50))
+    for plain in (False, True):
+        out = (torch.empty((cap, 3), dtype=torch.int32, device=dev), torch.empty(cap, dtype=torch.float64, device=dev),
+               torch.empty(cap, dtype=torch.uint8, device=dev))
+        ms = []
+        for k in range(reps + 3):
+            flush.fill_(k & 0xFF)
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            nrr.block_match(d_pre, d_intra, centers, w.block, w.radius, n_blocks=n_sel, box=box, out=out, plain=plain)
+            s1.record(stream)
+            s1.synchronize()
+            if k >= 3:
+                ms.append(s0.elapsed_time(s1))
+        nrr.device_status()
+        outs[plain] = out
+        times[plain] = sum(ms) / len(ms)
+    same = all(torch.equal(x.view(torch.uint8), y.view(torch.uint8)) for x, y in zip(outs[False], outs[True]))
+    return {"workload": "clinical blocks, matching only, L2 flushed before each launch",
+            "persistent_match_ms": times[False], "plain_match_ms": times[True],
+            "persistent_speedup": times[True] / times[False], "launches_timed": reps, "same_results": same}
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -556,18 +591,32 @@ def run_ours(a):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
+    side = torch.cuda.Stream(device=dev)
+
+    def registration(p, i, m, c_, n_, b_, o_):
+        # the box sums of the reference volume do not depend on the selection:
+        # they run on a second stream beside it (the selection's radix passes
+        # leave most of the GPU idle) and matching waits for both
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            bx = nrr.boxsums(i, w.block, out=b_)
+        nrr.select_blocks(p, m, w.block, w.stride, w.frac, max_blocks=cap, centers=c_, n_selected=n_, sync=False)
+        stream.wait_stream(side)
+        nrr.block_match(p, i, c_, w.block, w.radius, n_blocks=n_, box=bx, out=o_)
+
     def step(p, i, m, ev_phase=None):
         # ev_phase: events after selection, after box sums, after matching
+        # (the phases in sequence on one stream, to time each)
+        if ev_phase is None:
+            registration(p, i, m, centers, n_sel, box_raw, out)
+            return
         nrr.select_blocks(p, m, w.block, w.stride, w.frac, max_blocks=cap, centers=centers, n_selected=n_sel,
                           sync=False)
-        if ev_phase is not None:
-            ev_phase[0].record(stream)
+        ev_phase[0].record(stream)
         box = nrr.boxsums(i, w.block, out=box_raw)
-        if ev_phase is not None:
-            ev_phase[1].record(stream)
+        ev_phase[1].record(stream)
         nrr.block_match(p, i, centers, w.block, w.radius, n_blocks=n_sel, box=box, out=out)
-        if ev_phase is not None:
-            ev_phase[2].record(stream)
+        ev_phase[2].record(stream)
 
     for _ in range(max(3, a.warmup)):
         flush.fill_(1)
@@ -580,7 +629,8 @@ def run_ours(a):
     # one step captured as a CUDA graph (the step's launches are short and
     # many: replaying them from a graph keeps host launch latency out of the
     # device timeline); the graph's results are checked against the eager step
-    graph, graph_note = None, "one step captured as a CUDA graph and replayed"
+    graph, graph_note = None, ("one step captured as a CUDA graph and replayed; its box sums run on a second stream "
+                                "beside the selection")
     ref = [t.clone() for t in out] + [n_sel.clone()]
     try:
         graph = torch.cuda.CUDAGraph()
@@ -702,10 +752,7 @@ def run_ours(a):
             flush.fill_(k & 0xFF)
             p_, i_, m_ = din[k % 2]
             c_, n_, o_, b_ = dout[k % 2]
-            nrr.select_blocks(p_, m_, w.block, w.stride, w.frac, max_blocks=cap, centers=c_, n_selected=n_,
-                              sync=False)
-            bx = nrr.boxsums(i_, w.block, out=b_)
-            nrr.block_match(p_, i_, c_, w.block, w.radius, n_blocks=n_, box=bx, out=o_)
+            registration(p_, i_, m_, c_, n_, b_, o_)
             ev_done[k].record(stream)
             with torch.cuda.stream(d2h_s):
                 d2h_s.wait_event(ev_done[k])
@@ -758,6 +805,9 @@ def run_ours(a):
         "valid_blocks": valid_count,
         "clocks": clk.summary(t_start, t_end),
     }
+    if not a.no_plain:
+        line["plain_vs_persistent"] = _plain_vs_persistent(a, nrr, d_pre, d_intra, centers, n_sel, box_raw, w, flush,
+                                                           cap, dev)
     if not a.no_batched:
         line["batched"] = _batched_search(a, nrr, synth, d_pre, d_intra, d_mask, w, flush)
     if not a.no_serving:

@@ -258,6 +258,20 @@ nrr_status nrr_block_match_bs(const void *d_preop, const void *d_intraop, const 
                               int32_t *d_disp, double *d_ncc, uint8_t *d_valid, void *stream);
 
 /* ------------------------------------------------------------------------
+ * nrr_block_match_plain: nrr_block_match_bs in the plain launch form, one CTA
+ * per block, as the paper's GPU kernel maps its loop over blocks to thread
+ * blocks (Sec. 4.3), instead of persistent CTAs that walk the blocks with the
+ * next block's window copy in flight.  Arguments, results (identical to
+ * nrr_block_match_bs), ownership and errors are those of nrr_block_match_bs;
+ * it is there to measure what the persistent form gains.
+ * ---------------------------------------------------------------------- */
+nrr_status nrr_block_match_plain(const void *d_preop, const void *d_intraop, const void *d_boxsums,
+                                 nrr_dtype dtype, nrr_dims dims,
+                                 const int32_t *d_centers, int32_t n_blocks, const int32_t *d_n_blocks,
+                                 int32_t block, const int32_t radius[3],
+                                 int32_t *d_disp, double *d_ncc, uint8_t *d_valid, void *stream);
+
+/* ------------------------------------------------------------------------
  * Blocks with a different edge per axis (Sec. 5 lists the half block size,
  * like the half window size, per anatomical axis).  block = {bx, by, bz},
  * host int32[3], each odd in 3..11; N = bx*by*bz; the block centred at c

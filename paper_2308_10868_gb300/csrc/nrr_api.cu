@@ -227,10 +227,10 @@ static nrr_status check_match_args(const void *d_preop, const void *d_intraop, n
     return NRR_OK;
 }
 
-nrr_status nrr_block_match_bs_aniso(const void *d_preop, const void *d_intraop, const void *d_boxsums,
-                                    nrr_dtype dtype, nrr_dims dims, const int32_t *d_centers, int32_t n_blocks,
-                                    const int32_t *d_n_blocks, const int32_t block[3], const int32_t radius[3],
-                                    int32_t *d_disp, double *d_ncc, uint8_t *d_valid, void *stream)
+static nrr_status match_with_boxsums(const void *d_preop, const void *d_intraop, const void *d_boxsums,
+                                     nrr_dtype dtype, nrr_dims dims, const int32_t *d_centers, int32_t n_blocks,
+                                     const int32_t *d_n_blocks, const int32_t block[3], const int32_t radius[3],
+                                     int32_t *d_disp, double *d_ncc, uint8_t *d_valid, void *stream, bool plain)
 {
     clear_error();
     nrr_status st = check_match_args(d_preop, d_intraop, dtype, dims, d_centers, n_blocks, block, radius, d_disp,
@@ -253,10 +253,30 @@ nrr_status nrr_block_match_bs_aniso(const void *d_preop, const void *d_intraop, 
     for (int i = 0; i < 3; ++i) a.radius[i] = radius[i];
     a.n_jobs = 1;
     a.jobs[0] = MatchJob{d_centers, d_n_blocks, n_blocks, d_disp, d_ncc, d_valid};
-    a.ctas_per_sm = cubic ? tuned_ctas_per_sm(dtype, block[0], radius) : 0;
+    a.ctas_per_sm = cubic && !plain ? tuned_ctas_per_sm(dtype, block[0], radius) : 0;
+    a.one_cta_per_block = plain ? 1 : 0;
     st = device_error_word(&a.err);
     if (st != NRR_OK) return st;
     return launch_match(a, (cudaStream_t)stream);
+}
+
+nrr_status nrr_block_match_bs_aniso(const void *d_preop, const void *d_intraop, const void *d_boxsums,
+                                    nrr_dtype dtype, nrr_dims dims, const int32_t *d_centers, int32_t n_blocks,
+                                    const int32_t *d_n_blocks, const int32_t block[3], const int32_t radius[3],
+                                    int32_t *d_disp, double *d_ncc, uint8_t *d_valid, void *stream)
+{
+    return match_with_boxsums(d_preop, d_intraop, d_boxsums, dtype, dims, d_centers, n_blocks, d_n_blocks, block,
+                              radius, d_disp, d_ncc, d_valid, stream, false);
+}
+
+nrr_status nrr_block_match_plain(const void *d_preop, const void *d_intraop, const void *d_boxsums, nrr_dtype dtype,
+                                 nrr_dims dims, const int32_t *d_centers, int32_t n_blocks, const int32_t *d_n_blocks,
+                                 int32_t block, const int32_t radius[3], int32_t *d_disp, double *d_ncc,
+                                 uint8_t *d_valid, void *stream)
+{
+    const int32_t b3[3] = {block, block, block};
+    return match_with_boxsums(d_preop, d_intraop, d_boxsums, dtype, dims, d_centers, n_blocks, d_n_blocks, b3, radius,
+                              d_disp, d_ncc, d_valid, stream, true);
 }
 
 nrr_status nrr_block_match_bs(const void *d_preop, const void *d_intraop, const void *d_boxsums, nrr_dtype dtype,

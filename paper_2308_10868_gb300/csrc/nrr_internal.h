@@ -106,6 +106,7 @@ struct MatchLaunch {
     int n_jobs;
     MatchJob jobs[MATCH_MAX_JOBS];
     int ctas_per_sm;  // persistent CTAs per SM; 0 = as many as fit
+    int one_cta_per_block;  // plain launch: one CTA per block instead of persistent CTAs
     unsigned int *err;
 };
 nrr_status launch_match(const MatchLaunch &a, cudaStream_t stream);

@@ -1188,7 +1188,7 @@ nrr_status launch_match_variant_l(const MatchLaunch &m, cudaStream_t stream)
     if (m.ctas_per_sm > 0 && m.ctas_per_sm < occ) occ = m.ctas_per_sm;
     long long cap = 0;
     for (int j = 0; j < m.n_jobs; ++j) cap += m.jobs[j].cap;
-    long long grid = (long long)occ * sm_count();
+    long long grid = m.one_cta_per_block ? cap : (long long)occ * sm_count();
     if (grid > cap) grid = cap;
     if (grid < 1) return NRR_OK;
 

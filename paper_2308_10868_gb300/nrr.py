@@ -62,6 +62,7 @@ SIGNATURES = {
     "nrr_boxsums": (C.c_int, [_P, C.c_int, Dims, _I32, _P, _P]),
     "nrr_block_match": (C.c_int, [_P, _P, C.c_int, Dims, _P, _I32, _P, _I32, _P, _P, _P, _P, _P]),
     "nrr_block_match_bs": (C.c_int, [_P, _P, _P, C.c_int, Dims, _P, _I32, _P, _I32, _P, _P, _P, _P, _P]),
+    "nrr_block_match_plain": (C.c_int, [_P, _P, _P, C.c_int, Dims, _P, _I32, _P, _I32, _P, _P, _P, _P, _P]),
     "nrr_select_blocks_aniso": (C.c_int, [_P, _P, Dims, _P, _I32, C.c_double, _P, _I32, _P, _P, _P]),
     "nrr_boxsums_aniso": (C.c_int, [_P, C.c_int, Dims, _P, _P, _P]),
     "nrr_block_match_aniso": (C.c_int, [_P, _P, C.c_int, Dims, _P, _I32, _P, _P, _P, _P, _P, _P, _P]),
@@ -243,11 +244,14 @@ def boxsums(intraop: torch.Tensor, block, out: torch.Tensor | None = None, strea
 
 
 def block_match(preop: torch.Tensor, intraop: torch.Tensor, centers: torch.Tensor, block, radius,
-                n_blocks: torch.Tensor | None = None, box: torch.Tensor | None = None, out=None, stream=None):
+                n_blocks: torch.Tensor | None = None, box: torch.Tensor | None = None, out=None, stream=None,
+                plain: bool = False):
     """Exhaustive NCC block matching.  Returns (disp int32 (n,3), ncc f64 (n,),
     valid uint8 (n,)).  ``n_blocks`` is an optional device int32 count
     (<= len(centers)); ``box`` optional precomputed box sums; ``block`` the
-    block edge or (bx, by, bz)."""
+    block edge or (bx, by, bz).  ``plain`` (cubic blocks, box sums given)
+    calls nrr_block_match_plain: one CTA per block instead of persistent
+    CTAs, same results."""
     for t, nm in ((preop, "preop"), (intraop, "intraop"), (centers, "centers")):
         _cuda_contig(t, nm)
     if preop.shape != intraop.shape or preop.dtype != intraop.dtype:
@@ -263,7 +267,13 @@ def block_match(preop: torch.Tensor, intraop: torch.Tensor, centers: torch.Tenso
     r = (C.c_int32 * 3)(*radius3(radius))
     L = lib()
     b3 = block3(block)
-    if b3 is not None:
+    if plain and (b3 is not None or box is None):
+        raise ValueError("the plain launch takes a cubic block and precomputed box sums")
+    if plain:
+        st = L.nrr_block_match_plain(_ptr(preop), _ptr(intraop), _ptr(box), _dtype_code(preop), _dims(preop),
+                                     _ptr(centers), n, _ptr(n_blocks), block, r, _ptr(disp), _ptr(ncc), _ptr(valid),
+                                     _stream(stream))
+    elif b3 is not None:
         if box is None:
             st = L.nrr_block_match_aniso(_ptr(preop), _ptr(intraop), _dtype_code(preop), _dims(preop), _ptr(centers),
                                          n, _ptr(n_blocks), b3, r, _ptr(disp), _ptr(ncc), _ptr(valid), _stream(stream))

@@ -104,6 +104,28 @@ def test_match_clinical_workload_bit_exact(nrr):
     assert gv.all() and np.nanmedian(gn) > 0.9
 
 
+@pytest.mark.parametrize("key,r", [("small", None), ("clinical", None), ("small", (3, 1, 2))])
+def test_match_plain_launch(nrr, key, r):
+    """One CTA per block (nrr_block_match_plain) returns exactly what the
+    persistent launch returns; on the small workload, the oracle's result."""
+    pre, intra, mask = synth.workload_pair(key)
+    w = synth.WORKLOADS[key]
+    r = w.radius if r is None else r
+    centers, _ = oracle.select_blocks(pre, mask, w.block, w.stride, w.frac)
+    dpre, dintra = _dev_u16(nrr, pre), _dev_u16(nrr, intra)
+    dc = torch.from_numpy(np.ascontiguousarray(centers, dtype=np.int32)).cuda()
+    box = nrr.boxsums(dintra, w.block)
+    pd, pn, pv = (t.cpu().numpy() for t in nrr.block_match(dpre, dintra, dc, w.block, r, box=box, plain=True))
+    nrr.device_status()
+    qd, qn, qv = (t.cpu().numpy() for t in nrr.block_match(dpre, dintra, dc, w.block, r, box=box))
+    assert np.array_equal(pd, qd) and np.array_equal(pv, qv) and _same_ncc(pn, qn)
+    if key == "small":
+        rd, rn, rv = oracle.match(pre, intra, centers, w.block, r)
+        assert np.array_equal(pd, rd) and np.array_equal(pv, rv) and _same_ncc(pn, rn)
+    with pytest.raises(ValueError):
+        nrr.block_match(dpre, dintra, dc, w.block, r, plain=True)  # box sums required
+
+
 # windows whose (dy, dz) line grid pairs along z only, along y only (rz = 0),
 # with a line left over along y or along z (ry = 0), or is a single line
 @pytest.mark.parametrize("b,r", [(3, (1, 1, 1)), (5, (3, 2, 1)), (7, (0, 2, 3)), (9, (7, 7, 7)),
