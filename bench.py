@@ -56,6 +56,7 @@ def _args():
     p.add_argument("--no-aniso", action="store_true")
     p.add_argument("--no-spacing", action="store_true")
     p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--no-small", action="store_true")
     p.add_argument("--serve-open-requests", type=int, default=400)
     p.add_argument("--serve-sweep-requests", type=int, default=300)
     p.add_argument("--serve-closed-requests", type=int, default=300)
@@ -478,6 +479,49 @@ def _aniso(a, nrr, synth, d_pre, d_intra, d_mask, w, flush):
             "match_roofline_frac": 2.0 * evals * nblk / t_match / peak}
 
 
+def _small(a, nrr, synth, dev, flush):
+    """The small single registration (64x64x48 uint16, blocks 7^3 on a
+    stride-2 grid, top 10%, radius 4: about 940 blocks x 729 shifts), a
+    latency-bound case: selection, box sums and matching of one registration
+    on the launching stream, CUDA events around each (median of 20, L2 flushed
+    before each)."""
+    import torch
+
+    stream = torch.cuda.current_stream()
+    w = synth.WORKLOADS["small"]
+    pre, intra, mask = synth.workload_pair("small")
+    d_pre, d_intra = nrr.to_device_u16(pre, dev), nrr.to_device_u16(intra, dev)
+    d_mask = torch.from_numpy(mask).to(dev)
+    cap = nrr.max_selected(w.dims, w.stride, w.frac)
+    centers = torch.empty((cap, 3), dtype=torch.int32, device=dev)
+    n_sel = torch.zeros(1, dtype=torch.int32, device=dev)
+    out = (torch.empty((cap, 3), dtype=torch.int32, device=dev), torch.empty(cap, dtype=torch.float64, device=dev),
+           torch.empty(cap, dtype=torch.uint8, device=dev))
+    box_raw = torch.empty(nrr.boxsum_bytes(d_intra) + 256, dtype=torch.uint8, device=dev)
+    step_ms, match_ms = [], []
+    for k in range(23):
+        flush.fill_(k & 0xFF)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        nrr.select_blocks(d_pre, d_mask, w.block, w.stride, w.frac, max_blocks=cap, centers=centers, n_selected=n_sel,
+                          sync=False)
+        box = nrr.boxsums(d_intra, w.block, out=box_raw)
+        e[1].record(stream)
+        nrr.block_match(d_pre, d_intra, centers, w.block, w.radius, n_blocks=n_sel, box=box, out=out)
+        e[2].record(stream)
+        e[2].synchronize()
+        if k >= 3:
+            step_ms.append(e[0].elapsed_time(e[2]))
+            match_ms.append(e[1].elapsed_time(e[2]))
+    nrr.device_status()
+    n = int(n_sel.item())
+    evals = n * (2 * w.radius + 1) ** 3
+    st, mt = sorted(step_ms)[len(step_ms) // 2], sorted(match_ms)[len(match_ms) // 2]
+    return {"workload": w.name, "n_blocks": n, "shifts": (2 * w.radius + 1) ** 3, "evals": evals,
+            "step_ms": st, "match_ms": mt, "evals_per_s": evals / (st / 1e3),
+            "registrations_per_s": 1e3 / st, "valid_blocks": int(out[2][:n].sum().item())}
+
+
 def _spacing(a, nrr, synth, d_pre, d_mask, w, flush):
     """Selection with the face / edge / vertex connectivity patterns (6 / 18 /
     26 neighbours on the candidate grid) on the step's volume, against the
@@ -596,12 +640,15 @@ def run_ours(a):
     def registration(p, i, m, c_, n_, b_, o_):
         # the box sums of the reference volume do not depend on the selection:
         # they run on a second stream beside it (the selection's radix passes
-        # leave most of the GPU idle) and matching waits for both
-        side.wait_stream(stream)
+        # leave most of the GPU idle) and matching waits for both.  The fork
+        # and join are taken from the current stream, so that a graph capture
+        # (which runs on a capture stream of its own) records both branches.
+        cur = torch.cuda.current_stream()
+        side.wait_stream(cur)
         with torch.cuda.stream(side):
             bx = nrr.boxsums(i, w.block, out=b_)
         nrr.select_blocks(p, m, w.block, w.stride, w.frac, max_blocks=cap, centers=c_, n_selected=n_, sync=False)
-        stream.wait_stream(side)
+        cur.wait_stream(side)
         nrr.block_match(p, i, c_, w.block, w.radius, n_blocks=n_, box=bx, out=o_)
 
     def step(p, i, m, ev_phase=None):
@@ -636,7 +683,9 @@ def run_ours(a):
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, capture_error_mode="thread_local"):
             step(d_pre, d_intra, d_mask)
-        for t in out:
+        # everything the step computes is cleared first, so that a graph that
+        # skipped any of it fails the comparison below
+        for t in list(out) + [centers, n_sel, box_raw]:
             t.zero_()
         for _ in range(max(3, a.warmup)):
             flush.fill_(1)
@@ -728,6 +777,24 @@ def run_ours(a):
               torch.empty(cap, dtype=torch.uint8, device=dev)),
              torch.empty(nrr.boxsum_bytes(d_intra) + 256, dtype=torch.uint8, device=dev)) for _ in range(2)]
 
+    # each registration's compute (L2 flush, selection, box sums, matching)
+    # replayed from a CUDA graph captured from the same public calls, one per
+    # double-buffer parity: one launch per registration from the host instead
+    # of the calls' dozen (eager calls if capture is not available)
+    cgraphs = []
+    try:
+        for par in range(2):
+            g = torch.cuda.CUDAGraph()
+            p_, i_, m_ = din[par]
+            c_, n_, o_, b_ = dout[par]
+            with torch.cuda.graph(g, capture_error_mode="thread_local"):
+                flush.fill_(par + 1)
+                registration(p_, i_, m_, c_, n_, b_, o_)
+            cgraphs.append(g)
+    except Exception:
+        cgraphs = []
+        torch.cuda.synchronize()
+
     def pipelined(kk):
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev_in = [torch.cuda.Event() for _ in range(kk)]
@@ -749,10 +816,13 @@ def run_ours(a):
             stream.wait_event(ev_in[k])
             if k >= 2:
                 stream.wait_event(ev_out[k - 2])  # outputs k % 2 were read back
-            flush.fill_(k & 0xFF)
             p_, i_, m_ = din[k % 2]
             c_, n_, o_, b_ = dout[k % 2]
-            registration(p_, i_, m_, c_, n_, b_, o_)
+            if cgraphs:
+                cgraphs[k % 2].replay()
+            else:
+                flush.fill_(k & 0xFF)
+                registration(p_, i_, m_, c_, n_, b_, o_)
             ev_done[k].record(stream)
             with torch.cuda.stream(d2h_s):
                 d2h_s.wait_event(ev_done[k])
@@ -769,6 +839,11 @@ def run_ours(a):
     pipelined(3)
     e2e_value = world * evals / (pipelined(ke) / 1e3)
     assert int(h_out[3].item()) == n_blocks
+    # the last pipelined registration's results, read back to the host, are
+    # the device-resident step's results bit for bit
+    for h, d in zip(h_out[:3], ref[:3]):
+        if not torch.equal(h[:n_blocks].view(torch.uint8), d[:n_blocks].cpu().view(torch.uint8)):
+            raise RuntimeError("pipelined end-to-end results differ from the device-resident step")
 
     if rank != 0:
         return 0
@@ -795,7 +870,9 @@ def run_ours(a):
         "phases": _phases(w, select_ms, box_ms, match_ms, peaks),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
                 "pipelining": "each step's inputs copied from pinned host memory and results copied back inside "
-                              "the timed region, overlapped with the neighbouring steps' compute (3 streams)",
+                              "the timed region, overlapped with the neighbouring steps' compute (3 streams); "
+                              + ("each step's compute replayed from a CUDA graph captured from the public calls"
+                                 if cgraphs else "each step's compute launched by the public calls"),
                 "serial_value": e2e_serial},
         "gpu_launches": launches,
         "gpu_launches_per_step": launches / a.steps,
@@ -808,6 +885,8 @@ def run_ours(a):
     if not a.no_plain:
         line["plain_vs_persistent"] = _plain_vs_persistent(a, nrr, d_pre, d_intra, centers, n_sel, box_raw, w, flush,
                                                            cap, dev)
+    if not a.no_small:
+        line["small"] = _small(a, nrr, synth, dev, flush)
     if not a.no_batched:
         line["batched"] = _batched_search(a, nrr, synth, d_pre, d_intra, d_mask, w, flush)
     if not a.no_serving:
