@@ -332,6 +332,8 @@ __device__ __forceinline__ void search_line(const T *row0, int zstride, const fl
     constexpr int NC = (XO + WX - 1) / EPC + 1;  // 16-byte chunks covering [XO, XO + WX)
     constexpr int PT = (B + 3) / 4 * 4;
     constexpr int BX = match_bx<T, B, P>();
+    unsigned long long negc2;  // (-csh, -csh) as one f32x2 operand
+    asm("mov.b64 %0, {%1, %1};" : "=l"(negc2) : "f"(-csh));
 #pragma unroll 1
     for (int kz = 0; kz < bz; ++kz) {
 #pragma unroll 1
@@ -350,26 +352,37 @@ __device__ __forceinline__ void search_line(const T *row0, int zstride, const fl
                 t[4 * q + 2] = v.z;
                 t[4 * q + 3] = v.w;
             }
-            float j[WX];
+            // the raw bits of each value as a float: uint16 as 0x4B00|u, the
+            // float 2^23 + u (one byte-permute), float32 as it is
+            uint32_t raw[WX];
 #pragma unroll
             for (int e = 0; e < WX; ++e) {
-                constexpr int dummy = 0;
-                (void)dummy;
                 const int E = XO + e;  // element within the loaded chunks (compile-time after unrolling)
                 const uint4 &q = ch[E / EPC];
                 if constexpr (F32) {
                     const int w = E % 4;
-                    const uint32_t bits = w == 0 ? q.x : w == 1 ? q.y : w == 2 ? q.z : q.w;
-                    j[e] = __fsub_rn(__uint_as_float(bits), csh);
+                    raw[e] = w == 0 ? q.x : w == 1 ? q.y : w == 2 ? q.z : q.w;
                 } else {
                     const int w = (E % 8) / 2;
                     const uint32_t word = w == 0 ? q.x : w == 1 ? q.y : w == 2 ? q.z : q.w;
-                    // 0x4B00|u is the float 2^23 + u: one byte-permute, then
-                    // subtracting 2^23 + c gives u - c exactly
-                    const uint32_t bits = (E & 1) ? __byte_perm(word, 0x4B00u, 0x5432) : __byte_perm(word, 0x4B00u, 0x5410);
-                    j[e] = __fsub_rn(__uint_as_float(bits), csh);
+                    raw[e] = (E & 1) ? __byte_perm(word, 0x4B00u, 0x5432) : __byte_perm(word, 0x4B00u, 0x5410);
                 }
             }
+            // minus the centring constant (2^23 + c for uint16, so u - c
+            // exactly), two values per packed f32x2 subtraction
+            float j[WX];
+#pragma unroll
+            for (int e = 0; e + 1 < WX; e += 2) {
+                unsigned long long d;
+                asm("{\n\t.reg .b64 pa;\n\t"
+                    "mov.b64 pa, {%1, %2};\n\t"
+                    "add.rn.f32x2 %0, pa, %3;\n\t}"
+                    : "=l"(d)
+                    : "r"(raw[e]), "r"(raw[e + 1]), "l"(negc2));
+                j[e] = __uint_as_float((uint32_t)d);
+                j[e + 1] = __uint_as_float((uint32_t)(d >> 32));
+            }
+            if constexpr (WX & 1) j[WX - 1] = __fsub_rn(__uint_as_float(raw[WX - 1]), csh);
 #pragma unroll
             for (int kx = 0; kx < B; ++kx)
 #pragma unroll
