@@ -226,6 +226,9 @@ def _check_f32(nrr, pre32, intra32, centers, b, r):
     assert err.max() <= F32_NCC_TOL, err.max()
     diff = (gd != rd).any(axis=1) & ok
     assert (rn[diff] - at_gpu[diff] <= F32_TIE_TOL).all()
+    print(f"\nfloat32 b={b} r={r}: NCC error against FP64 at the returned shift: max {err.max():.3g}, "
+          f"mean {err.mean():.3g} over {int(ok.sum())} blocks; shift differs from the FP64 arg-max in "
+          f"{int(diff.sum())} (within {F32_TIE_TOL:g} of its score)")
     return err.max(), diff.mean()
 
 
