@@ -20,7 +20,8 @@
 //      shifts along x.  For every template row it reads the window row
 //      straight from the TMA buffer with 16-byte loads, turns the values it
 //      needs into floats shifted by a per-block constant c (J'_k = J_k - c;
-//      for uint16 one byte-permute and one subtraction, exact), and
+//      for uint16 one byte-permute per value, then the subtraction two
+//      values at a time as packed f32x2, exact), and
 //      accumulates A(d) = sum_k T_k J'_{k+d} with FP32 FFMA, fully unrolled
 //      over the row and the x shifts.  The offset xo is a compile-time
 //      parameter of the loop, so every register index is static.
@@ -30,11 +31,12 @@
 //      chain, Cauchy-Schwarz sum|T||J'| <= sqrt(sum T^2 * sum J'^2), plus the
 //      rounding of the final operations; doubled for margin).
 //   5. Shifts whose upper bound reaches the best lower bound survive (about
-//      one per block on the phantoms) and are rescored: a warp per survivor,
-//      or, with fewer survivors than warps, each survivor's terms split over
-//      several warps.  uint16 -> exact int64 sum, then the canonical FP64
-//      ratio num / sqrt(vI * vJ); float32 -> FP64 Pearson.  The best
-//      survivor under the tie-break rule is the block's answer.
+//      one per block on the phantoms) and are rescored: a warp per survivor
+//      (float32 with fewer survivors than warps: each survivor's terms split
+//      over several warps).  uint16 -> exact int64 sums, then the canonical
+//      FP64 ratio num / sqrt(vI * vJ); float32 -> Pearson sums in
+//      float-float pairs and one FP64 ratio.  The best survivor under the
+//      tie-break rule is the block's answer.
 // The exhaustive maximum is therefore found exactly: the true arg-max can
 // never be filtered out, because its upper bound is at least its value,
 // which is at least every other shift's value, hence at least every lower
