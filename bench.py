@@ -156,13 +156,14 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # recorded ncu traffic of the match kernel (valid only for the same source)
 # --------------------------------------------------------------------------
-def _kernel_source_hash():
+def _kernel_source_hash(csrc=None):
     """First 16 hex digits of sha256 over the match kernel's sources with
     their // comments and blank lines removed (an edit of a comment does not
     change the kernel the counters were taken on)."""
+    csrc = csrc or os.path.join(ROOT, "paper_2308_10868_gb300", "csrc")
     h = hashlib.sha256()
     for f in ("nrr_match.cuh", "nrr_ptx.cuh"):
-        text = open(os.path.join(ROOT, "paper_2308_10868_gb300", "csrc", f), encoding="utf-8").read()
+        text = open(os.path.join(csrc, f), encoding="utf-8").read()
         code = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
         h.update("\n".join(ln for ln in code if ln).encode())
     return h.hexdigest()[:16]
