@@ -1,0 +1,157 @@
+"""The match kernel's filter, checked on the CPU: for uint16 inputs the
+kernel scores every shift with an FP32 correlation and keeps for exact
+rescoring only the shifts whose upper bound reaches the best lower bound.
+That is exact only if, at every shift, the approximate NCC v and its bound e
+satisfy |v - NCC| <= e, NCC being the exact Pearson correlation (Sec. 3, the
+NCC equation).  This test emulates the kernel's float32 arithmetic in numpy,
+operation by operation and in the kernel's order (FMA chains over the
+template rows, the box-sum terms, the bound), with rsqrt.approx and
+sqrt.approx replaced by the exact value perturbed to the edges of their
+2^-22 relative error, and checks the inequality on data chosen to stress it:
+smooth blocks, full-range noise, near-flat blocks with a large mean, two-level
+blocks and near-perfect matches.
+"""
+import numpy as np
+import pytest
+
+U = np.float32(2.0 ** -24)
+F = np.float32
+
+
+def f32(x):
+    return np.asarray(x, dtype=np.float64).astype(np.float32)
+
+
+def fma32(a, b, c):
+    # a*b is exact in float64 (24 + 24 bits); one rounding to float64, then to float32
+    return (a.astype(np.float64) * b.astype(np.float64) + c.astype(np.float64)).astype(np.float32)
+
+
+def round_up32(x):
+    f = np.float32(x)
+    return f if float(f) >= x else np.nextafter(f, np.float32(np.inf))
+
+
+def approx(exact64, delta):
+    # an approximate unit with relative error |delta| <= 2^-22
+    return f32(exact64 * (1.0 + delta))
+
+
+def kernel_bound(I, W, R, delta_rsqrt, delta_sqrt):
+    """Approximate NCC v, bound e and exact NCC for every shift of the block
+    I (b^3, uint16 values) in the window W ((b+2R)^3), all shifts inside."""
+    b = I.shape[0]
+    N = b ** 3
+    P = 2 * R + 1
+    I64 = I.astype(np.int64)
+    S_I, S_II = int(I64.sum()), int((I64 * I64).sum())
+    vI = N * S_II - S_I * S_I
+    m = (2 * S_I + N) // (2 * N)  # nearest integer to the block mean
+    rr = N * m - S_I
+    qt = int(((I64 - m) ** 2).sum())
+    # window centring constant: nearest integer mean of the block at zero shift
+    W64 = W.astype(np.int64)
+    S_Jc = int(W64[R:R + b, R:R + b, R:R + b].sum())
+    c = (2 * S_Jc + N) // (2 * N)
+    T = (I64 - m).astype(np.float32)  # exact
+    Jc = (W64 - c).astype(np.float32)  # exact
+    # A(d) = sum_k T_k (J_{k+d} - c): FMA chains in the kernel's order
+    acc = np.zeros((P, P, P), np.float32)
+    for kz in range(b):
+        for ky in range(b):
+            for kx in range(b):
+                acc = fma32(np.full((P, P, P), T[kz, ky, kx], np.float32),
+                            Jc[kz:kz + P, ky:ky + P, kx:kx + P], acc)
+    # exact sums per shift
+    S_J = np.zeros((P, P, P), np.int64)
+    S_JJ = np.zeros((P, P, P), np.int64)
+    S_IJ = np.zeros((P, P, P), np.int64)
+    for dz in range(P):
+        for dy in range(P):
+            for dx in range(P):
+                blk = W64[dz:dz + b, dy:dy + b, dx:dx + b]
+                S_J[dz, dy, dx] = blk.sum()
+                S_JJ[dz, dy, dx] = (blk * blk).sum()
+                S_IJ[dz, dy, dx] = (blk * I64).sum()
+    vJ = N * S_JJ - S_J * S_J
+    num = N * S_IJ - S_I * S_J
+    with np.errstate(invalid="ignore", divide="ignore"):
+        ncc = num.astype(np.float64) / np.sqrt(float(vI) * vJ.astype(np.float64))
+    # the bound, as the kernel evaluates it (uint16 path)
+    fN = F(N)
+    GAMMA_N = N * 2.0 ** -24 / (1.0 - N * 2.0 ** -24)
+    qf = F(qt)
+    kq = round_up32(float(round_up32(float(F(N * GAMMA_N)) * float(round_up32(np.sqrt(float(qf)))))) * 1.000004)
+    fvI, frr = F(vI), F(rr)
+    vjf = f32(vJ)
+    s1pf = f32(S_J - N * c)
+    inv_n = F(1.0) / fN
+    s2p = (fma32(s1pf, s1pf, vjf) * inv_n) * (F(1.0) + F(16.0) * U)
+    inv = approx(1.0 / np.sqrt((fvI * vjf).astype(np.float64)), delta_rsqrt)
+    na = fN * acc
+    rs = frr * s1pf
+    v = (na + rs) * inv
+    sq = approx(np.sqrt(s2p.astype(np.float64)), delta_sqrt)
+    e = (kq * sq * inv + F(4.0) * U * (np.abs(na) + np.abs(rs)) * inv) * (F(1.0) + F(64.0) * U) + F(40.0) * U * np.abs(v)
+    e = F(2.0) * e + F(1e-9)
+    valid = vjf > 0
+    return v.astype(np.float64), e.astype(np.float64), ncc, valid
+
+
+def _smooth(rng, shape, lo, hi):
+    z, y, x = np.meshgrid(*[np.arange(s) for s in shape], indexing="ij")
+    f = np.zeros(shape)
+    for _ in range(6):
+        cz, cy, cx = (rng.uniform(0, s) for s in shape)
+        sg = rng.uniform(2, 6)
+        f += rng.uniform(-1, 1) * np.exp(-((z - cz) ** 2 + (y - cy) ** 2 + (x - cx) ** 2) / (2 * sg * sg))
+    f = (f - f.min()) / (np.ptp(f) + 1e-12)
+    return np.rint(lo + (hi - lo) * f).astype(np.uint16)
+
+
+def _cases():
+    rng = np.random.default_rng(20231)
+    b, R = 7, 3
+    w = b + 2 * R
+    cases = []
+    W = _smooth(rng, (w, w, w), 500, 4000)
+    cases.append(("smooth", W[R:R + b, R:R + b, R:R + b].copy(), W))
+    W2 = np.clip(W.astype(np.int64) + rng.normal(0, 30, W.shape).round().astype(np.int64), 0, 65535).astype(np.uint16)
+    cases.append(("smooth + noise, matching block", W[R + 1:R + 1 + b, R:R + b, R - 1:R - 1 + b].copy(), W2))
+    cases.append(("full-range noise", rng.integers(0, 65536, (b, b, b), dtype=np.uint16),
+                  rng.integers(0, 65536, (w, w, w), dtype=np.uint16)))
+    cases.append(("near-flat, large mean", (40000 + rng.integers(-3, 4, (b, b, b))).astype(np.uint16),
+                  (40000 + rng.integers(-3, 4, (w, w, w))).astype(np.uint16)))
+    cases.append(("two-level extremes", (65535 * rng.integers(0, 2, (b, b, b))).astype(np.uint16),
+                  (65535 * rng.integers(0, 2, (w, w, w))).astype(np.uint16)))
+    cases.append(("self-match", W[R:R + b, R:R + b, R:R + b].copy(), W))
+    return cases, R
+
+
+@pytest.mark.parametrize("delta_rsqrt,delta_sqrt", [(2.0 ** -22, 2.0 ** -22), (-2.0 ** -22, -2.0 ** -22),
+                                                      (2.0 ** -22, -2.0 ** -22), (0.0, 0.0)])
+def test_filter_bound_covers_the_error(delta_rsqrt, delta_sqrt):
+    cases, R = _cases()
+    for name, I, W in cases:
+        v, e, ncc, valid = kernel_bound(I, W, R, delta_rsqrt, delta_sqrt)
+        assert valid.any(), name
+        err = np.abs(v - ncc)[valid]
+        assert (err <= e[valid]).all(), (name, float((err - e[valid]).max()))
+
+
+def test_filter_bound_is_tight_enough_to_filter():
+    """The bound is a worst case (about fifty times the error seen here), but
+    it stays small against the spread of the NCC values, so one shift
+    survives on each case; and it is within a hundredfold of the error
+    actually made, so a bound a hundred times smaller would be violated (the
+    covering test above can fail)."""
+    cases, R = _cases()
+    for name, I, W in cases:
+        v, e, ncc, valid = kernel_bound(I, W, R, 2.0 ** -22, 2.0 ** -22)
+        lb = (v - e)[valid].max()
+        survivors = int(((v + e)[valid] >= lb).sum())
+        assert e[valid].max() < 1e-3, (name, e[valid].max())
+        assert survivors <= 3, (name, survivors)
+    name, I, W = cases[0]
+    v, e, ncc, valid = kernel_bound(I, W, R, 2.0 ** -22, 2.0 ** -22)
+    assert (np.abs(v - ncc)[valid] > e[valid] / 100).any()
