@@ -9,7 +9,8 @@ template rows, the box-sum terms, the bound), with rsqrt.approx and
 sqrt.approx replaced by the exact value perturbed to the edges of their
 2^-22 relative error, and checks the inequality on data chosen to stress it:
 smooth blocks, full-range noise, near-flat blocks with a large mean, two-level
-blocks and near-perfect matches.
+blocks and near-perfect matches.  The float32 path's bound is checked the same
+way further down.
 """
 import numpy as np
 import pytest
@@ -155,3 +156,142 @@ def test_filter_bound_is_tight_enough_to_filter():
     name, I, W = cases[0]
     v, e, ncc, valid = kernel_bound(I, W, R, 2.0 ** -22, 2.0 ** -22)
     assert (np.abs(v - ncc)[valid] > e[valid] / 100).any()
+
+
+# ---------------------------------------------------------------------------
+# float32 intensities: the same check for the float32 path's bound, which also
+# covers the rounding of the inputs' centring, of the float box sums (three
+# levels of b-term sums) and of the float block constants; shifts whose
+# reference spread the float sums cannot resolve are rescored unconditionally
+# (no bound is claimed for them).
+# ---------------------------------------------------------------------------
+def _box_f32(blk):
+    """Sum of a b^3 float32 block as the box kernel forms it: b terms along
+    x, then b of those along y, then b along z, each level in float32."""
+    sx = blk[:, :, 0].copy()
+    for x in range(1, blk.shape[2]):
+        sx = sx + blk[:, :, x]
+    sy = sx[:, 0].copy()
+    for y in range(1, blk.shape[1]):
+        sy = sy + sx[:, y]
+    sz = sy[0]
+    for z in range(1, blk.shape[0]):
+        sz = sz + sy[z]
+    return np.float32(sz)
+
+
+def kernel_bound_f32(I, W, R, delta_rsqrt, delta_sqrt):
+    b = I.shape[0]
+    N = b ** 3
+    P = 2 * R + 1
+    fN = F(N)
+    # block constants (the kernel sums I - I0 in float-float: about 2^-48
+    # relative, taken here as exact)
+    i0 = I[0, 0, 0]
+    d = I.astype(np.float64) - float(i0)
+    s1, s2 = float(d.sum()), float((d * d).sum())
+    tsh = i0 + F(s1) * (F(1.0) / fN)  # any float near the mean
+    ibar = float(i0) + s1 / N
+    dv = max(s2 - s1 * (s1 / N), 0.0)
+    em = ibar - float(tsh)
+    emu, fvI = F(em), F(dv)
+    kq = F(np.sqrt((dv + 2048.0 * 1.1102230246251565e-16 * s2 + N * em * em) * (1.0 + 2.4e-7)) * (1.0 + 1e-6))
+    T = I - tsh  # float32, rounded as in the kernel
+    # float box sums of J and J^2 at every shift, and the centring constant
+    S1 = np.zeros((P, P, P), np.float32)
+    S2 = np.zeros((P, P, P), np.float32)
+    for dz in range(P):
+        for dy in range(P):
+            for dx in range(P):
+                blk = W[dz:dz + b, dy:dy + b, dx:dx + b]
+                S1[dz, dy, dx] = _box_f32(blk)
+                S2[dz, dy, dx] = _box_f32(blk * blk)
+    c_f = S1[R, R, R] / fN
+    Jc = W - c_f
+    acc = np.zeros((P, P, P), np.float32)
+    for kz in range(b):
+        for ky in range(b):
+            for kx in range(b):
+                acc = fma32(np.full((P, P, P), T[kz, ky, kx], np.float32), Jc[kz:kz + P, ky:ky + P, kx:kx + P], acc)
+    # exact Pearson correlation of the float values (two-pass, float64)
+    I64 = I.astype(np.float64) - I.astype(np.float64).mean()
+    ncc = np.full((P, P, P), np.nan)
+    for dz in range(P):
+        for dy in range(P):
+            for dx in range(P):
+                J64 = W[dz:dz + b, dy:dy + b, dx:dx + b].astype(np.float64)
+                J64 = J64 - J64.mean()
+                den = np.sqrt((I64 * I64).sum() * (J64 * J64).sum())
+                if den > 0:
+                    ncc[dz, dy, dx] = (I64 * J64).sum() / den
+    # the bound, as the kernel evaluates it (float32 path)
+    GS = F((3 * b) * 2.0 ** -24 / (1.0 - (3 * b) * 2.0 ** -24))
+    GN = F(N * 2.0 ** -24 / (1.0 - N * 2.0 ** -24))
+    s1b, s2b = S1, np.maximum(S2, F(0.0))
+    d1 = approx(np.sqrt((fN * s2b).astype(np.float64)), delta_sqrt)
+    d1 = GS * d1 * F(1.01)
+    s1sq_n = (s1b * s1b) * (F(1.0) / fN)
+    vJa = s2b - s1sq_n
+    dvJ = GS * s2b + (F(2.0) * np.abs(s1b) + d1) * d1 / fN + F(4.0) * U * (s2b + s1sq_n)
+    s1p = s1b - fN * c_f
+    m2 = s2b + F(2.0) * np.abs(c_f) * np.abs(s1b) + fN * c_f * c_f
+    e2 = (s2b - F(2.0) * c_f * s1b) + fN * c_f * c_f
+    sj2 = (np.maximum(e2, F(0.0)) + (GS + F(8.0) * U) * m2 * F(1.01)) * (F(1.0) + F(4.0) * U)
+    resolved = (vJa - dvJ) > 0
+    with np.errstate(invalid="ignore", divide="ignore"):
+        rho = dvJ / (vJa - dvJ)
+    bounded = resolved & (rho <= F(0.25))
+    with np.errstate(invalid="ignore", divide="ignore"):
+        inv = approx(1.0 / np.sqrt((fvI * vJa).astype(np.float64)), delta_rsqrt)
+    sq = approx(np.sqrt(sj2.astype(np.float64)), delta_sqrt)
+    A = acc
+    es = emu * s1p
+    num = A - es
+    v = num * inv
+    enum = ((GN + F(3.0) * U) * kq * sq + np.abs(emu) * (np.abs(s1p) + d1 + F(2.0) * U * fN * np.abs(c_f)) * F(1.01)
+            + U * (np.abs(A) + np.abs(es)))
+    e = (enum * inv * (F(1.0) + F(0.7) * rho + F(4.0) * U) + np.abs(num) * inv * (F(0.7) * rho + F(6.0) * U)) \
+        * (F(1.0) + F(64.0) * U) + F(43.0) * U * np.abs(v)
+    e = F(2.0) * e + F(1e-9)
+    return v.astype(np.float64), e.astype(np.float64), ncc, bounded & ~np.isnan(ncc)
+
+
+def _cases_f32():
+    cases, R = _cases()
+    out = [(name, (I.astype(np.float32) / np.float32(65535.0)), (W.astype(np.float32) / np.float32(65535.0)))
+           for name, I, W in cases]
+    rng = np.random.default_rng(7)
+    b, w = 7, 7 + 2 * R
+    # offsets large against the spread: the centring matters (at 50x the
+    # float sums still resolve the spread; at 10^5x every shift is rescored)
+    for off, spread in ((50.0, 1.0), (1000.0, 0.01)):
+        I = np.float32(off) + rng.random((b, b, b)).astype(np.float32) * np.float32(spread)
+        W = np.float32(off) + rng.random((w, w, w)).astype(np.float32) * np.float32(spread)
+        out.append((f"offset {off:g}, spread {spread:g}", I, W))
+    return out, R
+
+
+@pytest.mark.parametrize("delta_rsqrt,delta_sqrt", [(2.0 ** -22, 2.0 ** -22), (-2.0 ** -22, -2.0 ** -22),
+                                                      (2.0 ** -22, -2.0 ** -22), (0.0, 0.0)])
+def test_filter_bound_f32_covers_the_error(delta_rsqrt, delta_sqrt):
+    cases, R = _cases_f32()
+    n_bounded_cases = 0
+    for name, I, W in cases:
+        with np.errstate(invalid="ignore", divide="ignore"):
+            v, e, ncc, bounded = kernel_bound_f32(I, W, R, delta_rsqrt, delta_sqrt)
+        if not bounded.any():  # spread not resolved: every shift is rescored exactly
+            continue
+        n_bounded_cases += 1
+        err = np.abs(v - ncc)[bounded]
+        assert (err <= e[bounded]).all(), (name, float((err - e[bounded]).max()))
+    assert n_bounded_cases >= 6
+
+
+def test_filter_bound_f32_leaves_few_survivors():
+    cases, R = _cases_f32()
+    for name, I, W in cases[:2]:
+        with np.errstate(invalid="ignore", divide="ignore"):
+            v, e, ncc, bounded = kernel_bound_f32(I, W, R, 2.0 ** -22, 2.0 ** -22)
+        assert bounded.all(), name  # smooth data: every shift is bounded, none forced to rescoring
+        lb = (v - e)[bounded].max()
+        assert int(((v + e)[bounded] >= lb).sum()) <= 3, name
