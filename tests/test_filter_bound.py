@@ -181,8 +181,8 @@ def _box_f32(blk):
 
 
 def kernel_bound_f32(I, W, R, delta_rsqrt, delta_sqrt):
-    b = I.shape[0]
-    N = b ** 3
+    bz, by, bx = I.shape  # a block with an edge per axis: the box-sum depth is bx + by + bz
+    N = bx * by * bz
     P = 2 * R + 1
     fN = F(N)
     # block constants (the kernel sums I - I0 in float-float: about 2^-48
@@ -203,15 +203,15 @@ def kernel_bound_f32(I, W, R, delta_rsqrt, delta_sqrt):
     for dz in range(P):
         for dy in range(P):
             for dx in range(P):
-                blk = W[dz:dz + b, dy:dy + b, dx:dx + b]
+                blk = W[dz:dz + bz, dy:dy + by, dx:dx + bx]
                 S1[dz, dy, dx] = _box_f32(blk)
                 S2[dz, dy, dx] = _box_f32(blk * blk)
     c_f = S1[R, R, R] / fN
     Jc = W - c_f
     acc = np.zeros((P, P, P), np.float32)
-    for kz in range(b):
-        for ky in range(b):
-            for kx in range(b):
+    for kz in range(bz):
+        for ky in range(by):
+            for kx in range(bx):
                 acc = fma32(np.full((P, P, P), T[kz, ky, kx], np.float32), Jc[kz:kz + P, ky:ky + P, kx:kx + P], acc)
     # exact Pearson correlation of the float values (two-pass, float64)
     I64 = I.astype(np.float64) - I.astype(np.float64).mean()
@@ -219,13 +219,14 @@ def kernel_bound_f32(I, W, R, delta_rsqrt, delta_sqrt):
     for dz in range(P):
         for dy in range(P):
             for dx in range(P):
-                J64 = W[dz:dz + b, dy:dy + b, dx:dx + b].astype(np.float64)
+                J64 = W[dz:dz + bz, dy:dy + by, dx:dx + bx].astype(np.float64)
                 J64 = J64 - J64.mean()
                 den = np.sqrt((I64 * I64).sum() * (J64 * J64).sum())
                 if den > 0:
                     ncc[dz, dy, dx] = (I64 * J64).sum() / den
     # the bound, as the kernel evaluates it (float32 path)
-    GS = F((3 * b) * 2.0 ** -24 / (1.0 - (3 * b) * 2.0 ** -24))
+    depth = bx + by + bz
+    GS = F(depth * 2.0 ** -24 / (1.0 - depth * 2.0 ** -24))
     GN = F(N * 2.0 ** -24 / (1.0 - N * 2.0 ** -24))
     s1b, s2b = S1, np.maximum(S2, F(0.0))
     d1 = approx(np.sqrt((fN * s2b).astype(np.float64)), delta_sqrt)
@@ -295,3 +296,18 @@ def test_filter_bound_f32_leaves_few_survivors():
         assert bounded.all(), name  # smooth data: every shift is bounded, none forced to rescoring
         lb = (v - e)[bounded].max()
         assert int(((v + e)[bounded] >= lb).sum()) <= 3, name
+
+
+def test_filter_bound_f32_blocks_with_an_edge_per_axis():
+    rng = np.random.default_rng(11)
+    R = 2
+    for bz, by, bx in ((3, 5, 9), (9, 7, 3), (11, 3, 5)):
+        shape = (bz + 2 * R, by + 2 * R, bx + 2 * R)
+        W = _smooth(rng, shape, 200, 3000).astype(np.float32) / np.float32(65535.0)
+        W = W + (rng.normal(0, 3, shape) / 65535.0).astype(np.float32)
+        I = W[R:R + bz, R:R + by, R:R + bx].copy()
+        with np.errstate(invalid="ignore", divide="ignore"):
+            v, e, ncc, bounded = kernel_bound_f32(I, W, R, 2.0 ** -22, -2.0 ** -22)
+        assert bounded.any()
+        err = np.abs(v - ncc)[bounded]
+        assert (err <= e[bounded]).all(), ((bz, by, bx), float((err - e[bounded]).max()))
