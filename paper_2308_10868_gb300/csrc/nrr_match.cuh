@@ -7,36 +7,42 @@
 //   1. TMA tiled loads bring the block's search window of the reference
 //      image, [c-h-R, c+h+R] per axis, and the floating block [c-h, c+h]^3
 //      into shared memory.  The x start is rounded down to a 16-byte
-//      boundary (offset xo); the box is widened so that its row and plane
-//      pitches make every 16-byte load of 8 consecutive threads hit 8
-//      distinct bank groups.  Out-of-volume voxels arrive as zeros and are
-//      excluded by coordinates.
-//   2. Every warp sums a share of the floating block; each thread combines
-//      the partials into the shift m (cheap, identical everywhere) and
-//      thread 0 alone derives the FP64 block constants (FP64 issue is
-//      scarce on this part).  The CTA stores the block mean-shifted
-//      (T_k = I_k - m) as float.
-//   3. Search: thread t owns one (dz, dy) line of the window and all 2*rx+1
-//      shifts along x.  For every template row it reads the window row
-//      straight from the TMA buffer with 16-byte loads, turns the values it
-//      needs into floats shifted by a per-block constant c (J'_k = J_k - c;
-//      for uint16 one byte-permute per value, then the subtraction two
-//      values at a time as packed f32x2, exact), and
-//      accumulates A(d) = sum_k T_k J'_{k+d} with FP32 FFMA, fully unrolled
-//      over the row and the x shifts.  The offset xo is a compile-time
-//      parameter of the loop, so every register index is static.
+//      boundary (offset xo); the CTA then shifts every window row left by xo
+//      in place, so the search reads each row from element 0 with aligned
+//      16-byte loads.  Out-of-volume voxels arrive as zeros and are excluded
+//      by coordinates.
+//   2. Every warp sums the whole floating block (uint16: exact integers;
+//      float32: float-float pairs), so every thread holds the block's
+//      statistics without a barrier; thread 0 stores the constants the later
+//      phases need.  The CTA stores the mean-shifted block T_k = I_k - m as
+//      float (uint16: scaled by 2^64, see 3).
+//   3. Search: a thread owns two neighbouring (dz, dy) lines of the window
+//      (one row apart along y, or along z for the lines left over) and all
+//      2*rx+1 shifts along x of both.  It walks the window rows the pair
+//      shares: each row is loaded once with 16-byte loads and converted once,
+//      then multiplied with the template row of the first line and with the
+//      previous template row for the second line.  Window values enter
+//      centred by the floating block's mean: uint16 u becomes the subnormal
+//      float (u - m) * 2^-149 by one byte-permute and a packed subtraction
+//      of two values (exact); the template scaled by 2^64 brings the
+//      products into the normal range, and every partial sum is a multiple
+//      of 2^-85, so none underflows.  A(d) = sum_k T_k J_{k+d} accumulates
+//      with FP32 FFMA, one chain of N terms per shift.
 //   4. Every shift gets an approximate NCC from A(d) and the box sums S_J,
-//      S_JJ (precomputed, exact for uint16) together with a rigorous bound on
-//      its error (recursive-summation bound gamma_N * sum|T||J'| for the FFMA
-//      chain, Cauchy-Schwarz sum|T||J'| <= sqrt(sum T^2 * sum J'^2), plus the
-//      rounding of the final operations; doubled for margin).
-//   5. Shifts whose upper bound reaches the best lower bound survive (about
-//      one per block on the phantoms) and are rescored: a warp per survivor
-//      (float32 with fewer survivors than warps: each survivor's terms split
-//      over several warps).  uint16 -> exact int64 sums, then the canonical
-//      FP64 ratio num / sqrt(vI * vJ); float32 -> Pearson sums in
+//      S_JJ (precomputed, exact for uint16; both lines' loads issued
+//      together) and a rigorous bound on its error (recursive-summation
+//      bound gamma_N * sum|T||J - m| for the FMA chain, Cauchy-Schwarz
+//      sum|T||J - m| <= sqrt(sum T^2 * sum (J - m)^2), plus the rounding of
+//      the final operations, each written as a separately rounded operation;
+//      doubled for margin).
+//   5. Shifts whose upper bound reaches the best lower bound over the CTA
+//      survive (about one per block on the phantoms); each warp rescores
+//      the survivors of its own lines: uint16 -> exact int64 sums, then the
+//      canonical FP64 ratio num / sqrt(vI * vJ); float32 -> Pearson sums in
 //      float-float pairs and one FP64 ratio.  The best survivor under the
 //      tie-break rule is the block's answer.
+// Three CTA barriers per block: after the template, after the lower bounds,
+// after the rescoring.
 // The exhaustive maximum is therefore found exactly: the true arg-max can
 // never be filtered out, because its upper bound is at least its value,
 // which is at least every other shift's value, hence at least every lower
@@ -72,36 +78,39 @@ constexpr int MATCH_MAX_THREADS = 256;
 constexpr int MATCH_MAX_WARPS = MATCH_MAX_THREADS / 32;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s
 
-// Per-block constants produced by warp 0 and read by the whole CTA.
-struct BlockConst {
-    long long vI;   // uint16: N*S_II - S_I^2 (exact)
-    long long rr;   // uint16: N*m - S_I
-    double dvI;     // float32: sum (I - Ibar)^2
-    double ibar;    // float32: mean of I
-    float ibh, ibl; // float32: the mean as a float pair (ibh + ibl)
-    float fvI;      // vI as float
-    float frr;      // uint16: rr as float (exact: |rr| <= N/2)
-    float kq;       // uint16: N*gamma_N*sqrt(sum T^2); float32: sqrt(sum T^2) (rounded up)
-    float mu;       // float32: float mean used for T
-    float emu;      // float32: Ibar - mu
-    int m;          // uint16: integer mean used for T
+// float32 block constants, derived by thread 0 and read by the CTA after
+// the template barrier.
+struct BlockConstF {
+    double dvI;      // sum (I - Ibar)^2
+    float ibh, ibl;  // the mean as a float pair (ibh + ibl)
+    float fvI;       // dvI as float
+    float kq;        // sqrt(sum T^2), rounded up
+    float emu;       // Ibar - mu (mu: the float mean used for T)
+};
+
+// uint16 block constants: every thread derives them from the warp sums;
+// thread 0 stores them for the phases after the search, so that they hold
+// no registers through it.
+struct BlockConstU {
+    long long vI;  // N*S_II - S_I^2 (exact)
+    long long rr;  // N*m - S_I
+    float frr;     // rr as float (exact: |rr| <= N/2)
+    float fvI;     // vI as float
+    float kq;      // N*gamma_L*sqrt(sum (I-m)^2), rounded up
+    int m;         // nearest integer to the block mean
 };
 
 struct MatchScratch {
-    BlockConst bc;
+    BlockConstF bc;
+    BlockConstU bu;
+    int cen[2][5];  // per window buffer: cx, cy, cz, job, index of the block in its job
+    int nb[2];      // per window buffer: the work item after that buffer's block
     float wlb[MATCH_MAX_WARPS];
     double bs[MATCH_MAX_WARPS];
     int bn2[MATCH_MAX_WARPS];
     int bcode[MATCH_MAX_WARPS];
     int bok[MATCH_MAX_WARPS];
-    int nsurv;
     int jstart[MATCH_MAX_JOBS + 1];  // first work item of each job
-    // per-warp partial statistics of the floating block
-    double pd1[MATCH_MAX_WARPS], pd2[MATCH_MAX_WARPS];
-    float plo[MATCH_MAX_WARPS], phi[MATCH_MAX_WARPS];
-    // float32: per-warp partial sums when few survivors are split across warps
-    double rf[MATCH_MAX_WARPS][3];
-    float rlo[MATCH_MAX_WARPS], rhi[MATCH_MAX_WARPS];
 };
 
 // Extra radius levels (level-aware kernel only): per-warp lower bounds and
@@ -127,20 +136,23 @@ __host__ __device__ constexpr int match_bx()
     return EPC * (c % 2 ? c : c + 1);
 }
 
-// Rows per plane of the window box.  Consecutive threads own consecutive
-// (dz, dy) lines; their rows are 1 apart except at the wrap from dy = py-1
-// to the next dz, where they are wyp - py + 1 apart.  With an odd number of
-// chunks per row, both steps map to the same bank-group step iff
-// wyp == py (mod 8).
+// Template pairs per row: the B columns padded to an even count, so a
+// 16-byte load brings two columns' (t, t) pairs.
+__host__ __device__ constexpr int match_tpr(int B) { return (B + 1) / 2 * 2; }
+
+// Rows per plane of the window box: the window's wy rows plus one (the pad
+// line of a thread with a single line reads one row further), rounded up to
+// an odd count.  Consecutive threads own lines one window plane apart; with
+// an odd number of 16-byte chunks per row and an odd number of rows per
+// plane, 8 consecutive planes start in 8 distinct bank groups.
 __host__ __device__ inline int match_wyp(int wy, int py)
 {
-    int w = wy;
-    while ((w - py) % 8 != 0) ++w;
-    return w;
+    (void)py;
+    return (wy + 1) | 1;
 }
 
 struct MatchLayout {
-    int u[2], ut[2], t, surv, sc, lsc, bar, total;
+    int u[2], ut[2], t, sc, lsc, bar, total;
 };
 
 // Shared-memory carve-up of one CTA (all offsets 128-byte aligned).  With
@@ -150,8 +162,10 @@ __host__ __device__ inline MatchLayout match_layout(int elem, int B, int P, int 
                                                    int pz, bool single_window, bool levels, int brows)
 {
     // brows: rows of the floating block (by * bz)
+    (void)P;
+    (void)py;
+    (void)pz;
     MatchLayout L;
-    const int pt = round_up_i(B, 4);
     int o = 0;
     for (int b = 0; b < 2; ++b) {
         if (single_window && b == 1) {
@@ -164,9 +178,7 @@ __host__ __device__ inline MatchLayout match_layout(int elem, int B, int P, int 
         o += round_up_i(btx * brows * elem, 128);
     }
     L.t = o;
-    o += round_up_i(brows * pt * 4, 128);
-    L.surv = o;
-    o += round_up_i(P * py * pz * 2, 128);
+    o += round_up_i(brows * ((B + 3) / 4 * 4) * 4, 128);
     L.sc = o;
     o += round_up_i((int)sizeof(MatchScratch), 128);
     L.lsc = o;
@@ -277,6 +289,25 @@ __device__ __forceinline__ float u16_minus(uint32_t u, float c_plus_2p23)
     return __fsub_rn(__uint_as_float(0x4B000000u | u), c_plus_2p23);
 }
 
+// Two floats as one 64-bit register pair (the operand form of the packed
+// f32x2 instructions), and the packed FMA itself (round to nearest, IEEE
+// subnormals kept: no .ftz).
+typedef unsigned long long f2_t;
+__device__ __forceinline__ f2_t f2_bits(uint32_t lo, uint32_t hi)
+{
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(lo), "r"(hi));
+    return r;
+}
+__device__ __forceinline__ float f2_lo(f2_t v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float f2_hi(f2_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c)
+{
+    f2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 __device__ __forceinline__ void write_out(int32_t *disp, double *ncc, uint8_t *valid, int blk, const Cand &b, int P,
                                           int py, int rx, int ry, int rz)
 {
@@ -320,85 +351,377 @@ __device__ __forceinline__ bool center_inside(int cx, int cy, int cz, int nx, in
     return cx >= hx && cy >= hy && cz >= hz && cx <= nx - 1 - hx && cy <= ny - 1 - hy && cz <= nz - 1 - hz;
 }
 
-// The search of one thread's line for a window whose row data starts XO
-// elements into each row of the box.  `row0` points at the thread's first
-// row; rows of the next template row are one box row apart, template planes
-// `zstride` elements apart.
-template <typename T, int B, int P, int XO>
-__device__ __forceinline__ void search_line(const T *row0, int zstride, const float *Tm, float csh, float (&acc)[P],
-                                            int by, int bz)
+// Bits of window element E (within the loaded 16-byte chunks) as the float
+// the search multiplies: float32 as it is, uint16 u as the subnormal u * 2^-149
+// (one byte-permute; elements past the loaded chunks are a zero pad).
+template <typename T, int NC>
+__device__ __forceinline__ uint32_t win_bits(const uint4 (&ch)[NC], int E)
 {
     constexpr bool F32 = std::is_same<T, float>::value;
+    constexpr int EPC = 16 / (int)sizeof(T);
+    if (E < 0 || E >= NC * EPC) return 0u;
+    const uint4 &q = ch[E / EPC];
+    if constexpr (F32) {
+        const int w = E % 4;
+        return w == 0 ? q.x : w == 1 ? q.y : w == 2 ? q.z : q.w;
+    } else {
+        const int w = (E % 8) / 2;
+        const uint32_t word = w == 0 ? q.x : w == 1 ? q.y : w == 2 ? q.z : q.w;
+        return (E & 1) ? __byte_perm(word, 0u, 0x4432) : __byte_perm(word, 0u, 0x4410);
+    }
+}
+
+// Line units.  Thread k of a CTA owns one or two (dz, dy) lines of the
+// search window.  Two lines one row apart along y (type A) or z (type B)
+// read the same window rows one template row apart, so each window row a
+// thread loads and converts serves both lines' products.  Type A pairs
+// (dy, dy+1) fill every plane dz (consecutive threads walk dz, so their
+// rows are one window plane apart: distinct bank groups); with an odd
+// number py of y-shifts the last line of each plane is left over, and those
+// pair along z (type B); with pz odd too one line stays single, paired with
+// a pad line one row further along y whose sums are discarded (the window
+// box holds that extra row).
+__host__ __device__ inline int match_units(int py, int pz)
+{
+    return pz * (py / 2) + ((py & 1) ? pz / 2 + (pz & 1) : 0);
+}
+struct LineUnit {
+    int dz0, dy0;  // first line (shift indices 0 .. pz-1, 0 .. py-1)
+    int along_z;   // the second line is (dz0 + 1, dy0) instead of (dz0, dy0 + 1)
+    int two;       // the second line is a real line (not the pad)
+};
+__device__ __forceinline__ bool line_unit(int k, int py, int pz, LineUnit &u)
+{
+    const int hp = py / 2, nA = pz * hp;
+    if (k < nA) {
+        u.dz0 = k % pz;
+        u.dy0 = 2 * (k / pz);
+        u.along_z = 0;
+        u.two = 1;
+        return true;
+    }
+    if (!(py & 1)) return false;
+    const int m = k - nA, nB = pz / 2;
+    if (m < nB) {
+        u.dz0 = 2 * m;
+        u.dy0 = py - 1;
+        u.along_z = 1;
+        u.two = 1;
+        return true;
+    }
+    if (m == nB && (pz & 1)) {
+        u.dz0 = pz - 1;
+        u.dy0 = py - 1;
+        u.along_z = 0;
+        u.two = 0;
+        return true;
+    }
+    return false;
+}
+
+// Shift every row of the window box left by xo elements in place, so that
+// each row's data starts at element 0 (rows 0 .. wy-1 of each of the wz
+// planes; the rows past them are never used).  A thread moves whole rows:
+// it loads a row's 16-byte chunks, shifts the words in registers by xo's
+// word part with two select stages (by one, then by two words) and the
+// uint16 half-word remainder with a funnel shift, and stores the row back.
+template <typename T, int BX>
+__device__ __forceinline__ void realign_window(T *U, int wyp, int wy, int wz, int xo, int tid, int nthr)
+{
+    constexpr bool F32 = std::is_same<T, float>::value;
+    constexpr int NCH = BX * (int)sizeof(T) / 16;  // 16-byte chunks per row
+    constexpr int RW = 4 * NCH;                    // words per row
+    const int s = F32 ? xo : xo >> 1;              // whole words to drop (0..3)
+    const uint32_t hs = F32 ? 0u : 16u * (uint32_t)(xo & 1);
+    const int nrows = wy * wz;
+    for (int row = tid; row < nrows; row += nthr) {
+        const int z = row / wy, y = row - z * wy;
+        uint4 *rp = reinterpret_cast<uint4 *>(U + (size_t)(z * wyp + y) * BX);
+        uint32_t w[RW];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            const uint4 v = rp[c];
+            w[4 * c + 0] = v.x;
+            w[4 * c + 1] = v.y;
+            w[4 * c + 2] = v.z;
+            w[4 * c + 3] = v.w;
+        }
+#pragma unroll
+        for (int k = 0; k + 1 < RW; ++k) w[k] = (s & 1) ? w[k + 1] : w[k];
+#pragma unroll
+        for (int k = 0; k + 2 < RW; ++k) w[k] = (s & 2) ? w[k + 2] : w[k];
+        if constexpr (!F32) {
+#pragma unroll
+            for (int k = 0; k + 1 < RW; ++k) w[k] = __funnelshift_r(w[k], w[k + 1], hs);
+        }
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) rp[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+    }
+}
+
+// The search of one thread's two lines.  `row0` points at the first line's
+// first window row (rows realigned: data from element 0); the template is
+// walked with its rows along the pair's direction ("inner", bI rows, window
+// rows sI elements apart, template rows tI rows apart) innermost and the
+// other direction ("outer", bO rows, sO, tO) outside.  Step i of an inner
+// pass reads one window row: the first line multiplies it with template row
+// i (i < bI), the second line, which sits one window row further on, with
+// template row i - 1 (i >= 1).  Ts holds the template, PT floats per row.
+// On return acc0[p] / acc1[p] = sum over the block of T_k * J_{k + p} for the
+// two lines (uint16: in units of 2^-85), each a chain of N FMAs, with
+// J_k = window value minus csh (uint16: csh = m * 2^-149, the floating
+// block's integer mean, so the difference is exact; float32: the float mean,
+// the difference rounded once).
+template <typename T, int B, int P>
+__device__ __forceinline__ void search_pair(const T *row0, int sI, int sO, const float *Ts, int tI, int tO, int bI, int bO,
+                                            float csh, float (&acc0)[P], float (&acc1)[P])
+{
     constexpr int WX = B + P - 1;
     constexpr int EPC = 16 / (int)sizeof(T);
-    constexpr int NC = (XO + WX - 1) / EPC + 1;  // 16-byte chunks covering [XO, XO + WX)
+    constexpr int NC = (WX - 1) / EPC + 1;  // 16-byte chunks covering [0, WX)
     constexpr int PT = (B + 3) / 4 * 4;
-    constexpr int BX = match_bx<T, B, P>();
-    unsigned long long negc2;  // (-csh, -csh) as one f32x2 operand
+    f2_t negc2;  // (-csh, -csh): the centring subtraction, two values per packed add
     asm("mov.b64 %0, {%1, %1};" : "=l"(negc2) : "f"(-csh));
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        acc0[p] = 0.f;
+        acc1[p] = 0.f;
+    }
 #pragma unroll 1
-    for (int kz = 0; kz < bz; ++kz) {
+    for (int o = 0; o < bO; ++o) {
+        const T *wp = row0 + o * sO;
+        const float *tp = Ts + o * tO * PT;
+        float tprev[B];
 #pragma unroll 1
-        for (int ky = 0; ky < by; ++ky) {
-            const T *row = row0 + kz * zstride + ky * BX;
-            const float *tr = Tm + (kz * by + ky) * PT;
+        for (int i = 0; i <= bI; ++i, wp += sI, tp += tI * PT) {
             uint4 ch[NC];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) ch[c] = *reinterpret_cast<const uint4 *>(row + c * EPC);
-            float t[PT];
+            for (int c = 0; c < NC; ++c) ch[c] = *reinterpret_cast<const uint4 *>(wp + c * EPC);
+            float tc[PT];
+            if (i < bI) {
 #pragma unroll
-            for (int q = 0; q < PT / 4; ++q) {
-                const float4 v = *reinterpret_cast<const float4 *>(tr + 4 * q);
-                t[4 * q + 0] = v.x;
-                t[4 * q + 1] = v.y;
-                t[4 * q + 2] = v.z;
-                t[4 * q + 3] = v.w;
-            }
-            // the raw bits of each value as a float: uint16 as 0x4B00|u, the
-            // float 2^23 + u (one byte-permute), float32 as it is
-            uint32_t raw[WX];
-#pragma unroll
-            for (int e = 0; e < WX; ++e) {
-                const int E = XO + e;  // element within the loaded chunks (compile-time after unrolling)
-                const uint4 &q = ch[E / EPC];
-                if constexpr (F32) {
-                    const int w = E % 4;
-                    raw[e] = w == 0 ? q.x : w == 1 ? q.y : w == 2 ? q.z : q.w;
-                } else {
-                    const int w = (E % 8) / 2;
-                    const uint32_t word = w == 0 ? q.x : w == 1 ? q.y : w == 2 ? q.z : q.w;
-                    raw[e] = (E & 1) ? __byte_perm(word, 0x4B00u, 0x5432) : __byte_perm(word, 0x4B00u, 0x5410);
+                for (int q = 0; q < PT / 4; ++q) {
+                    const float4 v = *reinterpret_cast<const float4 *>(tp + 4 * q);
+                    tc[4 * q + 0] = v.x;
+                    tc[4 * q + 1] = v.y;
+                    tc[4 * q + 2] = v.z;
+                    tc[4 * q + 3] = v.w;
                 }
             }
-            // minus the centring constant (2^23 + c for uint16, so u - c
-            // exactly), two values per packed f32x2 subtraction
+            // window values minus the centring constant, two per packed add
+            // (uint16: u * 2^-149 - m * 2^-149, exact on subnormals)
             float j[WX];
 #pragma unroll
             for (int e = 0; e + 1 < WX; e += 2) {
-                unsigned long long d;
-                asm("{\n\t.reg .b64 pa;\n\t"
-                    "mov.b64 pa, {%1, %2};\n\t"
-                    "add.rn.f32x2 %0, pa, %3;\n\t}"
+                f2_t d;
+                asm("add.rn.f32x2 %0, %1, %2;"
                     : "=l"(d)
-                    : "r"(raw[e]), "r"(raw[e + 1]), "l"(negc2));
-                j[e] = __uint_as_float((uint32_t)d);
-                j[e + 1] = __uint_as_float((uint32_t)(d >> 32));
+                    : "l"(f2_bits(win_bits<T, NC>(ch, e), win_bits<T, NC>(ch, e + 1))), "l"(negc2));
+                j[e] = f2_lo(d);
+                j[e + 1] = f2_hi(d);
             }
-            if constexpr (WX & 1) j[WX - 1] = __fsub_rn(__uint_as_float(raw[WX - 1]), csh);
+            if constexpr (WX & 1) j[WX - 1] = __fsub_rn(__uint_as_float(win_bits<T, NC>(ch, WX - 1)), csh);
+            if (i >= 1) {
 #pragma unroll
-            for (int kx = 0; kx < B; ++kx)
+                for (int kx = 0; kx < B; ++kx)
 #pragma unroll
-                for (int p = 0; p < P; ++p) acc[p] = __fmaf_rn(t[kx], j[kx + p], acc[p]);
+                    for (int p = 0; p < P; ++p) acc1[p] = __fmaf_rn(tprev[kx], j[kx + p], acc1[p]);
+            }
+            if (i < bI) {
+#pragma unroll
+                for (int kx = 0; kx < B; ++kx)
+#pragma unroll
+                    for (int p = 0; p < P; ++p) acc0[p] = __fmaf_rn(tc[kx], j[kx + p], acc0[p]);
+            }
+#pragma unroll
+            for (int kx = 0; kx < B; ++kx) tprev[kx] = tc[kx];
         }
     }
+}
+
+// Box sums S_J and S_JJ (uint16: v_J) of every x-shift of one line, and
+// the mask of the shifts whose block lies inside the volume.  The loads are
+// independent and issued together.
+template <typename T, int B, int P>
+__device__ __forceinline__ uint32_t line_boxsums(const MatchParams &a, int cx, int cy, int cz, int dyi, int dzi, int HY,
+                                                 int HZ, typename std::conditional<std::is_same<T, float>::value, float,
+                                                                                   int32_t>::type (&ps1)[P],
+                                                 float (&ps2)[P])
+{
+    typedef typename std::conditional<std::is_same<T, float>::value, float, int32_t>::type S1T;
+    constexpr int H = (B - 1) / 2;
+    constexpr int RX = (P - 1) / 2;
+    const int ny = a.ny, nz = a.nz, nx = a.nx;
+    const int Y = cy + dyi - a.ry, Z = cz + dzi - a.rz;
+    const bool yz_ok = Y >= HY && Y <= ny - 1 - HY && Z >= HZ && Z <= nz - 1 - HZ;
+    uint32_t vmask = 0;
+    const size_t rowbase = ((size_t)Z * ny + Y) * nx;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int X = cx + p - RX;
+        ps1[p] = 0;
+        ps2[p] = 0.f;
+        if (yz_ok && X >= H && X <= nx - 1 - H) {
+            vmask |= 1u << p;
+            ps1[p] = reinterpret_cast<const S1T *>(a.s1)[rowbase + X];
+            ps2[p] = reinterpret_cast<const float *>(a.s2)[rowbase + X];
+        }
+    }
+    return vmask;
+}
+
+// Approximate NCC of every x-shift of one line, with a rigorous bound on its
+// error (see the header comment); ub[p] = v + e and the best lower bound
+// v - e of the line (and of each level box holding it).
+template <typename T, int B, int P, bool LEV>
+__device__ __forceinline__ void line_bounds(const MatchJob &J, int nl, int dyi, int dzi, int ry, int rz, int N, int BY,
+                                            int BZ, const float (&acc)[P],
+                                            const typename std::conditional<std::is_same<T, float>::value, float,
+                                                                            int32_t>::type (&ps1)[P],
+                                            const float (&ps2)[P], uint32_t vmask, float kq, float fvI, float frr,
+                                            int m, float c_f, const BlockConstF &bcf, double GAMMA_L, float (&ub)[P],
+                                            float &lbm, float (&lbl)[MATCH_MAX_LEVELS])
+{
+    constexpr bool F32 = std::is_same<T, float>::value;
+    constexpr int RX = (P - 1) / 2;
+    constexpr float U32 = 5.9604644775390625e-08f;  // 2^-24, unit roundoff of binary32
+    constexpr float ASCALE = 0x1p85f;
+    const int dy = dyi - ry, dz = dzi - rz;
+    unsigned int lvl_line = 0;  // bit l: this line lies in level l
+    if constexpr (LEV) {
+#pragma unroll
+        for (int l = 0; l < MATCH_MAX_LEVELS; ++l)
+            if (l < nl && abs(dy) <= J.levels[l].r[1] && abs(dz) <= J.levels[l].r[2]) lvl_line |= 1u << l;
+    }
+    const float fN = (float)N;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        ub[p] = -INFINITY;
+        if (!((vmask >> p) & 1u)) continue;
+        float v, e;
+        if constexpr (!F32) {
+            // 32-bit integer and float arithmetic only: a 64-bit integer to
+            // float conversion issues on the FP64 pipe, which is narrow on
+            // this part.  v_J arrives rounded once (zero only for a flat
+            // block); S_J rounds at most once.
+            const float vjf = ps2[p];
+            if (!(vjf > 0.f)) continue;  // flat reference block
+            const float s1f = (float)(ps1[p] - N * m);  // S'_J = sum (J - m), exact before the rounding
+            // sum (J - m)^2 = (v_J + S'_J^2) / N, rounded up: the rounded v_J
+            // and S'_J and three operations stay below 6u
+            const float s2u = __fmul_rn(__fmul_rn(__fmaf_rn(s1f, s1f, vjf), 1.0f / fN), 1.f + 16.f * U32);
+            // rsqrt.approx and sqrt.approx (relative error below 2^-22 over
+            // the whole range) instead of the correctly rounded forms: the
+            // factor 1 + 64u on the error terms and 40u|v| for the centre
+            // value absorb their error
+            float inv, sq;
+            asm("rsqrt.approx.f32 %0, %1;" : "=f"(inv) : "f"(__fmul_rn(fvI, vjf)));
+            asm("sqrt.approx.f32 %0, %1;" : "=f"(sq) : "f"(s2u));
+            const float na = __fmul_rn(acc[p], fN * ASCALE);  // N * A
+            const float rs = __fmul_rn(frr, s1f);             // (N m - S_I) S'_J
+            v = __fmul_rn(__fadd_rn(na, rs), inv);
+            // e = (kq sq inv + 4u (|na| + |rs|) inv) (1 + 64u) + 40u |v|, each
+            // operation rounded on its own (no contraction)
+            const float t1 = __fmul_rn(__fmul_rn(kq, sq), inv);
+            const float t2 = __fmul_rn(__fmul_rn(4.f * U32, __fadd_rn(fabsf(na), fabsf(rs))), inv);
+            e = __fadd_rn(__fmul_rn(__fadd_rn(t1, t2), 1.f + 64.f * U32), __fmul_rn(40.f * U32, fabsf(v)));
+        } else {
+            const float GS = (float)((B + BY + BZ) * 5.9604644775390625e-08 /
+                                     (1.0 - (B + BY + BZ) * 5.9604644775390625e-08));  // box-sum depth
+            const float GN = (float)GAMMA_L;
+            const float s1 = ps1[p];
+            const float s2 = fmaxf(ps2[p], 0.f);
+            // every operation below is rounded on its own (no contraction)
+            float d1;  // |S1 err| bound (the factor 1.01 covers sqrt.approx)
+            asm("sqrt.approx.f32 %0, %1;" : "=f"(d1) : "f"(__fmul_rn(fN, s2)));
+            d1 = __fmul_rn(__fmul_rn(GS, d1), 1.01f);
+            const float s1sq_n = __fmul_rn(__fmul_rn(s1, s1), 1.0f / fN);
+            const float vJa = __fsub_rn(s2, s1sq_n);
+            const float dv = __fadd_rn(__fadd_rn(__fmul_rn(GS, s2),
+                                                 __fdiv_rn(__fmul_rn(__fadd_rn(__fmul_rn(2.f, fabsf(s1)), d1), d1), fN)),
+                                       __fmul_rn(4.f * U32, __fadd_rn(s2, s1sq_n)));
+            // S'_J ~ sum (J - c), and sum (J - c)^2 <= its estimate e2 plus
+            // the error of S_JJ, S_J and c terms (m2 bounds their size),
+            // rounded up
+            const float s1p = __fsub_rn(s1, __fmul_rn(fN, c_f));
+            const float m2 = __fadd_rn(__fadd_rn(s2, __fmul_rn(__fmul_rn(2.f, fabsf(c_f)), fabsf(s1))),
+                                       __fmul_rn(__fmul_rn(fN, c_f), c_f));
+            const float e2 = __fadd_rn(__fsub_rn(s2, __fmul_rn(__fmul_rn(2.f, c_f), s1)), __fmul_rn(__fmul_rn(fN, c_f), c_f));
+            const float sj2 = __fmul_rn(__fadd_rn(fmaxf(e2, 0.f), __fmul_rn(__fmul_rn(__fadd_rn(GS, 8.f * U32), m2), 1.01f)),
+                                        1.f + 4.f * U32);
+            if (!(vJa - dv > 0.f)) {  // spread of the reference block not resolved: rescore
+                ub[p] = INFINITY;
+                continue;
+            }
+            const float rho = __fdiv_rn(dv, __fsub_rn(vJa, dv));
+            if (!(rho <= 0.25f)) {
+                ub[p] = INFINITY;
+                continue;
+            }
+            float inv, sq;
+            asm("rsqrt.approx.f32 %0, %1;" : "=f"(inv) : "f"(__fmul_rn(bcf.fvI, vJa)));
+            asm("sqrt.approx.f32 %0, %1;" : "=f"(sq) : "f"(sj2));
+            const float A = acc[p];
+            const float es = __fmul_rn(bcf.emu, s1p);  // (Ibar - mu) S'_J
+            const float num = __fsub_rn(A, es);
+            v = __fmul_rn(num, inv);
+            const float enum_ = __fadd_rn(
+                __fadd_rn(__fmul_rn(__fmul_rn(__fadd_rn(GN, 3.f * U32), bcf.kq), sq),
+                          __fmul_rn(__fmul_rn(fabsf(bcf.emu),
+                                              __fadd_rn(__fadd_rn(fabsf(s1p), d1), __fmul_rn(2.f * U32, __fmul_rn(fN, fabsf(c_f))))),
+                                    1.01f)),
+                __fmul_rn(U32, __fadd_rn(fabsf(A), fabsf(es))));
+            const float r1 = __fadd_rn(__fadd_rn(1.f, __fmul_rn(0.7f, rho)), 4.f * U32);
+            const float r2 = __fadd_rn(__fmul_rn(0.7f, rho), 6.f * U32);
+            e = __fadd_rn(__fmul_rn(__fadd_rn(__fmul_rn(__fmul_rn(enum_, inv), r1), __fmul_rn(__fmul_rn(fabsf(num), inv), r2)),
+                                    1.f + 64.f * U32),
+                          __fmul_rn(43.f * U32, fabsf(v)));
+        }
+        e = __fadd_rn(__fmul_rn(2.f, e), 1e-9f);
+        ub[p] = __fadd_rn(v, e);
+        const float lo = __fsub_rn(v, e);
+        lbm = fmaxf(lbm, lo);
+        if (LEV && lvl_line) {
+#pragma unroll
+            for (int l = 0; l < MATCH_MAX_LEVELS; ++l)
+                if (((lvl_line >> l) & 1u) && abs(p - RX) <= J.levels[l].r[0]) lbl[l] = fmaxf(lbl[l], lo);
+        }
+    }
+}
+
+// x-shifts of one line that survive: they can be the best of the whole
+// window (ub >= LB) or of a level box holding them.
+template <int P, bool LEV>
+__device__ __forceinline__ uint32_t line_survivors(const MatchJob &J, int nl, int dyi, int dzi, int ry, int rz,
+                                                   const float (&ub)[P], float LB, const float (&LBl)[MATCH_MAX_LEVELS])
+{
+    constexpr int RX = (P - 1) / 2;
+    uint32_t lvl_line = 0;
+    if constexpr (LEV) {
+#pragma unroll
+        for (int l = 0; l < MATCH_MAX_LEVELS; ++l)
+            if (l < nl && abs(dyi - ry) <= J.levels[l].r[1] && abs(dzi - rz) <= J.levels[l].r[2]) lvl_line |= 1u << l;
+    }
+    uint32_t m = 0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        bool lv = false;
+        if (LEV && lvl_line) {
+#pragma unroll
+            for (int l = 0; l < MATCH_MAX_LEVELS; ++l)
+                lv |= ((lvl_line >> l) & 1u) && abs(p - RX) <= J.levels[l].r[0] && ub[p] >= LBl[l];
+        }
+        if (ub[p] > -INFINITY && (ub[p] >= LB || lv)) m |= 1u << p;
+    }
+    return m;
 }
 
 // The kernel body; the __global__ entries below differ only in their
 // register budget.  `a`, `tmapJ` and `tmapI` live in kernel-parameter space.
 // LEV: the jobs may report extra radius levels (batched search); without it
-// that code is compiled out of the search's per-shift loops.  ANI: the block
-// edges along y and z (a.by, a.bz) may differ from the x edge B; without it
-// they are B and every size below is a compile-time constant.
+// that code is compiled out.  ANI: the block edges along y and z (a.by,
+// a.bz) may differ from the x edge B; without it they are B and every size
+// below is a compile-time constant.
 template <typename T, int B, int P, bool LEV, bool ANI>
 __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorMap *tmapJ, const CUtensorMap *tmapI)
 {
@@ -408,29 +731,101 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
     const int BY = ANI ? a.by : B, BZ = ANI ? a.bz : B;
     const int HY = (BY - 1) / 2, HZ = (BZ - 1) / 2;
     const int N = ANI ? B * BY * BZ : N3;
+    const int NROW = BY * BZ;  // rows of the floating block
     constexpr int PT = (B + 3) / 4 * 4;
     constexpr int RX = (P - 1) / 2;
     constexpr int ALIGN = 16 / (int)sizeof(T);
     constexpr int BX = match_bx<T, B, P>();
     constexpr int BTX = round_up_c(B + ALIGN - 1, ALIGN);
-    constexpr float U32 = 5.9604644775390625e-08f;  // 2^-24, unit roundoff of binary32
-    const double GAMMA_N = (double)N * 5.9604644775390625e-08 / (1.0 - (double)N * 5.9604644775390625e-08);
+    // rounding depth of the search sums: one chain of N FMAs per shift
+    const double GAMMA_L = (double)N * 5.9604644775390625e-08 / (1.0 - (double)N * 5.9604644775390625e-08);
+    // uint16: the template is scaled by 2^64 and the window values enter as
+    // u * 2^-149, so a search sum is A * 2^-85
+    constexpr float TSCALE = 0x1p64f;
 
-    const int ry = a.ry, rz = a.rz, py = 2 * ry + 1, pz = 2 * rz + 1, lines = py * pz;
+    const int ry = a.ry, rz = a.rz, py = 2 * ry + 1, pz = 2 * rz + 1;
     const int wz = BZ + 2 * rz, wyp = a.wyp;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
 
     extern __shared__ __align__(128) unsigned char smem[];
     const MatchLayout L =
-        match_layout((int)sizeof(T), B, P, BX, BTX, wyp, wz, py, pz, a.single_window != 0, LEV, BY * BZ);
+        match_layout((int)sizeof(T), B, P, BX, BTX, wyp, wz, py, pz, a.single_window != 0, LEV, NROW);
     const bool single = a.single_window != 0;
-    float *Tm = reinterpret_cast<float *>(smem + L.t);
-    uint16_t *surv = reinterpret_cast<uint16_t *>(smem + L.surv);
+    float *Ts = reinterpret_cast<float *>(smem + L.t);
     MatchScratch *sc = reinterpret_cast<MatchScratch *>(smem + L.sc);
     MatchLevelScratch *ls = reinterpret_cast<MatchLevelScratch *>(smem + L.lsc);  // LEV only
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);  // [2]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nthr = blockDim.x, nwarp = nthr >> 5;
+    const uint32_t tx_bytes = (uint32_t)((BX * wyp * wz + BTX * BY * BZ) * (int)sizeof(T));
+
+    // this thread's lines
+    LineUnit un;
+    const bool has_unit = line_unit(tid, py, pz, un);
+    const int dz1 = un.dz0 + (un.along_z ? 1 : 0), dy1 = un.dy0 + (un.along_z ? 0 : 1);
+
+    // ---- thread 0's work-item bookkeeping ----------------------------------
+    auto locate = [&](int w, int &j, int &i) {
+        j = 0;
+        while (j + 1 < a.n_jobs && w >= sc->jstart[j + 1]) ++j;
+        i = w - sc->jstart[j];
+    };
+    // The candidate work item after a block is the one gridDim.x further on;
+    // its centre is loaded one block ahead (pf, pfx..) so that the load's
+    // latency is hidden behind a whole block.
+    int pf = 0, pfx = 0, pfy = 0, pfz = 0;
+    auto prefetch = [&](int w, int n) {
+        pf = w;
+        if (w < n) {
+            int j, i;
+            locate(w, j, i);
+            const int32_t *c = a.jobs[j].centers + 3 * i;
+            pfx = c[0];
+            pfy = c[1];
+            pfz = c[2];
+        }
+    };
+    // next work item at or after the prefetched candidate whose centre is
+    // inside; the skipped ones are reported invalid.  Records its centre in
+    // cen[buf] and prefetches the candidate after it.
+    auto advance = [&](int n, int buf) {
+        int w = pf;
+        int c0 = pfx, c1 = pfy, c2 = pfz;
+        while (w < n) {
+            int j, i;
+            locate(w, j, i);
+            if (center_inside(c0, c1, c2, nx, ny, nz, H, HY, HZ)) {
+                sc->cen[buf][0] = c0;
+                sc->cen[buf][1] = c1;
+                sc->cen[buf][2] = c2;
+                sc->cen[buf][3] = j;
+                sc->cen[buf][4] = i;
+                break;
+            }
+            write_invalid(a.jobs[j], i, P, py, RX, ry, rz);
+            w += gridDim.x;
+            if (w < n) {
+                int j2, i2;
+                locate(w, j2, i2);
+                const int32_t *c = a.jobs[j2].centers + 3 * i2;
+                c0 = c[0];
+                c1 = c[1];
+                c2 = c[2];
+            }
+        }
+        prefetch(w + gridDim.x, n);
+        return w < n ? w : n;
+    };
+    // both copies of the block recorded in cen[buf] into buffer buf
+    auto issue = [&](int buf) {
+        const int cx = sc->cen[buf][0], cy = sc->cen[buf][1], cz = sc->cen[buf][2];
+        const int x0 = cx - H - RX, xt = cx - H;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar + buf, tx_bytes);
+        tma_load_3d(smem + L.u[buf], tmapJ, bar + buf, x0 & ~(ALIGN - 1), cy - HY - ry, cz - HZ - rz);
+        tma_load_3d(smem + L.ut[buf], tmapI, bar + buf, xt & ~(ALIGN - 1), cy - HY, cz - HZ);
+    };
+
     if (tid == 0) {
         int w = 0;
         for (int j = 0; j < a.n_jobs; ++j) {
@@ -446,428 +841,197 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         mbar_init(bar + 0, 1);
         mbar_init(bar + 1, 1);
         fence_mbar_init();
+        prefetch(blockIdx.x, w);
+        const int first = advance(w, 0);
+        sc->nb[1] = first;  // the loop starts with buffer 0 holding `first`
+        if (first < w) issue(0);
     }
     __syncthreads();
     const int n = sc->jstart[a.n_jobs];  // work items over all jobs
-    auto locate = [&](int w, int &j, int &i) {
-        j = 0;
-        while (j + 1 < a.n_jobs && w >= sc->jstart[j + 1]) ++j;
-        i = w - sc->jstart[j];
-    };
-    auto centre = [&](int w, int &cx, int &cy, int &cz) {
-        int j, i;
-        locate(w, j, i);
-        const int32_t *c = a.jobs[j].centers + 3 * i;
-        cx = c[0];
-        cy = c[1];
-        cz = c[2];
-    };
-    // next work item of this CTA at or after w whose centre is inside;
-    // thread 0 reports the skipped ones as invalid
-    auto next_inside = [&](int w) {
-        for (; w < n; w += gridDim.x) {
-            int cx, cy, cz;
-            centre(w, cx, cy, cz);
-            if (center_inside(cx, cy, cz, nx, ny, nz, H, HY, HZ)) return w;
-            if (tid == 0) {
-                int j, i;
-                locate(w, j, i);
-                write_invalid(a.jobs[j], i, P, py, RX, ry, rz);
-            }
-        }
-        return n;
-    };
-    const uint32_t tx_bytes = (uint32_t)((BX * wyp * wz + BTX * BY * BZ) * (int)sizeof(T));
-    // thread 0: both copies of block w into buffer b
-    auto issue = [&](int w, int b) {
-        int cx, cy, cz;
-        centre(w, cx, cy, cz);
-        const int x0 = cx - H - RX, xt = cx - H;
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(bar + b, tx_bytes);
-        tma_load_3d(smem + L.u[b], tmapJ, bar + b, x0 & ~(ALIGN - 1), cy - HY - ry, cz - HZ - rz);
-        tma_load_3d(smem + L.ut[b], tmapI, bar + b, xt & ~(ALIGN - 1), cy - HY, cz - HZ);
-    };
+    int blk = sc->nb[1];
 
     uint32_t phase[2] = {0u, 0u};
     int i = 0;
-    int blk = next_inside(blockIdx.x);
-    if (blk < n && tid == 0) issue(blk, 0);
     while (blk < n) {
         const int b = i & 1;
         const T *U = reinterpret_cast<const T *>(smem + L.u[b]);
         const T *Ut = reinterpret_cast<const T *>(smem + L.ut[b]);
-        int job, bi;
-        locate(blk, job, bi);
-        const MatchJob &J = a.jobs[job];
-        const int cx = J.centers[3 * bi + 0], cy = J.centers[3 * bi + 1], cz = J.centers[3 * bi + 2];
+        const int cx = sc->cen[b][0], cy = sc->cen[b][1], cz = sc->cen[b][2];
+        const MatchJob &J = a.jobs[sc->cen[b][3]];
+        const int bi = sc->cen[b][4];
         const int x0 = cx - H - RX, xo = x0 - (x0 & ~(ALIGN - 1));
         const int xt = cx - H, xot = xt - (xt & ~(ALIGN - 1));
-        const size_t cidx = ((size_t)cz * ny + cy) * nx + cx;
-        // window centring constant from the box sum at the centre
-        float cshift;  // subtracted from the float of each window value (2^23 folded in for uint16)
-        int c_i = 0;
-        float c_f = 0.f;
-        if constexpr (F32) {
-            c_f = __fdiv_rn(reinterpret_cast<const float *>(a.s1)[cidx], (float)N);
-            cshift = c_f;
-        } else {
-            const long long s1c = reinterpret_cast<const int32_t *>(a.s1)[cidx];
-            c_i = (int)((2u * (uint32_t)s1c + (uint32_t)N) / (2u * (uint32_t)N));
-            cshift = 8388608.0f + (float)c_i;
-        }
-        if (tid == 0) sc->nsurv = 0;
 
-        // ---- wait for this block's copies; start the next block's --------
         const bool got = mbar_wait_bounded(bar + b, phase[b], WAIT_LIMIT_NS);
-        if (!__syncthreads_and(got)) {
-            if (tid == 0) {
-                atomicOr(a.err, DEV_ERR_TIMEOUT);
-                write_invalid(J, bi, P, py, RX, ry, rz);
-            }
-            mbar_wait_bounded(bar + b, phase[b], WAIT_LIMIT_NS);  // let an in-flight copy land before exiting
-            return;
-        }
         phase[b] ^= 1u;
-        const int nb = next_inside(blk + gridDim.x);
-        // buffer b^1 was released by the previous block's last barrier; a
-        // shared window buffer is refilled only once this block has read it
-        if (!single && nb < n && tid == 0) issue(nb, b ^ 1);
+        // window rows realigned to start at element 0 (read after barrier T)
+        if (xo) realign_window<T, BX>(const_cast<T *>(U), wyp, BY + 2 * ry, wz, xo, tid, nthr);
+        // thread 0: the next block (its centre goes to the other buffer's
+        // record, read by every thread after this block's last barrier)
+        if (tid == 0) sc->nb[b] = advance(n, b ^ 1);
 
-        // ---- floating block statistics.  Every warp sums a share (float32 in
-        // float-float, uint16 in exact integers) and every thread combines the
-        // per-warp partials after the barrier ----
-        {
-            constexpr int IPT = ANI ? 1 : (N3 + 63) / 64;  // values per thread at 64+ threads
-            if constexpr (F32) {
-                // sums of (I - I0) and (I - I0)^2 with I0 the block's first
-                // value (shifted data: the spread loses no digits to
-                // cancellation), in float-float; I - I0 is exact as dh + de
-                const float i0 = Ut[xot];
-                FF s1{0.f, 0.f}, s2{0.f, 0.f};
-                float lo = INFINITY, hi = -INFINITY;
-                for (int k0 = tid; k0 < N; k0 += IPT * nthr) {
-                    float vals[IPT];
-#pragma unroll
-                    for (int q = 0; q < IPT; ++q) {
-                        const int k = k0 + q * nthr;
-                        const int kzy = k / B, kx = k - kzy * B;
-                        vals[q] = k < N ? Ut[kzy * BTX + xot + kx] : 0.f;
-                    }
-#pragma unroll
-                    for (int q = 0; q < IPT; ++q)
-                        if (k0 + q * nthr < N) {
-                            float dh, de;
-                            two_sum(vals[q], -i0, dh, de);
-                            s1 = ff_add2(s1, dh, de);
-                            const float p = __fmul_rn(dh, dh);  // (dh + de)^2; de^2 is below the pair's precision
-                            s2 = ff_add2(s2, p, __fmaf_rn(2.f * dh, de, __fmaf_rn(dh, dh, -p)));
-                            lo = fminf(lo, vals[q]);
-                            hi = fmaxf(hi, vals[q]);
-                        }
-                }
-                s1 = warp_sum_ff(s1);
-                s2 = warp_sum_ff(s2);
-                lo = warp_min_f(lo);
-                hi = warp_max_f(hi);
-                if (lane == 0) {
-                    sc->pd1[warp] = ff_to_double(s1);
-                    sc->pd2[warp] = ff_to_double(s2);
-                    sc->plo[warp] = lo;
-                    sc->phi[warp] = hi;
-                }
-            } else {  // uint16: every warp sums a share (exact integer sums)
-                constexpr int KPT = ANI ? 0 : (N3 + 63) / 64;
-                long long s1 = 0;
-                unsigned long long s2 = 0;
-#pragma unroll
-                for (int q = 0; q < KPT; ++q) {
-                    const int k = tid + q * nthr;
-                    const int kzy = k / B, kx = k - kzy * B;
-                    const uint32_t v = k < N ? (uint32_t)Ut[kzy * BTX + xot + kx] : 0u;
-                    s1 += v;
-                    s2 += (unsigned long long)(v * v);
-                }
-                for (int k = tid + KPT * nthr; k < N; k += nthr) {  // fewer than 64 threads
-                    const int kzy = k / B, kx = k - kzy * B;
-                    const uint32_t v = (uint32_t)Ut[kzy * BTX + xot + kx];
-                    s1 += v;
-                    s2 += (unsigned long long)(v * v);
-                }
-                s1 = warp_sum(s1);
-                s2 = warp_sum(s2);
-                if (lane == 0) {
-                    reinterpret_cast<long long *>(sc->pd1)[warp] = s1;
-                    reinterpret_cast<long long *>(sc->pd2)[warp] = (long long)s2;
-                }
-            }
-        }
-        __syncthreads();
-        // float32: every thread needs only the template shift and the flat
-        // test, both cheap and computed identically everywhere; thread 0
-        // alone derives the FP64 block constants (FP64 issue is scarce on
-        // this part), read by all threads after the next barrier.
-        float tsh;
+        // ---- floating block statistics: every warp sums the whole block ----
+        // uint16: exact integer sums; thread 0 stores the block constants.
+        // float32: float-float sums of the values shifted by the block's
+        // first value; thread 0 derives the FP64 constants.
         bool flat;
+        int m = 0;        // uint16: nearest integer to the block mean
+        float tsh = 0.f;  // float32: the float mean mu used for T
         if constexpr (F32) {
-            float sf = 0.f, lo = INFINITY, hi = -INFINITY;
-            for (int w = 0; w < nwarp; ++w) {
-                sf += (float)sc->pd1[w];
-                lo = fminf(lo, sc->plo[w]);
-                hi = fmaxf(hi, sc->phi[w]);
+            const float i0 = Ut[xot];
+            FF s1{0.f, 0.f}, s2{0.f, 0.f};
+            float lo = INFINITY, hi = -INFINITY;
+            for (int row = lane; row < NROW; row += 32) {
+                float vals[B];
+#pragma unroll
+                for (int kx = 0; kx < B; ++kx) vals[kx] = Ut[row * BTX + xot + kx];
+#pragma unroll
+                for (int kx = 0; kx < B; ++kx) {
+                    float dh, de;
+                    two_sum(vals[kx], -i0, dh, de);
+                    s1 = ff_add2(s1, dh, de);
+                    const float p = __fmul_rn(dh, dh);  // (dh + de)^2; de^2 is below the pair's precision
+                    s2 = ff_add2(s2, p, __fmaf_rn(2.f * dh, de, __fmaf_rn(dh, dh, -p)));
+                    lo = fminf(lo, vals[kx]);
+                    hi = fmaxf(hi, vals[kx]);
+                }
             }
-            // any float near the mean serves as the shift mu (the partials
-            // are sums of I - I0)
-            tsh = __fadd_rn(Ut[xot], __fmul_rn(sf, 1.0f / (float)N));
+            s1 = warp_sum_ff(s1);
+            s2 = warp_sum_ff(s2);
+            lo = warp_min_f(lo);
+            hi = warp_max_f(hi);
+            // any float near the mean serves as the shift mu
+            tsh = __fadd_rn(i0, __fmul_rn(s1.h, 1.0f / (float)N));
             flat = !(lo < hi);
             if (tid == 0 && !flat) {
-                double s1 = 0.0, s2 = 0.0;  // sums of (I - I0) and (I - I0)^2
-                for (int w = 0; w < nwarp; ++w) {
-                    s1 += sc->pd1[w];
-                    s2 += sc->pd2[w];
-                }
-                const double i0 = (double)Ut[xot];
-                const double ibar = i0 + s1 / (double)N;
-                double dv = s2 - s1 * (s1 / (double)N);  // sum (I - Ibar)^2
+                const double d1 = ff_to_double(s1), d2 = ff_to_double(s2);  // sums of (I - I0) and (I - I0)^2
+                const double ibar = (double)i0 + d1 / (double)N;
+                double dv = d2 - d1 * (d1 / (double)N);  // sum (I - Ibar)^2
                 if (dv < 0.0) dv = 0.0;
-                sc->bc.ibh = (float)ibar;
-                sc->bc.ibl = (float)(ibar - (double)sc->bc.ibh);
+                BlockConstF &c = sc->bc;
+                c.ibh = (float)ibar;
+                c.ibl = (float)(ibar - (double)c.ibh);
                 const double em = ibar - (double)tsh;
-                BlockConst &c = sc->bc;
-                c.ibar = ibar;
-                c.mu = tsh;
                 c.emu = (float)em;
                 c.dvI = dv;
                 c.fvI = (float)dv;
                 // sum of T^2 with T = fl(I - mu): at most (1+u)^2 sum (I - mu)^2
                 // = (1+u)^2 (sum (I - Ibar)^2 + N (Ibar - mu)^2); the
                 // float-float sums (about 2^-48 relative per step, tens of
-                // steps) leave the spread inexact by well under 2048 ulp of s2
-                c.kq = (float)(sqrt((dv + 2048.0 * 1.1102230246251565e-16 * s2 + (double)N * em * em) * (1.0 + 2.4e-7)) *
+                // steps) leave the spread inexact by well under 2048 ulp of d2
+                c.kq = (float)(sqrt((dv + 2048.0 * 1.1102230246251565e-16 * d2 + (double)N * em * em) * (1.0 + 2.4e-7)) *
                                (1.0 + 1e-6));
             }
         } else {
-            // uint16: every thread adds the per-warp partials (exact) and
-            // derives the integer mean; thread 0 writes the block constants
-            long long s1 = 0, s2 = 0;
-            for (int w = 0; w < nwarp; ++w) {
-                s1 += reinterpret_cast<const long long *>(sc->pd1)[w];
-                s2 += reinterpret_cast<const long long *>(sc->pd2)[w];
+            int s1 = 0;
+            unsigned long long s2 = 0;
+            for (int row = lane; row < NROW; row += 32) {
+                uint32_t vals[B];
+#pragma unroll
+                for (int kx = 0; kx < B; ++kx) vals[kx] = Ut[row * BTX + xot + kx];
+#pragma unroll
+                for (int kx = 0; kx < B; ++kx) {
+                    s1 += (int)vals[kx];
+                    s2 += (unsigned long long)(vals[kx] * vals[kx]);  // below 2^32
+                }
             }
-            const long long vI = (long long)N * s2 - s1 * s1;
-            const long long m = (long long)((2u * (uint32_t)s1 + (uint32_t)N) / (2u * (uint32_t)N));  // nearest integer to the mean
+            s1 = warp_sum(s1);
+            s2 = warp_sum(s2);
+            const long long vI = (long long)N * (long long)s2 - (long long)s1 * s1;
+            m = (int)((2u * (uint32_t)s1 + (uint32_t)N) / (2u * (uint32_t)N));
             flat = vI == 0;
-            tsh = 8388608.0f + (float)(int)m;
-            if (tid == 0) {
-                BlockConst &c = sc->bc;
-                const long long qt = s2 - 2 * m * s1 + (long long)N * m * m;  // sum (I-m)^2, exact, below 2^48
+            if (tid == 0 && !flat) {
+                BlockConstU &c = sc->bu;
                 c.vI = vI;
-                c.m = (int)m;
+                c.m = m;
                 c.rr = (long long)N * m - s1;
                 c.frr = (float)(int)c.rr;
                 c.fvI = (float)vI;
-                // kq = N gamma_N sqrt(qt), rounded up in float (no FP64 on this
-                // path): qt < 2^48 becomes a float through two exact 24-bit
-                // halves and one rounding; the factor 1 + 4e-6 covers that
-                // rounding and the rounding of N gamma_N
+                // kq = N gamma_L sqrt(qt), qt = sum (I - m)^2 exact below
+                // 2^48, rounded up in float: qt becomes a float through two
+                // exact 24-bit halves and one rounding; the factor 1 + 4e-6
+                // covers that rounding and the rounding of N gamma_L
+                const long long qt = (long long)s2 - 2ll * m * s1 + (long long)N * m * m;
                 const float qf = __fmaf_rn((float)(int)(qt >> 24), 16777216.f, (float)(int)(qt & 0xFFFFFF));
-                c.kq = __fmul_ru(__fmul_ru((float)((double)N * GAMMA_N), __fsqrt_ru(qf)), 1.000004f);
+                c.kq = __fmul_ru(__fmul_ru((float)((double)N * GAMMA_L), __fsqrt_ru(qf)), 1.000004f);
             }
         }
+
+        // ---- template ---------------------------------------------------------
+        if (!flat) {
+            const int TB = NROW * PT;
+            for (int k = tid; k < TB; k += nthr) {
+                const int row = k / PT, kx = k - row * PT;
+                float t = 0.f;
+                if (kx < B) {
+                    if constexpr (F32)
+                        t = __fsub_rn(Ut[row * BTX + xot + kx], tsh);
+                    else
+                        t = __fmul_rn(u16_minus(Ut[row * BTX + xot + kx], 8388608.0f + (float)m), TSCALE);
+                }
+                Ts[k] = t;
+            }
+        }
+
+        // ---- barrier T: template written, copies landed (or gave up) --------
+        if (!__syncthreads_and(got)) {
+            if (tid == 0) {
+                atomicOr(a.err, DEV_ERR_TIMEOUT);
+                write_invalid(J, bi, P, py, RX, ry, rz);
+            }
+            mbar_wait_bounded(bar + b, phase[b] ^ 1u, WAIT_LIMIT_NS);  // let an in-flight copy land before exiting
+            return;
+        }
+        const int nb = sc->nb[b];
+        // buffer b^1 was last read before the previous block's last barrier
+        if (!single && nb < n && tid == 0) issue(b ^ 1);
         if (flat) {  // flat floating block: NCC undefined for every shift
-            if (single && nb < n && tid == 0) issue(nb, b ^ 1);  // the window is not read
+            if (single && nb < n && tid == 0) issue(b ^ 1);  // the window is not read
             if (tid == 0) write_invalid(J, bi, P, py, RX, ry, rz);
-            __syncthreads();
             blk = nb;
             ++i;
             continue;
         }
-        // ---- mean-shifted template (loads batched before stores) -----------
-        {
-            const int TB = BY * BZ * PT;
-            constexpr int TPT = ANI ? 0 : (B * B * PT + 63) / 64;  // items per thread at 64+ threads
-            float v[TPT > 0 ? TPT : 1];
-#pragma unroll
-            for (int j = 0; j < TPT; ++j) {
-                const int k = tid + j * nthr;
-                const int kzy = k / PT, kx = k - kzy * PT;
-                v[j] = 0.f;
-                if (k < TB && kx < B) {
-                    if constexpr (F32)
-                        v[j] = __fsub_rn(Ut[kzy * BTX + xot + kx], tsh);
-                    else
-                        v[j] = u16_minus(Ut[kzy * BTX + xot + kx], tsh);
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < TPT; ++j) {
-                const int k = tid + j * nthr;
-                if (k < TB) Tm[k] = v[j];
-            }
-            for (int k = tid + TPT * nthr; k < TB; k += nthr) {  // fewer than 64 threads
-                const int kzy = k / PT, kx = k - kzy * PT;
-                float w = 0.f;
-                if (kx < B) {
-                    if constexpr (F32)
-                        w = __fsub_rn(Ut[kzy * BTX + xot + kx], tsh);
-                    else
-                        w = u16_minus(Ut[kzy * BTX + xot + kx], tsh);
-                }
-                Tm[k] = w;
-            }
-        }
-        __syncthreads();
-        const BlockConst bc = sc->bc;
+        BlockConstF bcf;
+        if constexpr (F32) bcf = sc->bc;
 
-        // ---- search: FP32 accumulation of A(d) over the whole window ------
-        float ub[P];
+        // ---- search: FP32 accumulation of A(d) over the window, two lines ----
+        float ub0[P], ub1[P];
         float lbm = -INFINITY;
-        const int dyi = tid % py, dzi = tid / py;
         const int nl = LEV ? J.n_levels : 0;  // extra radius levels of this block's job
         float lbl[MATCH_MAX_LEVELS];
-        unsigned int lvl_line = 0;  // bit l: this thread's (dz, dy) line lies in level l
-        if constexpr (LEV) {
 #pragma unroll
-            for (int l = 0; l < MATCH_MAX_LEVELS; ++l) {
-                lbl[l] = -INFINITY;
-                if (l < nl && tid < lines && abs(dyi - ry) <= J.levels[l].r[1] && abs(dzi - rz) <= J.levels[l].r[2])
-                    lvl_line |= 1u << l;
-            }
+        for (int l = 0; l < MATCH_MAX_LEVELS; ++l) lbl[l] = -INFINITY;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            ub0[p] = -INFINITY;
+            ub1[p] = -INFINITY;
         }
-        if (tid < lines) {
-            const int dy = dyi - ry, dz = dzi - rz, Y = cy + dy, Z = cz + dz;
-            const bool yz_ok = Y >= HY && Y <= ny - 1 - HY && Z >= HZ && Z <= nz - 1 - HZ;
+        if (has_unit) {
+            float acc0[P], acc1[P];
+            const T *row0 = U + (un.dz0 * wyp + un.dy0) * BX;
+            const int sI = un.along_z ? wyp * BX : BX, sO = un.along_z ? BX : wyp * BX;
+            const int tI = un.along_z ? BY : 1, tO = un.along_z ? 1 : BY;
+            const int bI = un.along_z ? BZ : BY, bO = un.along_z ? BY : BZ;
+            // centring constant: the floating block's mean (uint16: the
+            // subnormal m * 2^-149, whose bits are m)
+            const float csh = F32 ? tsh : __uint_as_float((uint32_t)m);
+            search_pair<T, B, P>(row0, sI, sO, Ts, tI, tO, bI, bO, csh, acc0, acc1);
+            // both lines' box sums first (one L2 round trip), then the bounds
             typedef typename std::conditional<F32, float, int32_t>::type S1T;
-            typedef float S2T;  // uint16: v_J = N S_JJ - S_J^2 rounded to float; float32: S_JJ
-            float acc[P];
-#pragma unroll
-            for (int p = 0; p < P; ++p) acc[p] = 0.f;
-            const T *row0 = U + (dzi * wyp + dyi) * BX;
-            const int zs = wyp * BX;
-            switch (xo) {
-#define NRR_XO(k) \
-    case k:       \
-        if constexpr (k < ALIGN) search_line<T, B, P, k>(row0, zs, Tm, cshift, acc, BY, BZ); \
-        break;
-                NRR_XO(0)
-                NRR_XO(1)
-                NRR_XO(2)
-                NRR_XO(3)
-                NRR_XO(4)
-                NRR_XO(5)
-                NRR_XO(6)
-                NRR_XO(7)
-#undef NRR_XO
-            }
-
-            // box sums of this thread's shifts (independent loads, issued together)
-            S1T ps1[P];
-            S2T ps2[P];
-            uint32_t vmask = 0;
-            const size_t rowbase = ((size_t)Z * ny + Y) * nx;
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                const int X = cx + p - RX;
-                ps1[p] = 0;
-                ps2[p] = 0;
-                if (yz_ok && X >= H && X <= nx - 1 - H) {
-                    vmask |= 1u << p;
-                    ps1[p] = reinterpret_cast<const S1T *>(a.s1)[rowbase + X];
-                    ps2[p] = reinterpret_cast<const S2T *>(a.s2)[rowbase + X];
-                }
-            }
-            // ---- approximate NCC and its error bound per shift -----------
-            const float fN = (float)N;
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                ub[p] = -INFINITY;
-                if (!((vmask >> p) & 1u)) continue;
-                if constexpr (!F32) {
-                    // 32-bit integer and float arithmetic only: a 64-bit
-                    // integer to float conversion issues on the FP64 pipe,
-                    // which is narrow on this part.  v_J arrives rounded once
-                    // (zero only for a flat block); S'_J = S_J - N c is exact.
-                    const float vjf = ps2[p];
-                    if (!(vjf > 0.f)) continue;  // flat reference block
-                    const int s1p = ps1[p] - N * c_i;
-                    const float s1pf = (float)s1p;
-                    // sum (J - c)^2 = (v_J + S'_J^2) / N, rounded up: the
-                    // rounded v_J and S'_J and three operations stay below 6u
-                    const float s2p = __fmul_rn(__fmul_rn(__fmaf_rn(s1pf, s1pf, vjf), 1.0f / fN), 1.f + 16.f * U32);
-                    // rsqrt.approx and sqrt.approx (relative error below 2^-22
-                    // over the whole range) instead of the correctly rounded
-                    // forms: the factor 1 + 64u on the error terms and 40u|v|
-                    // for the centre value absorb their error
-                    float inv;
-                    asm("rsqrt.approx.f32 %0, %1;" : "=f"(inv) : "f"(__fmul_rn(bc.fvI, vjf)));
-                    const float na = __fmul_rn(fN, acc[p]);
-                    const float rs = __fmul_rn(bc.frr, s1pf);  // rr exact in float (|rr| <= N/2)
-                    const float v = __fmul_rn(__fadd_rn(na, rs), inv);
-                    float sq;
-                    asm("sqrt.approx.f32 %0, %1;" : "=f"(sq) : "f"(s2p));
-                    float e = (bc.kq * sq * inv + 4.f * U32 * (fabsf(na) + fabsf(rs)) * inv) * (1.f + 64.f * U32) +
-                              40.f * U32 * fabsf(v);
-                    e = 2.f * e + 1e-9f;
-                    ub[p] = v + e;
-                    lbm = fmaxf(lbm, v - e);
-                    if (LEV && lvl_line) {
-#pragma unroll
-                        for (int l = 0; l < MATCH_MAX_LEVELS; ++l)
-                            if (((lvl_line >> l) & 1u) && abs(p - RX) <= J.levels[l].r[0]) lbl[l] = fmaxf(lbl[l], v - e);
-                    }
-                } else {
-                    const float GS = (float)((B + BY + BZ) * 5.9604644775390625e-08 /
-                                             (1.0 - (B + BY + BZ) * 5.9604644775390625e-08));  // box-sum depth
-                    const float GN = (float)GAMMA_N;
-                    const float s1 = ps1[p];
-                    const float s2 = fmaxf(ps2[p], 0.f);
-                    float d1;  // |S1 err| bound (the factor 1.01 covers sqrt.approx)
-                    asm("sqrt.approx.f32 %0, %1;" : "=f"(d1) : "f"(fN * s2));
-                    d1 = GS * d1 * 1.01f;
-                    const float s1sq_n = __fmul_rn(__fmul_rn(s1, s1), 1.0f / fN);
-                    const float vJa = __fsub_rn(s2, s1sq_n);
-                    const float dv = GS * s2 + (2.f * fabsf(s1) + d1) * d1 / fN + 4.f * U32 * (s2 + s1sq_n);
-                    const float s1p = __fsub_rn(s1, __fmul_rn(fN, c_f));  // ~ sum (J - c)
-                    const float m2 = s2 + 2.f * fabsf(c_f) * fabsf(s1) + fN * c_f * c_f;
-                    const float e2 = __fadd_rn(__fsub_rn(s2, 2.f * c_f * s1), fN * c_f * c_f);
-                    const float sj2 = (fmaxf(e2, 0.f) + (GS + 8.f * U32) * m2 * 1.01f) * (1.f + 4.f * U32);
-                    if (!(vJa - dv > 0.f)) {  // spread of the reference block not resolved: rescore
-                        ub[p] = INFINITY;
-                        continue;
-                    }
-                    const float rho = dv / (vJa - dv);
-                    if (!(rho <= 0.25f)) {
-                        ub[p] = INFINITY;
-                        continue;
-                    }
-                    // approximate rsqrt / sqrt as for uint16: 1 + 64u on the
-                    // error terms and 40u|v| absorb their error
-                    float inv, sq;
-                    asm("rsqrt.approx.f32 %0, %1;" : "=f"(inv) : "f"(__fmul_rn(bc.fvI, vJa)));
-                    asm("sqrt.approx.f32 %0, %1;" : "=f"(sq) : "f"(sj2));
-                    const float A = acc[p];
-                    const float es = __fmul_rn(bc.emu, s1p);
-                    const float num = __fsub_rn(A, es);
-                    const float v = __fmul_rn(num, inv);
-                    const float enum_ = (GN + 3.f * U32) * bc.kq * sq +
-                                        fabsf(bc.emu) * (fabsf(s1p) + d1 + 2.f * U32 * fN * fabsf(c_f)) * 1.01f +
-                                        U32 * (fabsf(A) + fabsf(es));
-                    float e = (enum_ * inv * (1.f + 0.7f * rho + 4.f * U32) + fabsf(num) * inv * (0.7f * rho + 6.f * U32)) *
-                                  (1.f + 64.f * U32) +
-                              43.f * U32 * fabsf(v);
-                    e = 2.f * e + 1e-9f;
-                    ub[p] = v + e;
-                    lbm = fmaxf(lbm, v - e);
-                    if (LEV && lvl_line) {
-#pragma unroll
-                        for (int l = 0; l < MATCH_MAX_LEVELS; ++l)
-                            if (((lvl_line >> l) & 1u) && abs(p - RX) <= J.levels[l].r[0]) lbl[l] = fmaxf(lbl[l], v - e);
-                    }
-                }
-            }
+            S1T q1a[P], q1b[P];
+            float q2a[P], q2b[P];
+            const uint32_t va = line_boxsums<T, B, P>(a, cx, cy, cz, un.dy0, un.dz0, HY, HZ, q1a, q2a);
+            const uint32_t vb = un.two ? line_boxsums<T, B, P>(a, cx, cy, cz, dy1, dz1, HY, HZ, q1b, q2b) : 0u;
+            const float kq = F32 ? 0.f : sc->bu.kq, fvI = F32 ? 0.f : sc->bu.fvI, frr = F32 ? 0.f : sc->bu.frr;
+            line_bounds<T, B, P, LEV>(J, nl, un.dy0, un.dz0, ry, rz, N, BY, BZ, acc0, q1a, q2a, va, kq, fvI, frr, m, tsh,
+                                      bcf, GAMMA_L, ub0, lbm, lbl);
+            if (un.two)
+                line_bounds<T, B, P, LEV>(J, nl, dy1, dz1, ry, rz, N, BY, BZ, acc1, q1b, q2b, vb, kq, fvI, frr, m, tsh,
+                                          bcf, GAMMA_L, ub1, lbm, lbl);
         }
 
-        // ---- best lower bound over the window; survivors ------------------
+        // ---- best lower bound over the window ------------------------------
         lbm = warp_max_f(lbm);
         if (lane == 0) sc->wlb[warp] = lbm;
         if (LEV && nl) {
@@ -880,157 +1044,141 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                 }
             }
         }
+        // ---- barrier A: every warp's lower bounds ---------------------------
         __syncthreads();
         // float32 reads the window only in the search (its rescoring reads
         // global memory): a shared window buffer is refilled from here
         if constexpr (F32)
-            if (single && nb < n && tid == 0) issue(nb, b ^ 1);
+            if (single && nb < n && tid == 0) issue(b ^ 1);
         float LB = -INFINITY;
         for (int w = 0; w < nwarp; ++w) LB = fmaxf(LB, sc->wlb[w]);
-        // a shift survives if it can be the best of the whole window or of
-        // a level box holding it
         float LBl[MATCH_MAX_LEVELS];
-        if constexpr (LEV) {
 #pragma unroll
-            for (int l = 0; l < MATCH_MAX_LEVELS; ++l) {
-                LBl[l] = INFINITY;
-                if (l < nl) {
-                    LBl[l] = -INFINITY;
-                    for (int w = 0; w < nwarp; ++w) LBl[l] = fmaxf(LBl[l], ls->wlbl[l][w]);
-                }
+        for (int l = 0; l < MATCH_MAX_LEVELS; ++l) {
+            LBl[l] = INFINITY;
+            if (LEV && l < nl) {
+                LBl[l] = -INFINITY;
+                for (int w = 0; w < nwarp; ++w) LBl[l] = fmaxf(LBl[l], ls->wlbl[l][w]);
             }
         }
-        if (tid < lines) {
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                bool lv = false;
-                if (LEV && lvl_line) {
-#pragma unroll
-                    for (int l = 0; l < MATCH_MAX_LEVELS; ++l)
-                        lv |= ((lvl_line >> l) & 1u) && abs(p - RX) <= J.levels[l].r[0] && ub[p] >= LBl[l];
-                }
-                if (ub[p] > -INFINITY && (ub[p] >= LB || lv)) {
-                    int s = atomicAdd(&sc->nsurv, 1);
-                    surv[s] = (uint16_t)((dzi * py + dyi) * P + p);
-                }
-            }
+        // surviving x-shifts of this thread's lines: bits 0..P-1 line 0,
+        // bits 16.. line 1
+        uint32_t smask = 0;
+        if (has_unit) {
+            smask = line_survivors<P, LEV>(J, nl, un.dy0, un.dz0, ry, rz, ub0, LB, LBl);
+            if (un.two) smask |= line_survivors<P, LEV>(J, nl, dy1, dz1, ry, rz, ub1, LB, LBl) << 16;
         }
-        __syncthreads();
-        const int nsurv = sc->nsurv;
 
-        // ---- exact rescoring of the survivors ---------------------------------
-        // A warp rescores a whole survivor.  float32 (FP64 sums, slow on this
-        // part): with fewer survivors than warps, each survivor's terms are
-        // split over nwarp/nsurv warps whose partial sums thread 0 adds up.
-        const int parts = (!F32 || nsurv >= nwarp) ? 1 : (nsurv > 0 ? nwarp / nsurv : 1);
-        const int KS1 = N;  // terms of a whole survivor
+        // ---- exact rescoring of this warp's survivors -------------------------
         Cand wb{0.0, 0, 0, 0};
-        const int ntask = parts == 1 ? nsurv : nsurv * parts;
-        for (int task = warp; task < ntask; task += nwarp) {
-            const int sidx = task / parts, part = task - sidx * parts;
-            const int ks = (KS1 + parts - 1) / parts;
-            const int kbeg = part * ks, kend = kbeg + ks < N ? kbeg + ks : N;
-            const int code = surv[sidx];
-            const int sxi = code % P, syi = (code / P) % py, szi = code / (P * py);
-            const int dx = sxi - RX, dy = syi - ry, dz = szi - rz;
-            const size_t idx = ((size_t)(cz + dz) * ny + (cy + dy)) * nx + (cx + dx);
-            Cand c{0.0, dx * dx + dy * dy + dz * dz, code, 0};
-            if constexpr (!F32) {  // one warp per survivor: parts == 1
-                long long s1 = 0;
-                if (lane == 0) s1 = reinterpret_cast<const int32_t *>(a.s1)[idx];  // issued first, used after the warp sums
-                const int KPL = (N + 31) / 32;
-                constexpr int CH = ANI ? 6 : ((N3 + 31) / 32 < 6 ? (N3 + 31) / 32 : 6);
-                long long e = 0, q2 = 0;  // sum T (J - c), sum (J - c)^2: exact
+        uint32_t act = __ballot_sync(0xffffffffu, smask != 0);
+        while (act) {
+            const int src = __ffs(act) - 1;
+            act &= act - 1;
+            uint32_t mb = __shfl_sync(0xffffffffu, smask, src);
+            LineUnit su;
+            line_unit(warp * 32 + src, py, pz, su);
+            while (mb) {
+                const int bit = __ffs(mb) - 1;
+                mb &= mb - 1;
+                const int second = bit >> 4, sxi = bit & 15;
+                const int syi = su.dy0 + (second && !su.along_z ? 1 : 0);
+                const int szi = su.dz0 + (second && su.along_z ? 1 : 0);
+                const int code = (szi * py + syi) * P + sxi;
+                const int dx = sxi - RX, dy = syi - ry, dz = szi - rz;
+                Cand c{0.0, dx * dx + dy * dy + dz * dz, code, 0};
+                if constexpr (!F32) {
+                    const int mm = sc->bu.m;
+                    // sums of T J, J^2 and J over the block, exact
+                    const int KPL = (N + 31) / 32;
+                    constexpr int CH = ANI ? 6 : ((N3 + 31) / 32 < 6 ? (N3 + 31) / 32 : 6);
+                    long long e = 0;
+                    unsigned long long q2 = 0;
+                    int s1 = 0;
 #pragma unroll 1
-                for (int i0 = 0; i0 < KPL; i0 += CH) {
-                    int tv[CH], jv[CH];
+                    for (int i0 = 0; i0 < KPL; i0 += CH) {
+                        int tv[CH];
+                        uint32_t jv[CH];
 #pragma unroll
-                    for (int q = 0; q < CH; ++q) {
-                        const int k = lane + 32 * (i0 + q);
-                        const int kz = k / (B * BY), rem = k - kz * B * BY, ky = rem / B, kx = rem - ky * B;
-                        tv[q] = 0;
-                        jv[q] = 0;
-                        if (k < N) {
-                            tv[q] = (int)Tm[(kz * BY + ky) * PT + kx];
-                            jv[q] = (int)U[((szi + kz) * wyp + (syi + ky)) * BX + xo + sxi + kx] - c_i;
-                        }
-                    }
-#pragma unroll
-                    for (int q = 0; q < CH; ++q) {
-                        e += (long long)tv[q] * jv[q];
-                        q2 += (long long)jv[q] * jv[q];
-                    }
-                }
-                e = warp_sum(e);
-                q2 = warp_sum(q2);
-                if (lane == 0) {
-                    const long long s1p = s1 - (long long)N * c_i;  // sum (J - c)
-                    const long long vJ = (long long)N * q2 - s1p * s1p;  // = N S_JJ - S_J^2, exact
-                    const long long num = (long long)N * e + bc.rr * s1p;
-                    if (vJ > 0) {
-                        const double den = __dsqrt_rn(__dmul_rn((double)bc.vI, (double)vJ));
-                        c.s = __ddiv_rn((double)num, den);
-                        c.ok = 1;
-                    }
-                }
-            } else {
-                const float *pre = reinterpret_cast<const float *>(a.preop);
-                const float *intra = reinterpret_cast<const float *>(a.intraop);
-                // float-float sums of (I - Ibar) J, J and J^2 (FP32 pipe)
-                FF fij{0.f, 0.f}, fj{0.f, 0.f}, fjj{0.f, 0.f};
-                float lo = INFINITY, hi = -INFINITY;
-                for (int k = kbeg + lane; k < kend; k += 32) {
-                    const int kz = k / (B * BY), rem = k - kz * B * BY, ky = rem / B, kx = rem - ky * B;
-                    const float iv = pre[((size_t)(cz - HZ + kz) * ny + (cy - HY + ky)) * nx + (cx - H + kx)];
-                    const float jf =
-                        intra[((size_t)(cz + dz - HZ + kz) * ny + (cy + dy - HY + ky)) * nx + (cx + dx - H + kx)];
-                    float dh, de;
-                    two_sum(iv, -bc.ibh, dh, de);  // I - Ibar = dh + dl, nearly exact
-                    const float dl = __fsub_rn(de, bc.ibl);
-                    const float p = __fmul_rn(dh, jf);
-                    fij = ff_add2(fij, p, __fmaf_rn(dl, jf, __fmaf_rn(dh, jf, -p)));
-                    fj = ff_add(fj, jf);
-                    fjj = ff_add_prod(fjj, jf, jf);
-                    lo = fminf(lo, jf);
-                    hi = fmaxf(hi, jf);
-                }
-                fij = warp_sum_ff(fij);
-                fj = warp_sum_ff(fj);
-                fjj = warp_sum_ff(fjj);
-                const double sij = ff_to_double(fij), sj = ff_to_double(fj), sjj = ff_to_double(fjj);
-                lo = warp_min_f(lo);
-                hi = warp_max_f(hi);
-                if (lane == 0) {
-                    if (parts == 1) {
-                        if (lo < hi) {
-                            const double vJ = sjj - sj * sj / (double)N;
-                            if (vJ > 0.0) {
-                                c.s = sij / sqrt(bc.dvI * vJ);
-                                c.ok = 1;
+                        for (int q = 0; q < CH; ++q) {
+                            const int k = lane + 32 * (i0 + q);
+                            const int kz = k / (B * BY), rem = k - kz * B * BY, ky = rem / B, kx = rem - ky * B;
+                            tv[q] = 0;
+                            jv[q] = 0;
+                            if (k < N) {
+                                tv[q] = (int)Ut[(kz * BY + ky) * BTX + xot + kx] - mm;
+                                jv[q] = U[((szi + kz) * wyp + (syi + ky)) * BX + sxi + kx];
                             }
                         }
-                    } else {
-                        sc->rf[task][0] = sij;
-                        sc->rf[task][1] = sj;
-                        sc->rf[task][2] = sjj;
-                        sc->rlo[task] = lo;
-                        sc->rhi[task] = hi;
-                    }
-                }
-            }
-            if (lane == 0 && parts == 1) {
-                if (cand_better(c, wb)) wb = c;
-                if constexpr (LEV)
-                    for (int l = 0; l < nl; ++l)
-                    if (in_level(code, J.levels[l].r, P, py, RX, ry, rz)) {
-                        const Cand cur{ls->lbs[l][warp], ls->lbn2[l][warp], ls->lbcode[l][warp], ls->lbok[l][warp]};
-                        if (cand_better(c, cur)) {
-                            ls->lbs[l][warp] = c.s;
-                            ls->lbn2[l][warp] = c.n2;
-                            ls->lbcode[l][warp] = c.code;
-                            ls->lbok[l][warp] = c.ok;
+#pragma unroll
+                        for (int q = 0; q < CH; ++q) {
+                            e += (long long)tv[q] * (int)jv[q];
+                            q2 += (unsigned long long)(jv[q] * jv[q]);
+                            s1 += (int)jv[q];
                         }
                     }
+                    e = warp_sum(e);
+                    q2 = warp_sum(q2);
+                    s1 = warp_sum(s1);
+                    if (lane == 0) {
+                        const long long vJ = (long long)N * (long long)q2 - (long long)s1 * s1;  // N S_JJ - S_J^2
+                        const long long num = (long long)N * e + sc->bu.rr * s1;  // N S_IJ - S_I S_J
+                        if (vJ > 0) {
+                            const double den = __dsqrt_rn(__dmul_rn((double)sc->bu.vI, (double)vJ));
+                            c.s = __ddiv_rn((double)num, den);
+                            c.ok = 1;
+                        }
+                    }
+                } else {
+                    const float *pre = reinterpret_cast<const float *>(a.preop);
+                    const float *intra = reinterpret_cast<const float *>(a.intraop);
+                    // float-float sums of (I - Ibar) J, J and J^2 (FP32 pipe)
+                    FF fij{0.f, 0.f}, fj{0.f, 0.f}, fjj{0.f, 0.f};
+                    float lo = INFINITY, hi = -INFINITY;
+                    for (int k = lane; k < N; k += 32) {
+                        const int kz = k / (B * BY), rem = k - kz * B * BY, ky = rem / B, kx = rem - ky * B;
+                        const float iv = pre[((size_t)(cz - HZ + kz) * ny + (cy - HY + ky)) * nx + (cx - H + kx)];
+                        const float jf =
+                            intra[((size_t)(cz + dz - HZ + kz) * ny + (cy + dy - HY + ky)) * nx + (cx + dx - H + kx)];
+                        float dh, de;
+                        two_sum(iv, -bcf.ibh, dh, de);  // I - Ibar = dh + dl, nearly exact
+                        const float dl = __fsub_rn(de, bcf.ibl);
+                        const float p = __fmul_rn(dh, jf);
+                        fij = ff_add2(fij, p, __fmaf_rn(dl, jf, __fmaf_rn(dh, jf, -p)));
+                        fj = ff_add(fj, jf);
+                        fjj = ff_add_prod(fjj, jf, jf);
+                        lo = fminf(lo, jf);
+                        hi = fmaxf(hi, jf);
+                    }
+                    fij = warp_sum_ff(fij);
+                    fj = warp_sum_ff(fj);
+                    fjj = warp_sum_ff(fjj);
+                    lo = warp_min_f(lo);
+                    hi = warp_max_f(hi);
+                    if (lane == 0 && lo < hi) {
+                        const double sij = ff_to_double(fij), sj = ff_to_double(fj), sjj = ff_to_double(fjj);
+                        const double vJ = sjj - sj * sj / (double)N;
+                        if (vJ > 0.0) {
+                            c.s = sij / sqrt(bcf.dvI * vJ);
+                            c.ok = 1;
+                        }
+                    }
+                }
+                if (lane == 0) {
+                    if (cand_better(c, wb)) wb = c;
+                    if constexpr (LEV)
+                        for (int l = 0; l < nl; ++l)
+                            if (in_level(code, J.levels[l].r, P, py, RX, ry, rz)) {
+                                const Cand cur{ls->lbs[l][warp], ls->lbn2[l][warp], ls->lbcode[l][warp],
+                                               ls->lbok[l][warp]};
+                                if (cand_better(c, cur)) {
+                                    ls->lbs[l][warp] = c.s;
+                                    ls->lbn2[l][warp] = c.n2;
+                                    ls->lbcode[l][warp] = c.code;
+                                    ls->lbok[l][warp] = c.ok;
+                                }
+                            }
+                }
             }
         }
         if (lane == 0) {
@@ -1039,57 +1187,27 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
             sc->bcode[warp] = wb.code;
             sc->bok[warp] = wb.ok;
         }
+        // ---- barrier C: every warp's best survivor -----------------------------
         __syncthreads();
         if constexpr (!F32)  // uint16 rescoring read the window up to here
-            if (single && nb < n && tid == 0) issue(nb, b ^ 1);
+            if (single && nb < n && tid == 0) issue(b ^ 1);
         if (tid == 0) {
             Cand best{0.0, 0, 0, 0};
-            Cand bestl[MATCH_MAX_LEVELS];
             for (int w = 0; w < nwarp; ++w) {
                 Cand c{sc->bs[w], sc->bn2[w], sc->bcode[w], sc->bok[w]};
                 if (cand_better(c, best)) best = c;
             }
-            for (int l = 0; l < nl; ++l) {
-                bestl[l] = Cand{0.0, 0, 0, 0};
-                for (int w = 0; w < nwarp; ++w) {
-                    Cand c{ls->lbs[l][w], ls->lbn2[l][w], ls->lbcode[l][w], ls->lbok[l][w]};
-                    if (cand_better(c, bestl[l])) bestl[l] = c;
-                }
-            }
-            if (parts > 1) {
-                for (int si = 0; si < nsurv; ++si) {
-                    const int code = surv[si];
-                    const int sxi = code % P, syi = (code / P) % py, szi = code / (P * py);
-                    const int dx = sxi - RX, dy = syi - ry, dz = szi - rz;
-                    Cand c{0.0, dx * dx + dy * dy + dz * dz, code, 0};
-                    if constexpr (F32) {
-                        double sij = 0.0, sj = 0.0, sjj = 0.0;
-                        float lo = INFINITY, hi = -INFINITY;
-                        for (int q = 0; q < parts; ++q) {
-                            sij += sc->rf[si * parts + q][0];
-                            sj += sc->rf[si * parts + q][1];
-                            sjj += sc->rf[si * parts + q][2];
-                            lo = fminf(lo, sc->rlo[si * parts + q]);
-                            hi = fmaxf(hi, sc->rhi[si * parts + q]);
-                        }
-                        if (lo < hi) {
-                            const double vJ = sjj - sj * sj / (double)N;
-                            if (vJ > 0.0) {
-                                c.s = sij / sqrt(bc.dvI * vJ);
-                                c.ok = 1;
-                            }
-                        }
-                    }
-                    if (cand_better(c, best)) best = c;
-                    for (int l = 0; l < nl; ++l)
-                        if (in_level(code, J.levels[l].r, P, py, RX, ry, rz) && cand_better(c, bestl[l])) bestl[l] = c;
-                }
-            }
             write_result(J, bi, best, P, py, RX, ry, rz);
-            for (int l = 0; l < nl; ++l)
-                write_out(J.levels[l].disp, J.levels[l].ncc, J.levels[l].valid, bi, bestl[l], P, py, RX, ry, rz);
+            if constexpr (LEV)
+                for (int l = 0; l < nl; ++l) {
+                    Cand bl{0.0, 0, 0, 0};
+                    for (int w = 0; w < nwarp; ++w) {
+                        Cand c{ls->lbs[l][w], ls->lbn2[l][w], ls->lbcode[l][w], ls->lbok[l][w]};
+                        if (cand_better(c, bl)) bl = c;
+                    }
+                    write_out(J.levels[l].disp, J.levels[l].ncc, J.levels[l].valid, bi, bl, P, py, RX, ry, rz);
+                }
         }
-        __syncthreads();  // releases buffer b for the copies of the block after next
         blk = nb;
         ++i;
     }
@@ -1098,18 +1216,13 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
 }
 
 // Host side: launch one (element type, block size, x-shift count) variant.
-// Register budgets.  uint16: 96 per thread for blocks up to 7^3 with up to
-// 11 x-shifts (5 CTAs per SM are limited by shared memory there anyway), 128
-// above.  float32: the same limits expressed as resident CTAs per SM.
+// Register budget: 128 per thread.  A CTA holds one or two warps per
+// (2 * radius + 1) x-shift lines of 11 or fewer, so registers allow eight
+// or more CTAs per SM; shared memory limits them first.
 template <int B, int P>
 struct MatchRegs {
-    static constexpr int value = (P <= 11 && B <= 7) ? 96 : 128;
+    static constexpr int value = 128;
 };
-template <int B, int P>
-struct MatchMinBlocks {
-    static constexpr int value = (P <= 11 && B <= 7) ? 3 : 2;
-};
-
 template <int B, int P, bool LEV, bool ANI>
 __global__ void __maxnreg__((MatchRegs<B, P>::value))
     match_kernel_u16(const __grid_constant__ MatchParams a, const __grid_constant__ CUtensorMap tmapJ,
@@ -1119,7 +1232,7 @@ __global__ void __maxnreg__((MatchRegs<B, P>::value))
 }
 
 template <int B, int P, bool ANI>
-__global__ void __launch_bounds__(MATCH_MAX_THREADS, MatchMinBlocks<B, P>::value)
+__global__ void __maxnreg__((MatchRegs<B, P>::value))
     match_kernel_f32(const __grid_constant__ MatchParams a, const __grid_constant__ CUtensorMap tmapJ,
                      const __grid_constant__ CUtensorMap tmapI)
 {
@@ -1150,7 +1263,7 @@ nrr_status choose_layout(const MatchLaunch &m, MatchLayout *L, bool *single, int
     constexpr int ALIGN = 16 / (int)sizeof(T);
     const int by = launch_by(m), bz = launch_bz(m);
     const int ry = m.radius[1], rz = m.radius[2], py = 2 * ry + 1, pz = 2 * rz + 1;
-    const int wyp = match_wyp(by + 2 * ry, py), threads = round_up_i(py * pz, 32);
+    const int wyp = match_wyp(by + 2 * ry, py), threads = round_up_i(match_units(py, pz), 32);
     const MatchLayout L2 = match_layout((int)sizeof(T), B, P, match_bx<T, B, P>(), round_up_c(B + ALIGN - 1, ALIGN),
                                         wyp, bz + 2 * rz, py, pz, false, LEV, by * bz);
     const MatchLayout L1 = match_layout((int)sizeof(T), B, P, match_bx<T, B, P>(), round_up_c(B + ALIGN - 1, ALIGN),
@@ -1183,7 +1296,7 @@ nrr_status launch_match_variant_l(const MatchLaunch &m, cudaStream_t stream)
     const int by = launch_by(m), bz = launch_bz(m);
     const int ry = m.radius[1], rz = m.radius[2], py = 2 * ry + 1, pz = 2 * rz + 1;
     const int wy = by + 2 * ry, wz = bz + 2 * rz, wyp = match_wyp(wy, py);
-    const int threads = round_up_i(py * pz, 32);
+    const int threads = round_up_i(match_units(py, pz), 32);
     if (threads > MATCH_MAX_THREADS) return fail(NRR_E_INVALID, "search window too large");
     if (wyp > 256) return fail(NRR_E_INVALID, "search window too large");
 

@@ -4,13 +4,18 @@ rescoring only the shifts whose upper bound reaches the best lower bound.
 That is exact only if, at every shift, the approximate NCC v and its bound e
 satisfy |v - NCC| <= e, NCC being the exact Pearson correlation (Sec. 3, the
 NCC equation).  This test emulates the kernel's float32 arithmetic in numpy,
-operation by operation and in the kernel's order (FMA chains over the
-template rows, the box-sum terms, the bound), with rsqrt.approx and
-sqrt.approx replaced by the exact value perturbed to the edges of their
-2^-22 relative error, and checks the inequality on data chosen to stress it:
-smooth blocks, full-range noise, near-flat blocks with a large mean, two-level
-blocks and near-perfect matches.  The float32 path's bound is checked the same
-way further down.
+operation by operation and in the kernel's order: the window values enter
+centred by the floating block's integer mean m (the kernel forms them as the
+subnormals (u - m) * 2^-149 and scales the template by 2^64, a power-of-two
+rescaling that leaves every rounding unchanged, so the emulation works in
+units of one), one chain of N FMAs per shift, then the box-sum terms and the
+bound, each operation rounded on its own as the kernel writes it; rsqrt.approx and sqrt.approx are replaced by the exact value
+perturbed to the edges of their 2^-22 relative error.  The inequality is
+checked on data chosen to stress it: smooth blocks, full-range noise,
+near-flat blocks with a large mean, two-level blocks and near-perfect
+matches, with the FMA chain taken in both orders the kernel uses (template
+rows innermost along y, or along z).  The float32 path's bound is checked the
+same way further down.
 """
 import numpy as np
 import pytest
@@ -38,7 +43,22 @@ def approx(exact64, delta):
     return f32(exact64 * (1.0 + delta))
 
 
-def kernel_bound(I, W, R, delta_rsqrt, delta_sqrt):
+def _chain(T, W, P, order):
+    """A(d) = sum_k T_k W_{k+d} as one FMA chain per shift, the template
+    walked in the kernel's order: planes outside, rows, then columns
+    ("zyx"), or rows outside, planes, then columns ("yzx")."""
+    bz, by, bx = T.shape
+    acc = np.zeros((P, P, P), np.float32)
+    outer, inner = (bz, by) if order == "zyx" else (by, bz)
+    for o in range(outer):
+        for i in range(inner):
+            kz, ky = (o, i) if order == "zyx" else (i, o)
+            for kx in range(bx):
+                acc = fma32(np.full((P, P, P), T[kz, ky, kx], np.float32), W[kz:kz + P, ky:ky + P, kx:kx + P], acc)
+    return acc
+
+
+def kernel_bound(I, W, R, delta_rsqrt, delta_sqrt, order="zyx"):
     """Approximate NCC v, bound e and exact NCC for every shift of the block
     I (b^3, uint16 values) in the window W ((b+2R)^3), all shifts inside."""
     b = I.shape[0]
@@ -50,20 +70,11 @@ def kernel_bound(I, W, R, delta_rsqrt, delta_sqrt):
     m = (2 * S_I + N) // (2 * N)  # nearest integer to the block mean
     rr = N * m - S_I
     qt = int(((I64 - m) ** 2).sum())
-    # window centring constant: nearest integer mean of the block at zero shift
-    W64 = W.astype(np.int64)
-    S_Jc = int(W64[R:R + b, R:R + b, R:R + b].sum())
-    c = (2 * S_Jc + N) // (2 * N)
     T = (I64 - m).astype(np.float32)  # exact
-    Jc = (W64 - c).astype(np.float32)  # exact
-    # A(d) = sum_k T_k (J_{k+d} - c): FMA chains in the kernel's order
-    acc = np.zeros((P, P, P), np.float32)
-    for kz in range(b):
-        for ky in range(b):
-            for kx in range(b):
-                acc = fma32(np.full((P, P, P), T[kz, ky, kx], np.float32),
-                            Jc[kz:kz + P, ky:ky + P, kx:kx + P], acc)
+    Jc = (W.astype(np.int64) - m).astype(np.float32)  # exact
+    acc = _chain(T, Jc, P, order)
     # exact sums per shift
+    W64 = W.astype(np.int64)
     S_J = np.zeros((P, P, P), np.int64)
     S_JJ = np.zeros((P, P, P), np.int64)
     S_IJ = np.zeros((P, P, P), np.int64)
@@ -85,15 +96,18 @@ def kernel_bound(I, W, R, delta_rsqrt, delta_sqrt):
     kq = round_up32(float(round_up32(float(F(N * GAMMA_N)) * float(round_up32(np.sqrt(float(qf)))))) * 1.000004)
     fvI, frr = F(vI), F(rr)
     vjf = f32(vJ)
-    s1pf = f32(S_J - N * c)
+    s1f = f32(S_J - N * m)
     inv_n = F(1.0) / fN
-    s2p = (fma32(s1pf, s1pf, vjf) * inv_n) * (F(1.0) + F(16.0) * U)
-    inv = approx(1.0 / np.sqrt((fvI * vjf).astype(np.float64)), delta_rsqrt)
-    na = fN * acc
-    rs = frr * s1pf
+    s2u = (fma32(s1f, s1f, vjf) * inv_n) * (F(1.0) + F(16.0) * U)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        inv = approx(1.0 / np.sqrt((fvI * vjf).astype(np.float64)), delta_rsqrt)
+    na = acc * fN
+    rs = frr * s1f
     v = (na + rs) * inv
-    sq = approx(np.sqrt(s2p.astype(np.float64)), delta_sqrt)
-    e = (kq * sq * inv + F(4.0) * U * (np.abs(na) + np.abs(rs)) * inv) * (F(1.0) + F(64.0) * U) + F(40.0) * U * np.abs(v)
+    sq = approx(np.sqrt(s2u.astype(np.float64)), delta_sqrt)
+    t1 = (kq * sq) * inv
+    t2 = ((F(4.0) * U) * (np.abs(na) + np.abs(rs))) * inv
+    e = (t1 + t2) * (F(1.0) + F(64.0) * U) + (F(40.0) * U) * np.abs(v)
     e = F(2.0) * e + F(1e-9)
     valid = vjf > 0
     return v.astype(np.float64), e.astype(np.float64), ncc, valid
@@ -129,12 +143,13 @@ def _cases():
     return cases, R
 
 
+@pytest.mark.parametrize("order", ["zyx", "yzx"])
 @pytest.mark.parametrize("delta_rsqrt,delta_sqrt", [(2.0 ** -22, 2.0 ** -22), (-2.0 ** -22, -2.0 ** -22),
                                                       (2.0 ** -22, -2.0 ** -22), (0.0, 0.0)])
-def test_filter_bound_covers_the_error(delta_rsqrt, delta_sqrt):
+def test_filter_bound_covers_the_error(delta_rsqrt, delta_sqrt, order):
     cases, R = _cases()
     for name, I, W in cases:
-        v, e, ncc, valid = kernel_bound(I, W, R, delta_rsqrt, delta_sqrt)
+        v, e, ncc, valid = kernel_bound(I, W, R, delta_rsqrt, delta_sqrt, order)
         assert valid.any(), name
         err = np.abs(v - ncc)[valid]
         assert (err <= e[valid]).all(), (name, float((err - e[valid]).max()))
@@ -206,13 +221,9 @@ def kernel_bound_f32(I, W, R, delta_rsqrt, delta_sqrt):
                 blk = W[dz:dz + bz, dy:dy + by, dx:dx + bx]
                 S1[dz, dy, dx] = _box_f32(blk)
                 S2[dz, dy, dx] = _box_f32(blk * blk)
-    c_f = S1[R, R, R] / fN
-    Jc = W - c_f
-    acc = np.zeros((P, P, P), np.float32)
-    for kz in range(bz):
-        for ky in range(by):
-            for kx in range(bx):
-                acc = fma32(np.full((P, P, P), T[kz, ky, kx], np.float32), Jc[kz:kz + P, ky:ky + P, kx:kx + P], acc)
+    c_f = tsh  # centring constant: the float mean
+    Jc = W - c_f  # float32, rounded as in the kernel
+    acc = _chain(T, Jc, P, "zyx")
     # exact Pearson correlation of the float values (two-pass, float64)
     I64 = I.astype(np.float64) - I.astype(np.float64).mean()
     ncc = np.full((P, P, P), np.nan)
@@ -224,20 +235,21 @@ def kernel_bound_f32(I, W, R, delta_rsqrt, delta_sqrt):
                 den = np.sqrt((I64 * I64).sum() * (J64 * J64).sum())
                 if den > 0:
                     ncc[dz, dy, dx] = (I64 * J64).sum() / den
-    # the bound, as the kernel evaluates it (float32 path)
+    # the bound, as the kernel evaluates it (float32 path): every operation
+    # rounded on its own, in the kernel's order
     depth = bx + by + bz
     GS = F(depth * 2.0 ** -24 / (1.0 - depth * 2.0 ** -24))
     GN = F(N * 2.0 ** -24 / (1.0 - N * 2.0 ** -24))
     s1b, s2b = S1, np.maximum(S2, F(0.0))
     d1 = approx(np.sqrt((fN * s2b).astype(np.float64)), delta_sqrt)
-    d1 = GS * d1 * F(1.01)
+    d1 = (GS * d1) * F(1.01)
     s1sq_n = (s1b * s1b) * (F(1.0) / fN)
     vJa = s2b - s1sq_n
-    dvJ = GS * s2b + (F(2.0) * np.abs(s1b) + d1) * d1 / fN + F(4.0) * U * (s2b + s1sq_n)
+    dvJ = (GS * s2b + ((F(2.0) * np.abs(s1b) + d1) * d1) / fN) + (F(4.0) * U) * (s2b + s1sq_n)
     s1p = s1b - fN * c_f
-    m2 = s2b + F(2.0) * np.abs(c_f) * np.abs(s1b) + fN * c_f * c_f
-    e2 = (s2b - F(2.0) * c_f * s1b) + fN * c_f * c_f
-    sj2 = (np.maximum(e2, F(0.0)) + (GS + F(8.0) * U) * m2 * F(1.01)) * (F(1.0) + F(4.0) * U)
+    m2 = (s2b + (F(2.0) * np.abs(c_f)) * np.abs(s1b)) + (fN * c_f) * c_f
+    e2 = (s2b - (F(2.0) * c_f) * s1b) + (fN * c_f) * c_f
+    sj2 = (np.maximum(e2, F(0.0)) + ((GS + F(8.0) * U) * m2) * F(1.01)) * (F(1.0) + F(4.0) * U)
     resolved = (vJa - dvJ) > 0
     with np.errstate(invalid="ignore", divide="ignore"):
         rho = dvJ / (vJa - dvJ)
@@ -249,10 +261,12 @@ def kernel_bound_f32(I, W, R, delta_rsqrt, delta_sqrt):
     es = emu * s1p
     num = A - es
     v = num * inv
-    enum = ((GN + F(3.0) * U) * kq * sq + np.abs(emu) * (np.abs(s1p) + d1 + F(2.0) * U * fN * np.abs(c_f)) * F(1.01)
+    enum = ((((GN + F(3.0) * U) * kq) * sq
+             + (np.abs(emu) * ((np.abs(s1p) + d1) + (F(2.0) * U) * (fN * np.abs(c_f)))) * F(1.01))
             + U * (np.abs(A) + np.abs(es)))
-    e = (enum * inv * (F(1.0) + F(0.7) * rho + F(4.0) * U) + np.abs(num) * inv * (F(0.7) * rho + F(6.0) * U)) \
-        * (F(1.0) + F(64.0) * U) + F(43.0) * U * np.abs(v)
+    r1 = (F(1.0) + F(0.7) * rho) + F(4.0) * U
+    r2 = F(0.7) * rho + F(6.0) * U
+    e = ((enum * inv) * r1 + (np.abs(num) * inv) * r2) * (F(1.0) + F(64.0) * U) + (F(43.0) * U) * np.abs(v)
     e = F(2.0) * e + F(1e-9)
     return v.astype(np.float64), e.astype(np.float64), ncc, bounded & ~np.isnan(ncc)
 
