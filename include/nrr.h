@@ -442,6 +442,21 @@ nrr_status nrr_release(uint64_t ticket);
  * internal check fails (NRR_E_INTERNAL).  NRR_OK if neither happened. */
 nrr_status nrr_device_status(void *stream);
 
+/* Test hook for the bounded device-side waits (the paper has no counterpart:
+ * it exists so that tests can make a wait run out without faulting or
+ * hanging the GPU).  For kernels launched after the call:
+ *   limit_ns          the limit of every bounded wait; 0 restores the
+ *                     default of 2 s.  At most 60 s.
+ *   missing_arrivals  arrivals, 0..1024, added to the target of every grid
+ *                     barrier of the connectivity-pattern selection
+ *                     (nrr_select_blocks_spaced) that never come: with one
+ *                     or more, each barrier waits out its limit, the kernel
+ *                     records NRR_E_TIMEOUT in the device error word and
+ *                     returns.  0 restores normal barriers.
+ * Process-wide; takes effect at launch (a captured graph keeps the values
+ * it was captured with).  Returns NRR_E_INVALID for values out of range. */
+nrr_status nrr_test_set_wait(uint64_t limit_ns, int32_t missing_arrivals);
+
 #ifdef __cplusplus
 }
 #endif

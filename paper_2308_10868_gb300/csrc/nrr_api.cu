@@ -52,6 +52,15 @@ nrr_status device_error_word(unsigned int **ptr)
 }
 
 static std::atomic<long long> g_launches{0};
+static std::atomic<unsigned long long> g_wait_ns{0};
+static std::atomic<unsigned int> g_missing{0};
+
+uint64_t device_wait_ns()
+{
+    const unsigned long long v = g_wait_ns.load(std::memory_order_relaxed);
+    return v ? (uint64_t)v : DEVICE_WAIT_NS;
+}
+unsigned int test_missing_arrivals() { return g_missing.load(std::memory_order_relaxed); }
 
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
@@ -168,6 +177,16 @@ const char *nrr_status_string(nrr_status s)
 const char *nrr_last_error(void) { return g_last_error; }
 
 int32_t nrr_version(void) { return 100; }
+
+nrr_status nrr_test_set_wait(uint64_t limit_ns, int32_t missing_arrivals)
+{
+    clear_error();
+    if (missing_arrivals < 0 || missing_arrivals > 1024) return fail(NRR_E_INVALID, "missing_arrivals outside 0..1024");
+    if (limit_ns > 60000000000ull) return fail(NRR_E_INVALID, "limit_ns above 60 s");
+    g_wait_ns.store(limit_ns, std::memory_order_relaxed);
+    g_missing.store((unsigned int)missing_arrivals, std::memory_order_relaxed);
+    return NRR_OK;
+}
 
 int64_t nrr_kernel_launches(void) { return nrr::g_launches.load(std::memory_order_relaxed); }
 

@@ -28,6 +28,14 @@ nrr_status device_error_word(unsigned int **ptr);
 // Bits of the device error word.
 enum : unsigned int { DEV_ERR_TIMEOUT = 1u, DEV_ERR_INTERNAL = 2u };
 
+// Limit of the kernels' bounded device-side waits for later launches (2 s
+// unless a test shortened it through nrr_test_set_wait), and the arrivals
+// that never come which a test adds to the selection pattern's grid
+// barrier (0 outside tests).
+constexpr uint64_t DEVICE_WAIT_NS = 2000000000ull;
+uint64_t device_wait_ns();
+unsigned int test_missing_arrivals();
+
 // Encode a 3-D tiled tensor map over a [nz][ny][nx] volume of `dtype` with a
 // box of (bx, by, bz) elements; out-of-bounds reads fill zeros.
 nrr_status encode_volume_map(CUtensorMap *map, const void *base, nrr_dtype dtype, nrr_dims dims, int bx, int by,

@@ -38,8 +38,9 @@
 //   5. Shifts whose upper bound reaches the best lower bound over the CTA
 //      survive (about one per block on the phantoms); each warp rescores
 //      the survivors of its own lines: uint16 -> exact int64 sums, then the
-//      canonical FP64 ratio num / sqrt(vI * vJ); float32 -> Pearson sums in
-//      float-float pairs and one FP64 ratio.  The best survivor under the
+//      canonical FP64 ratio num / sqrt(vI * vJ); float32 -> Pearson sums of
+//      the values less the block's first value, in float-float pairs, and
+//      one FP64 ratio.  The best survivor under the
 //      tie-break rule is the block's answer.
 // Three CTA barriers per block: after the template, after the lower bounds,
 // after the rescoring.
@@ -72,11 +73,11 @@ struct MatchParams {
     int by, bz;         // block edges along y and z (the x edge is the template parameter B)
     MatchJob jobs[MATCH_MAX_JOBS];
     unsigned int *err;
+    uint64_t wait_ns;  // limit of the wait for a block's copies
 };
 
 constexpr int MATCH_MAX_THREADS = 256;
 constexpr int MATCH_MAX_WARPS = MATCH_MAX_THREADS / 32;
-constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s
 
 // float32 block constants, derived by thread 0 and read by the CTA after
 // the template barrier.
@@ -862,10 +863,10 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         const int x0 = cx - H - RX, xo = x0 - (x0 & ~(ALIGN - 1));
         const int xt = cx - H, xot = xt - (xt & ~(ALIGN - 1));
 
-        const bool got = mbar_wait_bounded(bar + b, phase[b], WAIT_LIMIT_NS);
+        const bool got = mbar_wait_bounded(bar + b, phase[b], a.wait_ns);
         phase[b] ^= 1u;
         // window rows realigned to start at element 0 (read after barrier T)
-        if (xo) realign_window<T, BX>(const_cast<T *>(U), wyp, BY + 2 * ry, wz, xo, tid, nthr);
+        if (xo && got) realign_window<T, BX>(const_cast<T *>(U), wyp, BY + 2 * ry, wz, xo, tid, nthr);
         // thread 0: the next block (its centre goes to the other buffer's
         // record, read by every thread after this block's last barrier)
         if (tid == 0) sc->nb[b] = advance(n, b ^ 1);
@@ -923,16 +924,20 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                                (1.0 + 1e-6));
             }
         } else {
+            // lanes take consecutive values of the block (consecutive
+            // addresses within a row: no bank conflicts)
             int s1 = 0;
             unsigned long long s2 = 0;
-            for (int row = lane; row < NROW; row += 32) {
-                uint32_t vals[B];
-#pragma unroll
-                for (int kx = 0; kx < B; ++kx) vals[kx] = Ut[row * BTX + xot + kx];
-#pragma unroll
-                for (int kx = 0; kx < B; ++kx) {
-                    s1 += (int)vals[kx];
-                    s2 += (unsigned long long)(vals[kx] * vals[kx]);  // below 2^32
+            constexpr int KPL = ANI ? 1 : (N3 + 31) / 32;
+            const int kpl = ANI ? (N + 31) / 32 : KPL;
+#pragma unroll 4
+            for (int q = 0; q < kpl; ++q) {
+                const int k = lane + 32 * q;
+                if (k < N) {
+                    const int row = k / B, kx = k - row * B;
+                    const uint32_t v = Ut[row * BTX + xot + kx];
+                    s1 += (int)v;
+                    s2 += (unsigned long long)(v * v);  // below 2^32
                 }
             }
             s1 = warp_sum(s1);
@@ -979,7 +984,9 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                 atomicOr(a.err, DEV_ERR_TIMEOUT);
                 write_invalid(J, bi, P, py, RX, ry, rz);
             }
-            mbar_wait_bounded(bar + b, phase[b] ^ 1u, WAIT_LIMIT_NS);  // let an in-flight copy land before exiting
+            // let an in-flight copy land before exiting (the full limit:
+            // a copy into this CTA's shared memory must not outlive it)
+            mbar_wait_bounded(bar + b, phase[b] ^ 1u, DEVICE_WAIT_NS);
             return;
         }
         const int nb = sc->nb[b];
@@ -1132,21 +1139,31 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                 } else {
                     const float *pre = reinterpret_cast<const float *>(a.preop);
                     const float *intra = reinterpret_cast<const float *>(a.intraop);
-                    // float-float sums of (I - Ibar) J, J and J^2 (FP32 pipe)
+                    // float-float sums of (I - Ibar) G, G and G^2 with
+                    // G = J - J0, J0 the reference block's first value: the
+                    // shifted values carry the block's spread, not its mean,
+                    // so sum G^2 - (sum G)^2 / N does not cancel however large
+                    // the intensities' offset (FP32 pipe; G exact as gh + ge)
+                    const size_t jrow = ((size_t)(cz + dz - HZ) * ny + (cy + dy - HY)) * nx + (cx + dx - H);
+                    const float j0 = intra[jrow];
                     FF fij{0.f, 0.f}, fj{0.f, 0.f}, fjj{0.f, 0.f};
                     float lo = INFINITY, hi = -INFINITY;
                     for (int k = lane; k < N; k += 32) {
                         const int kz = k / (B * BY), rem = k - kz * B * BY, ky = rem / B, kx = rem - ky * B;
                         const float iv = pre[((size_t)(cz - HZ + kz) * ny + (cy - HY + ky)) * nx + (cx - H + kx)];
-                        const float jf =
-                            intra[((size_t)(cz + dz - HZ + kz) * ny + (cy + dy - HY + ky)) * nx + (cx + dx - H + kx)];
+                        const float jf = intra[jrow + ((size_t)kz * ny + ky) * nx + kx];
                         float dh, de;
                         two_sum(iv, -bcf.ibh, dh, de);  // I - Ibar = dh + dl, nearly exact
                         const float dl = __fsub_rn(de, bcf.ibl);
-                        const float p = __fmul_rn(dh, jf);
-                        fij = ff_add2(fij, p, __fmaf_rn(dl, jf, __fmaf_rn(dh, jf, -p)));
-                        fj = ff_add(fj, jf);
-                        fjj = ff_add_prod(fjj, jf, jf);
+                        float gh, ge;
+                        two_sum(jf, -j0, gh, ge);  // G = J - J0 = gh + ge, exact
+                        // (dh + dl)(gh + ge): the product dh*gh exactly, the
+                        // cross terms to float precision, dl*ge below it
+                        const float p = __fmul_rn(dh, gh);
+                        fij = ff_add2(fij, p, __fmaf_rn(dl, gh, __fmaf_rn(dh, ge, __fmaf_rn(dh, gh, -p))));
+                        fj = ff_add2(fj, gh, ge);
+                        const float q = __fmul_rn(gh, gh);
+                        fjj = ff_add2(fjj, q, __fmaf_rn(2.f * gh, ge, __fmaf_rn(gh, gh, -q)));
                         lo = fminf(lo, jf);
                         hi = fmaxf(hi, jf);
                     }
@@ -1337,6 +1354,7 @@ nrr_status launch_match_variant_l(const MatchLaunch &m, cudaStream_t stream)
     p.bz = bz;
     for (int j = 0; j < MATCH_MAX_JOBS; ++j) p.jobs[j] = j < m.n_jobs ? m.jobs[j] : MatchJob{};
     p.err = m.err;
+    p.wait_ns = device_wait_ns();
     kern<<<(unsigned)grid, threads, L.total, stream>>>(p, mapJ, mapI);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "match kernel launch");

@@ -49,7 +49,6 @@ constexpr int SP_THREADS = 256;
 constexpr int TLX = 16, TLY = 8, TLZ = 8, TPTS = TLX * TLY * TLZ;  // tile of candidate grid points
 constexpr int HX = TLX + 2, HY = TLY + 2, HZ = TLZ + 2, HPTS = HX * HY * HZ;  // with a one-point halo
 constexpr int PPT = TPTS / SP_THREADS;  // tile points per thread
-constexpr uint64_t SP_WAIT_NS = 2000000000ull;
 constexpr int SP_MAX_ROUNDS = 1 << 20;
 constexpr int SP_BINS = 2048;  // histogram of the keys' top 11 bits
 constexpr int SP_PREFIX = 4;   // candidates in play per selected block, and growth factor
@@ -65,14 +64,15 @@ __constant__ signed char c_offs[26][3] = {
     {-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {1, 1, -1}, {-1, -1, 1}, {1, -1, 1}, {-1, 1, 1}, {1, 1, 1}};  // vertex
 
 // Grid-wide barrier number `index` (0, 1, ...): every CTA adds one arrival
-// and waits for (index + 1) * gridDim.x of them.  Returns false if the wait
-// ran out of time.
-__device__ bool grid_barrier(unsigned int *arrive, unsigned int index, uint64_t limit_ns)
+// and waits for (index + 1) * (gridDim.x + missing) of them (missing: 0, or
+// arrivals a test adds that never come).  Returns false if the wait ran out
+// of time.
+__device__ bool grid_barrier(unsigned int *arrive, unsigned int index, uint64_t limit_ns, unsigned int missing)
 {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned int target = (index + 1u) * gridDim.x;
+        const unsigned int target = (index + 1u) * (gridDim.x + missing);
         __threadfence();
         atomicAdd(arrive, 1u);
         int good = 1;
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(SP_THREADS, 2)
     spacing_kernel(long long *__restrict__ keys, int gx, int gy, long long ng, int slots, double frac,
                    unsigned char *__restrict__ state, unsigned int *__restrict__ hmask, SpacingSync *sync,
                    const unsigned long long *nc, const unsigned long long *maxkey, unsigned long long *npos,
-                   unsigned int *err)
+                   unsigned int *err, uint64_t wait_ns, unsigned int missing)
 {
     constexpr int NOFF = ORDER == 1 ? 6 : ORDER == 2 ? 18 : 26;
     const long long chunk = (long long)slots * SP_THREADS;
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(SP_THREADS, 2)
     __syncthreads();
     for (int e = threadIdx.x; e < SP_BINS; e += SP_THREADS)
         if (s_hist[e]) atomicAdd(&sync->hist[e], s_hist[e]);
-    if (!grid_barrier(&sync->arrive, nb++, SP_WAIT_NS)) {
+    if (!grid_barrier(&sync->arrive, nb++, wait_ns, missing)) {
         if (threadIdx.x == 0) atomicOr(err, DEV_ERR_TIMEOUT);
         return;
     }
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(SP_THREADS, 2)
             if (key >= t_lo && key < t_hi) store_state(state + g, SP_UNDECIDED);
             else if (t_hi == 0x7fffffffffffffffll && key < t_lo) store_state(state + g, SP_OUT_OF_PLAY);
         }
-        if (!grid_barrier(&sync->arrive, nb++, SP_WAIT_NS)) {
+        if (!grid_barrier(&sync->arrive, nb++, wait_ns, missing)) {
             if (threadIdx.x == 0) atomicOr(err, DEV_ERR_TIMEOUT);
             return;
         }
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(SP_THREADS, 2)
                 if (s_pend) atomicAdd(&sync->undecided[r % 3], s_pend);
                 if (s_acc) atomicAdd(npos, s_acc);
             }
-            if (!grid_barrier(&sync->arrive, nb++, SP_WAIT_NS)) {
+            if (!grid_barrier(&sync->arrive, nb++, wait_ns, missing)) {
                 if (threadIdx.x == 0) atomicOr(err, DEV_ERR_TIMEOUT);
                 return;
             }
@@ -344,7 +344,9 @@ nrr_status launch_order(long long *keys, int gx, int gy, long long ng, double fr
     unsigned int *err = nullptr;
     nrr_status st = device_error_word(&err);
     if (st != NRR_OK) return st;
-    void *args[] = {&keys, &gx, &gy, &ng, &slots, &frac, &state, &hmask, &sync, &nc, &maxkey, &npos, &err};
+    uint64_t wait_ns = device_wait_ns();
+    unsigned int missing = test_missing_arrivals();
+    void *args[] = {&keys, &gx, &gy, &ng, &slots, &frac, &state, &hmask, &sync, &nc, &maxkey, &npos, &err, &wait_ns, &missing};
     NRR_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)kern, dim3(blocks), dim3(SP_THREADS), args, 0, s));
     count_launches(1);
     return NRR_OK;

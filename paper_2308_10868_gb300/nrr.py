@@ -68,6 +68,7 @@ SIGNATURES = {
     "nrr_block_match_aniso": (C.c_int, [_P, _P, C.c_int, Dims, _P, _I32, _P, _P, _P, _P, _P, _P, _P]),
     "nrr_block_match_bs_aniso": (C.c_int, [_P, _P, _P, C.c_int, Dims, _P, _I32, _P, _P, _P, _P, _P, _P, _P]),
     "nrr_device_status": (C.c_int, [_P]),
+    "nrr_test_set_wait": (C.c_int, [C.c_uint64, _I32]),
     "nrr_autotune_match": (C.c_int, [_P, _P, _P, C.c_int, Dims, _P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P]),
     "nrr_tuning_get": (C.c_int, [C.c_int, _I32, _P, _P]),
     "nrr_tuning_set": (C.c_int, [C.c_int, _I32, _P, _I32]),
@@ -440,6 +441,13 @@ def device_status(stream=None) -> int:
     """Wait for the stream; raise if a kernel reported a timeout or failed
     check since the last call."""
     return _check(lib().nrr_device_status(_stream(stream)), "nrr_device_status")
+
+
+def test_set_wait(limit_ns: int, missing_arrivals: int = 0):
+    """Test hook (nrr_test_set_wait): the limit of later launches' bounded
+    device waits (0 = the 2 s default) and arrivals that never come at the
+    pattern selection's grid barriers (0 = none)."""
+    _check(lib().nrr_test_set_wait(int(limit_ns), int(missing_arrivals)), "nrr_test_set_wait")
 
 
 def to_device_u16(a, device="cuda") -> torch.Tensor:

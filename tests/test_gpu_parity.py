@@ -240,14 +240,44 @@ def test_f32_small_workload(nrr):
 
 
 def test_f32_integer_valued_equals_u16(nrr):
+    # Integer-valued float32 intensities: the float32 path's float-float sums
+    # are exact, so its NCC must equal the uint16 path's (and the oracle's
+    # canonical value) to rounding, and its displacements must be the
+    # oracle's except where the oracle's own scores of the two shifts tie.
     pre, intra, mask = synth.workload_pair("small")
     centers, _ = oracle.select_blocks(pre, mask, 7, 2, 0.1)
     dc = torch.from_numpy(centers).cuda()
     d16, n16, v16 = nrr.block_match(_dev_u16(nrr, pre), _dev_u16(nrr, intra), dc, 7, 4)
     d32, n32, v32 = nrr.block_match(torch.from_numpy(pre.astype(np.float32)).cuda(),
                                     torch.from_numpy(intra.astype(np.float32)).cuda(), dc, 7, 4)
-    assert torch.equal(v16, v32)
+    nrr.device_status()
+    rd, rn, rv = oracle.match(pre, intra, centers, 7, 4)
+    g32, n32h, v32h = d32.cpu().numpy(), n32.cpu().numpy(), v32.cpu().numpy()
+    assert torch.equal(v16, v32) and np.array_equal(v32h, rv)
+    ok = rv == 1
+    assert np.abs(n32h[ok] - rn[ok]).max() < 1e-12
     assert (n16 - n32).abs().max().item() < 1e-12
+    diff = np.nonzero((g32 != rd).any(axis=1) & ok)[0]
+    for i in diff:  # a different shift only on an exact tie of the canonical scores
+        assert abs(oracle.ncc_u16(pre, intra, 7, centers[i], g32[i]) - rn[i]) < 1e-12, (i, g32[i], rd[i])
+    print(f"\ninteger-valued float32: {len(diff)} of {int(ok.sum())} displacements differ from the oracle "
+          f"(canonical-score ties only)")
+
+
+@pytest.mark.parametrize("offset,spread", [(50.0, 1.0), (1000.0, 1e-2)])
+def test_f32_large_offset(nrr, offset, spread):
+    # Intensities on an offset large against their spread.  At 50x the float
+    # box sums still resolve every reference block's spread and the filter
+    # bound applies; at 10^5x they do not, the kernel rescores every shift
+    # exactly (the branch that gives up the bound), and the float-float
+    # rescoring must not lose the spread to the offset.
+    pre, intra, mask = synth.workload_pair("small")
+    centers, _ = oracle.select_blocks(pre, mask, 7, 2, 0.1)
+    centers = centers[:160]
+    off, sp = np.float32(offset), np.float32(spread)
+    p32 = (off + synth.as_f32(pre) * sp).astype(np.float32)
+    i32 = (off + synth.as_f32(intra) * sp).astype(np.float32)
+    _check_f32(nrr, p32, i32, centers, 7, 3)
 
 
 

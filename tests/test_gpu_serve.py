@@ -2,10 +2,10 @@
 
 Requests of mixed sizes and parameters run concurrently on several slots;
 each result must equal the same registration run alone through the
-synchronous calls, bit for bit (uint16) and within the float32 tolerance of
-the parity tests (float32 requests use the same kernels, so they are exact
-here too).  Failures are injected on the host (an allocation reported as
-failed), never on the GPU.
+synchronous calls, bit for bit (float32 requests use the same kernels, so
+they are exact here too), and the oracle: uint16 selections and matches bit
+for bit, float32 matches within the parity tests' tolerance.  Failures are
+injected on the host (an allocation reported as failed), never on the GPU.
 """
 import os
 import time
@@ -13,6 +13,7 @@ import time
 import numpy as np
 import pytest
 
+import oracle
 from paper_2308_10868_gb300 import synth
 
 torch = pytest.importorskip("torch")
@@ -31,13 +32,36 @@ def nrr():
     return m
 
 
-def _pairs(nrr):
+def _pairs(nrr, host=None):
     out = []
     for k, dims in enumerate([(64, 64, 48), (96, 80, 56), (128, 96, 64)]):
         pre, intra, mask, _ = synth.make_pair(dims, 4.0, 20.0, 300 + k)
+        if host is not None:
+            host.append((pre, intra, mask))
         out.append((nrr.to_device_u16(pre), nrr.to_device_u16(intra), torch.from_numpy(mask).cuda(),
                     torch.from_numpy(synth.as_f32(pre)).cuda(), torch.from_numpy(synth.as_f32(intra)).cuda()))
     return out
+
+
+def _check_oracle(pre, intra, mask, b, r, f, f32, got):
+    """A served result against the oracle run on the host copies."""
+    rc, _ = oracle.select_blocks(pre, mask, b, 2, f)
+    assert np.array_equal(got["centers"].cpu().numpy(), rc)
+    gd, gn, gv = (got[k].cpu().numpy() for k in ("disp", "ncc", "valid"))
+    if not f32:
+        rd, rn, rv = oracle.match(pre, intra, rc, b, r)
+        assert np.array_equal(gd, rd) and np.array_equal(gv, rv)
+        assert np.array_equal(np.isnan(gn), np.isnan(rn))
+        assert np.array_equal(gn[~np.isnan(gn)].view(np.int64), rn[~np.isnan(rn)].view(np.int64))
+    else:
+        p32, i32 = synth.as_f32(pre), synth.as_f32(intra)
+        rd, rn, rv = oracle.match(p32, i32, rc, b, r)
+        assert np.array_equal(gv, rv)
+        ok = rv == 1
+        at = np.array([oracle.pearson_f32(p32, i32, b, rc[i], gd[i]) if ok[i] else np.nan for i in range(len(rc))])
+        assert np.abs(gn[ok] - at[ok]).max(initial=0.0) <= 1e-6
+        diff = (gd != rd).any(axis=1) & ok
+        assert (rn[diff] - at[diff] <= 2e-6).all()
 
 
 def _wait(srv, tickets, timeout=60.0):
@@ -53,7 +77,8 @@ def _wait(srv, tickets, timeout=60.0):
 
 
 def test_mixed_stream_equals_lone_calls(nrr):
-    pairs = _pairs(nrr)
+    host = []
+    pairs = _pairs(nrr, host)
     rng = np.random.default_rng(7)
     reqs = []
     for i in range(24):
@@ -83,6 +108,7 @@ def test_mixed_stream_equals_lone_calls(nrr):
             assert np.array_equal(np.isnan(g), np.isnan(e))
             assert np.abs(g[~np.isnan(g)] - e[~np.isnan(e)]).max(initial=0.0) == 0.0
             assert 0.0 <= got["queued_s"] <= got["latency_s"]
+            _check_oracle(*host[p], b, r, f, f32, got)
             srv.release(t)
         with pytest.raises(nrr.NrrError) as ei:
             srv.poll(tickets[0])

@@ -349,28 +349,24 @@ def test_spaced_selection_equal_keys_gives_the_closed_form_lattice(conn, stride)
     assert np.array_equal(part, expect[order][:oracle.n_select(nc, frac)].astype(np.int32))
 
 
-@pytest.mark.parametrize("conn", [6, 18, 26])
-@pytest.mark.parametrize("b,stride,frac", [(3, 1, 0.08), (3, 2, 0.3), (5, 1, 1.0), (5, 3, 0.2)])
-def test_spaced_selection_is_the_greedy_independent_set(conn, b, stride, frac):
-    # The greedy result S is characterised by: (1) no two members of S are
-    # pattern neighbours; (2) |S| = min(n_sel, size of the full greedy set);
-    # (3) every unselected candidate with a positive key that precedes the
-    # last member of S in selection order (or any, if |S| < n_sel) has a
-    # member of S among its neighbours that precedes it.  Any set with these
-    # properties equals the greedy one (a first difference contradicts (1)).
-    pre = _phantom((30, 27, 25), seed=11 + conn)
-    mask = np.zeros(pre.shape, np.uint8)
-    mask[3:-3, 2:-2, 4:-1] = 1
-    got, nc = oracle.select_blocks_spaced(pre, mask, b, stride, frac, conn)
-    keys, _ = oracle.grid_keys(pre, mask, b, stride)
+def _selection_ranks(keys):
+    """Rank of every candidate with a positive key in selection order (key
+    descending, raster index ascending), keyed by its grid point (k, j, i)."""
     gz, gy, gx = keys.shape
-    rank = {}
-    flat = [(int(keys[k, j, i]), (k * gy + j) * gx + i, (k, j, i)) for k, j, i in np.argwhere(keys > 0)]
+    flat = [(int(keys[k, j, i]), (k * gy + j) * gx + i, (int(k), int(j), int(i))) for k, j, i in np.argwhere(keys > 0)]
     flat.sort(key=lambda t: (-t[0], t[1]))
-    for r, (_, _, kji) in enumerate(flat):
-        rank[tuple(int(q) for q in kji)] = r
-    S = {(int(c[2]) // stride, int(c[1]) // stride, int(c[0]) // stride) for c in got}
-    assert len(S) == len(got)
+    return {kji: r for r, (_, _, kji) in enumerate(flat)}
+
+
+def _greedy_violation(S, rank, conn, want):
+    """Why the grid-point set S is not the greedy selection with pattern
+    `conn` truncated at `want` members, or None if it is.  The greedy result
+    is characterised by: (1) no two members of S are pattern neighbours;
+    (2) |S| = min(want, size of the full greedy set); (3) every unselected
+    candidate with a positive key that precedes the last member of S in
+    selection order (or any, if |S| < want) has a member of S among its
+    neighbours that precedes it.  Any set with these properties equals the
+    greedy one (a first difference contradicts (1))."""
     offs = _pattern_offsets(conn)
 
     def nbrs(p):
@@ -380,17 +376,80 @@ def test_spaced_selection_is_the_greedy_independent_set(conn, b, stride, frac):
                 yield q
 
     for p in S:  # (1)
-        assert p in rank
-        assert not any(q in S for q in nbrs(p))
-    want = oracle.n_select(nc, frac)
-    assert len(S) <= want
+        if p not in rank:
+            return f"{p} is not a candidate with a positive key"
+        if any(q in S for q in nbrs(p)):
+            return f"{p} has a selected neighbour"
+    if len(S) > want:
+        return f"{len(S)} selected, more than {want}"
     last = max(rank[p] for p in S) if S else -1
     for p, r in rank.items():  # (3)
         if p in S or (len(S) == want and r > last):
             continue
-        assert any(q in S and rank[q] < r for q in nbrs(p)), p
-    if len(S) < want:  # (2): the walk ran out of candidates, nothing is left to add
-        assert all(p in S or any(q in S for q in nbrs(p)) for p in rank)
+        if not any(q in S and rank[q] < r for q in nbrs(p)):
+            return f"{p} was skipped without an earlier selected neighbour"
+    if len(S) < want and not all(p in S or any(q in S for q in nbrs(p)) for p in rank):  # (2)
+        return "the walk stopped short with candidates left to add"
+    return None
+
+
+@pytest.mark.parametrize("conn", [6, 18, 26])
+@pytest.mark.parametrize("b,stride,frac", [(3, 1, 0.08), (3, 2, 0.3), (5, 1, 1.0), (5, 3, 0.2)])
+def test_spaced_selection_is_the_greedy_independent_set(conn, b, stride, frac):
+    pre = _phantom((30, 27, 25), seed=11 + conn)
+    mask = np.zeros(pre.shape, np.uint8)
+    mask[3:-3, 2:-2, 4:-1] = 1
+    got, nc = oracle.select_blocks_spaced(pre, mask, b, stride, frac, conn)
+    keys, _ = oracle.grid_keys(pre, mask, b, stride)
+    rank = _selection_ranks(keys)
+    S = {(int(c[2]) // stride, int(c[1]) // stride, int(c[0]) // stride) for c in got}
+    assert len(S) == len(got)
+    assert _greedy_violation(S, rank, conn, oracle.n_select(nc, frac)) is None
+
+
+def _walk(rank, conn, want, mistake=None):
+    """The greedy walk in selection order, written out in Python, with an
+    optional planted mistake: "order" uses the next larger neighbourhood for
+    the exclusion (face -> edge, edge -> vertex, vertex -> face), "stop"
+    takes one member past `want`, "taken" marks a skipped candidate as taken
+    too (so it blocks its later neighbours)."""
+    use = {6: 18, 18: 26, 26: 6}[conn] if mistake == "order" else conn
+    offs = _pattern_offsets(use)
+    taken, S = set(), set()
+    limit = want + 1 if mistake == "stop" else want
+    for p, _ in sorted(rank.items(), key=lambda t: t[1]):
+        if len(S) >= limit:
+            break
+        blocked = any((p[0] + o[2], p[1] + o[1], p[2] + o[0]) in taken for o in offs)
+        if not blocked:
+            S.add(p)
+            taken.add(p)
+        elif mistake == "taken":
+            taken.add(p)
+    return S
+
+
+@pytest.mark.parametrize("conn", [6, 18, 26])
+def test_greedy_checks_catch_planted_mistakes(conn):
+    # The characterisation above must accept the correct walk (which must
+    # equal the oracle's selection) and reject each planted mistake: an
+    # exclusion neighbourhood one order off, a walk that does not stop at
+    # n_sel, a skipped candidate wrongly marked taken.
+    pre = _phantom((30, 27, 25), seed=23 + conn)
+    mask = np.zeros(pre.shape, np.uint8)
+    mask[3:-3, 2:-2, 4:-1] = 1
+    b, stride, frac = 3, 1, 0.08
+    got, nc = oracle.select_blocks_spaced(pre, mask, b, stride, frac, conn)
+    keys, _ = oracle.grid_keys(pre, mask, b, stride)
+    rank = _selection_ranks(keys)
+    want = oracle.n_select(nc, frac)
+    good = _walk(rank, conn, want)
+    assert good == {(int(c[2]) // stride, int(c[1]) // stride, int(c[0]) // stride) for c in got}
+    assert _greedy_violation(good, rank, conn, want) is None
+    for mistake in ("order", "stop", "taken"):
+        bad = _walk(rank, conn, want, mistake)
+        assert bad != good, mistake
+        assert _greedy_violation(bad, rank, conn, want) is not None, mistake
 
 
 @pytest.mark.parametrize("conn", [6, 26])
