@@ -26,8 +26,8 @@
  *    of 16 bytes (the row pitch of the TMA tensor map) and the base
  *    pointer 16-byte aligned.
  *  - Block edge `block` is the full odd edge b (3, 5, 7, 9 or 11);
- *    h = (b-1)/2.  Search radius is given per axis {rx, ry, rz}, each 0..7;
- *    the candidate shifts are d in [-rx,rx] x [-ry,ry] x [-rz,rz].
+ *    h = (b-1)/2.  Search radius is given per axis {rx, ry, rz}, each
+ *    0..15; the candidate shifts are d in [-rx,rx] x [-ry,ry] x [-rz,rz].
  *  - Centres and displacements are int32 triples (x, y, z).
  *  - NCC is Pearson's correlation of the block of the floating image at c
  *    with the block of the reference image at c+d.  A shift whose block
@@ -225,7 +225,7 @@ nrr_status nrr_boxsums(const void *d_intraop, nrr_dtype dtype, nrr_dims dims, in
  *   d_preop, d_intraop  device volumes of `dtype` (uint16 or float32)
  *   d_centers  device int32 [n_blocks][3]
  *   d_n_blocks device int32, optional: actual count, read on the device
- *   block      odd 3..11;  radius  host int32[3] = {rx, ry, rz}, each 0..7
+ *   block      odd 3..11;  radius  host int32[3] = {rx, ry, rz}, each 0..15
  *   d_disp     device int32 [n_blocks][3], written: best d (x, y, z)
  *   d_ncc      device double [n_blocks], written: NCC at d (NaN if invalid)
  *   d_valid    device uint8 [n_blocks], written: 1 if the block had at
@@ -239,6 +239,11 @@ nrr_status nrr_boxsums(const void *d_intraop, nrr_dtype dtype, nrr_dims dims, in
  * FP64, so the returned NCC is the FP64 Pearson value of the chosen shift
  * (the chosen shift can differ from an FP64 reference only between shifts
  * whose FP64 scores differ by rounding).
+ *
+ * A radius above 7 on an axis is searched as sub-windows of one smaller
+ * radius that tile [-r, r] on that axis (two for r = 8..11, three for
+ * r = 12..15; they may overlap), each block's sub-windows in turn within
+ * the same launch; the result is the same best shift under the rule above.
  *
  * nrr_block_match computes the box sums itself (scratch from the stream-
  * ordered pool); nrr_block_match_bs takes them precomputed by nrr_boxsums
@@ -358,7 +363,7 @@ nrr_status nrr_tuning_load(const char *path);
 typedef struct {
     int32_t block;      /* odd 3..11 */
     int32_t stride;     /* 1..64 */
-    int32_t radius[3];  /* 0..7 each */
+    int32_t radius[3];  /* 0..15 each; radius reuse across settings only up to 7 */
     double frac;        /* (0, 1] */
 } nrr_setting;
 

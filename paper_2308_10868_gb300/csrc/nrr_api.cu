@@ -237,7 +237,8 @@ static nrr_status check_match_args(const void *d_preop, const void *d_intraop, n
     if (st != NRR_OK) return st;
     if (!radius) return fail(NRR_E_INVALID, "radius is NULL");
     for (int i = 0; i < 3; ++i)
-        if (radius[i] < 0 || radius[i] > 7) return fail(NRR_E_INVALID, "radius[%d]=%d outside 0..7", i, radius[i]);
+        if (radius[i] < 0 || radius[i] > MATCH_MAX_R)
+            return fail(NRR_E_INVALID, "radius[%d]=%d outside 0..%d", i, radius[i], MATCH_MAX_R);
     if (n_blocks < 0) return fail(NRR_E_INVALID, "n_blocks < 0");
     if (!d_preop || !d_intraop) return fail(NRR_E_INVALID, "NULL volume");
     if (!aligned16(d_preop) || !aligned16(d_intraop)) return fail(NRR_E_INVALID, "volumes must be 16-byte aligned");

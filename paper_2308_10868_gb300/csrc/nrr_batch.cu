@@ -289,7 +289,8 @@ nrr_status nrr_batch_create(const uint16_t *d_preop, const uint16_t *d_intraop, 
             return fail(st, "setting %d: %s", i, why);
         }
         for (int k = 0; k < 3; ++k)
-            if (s.radius[k] < 0 || s.radius[k] > 7) return fail(NRR_E_INVALID, "setting %d: radius outside 0..7", i);
+            if (s.radius[k] < 0 || s.radius[k] > MATCH_MAX_R)
+                return fail(NRR_E_INVALID, "setting %d: radius outside 0..%d", i, MATCH_MAX_R);
     }
     nrr_batch_s *b = new nrr_batch_s();
     b->preop = d_preop;
@@ -393,7 +394,10 @@ nrr_status nrr_batch_create(const uint16_t *d_preop, const uint16_t *d_intraop, 
         int host = -1;
         for (int a_ : launched) {
             const nrr_setting &sa = settings[a_];
-            if (sa.block == su.block && sa.stride == su.stride && sa.frac >= su.frac &&
+            // a search answers smaller boxes only while one window holds it
+            const bool one_window = sa.radius[0] <= MATCH_WINDOW_R && sa.radius[1] <= MATCH_WINDOW_R &&
+                                    sa.radius[2] <= MATCH_WINDOW_R;
+            if (one_window && sa.block == su.block && sa.stride == su.stride && sa.frac >= su.frac &&
                 sa.radius[0] >= su.radius[0] && sa.radius[1] >= su.radius[1] && sa.radius[2] >= su.radius[2] &&
                 (int)b->outs[a_].levels.size() < MATCH_MAX_LEVELS) {
                 host = a_;

@@ -85,6 +85,11 @@ constexpr int MATCH_MAX_JOBS = 16;
 // Extra search radii a job reports besides its own (batched search): the
 // best shift within a smaller box [-r, r] per axis, from the same search.
 constexpr int MATCH_MAX_LEVELS = 4;
+// Largest search radius per axis one window holds, and the most sub-windows
+// per axis a larger radius is split into (radius up to 15 needs three).
+constexpr int MATCH_WINDOW_R = 7;
+constexpr int MATCH_MAX_SUB = 4;
+constexpr int MATCH_MAX_R = 15;
 struct MatchLevel {
     int32_t r[3];
     int32_t *disp;
@@ -116,7 +121,18 @@ struct MatchLaunch {
     int ctas_per_sm;  // persistent CTAs per SM; 0 = as many as fit
     int one_cta_per_block;  // plain launch: one CTA per block instead of persistent CTAs
     unsigned int *err;
+    // filled in by launch_match: sub-windows of radius sub_r per axis that
+    // tile [-radius, radius] (one of radius `radius` when it is at most
+    // MATCH_WINDOW_R), nsub per axis centred at soff
+    int sub_r[3];
+    int nsub[3];
+    int soff[3][MATCH_MAX_SUB];
 };
+// Sub-windows for a search radius R on one axis: k = ceil((2R+1)/15) windows
+// of one radius r (k(2r+1) >= 2R+1), centred at min(-R + r + i(2r+1),
+// R - r): they cover [-R, R], may overlap (a shift searched twice gives the
+// same exact score), and need one window of radius r in shared memory.
+void plan_subwindows(int R, int *r, int *k, int *off);
 nrr_status launch_match(const MatchLaunch &a, cudaStream_t stream);
 
 // Upper bound on resident match CTAs per SM for this launch's variant.

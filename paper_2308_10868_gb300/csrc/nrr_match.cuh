@@ -74,10 +74,24 @@ struct MatchParams {
     MatchJob jobs[MATCH_MAX_JOBS];
     unsigned int *err;
     uint64_t wait_ns;  // limit of the wait for a block's copies
+    // Search radius above what one window holds: the jobs' full radii, and
+    // the sub-windows (radius rx = (P-1)/2, ry, rz each) that tile
+    // [-R, R] per axis, nsub[axis] of them centred at soff[axis][0..]
+    int R[3];
+    int nsub[3];
+    int soff[3][MATCH_MAX_SUB];
+    int nsubt;  // nsub[0] * nsub[1] * nsub[2]
 };
 
 constexpr int MATCH_MAX_THREADS = 256;
 constexpr int MATCH_MAX_WARPS = MATCH_MAX_THREADS / 32;
+
+struct Cand {
+    double s;
+    int n2;
+    int code;
+    int ok;
+};
 
 // float32 block constants, derived by thread 0 and read by the CTA after
 // the template barrier.
@@ -104,8 +118,10 @@ struct BlockConstU {
 struct MatchScratch {
     BlockConstF bc;
     BlockConstU bu;
-    int cen[2][5];  // per window buffer: cx, cy, cz, job, index of the block in its job
+    int cen[2][6];  // per window buffer: cx, cy, cz, job, index of the block in its job, sub-window
+    Cand sbest;     // best candidate of the current block over its sub-windows so far
     int nb[2];      // per window buffer: the work item after that buffer's block
+    int ns[2];      // and its sub-window
     float wlb[MATCH_MAX_WARPS];
     double bs[MATCH_MAX_WARPS];
     int bn2[MATCH_MAX_WARPS];
@@ -189,13 +205,6 @@ __host__ __device__ inline MatchLayout match_layout(int elem, int B, int P, int 
     L.total = o;
     return L;
 }
-
-struct Cand {
-    double s;
-    int n2;
-    int code;
-    int ok;
-};
 
 // NCC descending, then |d|^2 ascending, then (dz, dy, dx) lexicographic
 // ascending; `code` increases with (dz, dy, dx) lexicographically.
@@ -309,6 +318,8 @@ __device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c)
     return d;
 }
 
+// Codes of candidate shifts run over the full search box [-R, R] per axis
+// (x fastest: P = 2 Rx + 1 x-shifts, py = 2 Ry + 1 y-shifts).
 __device__ __forceinline__ void write_out(int32_t *disp, double *ncc, uint8_t *valid, int blk, const Cand &b, int P,
                                           int py, int rx, int ry, int rz)
 {
@@ -744,9 +755,22 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
     // u * 2^-149, so a search sum is A * 2^-85
     constexpr float TSCALE = 0x1p64f;
 
-    const int ry = a.ry, rz = a.rz, py = 2 * ry + 1, pz = 2 * rz + 1;
+    const int ry = a.ry, rz = a.rz, py = 2 * ry + 1, pz = 2 * rz + 1;  // one (sub-)window
     const int wz = BZ + 2 * rz, wyp = a.wyp;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
+    // the full search box: candidate codes, displacements and levels use it
+    const int Rx = a.R[0], Ry = a.R[1], Rz = a.R[2], PxF = 2 * Rx + 1, PyF = 2 * Ry + 1;
+    const int nsubt = a.nsubt;
+    // offset of sub-window s (x fastest) from the block centre
+    auto sub_off = [&](int s, int &ox, int &oy, int &oz) {
+        ox = oy = oz = 0;
+        if (nsubt > 1) {
+            const int sx = s % a.nsub[0], sy = (s / a.nsub[0]) % a.nsub[1], sz = s / (a.nsub[0] * a.nsub[1]);
+            ox = a.soff[0][sx];
+            oy = a.soff[1][sy];
+            oz = a.soff[2][sz];
+        }
+    };
 
     extern __shared__ __align__(128) unsigned char smem[];
     const MatchLayout L =
@@ -801,9 +825,10 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                 sc->cen[buf][2] = c2;
                 sc->cen[buf][3] = j;
                 sc->cen[buf][4] = i;
+                sc->cen[buf][5] = 0;
                 break;
             }
-            write_invalid(a.jobs[j], i, P, py, RX, ry, rz);
+            write_invalid(a.jobs[j], i, PxF, PyF, Rx, Ry, Rz);
             w += gridDim.x;
             if (w < n) {
                 int j2, i2;
@@ -817,13 +842,26 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         prefetch(w + gridDim.x, n);
         return w < n ? w : n;
     };
-    // both copies of the block recorded in cen[buf] into buffer buf
+    // the next item: the block's next sub-window, else the next block
+    auto next_item = [&](int n, int buf, int cur_blk, int cur_s, int &ns) {
+        if (cur_s + 1 < nsubt) {
+            for (int q = 0; q < 5; ++q) sc->cen[buf ^ 1][q] = sc->cen[buf][q];
+            sc->cen[buf ^ 1][5] = cur_s + 1;
+            ns = cur_s + 1;
+            return cur_blk;
+        }
+        ns = 0;
+        return advance(n, buf ^ 1);
+    };
+    // both copies of the item recorded in cen[buf] into buffer buf
     auto issue = [&](int buf) {
         const int cx = sc->cen[buf][0], cy = sc->cen[buf][1], cz = sc->cen[buf][2];
-        const int x0 = cx - H - RX, xt = cx - H;
+        int ox, oy, oz;
+        sub_off(sc->cen[buf][5], ox, oy, oz);
+        const int x0 = cx + ox - H - RX, xt = cx - H;
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(bar + buf, tx_bytes);
-        tma_load_3d(smem + L.u[buf], tmapJ, bar + buf, x0 & ~(ALIGN - 1), cy - HY - ry, cz - HZ - rz);
+        tma_load_3d(smem + L.u[buf], tmapJ, bar + buf, x0 & ~(ALIGN - 1), cy + oy - HY - ry, cz + oz - HZ - rz);
         tma_load_3d(smem + L.ut[buf], tmapI, bar + buf, xt & ~(ALIGN - 1), cy - HY, cz - HZ);
     };
 
@@ -845,10 +883,11 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         prefetch(blockIdx.x, w);
         const int first = advance(w, 0);
         sc->nb[1] = first;  // the loop starts with buffer 0 holding `first`
+        sc->ns[1] = 0;
         if (first < w) issue(0);
     }
     __syncthreads();
-    const int n = sc->jstart[a.n_jobs];  // work items over all jobs
+    const int n = sc->jstart[a.n_jobs];  // blocks over all jobs
     int blk = sc->nb[1];
 
     uint32_t phase[2] = {0u, 0u};
@@ -860,7 +899,14 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         const int cx = sc->cen[b][0], cy = sc->cen[b][1], cz = sc->cen[b][2];
         const MatchJob &J = a.jobs[sc->cen[b][3]];
         const int bi = sc->cen[b][4];
-        const int x0 = cx - H - RX, xo = x0 - (x0 & ~(ALIGN - 1));
+        const int si = sc->cen[b][5];  // sub-window of this item
+        int x0;
+        {
+            int ox, oy, oz;
+            sub_off(si, ox, oy, oz);
+            x0 = cx + ox - H - RX;
+        }
+        const int xo = x0 - (x0 & ~(ALIGN - 1));
         const int xt = cx - H, xot = xt - (xt & ~(ALIGN - 1));
 
         const bool got = mbar_wait_bounded(bar + b, phase[b], a.wait_ns);
@@ -869,7 +915,11 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         if (xo && got) realign_window<T, BX>(const_cast<T *>(U), wyp, BY + 2 * ry, wz, xo, tid, nthr);
         // thread 0: the next block (its centre goes to the other buffer's
         // record, read by every thread after this block's last barrier)
-        if (tid == 0) sc->nb[b] = advance(n, b ^ 1);
+        if (tid == 0) {
+            int ns;
+            sc->nb[b] = next_item(n, b, blk, si, ns);
+            sc->ns[b] = ns;
+        }
 
         // ---- floating block statistics: every warp sums the whole block ----
         // uint16: exact integer sums; thread 0 stores the block constants.
@@ -924,20 +974,16 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                                (1.0 + 1e-6));
             }
         } else {
-            // lanes take consecutive values of the block (consecutive
-            // addresses within a row: no bank conflicts)
             int s1 = 0;
             unsigned long long s2 = 0;
-            constexpr int KPL = ANI ? 1 : (N3 + 31) / 32;
-            const int kpl = ANI ? (N + 31) / 32 : KPL;
-#pragma unroll 4
-            for (int q = 0; q < kpl; ++q) {
-                const int k = lane + 32 * q;
-                if (k < N) {
-                    const int row = k / B, kx = k - row * B;
-                    const uint32_t v = Ut[row * BTX + xot + kx];
-                    s1 += (int)v;
-                    s2 += (unsigned long long)(v * v);  // below 2^32
+            for (int row = lane; row < NROW; row += 32) {
+                uint32_t vals[B];
+#pragma unroll
+                for (int kx = 0; kx < B; ++kx) vals[kx] = Ut[row * BTX + xot + kx];
+#pragma unroll
+                for (int kx = 0; kx < B; ++kx) {
+                    s1 += (int)vals[kx];
+                    s2 += (unsigned long long)(vals[kx] * vals[kx]);  // below 2^32
                 }
             }
             s1 = warp_sum(s1);
@@ -982,7 +1028,7 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         if (!__syncthreads_and(got)) {
             if (tid == 0) {
                 atomicOr(a.err, DEV_ERR_TIMEOUT);
-                write_invalid(J, bi, P, py, RX, ry, rz);
+                write_invalid(J, bi, PxF, PyF, Rx, Ry, Rz);
             }
             // let an in-flight copy land before exiting (the full limit:
             // a copy into this CTA's shared memory must not outlive it)
@@ -994,7 +1040,7 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         if (!single && nb < n && tid == 0) issue(b ^ 1);
         if (flat) {  // flat floating block: NCC undefined for every shift
             if (single && nb < n && tid == 0) issue(b ^ 1);  // the window is not read
-            if (tid == 0) write_invalid(J, bi, P, py, RX, ry, rz);
+            if (tid == 0) write_invalid(J, bi, PxF, PyF, Rx, Ry, Rz);
             blk = nb;
             ++i;
             continue;
@@ -1024,12 +1070,17 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
             // subnormal m * 2^-149, whose bits are m)
             const float csh = F32 ? tsh : __uint_as_float((uint32_t)m);
             search_pair<T, B, P>(row0, sI, sO, Ts, tI, tO, bI, bO, csh, acc0, acc1);
-            // both lines' box sums first (one L2 round trip), then the bounds
+            // both lines' box sums first (one L2 round trip), then the bounds;
+            // the sub-window offset is read again (no registers held across
+            // the search)
+            int ox, oy, oz;
+            sub_off(sc->cen[b][5], ox, oy, oz);
             typedef typename std::conditional<F32, float, int32_t>::type S1T;
             S1T q1a[P], q1b[P];
             float q2a[P], q2b[P];
-            const uint32_t va = line_boxsums<T, B, P>(a, cx, cy, cz, un.dy0, un.dz0, HY, HZ, q1a, q2a);
-            const uint32_t vb = un.two ? line_boxsums<T, B, P>(a, cx, cy, cz, dy1, dz1, HY, HZ, q1b, q2b) : 0u;
+            const uint32_t va = line_boxsums<T, B, P>(a, cx + ox, cy + oy, cz + oz, un.dy0, un.dz0, HY, HZ, q1a, q2a);
+            const uint32_t vb =
+                un.two ? line_boxsums<T, B, P>(a, cx + ox, cy + oy, cz + oz, dy1, dz1, HY, HZ, q1b, q2b) : 0u;
             const float kq = F32 ? 0.f : sc->bu.kq, fvI = F32 ? 0.f : sc->bu.fvI, frr = F32 ? 0.f : sc->bu.frr;
             line_bounds<T, B, P, LEV>(J, nl, un.dy0, un.dz0, ry, rz, N, BY, BZ, acc0, q1a, q2a, va, kq, fvI, frr, m, tsh,
                                       bcf, GAMMA_L, ub0, lbm, lbl);
@@ -1078,6 +1129,8 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
 
         // ---- exact rescoring of this warp's survivors -------------------------
         Cand wb{0.0, 0, 0, 0};
+        int ox, oy, oz;
+        sub_off(sc->cen[b][5], ox, oy, oz);
         uint32_t act = __ballot_sync(0xffffffffu, smask != 0);
         while (act) {
             const int src = __ffs(act) - 1;
@@ -1091,8 +1144,9 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                 const int second = bit >> 4, sxi = bit & 15;
                 const int syi = su.dy0 + (second && !su.along_z ? 1 : 0);
                 const int szi = su.dz0 + (second && su.along_z ? 1 : 0);
-                const int code = (szi * py + syi) * P + sxi;
-                const int dx = sxi - RX, dy = syi - ry, dz = szi - rz;
+                // the shift in the full search box (this sub-window's offset added)
+                const int dx = sxi - RX + ox, dy = syi - ry + oy, dz = szi - rz + oz;
+                const int code = ((dz + Rz) * PyF + (dy + Ry)) * PxF + (dx + Rx);
                 Cand c{0.0, dx * dx + dy * dy + dz * dz, code, 0};
                 if constexpr (!F32) {
                     const int mm = sc->bu.m;
@@ -1185,7 +1239,7 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                     if (cand_better(c, wb)) wb = c;
                     if constexpr (LEV)
                         for (int l = 0; l < nl; ++l)
-                            if (in_level(code, J.levels[l].r, P, py, RX, ry, rz)) {
+                            if (in_level(code, J.levels[l].r, PxF, PyF, Rx, Ry, Rz)) {
                                 const Cand cur{ls->lbs[l][warp], ls->lbn2[l][warp], ls->lbcode[l][warp],
                                                ls->lbok[l][warp]};
                                 if (cand_better(c, cur)) {
@@ -1214,7 +1268,13 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                 Cand c{sc->bs[w], sc->bn2[w], sc->bcode[w], sc->bok[w]};
                 if (cand_better(c, best)) best = c;
             }
-            write_result(J, bi, best, P, py, RX, ry, rz);
+            // over the block's sub-windows (in order, in this CTA): the
+            // best so far, written with the last one
+            if (nsubt > 1) {
+                if (si > 0 && !cand_better(best, sc->sbest)) best = sc->sbest;
+                sc->sbest = best;
+            }
+            if (si == nsubt - 1) write_result(J, bi, best, PxF, PyF, Rx, Ry, Rz);
             if constexpr (LEV)
                 for (int l = 0; l < nl; ++l) {
                     Cand bl{0.0, 0, 0, 0};
@@ -1222,7 +1282,7 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                         Cand c{ls->lbs[l][w], ls->lbn2[l][w], ls->lbcode[l][w], ls->lbok[l][w]};
                         if (cand_better(c, bl)) bl = c;
                     }
-                    write_out(J.levels[l].disp, J.levels[l].ncc, J.levels[l].valid, bi, bl, P, py, RX, ry, rz);
+                    write_out(J.levels[l].disp, J.levels[l].ncc, J.levels[l].valid, bi, bl, PxF, PyF, Rx, Ry, Rz);
                 }
         }
         blk = nb;
@@ -1279,7 +1339,7 @@ nrr_status choose_layout(const MatchLaunch &m, MatchLayout *L, bool *single, int
 {
     constexpr int ALIGN = 16 / (int)sizeof(T);
     const int by = launch_by(m), bz = launch_bz(m);
-    const int ry = m.radius[1], rz = m.radius[2], py = 2 * ry + 1, pz = 2 * rz + 1;
+    const int ry = m.sub_r[1], rz = m.sub_r[2], py = 2 * ry + 1, pz = 2 * rz + 1;
     const int wyp = match_wyp(by + 2 * ry, py), threads = round_up_i(match_units(py, pz), 32);
     const MatchLayout L2 = match_layout((int)sizeof(T), B, P, match_bx<T, B, P>(), round_up_c(B + ALIGN - 1, ALIGN),
                                         wyp, bz + 2 * rz, py, pz, false, LEV, by * bz);
@@ -1311,7 +1371,7 @@ nrr_status launch_match_variant_l(const MatchLaunch &m, cudaStream_t stream)
     constexpr int BX = match_bx<T, B, P>();
     constexpr int BTX = round_up_c(B + ALIGN - 1, ALIGN);
     const int by = launch_by(m), bz = launch_bz(m);
-    const int ry = m.radius[1], rz = m.radius[2], py = 2 * ry + 1, pz = 2 * rz + 1;
+    const int ry = m.sub_r[1], rz = m.sub_r[2], py = 2 * ry + 1, pz = 2 * rz + 1;
     const int wy = by + 2 * ry, wz = bz + 2 * rz, wyp = match_wyp(wy, py);
     const int threads = round_up_i(match_units(py, pz), 32);
     if (threads > MATCH_MAX_THREADS) return fail(NRR_E_INVALID, "search window too large");
@@ -1355,6 +1415,13 @@ nrr_status launch_match_variant_l(const MatchLaunch &m, cudaStream_t stream)
     for (int j = 0; j < MATCH_MAX_JOBS; ++j) p.jobs[j] = j < m.n_jobs ? m.jobs[j] : MatchJob{};
     p.err = m.err;
     p.wait_ns = device_wait_ns();
+    p.nsubt = 1;
+    for (int a = 0; a < 3; ++a) {
+        p.R[a] = m.radius[a];
+        p.nsub[a] = m.nsub[a];
+        p.nsubt *= m.nsub[a];
+        for (int q = 0; q < MATCH_MAX_SUB; ++q) p.soff[a][q] = q < m.nsub[a] ? m.soff[a][q] : 0;
+    }
     kern<<<(unsigned)grid, threads, L.total, stream>>>(p, mapJ, mapI);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "match kernel launch");
@@ -1395,7 +1462,7 @@ nrr_status occupancy_variant(const MatchLaunch &m, int *occ)
 template <typename T, int B>
 nrr_status launch_match_b(const MatchLaunch &m, cudaStream_t stream, int *occ)
 {
-    switch (m.radius[0]) {
+    switch (m.sub_r[0]) {
 #define NRR_CASE(r, p) \
     case r: return occ ? occupancy_variant<T, B, p>(m, occ) : launch_match_variant<T, B, p>(m, stream);
         NRR_CASE(0, 1)
@@ -1408,7 +1475,7 @@ nrr_status launch_match_b(const MatchLaunch &m, cudaStream_t stream, int *occ)
         NRR_CASE(7, 15)
 #undef NRR_CASE
     }
-    return fail(NRR_E_INVALID, "radius x %d outside 0..7", m.radius[0]);
+    return fail(NRR_E_INVALID, "sub-window radius x %d outside 0..%d", m.sub_r[0], MATCH_WINDOW_R);
 }
 
 // One entry per (element type, block size); defined in the instantiation

@@ -16,12 +16,54 @@ static nrr_status dispatch(const MatchLaunch &m, cudaStream_t stream, int *occ)
     return fail(NRR_E_INVALID, "block %d not supported", m.block);
 }
 
-nrr_status launch_match(const MatchLaunch &m, cudaStream_t stream)
+void plan_subwindows(int R, int *r, int *k, int *off)
 {
-    if (m.n_jobs < 1 || m.n_jobs > MATCH_MAX_JOBS) return fail(NRR_E_INVALID, "1..%d jobs per launch", MATCH_MAX_JOBS);
+    const int n = 2 * R + 1;
+    int kk = (n + 2 * MATCH_WINDOW_R) / (2 * MATCH_WINDOW_R + 1);  // ceil(n / 15)
+    if (kk < 1) kk = 1;
+    int len = (n + kk - 1) / kk;
+    if (!(len & 1)) ++len;
+    const int rr = (len - 1) / 2;
+    for (int i = 0; i < kk; ++i) {
+        int o = -R + rr + i * len;
+        if (o > R - rr) o = R - rr;
+        off[i] = o;
+    }
+    *r = rr;
+    *k = kk;
+}
+
+static nrr_status with_subwindows(const MatchLaunch &m0, MatchLaunch &m)
+{
+    m = m0;
+    for (int a = 0; a < 3; ++a) {
+        if (m.radius[a] < 0 || m.radius[a] > MATCH_MAX_R)
+            return fail(NRR_E_INVALID, "radius[%d]=%d outside 0..%d", a, m.radius[a], MATCH_MAX_R);
+        plan_subwindows(m.radius[a], &m.sub_r[a], &m.nsub[a], m.soff[a]);
+        if (m.nsub[a] > MATCH_MAX_SUB) return fail(NRR_E_INTERNAL, "too many sub-windows");
+    }
+    if (m.nsub[0] * m.nsub[1] * m.nsub[2] > 1)
+        for (int j = 0; j < m.n_jobs; ++j)
+            if (m.jobs[j].n_levels > 0)
+                return fail(NRR_E_INVALID, "extra radius levels need a radius of at most %d per axis", MATCH_WINDOW_R);
+    return NRR_OK;
+}
+
+nrr_status launch_match(const MatchLaunch &m0, cudaStream_t stream)
+{
+    if (m0.n_jobs < 1 || m0.n_jobs > MATCH_MAX_JOBS) return fail(NRR_E_INVALID, "1..%d jobs per launch", MATCH_MAX_JOBS);
+    MatchLaunch m;
+    nrr_status st = with_subwindows(m0, m);
+    if (st != NRR_OK) return st;
     return dispatch(m, stream, nullptr);
 }
 
-nrr_status match_occupancy(const MatchLaunch &m, int *ctas_per_sm) { return dispatch(m, nullptr, ctas_per_sm); }
+nrr_status match_occupancy(const MatchLaunch &m0, int *ctas_per_sm)
+{
+    MatchLaunch m;
+    nrr_status st = with_subwindows(m0, m);
+    if (st != NRR_OK) return st;
+    return dispatch(m, nullptr, ctas_per_sm);
+}
 
 }  // namespace nrr

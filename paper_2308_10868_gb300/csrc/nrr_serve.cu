@@ -322,7 +322,7 @@ nrr_status nrr_submit(const nrr_request *req, uint64_t *ticket)
     st = check_dims(req->dims, req->dtype, req->block);
     if (st != NRR_OK) return st;
     for (int i = 0; i < 3; ++i)
-        if (req->radius[i] < 0 || req->radius[i] > 7) return fail(NRR_E_INVALID, "radius outside 0..7");
+        if (req->radius[i] < 0 || req->radius[i] > MATCH_MAX_R) return fail(NRR_E_INVALID, "radius outside 0..%d", MATCH_MAX_R);
     if (!req->d_preop || !req->d_intraop || !req->d_mask || !req->d_select)
         return fail(NRR_E_INVALID, "NULL volume, mask or selection volume");
     std::lock_guard<std::mutex> g(g_server_mu);

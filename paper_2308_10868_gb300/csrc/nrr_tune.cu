@@ -112,7 +112,7 @@ nrr_status nrr_autotune_match(const void *d_preop, const void *d_intraop, const 
     if (!d_preop || !d_intraop || !d_boxsums || !d_centers || !d_disp || !d_ncc || !d_valid || !radius || n_blocks < 1)
         return fail(NRR_E_INVALID, "NULL buffer or no blocks to tune on");
     for (int i = 0; i < 3; ++i)
-        if (radius[i] < 0 || radius[i] > 7) return fail(NRR_E_INVALID, "radius[%d] outside 0..7", i);
+        if (radius[i] < 0 || radius[i] > MATCH_MAX_R) return fail(NRR_E_INVALID, "radius[%d] outside 0..%d", i, MATCH_MAX_R);
     cudaStream_t s = (cudaStream_t)stream;
     MatchLaunch a{};
     a.preop = d_preop;

@@ -68,9 +68,10 @@ def test_argument_checks_need_no_device(L):
         assert L.nrr_select_blocks_spaced(fake, fake, d, 7, 2, 0.1, conn, fake, 10, None, None, None) == -1
         assert b"connectivity" in L.nrr_last_error()
     assert L.nrr_select_blocks_spaced(fake, fake, d, 6, 2, 0.1, 6, fake, 10, None, None, None) == -1
-    r = (C.c_int32 * 3)(4, 8, 4)
-    assert L.nrr_block_match(fake, fake, 0, d, fake, 5, None, 7, r, fake, fake, fake, None) == -1
-    assert b"radius" in L.nrr_last_error()
+    for bad in ((4, 16, 4), (-1, 3, 3), (3, 3, 99)):  # radius 0..15 per axis
+        r = (C.c_int32 * 3)(*bad)
+        assert L.nrr_block_match(fake, fake, 0, d, fake, 5, None, 7, r, fake, fake, fake, None) == -1
+        assert b"radius" in L.nrr_last_error()
     r = (C.c_int32 * 3)(4, 4, 4)
     assert L.nrr_block_match(fake, fake, 0, d, fake, 5, None, 13, r, fake, fake, fake, None) == -1
     assert L.nrr_block_match(None, fake, 0, d, fake, 5, None, 7, r, fake, fake, fake, None) == -1

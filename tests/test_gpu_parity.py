@@ -317,3 +317,34 @@ def test_box_sums_contents(nrr, b):
     assert np.array_equal(s1.astype(np.int64), r1)
     ref_a2 = (b ** 3 * r2 - r1 * r1).astype(np.float32)
     assert np.array_equal(a2.view(np.uint32), ref_a2.view(np.uint32))
+
+
+@pytest.mark.parametrize("b,r,nb", [(7, (8, 8, 8), 160), (5, (11, 3, 9), 160), (5, (15, 15, 15), 60),
+                                    (7, (9, 0, 12), 120)])
+def test_large_radius_bit_exact(nrr, b, r, nb):
+    # Radii above 7 are searched as sub-windows (two per axis for 8..11,
+    # three for 12..15); the best over them must be the oracle's exactly.
+    pre, intra, mask = synth.workload_pair("small")
+    centers, _ = oracle.select_blocks(pre, mask, b, 2, 0.1)
+    _check_u16(nrr, pre, intra, centers[:nb], b, r)
+
+
+def test_large_radius_recovers_a_large_translation(nrr):
+    # intraop = preop shifted by t with |t| up to 14: every block whose
+    # shifted block lies in the volume returns d = t with NCC exactly 1.
+    pre, _, mask = synth.workload_pair("small")
+    t = (12, -9, 14)
+    intra = synth.translate(pre, t)
+    centers, _ = oracle.select_blocks(pre, mask, 5, 2, 0.1)
+    gd, gn, gv = _check_u16(nrr, pre, intra, centers[:200], 5, (15, 15, 15))
+    nz, ny, nx = pre.shape
+    h = 2
+    full = np.array([all(h <= c[k] + t[k] <= (nx, ny, nz)[k] - 1 - h for k in range(3)) for c in centers[:200]])
+    assert full.sum() > 20
+    assert (gd[full] == np.array(t)).all() and (gn[full] == 1.0).all()
+
+
+def test_f32_large_radius(nrr):
+    pre, intra, mask = synth.workload_pair("small")
+    centers, _ = oracle.select_blocks(pre, mask, 7, 2, 0.1)
+    _check_f32(nrr, synth.as_f32(pre), synth.as_f32(intra), centers[:100], 7, (10, 4, 13))
