@@ -248,56 +248,71 @@ def run_reference(a):
 # --------------------------------------------------------------------------
 # the GPU path
 # --------------------------------------------------------------------------
+def _events_time(fn, flush, stream, fill):
+    """Seconds between CUDA events recorded on ``stream`` around ``fn()``
+    (host gaps inside ``fn`` included), L2 flushed before; returns (s, fn())."""
+    import torch
+
+    flush.fill_(fill)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3, out
+
+
+def _plan_counts(plan, n):
+    return [int(plan.view(i)[0].item()) for i in range(n)]
+
+
 def _batched_search(a, nrr, synth, d_pre, d_intra, d_mask, w, flush):
     """The batched parameter search: 64 settings on the clinical pair, one
-    graph-captured plan (autotuned) against 64 sequential plain calls."""
+    graph-captured plan (autotuned; and the same plan with the sharing off)
+    against 64 sequential plain calls; then settings spread over four pairs
+    of different sizes in one plan against their plain calls."""
     import torch
 
     settings = synth.parameter_settings(64)
     stream = torch.cuda.current_stream()
+    reps = max(2, a.batched_reps)
 
-    def evals_of(counts):
-        return sum(n * (2 * r + 1) ** 3 for n, (b, r, f) in zip(counts, settings))
+    def evals_of(counts, sets):
+        return sum(n * (2 * r + 1) ** 3 for n, (b, r, f) in zip(counts, sets))
 
     # plain: one select (host count) + one match (own box sums) per setting
-    def plain():
+    def plain(jobs):
         counts = []
-        for b, r, f in settings:
-            c = nrr.select_blocks(d_pre, d_mask, b, 2, f)
-            nrr.block_match(d_pre, d_intra, c, b, r)
+        for (p, i, m), (b, r, f) in jobs:
+            c = nrr.select_blocks(p, m, b, 2, f)
+            nrr.block_match(p, i, c, b, r)
             counts.append(c.shape[0])
         return counts
 
-    plain()
-    torch.cuda.synchronize()
-    t_plain = []
-    for _ in range(max(2, a.batched_reps // 2)):
-        flush.fill_(3)
+    def best(fn, fill):
+        fn()
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        counts = plain()
-        torch.cuda.synchronize()
-        t_plain.append(time.perf_counter() - t0)
+        ts, out = [], None
+        for _ in range(reps):
+            t, out = _events_time(fn, flush, stream, fill)
+            ts.append(t)
+        return min(ts), out
+
+    one = [((d_pre, d_intra, d_mask), s) for s in settings]
+    tp, counts = best(lambda: plain(one), 3)
     t0 = time.perf_counter()
     plan = nrr.BatchPlan(d_pre, d_intra, d_mask, [(b, 2, r, f) for b, r, f in settings], graph=True, autotune=True)
     t_create = time.perf_counter() - t0
-    for _ in range(2):
-        plan.run()
-    torch.cuda.synchronize()
-    t_batch = []
-    for _ in range(a.batched_reps):
-        flush.fill_(5)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        plan.run()
-        e1.record(stream)
-        e1.synchronize()
-        t_batch.append(e0.elapsed_time(e1) / 1e3)
+    tb, _ = best(plan.run, 5)
     nrr.device_status()
-    bcounts = [int(plan.view(i)[0].item()) for i in range(len(settings))]
-    assert bcounts == counts, "batched and plain selections differ"
+    assert _plan_counts(plan, len(settings)) == counts, "batched and plain selections differ"
     plan.close()
-    ev = evals_of(counts)
+    nod = nrr.BatchPlan(d_pre, d_intra, d_mask, [(b, 2, r, f) for b, r, f in settings], graph=True, dedup=False)
+    tn, _ = best(nod.run, 6)
+    nrr.device_status()
+    assert _plan_counts(nod, len(settings)) == counts, "no-dedup plan and plain selections differ"
+    nod.close()
+    ev = evals_of(counts, settings)
     # work the plan actually computes: settings that differ only in the
     # fraction share the largest one's matched blocks, and a unit whose box
     # nests in a matched unit's box with no larger fraction is reported by
@@ -314,17 +329,44 @@ def _batched_search(a, nrr, synth, d_pre, d_intra, d_mask, w, flush):
         else:
             launched.append([b, r, n, f, 0])
     ev_computed = sum(n * (2 * r + 1) ** 3 for b, r, n, f, _ in launched)
-    tp, tb = min(t_plain), min(t_batch)
-    return {"workload": "clinical pair x 64 settings (block 5/7/9, radius 3..7, fraction 2..10%, stride 2)",
-            "settings": len(settings), "evals": ev, "evals_computed_by_plan": ev_computed,
-            "dedup": "settings sharing (block, stride, radius) match the largest fraction's blocks once; a "
-                     "smaller search box nested in a matched one (no larger fraction) is reported by that "
-                     "search; the others' results are gathered (nested selections)",
-            "plain_ms": 1e3 * tp, "batched_ms": 1e3 * tb, "plan_create_s": t_create,
-            "plain_registrations_per_s": len(settings) / tp, "batched_registrations_per_s": len(settings) / tb,
-            "plain_evals_per_s": ev / tp, "batched_evals_per_s": ev / tb, "speedup": tp / tb,
-            "timing": "plain: host wall clock incl. its per-setting host syncs; batched: CUDA events around one "
-                      "graph launch; best of repeats, L2 flushed before each"}
+    out = {"workload": "clinical pair x 64 settings (block 5/7/9, radius 3..7, fraction 2..10%, stride 2)",
+           "settings": len(settings), "evals": ev, "evals_computed_by_plan": ev_computed,
+           "dedup": "settings sharing (block, stride, radius) match the largest fraction's blocks once; a "
+                    "smaller search box nested in a matched one (no larger fraction) is reported by that "
+                    "search; the others' results are gathered (nested selections)",
+           "plain_ms": 1e3 * tp, "batched_ms": 1e3 * tb, "batched_no_dedup_ms": 1e3 * tn,
+           "plan_create_s": t_create,
+           "plain_registrations_per_s": len(settings) / tp, "batched_registrations_per_s": len(settings) / tb,
+           "batched_no_dedup_registrations_per_s": len(settings) / tn,
+           "plain_evals_per_s": ev / tp, "batched_evals_per_s": ev / tb, "speedup": tp / tb,
+           "speedup_no_dedup": tp / tn,
+           "timing": "every arm: CUDA events on the launching stream around the whole arm (the plain arm's "
+                     "host gaps and per-setting count reads included); best of repeats, L2 flushed before each"}
+    # several registrations of different sizes in one plan: the clinical pair
+    # and the three served sizes, 16 settings each
+    pairs = [(d_pre, d_intra, d_mask)]
+    for k in range(len(synth.SERVE_SIZES)):
+        p_, i_, m_ = synth.serve_pair(k, 0)
+        pairs.append((nrr.to_device_u16(p_), nrr.to_device_u16(i_), torch.from_numpy(m_).to(d_pre.device)))
+    msets, pof = [], []
+    for k in range(len(pairs)):
+        for s_ in synth.parameter_settings(16, seed=synth.SEED_BASE + 40 + k):
+            msets.append(s_)
+            pof.append(k)
+    jobs = [(pairs[k], s_) for k, s_ in zip(pof, msets)]
+    tpm, mcounts = best(lambda: plain(jobs), 7)
+    mplan = nrr.BatchPlan(settings=[(b, 2, r, f) for b, r, f in msets], pairs=pairs, pair_of=pof, graph=True,
+                          autotune=True)
+    tbm, _ = best(mplan.run, 8)
+    nrr.device_status()
+    assert _plan_counts(mplan, len(msets)) == mcounts, "multi-pair plan and plain selections differ"
+    mplan.close()
+    out["multi_pair"] = {
+        "workload": "4 pairs (256x256x124 clinical, 128x128x64, 192x192x96, 256x256x160) x 16 settings each",
+        "settings": len(msets), "evals": evals_of(mcounts, msets), "plain_ms": 1e3 * tpm, "batched_ms": 1e3 * tbm,
+        "plain_registrations_per_s": len(msets) / tpm, "batched_registrations_per_s": len(msets) / tbm,
+        "speedup": tpm / tbm}
+    return out
 
 
 def _serving(a, nrr, synth, dev):

@@ -340,20 +340,27 @@ nrr_status nrr_tuning_load(const char *path);
  * parameter pool of the learned predictor, both run there as separate
  * registrations).
  *
- * A plan binds one uint16 volume pair and mask (device pointers that must
- * stay valid and unchanged in place for the plan's life) and n_settings
- * settings; each setting is a full registration's hot path: selection with
- * (block, stride, frac), then matching with (block, radius).  The plan owns
- * all scratch and result memory (allocated at creation, nothing is
- * allocated when it runs).  Work shared between settings is done once: box
- * sums per distinct block size, selection per distinct (block, stride,
- * frac); matching runs as one persistent launch per distinct (block,
- * radius) holding all of that variant's settings.
+ * A plan binds one or more uint16 volume pairs with their masks (device
+ * pointers that must stay valid and unchanged in place for the plan's life;
+ * the pairs may differ in size) and n_settings settings, each on one pair;
+ * each setting is a full registration's hot path: selection with (block,
+ * stride, frac), then matching with (block, radius).  The plan owns all
+ * scratch and result memory (allocated at creation, nothing is allocated
+ * when it runs).  Work shared between settings is done once: box sums per
+ * distinct (pair, block size), selection per distinct (pair, block, stride,
+ * frac), one match of the largest fraction per (pair, block, stride,
+ * radius) with smaller fractions gathered from it, and smaller radii
+ * answered by a larger radius's search (up to radius 7 per axis).
+ * Matching runs as one persistent launch per distinct (block, radius)
+ * holding that variant's settings of every pair (up to 16 per launch).
  *
  * flags: NRR_BATCH_GRAPH captures the whole sweep into one CUDA graph at
  * creation, so nrr_batch_run is a single graph launch with no host round
  * trip; NRR_BATCH_AUTOTUNE runs the sweep once at creation and autotunes
- * every match variant on it (creation then waits for the device).
+ * every match variant on it (creation then waits for the device);
+ * NRR_BATCH_NO_DEDUP selects and matches every setting by itself (no
+ * shared selections, gathered fractions or radius levels; the results are
+ * the same bit for bit), to measure what the sharing saves.
  * nrr_batch_run enqueues one sweep on `stream` (asynchronous).  After it
  * completes, nrr_batch_view_get gives setting s's device arrays: the count
  * (device int32), centres, displacements, NCC and valid flags, each with
@@ -378,11 +385,28 @@ typedef struct {
     int32_t capacity;
 } nrr_batch_view;
 
-enum { NRR_BATCH_GRAPH = 1, NRR_BATCH_AUTOTUNE = 2 };
+enum { NRR_BATCH_GRAPH = 1, NRR_BATCH_AUTOTUNE = 2, NRR_BATCH_NO_DEDUP = 4 };
 
+/* One volume pair of a plan: uint16 reference (pre-operative) and floating
+ * (intra-operative) volumes and the mask, device, [nz][ny][nx] x-fastest,
+ * volumes 16-byte aligned, nx * 2 a multiple of 16. */
+typedef struct {
+    const uint16_t *d_preop;
+    const uint16_t *d_intraop;
+    const uint8_t *d_mask;
+    nrr_dims dims;
+} nrr_pair;
+
+/* A plan over one pair: nrr_batch_create_pairs with that single pair. */
 nrr_status nrr_batch_create(const uint16_t *d_preop, const uint16_t *d_intraop, const uint8_t *d_mask,
                             nrr_dims dims, const nrr_setting *settings, int32_t n_settings, int32_t flags,
                             nrr_batch *plan);
+/* pairs: n_pairs >= 1 entries (host, read during the call); pair_of: host
+ * [n_settings], setting s runs on pairs[pair_of[s]] (NULL: all on pair 0).
+ * Errors: NRR_E_INVALID for a bad pair, setting or pair index (the message
+ * names it). */
+nrr_status nrr_batch_create_pairs(const nrr_pair *pairs, int32_t n_pairs, const nrr_setting *settings,
+                                  const int32_t *pair_of, int32_t n_settings, int32_t flags, nrr_batch *plan);
 nrr_status nrr_batch_run(nrr_batch plan, void *stream);
 nrr_status nrr_batch_view_get(nrr_batch plan, int32_t setting, nrr_batch_view *view);
 nrr_status nrr_batch_destroy(nrr_batch plan);

@@ -1,6 +1,6 @@
 // Batched parameter search: many (block size, search radius, selection
-// fraction) settings of the registration run on one volume pair as one unit
-// of GPU work.
+// fraction) settings of the registration, on one or many volume pairs of
+// different sizes, run as one unit of GPU work.
 //
 // The paper runs such sweeps as separate registrations spread over grid or
 // cloud resources (Sec. 4.2, speculative execution with many parameter
@@ -21,14 +21,20 @@
 //     (an extra radius level of the same search), and its settings gather
 //     from those results;
 //   - one persistent match launch per distinct (block, radius), whose job
-//     table holds the matched selection of every unit of that variant (up
-//     to 16 per launch);
+//     table holds the matched selection of every unit of that variant, of
+//     every volume pair (up to 16 per launch; each job carries its pair's
+//     volumes, box sums, sizes and tensor maps, so one launch mixes
+//     registrations of different sizes);
+//   - with NRR_BATCH_NO_DEDUP every setting is selected and matched on its
+//     own (no shared selections' prefixes, no radius levels): the same
+//     results, for measuring what the sharing saves;
 //   - all of it forked over internal streams with event dependencies and
 //     captured as a single CUDA graph, so a run is one graph launch with no
 //     host round trip.
 // Results stay on the device; every setting's count, centres, displacements,
 // NCC and valid flags are reachable through nrr_batch_view_get.
 #include <stdio.h>
+#include <string.h>
 
 #include <algorithm>
 #include <map>
@@ -42,7 +48,13 @@ namespace nrr {
 namespace {
 constexpr int NSTREAMS = 8;
 
+struct PairEntry {
+    const uint16_t *preop, *intraop;
+    const uint8_t *mask;
+    nrr_dims dims;
+};
 struct SelEntry {
+    int pair, box;  // its volume pair and box sums
     int block, stride;
     double frac;
     SelectPlan plan;
@@ -53,6 +65,7 @@ struct SelEntry {
     cudaEvent_t done;
 };
 struct BoxEntry {
+    int pair;
     int block;
     void *buf;
     cudaEvent_t done;
@@ -114,6 +127,7 @@ struct Group {
     int block;
     int radius[3];
     std::vector<int> settings;
+    CUtensorMap *maps;  // device [pair][2]: window and floating-block maps of this variant
 };
 }  // namespace
 
@@ -121,10 +135,10 @@ struct Group {
 
 struct nrr_batch_s {
     int device = 0;
-    const uint16_t *preop = nullptr, *intraop = nullptr;
-    const uint8_t *mask = nullptr;
-    nrr_dims dims{};
+    std::vector<nrr::PairEntry> pairs;
+    std::vector<int> pair_of;  // per setting
     int flags = 0;
+    int64_t graph_launches = 0;
     std::vector<nrr_setting> settings;
     std::vector<nrr::SelEntry> sels;
     std::vector<nrr::BoxEntry> boxes;
@@ -158,13 +172,15 @@ static nrr_status batch_enqueue(nrr_batch_s *b, cudaStream_t s)
     int rr = 0;
     for (auto &bx : b->boxes) {
         cudaStream_t st = b->streams[rr++ % NSTREAMS];
-        nrr_status r = launch_boxsums(b->intraop, NRR_U16, b->dims, bx.block, bx.buf, st);
+        const PairEntry &pe = b->pairs[bx.pair];
+        nrr_status r = launch_boxsums(pe.intraop, NRR_U16, pe.dims, bx.block, bx.buf, st);
         if (r != NRR_OK) return r;
         NRR_CUDA_TRY(cudaEventRecord(bx.done, st));
     }
     for (auto &se : b->sels) {
         cudaStream_t st = b->streams[rr++ % NSTREAMS];
-        nrr_status r = enqueue_select(b->preop, b->mask, b->dims, se.block, se.stride, se.frac, se.centers, se.cap,
+        const PairEntry &pe = b->pairs[se.pair];
+        nrr_status r = enqueue_select(pe.preop, pe.mask, pe.dims, se.block, se.stride, se.frac, se.centers, se.cap,
                                       se.d_n, se.ws, se.plan, st);
         if (r != NRR_OK) return r;
         NRR_CUDA_TRY(cudaEventRecord(se.done, st));
@@ -185,22 +201,13 @@ static nrr_status batch_enqueue(nrr_batch_s *b, cudaStream_t s)
     });
     for (int gi : order) {
         const Group &G = b->groups[gi];
-        const BoxEntry *bx = nullptr;
-        for (auto &e : b->boxes)
-            if (e.block == G.block) bx = &e;
         std::vector<int> matched;
         for (int s_ : G.settings)
             if (b->outs[s_].src == s_) matched.push_back(s_);
         cudaStream_t st = b->streams[rr++ % NSTREAMS];  // the group's launches, then its gathers
-        NRR_CUDA_TRY(cudaStreamWaitEvent(st, bx->done, 0));
         for (size_t c0 = 0; c0 < matched.size(); c0 += MATCH_MAX_JOBS) {
             MatchLaunch a{};
-            a.preop = b->preop;
-            a.intraop = b->intraop;
-            a.s1 = bx->buf;
-            a.s2 = (const char *)bx->buf + boxsum_s2_offset(b->dims, NRR_U16);
             a.dtype = NRR_U16;
-            a.dims = b->dims;
             a.block = G.block;
             for (int i = 0; i < 3; ++i) a.radius[i] = G.radius[i];
             a.err = b->err;
@@ -208,12 +215,32 @@ static nrr_status batch_enqueue(nrr_batch_s *b, cudaStream_t s)
             for (size_t c = c0; c < matched.size() && c < c0 + MATCH_MAX_JOBS; ++c) {
                 const SettingOut &o = b->outs[matched[c]];
                 const SelEntry &se = b->sels[o.sel];
+                const PairEntry &pe = b->pairs[se.pair];
+                const BoxEntry *bx = &b->boxes[se.box];
+                NRR_CUDA_TRY(cudaStreamWaitEvent(st, bx->done, 0));
                 NRR_CUDA_TRY(cudaStreamWaitEvent(st, se.done, 0));
                 MatchJob jb{se.centers, se.d_n, se.cap, o.disp, o.ncc, o.valid};
                 jb.n_levels = (int32_t)o.levels.size();
                 for (size_t l = 0; l < o.levels.size(); ++l)
                     jb.levels[l] = MatchLevel{{o.levels[l].r[0], o.levels[l].r[1], o.levels[l].r[2]}, o.levels[l].disp,
                                               o.levels[l].ncc, o.levels[l].valid};
+                // this job's pair: volumes, box sums, sizes, tensor maps
+                jb.preop = pe.preop;
+                jb.intraop = pe.intraop;
+                jb.s1 = bx->buf;
+                jb.s2 = (const char *)bx->buf + boxsum_s2_offset(pe.dims, NRR_U16);
+                jb.nx = pe.dims.nx;
+                jb.ny = pe.dims.ny;
+                jb.nz = pe.dims.nz;
+                jb.mapJ = G.maps + 2 * se.pair;
+                jb.mapI = G.maps + 2 * se.pair + 1;
+                if (a.n_jobs == 0) {  // the launch's own maps: the first job's pair
+                    a.preop = pe.preop;
+                    a.intraop = pe.intraop;
+                    a.s1 = jb.s1;
+                    a.s2 = jb.s2;
+                    a.dims = pe.dims;
+                }
                 a.jobs[a.n_jobs++] = jb;
             }
             nrr_status r = launch_match(a, st);
@@ -230,8 +257,9 @@ static nrr_status batch_enqueue(nrr_batch_s *b, cudaStream_t s)
             const uint8_t *mv = o.lvl < 0 ? m.valid : m.levels[o.lvl].valid;
             NRR_CUDA_TRY(cudaStreamWaitEvent(st, se.done, 0));
             const int grid = (se.cap + 255) / 256;
+            const nrr_dims &dd = b->pairs[se.pair].dims;
             gather_nested_kernel<<<grid < 1 ? 1 : grid, 256, 0, st>>>(
-                se.centers, se.d_n, se.cap, sm.centers, sm.d_n, sm.cap, b->dims.nx, b->dims.ny, md, mn, mv, o.disp,
+                se.centers, se.d_n, se.cap, sm.centers, sm.d_n, sm.cap, dd.nx, dd.ny, md, mn, mv, o.disp,
                 o.ncc, o.valid, b->err);
             NRR_CUDA_TRY(cudaGetLastError());
             count_launches(1);
@@ -270,19 +298,25 @@ using namespace nrr;
 
 extern "C" {
 
-nrr_status nrr_batch_create(const uint16_t *d_preop, const uint16_t *d_intraop, const uint8_t *d_mask, nrr_dims dims,
-                            const nrr_setting *settings, int32_t n_settings, int32_t flags, nrr_batch *out)
+nrr_status nrr_batch_create_pairs(const nrr_pair *pairs, int32_t n_pairs, const nrr_setting *settings,
+                                  const int32_t *pair_of, int32_t n_settings, int32_t flags, nrr_batch *out)
 {
     clear_error();
     if (!out) return fail(NRR_E_INVALID, "out is NULL");
     *out = nullptr;
-    if (!d_preop || !d_intraop || !d_mask || !settings || n_settings < 1)
-        return fail(NRR_E_INVALID, "NULL volume/mask/settings or no settings");
-    if (((uintptr_t)d_preop & 15u) || ((uintptr_t)d_intraop & 15u))
-        return fail(NRR_E_INVALID, "volumes must be 16-byte aligned");
+    if (!pairs || n_pairs < 1 || !settings || n_settings < 1)
+        return fail(NRR_E_INVALID, "NULL pairs/settings, no pairs or no settings");
+    for (int p = 0; p < n_pairs; ++p) {
+        const nrr_pair &pe = pairs[p];
+        if (!pe.d_preop || !pe.d_intraop || !pe.d_mask) return fail(NRR_E_INVALID, "pair %d: NULL volume or mask", p);
+        if (((uintptr_t)pe.d_preop & 15u) || ((uintptr_t)pe.d_intraop & 15u))
+            return fail(NRR_E_INVALID, "pair %d: volumes must be 16-byte aligned", p);
+    }
     for (int i = 0; i < n_settings; ++i) {
         const nrr_setting &s = settings[i];
-        nrr_status st = check_select_args(dims, s.block, s.stride, s.frac);
+        const int pi = pair_of ? pair_of[i] : 0;
+        if (pi < 0 || pi >= n_pairs) return fail(NRR_E_INVALID, "setting %d: pair index %d outside 0..%d", i, pi, n_pairs - 1);
+        nrr_status st = check_select_args(pairs[pi].dims, s.block, s.stride, s.frac);
         if (st != NRR_OK) {
             char why[256];
             snprintf(why, sizeof why, "%s", nrr_last_error());
@@ -292,11 +326,11 @@ nrr_status nrr_batch_create(const uint16_t *d_preop, const uint16_t *d_intraop, 
             if (s.radius[k] < 0 || s.radius[k] > MATCH_MAX_R)
                 return fail(NRR_E_INVALID, "setting %d: radius outside 0..%d", i, MATCH_MAX_R);
     }
+    const bool dedup = !(flags & NRR_BATCH_NO_DEDUP);
     nrr_batch_s *b = new nrr_batch_s();
-    b->preop = d_preop;
-    b->intraop = d_intraop;
-    b->mask = d_mask;
-    b->dims = dims;
+    for (int p = 0; p < n_pairs; ++p)
+        b->pairs.push_back(PairEntry{pairs[p].d_preop, pairs[p].d_intraop, pairs[p].d_mask, pairs[p].dims});
+    for (int i = 0; i < n_settings; ++i) b->pair_of.push_back(pair_of ? pair_of[i] : 0);
     b->flags = flags;
     b->settings.assign(settings, settings + n_settings);
     cudaGetDevice(&b->device);
@@ -306,24 +340,30 @@ nrr_status nrr_batch_create(const uint16_t *d_preop, const uint16_t *d_intraop, 
         return r;
     };
     if (st != NRR_OK) return bail(st);
-    // distinct box-sum block sizes, selections and match variants
-    std::map<int, int> box_of;
-    std::map<std::tuple<int, int, double>, int> sel_of;
+    // distinct box sums, selections and match variants; without dedup every
+    // setting gets its own box sums, selection and match (uniq = its index)
+    std::map<std::tuple<int, int, int>, int> box_of;
+    std::map<std::tuple<int, int, int, double, int>, int> sel_of;
     std::map<std::tuple<int, int, int, int>, int> grp_of;
     for (int i = 0; i < n_settings; ++i) {
         const nrr_setting &s = settings[i];
-        if (!box_of.count(s.block)) {
-            box_of[s.block] = (int)b->boxes.size();
-            BoxEntry e{s.block, nullptr, nullptr};
+        const int pi = b->pair_of[i], uniq = dedup ? -1 : i;
+        const nrr_dims dims = b->pairs[pi].dims;
+        auto bk = std::make_tuple(pi, s.block, uniq);
+        if (!box_of.count(bk)) {
+            box_of[bk] = (int)b->boxes.size();
+            BoxEntry e{pi, s.block, nullptr, nullptr};
             if ((st = batch_alloc(b, boxsum_bytes(dims, NRR_U16), &e.buf)) != NRR_OK) return bail(st);
             if (cudaEventCreateWithFlags(&e.done, cudaEventDisableTiming) != cudaSuccess)
                 return bail(fail(NRR_E_CUDA, "event"));
             b->boxes.push_back(e);
         }
-        auto sk = std::make_tuple(s.block, s.stride, s.frac);
+        auto sk = std::make_tuple(pi, s.block, s.stride, s.frac, uniq);
         if (!sel_of.count(sk)) {
             sel_of[sk] = (int)b->sels.size();
             SelEntry e{};
+            e.pair = pi;
+            e.box = box_of[bk];
             e.block = s.block;
             e.stride = s.stride;
             e.frac = s.frac;
@@ -358,24 +398,53 @@ nrr_status nrr_batch_create(const uint16_t *d_preop, const uint16_t *d_intraop, 
             Group g;
             g.block = s.block;
             for (int k = 0; k < 3; ++k) g.radius[k] = s.radius[k];
+            g.maps = nullptr;
             b->groups.push_back(g);
         }
         b->groups[grp_of[gk]].settings.push_back(i);
     }
-    // per (block, stride, radius): the setting with the largest fraction is
-    // matched, the others gather from it (their selections are nested in it)
-    std::map<std::tuple<int, int, int, int, int>, int> unit_of;
-    for (int i = 0; i < n_settings; ++i) {
-        const nrr_setting &s = settings[i];
-        auto uk = std::make_tuple(s.block, s.stride, s.radius[0], s.radius[1], s.radius[2]);
-        auto it = unit_of.find(uk);
-        if (it == unit_of.end() || settings[it->second].frac < s.frac) unit_of[uk] = i;
+    // each match variant's tensor maps for every pair (window and
+    // floating-block boxes of that variant), encoded here once and kept on
+    // the device: the jobs of one launch read them from there
+    for (auto &G : b->groups) {
+        std::vector<CUtensorMap> maps(2 * (size_t)n_pairs);
+        memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
+        int wb[3], tb[3];
+        match_boxes(NRR_U16, G.block, G.block, G.block, G.radius, wb, tb);
+        for (int pi = 0; pi < n_pairs; ++pi) {
+            bool used = false;
+            for (int s_ : G.settings) used |= b->pair_of[s_] == pi;
+            if (!used) continue;
+            const PairEntry &pe = b->pairs[pi];
+            if ((st = encode_volume_map(&maps[2 * pi], pe.intraop, NRR_U16, pe.dims, wb[0], wb[1], wb[2])) != NRR_OK ||
+                (st = encode_volume_map(&maps[2 * pi + 1], pe.preop, NRR_U16, pe.dims, tb[0], tb[1], tb[2])) != NRR_OK)
+                return bail(st);
+        }
+        void *p;
+        if ((st = batch_alloc(b, maps.size() * sizeof(CUtensorMap), &p)) != NRR_OK) return bail(st);
+        if (cudaMemcpy(p, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(fail(NRR_E_CUDA, "tensor map copy"));
+        G.maps = (CUtensorMap *)p;
     }
-    // per (block, stride): a unit whose radius box lies in a matched unit's
-    // box and whose fraction is not larger is served by that unit's job as an
-    // extra radius level (its blocks are among the larger unit's, and the
-    // search over the larger box contains the smaller one); units are taken
-    // largest box first
+    // per (pair, block, stride, radius): the setting with the largest
+    // fraction is matched, the others gather from it (their selections are
+    // nested in it)
+    std::map<std::tuple<int, int, int, int, int, int, int>, int> unit_of;
+    auto unit_key = [&](int i) {
+        const nrr_setting &s = settings[i];
+        return std::make_tuple(b->pair_of[i], s.block, s.stride, s.radius[0], s.radius[1], s.radius[2],
+                               dedup ? -1 : i);
+    };
+    for (int i = 0; i < n_settings; ++i) {
+        auto uk = unit_key(i);
+        auto it = unit_of.find(uk);
+        if (it == unit_of.end() || settings[it->second].frac < settings[i].frac) unit_of[uk] = i;
+    }
+    // per (pair, block, stride): a unit whose radius box lies in a matched
+    // unit's box and whose fraction is not larger is served by that unit's
+    // job as an extra radius level (its blocks are among the larger unit's,
+    // and the search over the larger box contains the smaller one); units
+    // are taken largest box first
     std::vector<int> prim;
     for (auto &kv : unit_of) prim.push_back(kv.second);
     auto vol = [&](int i) {
@@ -397,8 +466,9 @@ nrr_status nrr_batch_create(const uint16_t *d_preop, const uint16_t *d_intraop, 
             // a search answers smaller boxes only while one window holds it
             const bool one_window = sa.radius[0] <= MATCH_WINDOW_R && sa.radius[1] <= MATCH_WINDOW_R &&
                                     sa.radius[2] <= MATCH_WINDOW_R;
-            if (one_window && sa.block == su.block && sa.stride == su.stride && sa.frac >= su.frac &&
-                sa.radius[0] >= su.radius[0] && sa.radius[1] >= su.radius[1] && sa.radius[2] >= su.radius[2] &&
+            if (dedup && one_window && b->pair_of[a_] == b->pair_of[u] && sa.block == su.block &&
+                sa.stride == su.stride && sa.frac >= su.frac && sa.radius[0] >= su.radius[0] &&
+                sa.radius[1] >= su.radius[1] && sa.radius[2] >= su.radius[2] &&
                 (int)b->outs[a_].levels.size() < MATCH_MAX_LEVELS) {
                 host = a_;
                 break;
@@ -420,8 +490,7 @@ nrr_status nrr_batch_create(const uint16_t *d_preop, const uint16_t *d_intraop, 
         served[u] = std::make_pair(host, (int)b->outs[host].levels.size() - 1);
     }
     for (int i = 0; i < n_settings; ++i) {
-        const nrr_setting &s = settings[i];
-        const int u = unit_of[std::make_tuple(s.block, s.stride, s.radius[0], s.radius[1], s.radius[2])];
+        const int u = unit_of[unit_key(i)];
         auto it = served.find(u);
         b->outs[i].src = it == served.end() ? u : it->second.first;
         b->outs[i].lvl = it == served.end() ? -1 : it->second.second;
@@ -452,18 +521,18 @@ nrr_status nrr_batch_create(const uint16_t *d_preop, const uint16_t *d_intraop, 
             if (cudaMemcpy(&n, se.d_n, sizeof(n), cudaMemcpyDeviceToHost) != cudaSuccess)
                 return bail(fail(NRR_E_CUDA, "count copy"));
             if (n < 1) continue;
-            const BoxEntry *bx = nullptr;
-            for (auto &e : b->boxes)
-                if (e.block == G.block) bx = &e;
-            st = nrr_autotune_match(b->preop, b->intraop, bx->buf, NRR_U16, dims, se.centers, n, G.block, G.radius,
-                                    o.disp, o.ncc, o.valid, nullptr, nullptr, b->launch);
+            const PairEntry &pe = b->pairs[se.pair];
+            st = nrr_autotune_match(pe.preop, pe.intraop, b->boxes[se.box].buf, NRR_U16, pe.dims, se.centers, n,
+                                    G.block, G.radius, o.disp, o.ncc, o.valid, nullptr, nullptr, b->launch);
             if (st != NRR_OK) return bail(st);
         }
     }
     if (flags & NRR_BATCH_GRAPH) {
         if (cudaStreamBeginCapture(b->launch, cudaStreamCaptureModeRelaxed) != cudaSuccess)
             return bail(fail(NRR_E_CUDA, "cudaStreamBeginCapture"));
+        const int64_t before = nrr_kernel_launches();
         st = batch_enqueue(b, b->launch);
+        b->graph_launches = nrr_kernel_launches() - before;  // kernels one replay runs
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(b->launch, &g);
         if (st != NRR_OK) {
@@ -479,6 +548,13 @@ nrr_status nrr_batch_create(const uint16_t *d_preop, const uint16_t *d_intraop, 
     return NRR_OK;
 }
 
+nrr_status nrr_batch_create(const uint16_t *d_preop, const uint16_t *d_intraop, const uint8_t *d_mask, nrr_dims dims,
+                            const nrr_setting *settings, int32_t n_settings, int32_t flags, nrr_batch *out)
+{
+    const nrr_pair one{d_preop, d_intraop, d_mask, dims};
+    return nrr_batch_create_pairs(&one, 1, settings, nullptr, n_settings, flags, out);
+}
+
 nrr_status nrr_batch_run(nrr_batch b, void *stream)
 {
     clear_error();
@@ -488,8 +564,7 @@ nrr_status nrr_batch_run(nrr_batch b, void *stream)
     NRR_CUDA_TRY(cudaStreamWaitEvent(b->launch, b->ev_in, 0));
     if (b->exec) {
         NRR_CUDA_TRY(cudaGraphLaunch(b->exec, b->launch));
-        count_launches((int)(b->boxes.size() + b->sels.size() * 14));
-        for (auto &G : b->groups) count_launches((int)((G.settings.size() + MATCH_MAX_JOBS - 1) / MATCH_MAX_JOBS));
+        count_launches((int)b->graph_launches);
     } else {
         nrr_status st = batch_enqueue(b, b->launch);
         if (st != NRR_OK) return st;

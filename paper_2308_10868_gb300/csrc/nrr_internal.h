@@ -105,6 +105,14 @@ struct MatchJob {
     uint8_t *valid;
     int32_t n_levels;  // 0 .. MATCH_MAX_LEVELS
     MatchLevel levels[MATCH_MAX_LEVELS];
+    // The job's volume pair (jobs of one launch may come from different
+    // registrations of different sizes): null / 0 fields take the launch's
+    // volumes, box sums and dims; mapJ / mapI are device copies of the
+    // job's tensor maps (window and floating block boxes of the launch's
+    // variant), null for the launch's own maps.
+    const void *preop, *intraop, *s1, *s2;
+    int32_t nx, ny, nz;
+    const CUtensorMap *mapJ, *mapI;
 };
 struct MatchLaunch {
     const void *preop;
@@ -133,6 +141,10 @@ struct MatchLaunch {
 // R - r): they cover [-R, R], may overlap (a shift searched twice gives the
 // same exact score), and need one window of radius r in shared memory.
 void plan_subwindows(int R, int *r, int *k, int *off);
+// TMA boxes of a match launch's variant (dtype, block edges, search radius):
+// the window box (wbox[3], x y z) and the floating-block box (tbox[3]), for
+// tensor maps a caller encodes itself (jobs with their own volumes).
+void match_boxes(nrr_dtype dtype, int block, int by, int bz, const int32_t radius[3], int wbox[3], int tbox[3]);
 nrr_status launch_match(const MatchLaunch &a, cudaStream_t stream);
 
 // Upper bound on resident match CTAs per SM for this launch's variant.

@@ -555,15 +555,16 @@ __device__ __forceinline__ void search_pair(const T *row0, int sI, int sO, const
 // the mask of the shifts whose block lies inside the volume.  The loads are
 // independent and issued together.
 template <typename T, int B, int P>
-__device__ __forceinline__ uint32_t line_boxsums(const MatchParams &a, int cx, int cy, int cz, int dyi, int dzi, int HY,
-                                                 int HZ, typename std::conditional<std::is_same<T, float>::value, float,
-                                                                                   int32_t>::type (&ps1)[P],
+__device__ __forceinline__ uint32_t line_boxsums(const MatchParams &a, const MatchJob &J, int cx, int cy, int cz,
+                                                 int dyi, int dzi, int HY, int HZ,
+                                                 typename std::conditional<std::is_same<T, float>::value, float,
+                                                                           int32_t>::type (&ps1)[P],
                                                  float (&ps2)[P])
 {
     typedef typename std::conditional<std::is_same<T, float>::value, float, int32_t>::type S1T;
     constexpr int H = (B - 1) / 2;
     constexpr int RX = (P - 1) / 2;
-    const int ny = a.ny, nz = a.nz, nx = a.nx;
+    const int ny = J.ny, nz = J.nz, nx = J.nx;
     const int Y = cy + dyi - a.ry, Z = cz + dzi - a.rz;
     const bool yz_ok = Y >= HY && Y <= ny - 1 - HY && Z >= HZ && Z <= nz - 1 - HZ;
     uint32_t vmask = 0;
@@ -575,8 +576,8 @@ __device__ __forceinline__ uint32_t line_boxsums(const MatchParams &a, int cx, i
         ps2[p] = 0.f;
         if (yz_ok && X >= H && X <= nx - 1 - H) {
             vmask |= 1u << p;
-            ps1[p] = reinterpret_cast<const S1T *>(a.s1)[rowbase + X];
-            ps2[p] = reinterpret_cast<const float *>(a.s2)[rowbase + X];
+            ps1[p] = reinterpret_cast<const S1T *>(J.s1)[rowbase + X];
+            ps2[p] = reinterpret_cast<const float *>(J.s2)[rowbase + X];
         }
     }
     return vmask;
@@ -757,7 +758,6 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
 
     const int ry = a.ry, rz = a.rz, py = 2 * ry + 1, pz = 2 * rz + 1;  // one (sub-)window
     const int wz = BZ + 2 * rz, wyp = a.wyp;
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
     // the full search box: candidate codes, displacements and levels use it
     const int Rx = a.R[0], Ry = a.R[1], Rz = a.R[2], PxF = 2 * Rx + 1, PyF = 2 * Ry + 1;
     const int nsubt = a.nsubt;
@@ -819,7 +819,8 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         while (w < n) {
             int j, i;
             locate(w, j, i);
-            if (center_inside(c0, c1, c2, nx, ny, nz, H, HY, HZ)) {
+            const MatchJob &Jw = a.jobs[j];
+            if (center_inside(c0, c1, c2, Jw.nx, Jw.ny, Jw.nz, H, HY, HZ)) {
                 sc->cen[buf][0] = c0;
                 sc->cen[buf][1] = c1;
                 sc->cen[buf][2] = c2;
@@ -856,18 +857,22 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
     // both copies of the item recorded in cen[buf] into buffer buf
     auto issue = [&](int buf) {
         const int cx = sc->cen[buf][0], cy = sc->cen[buf][1], cz = sc->cen[buf][2];
+        const MatchJob &Jb = a.jobs[sc->cen[buf][3]];
+        const CUtensorMap *mJ = Jb.mapJ ? Jb.mapJ : tmapJ, *mI = Jb.mapI ? Jb.mapI : tmapI;
         int ox, oy, oz;
         sub_off(sc->cen[buf][5], ox, oy, oz);
         const int x0 = cx + ox - H - RX, xt = cx - H;
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(bar + buf, tx_bytes);
-        tma_load_3d(smem + L.u[buf], tmapJ, bar + buf, x0 & ~(ALIGN - 1), cy + oy - HY - ry, cz + oz - HZ - rz);
-        tma_load_3d(smem + L.ut[buf], tmapI, bar + buf, xt & ~(ALIGN - 1), cy - HY, cz - HZ);
+        tma_load_3d(smem + L.u[buf], mJ, bar + buf, x0 & ~(ALIGN - 1), cy + oy - HY - ry, cz + oz - HZ - rz);
+        tma_load_3d(smem + L.ut[buf], mI, bar + buf, xt & ~(ALIGN - 1), cy - HY, cz - HZ);
     };
 
     if (tid == 0) {
         int w = 0;
         for (int j = 0; j < a.n_jobs; ++j) {
+            if (a.jobs[j].mapJ) tensormap_acquire(a.jobs[j].mapJ);
+            if (a.jobs[j].mapI) tensormap_acquire(a.jobs[j].mapI);
             sc->jstart[j] = w;
             int m = a.jobs[j].cap;
             if (a.jobs[j].d_n) {
@@ -899,6 +904,7 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         const int cx = sc->cen[b][0], cy = sc->cen[b][1], cz = sc->cen[b][2];
         const MatchJob &J = a.jobs[sc->cen[b][3]];
         const int bi = sc->cen[b][4];
+        const int nx = J.nx, ny = J.ny, nz = J.nz;  // this block's volumes
         const int si = sc->cen[b][5];  // sub-window of this item
         int x0;
         {
@@ -1078,9 +1084,9 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
             typedef typename std::conditional<F32, float, int32_t>::type S1T;
             S1T q1a[P], q1b[P];
             float q2a[P], q2b[P];
-            const uint32_t va = line_boxsums<T, B, P>(a, cx + ox, cy + oy, cz + oz, un.dy0, un.dz0, HY, HZ, q1a, q2a);
+            const uint32_t va = line_boxsums<T, B, P>(a, J, cx + ox, cy + oy, cz + oz, un.dy0, un.dz0, HY, HZ, q1a, q2a);
             const uint32_t vb =
-                un.two ? line_boxsums<T, B, P>(a, cx + ox, cy + oy, cz + oz, dy1, dz1, HY, HZ, q1b, q2b) : 0u;
+                un.two ? line_boxsums<T, B, P>(a, J, cx + ox, cy + oy, cz + oz, dy1, dz1, HY, HZ, q1b, q2b) : 0u;
             const float kq = F32 ? 0.f : sc->bu.kq, fvI = F32 ? 0.f : sc->bu.fvI, frr = F32 ? 0.f : sc->bu.frr;
             line_bounds<T, B, P, LEV>(J, nl, un.dy0, un.dz0, ry, rz, N, BY, BZ, acc0, q1a, q2a, va, kq, fvI, frr, m, tsh,
                                       bcf, GAMMA_L, ub0, lbm, lbl);
@@ -1191,8 +1197,8 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                         }
                     }
                 } else {
-                    const float *pre = reinterpret_cast<const float *>(a.preop);
-                    const float *intra = reinterpret_cast<const float *>(a.intraop);
+                    const float *pre = reinterpret_cast<const float *>(J.preop);
+                    const float *intra = reinterpret_cast<const float *>(J.intraop);
                     // float-float sums of (I - Ibar) G, G and G^2 with
                     // G = J - J0, J0 the reference block's first value: the
                     // shifted values carry the block's spread, not its mean,
@@ -1377,6 +1383,15 @@ nrr_status launch_match_variant_l(const MatchLaunch &m, cudaStream_t stream)
     if (threads > MATCH_MAX_THREADS) return fail(NRR_E_INVALID, "search window too large");
     if (wyp > 256) return fail(NRR_E_INVALID, "search window too large");
 
+    for (int j = 0; j < m.n_jobs; ++j)
+        if (m.jobs[j].mapJ || m.jobs[j].mapI) {
+            // maps a caller encoded must have this variant's boxes
+            int wb[3], tb[3];
+            match_boxes(m.dtype, m.block, by, bz, m.radius, wb, tb);
+            if (wb[0] != BX || wb[1] != wyp || wb[2] != wz || tb[0] != BTX || tb[1] != by || tb[2] != bz)
+                return fail(NRR_E_INTERNAL, "job tensor map boxes differ from the launch's");
+            break;
+        }
     CUtensorMap mapJ, mapI;
     nrr_status st = encode_volume_map(&mapJ, m.intraop, m.dtype, m.dims, BX, wyp, wz);
     if (st != NRR_OK) return st;
@@ -1412,7 +1427,19 @@ nrr_status launch_match_variant_l(const MatchLaunch &m, cudaStream_t stream)
     p.single_window = single ? 1 : 0;
     p.by = by;
     p.bz = bz;
-    for (int j = 0; j < MATCH_MAX_JOBS; ++j) p.jobs[j] = j < m.n_jobs ? m.jobs[j] : MatchJob{};
+    for (int j = 0; j < MATCH_MAX_JOBS; ++j) {
+        MatchJob jb = j < m.n_jobs ? m.jobs[j] : MatchJob{};
+        if (!jb.preop) jb.preop = m.preop;
+        if (!jb.intraop) jb.intraop = m.intraop;
+        if (!jb.s1) jb.s1 = m.s1;
+        if (!jb.s2) jb.s2 = m.s2;
+        if (!jb.nx) {
+            jb.nx = m.dims.nx;
+            jb.ny = m.dims.ny;
+            jb.nz = m.dims.nz;
+        }
+        p.jobs[j] = jb;
+    }
     p.err = m.err;
     p.wait_ns = device_wait_ns();
     p.nsubt = 1;

@@ -33,6 +33,22 @@ void plan_subwindows(int R, int *r, int *k, int *off)
     *k = kk;
 }
 
+void match_boxes(nrr_dtype dtype, int block, int by, int bz, const int32_t radius[3], int wbox[3], int tbox[3])
+{
+    int r[3], k, off[MATCH_MAX_SUB];
+    for (int a = 0; a < 3; ++a) plan_subwindows(radius[a], &r[a], &k, off);
+    const int es = (int)elem_size(dtype), epc = 16 / es;
+    const int P = 2 * r[0] + 1, py = 2 * r[1] + 1;
+    int c = (block + P - 1 + 2 * epc - 2) / epc;  // as match_bx: chunks, made odd
+    if (!(c & 1)) ++c;
+    wbox[0] = epc * c;
+    wbox[1] = match_wyp(by + 2 * r[1], py);
+    wbox[2] = bz + 2 * r[2];
+    tbox[0] = round_up_i(block + epc - 1, epc);
+    tbox[1] = by;
+    tbox[2] = bz;
+}
+
 static nrr_status with_subwindows(const MatchLaunch &m0, MatchLaunch &m)
 {
     m = m0;

@@ -87,4 +87,13 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
+// A tensor map the host wrote into global memory (rather than a kernel
+// parameter) is read by the TMA unit through the tensormap proxy: acquire it
+// once in the issuing thread before the first copy that uses it.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap *map)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+                 : "memory");
+}
+
 }  // namespace nrr

@@ -37,7 +37,11 @@ class BatchView(C.Structure):
                 ("valid", C.c_void_p), ("capacity", C.c_int32)]
 
 
-NRR_BATCH_GRAPH, NRR_BATCH_AUTOTUNE = 1, 2
+class Pair(C.Structure):
+    _fields_ = [("d_preop", C.c_void_p), ("d_intraop", C.c_void_p), ("d_mask", C.c_void_p), ("dims", Dims)]
+
+
+NRR_BATCH_GRAPH, NRR_BATCH_AUTOTUNE, NRR_BATCH_NO_DEDUP = 1, 2, 4
 
 
 class Request(C.Structure):
@@ -75,6 +79,7 @@ SIGNATURES = {
     "nrr_tuning_save": (C.c_int, [C.c_char_p]),
     "nrr_tuning_load": (C.c_int, [C.c_char_p]),
     "nrr_batch_create": (C.c_int, [_P, _P, _P, Dims, _P, _I32, _I32, _P]),
+    "nrr_batch_create_pairs": (C.c_int, [_P, _I32, _P, _P, _I32, _I32, _P]),
     "nrr_batch_run": (C.c_int, [_P, _P]),
     "nrr_batch_view_get": (C.c_int, [_P, _I32, _P]),
     "nrr_batch_destroy": (C.c_int, [_P]),
@@ -338,24 +343,39 @@ def tuning_set(dtype_code: int, block: int, radius, ctas_per_sm: int):
 
 
 class BatchPlan:
-    """A batched parameter search over one uint16 volume pair (see
-    nrr_batch_create).  ``settings`` is a list of (block, stride, radius,
-    frac) with radius an int or 3 ints."""
+    """A batched parameter search (see nrr_batch_create_pairs) over one uint16
+    volume pair (``preop, intraop, mask``) or, with ``pairs`` a list of
+    (preop, intraop, mask) and ``pair_of`` each setting's pair index, over
+    several pairs of different sizes.  ``settings`` is a list of (block,
+    stride, radius, frac) with radius an int or 3 ints."""
 
-    def __init__(self, preop, intraop, mask, settings, graph: bool = True, autotune: bool = False):
-        for t, nm in ((preop, "preop"), (intraop, "intraop"), (mask, "mask")):
-            _cuda_contig(t, nm)
-        self._keep = (preop, intraop, mask)  # the plan holds their addresses
-        self.device = preop.device
+    def __init__(self, preop=None, intraop=None, mask=None, settings=(), graph: bool = True,
+                 autotune: bool = False, dedup: bool = True, pairs=None, pair_of=None):
+        if pairs is None:
+            pairs = [(preop, intraop, mask)]
+        parr = (Pair * len(pairs))()
+        for k, (p, i, m) in enumerate(pairs):
+            for t, nm in ((p, "preop"), (i, "intraop"), (m, "mask")):
+                _cuda_contig(t, nm)
+            parr[k].d_preop, parr[k].d_intraop, parr[k].d_mask = _ptr(p), _ptr(i), _ptr(m)
+            parr[k].dims = _dims(p)
+        self._keep = list(pairs)  # the plan holds their addresses
+        self.device = pairs[0][0].device
         arr = (Setting * len(settings))()
         for i, (b, st, r, f) in enumerate(settings):
             arr[i].block, arr[i].stride, arr[i].frac = b, st, float(f)
             arr[i].radius[:] = list(radius3(r))
+        pof = None
+        if pair_of is not None:
+            if len(pair_of) != len(settings):
+                raise ValueError("pair_of needs one pair index per setting")
+            pof = (C.c_int32 * len(settings))(*[int(x) for x in pair_of])
         self.settings = list(settings)
-        flags = (NRR_BATCH_GRAPH if graph else 0) | (NRR_BATCH_AUTOTUNE if autotune else 0)
+        flags = ((NRR_BATCH_GRAPH if graph else 0) | (NRR_BATCH_AUTOTUNE if autotune else 0) |
+                 (0 if dedup else NRR_BATCH_NO_DEDUP))
         h = C.c_void_p(0)
-        _check(lib().nrr_batch_create(_ptr(preop), _ptr(intraop), _ptr(mask), _dims(preop), arr, len(settings),
-                                      flags, C.byref(h)), "nrr_batch_create")
+        _check(lib().nrr_batch_create_pairs(parr, len(pairs), arr, pof, len(settings), flags, C.byref(h)),
+               "nrr_batch_create_pairs")
         self._h = h
 
     def run(self, stream=None):

@@ -109,3 +109,20 @@ def test_serving_and_batch_arguments_need_no_device(L):
     assert L.nrr_batch_create(1 << 20, 1 << 20, 1 << 20, nrr.Dims(64, 64, 48), s, 1, 0, C.byref(h)) == -1
     assert b"setting 0" in L.nrr_last_error()
     assert L.nrr_batch_run(None, None) == -1
+    pr = (nrr.Pair * 2)()
+    for k in range(2):
+        pr[k].d_preop = pr[k].d_intraop = pr[k].d_mask = 1 << 20
+        pr[k].dims = nrr.Dims(64, 64, 48)
+    s[0].block = 7
+    s[0].stride, s[0].frac = 2, 0.1
+    bad = (C.c_int32 * 1)(2)  # pair index out of range
+    assert L.nrr_batch_create_pairs(pr, 2, s, bad, 1, 0, C.byref(h)) == -1
+    assert b"pair index" in L.nrr_last_error()
+    pr[1].d_mask = None
+    assert L.nrr_batch_create_pairs(pr, 2, s, None, 1, 0, C.byref(h)) == -1
+    assert b"pair 1" in L.nrr_last_error()
+    pr[1].d_mask, pr[1].dims = 1 << 20, nrr.Dims(60, 64, 48)  # nx * 2 not a multiple of 16
+    one = (C.c_int32 * 1)(1)
+    assert L.nrr_batch_create_pairs(pr, 2, s, one, 1, 0, C.byref(h)) == -1
+    assert b"setting 0" in L.nrr_last_error()
+    assert L.nrr_batch_create_pairs(None, 0, s, None, 1, 0, C.byref(h)) == -1

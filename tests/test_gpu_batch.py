@@ -143,3 +143,63 @@ def test_batch_smaller_radii_reported_by_the_larger_search(nrr, pair):
     c, d, n, v = [t.cpu().numpy() for t in plan.result(2)]
     assert np.array_equal(c, rc) and np.array_equal(d, rd) and np.array_equal(v, rv)
     plan.close()
+
+
+@pytest.fixture(scope="module")
+def uneven_pairs(nrr):
+    out = []
+    for k, dims in enumerate([(64, 64, 48), (96, 80, 56), (128, 96, 64)]):
+        pre, intra, mask, _ = synth.make_pair(dims, 4.0, 20.0, 500 + k)
+        out.append((pre, intra, mask, nrr.to_device_u16(pre), nrr.to_device_u16(intra), torch.from_numpy(mask).cuda()))
+    return out
+
+
+# settings spread over three pairs of different sizes: one launch per
+# (block, radius) then holds jobs of several pairs (radius 9 needs
+# sub-windows; the radius-2 settings nest in the radius-4 ones)
+MULTI = [(0, (7, 2, 3, 0.1)), (1, (7, 2, 3, 0.1)), (2, (7, 2, 3, 0.05)), (2, (7, 2, 3, 0.1)),
+         (1, (5, 2, 4, 0.08)), (1, (5, 2, 2, 0.08)), (0, (5, 2, 4, 0.1)), (2, (5, 3, (4, 2, 3), 0.06)),
+         (0, (9, 2, 9, 0.03)), (2, (9, 2, 9, 0.02)), (1, (7, 3, (2, 3, 1), 0.04))]
+
+
+@pytest.mark.parametrize("dedup", [True, False])
+def test_batch_over_uneven_pairs_equals_single_calls(nrr, uneven_pairs, dedup):
+    pairs = [(p[3], p[4], p[5]) for p in uneven_pairs]
+    settings = [s for _, s in MULTI]
+    pof = [p for p, _ in MULTI]
+    plan = nrr.BatchPlan(settings=settings, pairs=pairs, pair_of=pof, graph=True, dedup=dedup)
+    for rep in range(2):
+        plan.run()
+        torch.cuda.synchronize()
+        nrr.device_status()
+        for i, (p, s) in enumerate(MULTI):
+            got = [t.cpu().numpy() for t in plan.result(i)]
+            assert _same(got, _single(nrr, *pairs[p], s)), (dedup, rep, i, p, s)
+    # one setting per pair directly against the oracle
+    for i in (0, 4, 7):
+        p, (b, st, r, f) = MULTI[i]
+        pre, intra, mask = uneven_pairs[p][:3]
+        rc, _ = oracle.select_blocks(pre, mask, b, st, f)
+        rd, rn, rv = oracle.match(pre, intra, rc, b, r)
+        c, d, n, v = [t.cpu().numpy() for t in plan.result(i)]
+        assert np.array_equal(c, rc) and np.array_equal(d, rd) and np.array_equal(v, rv)
+        assert np.array_equal(n[~np.isnan(n)].view(np.int64), rn[~np.isnan(rn)].view(np.int64))
+    plan.close()
+
+
+def test_batch_pairs_with_and_without_dedup_agree(nrr, uneven_pairs):
+    # the sharing (nested fractions, radius levels, shared selections) must
+    # not change a bit: the same plan without it gives the same results
+    pairs = [(p[3], p[4], p[5]) for p in uneven_pairs]
+    settings = [(5, 2, r, f) for r in (1, 2, 3) for f in (0.03, 0.06)] * 3
+    pof = [k // 6 for k in range(len(settings))]
+    a = nrr.BatchPlan(settings=settings, pairs=pairs, pair_of=pof, graph=True)
+    b = nrr.BatchPlan(settings=settings, pairs=pairs, pair_of=pof, graph=False, dedup=False)
+    a.run()
+    b.run()
+    torch.cuda.synchronize()
+    nrr.device_status()
+    for i in range(len(settings)):
+        assert _same([t.cpu().numpy() for t in a.result(i)], [t.cpu().numpy() for t in b.result(i)]), i
+    a.close()
+    b.close()
