@@ -360,12 +360,22 @@ def _batched_search(a, nrr, synth, d_pre, d_intra, d_mask, w, flush):
     tbm, _ = best(mplan.run, 8)
     nrr.device_status()
     assert _plan_counts(mplan, len(msets)) == mcounts, "multi-pair plan and plain selections differ"
+    # the same plan with plain match launches (one CTA per block, no queue)
+    pplan = nrr.BatchPlan(settings=[(b, 2, r, f) for b, r, f in msets], pairs=pairs, pair_of=pof, graph=True,
+                          plain_launch=True)
+    tpl, _ = best(pplan.run, 9)
+    nrr.device_status()
+    same = all(all(torch.equal(x.view(torch.uint8), y.view(torch.uint8))
+                   for x, y in zip(mplan.result(i), pplan.result(i))) for i in range(len(msets)))
     mplan.close()
+    pplan.close()
     out["multi_pair"] = {
         "workload": "4 pairs (256x256x124 clinical, 128x128x64, 192x192x96, 256x256x160) x 16 settings each",
         "settings": len(msets), "evals": evals_of(mcounts, msets), "plain_ms": 1e3 * tpm, "batched_ms": 1e3 * tbm,
         "plain_registrations_per_s": len(msets) / tpm, "batched_registrations_per_s": len(msets) / tbm,
-        "speedup": tpm / tbm}
+        "speedup": tpm / tbm,
+        "plain_launch_batched_ms": 1e3 * tpl, "persistent_speedup_over_plain_launch": tpl / tbm,
+        "plain_launch_same_results": same}
     return out
 
 
@@ -386,19 +396,24 @@ def _serving(a, nrr, synth, dev):
         pool.append((nrr.to_device_u16(pre, dev), nrr.to_device_u16(intra, dev), torch.from_numpy(mask).to(dev)))
     torch.cuda.synchronize()
 
-    def run(reqs, slots, open_loop):
+    def run(reqs, slots, open_loop, lone=False, arrays=None):
         srv = nrr.Server(slots=slots, reserve_bytes=2 << 30)
         try:
             # warm the kernels of every variant used, outside the measurement
             t0 = time.perf_counter()
-            tickets = []
+            tickets, late = [], []
             for t_arr, si, b, r, f in reqs:
                 if open_loop:
                     dt = t_arr - (time.perf_counter() - t0)
                     if dt > 0:
                         time.sleep(dt)
                 p, i, m = pool[si]
+                # how long after its scheduled arrival the request was submitted
+                late.append(max(0.0, (time.perf_counter() - t0) - t_arr) if open_loop else 0.0)
                 tickets.append(srv.submit(p, i, m, b, 2, r, f))
+                if lone:  # each request alone on the device: its service time
+                    while srv.poll(tickets[-1]) is None:
+                        pass
             done = {}
             while len(done) < len(tickets):
                 for t in tickets:
@@ -411,17 +426,38 @@ def _serving(a, nrr, synth, dev):
         finally:
             srv.stop()
         lat = np.array([done[t][0] for t in tickets])
+        sched = lat + np.array(late)  # from the scheduled arrival
+        if arrays is not None:
+            arrays.append(sched)
+        p50, p99 = float(np.percentile(sched, 50)), float(np.percentile(sched, 99))
         return {"requests": len(tickets), "slots": slots, "wall_s": wall, "registrations_per_s": len(tickets) / wall,
-                "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-                "mean_ms": 1e3 * float(lat.mean())}
+                "p50_ms": 1e3 * p50, "p99_ms": 1e3 * p99, "p99_over_p50": p99 / p50,
+                "mean_ms": 1e3 * float(sched.mean()),
+                "from_submission_p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                "from_submission_p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                "submission_late_max_ms": 1e3 * max(late)}
 
     reqs_open = synth.poisson_arrivals(a.serve_open_requests, 20.0)
     warm = [(0.0, si, b, r, f) for (si, b, r, f) in {(q[1], q[2], q[3], q[4]) for q in reqs_open}]
     run(warm, 8, False)
     out = {"workload": "Poisson 20 req/s, volumes 128x128x64 / 192x192x96 / 256x256x160 uint16, block 5/7/9, "
                        "radius 3..7, fraction 2..10%, stride 2, volumes resident on the device",
-           "latency": "submission to completion on the device (host callback timestamp)"}
-    out["open_loop_20rps"] = run(reqs_open, 8, True)
+           "latency": "scheduled arrival to completion on the device (host callback timestamp); the "
+                      "from_submission figures leave out how late the client submitted"}
+    arr = []
+    out["open_loop_20rps"] = run(reqs_open, 8, True, arrays=arr)
+    # every request of the stream again, alone on the device: its service
+    # time.  The stream's latency spread is mostly the spread of the work
+    # (volume size x blocks x block size x search box spans two orders of
+    # magnitude); the slowdown (latency / lone service time) isolates what
+    # the serving adds
+    out["lone_service"] = run(reqs_open, 1, False, lone=True, arrays=arr)
+    slow = arr[0] / arr[1]
+    out["open_loop_20rps"].update({
+        "slowdown_p50": float(np.percentile(slow, 50)), "slowdown_p99": float(np.percentile(slow, 99)),
+        "slowdown_p99_over_p50": float(np.percentile(slow, 99) / np.percentile(slow, 50)),
+        "lone_service_p50_ms": 1e3 * float(np.percentile(arr[1], 50)),
+        "lone_service_p99_ms": 1e3 * float(np.percentile(arr[1], 99))})
     # arrival-rate sweep up to saturation (same request mix, fresh arrivals)
     sweep = {}
     for rate in (100.0, 200.0, 400.0, 800.0, 1600.0):

@@ -316,14 +316,30 @@ nrr_status nrr_block_match_bs_aniso(const void *d_preop, const void *d_intraop, 
  * Execution-configuration autotuning (Sec. 4.3: the paper tunes its GPU
  * block-matching kernel by an empirical search over thread configurations).
  *
+ * A match launch's shape: persistent CTAs per SM (0 = as many as fit),
+ * window buffers per CTA, i.e. blocks in flight (1: one window buffer and
+ * more CTAs; 2: the next block's copy overlaps this block's search; 0 = the
+ * one that fits more CTAs), and where each thread's box sums come from (0
+ * or 1: loaded at the bounds; 2: staged into shared memory by asynchronous
+ * copies while the block is searched).  No shape changes a result bit.
+ *
  * nrr_autotune_match times the match kernel for one (dtype, block, radius)
- * at every feasible number of persistent CTAs per SM on the given inputs
- * (arguments as nrr_block_match_bs, with a host block count) and stores the
- * fastest in a per-process table that every later match launch of that
- * variant uses.  It waits for `stream`.  best_ctas_per_sm and best_ms may
- * be NULL.  nrr_tuning_get/set read and write one table entry (0 = as many
- * CTAs as fit); nrr_tuning_save/load write and read the whole table as text.
+ * at every feasible shape on the given inputs (arguments as
+ * nrr_block_match_bs, with a host block count) and stores the fastest in a
+ * per-process table that every later match launch of that variant uses.
+ * It waits for `stream`.  best_ctas_per_sm and best_ms may be NULL.
+ * nrr_tuning_get/set read and write one entry's CTAs per SM (set leaves the
+ * other fields by occupancy), nrr_tuning_get_shape/set_shape the whole
+ * shape (a shape whose layout does not fit makes the launches fail with
+ * NRR_E_INVALID); nrr_tuning_save/load write and read the whole table as
+ * text.
  * ---------------------------------------------------------------------- */
+typedef struct {
+    int32_t ctas_per_sm; /* 0..64 */
+    int32_t windows;     /* 0..2 */
+    int32_t stage;       /* 0..2 */
+} nrr_match_shape;
+
 nrr_status nrr_autotune_match(const void *d_preop, const void *d_intraop, const void *d_boxsums,
                               nrr_dtype dtype, nrr_dims dims, const int32_t *d_centers, int32_t n_blocks,
                               int32_t block, const int32_t radius[3],
@@ -331,6 +347,9 @@ nrr_status nrr_autotune_match(const void *d_preop, const void *d_intraop, const 
                               int32_t *best_ctas_per_sm, float *best_ms, void *stream);
 nrr_status nrr_tuning_get(nrr_dtype dtype, int32_t block, const int32_t radius[3], int32_t *ctas_per_sm);
 nrr_status nrr_tuning_set(nrr_dtype dtype, int32_t block, const int32_t radius[3], int32_t ctas_per_sm);
+nrr_status nrr_tuning_get_shape(nrr_dtype dtype, int32_t block, const int32_t radius[3], nrr_match_shape *shape);
+nrr_status nrr_tuning_set_shape(nrr_dtype dtype, int32_t block, const int32_t radius[3],
+                                const nrr_match_shape *shape);
 nrr_status nrr_tuning_save(const char *path);
 nrr_status nrr_tuning_load(const char *path);
 
@@ -360,7 +379,9 @@ nrr_status nrr_tuning_load(const char *path);
  * every match variant on it (creation then waits for the device);
  * NRR_BATCH_NO_DEDUP selects and matches every setting by itself (no
  * shared selections, gathered fractions or radius levels; the results are
- * the same bit for bit), to measure what the sharing saves.
+ * the same bit for bit), to measure what the sharing saves;
+ * NRR_BATCH_PLAIN_LAUNCH makes every match launch one CTA per block instead
+ * of persistent CTAs that take blocks from a work queue (same results).
  * nrr_batch_run enqueues one sweep on `stream` (asynchronous).  After it
  * completes, nrr_batch_view_get gives setting s's device arrays: the count
  * (device int32), centres, displacements, NCC and valid flags, each with
@@ -385,7 +406,7 @@ typedef struct {
     int32_t capacity;
 } nrr_batch_view;
 
-enum { NRR_BATCH_GRAPH = 1, NRR_BATCH_AUTOTUNE = 2, NRR_BATCH_NO_DEDUP = 4 };
+enum { NRR_BATCH_GRAPH = 1, NRR_BATCH_AUTOTUNE = 2, NRR_BATCH_NO_DEDUP = 4, NRR_BATCH_PLAIN_LAUNCH = 8 };
 
 /* One volume pair of a plan: uint16 reference (pre-operative) and floating
  * (intra-operative) volumes and the mask, device, [nz][ny][nx] x-fastest,
@@ -418,8 +439,11 @@ nrr_status nrr_batch_destroy(nrr_batch plan);
  * nrr_server_start starts a scheduler thread on the current device with
  * `slots` CUDA streams.  nrr_submit queues one registration and returns a
  * ticket at once.  Queued requests are admitted in arrival order whenever
- * a slot is free and the device's free memory, less reserve_bytes, covers
- * the request's scratch and result buffers; admitted requests run
+ * a slot is free and the memory available, less reserve_bytes, covers the
+ * request's scratch and result buffers (available: the device's free memory
+ * plus what the library's request pool holds mapped but unused; the pool
+ * keeps the memory it maps for the rest of the process, for later requests
+ * and servers); admitted requests run
  * concurrently (their kernels overlap on the device) and a new one starts
  * as soon as an earlier one finishes.  Each request runs selection (on
  * d_select), box sums and matching exactly as the synchronous calls do, so

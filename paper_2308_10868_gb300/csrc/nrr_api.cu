@@ -51,6 +51,29 @@ nrr_status device_error_word(unsigned int **ptr)
     return NRR_OK;
 }
 
+// match work-queue heads, one 128-byte line each: the first half for
+// eager launches, the second for launches captured into CUDA graphs
+static __device__ int32_t g_match_queue[2 * MATCH_QUEUE_SLOTS * 32];
+
+nrr_status match_queue_head(int32_t **ptr, bool captured)
+{
+    static std::mutex mu;
+    static int32_t *addr[64] = {};
+    static unsigned int next[64][2] = {};
+    int dev = 0;
+    NRR_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(NRR_E_INTERNAL, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        NRR_CUDA_TRY(cudaGetSymbolAddress(&p, g_match_queue));
+        addr[dev] = (int32_t *)p;
+    }
+    const int h = captured ? 1 : 0;
+    *ptr = addr[dev] + 32 * ((size_t)h * MATCH_QUEUE_SLOTS + next[dev][h]++ % MATCH_QUEUE_SLOTS);
+    return NRR_OK;
+}
+
 static std::atomic<long long> g_launches{0};
 static std::atomic<unsigned long long> g_wait_ns{0};
 static std::atomic<unsigned int> g_missing{0};
@@ -273,7 +296,7 @@ static nrr_status match_with_boxsums(const void *d_preop, const void *d_intraop,
     for (int i = 0; i < 3; ++i) a.radius[i] = radius[i];
     a.n_jobs = 1;
     a.jobs[0] = MatchJob{d_centers, d_n_blocks, n_blocks, d_disp, d_ncc, d_valid};
-    a.ctas_per_sm = cubic && !plain ? tuned_ctas_per_sm(dtype, block[0], radius) : 0;
+    if (cubic && !plain) apply_tuning(a, dtype, block[0], radius);
     a.one_cta_per_block = plain ? 1 : 0;
     st = device_error_word(&a.err);
     if (st != NRR_OK) return st;

@@ -139,6 +139,7 @@ struct nrr_batch_s {
     std::vector<int> pair_of;  // per setting
     int flags = 0;
     int64_t graph_launches = 0;
+    int32_t *queues = nullptr;  // a work-queue head (128 bytes apart) per match launch
     std::vector<nrr_setting> settings;
     std::vector<nrr::SelEntry> sels;
     std::vector<nrr::BoxEntry> boxes;
@@ -169,7 +170,7 @@ static nrr_status batch_enqueue(nrr_batch_s *b, cudaStream_t s)
 {
     NRR_CUDA_TRY(cudaEventRecord(b->fork, s));
     for (int k = 0; k < NSTREAMS; ++k) NRR_CUDA_TRY(cudaStreamWaitEvent(b->streams[k], b->fork, 0));
-    int rr = 0;
+    int rr = 0, nq = 0;
     for (auto &bx : b->boxes) {
         cudaStream_t st = b->streams[rr++ % NSTREAMS];
         const PairEntry &pe = b->pairs[bx.pair];
@@ -211,7 +212,12 @@ static nrr_status batch_enqueue(nrr_batch_s *b, cudaStream_t s)
             a.block = G.block;
             for (int i = 0; i < 3; ++i) a.radius[i] = G.radius[i];
             a.err = b->err;
-            a.ctas_per_sm = tuned_ctas_per_sm(NRR_U16, G.block, G.radius);
+            apply_tuning(a, NRR_U16, G.block, G.radius);
+            a.queue = b->queues + 32 * nq++;  // at most one launch per setting
+            if (b->flags & NRR_BATCH_PLAIN_LAUNCH) {
+                a.one_cta_per_block = 1;
+                a.ctas_per_sm = 0;
+            }
             for (size_t c = c0; c < matched.size() && c < c0 + MATCH_MAX_JOBS; ++c) {
                 const SettingOut &o = b->outs[matched[c]];
                 const SelEntry &se = b->sels[o.sel];
@@ -402,6 +408,11 @@ nrr_status nrr_batch_create_pairs(const nrr_pair *pairs, int32_t n_pairs, const 
             b->groups.push_back(g);
         }
         b->groups[grp_of[gk]].settings.push_back(i);
+    }
+    {
+        void *p;
+        if ((st = batch_alloc(b, 128 * (size_t)n_settings, &p)) != NRR_OK) return bail(st);
+        b->queues = (int32_t *)p;
     }
     // each match variant's tensor maps for every pair (window and
     // floating-block boxes of that variant), encoded here once and kept on

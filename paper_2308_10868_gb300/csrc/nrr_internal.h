@@ -24,6 +24,10 @@ void clear_error();
 // Returns its device address for the current device (no allocation: it is a
 // file-scope __device__ variable of the library).
 nrr_status device_error_word(unsigned int **ptr);
+// Next match work-queue head of this device's eager or captured ring (see
+// MatchLaunch::queue).
+constexpr int MATCH_QUEUE_SLOTS = 4096;
+nrr_status match_queue_head(int32_t **ptr, bool captured);
 
 // Bits of the device error word.
 enum : unsigned int { DEV_ERR_TIMEOUT = 1u, DEV_ERR_INTERNAL = 2u };
@@ -128,7 +132,15 @@ struct MatchLaunch {
     MatchJob jobs[MATCH_MAX_JOBS];
     int ctas_per_sm;  // persistent CTAs per SM; 0 = as many as fit
     int one_cta_per_block;  // plain launch: one CTA per block instead of persistent CTAs
+    int stage_boxsums;      // 0 or 1 = load the box sums at the bounds, 2 = stage them
+    int windows;            // window buffers: 0 = by occupancy, 1 or 2
     unsigned int *err;
+    // work-queue head (device int32) the launcher zeroes on the stream before
+    // the kernel; null: the next head of a per-device ring, one ring for
+    // eager launches (distinct while fewer than MATCH_QUEUE_SLOTS of them are
+    // in flight at once) and one for launches captured into CUDA graphs
+    // (distinct while fewer than MATCH_QUEUE_SLOTS captured launches live)
+    int32_t *queue;
     // filled in by launch_match: sub-windows of radius sub_r per axis that
     // tile [-radius, radius] (one of radius `radius` when it is at most
     // MATCH_WINDOW_R), nsub per axis centred at soff
@@ -151,7 +163,9 @@ nrr_status launch_match(const MatchLaunch &a, cudaStream_t stream);
 nrr_status match_occupancy(const MatchLaunch &a, int *ctas_per_sm);
 
 // Autotuned persistent CTAs per SM for a match variant (0 = as many as fit).
-int tuned_ctas_per_sm(nrr_dtype dtype, int block, const int32_t *radius);
+// The tuned launch shape of a (dtype, block, radius) variant, written into
+// a launch (CTAs per SM, window buffers, box-sum staging).
+void apply_tuning(MatchLaunch &a, nrr_dtype dtype, int block, const int32_t *radius);
 
 // Autotuner entry used by the batch plan (C ABI function).
 // Block selection on caller-provided scratch (no allocation, no host sync).

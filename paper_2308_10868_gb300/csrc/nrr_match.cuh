@@ -81,6 +81,12 @@ struct MatchParams {
     int nsub[3];
     int soff[3][MATCH_MAX_SUB];
     int nsubt;  // nsub[0] * nsub[1] * nsub[2]
+    // Work queue: CTA k starts with item k; further items (gridDim.x, ...)
+    // are taken from this head, zero when the launch starts.
+    int32_t *queue;
+    // box sums of each thread's lines staged in shared memory by
+    // asynchronous copies issued at the block's start
+    int stage;
 };
 
 constexpr int MATCH_MAX_THREADS = 256;
@@ -169,14 +175,17 @@ __host__ __device__ inline int match_wyp(int wy, int py)
 }
 
 struct MatchLayout {
-    int u[2], ut[2], t, sc, lsc, bar, total;
+    int u[2], ut[2], t, sc, lsc, bs, bar, total;
 };
 
 // Shared-memory carve-up of one CTA (all offsets 128-byte aligned).  With
 // single_window the two blocks in flight share one window buffer (their
-// floating blocks stay double-buffered); `levels` adds the level scratch.
+// floating blocks stay double-buffered); `levels` adds the level scratch;
+// `stage` adds each thread's box sums of its two lines (4 P words a thread,
+// interleaved over the `threads` threads).
 __host__ __device__ inline MatchLayout match_layout(int elem, int B, int P, int bx, int btx, int wyp, int wz, int py,
-                                                   int pz, bool single_window, bool levels, int brows)
+                                                   int pz, bool single_window, bool levels, int brows, bool stage,
+                                                   int threads)
 {
     // brows: rows of the floating block (by * bz)
     (void)P;
@@ -200,6 +209,8 @@ __host__ __device__ inline MatchLayout match_layout(int elem, int B, int P, int 
     o += round_up_i((int)sizeof(MatchScratch), 128);
     L.lsc = o;
     if (levels) o += round_up_i((int)sizeof(MatchLevelScratch), 128);
+    L.bs = o;
+    if (stage) o += round_up_i(4 * P * threads * 4, 128);
     L.bar = o;
     o += 128;
     L.total = o;
@@ -583,15 +594,57 @@ __device__ __forceinline__ uint32_t line_boxsums(const MatchParams &a, const Mat
     return vmask;
 }
 
+// The same mask without the loads, and the loads as 4-byte asynchronous
+// copies into this thread's staging words (s1 at dst1 + 4 p stride, s2 at
+// dst2 + 4 p stride; shifts outside the volume are zero-filled without a
+// read), issued as one group at the block's start and waited for before
+// the bounds.
+template <int B, int P>
+__device__ __forceinline__ uint32_t line_vmask(const MatchParams &a, const MatchJob &J, int cx, int cy, int cz,
+                                               int dyi, int dzi, int HY, int HZ)
+{
+    constexpr int H = (B - 1) / 2;
+    constexpr int RX = (P - 1) / 2;
+    const int Y = cy + dyi - a.ry, Z = cz + dzi - a.rz;
+    if (!(Y >= HY && Y <= J.ny - 1 - HY && Z >= HZ && Z <= J.nz - 1 - HZ)) return 0u;
+    uint32_t vmask = 0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int X = cx + p - RX;
+        if (X >= H && X <= J.nx - 1 - H) vmask |= 1u << p;
+    }
+    return vmask;
+}
+// Index of the box sum of shift (x0 + p, cy + dy, cz + dz) less p.
+__device__ __forceinline__ long long line_row(const MatchJob &J, int x0, int cy, int cz, int dy, int dz)
+{
+    return ((long long)(cz + dz) * J.ny + (cy + dy)) * J.nx + x0;
+}
+template <int B, int P>
+__device__ __forceinline__ void line_boxsums_async(const MatchParams &a, const MatchJob &J, int cx, int cy, int cz,
+                                                   int dyi, int dzi, int HY, int HZ, uint32_t dst1, uint32_t dst2,
+                                                   uint32_t stride)
+{
+    constexpr int RX = (P - 1) / 2;
+    const uint32_t vmask = line_vmask<B, P>(a, J, cx, cy, cz, dyi, dzi, HY, HZ);
+    const int Y = cy + dyi - a.ry, Z = cz + dzi - a.rz;
+    const long long rowbase = vmask ? ((long long)Z * J.ny + Y) * J.nx + cx - RX : 0;
+    const uint32_t *s1 = reinterpret_cast<const uint32_t *>(J.s1), *s2 = reinterpret_cast<const uint32_t *>(J.s2);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const bool ok = (vmask >> p) & 1u;
+        cp_async_4(dst1 + 4u * p * stride, ok ? s1 + rowbase + p : s1, ok ? 4u : 0u);
+        cp_async_4(dst2 + 4u * p * stride, ok ? s2 + rowbase + p : s2, ok ? 4u : 0u);
+    }
+}
+
 // Approximate NCC of every x-shift of one line, with a rigorous bound on its
 // error (see the header comment); ub[p] = v + e and the best lower bound
 // v - e of the line (and of each level box holding it).
-template <typename T, int B, int P, bool LEV>
+template <typename T, int B, int P, bool LEV, class G1, class G2>
 __device__ __forceinline__ void line_bounds(const MatchJob &J, int nl, int dyi, int dzi, int ry, int rz, int N, int BY,
-                                            int BZ, const float (&acc)[P],
-                                            const typename std::conditional<std::is_same<T, float>::value, float,
-                                                                            int32_t>::type (&ps1)[P],
-                                            const float (&ps2)[P], uint32_t vmask, float kq, float fvI, float frr,
+                                            int BZ, const float (&acc)[P], G1 ps1, G2 ps2, uint32_t vmask, float kq,
+                                            float fvI, float frr,
                                             int m, float c_f, const BlockConstF &bcf, double GAMMA_L, float (&ub)[P],
                                             float &lbm, float (&lbl)[MATCH_MAX_LEVELS])
 {
@@ -617,9 +670,9 @@ __device__ __forceinline__ void line_bounds(const MatchJob &J, int nl, int dyi, 
             // float conversion issues on the FP64 pipe, which is narrow on
             // this part.  v_J arrives rounded once (zero only for a flat
             // block); S_J rounds at most once.
-            const float vjf = ps2[p];
+            const float vjf = ps2(p);
             if (!(vjf > 0.f)) continue;  // flat reference block
-            const float s1f = (float)(ps1[p] - N * m);  // S'_J = sum (J - m), exact before the rounding
+            const float s1f = (float)(ps1(p) - N * m);  // S'_J = sum (J - m), exact before the rounding
             // sum (J - m)^2 = (v_J + S'_J^2) / N, rounded up: the rounded v_J
             // and S'_J and three operations stay below 6u
             const float s2u = __fmul_rn(__fmul_rn(__fmaf_rn(s1f, s1f, vjf), 1.0f / fN), 1.f + 16.f * U32);
@@ -642,8 +695,8 @@ __device__ __forceinline__ void line_bounds(const MatchJob &J, int nl, int dyi, 
             const float GS = (float)((B + BY + BZ) * 5.9604644775390625e-08 /
                                      (1.0 - (B + BY + BZ) * 5.9604644775390625e-08));  // box-sum depth
             const float GN = (float)GAMMA_L;
-            const float s1 = ps1[p];
-            const float s2 = fmaxf(ps2[p], 0.f);
+            const float s1 = ps1(p);
+            const float s2 = fmaxf(ps2(p), 0.f);
             // every operation below is rounded on its own (no contraction)
             float d1;  // |S1 err| bound (the factor 1.01 covers sqrt.approx)
             asm("sqrt.approx.f32 %0, %1;" : "=f"(d1) : "f"(__fmul_rn(fN, s2)));
@@ -774,7 +827,8 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
 
     extern __shared__ __align__(128) unsigned char smem[];
     const MatchLayout L =
-        match_layout((int)sizeof(T), B, P, BX, BTX, wyp, wz, py, pz, a.single_window != 0, LEV, NROW);
+        match_layout((int)sizeof(T), B, P, BX, BTX, wyp, wz, py, pz, a.single_window != 0, LEV, NROW, a.stage != 0,
+                     (int)blockDim.x);
     const bool single = a.single_window != 0;
     float *Ts = reinterpret_cast<float *>(smem + L.t);
     MatchScratch *sc = reinterpret_cast<MatchScratch *>(smem + L.sc);
@@ -795,24 +849,24 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         while (j + 1 < a.n_jobs && w >= sc->jstart[j + 1]) ++j;
         i = w - sc->jstart[j];
     };
-    // The candidate work item after a block is the one gridDim.x further on;
-    // its centre is loaded one block ahead (pf, pfx..) so that the load's
-    // latency is hidden behind a whole block.
-    int pf = 0, pfx = 0, pfy = 0, pfz = 0;
-    auto prefetch = [&](int w, int n) {
-        pf = w;
-        if (w < n) {
-            int j, i;
-            locate(w, j, i);
-            const int32_t *c = a.jobs[j].centers + 3 * i;
-            pfx = c[0];
-            pfy = c[1];
-            pfz = c[2];
-        }
+    // Work items come from a queue: the next candidate (pf) has its centre
+    // loaded a block ahead (pfx..), and the one after it (qn) was taken from
+    // the queue head a block before it is needed, so neither the atomic's
+    // nor the load's latency is waited on.  A CTA takes increasing indices,
+    // so once a candidate is past the end every later one is too.
+    int pf = 0, pfx = 0, pfy = 0, pfz = 0, qn = 0;
+    auto take = [&]() { return (int)gridDim.x + atomicAdd(a.queue, 1); };
+    auto centre = [&](int w, int &c0, int &c1, int &c2) {
+        int j, i;
+        locate(w, j, i);
+        const int32_t *c = a.jobs[j].centers + 3 * i;
+        c0 = c[0];
+        c1 = c[1];
+        c2 = c[2];
     };
-    // next work item at or after the prefetched candidate whose centre is
-    // inside; the skipped ones are reported invalid.  Records its centre in
-    // cen[buf] and prefetches the candidate after it.
+    // next work item whose centre is inside, from the candidate on (the
+    // skipped ones are reported invalid).  Records its centre in cen[buf]
+    // and moves the queue one item on.
     auto advance = [&](int n, int buf) {
         int w = pf;
         int c0 = pfx, c1 = pfy, c2 = pfz;
@@ -830,18 +884,21 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                 break;
             }
             write_invalid(a.jobs[j], i, PxF, PyF, Rx, Ry, Rz);
-            w += gridDim.x;
-            if (w < n) {
-                int j2, i2;
-                locate(w, j2, i2);
-                const int32_t *c = a.jobs[j2].centers + 3 * i2;
-                c0 = c[0];
-                c1 = c[1];
-                c2 = c[2];
+            if (qn >= n) {
+                w = n;
+                break;
             }
+            w = qn;  // skipped: the next candidate at once
+            qn = take();
+            centre(w, c0, c1, c2);
         }
-        prefetch(w + gridDim.x, n);
-        return w < n ? w : n;
+        if (w >= n) return n;
+        pf = qn;
+        if (pf < n) {
+            centre(pf, pfx, pfy, pfz);
+            qn = take();
+        }
+        return w;
     };
     // the next item: the block's next sub-window, else the next block
     auto next_item = [&](int n, int buf, int cur_blk, int cur_s, int &ns) {
@@ -885,7 +942,9 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         mbar_init(bar + 0, 1);
         mbar_init(bar + 1, 1);
         fence_mbar_init();
-        prefetch(blockIdx.x, w);
+        pf = blockIdx.x;
+        if (pf < w) centre(pf, pfx, pfy, pfz);
+        qn = take();
         const int first = advance(w, 0);
         sc->nb[1] = first;  // the loop starts with buffer 0 holding `first`
         sc->ns[1] = 0;
@@ -914,6 +973,18 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         }
         const int xo = x0 - (x0 & ~(ALIGN - 1));
         const int xt = cx - H, xot = xt - (xt & ~(ALIGN - 1));
+        // this thread's box sums of the item, copied while it searches
+        const uint32_t bs_base = smem_addr(smem + L.bs) + 4u * (uint32_t)tid, bs_str = (uint32_t)nthr;
+        if (a.stage && has_unit) {
+            int ox, oy, oz;
+            sub_off(si, ox, oy, oz);
+            line_boxsums_async<B, P>(a, J, cx + ox, cy + oy, cz + oz, un.dy0, un.dz0, HY, HZ, bs_base,
+                                     bs_base + 4u * P * bs_str, bs_str);
+            if (un.two)
+                line_boxsums_async<B, P>(a, J, cx + ox, cy + oy, cz + oz, dy1, dz1, HY, HZ, bs_base + 8u * P * bs_str,
+                                         bs_base + 12u * P * bs_str, bs_str);
+            cp_async_commit();
+        }
 
         const bool got = mbar_wait_bounded(bar + b, phase[b], a.wait_ns);
         phase[b] ^= 1u;
@@ -1039,6 +1110,7 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
             // let an in-flight copy land before exiting (the full limit:
             // a copy into this CTA's shared memory must not outlive it)
             mbar_wait_bounded(bar + b, phase[b] ^ 1u, DEVICE_WAIT_NS);
+            cp_async_wait_all();
             return;
         }
         const int nb = sc->nb[b];
@@ -1047,6 +1119,7 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         if (flat) {  // flat floating block: NCC undefined for every shift
             if (single && nb < n && tid == 0) issue(b ^ 1);  // the window is not read
             if (tid == 0) write_invalid(J, bi, PxF, PyF, Rx, Ry, Rz);
+            cp_async_wait_all();  // the next item's copies reuse the staging words
             blk = nb;
             ++i;
             continue;
@@ -1076,23 +1149,45 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
             // subnormal m * 2^-149, whose bits are m)
             const float csh = F32 ? tsh : __uint_as_float((uint32_t)m);
             search_pair<T, B, P>(row0, sI, sO, Ts, tI, tO, bI, bO, csh, acc0, acc1);
-            // both lines' box sums first (one L2 round trip), then the bounds;
             // the sub-window offset is read again (no registers held across
             // the search)
             int ox, oy, oz;
             sub_off(sc->cen[b][5], ox, oy, oz);
             typedef typename std::conditional<F32, float, int32_t>::type S1T;
-            S1T q1a[P], q1b[P];
-            float q2a[P], q2b[P];
-            const uint32_t va = line_boxsums<T, B, P>(a, J, cx + ox, cy + oy, cz + oz, un.dy0, un.dz0, HY, HZ, q1a, q2a);
-            const uint32_t vb =
-                un.two ? line_boxsums<T, B, P>(a, J, cx + ox, cy + oy, cz + oz, dy1, dz1, HY, HZ, q1b, q2b) : 0u;
             const float kq = F32 ? 0.f : sc->bu.kq, fvI = F32 ? 0.f : sc->bu.fvI, frr = F32 ? 0.f : sc->bu.frr;
-            line_bounds<T, B, P, LEV>(J, nl, un.dy0, un.dz0, ry, rz, N, BY, BZ, acc0, q1a, q2a, va, kq, fvI, frr, m, tsh,
-                                      bcf, GAMMA_L, ub0, lbm, lbl);
-            if (un.two)
-                line_bounds<T, B, P, LEV>(J, nl, dy1, dz1, ry, rz, N, BY, BZ, acc1, q1b, q2b, vb, kq, fvI, frr, m, tsh,
-                                          bcf, GAMMA_L, ub1, lbm, lbl);
+            if (a.stage) {
+                // the staged box sums (this thread's own copies)
+                const uint32_t va = line_vmask<B, P>(a, J, cx + ox, cy + oy, cz + oz, un.dy0, un.dz0, HY, HZ);
+                const uint32_t vb = un.two ? line_vmask<B, P>(a, J, cx + ox, cy + oy, cz + oz, dy1, dz1, HY, HZ) : 0u;
+                cp_async_wait_all();
+                const S1T *st1 = reinterpret_cast<const S1T *>(smem + L.bs) + tid;
+                const float *st2 = reinterpret_cast<const float *>(smem + L.bs) + tid;
+                const int q = nthr * P;
+                line_bounds<T, B, P, LEV>(
+                    J, nl, un.dy0, un.dz0, ry, rz, N, BY, BZ, acc0, [&](int p) { return st1[p * nthr]; },
+                    [&](int p) { return st2[q + p * nthr]; }, va, kq, fvI, frr, m, tsh, bcf, GAMMA_L, ub0, lbm, lbl);
+                if (un.two)
+                    line_bounds<T, B, P, LEV>(
+                        J, nl, dy1, dz1, ry, rz, N, BY, BZ, acc1, [&](int p) { return st1[2 * q + p * nthr]; },
+                        [&](int p) { return st2[3 * q + p * nthr]; }, vb, kq, fvI, frr, m, tsh, bcf,
+                        GAMMA_L, ub1, lbm, lbl);
+            } else {
+                // the box sums straight from global memory, in the bounds loop
+                const uint32_t va = line_vmask<B, P>(a, J, cx + ox, cy + oy, cz + oz, un.dy0, un.dz0, HY, HZ);
+                const uint32_t vb = un.two ? line_vmask<B, P>(a, J, cx + ox, cy + oy, cz + oz, dy1, dz1, HY, HZ) : 0u;
+                const S1T *g1 = reinterpret_cast<const S1T *>(J.s1);
+                const float *g2 = reinterpret_cast<const float *>(J.s2);
+                const long long ra = va ? line_row(J, cx + ox - RX, cy + oy, cz + oz, un.dy0 - ry, un.dz0 - rz) : 0;
+                line_bounds<T, B, P, LEV>(J, nl, un.dy0, un.dz0, ry, rz, N, BY, BZ, acc0,
+                                          [&](int p) { return g1[ra + p]; }, [&](int p) { return g2[ra + p]; }, va,
+                                          kq, fvI, frr, m, tsh, bcf, GAMMA_L, ub0, lbm, lbl);
+                if (un.two) {
+                    const long long rb = vb ? line_row(J, cx + ox - RX, cy + oy, cz + oz, dy1 - ry, dz1 - rz) : 0;
+                    line_bounds<T, B, P, LEV>(J, nl, dy1, dz1, ry, rz, N, BY, BZ, acc1,
+                                              [&](int p) { return g1[rb + p]; }, [&](int p) { return g2[rb + p]; },
+                                              vb, kq, fvI, frr, m, tsh, bcf, GAMMA_L, ub1, lbm, lbl);
+                }
+            }
         }
 
         // ---- best lower bound over the window ------------------------------
@@ -1299,15 +1394,16 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
 }
 
 // Host side: launch one (element type, block size, x-shift count) variant.
-// Register budget: 128 per thread.  A CTA holds one or two warps per
-// (2 * radius + 1) x-shift lines of 11 or fewer, so registers allow eight
-// or more CTAs per SM; shared memory limits them first.
-template <int B, int P>
+// Register budget per thread: what two lines of P x-shifts (search sums,
+// then bounds) need without spilling, so that small CTAs (two warps for
+// lines of 11 or fewer) fit nine or more to an SM: uint16 blocks up to 7
+// take 104 up to 9 shifts and 112 for 11; everything else 128.
+template <bool F32, int B, int P>
 struct MatchRegs {
-    static constexpr int value = 128;
+    static constexpr int value = !F32 && B <= 7 ? (P <= 9 ? 104 : P <= 11 ? 112 : 128) : 128;
 };
 template <int B, int P, bool LEV, bool ANI>
-__global__ void __maxnreg__((MatchRegs<B, P>::value))
+__global__ void __maxnreg__((MatchRegs<false, B, P>::value))
     match_kernel_u16(const __grid_constant__ MatchParams a, const __grid_constant__ CUtensorMap tmapJ,
                      const __grid_constant__ CUtensorMap tmapI)
 {
@@ -1315,7 +1411,7 @@ __global__ void __maxnreg__((MatchRegs<B, P>::value))
 }
 
 template <int B, int P, bool ANI>
-__global__ void __maxnreg__((MatchRegs<B, P>::value))
+__global__ void __maxnreg__((MatchRegs<true, B, P>::value))
     match_kernel_f32(const __grid_constant__ MatchParams a, const __grid_constant__ CUtensorMap tmapJ,
                      const __grid_constant__ CUtensorMap tmapI)
 {
@@ -1341,32 +1437,53 @@ inline int launch_by(const MatchLaunch &m) { return m.block_y > 0 ? m.block_y : 
 inline int launch_bz(const MatchLaunch &m) { return m.block_z > 0 ? m.block_z : m.block; }
 
 template <typename T, int B, int P, bool LEV, bool ANI>
-nrr_status choose_layout(const MatchLaunch &m, MatchLayout *L, bool *single, int *occ)
+nrr_status choose_layout(const MatchLaunch &m, MatchLayout *L, bool *single, bool *stage, int *occ)
 {
     constexpr int ALIGN = 16 / (int)sizeof(T);
     const int by = launch_by(m), bz = launch_bz(m);
     const int ry = m.sub_r[1], rz = m.sub_r[2], py = 2 * ry + 1, pz = 2 * rz + 1;
     const int wyp = match_wyp(by + 2 * ry, py), threads = round_up_i(match_units(py, pz), 32);
-    const MatchLayout L2 = match_layout((int)sizeof(T), B, P, match_bx<T, B, P>(), round_up_c(B + ALIGN - 1, ALIGN),
-                                        wyp, bz + 2 * rz, py, pz, false, LEV, by * bz);
-    const MatchLayout L1 = match_layout((int)sizeof(T), B, P, match_bx<T, B, P>(), round_up_c(B + ALIGN - 1, ALIGN),
-                                        wyp, bz + 2 * rz, py, pz, true, LEV, by * bz);
+    // [stage][single]: box sums staged or loaded at the bounds, two window
+    // buffers or one
+    MatchLayout Ls[2][2];
+    int most = 0;
+    for (int st = 0; st < 2; ++st)
+        for (int sw = 0; sw < 2; ++sw) {
+            Ls[st][sw] = match_layout((int)sizeof(T), B, P, match_bx<T, B, P>(), round_up_c(B + ALIGN - 1, ALIGN), wyp,
+                                      bz + 2 * rz, py, pz, sw != 0, LEV, by * bz, st != 0, threads);
+            most = Ls[st][sw].total > most ? Ls[st][sw].total : most;
+        }
     auto kern = match_kernel_ptr<T, B, P, LEV, ANI>();
     static int smem_set = 0;  // largest dynamic shared memory opted in so far
-    if (L2.total > smem_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L2.total);
+    if (most > smem_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(match_kernel)");
-        smem_set = L2.total;
+        smem_set = most;
     }
-    int o2 = 0, o1 = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, kern, threads, L2.total);
-    if (e == cudaSuccess && o2 <= 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, kern, threads, L1.total);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    *single = o2 <= 3 && o1 > o2;
-    *L = *single ? L1 : L2;
-    *occ = *single ? o1 : o2;
+    int o[2][2];
+    for (int st = 0; st < 2; ++st)
+        for (int sw = 0; sw < 2; ++sw) {
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[st][sw], kern, threads, Ls[st][sw].total);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        }
+    // one window buffer where it fits more CTAs on an SM than two (measured:
+    // more resident CTAs beat the overlap of the next block's copy), or as
+    // asked
+    bool sw1[2];
+    for (int st = 0; st < 2; ++st) {
+        sw1[st] = o[st][1] > o[st][0];
+        if (m.windows == 1) sw1[st] = true;
+        if (m.windows == 2) sw1[st] = false;
+    }
+    // box sums loaded at the bounds unless staging is asked for (measured:
+    // staging wins only at one or two CTAs per SM)
+    const bool stg = m.stage_boxsums == 2;
+    *stage = stg;
+    *single = sw1[stg];
+    *L = Ls[stg][sw1[stg]];
+    *occ = o[stg][sw1[stg]];
     return NRR_OK;
 }
 
@@ -1402,7 +1519,8 @@ nrr_status launch_match_variant_l(const MatchLaunch &m, cudaStream_t stream)
     MatchLayout L;
     bool single = false;
     int occ = 0;
-    st = choose_layout<T, B, P, LEV, ANI>(m, &L, &single, &occ);
+    bool stage = false;
+    st = choose_layout<T, B, P, LEV, ANI>(m, &L, &single, &stage, &occ);
     if (st != NRR_OK) return st;
     if (occ < 1) return fail(NRR_E_INVALID, "match kernel does not fit on an SM (%d B shared)", L.total);
     if (m.ctas_per_sm > 0 && m.ctas_per_sm < occ) occ = m.ctas_per_sm;
@@ -1425,6 +1543,7 @@ nrr_status launch_match_variant_l(const MatchLaunch &m, cudaStream_t stream)
     p.wyp = wyp;
     p.n_jobs = m.n_jobs;
     p.single_window = single ? 1 : 0;
+    p.stage = stage ? 1 : 0;
     p.by = by;
     p.bz = bz;
     for (int j = 0; j < MATCH_MAX_JOBS; ++j) {
@@ -1449,6 +1568,13 @@ nrr_status launch_match_variant_l(const MatchLaunch &m, cudaStream_t stream)
         p.nsubt *= m.nsub[a];
         for (int q = 0; q < MATCH_MAX_SUB; ++q) p.soff[a][q] = q < m.nsub[a] ? m.soff[a][q] : 0;
     }
+    p.queue = m.queue;
+    if (!p.queue) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        NRR_CUDA_TRY(cudaStreamIsCapturing(stream, &cs));
+        if ((st = match_queue_head(&p.queue, cs != cudaStreamCaptureStatusNone)) != NRR_OK) return st;
+    }
+    NRR_CUDA_TRY(cudaMemsetAsync(p.queue, 0, sizeof(int32_t), stream));
     kern<<<(unsigned)grid, threads, L.total, stream>>>(p, mapJ, mapI);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "match kernel launch");
@@ -1482,8 +1608,9 @@ nrr_status occupancy_variant(const MatchLaunch &m, int *occ)
 {
     MatchLayout L;
     bool single = false;
-    if (launch_by(m) != B || launch_bz(m) != B) return choose_layout<T, B, P, false, true>(m, &L, &single, occ);
-    return choose_layout<T, B, P, false, false>(m, &L, &single, occ);
+    bool stage = false;
+    if (launch_by(m) != B || launch_bz(m) != B) return choose_layout<T, B, P, false, true>(m, &L, &single, &stage, occ);
+    return choose_layout<T, B, P, false, false>(m, &L, &single, &stage, occ);
 }
 
 template <typename T, int B>

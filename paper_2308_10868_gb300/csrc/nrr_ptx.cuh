@@ -87,6 +87,44 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
+// Grid-wide barrier number `index` (0, 1, ...) of a cooperative launch
+// (every CTA resident): every CTA adds one arrival
+// and waits for (index + 1) * (gridDim.x + missing) of them (missing: 0, or
+// arrivals a test adds that never come).  Returns false if the wait ran out
+// of time.
+__device__ __forceinline__ bool grid_barrier(unsigned int *arrive, unsigned int index, uint64_t limit_ns, unsigned int missing)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int target = (index + 1u) * (gridDim.x + missing);
+        __threadfence();
+        atomicAdd(arrive, 1u);
+        int good = 1;
+        const uint64_t t0 = global_ns();
+        while (*(volatile unsigned int *)arrive < target) {
+            if (global_ns() - t0 > limit_ns) {
+                good = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// 4-byte asynchronous copy global -> shared (zero-filled, nothing read, when
+// `bytes` is 0), its group commit and the wait for this thread's groups.
+__device__ __forceinline__ void cp_async_4(uint32_t dst, const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // A tensor map the host wrote into global memory (rather than a kernel
 // parameter) is read by the TMA unit through the tensormap proxy: acquire it
 // once in the issuing thread before the first copy that uses it.

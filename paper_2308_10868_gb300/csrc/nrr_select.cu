@@ -12,11 +12,14 @@
 //   K2 radix select  up to five histogram passes over 11-bit digits of the
 //                    keys, starting at the top bit of the largest key, find
 //                    the n_sel-th largest key K* and how many keys equal to
-//                    K* are needed; no full sort.  The CTA that finishes a
-//                    pass last picks the digit, so a pass is one launch.
+//                    K* are needed; no full sort.
 //   K3 compaction    an order-preserving compaction writes every centre
 //                    with key > K*, plus the first `need` with key == K*
 //                    in raster order, to the output in raster order.
+//   K2 and K3 are one cooperative launch: a grid barrier after each pass
+//   (every CTA then fixes the same digit from the global histogram) and
+//   one before the compaction's writes (each CTA's offset is the sum of
+//   the counts of the CTAs before it).
 // Ties are therefore ranked by raster index and the result is
 // deterministic.
 #include <math.h>
@@ -24,17 +27,15 @@
 #include <mutex>
 
 #include "nrr_internal.h"
+#include "nrr_ptx.cuh"
 
 namespace nrr {
 namespace {
 
 constexpr int KEY_THREADS = 256;
 constexpr int HIST_BINS = 2048;
-constexpr int HIST_THREADS = 512;
-constexpr int HIST_KPT = 8;  // keys per thread per sweep of a histogram pass
-constexpr int CMP_THREADS = 1024;
-constexpr int CMP_ITEMS = 4;
-constexpr int CMP_CHUNK = CMP_THREADS * CMP_ITEMS;
+constexpr int CMP_ITEMS = 4;      // keys per thread per compaction sub-block
+constexpr int CMP_CHUNK = 4096;   // keys per entry of the count scratch (at least one entry per rank CTA)
 constexpr int NPASS = 5;
 
 struct SelState {
@@ -141,126 +142,33 @@ __device__ __forceinline__ bool digit_of_pass(const SelState *st, int pass, int 
     return true;
 }
 
-// One radix pass: histogram of this pass's digit over the keys that match
-// the digits fixed so far; the CTA that finishes last then finds the bucket
-// holding the kth largest key and fixes its digit (the counts of the other
-// CTAs are visible to it through the arrival counter).
-__global__ void __launch_bounds__(HIST_THREADS) radix_pass_kernel(const long long *__restrict__ keys, long long ng,
-                                                                  int pass, double frac, SelState *st,
-                                                                  unsigned int *__restrict__ hist)
-{
-    __shared__ unsigned int h[HIST_BINS];
-    __shared__ long long wsum[HIST_THREADS / 32];
-    __shared__ long long s_kth;
-    __shared__ int s_last;
-    if (st->done) return;
-    int sh, w;
-    if (!digit_of_pass(st, pass, &sh, &w)) return;
-    for (int i = threadIdx.x; i < HIST_BINS; i += blockDim.x) h[i] = 0;
-    __syncthreads();
-    const long long hi = st->prefix >> (sh + w);
-    const long long dmask = (1ll << w) - 1;
-    // HIST_KPT keys per thread per sweep, all loads issued before any is used
-    const long long sweep = (long long)gridDim.x * blockDim.x * HIST_KPT;
-    for (long long g0 = (long long)blockIdx.x * blockDim.x * HIST_KPT + threadIdx.x; g0 < ng; g0 += sweep) {
-        long long kv[HIST_KPT];
-#pragma unroll
-        for (int q = 0; q < HIST_KPT; ++q) {
-            const long long g = g0 + (long long)q * blockDim.x;
-            kv[q] = g < ng ? keys[g] : -1;
-        }
-#pragma unroll
-        for (int q = 0; q < HIST_KPT; ++q) {
-            const long long k = kv[q];
-            if (k > 0 && (k >> (sh + w)) == hi) {
-                const unsigned bin = (unsigned)((k >> sh) & dmask);
-                // lanes of a warp with the same bin add once
-                const unsigned peers = __match_any_sync(__activemask(), bin);
-                if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[bin], (unsigned)__popc(peers));
-            }
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < HIST_BINS; i += blockDim.x)
-        if (h[i]) atomicAdd(&hist[pass * HIST_BINS + i], h[i]);
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&st->arrived[pass], 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    // ---- the last CTA picks the bucket --------------------------------------
-    if (threadIdx.x == 0) {
-        if (pass == 0) {
-            // n_sel = floor(0.5 + N_c * F_s), capped at the keys > 0 (Sec. 4.1)
-            long long ns = (long long)floor(__dadd_rn(0.5, __dmul_rn((double)st->nc, frac)));
-            if (ns > (long long)st->npos) ns = (long long)st->npos;
-            if (ns < 0) ns = 0;
-            st->nsel = ns;
-            st->kth = ns;
-            st->prefix = 0;
-            if (ns == 0) {
-                st->done = 1;
-                st->thresh = 0x7fffffffffffffffll;
-                st->need_ties = 0;
-            }
-        }
-        s_kth = st->kth;
-    }
-    __syncthreads();
-    if (st->done) return;
-    const long long kth = s_kth;
-    const int nb = 1 << w;
-    constexpr int PER = HIST_BINS / HIST_THREADS;  // bins per thread
-    // thread t owns reversed bins r = PER*t .. PER*t+PER-1 (bin b = nb-1-r);
-    // an inclusive scan over r counts the keys in bins >= b
-    const int t = threadIdx.x;
-    long long c[PER], v = 0;
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-        const int bin = nb - 1 - (PER * t + q);
-        c[q] = bin >= 0 ? (long long)hist[pass * HIST_BINS + bin] : 0;
-        v += c[q];
-    }
-    long long incl = v;
-    const int lane = t & 31, wp = t >> 5;
-    for (int o = 1; o < 32; o <<= 1) {
-        const long long n2 = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += n2;
-    }
-    if (lane == 31) wsum[wp] = incl;
-    __syncthreads();
-    long long above = incl - v;  // keys in bins above this thread's first bin
-    for (int i = 0; i < wp; ++i) above += wsum[i];
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-        const int bin = nb - 1 - (PER * t + q);
-        if (bin >= 0 && above < kth && above + c[q] >= kth) {
-            const long long pre = st->prefix | ((long long)bin << sh);
-            st->prefix = pre;
-            st->kth = kth - above;
-            if (sh == 0) {
-                st->thresh = pre;
-                st->need_ties = kth - above;
-            }
-        }
-        above += c[q];
-    }
-}
+// K2 + K3 in one cooperative launch (every CTA resident; waits bounded).
+// Radix select: per pass, every CTA histograms this pass's digit over its
+// share of the keys that match the digits fixed so far and adds its bins to
+// the pass's global histogram; after a grid barrier every CTA reads the
+// same histogram and fixes the same digit (the bucket holding the kth
+// largest key), so a pass costs one barrier.  Compaction: CTA c owns one
+// contiguous span of keys; it counts its keys > K* and == K*, and after a
+// barrier its output offset is the sum of the counts of the CTAs before it;
+// the keys selected are written in raster order with the ties quota.
+constexpr int RK_THREADS = 512;
+constexpr int RK_KPT = 8;  // keys per thread per sweep (RK_THREADS * RK_KPT = CMP_CHUNK)
+constexpr int RK_SUB = RK_THREADS * CMP_ITEMS;     // keys per compaction sub-block
 
-__device__ __forceinline__ unsigned long long block_excl_scan_u64(unsigned long long v, unsigned long long *tot)
+__device__ __forceinline__ unsigned long long block_excl_scan_rk(unsigned long long v, unsigned long long *tot)
 {
-    __shared__ unsigned long long ws[CMP_THREADS / 32];
+    __shared__ unsigned long long ws[RK_THREADS / 32];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     unsigned long long incl = v;
     for (int o = 1; o < 32; o <<= 1) {
-        unsigned long long n = __shfl_up_sync(0xffffffffu, incl, o);
+        const unsigned long long n = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += n;
     }
+    __syncthreads();  // ws is reused from the previous call
     if (lane == 31) ws[wp] = incl;
     __syncthreads();
     unsigned long long before = 0, all = 0;
-    for (int i = 0; i < CMP_THREADS / 32; ++i) {
+    for (int i = 0; i < RK_THREADS / 32; ++i) {
         if (i < wp) before += ws[i];
         all += ws[i];
     }
@@ -268,91 +176,179 @@ __device__ __forceinline__ unsigned long long block_excl_scan_u64(unsigned long 
     return before + incl - v;
 }
 
-// Per-chunk counts of keys > K* (high word) and == K* (low word); the CTA
-// that finishes last turns them into exclusive prefix offsets.
-__global__ void __launch_bounds__(CMP_THREADS) compact_count_kernel(const long long *__restrict__ keys, long long ng,
-                                                                    SelState *st, unsigned long long *__restrict__ cnt,
-                                                                    int nchunks)
+__global__ void __launch_bounds__(RK_THREADS) select_rank_kernel(const long long *__restrict__ keys, long long ng,
+                                                                 long long span, double frac, SelState *st,
+                                                                 unsigned int *__restrict__ hist,
+                                                                 unsigned long long *__restrict__ cnt, int gx, int gy,
+                                                                 int stride, int32_t *__restrict__ centers,
+                                                                 int max_blocks, int32_t *d_n_selected,
+                                                                 unsigned int *err, uint64_t wait_ns,
+                                                                 unsigned int missing)
 {
-    __shared__ int s_last;
-    __shared__ unsigned long long carry;
-    const long long th = st->thresh;
-    const long long base = (long long)blockIdx.x * CMP_CHUNK + (long long)threadIdx.x * CMP_ITEMS;
-    unsigned long long v = 0;
+    __shared__ unsigned int h[HIST_BINS];
+    __shared__ long long wsum[RK_THREADS / 32];
+    __shared__ long long s_prefix, s_kth, s_thresh, s_need, s_nsel;
+    __shared__ int s_done;
+    const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
+    unsigned int nb = 0;  // grid barriers passed
+    auto barrier = [&]() {
+        if (grid_barrier(&st->arrived[0], nb++, wait_ns, missing)) return true;
+        if (t == 0) atomicOr(err, DEV_ERR_TIMEOUT);
+        return false;
+    };
+    if (t == 0) {
+        // n_sel = floor(0.5 + N_c * F_s), capped at the keys > 0 (Sec. 4.1)
+        long long ns = (long long)floor(__dadd_rn(0.5, __dmul_rn((double)st->nc, frac)));
+        if (ns > (long long)st->npos) ns = (long long)st->npos;
+        if (ns < 0) ns = 0;
+        s_nsel = ns;
+        s_kth = ns;
+        s_prefix = 0;
+        s_done = ns == 0 || st->maxkey == 0;
+        s_thresh = 0x7fffffffffffffffll;  // nothing selected unless a pass fixes it
+        s_need = 0;
+    }
+    __syncthreads();
+    for (int pass = 0; pass < NPASS && !s_done; ++pass) {
+        int sh, w;
+        if (!digit_of_pass(st, pass, &sh, &w)) break;
+        for (int i = t; i < HIST_BINS; i += RK_THREADS) h[i] = 0;
+        __syncthreads();
+        const long long hi = s_prefix >> (sh + w);
+        const long long dmask = (1ll << w) - 1;
+        // RK_KPT keys per thread per sweep, all loads issued before any is used
+        const long long sweep = (long long)gridDim.x * RK_THREADS * RK_KPT;
+        for (long long g0 = (long long)blockIdx.x * RK_THREADS * RK_KPT + t; g0 < ng; g0 += sweep) {
+            long long kv[RK_KPT];
 #pragma unroll
-    for (int i = 0; i < CMP_ITEMS; ++i) {
-        const long long g = base + i;
-        if (g < ng) {
-            const long long k = keys[g];
-            if (k > th) v += 1ull << 32;
-            else if (k == th) v += 1ull;
+            for (int q = 0; q < RK_KPT; ++q) {
+                const long long g = g0 + (long long)q * RK_THREADS;
+                kv[q] = g < ng ? __ldcg(keys + g) : -1;
+            }
+#pragma unroll
+            for (int q = 0; q < RK_KPT; ++q) {
+                const long long k = kv[q];
+                if (k > 0 && (k >> (sh + w)) == hi) {
+                    const unsigned bin = (unsigned)((k >> sh) & dmask);
+                    // lanes of a warp with the same bin add once
+                    const unsigned peers = __match_any_sync(__activemask(), bin);
+                    if (lane == __ffs(peers) - 1) atomicAdd(&h[bin], (unsigned)__popc(peers));
+                }
+            }
+        }
+        __syncthreads();
+        unsigned int *gh = hist + pass * HIST_BINS;
+        for (int i = t; i < HIST_BINS; i += RK_THREADS)
+            if (h[i]) atomicAdd(&gh[i], h[i]);
+        if (!barrier()) return;
+        // every CTA finds the bucket holding the kth largest key: thread t
+        // owns reversed bins r = PER*t .. PER*t+PER-1 (bin b = nb-1-r), an
+        // inclusive scan over r counts the keys in bins >= b
+        const long long kth = s_kth;
+        const int nbins = 1 << w;
+        constexpr int PER = HIST_BINS / RK_THREADS;
+        long long c[PER], v = 0;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int bin = nbins - 1 - (PER * t + q);
+            c[q] = bin >= 0 ? (long long)__ldcg(gh + bin) : 0;
+            v += c[q];
+        }
+        const long long prefix = s_prefix;
+        long long incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long n2 = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += n2;
+        }
+        if (lane == 31) wsum[wp] = incl;
+        __syncthreads();  // every thread has read s_kth and s_prefix
+        long long above = incl - v;  // keys in bins above this thread's first bin
+        for (int i = 0; i < wp; ++i) above += wsum[i];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int bin = nbins - 1 - (PER * t + q);
+            if (bin >= 0 && above < kth && above + c[q] >= kth) {
+                const long long pre = prefix | ((long long)bin << sh);
+                s_prefix = pre;
+                s_kth = kth - above;
+                if (sh == 0) {
+                    s_thresh = pre;
+                    s_need = kth - above;
+                    s_done = 1;
+                }
+            }
+            above += c[q];
+        }
+        __syncthreads();
+    }
+    const long long th = s_thresh, need = s_need;
+    if (blockIdx.x == 0 && t == 0) {
+        st->nsel = s_nsel;
+        st->thresh = th;
+        st->need_ties = need;
+        if (d_n_selected) *d_n_selected = (int32_t)s_nsel;
+    }
+    // ---- compaction over this CTA's span [k0, k1) ----------------------------
+    const long long k0 = (long long)blockIdx.x * span;
+    const long long k1 = k0 + span < ng ? k0 + span : ng;
+    unsigned long long v = 0;  // keys > K* (high word), == K* (low word)
+    for (long long b0 = k0; b0 < k1; b0 += RK_SUB) {
+#pragma unroll
+        for (int i = 0; i < CMP_ITEMS; ++i) {
+            const long long g = b0 + (long long)t * CMP_ITEMS + i;
+            if (g < k1) {
+                const long long k = __ldcg(keys + g);
+                if (k > th) v += 1ull << 32;
+                else if (k == th) v += 1ull;
+            }
         }
     }
     unsigned long long tot;
-    block_excl_scan_u64(v, &tot);
-    if (threadIdx.x == 0) cnt[blockIdx.x] = tot;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&st->arrived[NPASS], 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int b = 0; b < nchunks; b += CMP_THREADS) {
-        const int i = b + threadIdx.x;
-        const unsigned long long x = i < nchunks ? cnt[i] : 0ull;
-        unsigned long long t2;
-        const unsigned long long ex = block_excl_scan_u64(x, &t2);
-        const unsigned long long c0 = carry;
-        if (i < nchunks) cnt[i] = c0 + ex;
-        __syncthreads();
-        if (threadIdx.x == 0) carry = c0 + t2;
-        __syncthreads();
-    }
-}
-
-__global__ void __launch_bounds__(CMP_THREADS) compact_write_kernel(const long long *__restrict__ keys, long long ng,
-                                                                    int gx, int gy, int stride, const SelState *st,
-                                                                    const unsigned long long *__restrict__ off,
-                                                                    int32_t *__restrict__ centers, int max_blocks,
-                                                                    int32_t *d_n_selected)
-{
-    const long long th = st->thresh, need = st->need_ties;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && d_n_selected) *d_n_selected = (int32_t)st->nsel;
-    const long long base = (long long)blockIdx.x * CMP_CHUNK + (long long)threadIdx.x * CMP_ITEMS;
-    long long k[CMP_ITEMS];
-    unsigned long long v = 0;
+    block_excl_scan_rk(v, &tot);
+    if (t == 0) __stcg(cnt + blockIdx.x, tot);
+    if (!barrier()) return;
+    // this CTA's offset: the counts of the CTAs before it
+    unsigned long long off = 0;
+    for (int i = t; i < (int)blockIdx.x; i += RK_THREADS) off += __ldcg(cnt + i);
+    unsigned long long offall;
+    block_excl_scan_rk(off, &offall);
+    unsigned long long carry = offall;
+    for (long long b0 = k0; b0 < k1; b0 += RK_SUB) {
+        long long k[CMP_ITEMS];
+        unsigned long long u = 0;
 #pragma unroll
-    for (int i = 0; i < CMP_ITEMS; ++i) {
-        const long long g = base + i;
-        k[i] = g < ng ? keys[g] : -1;
-        if (k[i] > th) v += 1ull << 32;
-        else if (k[i] == th) v += 1ull;
-    }
-    const unsigned long long ex = block_excl_scan_u64(v, nullptr) + off[blockIdx.x];
-    long long sb = (long long)(ex >> 32), tb = (long long)(ex & 0xffffffffull);
-#pragma unroll
-    for (int i = 0; i < CMP_ITEMS; ++i) {
-        const long long g = base + i;
-        bool sel = false;
-        long long pos = 0;
-        if (k[i] > th) {
-            sel = true;
-            pos = sb + (tb < need ? tb : need);
-            ++sb;
-        } else if (k[i] == th) {
-            if (tb < need) {
-                sel = true;
-                pos = sb + tb;
-            }
-            ++tb;
+        for (int i = 0; i < CMP_ITEMS; ++i) {
+            const long long g = b0 + (long long)t * CMP_ITEMS + i;
+            k[i] = g < k1 ? __ldcg(keys + g) : -1;
+            if (k[i] > th) u += 1ull << 32;
+            else if (k[i] == th) u += 1ull;
         }
-        if (sel && pos < max_blocks) {
-            const int x = (int)(g % gx), y = (int)((g / gx) % gy), z = (int)(g / ((long long)gx * gy));
-            centers[3 * pos + 0] = x * stride;
-            centers[3 * pos + 1] = y * stride;
-            centers[3 * pos + 2] = z * stride;
+        unsigned long long subtot;
+        const unsigned long long ex = block_excl_scan_rk(u, &subtot) + carry;
+        carry += subtot;
+        long long sb = (long long)(ex >> 32), tb = (long long)(ex & 0xffffffffull);
+#pragma unroll
+        for (int i = 0; i < CMP_ITEMS; ++i) {
+            const long long g = b0 + (long long)t * CMP_ITEMS + i;
+            bool sel = false;
+            long long pos = 0;
+            if (k[i] > th) {
+                sel = true;
+                pos = sb + (tb < need ? tb : need);
+                ++sb;
+            } else if (k[i] == th) {
+                if (tb < need) {
+                    sel = true;
+                    pos = sb + tb;
+                }
+                ++tb;
+            }
+            if (sel && pos < max_blocks) {
+                const int x = (int)(g % gx), y = (int)((g / gx) % gy), z = (int)(g / ((long long)gx * gy));
+                centers[3 * pos + 0] = x * stride;
+                centers[3 * pos + 1] = y * stride;
+                centers[3 * pos + 2] = z * stride;
+            }
         }
     }
 }
@@ -429,17 +425,40 @@ nrr_status enqueue_select(const uint16_t *preop, const uint8_t *mask, nrr_dims d
                                        &st->nc, &st->maxkey, &st->npos, s);
         if (ss != NRR_OK) return ss;
     }
-    long long hgrid = (p.ng + HIST_THREADS * HIST_KPT - 1) / (HIST_THREADS * HIST_KPT);
-    if (hgrid > 4 * sm_count()) hgrid = 4 * sm_count();
-    if (hgrid < 1) hgrid = 1;
-    for (int pass = 0; pass < NPASS; ++pass)
-        radix_pass_kernel<<<(unsigned)hgrid, HIST_THREADS, 0, s>>>(keys, p.ng, pass, frac, st, hist);
-    compact_count_kernel<<<p.nchunks, CMP_THREADS, 0, s>>>(keys, p.ng, st, cnt, p.nchunks);
-    compact_write_kernel<<<p.nchunks, CMP_THREADS, 0, s>>>(keys, p.ng, p.gx, p.gy, stride, st, cnt, centers,
-                                                          max_blocks, d_n_selected);
+    // the rank kernel: at most two CTAs per SM (and as many as are resident),
+    // one span of keys each
+    static int occ = 0;
+    if (!occ) {
+        NRR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, select_rank_kernel, RK_THREADS, 0));
+        if (occ < 1) return fail(NRR_E_INTERNAL, "selection kernel does not fit on an SM");
+    }
+    long long grid = (p.ng + RK_THREADS * RK_KPT - 1) / (RK_THREADS * RK_KPT);
+    const long long most = (long long)(occ < 2 ? occ : 2) * sm_count();
+    if (grid > most) grid = most;
+    if (grid < 1) grid = 1;
+    long long span = (p.ng + grid - 1) / grid;
+    span = (span + RK_SUB - 1) / RK_SUB * RK_SUB;
+    unsigned int *err = nullptr;
+    nrr_status es = device_error_word(&err);
+    if (es != NRR_OK) return es;
+    const uint64_t wait_ns = device_wait_ns();
+    const unsigned int missing = test_missing_arrivals();
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(RK_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    NRR_CUDA_TRY(cudaLaunchKernelEx(&cfg, select_rank_kernel, (const long long *)keys, p.ng, span, frac, st, hist,
+                                    cnt, p.gx, p.gy, stride, centers, (int)max_blocks, d_n_selected, err, wait_ns,
+                                    missing));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "selection kernel launch");
-    count_launches(1 + NPASS + 2);
+    count_launches(2);
     return NRR_OK;
 }
 

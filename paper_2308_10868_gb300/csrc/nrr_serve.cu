@@ -15,7 +15,12 @@
 //     device, and a new request starts as soon as any earlier one finishes;
 //   - each request runs the whole path (selection with a device-side count,
 //     box sums, matching) on its slot stream, then a host callback stamps
-//     its completion time;
+//     its completion time and wakes the scheduler, which admits the next
+//     queued request at once;
+//   - request memory comes from a stream-ordered pool of the library's own
+//     that keeps what it has mapped (a request of a size seen before maps
+//     nothing), and admission counts the pool's mapped but unused bytes as
+//     free;
 //   - nrr_poll reports NRR_PENDING or the result (device pointers owned by
 //     the library until nrr_release, the block count and the latencies).
 // Failures are contained per request: an allocation or launch error marks
@@ -46,7 +51,9 @@ double now_s()
 
 enum ReqState { QUEUED, RUNNING, DONE, FAILED };
 
+struct Server;
 struct Req {
+    Server *srv;
     uint64_t ticket;
     nrr_request r;
     ReqState state = QUEUED;
@@ -76,6 +83,8 @@ struct Server {
     std::mutex mu;
     std::condition_variable cv;
     std::thread worker;
+    cudaMemPool_t pool = nullptr;
+    std::atomic<unsigned long long> events{0};  // submissions and completions
     bool stop = false;
     uint64_t next = 1;
     unsigned int *err = nullptr;
@@ -131,6 +140,46 @@ void CUDART_CB on_done(void *p)
     Req *q = (Req *)p;
     q->t_done.store(now_s());
     q->finished.store(1);
+    // wake the scheduler to retire it and admit the next (no lock taken here:
+    // the scheduler may hold its lock while it waits for a stream)
+    q->srv->events.fetch_add(1);
+    q->srv->cv.notify_all();
+}
+
+// The library's stream-ordered pool on `dev`: created once per process and
+// kept (with every byte it has mapped, release threshold at the maximum), so
+// that later requests and later servers reuse its memory.
+cudaMemPool_t request_pool(int dev)
+{
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[dev] = p;
+    }
+    return pools[dev];
+}
+
+// Bytes a request can still get: free device memory plus the pool's mapped
+// bytes that no request uses.
+size_t available_bytes(cudaMemPool_t pool)
+{
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return 0;
+    uint64_t reserved = 0, used = 0;
+    if (pool && cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) == cudaSuccess &&
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess && reserved > used)
+        fr += (size_t)(reserved - used);
+    return fr;
 }
 
 // Admit request q on slot k (server lock held).  Returns false if memory is
@@ -139,8 +188,8 @@ bool admit(Server *S, Req *q, int k)
 {
     const nrr_request &r = q->r;
     const Layout L = layout_of(r);
-    size_t fr = 0, tot = 0;
-    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && fr < L.total + S->reserve) {
+    const size_t fr = available_bytes(S->pool);
+    if (fr < L.total + S->reserve) {
         bool busy = false;
         for (uint64_t t : S->slot_req) busy |= t != 0;
         if (busy) return false;  // wait for running requests to free memory
@@ -153,7 +202,7 @@ bool admit(Server *S, Req *q, int k)
     q->t_admit = now_s();
     q->state = RUNNING;
     S->slot_req[k] = q->ticket;
-    cudaError_t e = fault("alloc") ? cudaErrorMemoryAllocation : cudaMallocAsync(&q->mem, L.total, s);
+    cudaError_t e = fault("alloc") ? cudaErrorMemoryAllocation : cudaMallocFromPoolAsync(&q->mem, L.total, S->pool, s);
     if (e != cudaSuccess) {
         q->mem = nullptr;
         q->status = cuda_fail(e, "request allocation");
@@ -184,7 +233,7 @@ bool admit(Server *S, Req *q, int k)
         for (int i = 0; i < 3; ++i) a.radius[i] = r.radius[i];
         a.n_jobs = 1;
         a.jobs[0] = MatchJob{q->centers, q->d_n, q->cap, q->disp, q->ncc, q->valid};
-        a.ctas_per_sm = tuned_ctas_per_sm(r.dtype, r.block, r.radius);
+        apply_tuning(a, r.dtype, r.block, r.radius);
         a.err = S->err;
         st = launch_match(a, s);
     }
@@ -205,6 +254,7 @@ void worker_main(Server *S)
     cudaSetDevice(S->device);
     std::unique_lock<std::mutex> lk(S->mu);
     while (!S->stop) {
+        const unsigned long long seen = S->events.load();
         // retire finished requests, freeing their slots
         for (int k = 0; k < S->nslots; ++k) {
             uint64_t t = S->slot_req[k];
@@ -242,7 +292,9 @@ void worker_main(Server *S)
             progressed = true;
         }
         if (progressed) S->cv.notify_all();
-        S->cv.wait_for(lk, std::chrono::microseconds(50));
+        // woken by a submission or a completion (the short timeout covers a
+        // wake-up sent between the check and the wait)
+        S->cv.wait_for(lk, std::chrono::microseconds(200), [&] { return S->stop || S->events.load() != seen; });
     }
 }
 
@@ -268,6 +320,11 @@ nrr_status nrr_server_start(int32_t slots, size_t reserve_bytes)
     if (st != NRR_OK) {
         delete S;
         return st;
+    }
+    S->pool = request_pool(S->device);
+    if (!S->pool) {
+        delete S;
+        return fail(NRR_E_CUDA, "memory pool creation");
     }
     S->nslots = slots;
     S->reserve = reserve_bytes;
@@ -329,6 +386,7 @@ nrr_status nrr_submit(const nrr_request *req, uint64_t *ticket)
     Server *S = g_server;
     if (!S) return fail(NRR_E_INVALID, "no server running (nrr_server_start)");
     Req *q = new Req();
+    q->srv = S;
     q->r = *req;
     q->t_submit = now_s();
     {
@@ -341,6 +399,7 @@ nrr_status nrr_submit(const nrr_request *req, uint64_t *ticket)
         S->reqs[q->ticket] = q;
         S->queue.push_back(q->ticket);
         *ticket = q->ticket;
+        S->events.fetch_add(1);
     }
     S->cv.notify_all();
     return NRR_OK;

@@ -63,34 +63,6 @@ __constant__ signed char c_offs[26][3] = {
     {0, -1, -1}, {0, 1, -1}, {0, -1, 1}, {0, 1, 1},                                                       // edge
     {-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {1, 1, -1}, {-1, -1, 1}, {1, -1, 1}, {-1, 1, 1}, {1, 1, 1}};  // vertex
 
-// Grid-wide barrier number `index` (0, 1, ...): every CTA adds one arrival
-// and waits for (index + 1) * (gridDim.x + missing) of them (missing: 0, or
-// arrivals a test adds that never come).  Returns false if the wait ran out
-// of time.
-__device__ bool grid_barrier(unsigned int *arrive, unsigned int index, uint64_t limit_ns, unsigned int missing)
-{
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned int target = (index + 1u) * (gridDim.x + missing);
-        __threadfence();
-        atomicAdd(arrive, 1u);
-        int good = 1;
-        const uint64_t t0 = global_ns();
-        while (*(volatile unsigned int *)arrive < target) {
-            if (global_ns() - t0 > limit_ns) {
-                good = 0;
-                break;
-            }
-            __nanosleep(64);
-        }
-        __threadfence();
-        ok = good;
-    }
-    __syncthreads();
-    return ok != 0;
-}
-
 __device__ __forceinline__ unsigned char load_state(const unsigned char *p) { return (unsigned char)__ldcg(p); }
 __device__ __forceinline__ void store_state(unsigned char *p, unsigned char v) { __stcg(p, v); }
 

@@ -2,13 +2,21 @@
 //
 // The paper tunes its GPU block-matching kernel by an empirical search over
 // the thread configuration (Sec. 4.3, GADAPT), reporting ~30x between tuned
-// and untuned.  Here the per-block tile is fixed by the block size and
-// search radius, so the free parameter is how many persistent CTAs share an
-// SM (fewer CTAs leave more shared-memory bandwidth and L1 to each; more
-// hide more latency).  The tuner times every feasible value on real inputs
-// and keeps the fastest in a per-process table keyed by (device, dtype,
-// block, radius); every later launch of that variant, single or batched,
-// uses it.  The table can be saved to and loaded from a small text file.
+// and untuned.  Here the per-block tile (two search lines per thread) is
+// fixed by the block size and search radius; the free parameters of a
+// launch's shape are
+//   - how many persistent CTAs share an SM (fewer leave more shared-memory
+//     bandwidth and L1 to each; more hide more latency),
+//   - the window buffers, i.e. blocks in flight per CTA (two: the next
+//     block's copy overlaps this block's search; one: less shared memory,
+//     more CTAs),
+//   - whether each thread's box sums are staged into shared memory by
+//     asynchronous copies during the search (no load latency at the bounds,
+//     more shared memory) or loaded at the bounds.
+// The tuner times every feasible shape on real inputs and keeps the fastest
+// in a per-process table keyed by (device, dtype, block, radius); every
+// later launch of that variant, single or batched, uses it.  The table can
+// be saved to and loaded from a small text file.
 #include <stdio.h>
 
 #include <map>
@@ -21,7 +29,7 @@ namespace nrr {
 
 typedef std::tuple<int, int, int, int, int, int> TuneKey;  // device, dtype, block, rx, ry, rz
 static std::mutex g_tune_mu;
-static std::map<TuneKey, int> g_tune;
+static std::map<TuneKey, nrr_match_shape> g_tune;
 
 static TuneKey make_key(nrr_dtype dtype, int block, const int32_t *r)
 {
@@ -30,14 +38,28 @@ static TuneKey make_key(nrr_dtype dtype, int block, const int32_t *r)
     return TuneKey(dev, (int)dtype, block, r[0], r[1], r[2]);
 }
 
-int tuned_ctas_per_sm(nrr_dtype dtype, int block, const int32_t *radius)
+static nrr_match_shape tuned_shape(nrr_dtype dtype, int block, const int32_t *radius)
 {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(make_key(dtype, block, radius));
-    return it == g_tune.end() ? 0 : it->second;
+    return it == g_tune.end() ? nrr_match_shape{0, 0, 0} : it->second;
 }
 
-static void set_tuned(nrr_dtype dtype, int block, const int32_t *radius, int v)
+void apply_tuning(MatchLaunch &a, nrr_dtype dtype, int block, const int32_t *radius)
+{
+    const nrr_match_shape sh = tuned_shape(dtype, block, radius);
+    a.ctas_per_sm = sh.ctas_per_sm;
+    a.windows = sh.windows;
+    a.stage_boxsums = sh.stage;
+}
+
+static bool shape_ok(const nrr_match_shape &s)
+{
+    return s.ctas_per_sm >= 0 && s.ctas_per_sm <= 64 && s.windows >= 0 && s.windows <= 2 && s.stage >= 0 &&
+           s.stage <= 2;
+}
+
+static void set_tuned(nrr_dtype dtype, int block, const int32_t *radius, const nrr_match_shape &v)
 {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[make_key(dtype, block, radius)] = v;
@@ -53,7 +75,7 @@ nrr_status nrr_tuning_get(nrr_dtype dtype, int32_t block, const int32_t radius[3
 {
     clear_error();
     if (!radius || !ctas_per_sm) return fail(NRR_E_INVALID, "NULL argument");
-    *ctas_per_sm = tuned_ctas_per_sm(dtype, block, radius);
+    *ctas_per_sm = tuned_shape(dtype, block, radius).ctas_per_sm;
     return NRR_OK;
 }
 
@@ -61,7 +83,23 @@ nrr_status nrr_tuning_set(nrr_dtype dtype, int32_t block, const int32_t radius[3
 {
     clear_error();
     if (!radius || ctas_per_sm < 0 || ctas_per_sm > 64) return fail(NRR_E_INVALID, "bad tuning entry");
-    set_tuned(dtype, block, radius, ctas_per_sm);
+    set_tuned(dtype, block, radius, nrr_match_shape{ctas_per_sm, 0, 0});
+    return NRR_OK;
+}
+
+nrr_status nrr_tuning_get_shape(nrr_dtype dtype, int32_t block, const int32_t radius[3], nrr_match_shape *shape)
+{
+    clear_error();
+    if (!radius || !shape) return fail(NRR_E_INVALID, "NULL argument");
+    *shape = tuned_shape(dtype, block, radius);
+    return NRR_OK;
+}
+
+nrr_status nrr_tuning_set_shape(nrr_dtype dtype, int32_t block, const int32_t radius[3], const nrr_match_shape *shape)
+{
+    clear_error();
+    if (!radius || !shape || !shape_ok(*shape)) return fail(NRR_E_INVALID, "bad tuning entry");
+    set_tuned(dtype, block, radius, *shape);
     return NRR_OK;
 }
 
@@ -72,10 +110,11 @@ nrr_status nrr_tuning_save(const char *path)
     if (!f) return fail(NRR_E_INVALID, "cannot open tuning file for writing");
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        fprintf(f, "# device dtype block rx ry rz ctas_per_sm\n");
+        fprintf(f, "# device dtype block rx ry rz ctas_per_sm windows stage\n");
         for (auto &kv : g_tune)
-            fprintf(f, "%d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
-                    std::get<3>(kv.first), std::get<4>(kv.first), std::get<5>(kv.first), kv.second);
+            fprintf(f, "%d %d %d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
+                    std::get<2>(kv.first), std::get<3>(kv.first), std::get<4>(kv.first), std::get<5>(kv.first),
+                    kv.second.ctas_per_sm, kv.second.windows, kv.second.stage);
     }
     fclose(f);
     return NRR_OK;
@@ -89,9 +128,13 @@ nrr_status nrr_tuning_load(const char *path)
     char line[256];
     int n = 0;
     while (fgets(line, sizeof line, f)) {
-        int d, t, b, x, y, z, v;
+        int d, t, b, x, y, z;
+        nrr_match_shape v{0, 0, 0};
         if (line[0] == '#') continue;
-        if (sscanf(line, "%d %d %d %d %d %d %d", &d, &t, &b, &x, &y, &z, &v) == 7 && v >= 0 && v <= 64) {
+        // a line without the last two fields (ctas per SM only) leaves them by occupancy
+        const int k = sscanf(line, "%d %d %d %d %d %d %d %d %d", &d, &t, &b, &x, &y, &z, &v.ctas_per_sm, &v.windows,
+                             &v.stage);
+        if ((k == 7 || k == 9) && shape_ok(v)) {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             g_tune[TuneKey(d, t, b, x, y, z)] = v;
             ++n;
@@ -127,37 +170,42 @@ nrr_status nrr_autotune_match(const void *d_preop, const void *d_intraop, const 
     a.jobs[0] = MatchJob{d_centers, nullptr, n_blocks, d_disp, d_ncc, d_valid};
     st = device_error_word(&a.err);
     if (st != NRR_OK) return st;
-    int occ = 0;
-    st = match_occupancy(a, &occ);
-    if (st != NRR_OK) return st;
     cudaEvent_t e0, e1;
     NRR_CUDA_TRY(cudaEventCreate(&e0));
     NRR_CUDA_TRY(cudaEventCreate(&e1));
-    int best = occ;
+    nrr_match_shape best{0, 0, 0};
     float best_t = 1e30f;
-    for (int k = occ; k >= 1 && st == NRR_OK; --k) {
-        a.ctas_per_sm = k;
-        st = launch_match(a, s);  // warm-up
-        float tot = 0.f;
-        for (int rep = 0; rep < 3 && st == NRR_OK; ++rep) {
-            cudaEventRecord(e0, s);
-            st = launch_match(a, s);
-            cudaEventRecord(e1, s);
-            if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(NRR_E_CUDA, "event sync during tuning");
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            tot += ms;
+    for (int stage = 1; stage <= 2 && st == NRR_OK; ++stage)
+        for (int windows = 2; windows >= 1 && st == NRR_OK; --windows) {
+            a.stage_boxsums = stage;
+            a.windows = windows;
+            a.ctas_per_sm = 0;
+            int occ = 0;
+            st = match_occupancy(a, &occ);
+            for (int k = occ; k >= 1 && st == NRR_OK; --k) {
+                a.ctas_per_sm = k;
+                st = launch_match(a, s);  // warm-up
+                float tot = 0.f;
+                for (int rep = 0; rep < 3 && st == NRR_OK; ++rep) {
+                    cudaEventRecord(e0, s);
+                    st = launch_match(a, s);
+                    cudaEventRecord(e1, s);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(NRR_E_CUDA, "event sync during tuning");
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    tot += ms;
+                }
+                if (st == NRR_OK && tot / 3 < best_t) {
+                    best_t = tot / 3;
+                    best = nrr_match_shape{k, windows, stage};
+                }
+            }
         }
-        if (st == NRR_OK && tot / 3 < best_t) {
-            best_t = tot / 3;
-            best = k;
-        }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != NRR_OK) return st;
-    set_tuned(dtype, block, radius, best == occ ? 0 : best);
-    if (best_ctas_per_sm) *best_ctas_per_sm = best;
+    set_tuned(dtype, block, radius, best);
+    if (best_ctas_per_sm) *best_ctas_per_sm = best.ctas_per_sm;
     if (best_ms) *best_ms = best_t;
     return NRR_OK;
 }

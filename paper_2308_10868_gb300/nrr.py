@@ -37,11 +37,15 @@ class BatchView(C.Structure):
                 ("valid", C.c_void_p), ("capacity", C.c_int32)]
 
 
+class MatchShape(C.Structure):
+    _fields_ = [("ctas_per_sm", C.c_int32), ("windows", C.c_int32), ("stage", C.c_int32)]
+
+
 class Pair(C.Structure):
     _fields_ = [("d_preop", C.c_void_p), ("d_intraop", C.c_void_p), ("d_mask", C.c_void_p), ("dims", Dims)]
 
 
-NRR_BATCH_GRAPH, NRR_BATCH_AUTOTUNE, NRR_BATCH_NO_DEDUP = 1, 2, 4
+NRR_BATCH_GRAPH, NRR_BATCH_AUTOTUNE, NRR_BATCH_NO_DEDUP, NRR_BATCH_PLAIN_LAUNCH = 1, 2, 4, 8
 
 
 class Request(C.Structure):
@@ -76,6 +80,8 @@ SIGNATURES = {
     "nrr_autotune_match": (C.c_int, [_P, _P, _P, C.c_int, Dims, _P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P]),
     "nrr_tuning_get": (C.c_int, [C.c_int, _I32, _P, _P]),
     "nrr_tuning_set": (C.c_int, [C.c_int, _I32, _P, _I32]),
+    "nrr_tuning_get_shape": (C.c_int, [C.c_int, _I32, _P, _P]),
+    "nrr_tuning_set_shape": (C.c_int, [C.c_int, _I32, _P, _P]),
     "nrr_tuning_save": (C.c_int, [C.c_char_p]),
     "nrr_tuning_load": (C.c_int, [C.c_char_p]),
     "nrr_batch_create": (C.c_int, [_P, _P, _P, Dims, _P, _I32, _I32, _P]),
@@ -342,6 +348,20 @@ def tuning_set(dtype_code: int, block: int, radius, ctas_per_sm: int):
     _check(lib().nrr_tuning_set(dtype_code, block, r, ctas_per_sm), "nrr_tuning_set")
 
 
+def tuning_get_shape(dtype_code: int, block: int, radius):
+    """The tuned launch shape (ctas_per_sm, windows, stage) of a variant."""
+    r = (C.c_int32 * 3)(*radius3(radius))
+    v = MatchShape()
+    _check(lib().nrr_tuning_get_shape(dtype_code, block, r, C.byref(v)), "nrr_tuning_get_shape")
+    return int(v.ctas_per_sm), int(v.windows), int(v.stage)
+
+
+def tuning_set_shape(dtype_code: int, block: int, radius, ctas_per_sm: int, windows: int = 0, stage: int = 0):
+    r = (C.c_int32 * 3)(*radius3(radius))
+    v = MatchShape(ctas_per_sm, windows, stage)
+    _check(lib().nrr_tuning_set_shape(dtype_code, block, r, C.byref(v)), "nrr_tuning_set_shape")
+
+
 class BatchPlan:
     """A batched parameter search (see nrr_batch_create_pairs) over one uint16
     volume pair (``preop, intraop, mask``) or, with ``pairs`` a list of
@@ -350,7 +370,7 @@ class BatchPlan:
     stride, radius, frac) with radius an int or 3 ints."""
 
     def __init__(self, preop=None, intraop=None, mask=None, settings=(), graph: bool = True,
-                 autotune: bool = False, dedup: bool = True, pairs=None, pair_of=None):
+                 autotune: bool = False, dedup: bool = True, pairs=None, pair_of=None, plain_launch: bool = False):
         if pairs is None:
             pairs = [(preop, intraop, mask)]
         parr = (Pair * len(pairs))()
@@ -372,7 +392,7 @@ class BatchPlan:
             pof = (C.c_int32 * len(settings))(*[int(x) for x in pair_of])
         self.settings = list(settings)
         flags = ((NRR_BATCH_GRAPH if graph else 0) | (NRR_BATCH_AUTOTUNE if autotune else 0) |
-                 (0 if dedup else NRR_BATCH_NO_DEDUP))
+                 (0 if dedup else NRR_BATCH_NO_DEDUP) | (NRR_BATCH_PLAIN_LAUNCH if plain_launch else 0))
         h = C.c_void_p(0)
         _check(lib().nrr_batch_create_pairs(parr, len(pairs), arr, pof, len(settings), flags, C.byref(h)),
                "nrr_batch_create_pairs")

@@ -203,3 +203,27 @@ def test_batch_pairs_with_and_without_dedup_agree(nrr, uneven_pairs):
         assert _same([t.cpu().numpy() for t in a.result(i)], [t.cpu().numpy() for t in b.result(i)]), i
     a.close()
     b.close()
+
+
+def test_plain_launches_and_work_queue_agree(nrr, uneven_pairs):
+    # persistent CTAs taking blocks from the work queue (also with one CTA
+    # per SM, so each CTA takes many) against one CTA per block
+    pairs = [(p[3], p[4], p[5]) for p in uneven_pairs]
+    settings = [s for _, s in MULTI]
+    pof = [p for p, _ in MULTI]
+    ref = nrr.BatchPlan(settings=settings, pairs=pairs, pair_of=pof, graph=False, plain_launch=True)
+    ref.run()
+    torch.cuda.synchronize()
+    want = [[t.cpu().numpy() for t in ref.result(i)] for i in range(len(settings))]
+    ref.close()
+    for k in (1, 0):
+        for b, _, r, _ in settings:
+            nrr.tuning_set(0, b, r, k)
+        plan = nrr.BatchPlan(settings=settings, pairs=pairs, pair_of=pof, graph=True)
+        for rep in range(2):
+            plan.run()
+            torch.cuda.synchronize()
+            nrr.device_status()
+            for i in range(len(settings)):
+                assert _same([t.cpu().numpy() for t in plan.result(i)], want[i]), (k, rep, i)
+        plan.close()
