@@ -11,11 +11,13 @@
 // `stride` voxels apart; stride 1 for matching).  Its input brick, with the
 // b-1 halo, is brought into shared memory by TMA in z-chunks of CZ planes,
 // each completing its own mbarrier, so the first planes are summed while the
-// later ones are still in flight.  Per input plane: sums of b along x at the
-// output columns, for every row of the plane (double-buffered, so one barrier
-// per plane suffices); then sums of b of those along y at the output rows,
-// one thread per output column; the last b plane sums stay in registers and
-// at every output plane their sum is the result.
+// later ones are still in flight.  Per phase of PP input planes: sums of b
+// along x at the output columns, for every row of those planes, a few
+// outputs per thread so that the whole CTA shares the work
+// (double-buffered, so one barrier per phase suffices); then sums of b of
+// those along y at the output rows, one thread per output column; the last
+// b plane sums stay in registers and at every output plane their sum is the
+// result.
 //   uint16: exact (32-bit sums of J, 64-bit sums of J^2, running z sums);
 //           stored as S_J (int32) and v_J = N*S_JJ - S_J^2 rounded once to
 //           float (the match kernel's filter needs only an approximation
@@ -32,9 +34,10 @@ namespace {
 
 constexpr int TX = 32, MAX_TY = 8, MAX_NT = TX * MAX_TY;
 constexpr int CZ = 4;          // planes per TMA chunk
+constexpr int PP = 2;          // planes per phase (x sums of PP planes, one barrier, their y sums); divides CZ
 constexpr int MAX_CHUNKS = 8;  // so at most 32 input planes per CTA
 constexpr uint64_t BOX_WAIT_NS = 2000000000ull;
-constexpr size_t BOX_SMEM_TARGET = 110 * 1024;  // keeps two CTAs per SM
+constexpr size_t BOX_SMEM_TARGET = 112 * 1024;  // keeps two CTAs per SM
 
 // Per-element quantities summed: uint16 -> J (32-bit) and J^2 (64-bit,
 // exact); float32 -> J and J^2 in float.
@@ -80,7 +83,7 @@ __host__ __device__ inline BoxGeom box_geom(int B, int S, int TY, int ZC, int es
     g.chunk_pitch = ((size_t)g.bw * g.ih * CZ * es + 127) / 128 * 128;
     g.r_off = g.chunk_pitch * g.nchunk;
     const size_t a12 = es == 2 ? 12 : 8;  // bytes of (A1, A2) per x sum
-    g.smem = g.r_off + 2 * (size_t)g.ih * TX * a12;
+    g.smem = g.r_off + 2 * PP * (size_t)g.ih * TX * a12;
     return g;
 }
 
@@ -115,8 +118,8 @@ __global__ void __launch_bounds__(MAX_NT, (BoxMinBlocks<B, KEYS>::value)) box_ke
     __shared__ __align__(8) uint64_t bar[MAX_CHUNKS];
     const BoxGeom &g = a.g;
     const int IH = g.ih, IZ = g.iz, BW = g.bw, NT = TX * g.TY;
-    A2 *rb2 = reinterpret_cast<A2 *>(smem + g.r_off);                              // [2][IH][TX]
-    A1 *rb1 = reinterpret_cast<A1 *>(smem + g.r_off + 2 * sizeof(A2) * IH * TX);  // [2][IH][TX]
+    A2 *rb2 = reinterpret_cast<A2 *>(smem + g.r_off);                                   // [2][PP][IH][TX]
+    A1 *rb1 = reinterpret_cast<A1 *>(smem + g.r_off + 2 * PP * sizeof(A2) * IH * TX);  // [2][PP][IH][TX]
 
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
     const int i0 = blockIdx.x * TX, j0 = blockIdx.y * g.TY, k0 = blockIdx.z * g.ZC;
@@ -160,14 +163,15 @@ __global__ void __launch_bounds__(MAX_NT, (BoxMinBlocks<B, KEYS>::value)) box_ke
         }
     }
 
-    // planes in groups of B, so that ring slot u always holds the plane
-    // sums of the planes congruent to u modulo B (static register indices)
-    for (int iz0 = 0; iz0 < IZ; iz0 += B) {
+    // planes in groups of 2B, PP at a time, so that ring slot (u mod B)
+    // always holds the plane sums of the planes congruent to u modulo B
+    // (static register indices)
+    for (int iz0 = 0; iz0 < IZ; iz0 += 2 * B) {
 #pragma unroll
-    for (int u = 0; u < B; ++u) {
-        const int iz = iz0 + u;
+    for (int u = 0; u < 2 * B; u += PP) {
+        const int iz = iz0 + u;  // first plane of this phase
         if (iz >= IZ) break;
-        if (iz % CZ == 0) {
+        if (iz % CZ == 0) {  // PP divides CZ: a phase's planes share a chunk
             const bool got = mbar_wait_bounded(bar + iz / CZ, 0, BOX_WAIT_NS);
             if (!__syncthreads_and(got)) {
                 if (tid == 0) {
@@ -179,17 +183,21 @@ __global__ void __launch_bounds__(MAX_NT, (BoxMinBlocks<B, KEYS>::value)) box_ke
                 return;
             }
         }
-        const T *plane = reinterpret_cast<const T *>(smem + (iz / CZ) * g.chunk_pitch) + (iz % CZ) * IH * BW;
-        A1 *r1 = rb1 + (iz & 1) * IH * TX;
-        A2 *r2 = rb2 + (iz & 1) * IH * TX;
-        // x sums at the output columns of every row of plane iz
+        const int set = (iz / PP) & 1;
+        A1 *const r1s = rb1 + set * PP * IH * TX;
+        A2 *const r2s = rb2 + set * PP * IH * TX;
+        // x sums at the output columns of every row of planes iz .. iz+PP-1
         if constexpr (BoxQ<T>::exact) {
-            // a thread slides along 8 consecutive outputs of a row: the next
+            // a thread slides along SEG consecutive outputs of a row: the next
             // sum adds the S entering values and drops the S leaving ones
             // (modular 32/64-bit arithmetic, exact since the true sums fit)
-            constexpr int SEG = 8, NSEG = TX / SEG, NV = (SEG - 1) * S + B;
-            for (int it = tid; it < IH * NSEG; it += NT) {
-                const int seg = it % NSEG, iy = it / NSEG;
+            constexpr int SEG = 4, NSEG = TX / SEG, NV = (SEG - 1) * S + B;
+            for (int it = tid; it < PP * IH * NSEG; it += NT) {
+                const int pl = it / (IH * NSEG), rem = it - pl * (IH * NSEG);
+                const int seg = rem % NSEG, iy = rem / NSEG;
+                if (iz + pl >= IZ) continue;
+                const T *plane = reinterpret_cast<const T *>(smem + ((iz + pl) / CZ) * g.chunk_pitch) +
+                                 ((iz + pl) % CZ) * IH * BW;
                 const T *src = plane + iy * BW + g.xoff + seg * SEG * S;
                 uint32_t v[NV], sq[NV];
 #pragma unroll
@@ -216,16 +224,19 @@ __global__ void __launch_bounds__(MAX_NT, (BoxMinBlocks<B, KEYS>::value)) box_ke
                     o1[i] = a1;
                     o2[i] = a2;
                 }
-                uint4 *d1 = reinterpret_cast<uint4 *>(r1 + iy * TX + seg * SEG);  // 16-byte aligned
-                d1[0] = make_uint4(o1[0], o1[1], o1[2], o1[3]);
-                d1[1] = make_uint4(o1[4], o1[5], o1[6], o1[7]);
-                ulonglong2 *d2 = reinterpret_cast<ulonglong2 *>(r2 + iy * TX + seg * SEG);
-#pragma unroll
-                for (int q = 0; q < SEG / 2; ++q) d2[q] = make_ulonglong2(o2[2 * q], o2[2 * q + 1]);
+                const int o = (pl * IH + iy) * TX + seg * SEG;
+                *reinterpret_cast<uint4 *>(r1s + o) = make_uint4(o1[0], o1[1], o1[2], o1[3]);  // 16-byte aligned
+                ulonglong2 *d2 = reinterpret_cast<ulonglong2 *>(r2s + o);
+                d2[0] = make_ulonglong2(o2[0], o2[1]);
+                d2[1] = make_ulonglong2(o2[2], o2[3]);
             }
         } else {  // float: every x sum a direct b-term sum (fixed depth)
-            for (int it = tid; it < IH * TX; it += NT) {
-                const int ox = it % TX, iy = it / TX;
+            for (int it = tid; it < PP * IH * TX; it += NT) {
+                const int pl = it / (IH * TX), rem = it - pl * (IH * TX);
+                const int ox = rem % TX, iy = rem / TX;
+                if (iz + pl >= IZ) continue;
+                const T *plane = reinterpret_cast<const T *>(smem + ((iz + pl) / CZ) * g.chunk_pitch) +
+                                 ((iz + pl) % CZ) * IH * BW;
                 const T *src = plane + iy * BW + g.xoff + ox * S;
                 A1 a1 = 0;
                 A2 a2 = 0;
@@ -235,65 +246,73 @@ __global__ void __launch_bounds__(MAX_NT, (BoxMinBlocks<B, KEYS>::value)) box_ke
                     a1 += v;
                     a2 += __fmul_rn(v, v);
                 }
-                r1[iy * TX + ox] = a1;
-                r2[iy * TX + ox] = a2;
+                r1s[(pl * IH + iy) * TX + ox] = a1;
+                r2s[(pl * IH + iy) * TX + ox] = a2;
             }
         }
-        __syncthreads();  // x sums of plane iz ready (and plane iz-2's buffer is free)
-        A1 p1 = 0;
-        A2 p2 = 0;
+        __syncthreads();  // x sums of this phase ready (and the phase before last's buffers are free)
 #pragma unroll
-        for (int k = 0; k < B; ++k) {
-            p1 += r1[(ty * S + k) * TX + tx];
-            p2 += r2[(ty * S + k) * TX + tx];
-        }
-        if constexpr (BoxQ<T>::exact) {  // slot u held plane iz - B
-            run1 += p1 - ring1[u];
-            run2 += p2 - ring2[u];
-        }
-        ring1[u] = p1;
-        ring2[u] = p2;
-        // the ring now holds input planes iz-B+1..iz: an output plane when
-        // they are the planes of local output kk
-        const int q = iz - (B - 1);
-        if (q < 0 || q % S) continue;
-        const int kk = q / S, k = k0 + kk;
-        if (kk >= g.ZC || k >= a.gz || i >= a.gx || j >= a.gy) continue;
-        A1 o1;
-        A2 o2;
-        if constexpr (BoxQ<T>::exact) {
-            o1 = run1;
-            o2 = run2;
-        } else {  // a direct sum of the b plane sums (fixed depth b)
-            o1 = 0;
-            o2 = 0;
+        for (int pl = 0; pl < PP; ++pl) {
+            const int izp = iz + pl;
+            if (izp >= IZ) break;
+            const int slot = (u + pl) % B;
+            const A1 *r1 = r1s + pl * IH * TX;
+            const A2 *r2 = r2s + pl * IH * TX;
+            A1 p1 = 0;
+            A2 p2 = 0;
 #pragma unroll
-            for (int t = 0; t < B; ++t) {
-                o1 += ring1[t];
-                o2 += ring2[t];
+            for (int k = 0; k < B; ++k) {
+                p1 += r1[(ty * S + k) * TX + tx];
+                p2 += r2[(ty * S + k) * TX + tx];
             }
-        }
-        const int x = i * S, y = j * S, z = k * S;
-        const bool in = x >= H && x <= a.nx - 1 - H && y >= H && y <= a.ny - 1 - H && z >= H && z <= a.nz - 1 - H;
-        if constexpr (KEYS) {
-            long long key = -1;
-            if (in && ((mbits >> kk) & 1u)) {
-                key = N * (long long)o2 - (long long)o1 * (long long)o1;
-                cand += 1;
-                pos += key > 0;
-                kmax = (unsigned long long)key > kmax ? (unsigned long long)key : kmax;
+            if constexpr (BoxQ<T>::exact) {  // the slot held plane izp - B
+                run1 += p1 - ring1[slot];
+                run2 += p2 - ring2[slot];
             }
-            a.keys[((long long)k * a.gy + j) * a.gx + i] = key;
-        } else {
-            const size_t idx = ((size_t)z * a.ny + y) * a.nx + x;
+            ring1[slot] = p1;
+            ring2[slot] = p2;
+            // the ring now holds input planes izp-B+1..izp: an output plane
+            // when they are the planes of local output kk
+            const int q = izp - (B - 1);
+            if (q < 0 || q % S) continue;
+            const int kk = q / S, k = k0 + kk;
+            if (kk >= g.ZC || k >= a.gz || i >= a.gx || j >= a.gy) continue;
+            A1 o1;
+            A2 o2;
             if constexpr (BoxQ<T>::exact) {
-                reinterpret_cast<int32_t *>(a.out1)[idx] = in ? (int32_t)o1 : 0;
-                // v_J = N*S_JJ - S_J^2 (exact in 64 bits), rounded once to float
-                reinterpret_cast<float *>(a.out2)[idx] =
-                    in ? __ll2float_rn(N * (long long)o2 - (long long)o1 * (long long)o1) : 0.f;
+                o1 = run1;
+                o2 = run2;
+            } else {  // a direct sum of the b plane sums (fixed depth b)
+                o1 = 0;
+                o2 = 0;
+#pragma unroll
+                for (int t = 0; t < B; ++t) {
+                    o1 += ring1[t];
+                    o2 += ring2[t];
+                }
+            }
+            const int x = i * S, y = j * S, z = k * S;
+            const bool in = x >= H && x <= a.nx - 1 - H && y >= H && y <= a.ny - 1 - H && z >= H && z <= a.nz - 1 - H;
+            if constexpr (KEYS) {
+                long long key = -1;
+                if (in && ((mbits >> kk) & 1u)) {
+                    key = N * (long long)o2 - (long long)o1 * (long long)o1;
+                    cand += 1;
+                    pos += key > 0;
+                    kmax = (unsigned long long)key > kmax ? (unsigned long long)key : kmax;
+                }
+                a.keys[((long long)k * a.gy + j) * a.gx + i] = key;
             } else {
-                reinterpret_cast<float *>(a.out1)[idx] = in ? (float)o1 : 0.f;
-                reinterpret_cast<float *>(a.out2)[idx] = in ? (float)o2 : 0.f;
+                const size_t idx = ((size_t)z * a.ny + y) * a.nx + x;
+                if constexpr (BoxQ<T>::exact) {
+                    reinterpret_cast<int32_t *>(a.out1)[idx] = in ? (int32_t)o1 : 0;
+                    // v_J = N*S_JJ - S_J^2 (exact in 64 bits), rounded once to float
+                    reinterpret_cast<float *>(a.out2)[idx] =
+                        in ? __ll2float_rn(N * (long long)o2 - (long long)o1 * (long long)o1) : 0.f;
+                } else {
+                    reinterpret_cast<float *>(a.out1)[idx] = in ? (float)o1 : 0.f;
+                    reinterpret_cast<float *>(a.out2)[idx] = in ? (float)o2 : 0.f;
+                }
             }
         }
     }
