@@ -385,8 +385,9 @@ def _serving(a, nrr, synth, dev):
     fraction); volumes resident on the device.  Reports p50/p99 latency
     (submission to completion on the device) and registrations/s, the same
     for arrival rates from 100 to 1600 requests/s, and a saturation run (all
-    requests queued at once) served with 8 slots against one-at-a-time FIFO
-    service (1 slot)."""
+    requests queued at once) served with 8 slots (same-variant requests
+    grouped into one match launch, and without grouping) against
+    one-at-a-time FIFO service (1 slot, no grouping)."""
     import numpy as np
     import torch
 
@@ -396,8 +397,8 @@ def _serving(a, nrr, synth, dev):
         pool.append((nrr.to_device_u16(pre, dev), nrr.to_device_u16(intra, dev), torch.from_numpy(mask).to(dev)))
     torch.cuda.synchronize()
 
-    def run(reqs, slots, open_loop, lone=False, arrays=None):
-        srv = nrr.Server(slots=slots, reserve_bytes=2 << 30)
+    def run(reqs, slots, open_loop, lone=False, arrays=None, max_group=16):
+        srv = nrr.Server(slots=slots, reserve_bytes=2 << 30, max_group=max_group)
         try:
             # warm the kernels of every variant used, outside the measurement
             t0 = time.perf_counter()
@@ -467,7 +468,8 @@ def _serving(a, nrr, synth, dev):
     reqs_closed = [(0.0, si, b, r, f) for (_, si, b, r, f) in synth.poisson_arrivals(a.serve_closed_requests, 20.0,
                                                                                       seed=synth.SEED_BASE + 11)]
     out["saturated_served_8_slots"] = run(reqs_closed, 8, False)
-    out["saturated_fifo_1_slot"] = run(reqs_closed, 1, False)
+    out["saturated_8_slots_no_grouping"] = run(reqs_closed, 8, False, max_group=1)
+    out["saturated_fifo_1_slot"] = run(reqs_closed, 1, False, max_group=1)
     out["saturated_speedup"] = (out["saturated_served_8_slots"]["registrations_per_s"] /
                                 out["saturated_fifo_1_slot"]["registrations_per_s"])
     return out

@@ -443,7 +443,9 @@ nrr_status nrr_batch_destroy(nrr_batch plan);
  * request's scratch and result buffers (available: the device's free memory
  * plus what the library's request pool holds mapped but unused; the pool
  * keeps the memory it maps for the rest of the process, for later requests
- * and servers); admitted requests run
+ * and servers); queued requests of the same dtype, block and radius as an
+ * admitted one join it (up to 16: each runs its own selection and box sums,
+ * one match launch holds all their jobs); admitted requests run
  * concurrently (their kernels overlap on the device) and a new one starts
  * as soon as an earlier one finishes.  Each request runs selection (on
  * d_select), box sums and matching exactly as the synchronous calls do, so
@@ -485,6 +487,9 @@ typedef struct {
 } nrr_result;
 
 nrr_status nrr_server_start(int32_t slots, size_t reserve_bytes);
+/* As nrr_server_start with at most max_group (1..16) requests per match
+ * launch (nrr_server_start: 16; 1: every request on its own). */
+nrr_status nrr_server_start_ex(int32_t slots, size_t reserve_bytes, int32_t max_group);
 nrr_status nrr_server_stop(void);
 nrr_status nrr_submit(const nrr_request *req, uint64_t *ticket);
 nrr_status nrr_poll(uint64_t ticket, nrr_result *out);

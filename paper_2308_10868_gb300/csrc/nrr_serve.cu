@@ -10,9 +10,14 @@
 //     returns a ticket at once;
 //   - the scheduler admits queued requests in arrival order whenever a slot
 //     is free and the free device memory, less a reserve, covers the
-//     request's scratch and result buffers; several admitted requests run
-//     at the same time on different streams, so their kernels overlap on the
-//     device, and a new request starts as soon as any earlier one finishes;
+//     request's scratch and result buffers; queued requests of the same
+//     variant (dtype, block, radius) as the admitted one join it, up to 16:
+//     each runs its own selection and box sums, and one match launch holds
+//     all their jobs (each with its own volumes, sizes and tensor maps), so
+//     a busy queue of small requests fills the GPU with one launch instead
+//     of many partly filled ones; several admitted groups run at the same
+//     time on different streams, so their kernels overlap on the device,
+//     and a new group starts as soon as any earlier one finishes;
 //   - each request runs the whole path (selection with a device-side count,
 //     box sums, matching) on its slot stream, then a host callback stamps
 //     its completion time and wakes the scheduler, which admits the next
@@ -75,9 +80,10 @@ struct Server {
     int device = 0;
     int nslots = 0;
     size_t reserve = 0;
+    int max_group = MATCH_MAX_JOBS;  // requests per match launch
     size_t max_queue = 65536;
     std::vector<cudaStream_t> slots;
-    std::vector<uint64_t> slot_req;  // 0 = free
+    std::vector<std::vector<uint64_t>> slot_req;  // tickets running on each slot (empty = free)
     std::deque<uint64_t> queue;
     std::unordered_map<uint64_t, Req *> reqs;
     std::mutex mu;
@@ -95,7 +101,7 @@ Server *g_server = nullptr;
 
 struct Layout {
     SelectPlan sp;
-    size_t off_ws, off_box, off_centers, off_n, off_disp, off_ncc, off_valid, total;
+    size_t off_ws, off_box, off_centers, off_n, off_disp, off_ncc, off_valid, off_maps, total;
     int32_t cap;
 };
 
@@ -121,6 +127,8 @@ Layout layout_of(const nrr_request &r)
     o += align_up((size_t)L.cap * 8, 256);
     L.off_valid = o;
     o += align_up((size_t)L.cap, 256);
+    L.off_maps = o;  // the request's two tensor maps when it joins another's launch
+    o += 256;
     L.total = o;
     return L;
 }
@@ -182,33 +190,35 @@ size_t available_bytes(cudaMemPool_t pool)
     return fr;
 }
 
-// Admit request q on slot k (server lock held).  Returns false if memory is
-// short right now (q stays queued).
-bool admit(Server *S, Req *q, int k)
+// Prepare request q on slot k (server lock held): its memory, then its
+// selection and box sums on the slot's stream; `follower` (it joins the
+// launch of an earlier request of the same variant) also gets its tensor
+// maps copied to its memory.  Fills its match job.  Returns 0 if memory is
+// short right now (q stays queued), 1 if prepared, 2 if it failed (its
+// status is set; nothing of it is left running).
+int prepare(Server *S, Req *q, int k, bool follower, MatchJob *job)
 {
     const nrr_request &r = q->r;
     const Layout L = layout_of(r);
     const size_t fr = available_bytes(S->pool);
     if (fr < L.total + S->reserve) {
-        bool busy = false;
-        for (uint64_t t : S->slot_req) busy |= t != 0;
-        if (busy) return false;  // wait for running requests to free memory
+        bool busy = follower;
+        for (auto &v : S->slot_req) busy |= !v.empty();
+        if (busy) return 0;  // wait for running requests to free memory
         q->status = fail(NRR_E_NOMEM, "request needs %zu bytes, %zu free", L.total, fr);
         q->state = FAILED;  // would never fit
-        return true;
+        return 2;
     }
     cudaStream_t s = S->slots[k];
     q->slot = k;
     q->t_admit = now_s();
     q->state = RUNNING;
-    S->slot_req[k] = q->ticket;
     cudaError_t e = fault("alloc") ? cudaErrorMemoryAllocation : cudaMallocFromPoolAsync(&q->mem, L.total, S->pool, s);
     if (e != cudaSuccess) {
         q->mem = nullptr;
         q->status = cuda_fail(e, "request allocation");
         q->state = FAILED;
-        S->slot_req[k] = 0;
-        return true;
+        return 2;
     }
     unsigned char *m = (unsigned char *)q->mem;
     q->bytes = L.total;
@@ -221,31 +231,105 @@ bool admit(Server *S, Req *q, int k)
     nrr_status st = enqueue_select(r.d_select, r.d_mask, r.dims, r.block, r.stride, r.frac,
                                    q->centers, q->cap, q->d_n, m + L.off_ws, L.sp, s);
     if (st == NRR_OK) st = launch_boxsums(r.d_intraop, r.dtype, r.dims, r.block, m + L.off_box, s);
-    if (st == NRR_OK) {
-        MatchLaunch a{};
-        a.preop = r.d_preop;
-        a.intraop = r.d_intraop;
-        a.s1 = m + L.off_box;
-        a.s2 = m + L.off_box + boxsum_s2_offset(r.dims, r.dtype);
-        a.dtype = r.dtype;
-        a.dims = r.dims;
-        a.block = r.block;
-        for (int i = 0; i < 3; ++i) a.radius[i] = r.radius[i];
-        a.n_jobs = 1;
-        a.jobs[0] = MatchJob{q->centers, q->d_n, q->cap, q->disp, q->ncc, q->valid};
-        apply_tuning(a, r.dtype, r.block, r.radius);
-        a.err = S->err;
-        st = launch_match(a, s);
+    *job = MatchJob{q->centers, q->d_n, q->cap, q->disp, q->ncc, q->valid};
+    job->preop = r.d_preop;
+    job->intraop = r.d_intraop;
+    job->s1 = m + L.off_box;
+    job->s2 = m + L.off_box + boxsum_s2_offset(r.dims, r.dtype);
+    job->nx = r.dims.nx;
+    job->ny = r.dims.ny;
+    job->nz = r.dims.nz;
+    if (st == NRR_OK && follower) {
+        CUtensorMap maps[2];
+        int wb[3], tb[3];
+        match_boxes(r.dtype, r.block, r.block, r.block, r.radius, wb, tb);
+        st = encode_volume_map(&maps[0], r.d_intraop, r.dtype, r.dims, wb[0], wb[1], wb[2]);
+        if (st == NRR_OK) st = encode_volume_map(&maps[1], r.d_preop, r.dtype, r.dims, tb[0], tb[1], tb[2]);
+        if (st == NRR_OK && cudaMemcpyAsync(m + L.off_maps, maps, sizeof maps, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            st = fail(NRR_E_CUDA, "tensor map copy");
+        job->mapJ = reinterpret_cast<const CUtensorMap *>(m + L.off_maps);
+        job->mapI = job->mapJ + 1;
     }
-    if (st == NRR_OK && cudaLaunchHostFunc(s, on_done, q) != cudaSuccess) st = fail(NRR_E_CUDA, "host callback");
     if (st != NRR_OK) {
         q->status = st;
         q->state = FAILED;
         cudaStreamSynchronize(s);  // nothing of this request may still run
         cudaFreeAsync(q->mem, s);
         q->mem = nullptr;
-        S->slot_req[k] = 0;
+        return 2;
     }
+    return 1;
+}
+
+bool same_variant(const nrr_request &a, const nrr_request &b)
+{
+    return a.dtype == b.dtype && a.block == b.block && a.radius[0] == b.radius[0] && a.radius[1] == b.radius[1] &&
+           a.radius[2] == b.radius[2];
+}
+
+// Admit the request at the queue's front on free slot k, with queued
+// requests of the same variant (dtype, block, radius) behind it, up to
+// MATCH_MAX_JOBS in all: each runs its own selection and box sums on the
+// slot's stream, then one match launch holds all their jobs (server lock
+// held).  Returns false if the front request must wait for memory.
+bool admit_group(Server *S, int k)
+{
+    const uint64_t t0 = S->queue.front();
+    Req *q0 = S->reqs[t0];
+    MatchJob jobs[MATCH_MAX_JOBS];
+    std::vector<Req *> group;
+    const int r0 = prepare(S, q0, k, false, &jobs[0]);
+    if (r0 == 0) return false;
+    S->queue.pop_front();
+    if (r0 == 2) return true;
+    group.push_back(q0);
+    // followers: the next same-variant requests among the first queued ones
+    constexpr size_t SCAN = 64;
+    for (size_t pos = 0; pos < S->queue.size() && pos < SCAN && group.size() < (size_t)S->max_group;) {
+        auto it = S->reqs.find(S->queue[pos]);
+        if (it == S->reqs.end()) {  // released while queued
+            S->queue.erase(S->queue.begin() + pos);
+            continue;
+        }
+        Req *q = it->second;
+        if (!same_variant(q->r, q0->r)) {
+            ++pos;
+            continue;
+        }
+        const int r = prepare(S, q, k, true, &jobs[group.size()]);
+        if (r == 0) break;
+        S->queue.erase(S->queue.begin() + pos);
+        if (r == 1) group.push_back(q);
+    }
+    const nrr_request &r = q0->r;
+    MatchLaunch a{};
+    a.preop = r.d_preop;
+    a.intraop = r.d_intraop;
+    a.s1 = jobs[0].s1;
+    a.s2 = jobs[0].s2;
+    a.dtype = r.dtype;
+    a.dims = r.dims;
+    a.block = r.block;
+    for (int i = 0; i < 3; ++i) a.radius[i] = r.radius[i];
+    a.n_jobs = (int)group.size();
+    for (size_t g = 0; g < group.size(); ++g) a.jobs[g] = jobs[g];
+    apply_tuning(a, r.dtype, r.block, r.radius);
+    a.err = S->err;
+    cudaStream_t s = S->slots[k];
+    nrr_status st = launch_match(a, s);
+    for (size_t g = 0; g < group.size() && st == NRR_OK; ++g)
+        if (cudaLaunchHostFunc(s, on_done, group[g]) != cudaSuccess) st = fail(NRR_E_CUDA, "host callback");
+    if (st != NRR_OK) {
+        cudaStreamSynchronize(s);  // nothing of these requests may still run
+        for (Req *q : group) {
+            q->status = st;
+            q->state = FAILED;
+            cudaFreeAsync(q->mem, s);
+            q->mem = nullptr;
+        }
+        return true;
+    }
+    for (Req *q : group) S->slot_req[k].push_back(q->ticket);
     return true;
 }
 
@@ -255,40 +339,36 @@ void worker_main(Server *S)
     std::unique_lock<std::mutex> lk(S->mu);
     while (!S->stop) {
         const unsigned long long seen = S->events.load();
-        // retire finished requests, freeing their slots
+        // retire finished requests; a slot is free once all of its are
         for (int k = 0; k < S->nslots; ++k) {
-            uint64_t t = S->slot_req[k];
-            if (!t) continue;
-            auto it = S->reqs.find(t);
-            if (it == S->reqs.end()) {
-                S->slot_req[k] = 0;
-                continue;
-            }
-            Req *q = it->second;
-            if (q->finished.load()) {
-                q->state = DONE;
-                S->slot_req[k] = 0;
+            auto &v = S->slot_req[k];
+            for (size_t i = 0; i < v.size();) {
+                auto it = S->reqs.find(v[i]);
+                if (it != S->reqs.end() && !it->second->finished.load()) {
+                    ++i;
+                    continue;
+                }
+                if (it != S->reqs.end()) it->second->state = DONE;
+                v.erase(v.begin() + i);
                 S->cv.notify_all();
             }
         }
-        // admit in arrival order while slots and memory allow
+        // admit in arrival order (with same-variant followers) while slots
+        // and memory allow
         bool progressed = false;
         while (!S->queue.empty()) {
             int k = -1;
             for (int i = 0; i < S->nslots; ++i)
-                if (!S->slot_req[i]) {
+                if (S->slot_req[i].empty()) {
                     k = i;
                     break;
                 }
             if (k < 0) break;
-            const uint64_t t = S->queue.front();
-            auto it = S->reqs.find(t);
-            if (it == S->reqs.end()) {  // released while queued
+            if (S->reqs.find(S->queue.front()) == S->reqs.end()) {  // released while queued
                 S->queue.pop_front();
                 continue;
             }
-            if (!admit(S, it->second, k)) break;
-            S->queue.pop_front();
+            if (!admit_group(S, k)) break;
             progressed = true;
         }
         if (progressed) S->cv.notify_all();
@@ -307,8 +387,14 @@ extern "C" {
 
 nrr_status nrr_server_start(int32_t slots, size_t reserve_bytes)
 {
+    return nrr_server_start_ex(slots, reserve_bytes, MATCH_MAX_JOBS);
+}
+
+nrr_status nrr_server_start_ex(int32_t slots, size_t reserve_bytes, int32_t max_group)
+{
     clear_error();
     if (slots < 1 || slots > 64) return fail(NRR_E_INVALID, "slots must be 1..64");
+    if (max_group < 1 || max_group > MATCH_MAX_JOBS) return fail(NRR_E_INVALID, "max_group must be 1..%d", MATCH_MAX_JOBS);
     std::lock_guard<std::mutex> g(g_server_mu);
     if (g_server) return fail(NRR_E_INVALID, "server already running");
     Server *S = new Server();
@@ -328,8 +414,9 @@ nrr_status nrr_server_start(int32_t slots, size_t reserve_bytes)
     }
     S->nslots = slots;
     S->reserve = reserve_bytes;
+    S->max_group = max_group;
     S->slots.resize(slots);
-    S->slot_req.assign(slots, 0);
+    S->slot_req.assign(slots, std::vector<uint64_t>());
     for (int k = 0; k < slots; ++k) {
         if (cudaStreamCreateWithFlags(&S->slots[k], cudaStreamNonBlocking) != cudaSuccess) {
             for (int j = 0; j < k; ++j) cudaStreamDestroy(S->slots[j]);

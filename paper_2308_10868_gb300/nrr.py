@@ -90,6 +90,7 @@ SIGNATURES = {
     "nrr_batch_view_get": (C.c_int, [_P, _I32, _P]),
     "nrr_batch_destroy": (C.c_int, [_P]),
     "nrr_server_start": (C.c_int, [_I32, C.c_size_t]),
+    "nrr_server_start_ex": (C.c_int, [_I32, C.c_size_t, _I32]),
     "nrr_server_stop": (C.c_int, []),
     "nrr_submit": (C.c_int, [_P, _P]),
     "nrr_poll": (C.c_int, [C.c_uint64, _P]),
@@ -432,8 +433,8 @@ class Server:
     """Registration server with continuous batching (see nrr_server_start).
     Volumes passed to submit() must stay alive until the request is done."""
 
-    def __init__(self, slots: int = 8, reserve_bytes: int = 1 << 30):
-        _check(lib().nrr_server_start(slots, reserve_bytes), "nrr_server_start")
+    def __init__(self, slots: int = 8, reserve_bytes: int = 1 << 30, max_group: int = 16):
+        _check(lib().nrr_server_start_ex(slots, reserve_bytes, max_group), "nrr_server_start_ex")
         self._live = {}
 
     def submit(self, preop, intraop, mask, block: int, stride: int, radius, frac: float, select=None) -> int:

@@ -103,6 +103,8 @@ def test_serving_and_batch_arguments_need_no_device(L):
     assert b"no server" in L.nrr_last_error()
     assert L.nrr_poll(1, None) == -1 and L.nrr_release(1) == -1
     assert L.nrr_server_start(0, 0) == -1
+    assert L.nrr_server_start_ex(1, 0, 0) == -1 and L.nrr_server_start_ex(1, 0, 17) == -1
+    assert b"max_group" in L.nrr_last_error()
     s = (nrr.Setting * 1)()
     s[0].block, s[0].stride, s[0].frac = 6, 2, 0.1
     h = C.c_void_p(0)

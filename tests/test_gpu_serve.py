@@ -152,3 +152,37 @@ def test_server_lifecycle_errors(nrr):
         assert ei.value.status == -7
     finally:
         srv.stop()
+
+
+def test_queued_same_variant_requests_share_a_launch(nrr):
+    # one slot and a burst of same-variant requests on volumes of three
+    # sizes: the ones queued behind a running group join one match launch
+    # (each job with its own volumes and maps); every result must equal the
+    # same registration run alone, and the oracle
+    host = []
+    pairs = _pairs(nrr, host)
+    reqs = [(k % 3, 7, 3, (0.02, 0.05, 0.08)[(k // 3) % 3], k % 4 == 3) for k in range(14)]
+    srv = nrr.Server(slots=1, reserve_bytes=0)
+    try:
+        tickets = []
+        for p, b, r, f, f32 in reqs:
+            dp, di, dm, fp, fi = pairs[p]
+            tickets.append(srv.submit(fp, fi, dm, b, 2, r, f, select=dp) if f32 else srv.submit(dp, di, dm, b, 2, r, f))
+        res = _wait(srv, tickets)
+        for t, (p, b, r, f, f32) in zip(tickets, reqs):
+            dp, di, dm, fp, fi = pairs[p]
+            c = nrr.select_blocks(dp, dm, b, 2, f)
+            d, n, v = nrr.block_match(fp if f32 else dp, fi if f32 else di, c, b, r)
+            got = res[t]
+            assert torch.equal(got["centers"], c) and torch.equal(got["disp"], d) and torch.equal(got["valid"], v)
+            g, e = got["ncc"].cpu().numpy(), n.cpu().numpy()
+            assert np.array_equal(g.view(np.uint64), e.view(np.uint64))
+            srv.release(t)
+        for i in (1, 2):
+            p, b, r, f, f32 = reqs[i]
+            dp, di, dm, fp, fi = pairs[p]
+            c = nrr.select_blocks(dp, dm, b, 2, f)
+            d, n, v = nrr.block_match(dp, di, c, b, r)
+            _check_oracle(*host[p], b, r, f, False, {"centers": c, "disp": d, "ncc": n, "valid": v})
+    finally:
+        srv.stop()
