@@ -478,8 +478,9 @@ def _serving(a, nrr, synth, dev):
 def _highres(a, nrr, synth, dev, flush):
     """The high-resolution variant: 512x512x256, block 9^3, stride 3, top 5%,
     radius 7 (3375 shifts), as uint16 (exact path) and as float32 u/65535
-    (FP32 search, FP64 rescoring).  Their agreement with the oracle is checked
-    by tests/test_gpu_highres.py, not here."""
+    (FP32 search, FP64 rescoring), and as float32 on an offset of 100.  Their agreement with the oracle is checked by
+    tests/test_gpu_highres.py and tests/test_gpu_parity.py, not here."""
+    import numpy as np
     import torch
 
     w = synth.WORKLOADS["highres"]
@@ -493,7 +494,18 @@ def _highres(a, nrr, synth, dev, flush):
     n = centers.shape[0]
     evals = n * (2 * w.radius + 1) ** 3
     out = {"workload": w.name, "n_blocks": n, "shifts": (2 * w.radius + 1) ** 3, "evals": evals}
-    for name, (p, i) in (("u16", (dpre, dintra)), ("f32", (fpre, fintra))):
+    # float32 on a large offset: 100 + u/65535 (a block's spread is 10^-2 to
+    # 10^-4 of the intensity range, so the offset is 10^4 to 10^6 times it),
+    # which the centred float box sums keep boundable; the float spacing at
+    # 100 (2^-17) still resolves every uint16 step (about 2^-16)
+    opre = torch.from_numpy((np.float32(100.0) + p32).astype(np.float32)).to(dev)
+    ointra = torch.from_numpy((np.float32(100.0) + i32).astype(np.float32)).to(dev)
+    # the same with the reference volume's centre voxel set to 0: c = 0, so
+    # the box sums are the plain sums of J and J^2 (what centring removes)
+    zintra = ointra.clone()
+    zintra[zintra.shape[0] // 2, zintra.shape[1] // 2, zintra.shape[2] // 2] = 0.0
+    for name, (p, i) in (("u16", (dpre, dintra)), ("f32", (fpre, fintra)), ("f32_offset", (opre, ointra)),
+                         ("f32_offset_sums_uncentred", (opre, zintra))):
         box = nrr.boxsums(i, w.block)
         res = nrr.block_match(p, i, centers, w.block, w.radius, box=box)
         ts = []

@@ -199,11 +199,15 @@ nrr_status nrr_select_blocks_noalloc(const uint16_t *d_preop, const uint8_t *d_m
 /* ------------------------------------------------------------------------
  * Box sums of the reference image, from the per-shift sums S_J and S_JJ of
  * the NCC (Sec. 3): for every voxel v whose b^3 block lies in the volume,
- *   S1[v] = sum of J over the block centred at v,
+ *   S1[v] = uint16:  sum of J over the block centred at v,
+ *           float32: sum of (J - c) over the block, c = J at the volume's
+ *                    centre voxel (nx/2, ny/2, nz/2), each J - c rounded
+ *                    once (so that the sums keep a block's spread even on
+ *                    a large intensity offset),
  *   A2[v] = uint16:  N * (sum of J^2) - S1[v]^2  (N = b^3; exact in 64 bits,
  *                    then rounded once to float32: N^2 times the block's
  *                    variance),
- *           float32: sum of J^2 over the block.
+ *           float32: sum of (J - c)^2 over the block.
  * uint16: S1 is int32 (exact), A2 float32.  float32: both float32.
  * Layout of d_boxsums: S1 as [nz][ny][nx] elements, then A2 as [nz][ny][nx]
  * elements starting at the next 256-byte boundary (8 bytes per voxel in

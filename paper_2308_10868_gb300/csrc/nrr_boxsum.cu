@@ -22,8 +22,10 @@
 //           stored as S_J (int32) and v_J = N*S_JJ - S_J^2 rounded once to
 //           float (the match kernel's filter needs only an approximation
 //           of v_J, and its exact rescoring recomputes the sums).
-//   float32: float sums whose every output is three levels of b-term sums;
-//            the match kernel's error bound relies on that shape.
+//   float32: float sums of J - c (c the volume's centre value; the
+//            difference rounded once) whose every output is three levels
+//            of b-term sums; the match kernel's error bound relies on that
+//            shape.
 #include <stddef.h>
 
 #include "nrr_internal.h"
@@ -93,6 +95,7 @@ struct BoxArgs {
     int gx, gy, gz;  // outputs per axis (grid points for keys, voxels for box sums)
     // box sums
     void *out1, *out2;
+    const float *centre;  // float32: the volume's centre voxel, c of the sums of J - c
     // keys
     const uint8_t *mask;
     long long *keys;
@@ -138,6 +141,8 @@ __global__ void __launch_bounds__(MAX_NT, (BoxMinBlocks<B, KEYS>::value)) box_ke
     }
 
     const int i = i0 + tx, j = j0 + ty;  // this thread's output column
+    float cval = 0.f;  // float32: the sums are of J - c
+    if constexpr (!BoxQ<T>::exact) cval = *a.centre;
     A1 ring1[B];
     A2 ring2[B];
     A1 run1 = 0;  // exact path: running sums of the ring
@@ -242,7 +247,7 @@ __global__ void __launch_bounds__(MAX_NT, (BoxMinBlocks<B, KEYS>::value)) box_ke
                 A2 a2 = 0;
 #pragma unroll
                 for (int k = 0; k < B; ++k) {
-                    const T v = src[k];
+                    const float v = __fsub_rn((float)src[k], cval);
                     a1 += v;
                     a2 += __fmul_rn(v, v);
                 }
@@ -417,6 +422,7 @@ nrr_status launch_boxsums(const void *d_intraop, nrr_dtype dtype, nrr_dims dims,
     a.nz = a.gz = dims.nz;
     a.out1 = d_boxsums;
     a.out2 = (char *)d_boxsums + boxsum_s2_offset(dims, dtype);
+    a.centre = (const float *)d_intraop + volume_centre_index(dims.nx, dims.ny, dims.nz);
     nrr_status s = device_error_word(&a.err);
     if (s != NRR_OK) return s;
     CUtensorMap map;

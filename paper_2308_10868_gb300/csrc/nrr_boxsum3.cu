@@ -1,7 +1,7 @@
 // Box sums of the reference volume for blocks with a different edge per axis
 // (bx, by, bz): S_J = sum J and, for uint16, v_J = N S_JJ - S_J^2 (N =
 // bx by bz, exact in 64-bit integers, rounded once to float), for float32
-// S_J and S_JJ in float.  Same output layout as the cubic box kernel: the
+// the sums of J - c and (J - c)^2 in float (c the volume's centre value).  Same output layout as the cubic box kernel: the
 // first array (int32 or float) at offset 0, the second (float) at
 // boxsum_s2_offset.  Values are written where the whole block fits in the
 // volume and are zero elsewhere (the match kernel reads only the former).
@@ -9,8 +9,9 @@
 // Three separable passes over the volume (x, then y, then z), one thread per
 // voxel, coalesced along x; the first two write their partial sums to a
 // scratch buffer.  The summation along each axis is sequential, so a float32
-// sum carries at most bx + by + bz roundings per term, the depth the match
-// kernel's error bound assumes.
+// sum carries at most bx + by + bz roundings per term besides the rounding
+// of J - c and of its square, the depth the match kernel's error bound
+// assumes.
 #include "nrr_internal.h"
 
 namespace nrr {
@@ -67,14 +68,16 @@ __global__ void __launch_bounds__(P3_THREADS) box3_u16_yz(const uint32_t *__rest
 
 // float32: x pass from the volume
 __global__ void __launch_bounds__(P3_THREADS) box3_f32_x(const float *__restrict__ vol, int nx, long long nvox, int h,
-                                                         float *__restrict__ s, float *__restrict__ q)
+                                                         const float *__restrict__ centre, float *__restrict__ s,
+                                                         float *__restrict__ q)
 {
+    const float c = *centre;  // the sums are of J - c
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(v % nx);
         float a = 0.f, b = 0.f;
         if (x >= h && x <= nx - 1 - h)
             for (int k = -h; k <= h; ++k) {
-                const float u = vol[v + k];
+                const float u = __fsub_rn(vol[v + k], c);
                 a = __fadd_rn(a, u);
                 b = __fadd_rn(b, __fmul_rn(u, u));
             }
@@ -135,7 +138,10 @@ nrr_status launch_boxsums3(const void *d_intraop, nrr_dtype dtype, nrr_dims dims
     } else {
         const size_t off_q = align_up((size_t)nvox * 4, 256);
         float *sa = (float *)A, *sb = (float *)Bf, *qa = (float *)(A + off_q), *qb = (float *)(Bf + off_q);
-        box3_f32_x<<<g, P3_THREADS, 0, stream>>>((const float *)d_intraop, dims.nx, nvox, hx, sa, qa);
+        box3_f32_x<<<g, P3_THREADS, 0, stream>>>((const float *)d_intraop, dims.nx, nvox, hx,
+                                                 (const float *)d_intraop +
+                                                     volume_centre_index(dims.nx, dims.ny, dims.nz),
+                                                 sa, qa);
         box3_f32_yz<<<g, P3_THREADS, 0, stream>>>(sa, qa, dims.ny, sy, nvox, hy, sb, qb);
         box3_f32_yz<<<g, P3_THREADS, 0, stream>>>(sb, qb, dims.nz, sz, nvox, hz, (float *)o1, (float *)o2);
     }

@@ -55,6 +55,15 @@ nrr_status check_dims(nrr_dims dims, nrr_dtype dtype, int32_t block);
 // Per-axis block edges (x, y, z): each odd in 3..11 and no larger than the volume.
 nrr_status check_dims3(nrr_dims dims, nrr_dtype dtype, const int32_t *block);
 inline size_t elem_size(nrr_dtype t) { return t == NRR_F32 ? 4 : 2; }
+// float32 box sums are sums of J - c with c the reference volume's value at
+// its centre voxel (nx/2, ny/2, nz/2): with c near the data the sums keep
+// a block's spread even when the intensities sit on a large offset.  This
+// is that voxel's index; the box-sum kernels and the match kernel read c
+// from it.
+__host__ __device__ inline long long volume_centre_index(int nx, int ny, int nz)
+{
+    return ((long long)(nz / 2) * ny + ny / 2) * nx + nx / 2;
+}
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Box sums: number of bytes and the two sub-arrays of a box-sum buffer.

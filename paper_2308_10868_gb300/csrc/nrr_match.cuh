@@ -1,9 +1,15 @@
 // NCC block-matching kernel (Sec. 3 NCC equation and O(B x W) bound;
 // Sec. 4.3 block-matching loop), written for sm_103a.
 //
-// A persistent CTA walks its share of the registration blocks, two blocks in
-// flight: while block i is processed, the TMA copies of block i+1 land in
-// the other half of a double buffer.  Per block:
+// Persistent CTAs take the registration blocks of up to 16 jobs (each job
+// one registration, with its own volumes, sizes and box sums) from a work
+// queue, the next item's index fetched a block ahead.  Two blocks are in
+// flight: the TMA copies of block i+1 land while block i is processed, in
+// the other half of a double window buffer, or, with one window buffer
+// (more CTAs per SM), as soon as block i's window has been read.  A search
+// radius above 7 on an axis is covered by sub-windows of one radius that
+// tile [-R, R]; a block's sub-windows are consecutive items of the same
+// CTA, which keeps the best over all of them.  Per block (or sub-window):
 //   1. TMA tiled loads bring the block's search window of the reference
 //      image, [c-h-R, c+h+R] per axis, and the floating block [c-h, c+h]^3
 //      into shared memory.  The x start is rounded down to a 16-byte
@@ -29,8 +35,11 @@
 //      of 2^-85, so none underflows.  A(d) = sum_k T_k J_{k+d} accumulates
 //      with FP32 FFMA, one chain of N terms per shift.
 //   4. Every shift gets an approximate NCC from A(d) and the box sums S_J,
-//      S_JJ (precomputed, exact for uint16; both lines' loads issued
-//      together) and a rigorous bound on its error (recursive-summation
+//      S_JJ (precomputed: exact for uint16; for float32 sums of J - c, c
+//      the reference volume's centre value; read from global memory in the
+//      bound's loop, or staged per thread into shared memory by
+//      asynchronous copies during the search) and a rigorous bound on its
+//      error (recursive-summation
 //      bound gamma_N * sum|T||J - m| for the FMA chain, Cauchy-Schwarz
 //      sum|T||J - m| <= sqrt(sum T^2 * sum (J - m)^2), plus the rounding of
 //      the final operations, each written as a separately rounded operation;
@@ -107,6 +116,7 @@ struct BlockConstF {
     float fvI;       // dvI as float
     float kq;        // sqrt(sum T^2), rounded up
     float emu;       // Ibar - mu (mu: the float mean used for T)
+    float cv;        // c of the box sums (sums of J - c): the reference volume's centre value
 };
 
 // uint16 block constants: every thread derives them from the warp sums;
@@ -692,8 +702,12 @@ __device__ __forceinline__ void line_bounds(const MatchJob &J, int nl, int dyi, 
             const float t2 = __fmul_rn(__fmul_rn(4.f * U32, __fadd_rn(fabsf(na), fabsf(rs))), inv);
             e = __fadd_rn(__fmul_rn(__fadd_rn(t1, t2), 1.f + 64.f * U32), __fmul_rn(40.f * U32, fabsf(v)));
         } else {
-            const float GS = (float)((B + BY + BZ) * 5.9604644775390625e-08 /
-                                     (1.0 - (B + BY + BZ) * 5.9604644775390625e-08));  // box-sum depth
+            // box-sum depth: the b-term levels, the rounding of J - c and of
+            // its square
+            const float GS = (float)((B + BY + BZ + 3) * 5.9604644775390625e-08 /
+                                     (1.0 - (B + BY + BZ + 3) * 5.9604644775390625e-08));
+            // the box sums are of J - cv; the window is centred by c_f:
+            // dl = fl(c_f - cv), and c_f - (cv + dl) is at most 1.01 u |dl|
             const float GN = (float)GAMMA_L;
             const float s1 = ps1(p);
             const float s2 = fmaxf(ps2(p), 0.f);
@@ -706,14 +720,15 @@ __device__ __forceinline__ void line_bounds(const MatchJob &J, int nl, int dyi, 
             const float dv = __fadd_rn(__fadd_rn(__fmul_rn(GS, s2),
                                                  __fdiv_rn(__fmul_rn(__fadd_rn(__fmul_rn(2.f, fabsf(s1)), d1), d1), fN)),
                                        __fmul_rn(4.f * U32, __fadd_rn(s2, s1sq_n)));
-            // S'_J ~ sum (J - c), and sum (J - c)^2 <= its estimate e2 plus
-            // the error of S_JJ, S_J and c terms (m2 bounds their size),
-            // rounded up
-            const float s1p = __fsub_rn(s1, __fmul_rn(fN, c_f));
-            const float m2 = __fadd_rn(__fadd_rn(s2, __fmul_rn(__fmul_rn(2.f, fabsf(c_f)), fabsf(s1))),
-                                       __fmul_rn(__fmul_rn(fN, c_f), c_f));
-            const float e2 = __fadd_rn(__fsub_rn(s2, __fmul_rn(__fmul_rn(2.f, c_f), s1)), __fmul_rn(__fmul_rn(fN, c_f), c_f));
-            const float sj2 = __fmul_rn(__fadd_rn(fmaxf(e2, 0.f), __fmul_rn(__fmul_rn(__fadd_rn(GS, 8.f * U32), m2), 1.01f)),
+            // S'_J ~ sum (J - c_f), and sum (J - c_f)^2 <= its estimate e2
+            // plus the error of the sums, of the dl terms and of c_f - (cv +
+            // dl) (m2 bounds their size), rounded up
+            const float dl = __fsub_rn(c_f, bcf.cv);
+            const float s1p = __fsub_rn(s1, __fmul_rn(fN, dl));
+            const float m2 = __fadd_rn(__fadd_rn(s2, __fmul_rn(__fmul_rn(2.f, fabsf(dl)), fabsf(s1))),
+                                       __fmul_rn(__fmul_rn(fN, dl), dl));
+            const float e2 = __fadd_rn(__fsub_rn(s2, __fmul_rn(__fmul_rn(2.f, dl), s1)), __fmul_rn(__fmul_rn(fN, dl), dl));
+            const float sj2 = __fmul_rn(__fadd_rn(fmaxf(e2, 0.f), __fmul_rn(__fmul_rn(__fadd_rn(GS, 12.f * U32), m2), 1.01f)),
                                         1.f + 4.f * U32);
             if (!(vJa - dv > 0.f)) {  // spread of the reference block not resolved: rescore
                 ub[p] = INFINITY;
@@ -734,7 +749,7 @@ __device__ __forceinline__ void line_bounds(const MatchJob &J, int nl, int dyi, 
             const float enum_ = __fadd_rn(
                 __fadd_rn(__fmul_rn(__fmul_rn(__fadd_rn(GN, 3.f * U32), bcf.kq), sq),
                           __fmul_rn(__fmul_rn(fabsf(bcf.emu),
-                                              __fadd_rn(__fadd_rn(fabsf(s1p), d1), __fmul_rn(2.f * U32, __fmul_rn(fN, fabsf(c_f))))),
+                                              __fadd_rn(__fadd_rn(fabsf(s1p), d1), __fmul_rn(4.f * U32, __fmul_rn(fN, fabsf(dl))))),
                                     1.01f)),
                 __fmul_rn(U32, __fadd_rn(fabsf(A), fabsf(es))));
             const float r1 = __fadd_rn(__fadd_rn(1.f, __fmul_rn(0.7f, rho)), 4.f * U32);
@@ -964,6 +979,9 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
         const MatchJob &J = a.jobs[sc->cen[b][3]];
         const int bi = sc->cen[b][4];
         const int nx = J.nx, ny = J.ny, nz = J.nz;  // this block's volumes
+        float cv_pre = 0.f;  // float32: c of the box sums, loaded ahead of the statistics
+        if constexpr (F32)
+            if (tid == 0) cv_pre = reinterpret_cast<const float *>(J.intraop)[volume_centre_index(nx, ny, nz)];
         const int si = sc->cen[b][5];  // sub-window of this item
         int x0;
         {
@@ -1041,6 +1059,7 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                 c.ibl = (float)(ibar - (double)c.ibh);
                 const double em = ibar - (double)tsh;
                 c.emu = (float)em;
+                c.cv = cv_pre;
                 c.dvI = dv;
                 c.fvI = (float)dv;
                 // sum of T^2 with T = fl(I - mu): at most (1+u)^2 sum (I - mu)^2

@@ -176,9 +176,9 @@ def test_filter_bound_is_tight_enough_to_filter():
 # ---------------------------------------------------------------------------
 # float32 intensities: the same check for the float32 path's bound, which also
 # covers the rounding of the inputs' centring, of the float box sums (three
-# levels of b-term sums) and of the float block constants; shifts whose
-# reference spread the float sums cannot resolve are rescored unconditionally
-# (no bound is claimed for them).
+# levels of b-term sums of J - c, c the reference volume's centre value) and
+# of the float block constants; shifts whose reference spread the float sums
+# cannot resolve are rescored unconditionally (no bound is claimed for them).
 # ---------------------------------------------------------------------------
 def _box_f32(blk):
     """Sum of a b^3 float32 block as the box kernel forms it: b terms along
@@ -195,7 +195,9 @@ def _box_f32(blk):
     return np.float32(sz)
 
 
-def kernel_bound_f32(I, W, R, delta_rsqrt, delta_sqrt):
+def kernel_bound_f32(I, W, R, delta_rsqrt, delta_sqrt, cv=None):
+    """cv: the box sums' centre c (the reference volume's centre value; by
+    default the window's centre voxel here)."""
     bz, by, bx = I.shape  # a block with an edge per axis: the box-sum depth is bx + by + bz
     N = bx * by * bz
     P = 2 * R + 1
@@ -212,13 +214,17 @@ def kernel_bound_f32(I, W, R, delta_rsqrt, delta_sqrt):
     emu, fvI = F(em), F(dv)
     kq = F(np.sqrt((dv + 2048.0 * 1.1102230246251565e-16 * s2 + N * em * em) * (1.0 + 2.4e-7)) * (1.0 + 1e-6))
     T = I - tsh  # float32, rounded as in the kernel
-    # float box sums of J and J^2 at every shift, and the centring constant
+    # float box sums of J - c and (J - c)^2 at every shift (J - c rounded
+    # once, its square once), and the centring constant
+    if cv is None:
+        cv = W[W.shape[0] // 2, W.shape[1] // 2, W.shape[2] // 2]
+    cv = F(cv)
     S1 = np.zeros((P, P, P), np.float32)
     S2 = np.zeros((P, P, P), np.float32)
     for dz in range(P):
         for dy in range(P):
             for dx in range(P):
-                blk = W[dz:dz + bz, dy:dy + by, dx:dx + bx]
+                blk = (W[dz:dz + bz, dy:dy + by, dx:dx + bx] - cv).astype(np.float32)
                 S1[dz, dy, dx] = _box_f32(blk)
                 S2[dz, dy, dx] = _box_f32(blk * blk)
     c_f = tsh  # centring constant: the float mean
@@ -237,7 +243,7 @@ def kernel_bound_f32(I, W, R, delta_rsqrt, delta_sqrt):
                     ncc[dz, dy, dx] = (I64 * J64).sum() / den
     # the bound, as the kernel evaluates it (float32 path): every operation
     # rounded on its own, in the kernel's order
-    depth = bx + by + bz
+    depth = bx + by + bz + 3  # the levels, the rounding of J - c and of its square
     GS = F(depth * 2.0 ** -24 / (1.0 - depth * 2.0 ** -24))
     GN = F(N * 2.0 ** -24 / (1.0 - N * 2.0 ** -24))
     s1b, s2b = S1, np.maximum(S2, F(0.0))
@@ -246,10 +252,11 @@ def kernel_bound_f32(I, W, R, delta_rsqrt, delta_sqrt):
     s1sq_n = (s1b * s1b) * (F(1.0) / fN)
     vJa = s2b - s1sq_n
     dvJ = (GS * s2b + ((F(2.0) * np.abs(s1b) + d1) * d1) / fN) + (F(4.0) * U) * (s2b + s1sq_n)
-    s1p = s1b - fN * c_f
-    m2 = (s2b + (F(2.0) * np.abs(c_f)) * np.abs(s1b)) + (fN * c_f) * c_f
-    e2 = (s2b - (F(2.0) * c_f) * s1b) + (fN * c_f) * c_f
-    sj2 = (np.maximum(e2, F(0.0)) + ((GS + F(8.0) * U) * m2) * F(1.01)) * (F(1.0) + F(4.0) * U)
+    dl = c_f - cv
+    s1p = s1b - fN * dl
+    m2 = (s2b + (F(2.0) * np.abs(dl)) * np.abs(s1b)) + (fN * dl) * dl
+    e2 = (s2b - (F(2.0) * dl) * s1b) + (fN * dl) * dl
+    sj2 = (np.maximum(e2, F(0.0)) + ((GS + F(12.0) * U) * m2) * F(1.01)) * (F(1.0) + F(4.0) * U)
     resolved = (vJa - dvJ) > 0
     with np.errstate(invalid="ignore", divide="ignore"):
         rho = dvJ / (vJa - dvJ)
@@ -262,7 +269,7 @@ def kernel_bound_f32(I, W, R, delta_rsqrt, delta_sqrt):
     num = A - es
     v = num * inv
     enum = ((((GN + F(3.0) * U) * kq) * sq
-             + (np.abs(emu) * ((np.abs(s1p) + d1) + (F(2.0) * U) * (fN * np.abs(c_f)))) * F(1.01))
+             + (np.abs(emu) * ((np.abs(s1p) + d1) + (F(4.0) * U) * (fN * np.abs(dl)))) * F(1.01))
             + U * (np.abs(A) + np.abs(es)))
     r1 = (F(1.0) + F(0.7) * rho) + F(4.0) * U
     r2 = F(0.7) * rho + F(6.0) * U
@@ -277,8 +284,8 @@ def _cases_f32():
            for name, I, W in cases]
     rng = np.random.default_rng(7)
     b, w = 7, 7 + 2 * R
-    # offsets large against the spread: the centring matters (at 50x the
-    # float sums still resolve the spread; at 10^5x every shift is rescored)
+    # offsets large against the spread: the centring matters (sums of J - c
+    # with c on the offset keep the spread at 50x and at 10^5x)
     for off, spread in ((50.0, 1.0), (1000.0, 0.01)):
         I = np.float32(off) + rng.random((b, b, b)).astype(np.float32) * np.float32(spread)
         W = np.float32(off) + rng.random((w, w, w)).astype(np.float32) * np.float32(spread)
@@ -286,20 +293,40 @@ def _cases_f32():
     return out, R
 
 
+@pytest.mark.parametrize("centre", ["volume", "zero", "far"])
 @pytest.mark.parametrize("delta_rsqrt,delta_sqrt", [(2.0 ** -22, 2.0 ** -22), (-2.0 ** -22, -2.0 ** -22),
                                                       (2.0 ** -22, -2.0 ** -22), (0.0, 0.0)])
-def test_filter_bound_f32_covers_the_error(delta_rsqrt, delta_sqrt):
+def test_filter_bound_f32_covers_the_error(delta_rsqrt, delta_sqrt, centre):
+    # c: the volume's centre value (near the data), zero (a volume whose
+    # centre is background) or a value far from the data
     cases, R = _cases_f32()
     n_bounded_cases = 0
     for name, I, W in cases:
+        cv = {"volume": None, "zero": 0.0, "far": float(W.max()) * 3.0 + 1.0}[centre]
         with np.errstate(invalid="ignore", divide="ignore"):
-            v, e, ncc, bounded = kernel_bound_f32(I, W, R, delta_rsqrt, delta_sqrt)
+            v, e, ncc, bounded = kernel_bound_f32(I, W, R, delta_rsqrt, delta_sqrt, cv=cv)
         if not bounded.any():  # spread not resolved: every shift is rescored exactly
             continue
         n_bounded_cases += 1
         err = np.abs(v - ncc)[bounded]
-        assert (err <= e[bounded]).all(), (name, float((err - e[bounded]).max()))
-    assert n_bounded_cases >= 6
+        assert (err <= e[bounded]).all(), (name, centre, float((err - e[bounded]).max()))
+    # a c far from the data makes its own offset: fewer cases are resolved
+    assert n_bounded_cases >= {"volume": 7, "zero": 6, "far": 4}[centre]
+
+
+def test_filter_bound_f32_large_offset_is_bounded_with_the_centred_sums():
+    # an offset 10^5 times the spread: with c from the volume the spread is
+    # resolved and the bound filters (no shift forced to rescoring); with
+    # uncentred sums (c = 0) it is not
+    cases, R = _cases_f32()
+    name, I, W = cases[-1]
+    assert name.startswith("offset 1000")
+    with np.errstate(invalid="ignore", divide="ignore"):
+        v, e, ncc, bounded = kernel_bound_f32(I, W, R, 2.0 ** -22, 2.0 ** -22)
+        assert bounded.all()
+        lb = (v - e)[bounded].max()
+        assert int(((v + e)[bounded] >= lb).sum()) <= 3
+        assert not kernel_bound_f32(I, W, R, 2.0 ** -22, 2.0 ** -22, cv=0.0)[3].any()
 
 
 def test_filter_bound_f32_leaves_few_survivors():

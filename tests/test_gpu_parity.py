@@ -266,11 +266,11 @@ def test_f32_integer_valued_equals_u16(nrr):
 
 @pytest.mark.parametrize("offset,spread", [(50.0, 1.0), (1000.0, 1e-2)])
 def test_f32_large_offset(nrr, offset, spread):
-    # Intensities on an offset large against their spread.  At 50x the float
-    # box sums still resolve every reference block's spread and the filter
-    # bound applies; at 10^5x they do not, the kernel rescores every shift
-    # exactly (the branch that gives up the bound), and the float-float
-    # rescoring must not lose the spread to the offset.
+    # Intensities on an offset large against their spread (50x and 10^5x).
+    # The float box sums are of J - c with c the volume's centre value, so
+    # they keep every reference block's spread and the filter bound applies
+    # on both; the float-float rescoring must not lose the spread to the
+    # offset either.
     pre, intra, mask = synth.workload_pair("small")
     centers, _ = oracle.select_blocks(pre, mask, 7, 2, 0.1)
     centers = centers[:160]
