@@ -117,6 +117,7 @@ struct BlockConstF {
     float kq;        // sqrt(sum T^2), rounded up
     float emu;       // Ibar - mu (mu: the float mean used for T)
     float cv;        // c of the box sums (sums of J - c): the reference volume's centre value
+    float eI;        // bound on emu's error beyond 2u |emu| (the float-float mean's), rounded up
 };
 
 // uint16 block constants: every thread derives them from the warp sums;
@@ -746,11 +747,18 @@ __device__ __forceinline__ void line_bounds(const MatchJob &J, int nl, int dyi, 
             const float es = __fmul_rn(bcf.emu, s1p);  // (Ibar - mu) S'_J
             const float num = __fsub_rn(A, es);
             v = __fmul_rn(num, inv);
+            // the numerator's error: the search sum's (GN, and 3u for the
+            // roundings of T and of the window values), then es = emu S'_J:
+            // emu errs by at most 2u |emu| + eI and s1p by d1 + 4uN|dl| +
+            // 2u |s1p| (the box sums, N dl and c_f - (cv + dl), the
+            // subtraction), with |S'_J| <= sb
+            const float aem = fabsf(bcf.emu);
+            const float ds = __fadd_rn(d1, __fmul_rn(4.f * U32, __fmul_rn(fN, fabsf(dl))));
+            const float sb = __fadd_rn(fabsf(s1p), ds);
+            const float tes = __fadd_rn(__fmul_rn(sb, __fadd_rn(__fmul_rn(2.f * U32, aem), bcf.eI)),
+                                        __fmul_rn(aem, __fadd_rn(ds, __fmul_rn(2.f * U32, fabsf(s1p)))));
             const float enum_ = __fadd_rn(
-                __fadd_rn(__fmul_rn(__fmul_rn(__fadd_rn(GN, 3.f * U32), bcf.kq), sq),
-                          __fmul_rn(__fmul_rn(fabsf(bcf.emu),
-                                              __fadd_rn(__fadd_rn(fabsf(s1p), d1), __fmul_rn(4.f * U32, __fmul_rn(fN, fabsf(dl))))),
-                                    1.01f)),
+                __fadd_rn(__fmul_rn(__fmul_rn(__fadd_rn(GN, 3.f * U32), bcf.kq), sq), __fmul_rn(tes, 1.01f)),
                 __fmul_rn(U32, __fadd_rn(fabsf(A), fabsf(es))));
             const float r1 = __fadd_rn(__fadd_rn(1.f, __fmul_rn(0.7f, rho)), 4.f * U32);
             const float r2 = __fadd_rn(__fmul_rn(0.7f, rho), 6.f * U32);
@@ -1060,6 +1068,12 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
                 const double em = ibar - (double)tsh;
                 c.emu = (float)em;
                 c.cv = cv_pre;
+                // the mean's error: the float-float sum of the N terms I - I0
+                // errs by at most 2^-36 sum |I - I0| <= 2^-36 sqrt(N d2), and
+                // i0 + d1 / N rounds twice in FP64; emu's own rounding (and
+                // that of em) stays within 2u |emu|
+                c.eI = __double2float_ru((0x1p-36 * sqrt((double)N * d2) / (double)N +
+                                          0x1p-52 * (fabs((double)i0) + fabs(d1) / (double)N)) * 1.01);
                 c.dvI = dv;
                 c.fvI = (float)dv;
                 // sum of T^2 with T = fl(I - mu): at most (1+u)^2 sum (I - mu)^2

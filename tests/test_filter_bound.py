@@ -212,6 +212,9 @@ def kernel_bound_f32(I, W, R, delta_rsqrt, delta_sqrt, cv=None):
     dv = max(s2 - s1 * (s1 / N), 0.0)
     em = ibar - float(tsh)
     emu, fvI = F(em), F(dv)
+    # bound on emu's error beyond 2u |emu|, as the kernel forms it
+    eI = F(np.nextafter(np.float32((2.0 ** -36 * np.sqrt(N * s2) / N + 2.0 ** -52 * (abs(float(i0)) + abs(s1) / N)) * 1.01),
+                        np.float32(np.inf)))
     kq = F(np.sqrt((dv + 2048.0 * 1.1102230246251565e-16 * s2 + N * em * em) * (1.0 + 2.4e-7)) * (1.0 + 1e-6))
     T = I - tsh  # float32, rounded as in the kernel
     # float box sums of J - c and (J - c)^2 at every shift (J - c rounded
@@ -268,9 +271,11 @@ def kernel_bound_f32(I, W, R, delta_rsqrt, delta_sqrt, cv=None):
     es = emu * s1p
     num = A - es
     v = num * inv
-    enum = ((((GN + F(3.0) * U) * kq) * sq
-             + (np.abs(emu) * ((np.abs(s1p) + d1) + (F(4.0) * U) * (fN * np.abs(dl)))) * F(1.01))
-            + U * (np.abs(A) + np.abs(es)))
+    aem = np.abs(emu)
+    ds = d1 + (F(4.0) * U) * (fN * np.abs(dl))
+    sb = np.abs(s1p) + ds
+    tes = sb * ((F(2.0) * U) * aem + eI) + aem * (ds + (F(2.0) * U) * np.abs(s1p))
+    enum = ((((GN + F(3.0) * U) * kq) * sq + tes * F(1.01)) + U * (np.abs(A) + np.abs(es)))
     r1 = (F(1.0) + F(0.7) * rho) + F(4.0) * U
     r2 = F(0.7) * rho + F(6.0) * U
     e = ((enum * inv) * r1 + (np.abs(num) * inv) * r2) * (F(1.0) + F(64.0) * U) + (F(43.0) * U) * np.abs(v)
