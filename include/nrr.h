@@ -173,16 +173,22 @@ nrr_status nrr_select_blocks_spaced(const uint16_t *d_preop, const uint8_t *d_ma
  * the same arguments, results and errors, but takes its scratch from a
  * fixed array of NRR_SELECT_STATIC_SCRATCH_BYTES (32 MiB) built into the
  * library instead of from an allocator: it calls no cudaMalloc, cudaFree or
- * other allocating routine.  Every GPU that loads the library holds that
- * array until the process exits.
+ * other allocating routine.  The array is reserved on a device when the
+ * library's selection module is loaded there: with lazy module loading
+ * (the CUDA default) that happens at the first selection call of any kind
+ * on that device at the latest, and that call can then need the 32 MiB and
+ * fail with NRR_E_CUDA (out of memory) if the process's own allocator
+ * already holds all device memory.  Make a first selection call (this entry
+ * point on a tiny volume will do) at start-up, while memory is still free
+ * and before any stream capture; the array is then held until the process
+ * exits.
  *
  *  - Limit: the scratch needs about 8 bytes per candidate grid point
  *    (ceil(nx/stride) * ceil(ny/stride) * ceil(nz/stride)), so up to about
  *    4 million grid points; a larger grid returns NRR_E_CAPACITY and writes
  *    nothing.
- *  - The first call on each device looks up the array's device address
- *    (a one-time set-up, no allocation); make that first call before any
- *    stream capture.
+ *  - The first call on each device also looks up the array's device
+ *    address (once); the start-up call above covers it.
  *  - All calls share the one array and each leaves its contents there (each
  *    call clears what it needs zeroed before use).  Calls whose work could
  *    overlap on the GPU (different streams without ordering between them,

@@ -183,7 +183,7 @@ struct SelectPlan {
     long long ng;
     int nchunks;
     int connectivity;  // 0, 6, 18 or 26
-    size_t off_keys, off_hist, off_state, off_sync, off_cnt, off_sp_state, off_sp_mask, bytes;
+    size_t off_keys, off_hist, off_state, off_sync, off_cnt, off_list, off_sp_state, off_sp_mask, bytes;
 };
 SelectPlan select_plan(nrr_dims d, int stride, int connectivity = 0);
 nrr_status enqueue_select(const uint16_t *preop, const uint8_t *mask, nrr_dims d, int block, int stride, double frac,

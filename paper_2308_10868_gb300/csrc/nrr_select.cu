@@ -47,7 +47,8 @@ struct SelState {
     long long thresh;         // key of the nsel-th largest (K*)
     long long need_ties;      // how many keys equal to K* are selected
     unsigned long long maxkey;  // largest key (sets the first digit)
-    unsigned int arrived[NPASS + 1];  // CTAs finished per histogram pass / count pass
+    unsigned int arrived[NPASS + 1];  // [0]: the rank kernel's grid-barrier arrivals
+    unsigned int nlist;       // keys collected from a small bucket
     int done;                 // nothing (more) to select
 };
 
@@ -154,6 +155,7 @@ __device__ __forceinline__ bool digit_of_pass(const SelState *st, int pass, int 
 constexpr int RK_THREADS = 512;
 constexpr int RK_KPT = 8;  // keys per thread per sweep (RK_THREADS * RK_KPT = CMP_CHUNK)
 constexpr int RK_SUB = RK_THREADS * CMP_ITEMS;     // keys per compaction sub-block
+constexpr int RK_SMALL = 2048;  // a bucket this small is collected and finished inside every CTA
 
 __device__ __forceinline__ unsigned long long block_excl_scan_rk(unsigned long long v, unsigned long long *tot)
 {
@@ -179,6 +181,7 @@ __device__ __forceinline__ unsigned long long block_excl_scan_rk(unsigned long l
 __global__ void __launch_bounds__(RK_THREADS) select_rank_kernel(const long long *__restrict__ keys, long long ng,
                                                                  long long span, double frac, SelState *st,
                                                                  unsigned int *__restrict__ hist,
+                                                                 long long *__restrict__ list,
                                                                  unsigned long long *__restrict__ cnt, int gx, int gy,
                                                                  int stride, int32_t *__restrict__ centers,
                                                                  int max_blocks, int32_t *d_n_selected,
@@ -187,7 +190,8 @@ __global__ void __launch_bounds__(RK_THREADS) select_rank_kernel(const long long
 {
     __shared__ unsigned int h[HIST_BINS];
     __shared__ long long wsum[RK_THREADS / 32];
-    __shared__ long long s_prefix, s_kth, s_thresh, s_need, s_nsel;
+    __shared__ long long lk[RK_SMALL];  // a small bucket's keys
+    __shared__ long long s_prefix, s_kth, s_thresh, s_need, s_nsel, s_bcount;
     __shared__ int s_done;
     const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
     unsigned int nb = 0;  // grid barriers passed
@@ -207,8 +211,52 @@ __global__ void __launch_bounds__(RK_THREADS) select_rank_kernel(const long long
         s_done = ns == 0 || st->maxkey == 0;
         s_thresh = 0x7fffffffffffffffll;  // nothing selected unless a pass fixes it
         s_need = 0;
+        s_bcount = 0;
     }
     __syncthreads();
+    // every CTA finds the bucket of `src` (nbins bins of the digit at bit
+    // sh) holding the kth largest key: thread t owns reversed bins r =
+    // PER*t .. PER*t+PER-1 (bin b = nbins-1-r), an inclusive scan over r
+    // counts the keys in bins >= b; the digit joins the prefix, kth becomes
+    // the rank inside the bucket, and at bit 0 the threshold is fixed
+    auto pick = [&](const unsigned int *src, bool global, int nbins, int sh) {
+        constexpr int PER = HIST_BINS / RK_THREADS;
+        const long long kth = s_kth, prefix = s_prefix;
+        long long c[PER], v = 0;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int bin = nbins - 1 - (PER * t + q);
+            c[q] = bin >= 0 ? (long long)(global ? __ldcg(src + bin) : src[bin]) : 0;
+            v += c[q];
+        }
+        long long incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long n2 = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += n2;
+        }
+        if (lane == 31) wsum[wp] = incl;
+        __syncthreads();  // every thread has read s_kth and s_prefix
+        long long above = incl - v;  // keys in bins above this thread's first bin
+        for (int i = 0; i < wp; ++i) above += wsum[i];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int bin = nbins - 1 - (PER * t + q);
+            if (bin >= 0 && above < kth && above + c[q] >= kth) {
+                const long long pre = prefix | ((long long)bin << sh);
+                s_prefix = pre;
+                s_kth = kth - above;
+                s_bcount = c[q];
+                if (sh == 0) {
+                    s_thresh = pre;
+                    s_need = kth - above;
+                    s_done = 1;
+                }
+            }
+            above += c[q];
+        }
+        __syncthreads();
+    };
+    int sh_fixed = 64;  // the digits at and above this bit are fixed
     for (int pass = 0; pass < NPASS && !s_done; ++pass) {
         int sh, w;
         if (!digit_of_pass(st, pass, &sh, &w)) break;
@@ -241,45 +289,46 @@ __global__ void __launch_bounds__(RK_THREADS) select_rank_kernel(const long long
         for (int i = t; i < HIST_BINS; i += RK_THREADS)
             if (h[i]) atomicAdd(&gh[i], h[i]);
         if (!barrier()) return;
-        // every CTA finds the bucket holding the kth largest key: thread t
-        // owns reversed bins r = PER*t .. PER*t+PER-1 (bin b = nb-1-r), an
-        // inclusive scan over r counts the keys in bins >= b
-        const long long kth = s_kth;
-        const int nbins = 1 << w;
-        constexpr int PER = HIST_BINS / RK_THREADS;
-        long long c[PER], v = 0;
+        pick(gh, true, 1 << w, sh);
+        sh_fixed = sh;
+        if (!s_done && s_bcount <= RK_SMALL) break;  // a small bucket: finished below
+    }
+    if (!s_done && sh_fixed < 64 && s_bcount <= RK_SMALL) {
+        // collect the bucket's keys (every key > 0 whose digits above
+        // sh_fixed are the prefix's), then every CTA finishes the radix
+        // select on them in shared memory, with no more grid barriers
+        const long long hi = s_prefix >> sh_fixed;
+        const long long sweep = (long long)gridDim.x * RK_THREADS * RK_KPT;
+        for (long long g0 = (long long)blockIdx.x * RK_THREADS * RK_KPT + t; g0 < ng; g0 += sweep) {
+            long long kv[RK_KPT];
 #pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int bin = nbins - 1 - (PER * t + q);
-            c[q] = bin >= 0 ? (long long)__ldcg(gh + bin) : 0;
-            v += c[q];
-        }
-        const long long prefix = s_prefix;
-        long long incl = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long n2 = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += n2;
-        }
-        if (lane == 31) wsum[wp] = incl;
-        __syncthreads();  // every thread has read s_kth and s_prefix
-        long long above = incl - v;  // keys in bins above this thread's first bin
-        for (int i = 0; i < wp; ++i) above += wsum[i];
-#pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int bin = nbins - 1 - (PER * t + q);
-            if (bin >= 0 && above < kth && above + c[q] >= kth) {
-                const long long pre = prefix | ((long long)bin << sh);
-                s_prefix = pre;
-                s_kth = kth - above;
-                if (sh == 0) {
-                    s_thresh = pre;
-                    s_need = kth - above;
-                    s_done = 1;
-                }
+            for (int q = 0; q < RK_KPT; ++q) {
+                const long long g = g0 + (long long)q * RK_THREADS;
+                kv[q] = g < ng ? __ldcg(keys + g) : -1;
             }
-            above += c[q];
+#pragma unroll
+            for (int q = 0; q < RK_KPT; ++q)
+                if (kv[q] > 0 && (kv[q] >> sh_fixed) == hi) {
+                    const unsigned pos = atomicAdd(&st->nlist, 1u);
+                    if (pos < (unsigned)RK_SMALL) __stcg(list + pos, kv[q]);
+                }
         }
-        __syncthreads();
+        if (!barrier()) return;
+        const int nl = (int)s_bcount;
+        for (int i = t; i < nl; i += RK_THREADS) lk[i] = __ldcg(list + i);
+        int shr = sh_fixed;
+        while (!s_done && shr > 0) {
+            const int w = shr < 11 ? shr : 11, shift = shr - w;
+            for (int i = t; i < HIST_BINS; i += RK_THREADS) h[i] = 0;
+            __syncthreads();  // and lk is loaded
+            const long long hib = s_prefix >> shr;
+            const long long dmask = (1ll << w) - 1;
+            for (int i = t; i < nl; i += RK_THREADS)
+                if ((lk[i] >> shr) == hib) atomicAdd(&h[(unsigned)((lk[i] >> shift) & dmask)], 1u);
+            __syncthreads();
+            pick(h, false, 1 << w, shift);
+            shr = shift;
+        }
     }
     const long long th = s_thresh, need = s_need;
     if (blockIdx.x == 0 && t == 0) {
@@ -384,6 +433,8 @@ SelectPlan select_plan(nrr_dims d, int stride, int connectivity)
     o += align_up(sizeof(SpacingSync), 256);
     p.off_cnt = o;
     o += align_up((size_t)p.nchunks * 8, 256);
+    p.off_list = o;
+    o += align_up(sizeof(long long) * RK_SMALL, 256);
     p.off_sp_state = p.off_sp_mask = o;
     if (connectivity) {
         o += align_up((size_t)p.ng, 256);
@@ -454,8 +505,8 @@ nrr_status enqueue_select(const uint16_t *preop, const uint8_t *mask, nrr_dims d
     cfg.attrs = at;
     cfg.numAttrs = 1;
     NRR_CUDA_TRY(cudaLaunchKernelEx(&cfg, select_rank_kernel, (const long long *)keys, p.ng, span, frac, st, hist,
-                                    cnt, p.gx, p.gy, stride, centers, (int)max_blocks, d_n_selected, err, wait_ns,
-                                    missing));
+                                    (long long *)(ws + p.off_list), cnt, p.gx, p.gy, stride, centers, (int)max_blocks,
+                                    d_n_selected, err, wait_ns, missing));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "selection kernel launch");
     count_launches(2);
