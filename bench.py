@@ -405,9 +405,13 @@ def _serving(a, nrr, synth, dev):
             tickets, late = [], []
             for t_arr, si, b, r, f in reqs:
                 if open_loop:
+                    # sleep to within a millisecond of the arrival, then spin
+                    # (sleep alone can wake late by several milliseconds)
                     dt = t_arr - (time.perf_counter() - t0)
-                    if dt > 0:
-                        time.sleep(dt)
+                    if dt > 2e-3:
+                        time.sleep(dt - 1e-3)
+                    while time.perf_counter() - t0 < t_arr:
+                        pass
                 p, i, m = pool[si]
                 # how long after its scheduled arrival the request was submitted
                 late.append(max(0.0, (time.perf_counter() - t0) - t_arr) if open_loop else 0.0)
