@@ -65,13 +65,16 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <type_traits>
+#include <vector>
 
 #include "nrr_internal.h"
 #include "nrr_ptx.cuh"
 
 namespace nrr {
 
+constexpr int MATCH_MAX_THREADS_C = 256;
 struct MatchParams {
     const void *preop;
     const void *intraop;
@@ -99,9 +102,13 @@ struct MatchParams {
     // box sums of each thread's lines staged in shared memory by
     // asynchronous copies issued at the block's start
     int stage;
+    // thread k takes line unit unit_of[k] (255: none), an order of the units
+    // in which the 16-byte window loads of every 8 consecutive threads fall
+    // in distinct bank groups where possible
+    uint8_t unit_of[MATCH_MAX_THREADS_C];
 };
 
-constexpr int MATCH_MAX_THREADS = 256;
+constexpr int MATCH_MAX_THREADS = MATCH_MAX_THREADS_C;
 constexpr int MATCH_MAX_WARPS = MATCH_MAX_THREADS / 32;
 
 struct Cand {
@@ -940,7 +947,7 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
     // this thread's lines
     LineUnit un;
     constexpr int LPT = match_lpt<T, ANI>();
-    const bool has_unit = line_unit<LPT>(tid, py, pz, un);
+    const bool has_unit = line_unit<LPT>(a.unit_of[tid], py, pz, un);
     const int dz1 = un.dz0 + (un.along_z ? 1 : 0), dy1 = un.dy0 + (un.along_z ? 0 : 1);
 
     // ---- thread 0's work-item bookkeeping ----------------------------------
@@ -1351,7 +1358,7 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
             act &= act - 1;
             uint32_t mb = __shfl_sync(0xffffffffu, smask, src);
             LineUnit su;
-            line_unit<LPT>(warp * 32 + src, py, pz, su);
+            line_unit<LPT>(a.unit_of[warp * 32 + src], py, pz, su);
             while (mb) {
                 const int bit = __ffs(mb) - 1;
                 mb &= mb - 1;
@@ -1549,6 +1556,53 @@ constexpr auto match_kernel_ptr()
 inline int launch_by(const MatchLaunch &m) { return m.block_y > 0 ? m.block_y : m.block; }
 inline int launch_bz(const MatchLaunch &m) { return m.block_z > 0 ? m.block_z : m.block; }
 
+// Host: the order of line units over threads.  A type A unit's 16-byte
+// window loads start at bank group ((dz * wyp + dy) * bxc) mod 8 (bxc =
+// 16-byte chunks per window row) and move in step with every other type A
+// unit's, so units are dealt to groups of 8 consecutive threads with
+// distinct start groups as far as the counts allow; the type B and single
+// units, whose loads move differently, follow.  One line per thread keeps
+// the identity order (consecutive threads are a window plane apart).
+inline void match_unit_order(int py, int pz, int wyp, int bxc, int lpt, int threads, uint8_t *unit_of)
+{
+    for (int k = 0; k < MATCH_MAX_THREADS_C; ++k) unit_of[k] = 255;
+    const int nu = match_units(py, pz, lpt);
+    if (lpt == 1) {
+        for (int k = 0; k < nu && k < threads; ++k) unit_of[k] = (uint8_t)k;
+        return;
+    }
+    const int nA = pz * (py / 2);
+    std::vector<int> byg[8];
+    for (int k = nA - 1; k >= 0; --k) {
+        const int dz = k % pz, dy = 2 * (k / pz);
+        byg[((dz * wyp + dy) * bxc) & 7].push_back(k);
+    }
+    // each group of 8 threads: one unit from each of the fullest start
+    // groups, then, if fewer than 8 groups are left, further units anyway
+    int t = 0, left = nA;
+    while (left > 0) {
+        int order[8];
+        for (int g = 0; g < 8; ++g) order[g] = g;
+        std::sort(order, order + 8, [&](int x, int y) { return byg[x].size() > byg[y].size(); });
+        int n = 0;
+        for (int q = 0; q < 8 && left > 0; ++q)
+            if (!byg[order[q]].empty()) {
+                unit_of[t++] = (uint8_t)byg[order[q]].back();
+                byg[order[q]].pop_back();
+                --left;
+                ++n;
+            }
+        for (int q = 0; n < 8 && left > 0; q = (q + 1) & 7)
+            if (!byg[order[q]].empty()) {
+                unit_of[t++] = (uint8_t)byg[order[q]].back();
+                byg[order[q]].pop_back();
+                --left;
+                ++n;
+            }
+    }
+    for (int k = nA; k < nu; ++k) unit_of[t++] = (uint8_t)k;
+}
+
 template <typename T, int B, int P, bool LEV, bool ANI>
 nrr_status choose_layout(const MatchLaunch &m, MatchLayout *L, bool *single, bool *stage, int *occ)
 {
@@ -1657,6 +1711,7 @@ nrr_status launch_match_variant_l(const MatchLaunch &m, cudaStream_t stream)
     p.n_jobs = m.n_jobs;
     p.single_window = single ? 1 : 0;
     p.stage = stage ? 1 : 0;
+    match_unit_order(py, pz, wyp, BX * (int)sizeof(T) / 16, match_lpt<T, ANI>(), threads, p.unit_of);
     p.by = by;
     p.bz = bz;
     for (int j = 0; j < MATCH_MAX_JOBS; ++j) {

@@ -28,7 +28,7 @@ def test_kernel_hash_ignores_comments_but_not_code(tmp_path):
     text = p.read_text()
     p.write_text("// a comment added at the top\n\n" + text.replace("\n", "  // trailing note\n", 3))
     assert bench._kernel_source_hash(d) == h0
-    p.write_text(text.replace("constexpr int MATCH_MAX_THREADS = 256;", "constexpr int MATCH_MAX_THREADS = 128;"))
+    p.write_text(text.replace("constexpr int MATCH_MAX_THREADS_C = 256;", "constexpr int MATCH_MAX_THREADS_C = 128;"))
     assert bench._kernel_source_hash(d) != h0
 
 
