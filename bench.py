@@ -57,9 +57,9 @@ def _args():
     p.add_argument("--no-spacing", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-small", action="store_true")
-    p.add_argument("--serve-open-requests", type=int, default=400)
+    p.add_argument("--serve-open-requests", type=int, default=1000)  # 50 s at 20 req/s
     p.add_argument("--serve-sweep-requests", type=int, default=300)
-    p.add_argument("--serve-closed-requests", type=int, default=300)
+    p.add_argument("--serve-closed-requests", type=int, default=1000)
     return p.parse_args()
 
 
@@ -383,8 +383,8 @@ def _serving(a, nrr, synth, dev):
     """The served stream: Poisson arrivals (mean 20 requests/s) of
     registrations of three volume sizes with random (block, radius,
     fraction); volumes resident on the device.  Reports p50/p99 latency
-    (submission to completion on the device) and registrations/s, the same
-    for arrival rates from 100 to 1600 requests/s, and a saturation run (all
+    (scheduled arrival to completion on the device) and registrations/s, the
+    same for arrival rates from 50 to 1600 requests/s, and a saturation run (all
     requests queued at once) served with 8 slots (same-variant requests
     grouped into one match launch, and without grouping) against
     one-at-a-time FIFO service (1 slot, no grouping)."""
@@ -465,7 +465,7 @@ def _serving(a, nrr, synth, dev):
         "lone_service_p99_ms": 1e3 * float(np.percentile(arr[1], 99))})
     # arrival-rate sweep up to saturation (same request mix, fresh arrivals)
     sweep = {}
-    for rate in (100.0, 200.0, 400.0, 800.0, 1600.0):
+    for rate in (50.0, 100.0, 200.0, 400.0, 800.0, 1600.0):
         reqs = synth.poisson_arrivals(a.serve_sweep_requests, rate, seed=synth.SEED_BASE + 20 + int(rate))
         sweep[f"{rate:g}rps"] = run(reqs, 8, True)
     out["open_loop_rate_sweep"] = sweep

@@ -12,7 +12,8 @@
 //     is free and the free device memory, less a reserve, covers the
 //     request's scratch and result buffers; queued requests of the same
 //     variant (dtype, block, radius) as the admitted one join it, up to 16:
-//     each runs its own selection and box sums, and one match launch holds
+//     each runs its own selection and box sums (the later ones on helper
+//     streams of the slot, beside the first), and one match launch holds
 //     all their jobs (each with its own volumes, sizes and tensor maps), so
 //     a busy queue of small requests fills the GPU with one launch instead
 //     of many partly filled ones; several admitted groups run at the same
@@ -83,6 +84,12 @@ struct Server {
     int max_group = MATCH_MAX_JOBS;  // requests per match launch
     size_t max_queue = 65536;
     std::vector<cudaStream_t> slots;
+    // per slot: streams on which a group's later requests run their
+    // selection and box sums beside the first one's, and an event per
+    // request that the group's match launch waits for
+    static constexpr int HELPERS = 4;
+    std::vector<cudaStream_t> helpers;   // [slot][HELPERS]
+    std::vector<cudaEvent_t> ready;      // [slot][MATCH_MAX_JOBS]
     std::vector<std::vector<uint64_t>> slot_req;  // tickets running on each slot (empty = free)
     std::deque<uint64_t> queue;
     std::unordered_map<uint64_t, Req *> reqs;
@@ -196,7 +203,7 @@ size_t available_bytes(cudaMemPool_t pool)
 // maps copied to its memory.  Fills its match job.  Returns 0 if memory is
 // short right now (q stays queued), 1 if prepared, 2 if it failed (its
 // status is set; nothing of it is left running).
-int prepare(Server *S, Req *q, int k, bool follower, MatchJob *job)
+int prepare(Server *S, Req *q, int k, cudaStream_t s, bool follower, MatchJob *job)
 {
     const nrr_request &r = q->r;
     const Layout L = layout_of(r);
@@ -209,7 +216,6 @@ int prepare(Server *S, Req *q, int k, bool follower, MatchJob *job)
         q->state = FAILED;  // would never fit
         return 2;
     }
-    cudaStream_t s = S->slots[k];
     q->slot = k;
     q->t_admit = now_s();
     q->state = RUNNING;
@@ -278,7 +284,8 @@ bool admit_group(Server *S, int k)
     Req *q0 = S->reqs[t0];
     MatchJob jobs[MATCH_MAX_JOBS];
     std::vector<Req *> group;
-    const int r0 = prepare(S, q0, k, false, &jobs[0]);
+    cudaStream_t s = S->slots[k];
+    const int r0 = prepare(S, q0, k, s, false, &jobs[0]);
     if (r0 == 0) return false;
     S->queue.pop_front();
     if (r0 == 2) return true;
@@ -296,13 +303,29 @@ bool admit_group(Server *S, int k)
             ++pos;
             continue;
         }
-        const int r = prepare(S, q, k, true, &jobs[group.size()]);
+        // a follower's selection and box sums run on a helper stream beside
+        // the others'; the match launch waits for its event
+        const size_t g = group.size();
+        cudaStream_t hs = S->helpers[(size_t)k * Server::HELPERS + (g - 1) % Server::HELPERS];
+        cudaEvent_t ev = S->ready[(size_t)k * MATCH_MAX_JOBS + g];
+        if (cudaEventRecord(ev, s) != cudaSuccess || cudaStreamWaitEvent(hs, ev, 0) != cudaSuccess) break;
+        const int r = prepare(S, q, k, hs, true, &jobs[g]);
         if (r == 0) break;
         S->queue.erase(S->queue.begin() + pos);
-        if (r == 1) group.push_back(q);
+        if (r == 1) {
+            if (cudaEventRecord(ev, hs) != cudaSuccess || cudaStreamWaitEvent(s, ev, 0) != cudaSuccess) {
+                cudaStreamSynchronize(hs);  // nothing of it may still run
+                q->status = fail(NRR_E_CUDA, "event");
+                q->state = FAILED;
+                cudaFreeAsync(q->mem, s);
+                q->mem = nullptr;
+                continue;
+            }
+            group.push_back(q);
+        }
     }
     const nrr_request &r = q0->r;
-    MatchLaunch a{};
+    MatchLaunch a{};  // on the slot's stream, after every member's event
     a.preop = r.d_preop;
     a.intraop = r.d_intraop;
     a.s1 = jobs[0].s1;
@@ -315,7 +338,6 @@ bool admit_group(Server *S, int k)
     for (size_t g = 0; g < group.size(); ++g) a.jobs[g] = jobs[g];
     apply_tuning(a, r.dtype, r.block, r.radius);
     a.err = S->err;
-    cudaStream_t s = S->slots[k];
     nrr_status st = launch_match(a, s);
     for (size_t g = 0; g < group.size() && st == NRR_OK; ++g)
         if (cudaLaunchHostFunc(s, on_done, group[g]) != cudaSuccess) st = fail(NRR_E_CUDA, "host callback");
@@ -417,12 +439,23 @@ nrr_status nrr_server_start_ex(int32_t slots, size_t reserve_bytes, int32_t max_
     S->max_group = max_group;
     S->slots.resize(slots);
     S->slot_req.assign(slots, std::vector<uint64_t>());
-    for (int k = 0; k < slots; ++k) {
-        if (cudaStreamCreateWithFlags(&S->slots[k], cudaStreamNonBlocking) != cudaSuccess) {
-            for (int j = 0; j < k; ++j) cudaStreamDestroy(S->slots[j]);
-            delete S;
-            return fail(NRR_E_CUDA, "stream creation");
-        }
+    S->helpers.assign((size_t)slots * Server::HELPERS, nullptr);
+    S->ready.assign((size_t)slots * MATCH_MAX_JOBS, nullptr);
+    bool ok = true;
+    for (int k = 0; k < slots && ok; ++k) ok = cudaStreamCreateWithFlags(&S->slots[k], cudaStreamNonBlocking) == cudaSuccess;
+    for (auto &h : S->helpers)
+        if (ok) ok = cudaStreamCreateWithFlags(&h, cudaStreamNonBlocking) == cudaSuccess;
+    for (auto &e : S->ready)
+        if (ok) ok = cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        for (auto &st : S->slots)
+            if (st) cudaStreamDestroy(st);
+        for (auto &h : S->helpers)
+            if (h) cudaStreamDestroy(h);
+        for (auto &e : S->ready)
+            if (e) cudaEventDestroy(e);
+        delete S;
+        return fail(NRR_E_CUDA, "stream or event creation");
     }
     S->worker = std::thread(worker_main, S);
     g_server = S;
@@ -446,12 +479,15 @@ nrr_status nrr_server_stop(void)
     S->cv.notify_all();
     S->worker.join();
     for (auto &st : S->slots) cudaStreamSynchronize(st);
+    for (auto &h : S->helpers) cudaStreamSynchronize(h);
     for (auto &kv : S->reqs) {
         Req *q = kv.second;
         if (q->mem) cudaFree(q->mem);
         delete q;
     }
     for (auto &st : S->slots) cudaStreamDestroy(st);
+    for (auto &h : S->helpers) cudaStreamDestroy(h);
+    for (auto &e : S->ready) cudaEventDestroy(e);
     delete S;
     return NRR_OK;
 }
