@@ -227,3 +227,27 @@ def test_plain_launches_and_work_queue_agree(nrr, uneven_pairs):
             for i in range(len(settings)):
                 assert _same([t.cpu().numpy() for t in plan.result(i)], want[i]), (k, rep, i)
         plan.close()
+
+
+@pytest.mark.parametrize("dtype", ["u16", "f32"])
+def test_every_launch_shape_gives_the_same_bits(nrr, pair, dtype):
+    # CTAs per SM, one or two window buffers, box sums loaded at the bound
+    # or staged into shared memory by asynchronous copies: no shape may
+    # change a result bit (the autotuner picks among them)
+    pre, intra, mask, dpre, dintra, dmask = pair
+    p, i = (dpre, dintra) if dtype == "u16" else (torch.from_numpy(synth.as_f32(pre)).cuda(),
+                                                   torch.from_numpy(synth.as_f32(intra)).cuda())
+    code = 0 if dtype == "u16" else 1
+    c = nrr.select_blocks(dpre, dmask, 7, 2, 0.1)
+    for b, r in ((7, 4), (5, (3, 2, 5)), (7, 9)):
+        ref = [t.cpu().numpy() for t in nrr.block_match(p, i, c, b, r)]
+        for k, windows, stage in ((1, 1, 1), (2, 2, 1), (1, 1, 2), (0, 2, 2), (3, 1, 2), (0, 0, 0)):
+            nrr.tuning_set_shape(code, b, r, k, windows, stage)
+            try:
+                got = [t.cpu().numpy() for t in nrr.block_match(p, i, c, b, r)]
+            except nrr.NrrError as e:  # a layout that does not fit is refused, never run
+                assert e.status == -1 and "does not fit" in str(e), str(e)
+                continue
+            nrr.device_status()
+            assert _same(got, ref), (dtype, b, r, k, windows, stage)
+        nrr.tuning_set_shape(code, b, r, 0, 0, 0)
