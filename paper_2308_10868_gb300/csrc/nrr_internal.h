@@ -183,7 +183,7 @@ struct SelectPlan {
     long long ng;
     int nchunks;
     int connectivity;  // 0, 6, 18 or 26
-    size_t off_keys, off_hist, off_state, off_sync, off_cnt, off_list, off_sp_state, off_sp_mask, bytes;
+    size_t off_keys, off_hist, off_state, off_sync, off_cnt, off_list, off_sp_state, off_sp_mask, off_sp_tiles, bytes;
 };
 SelectPlan select_plan(nrr_dims d, int stride, int connectivity = 0);
 nrr_status enqueue_select(const uint16_t *preop, const uint8_t *mask, nrr_dims d, int block, int stride, double frac,
@@ -202,10 +202,12 @@ struct SpacingSync {
     unsigned long long undecided[3];
     unsigned int hist[2048];
 };
+// Tile of the candidate grid the connectivity-pattern kernel works on.
+constexpr int SP_TILE_X = 16, SP_TILE_Y = 8, SP_TILE_Z = 8;
 nrr_status launch_spacing(int connectivity, long long *keys, int gx, int gy, long long ng, double frac,
                           unsigned char *state, unsigned int *hmask, SpacingSync *sync,
                           const unsigned long long *nc, const unsigned long long *maxkey, unsigned long long *npos,
-                          cudaStream_t s);
+                          unsigned int *tile_pend, cudaStream_t s);
 // Offset of the selected count (int64) inside the selection scratch.
 size_t select_count_offset(const SelectPlan &p);
 nrr_status check_select_args(nrr_dims dims, int32_t block, int32_t stride, double frac);

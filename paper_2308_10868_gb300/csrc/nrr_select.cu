@@ -435,11 +435,15 @@ SelectPlan select_plan(nrr_dims d, int stride, int connectivity)
     o += align_up((size_t)p.nchunks * 8, 256);
     p.off_list = o;
     o += align_up(sizeof(long long) * RK_SMALL, 256);
-    p.off_sp_state = p.off_sp_mask = o;
+    p.off_sp_state = p.off_sp_mask = p.off_sp_tiles = o;
     if (connectivity) {
         o += align_up((size_t)p.ng, 256);
         p.off_sp_mask = o;
         o += align_up((size_t)p.ng * 4, 256);
+        p.off_sp_tiles = o;  // a pending flag per tile of the pattern kernel
+        const size_t ntiles = (size_t)((p.gx + SP_TILE_X - 1) / SP_TILE_X) * ((p.gy + SP_TILE_Y - 1) / SP_TILE_Y) *
+                              ((p.gz + SP_TILE_Z - 1) / SP_TILE_Z);
+        o += align_up(ntiles * 4, 256);
     }
     p.bytes = o;
     return p;
@@ -473,7 +477,7 @@ nrr_status enqueue_select(const uint16_t *preop, const uint8_t *mask, nrr_dims d
     if (p.connectivity) {
         nrr_status ss = launch_spacing(p.connectivity, keys, p.gx, p.gy, p.ng, frac, ws + p.off_sp_state,
                                        (unsigned int *)(ws + p.off_sp_mask), (SpacingSync *)(ws + p.off_sync),
-                                       &st->nc, &st->maxkey, &st->npos, s);
+                                       &st->nc, &st->maxkey, &st->npos, (unsigned int *)(ws + p.off_sp_tiles), s);
         if (ss != NRR_OK) return ss;
     }
     // the rank kernel: at most two CTAs per SM (and as many as are resident),

@@ -46,7 +46,7 @@ namespace nrr {
 namespace {
 
 constexpr int SP_THREADS = 256;
-constexpr int TLX = 16, TLY = 8, TLZ = 8, TPTS = TLX * TLY * TLZ;  // tile of candidate grid points
+constexpr int TLX = SP_TILE_X, TLY = SP_TILE_Y, TLZ = SP_TILE_Z, TPTS = TLX * TLY * TLZ;  // tile of candidate grid points
 constexpr int HX = TLX + 2, HY = TLY + 2, HZ = TLZ + 2, HPTS = HX * HY * HZ;  // with a one-point halo
 constexpr int PPT = TPTS / SP_THREADS;  // tile points per thread
 constexpr int SP_MAX_ROUNDS = 1 << 20;
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(SP_THREADS, 2)
     spacing_kernel(long long *__restrict__ keys, int gx, int gy, long long ng, int slots, double frac,
                    unsigned char *__restrict__ state, unsigned int *__restrict__ hmask, SpacingSync *sync,
                    const unsigned long long *nc, const unsigned long long *maxkey, unsigned long long *npos,
-                   unsigned int *err, uint64_t wait_ns, unsigned int missing)
+                   unsigned int *__restrict__ tile_pend, unsigned int *err, uint64_t wait_ns, unsigned int missing)
 {
     constexpr int NOFF = ORDER == 1 ? 6 : ORDER == 2 ? 18 : 26;
     const long long chunk = (long long)slots * SP_THREADS;
@@ -130,6 +130,7 @@ __global__ void __launch_bounds__(SP_THREADS, 2)
     __shared__ unsigned int s_hist[SP_BINS];
     __shared__ unsigned char s_state[HPTS];
     __shared__ unsigned long long s_pend, s_acc;
+    __shared__ unsigned int s_tp;
 
     // ---- each candidate's higher-priority neighbours; histogram of the keys
     for (int e = threadIdx.x; e < SP_BINS; e += SP_THREADS) s_hist[e] = 0;
@@ -178,6 +179,10 @@ __global__ void __launch_bounds__(SP_THREADS, 2)
             if (key >= t_lo && key < t_hi) store_state(state + g, SP_UNDECIDED);
             else if (t_hi == 0x7fffffffffffffffll && key < t_lo) store_state(state + g, SP_OUT_OF_PLAY);
         }
+        // every tile may hold newly undecided points: all of this CTA's tiles
+        // are visited in the next round (a CTA always takes the same tiles)
+        for (int t = blockIdx.x + threadIdx.x * (int)gridDim.x; t < ntiles; t += SP_THREADS * (int)gridDim.x)
+            tile_pend[t] = 1u;
         if (!grid_barrier(&sync->arrive, nb++, wait_ns, missing)) {
             if (threadIdx.x == 0) atomicOr(err, DEV_ERR_TIMEOUT);
             return;
@@ -193,8 +198,13 @@ __global__ void __launch_bounds__(SP_THREADS, 2)
             }
             unsigned int pend = 0, acc = 0;
             for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+                // a tile left with no undecided point has nothing more to
+                // decide (states only move from undecided to final); the flag
+                // was written by this CTA, before a barrier
+                if (__ldcg(tile_pend + t) == 0u) continue;
                 const int i0 = (t % ntx) * TLX, j0 = ((t / ntx) % nty) * TLY, k0 = (t / (ntx * nty)) * TLZ;
                 __syncthreads();  // the previous tile's shared states are no longer read
+                if (threadIdx.x == 0) s_tp = 0;
                 for (int e = threadIdx.x; e < HPTS; e += SP_THREADS) {
                     const int i = i0 - 1 + e % HX, j = j0 - 1 + (e / HX) % HY, k = k0 - 1 + e / (HX * HY);
                     unsigned char v = SP_OUT_OF_PLAY;
@@ -261,6 +271,10 @@ __global__ void __launch_bounds__(SP_THREADS, 2)
                     }
                     pend += (open >> q) & 1u;
                 }
+                // this tile's points still undecided after the pass
+                if (open) atomicAdd(&s_tp, (unsigned int)__popc(open));
+                __syncthreads();
+                if (threadIdx.x == 0) __stcg(tile_pend + t, s_tp);
             }
             if (pend) atomicAdd(&s_pend, (unsigned long long)pend);
             if (acc) atomicAdd(&s_acc, (unsigned long long)acc);
@@ -300,7 +314,8 @@ __global__ void __launch_bounds__(SP_THREADS, 2)
 template <int ORDER>
 nrr_status launch_order(long long *keys, int gx, int gy, long long ng, double frac, unsigned char *state,
                         unsigned int *hmask, SpacingSync *sync, const unsigned long long *nc,
-                        const unsigned long long *maxkey, unsigned long long *npos, cudaStream_t s)
+                        const unsigned long long *maxkey, unsigned long long *npos, unsigned int *tile_pend,
+                        cudaStream_t s)
 {
     auto kern = spacing_kernel<ORDER>;
     int occ = 0;
@@ -318,7 +333,8 @@ nrr_status launch_order(long long *keys, int gx, int gy, long long ng, double fr
     if (st != NRR_OK) return st;
     uint64_t wait_ns = device_wait_ns();
     unsigned int missing = test_missing_arrivals();
-    void *args[] = {&keys, &gx, &gy, &ng, &slots, &frac, &state, &hmask, &sync, &nc, &maxkey, &npos, &err, &wait_ns, &missing};
+    void *args[] = {&keys, &gx,   &gy,  &ng,  &slots,   &frac,    &state,  &hmask,
+                    &sync, &nc,   &maxkey, &npos, &tile_pend, &err, &wait_ns, &missing};
     NRR_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)kern, dim3(blocks), dim3(SP_THREADS), args, 0, s));
     count_launches(1);
     return NRR_OK;
@@ -329,13 +345,13 @@ nrr_status launch_order(long long *keys, int gx, int gy, long long ng, double fr
 nrr_status launch_spacing(int connectivity, long long *keys, int gx, int gy, long long ng, double frac,
                           unsigned char *state, unsigned int *hmask, SpacingSync *sync,
                           const unsigned long long *nc, const unsigned long long *maxkey, unsigned long long *npos,
-                          cudaStream_t s)
+                          unsigned int *tile_pend, cudaStream_t s)
 {
     if (ng <= 0) return NRR_OK;
     switch (connectivity) {
-    case 6: return launch_order<1>(keys, gx, gy, ng, frac, state, hmask, sync, nc, maxkey, npos, s);
-    case 18: return launch_order<2>(keys, gx, gy, ng, frac, state, hmask, sync, nc, maxkey, npos, s);
-    case 26: return launch_order<3>(keys, gx, gy, ng, frac, state, hmask, sync, nc, maxkey, npos, s);
+    case 6: return launch_order<1>(keys, gx, gy, ng, frac, state, hmask, sync, nc, maxkey, npos, tile_pend, s);
+    case 18: return launch_order<2>(keys, gx, gy, ng, frac, state, hmask, sync, nc, maxkey, npos, tile_pend, s);
+    case 26: return launch_order<3>(keys, gx, gy, ng, frac, state, hmask, sync, nc, maxkey, npos, tile_pend, s);
     default: return fail(NRR_E_INVALID, "connectivity %d is not 0, 6, 18 or 26", connectivity);
     }
 }
