@@ -331,7 +331,11 @@ nrr_status nrr_block_match_bs_aniso(const void *d_preop, const void *d_intraop, 
  * more CTAs; 2: the next block's copy overlaps this block's search; 0 = the
  * one that fits more CTAs), and where each thread's box sums come from (0
  * or 1: loaded at the bounds; 2: staged into shared memory by asynchronous
- * copies while the block is searched).  No shape changes a result bit.
+ * copies while the block is searched), and the search lines each thread
+ * owns (uint16 cubic blocks only: 1, or 2 sharing each converted window row;
+ * 0 = by the x-shift count 2r+1 of one window: one line up to 5 and at 9,
+ * else two; float32 and per-axis blocks always take one and ignore the
+ * field).  No shape changes a result bit.
  *
  * nrr_autotune_match times the match kernel for one (dtype, block, radius)
  * at every feasible shape on the given inputs (arguments as
@@ -348,6 +352,7 @@ typedef struct {
     int32_t ctas_per_sm; /* 0..64 */
     int32_t windows;     /* 0..2 */
     int32_t stage;       /* 0..2 */
+    int32_t lines;       /* 0..2 */
 } nrr_match_shape;
 
 nrr_status nrr_autotune_match(const void *d_preop, const void *d_intraop, const void *d_boxsums,

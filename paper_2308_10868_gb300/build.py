@@ -27,7 +27,9 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 
 PLAIN_UNITS = ["nrr_api.cu", "nrr_select.cu", "nrr_spacing.cu", "nrr_boxsum.cu", "nrr_boxsum3.cu", "nrr_match_dispatch.cu", "nrr_tune.cu", "nrr_batch.cu", "nrr_serve.cu"]
-MATCH_VARIANTS = [(f32, b) for f32 in (0, 1) for b in (3, 5, 7, 9, 11)]
+# (float32?, block edge, search lines per thread): uint16 cubic blocks come
+# with one or two lines per thread, float32 with one
+MATCH_VARIANTS = [(0, b, l) for b in (3, 5, 7, 9, 11) for l in (1, 2)] + [(1, b, 1) for b in (3, 5, 7, 9, 11)]
 
 
 def _nvcc() -> str:
@@ -39,12 +41,13 @@ def _nvcc() -> str:
 
 def _units():
     units = []
+    # the match variants first: they take longest
+    for f32, b, lpt in MATCH_VARIANTS:
+        name = f"nrr_match_f32_b{b}.o" if f32 else f"nrr_match_u16_b{b}_l{lpt}.o"
+        defs = [f"-DNRR_INST_F32={f32}", f"-DNRR_INST_B={b}"] + ([] if f32 else [f"-DNRR_INST_LPT={lpt}"])
+        units.append((os.path.join(CSRC, "nrr_match_inst.cu"), os.path.join(OUT_DIR, name), defs))
     for u in PLAIN_UNITS:
         units.append((os.path.join(CSRC, u), os.path.join(OUT_DIR, u.replace(".cu", ".o")), []))
-    for f32, b in MATCH_VARIANTS:
-        name = f"nrr_match_{'f32' if f32 else 'u16'}_b{b}.o"
-        units.append((os.path.join(CSRC, "nrr_match_inst.cu"), os.path.join(OUT_DIR, name),
-                      [f"-DNRR_INST_F32={f32}", f"-DNRR_INST_B={b}"]))
     return units
 
 

@@ -143,6 +143,7 @@ struct MatchLaunch {
     int one_cta_per_block;  // plain launch: one CTA per block instead of persistent CTAs
     int stage_boxsums;      // 0 or 1 = load the box sums at the bounds, 2 = stage them
     int windows;            // window buffers: 0 = by occupancy, 1 or 2
+    int lines;              // search lines per thread: 0 = by x-shift count, 1 or 2 (uint16 cubic blocks only)
     unsigned int *err;
     // work-queue head (device int32) the launcher zeroes on the stream before
     // the kernel; null: the next head of a per-device ring, one ring for

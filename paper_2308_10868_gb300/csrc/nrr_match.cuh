@@ -434,11 +434,17 @@ __host__ __device__ inline int match_units(int py, int pz, int lpt = 2)
     if (lpt == 1) return py * pz;
     return pz * (py / 2) + ((py & 1) ? pz / 2 + (pz & 1) : 0);
 }
-// lines per thread of a kernel variant
-template <typename T, bool ANI>
-__host__ __device__ constexpr int match_lpt()
+// Search lines per thread of a uint16 cubic-block launch when its shape asks
+// for none, by x-shift count P of one (sub-)window.  Measured on the clinical
+// pair (b = 5, 7, 9): one line is 20-30 % faster at P = 5 and 9, where two
+// lines per thread leave a larger share of the CTA's last warp idle (15 units
+// in 32 threads at R = 2, 45 in 64 at R = 4); even at P = 7; two are 10-30 %
+// faster from P = 11 on.  At P = 1 and 3 a single warp holds every line, so
+// one line per thread halves each thread's serial work.  Float32 windows and
+// per-axis blocks always take one line per thread.
+__host__ __device__ constexpr int match_default_lines(int P)
 {
-    return std::is_same<T, float>::value || ANI ? 1 : 2;
+    return P <= 5 || P == 9 ? 1 : 2;
 }
 struct LineUnit {
     int dz0, dy0;  // first line (shift indices 0 .. pz-1, 0 .. py-1)
@@ -893,8 +899,9 @@ __device__ __forceinline__ uint32_t line_survivors(const MatchJob &J, int nl, in
 // LEV: the jobs may report extra radius levels (batched search); without it
 // that code is compiled out.  ANI: the block edges along y and z (a.by,
 // a.bz) may differ from the x edge B; without it they are B and every size
-// below is a compile-time constant.
-template <typename T, int B, int P, bool LEV, bool ANI>
+// below is a compile-time constant.  LPT: search lines per thread (1 or 2;
+// 2 for uint16 cubic blocks only).
+template <typename T, int B, int P, bool LEV, bool ANI, int LPT>
 __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorMap *tmapJ, const CUtensorMap *tmapI)
 {
     constexpr bool F32 = std::is_same<T, float>::value;
@@ -946,7 +953,7 @@ __device__ __forceinline__ void match_body(const MatchParams &a, const CUtensorM
 
     // this thread's lines
     LineUnit un;
-    constexpr int LPT = match_lpt<T, ANI>();
+    static_assert(LPT == 1 || (LPT == 2 && !ANI && !std::is_same<T, float>::value), "lines per thread");
     const bool has_unit = line_unit<LPT>(a.unit_of[tid], py, pz, un);
     const int dz1 = un.dz0 + (un.along_z ? 1 : 0), dy1 = un.dy0 + (un.along_z ? 0 : 1);
 
@@ -1522,12 +1529,12 @@ template <bool F32, int B, int P>
 struct MatchRegs {
     static constexpr int value = !F32 && B <= 7 ? (P <= 9 ? 104 : P <= 11 ? 112 : 128) : 128;
 };
-template <int B, int P, bool LEV, bool ANI>
+template <int B, int P, bool LEV, bool ANI, int LPT>
 __global__ void __maxnreg__((MatchRegs<false, B, P>::value))
     match_kernel_u16(const __grid_constant__ MatchParams a, const __grid_constant__ CUtensorMap tmapJ,
                      const __grid_constant__ CUtensorMap tmapI)
 {
-    match_body<uint16_t, B, P, LEV, ANI>(a, &tmapJ, &tmapI);
+    match_body<uint16_t, B, P, LEV, ANI, LPT>(a, &tmapJ, &tmapI);
 }
 
 template <int B, int P, bool ANI>
@@ -1535,16 +1542,16 @@ __global__ void __maxnreg__((MatchRegs<true, B, P>::value))
     match_kernel_f32(const __grid_constant__ MatchParams a, const __grid_constant__ CUtensorMap tmapJ,
                      const __grid_constant__ CUtensorMap tmapI)
 {
-    match_body<float, B, P, false, ANI>(a, &tmapJ, &tmapI);
+    match_body<float, B, P, false, ANI, 1>(a, &tmapJ, &tmapI);
 }
 
-template <typename T, int B, int P, bool LEV, bool ANI>
+template <typename T, int B, int P, bool LEV, bool ANI, int LPT>
 constexpr auto match_kernel_ptr()
 {
     if constexpr (std::is_same<T, float>::value)
         return match_kernel_f32<B, P, ANI>;  // float32 jobs report no extra levels
     else
-        return match_kernel_u16<B, P, LEV, ANI>;
+        return match_kernel_u16<B, P, LEV, ANI, LPT>;
 }
 
 // Shared-memory layout of a launch: double-buffered windows, unless that
@@ -1603,13 +1610,13 @@ inline void match_unit_order(int py, int pz, int wyp, int bxc, int lpt, int thre
     for (int k = nA; k < nu; ++k) unit_of[t++] = (uint8_t)k;
 }
 
-template <typename T, int B, int P, bool LEV, bool ANI>
+template <typename T, int B, int P, bool LEV, bool ANI, int LPT>
 nrr_status choose_layout(const MatchLaunch &m, MatchLayout *L, bool *single, bool *stage, int *occ)
 {
     constexpr int ALIGN = 16 / (int)sizeof(T);
     const int by = launch_by(m), bz = launch_bz(m);
     const int ry = m.sub_r[1], rz = m.sub_r[2], py = 2 * ry + 1, pz = 2 * rz + 1;
-    const int wyp = match_wyp(by + 2 * ry, py), threads = round_up_i(match_units(py, pz, match_lpt<T, ANI>()), 32);
+    const int wyp = match_wyp(by + 2 * ry, py), threads = round_up_i(match_units(py, pz, LPT), 32);
     // [stage][single]: box sums staged or loaded at the bounds, two window
     // buffers or one
     MatchLayout Ls[2][2];
@@ -1620,7 +1627,7 @@ nrr_status choose_layout(const MatchLaunch &m, MatchLayout *L, bool *single, boo
                                       bz + 2 * rz, py, pz, sw != 0, LEV, by * bz, st != 0, threads);
             most = Ls[st][sw].total > most ? Ls[st][sw].total : most;
         }
-    auto kern = match_kernel_ptr<T, B, P, LEV, ANI>();
+    auto kern = match_kernel_ptr<T, B, P, LEV, ANI, LPT>();
     static int smem_set = 0;  // largest dynamic shared memory opted in so far
     if (most > smem_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
@@ -1654,7 +1661,7 @@ nrr_status choose_layout(const MatchLaunch &m, MatchLayout *L, bool *single, boo
     return NRR_OK;
 }
 
-template <typename T, int B, int P, bool LEV, bool ANI>
+template <typename T, int B, int P, bool LEV, bool ANI, int LPT>
 nrr_status launch_match_variant_l(const MatchLaunch &m, cudaStream_t stream)
 {
     constexpr int ALIGN = 16 / (int)sizeof(T);
@@ -1663,7 +1670,7 @@ nrr_status launch_match_variant_l(const MatchLaunch &m, cudaStream_t stream)
     const int by = launch_by(m), bz = launch_bz(m);
     const int ry = m.sub_r[1], rz = m.sub_r[2], py = 2 * ry + 1, pz = 2 * rz + 1;
     const int wy = by + 2 * ry, wz = bz + 2 * rz, wyp = match_wyp(wy, py);
-    const int threads = round_up_i(match_units(py, pz, match_lpt<T, ANI>()), 32);
+    const int threads = round_up_i(match_units(py, pz, LPT), 32);
     if (threads > MATCH_MAX_THREADS) return fail(NRR_E_INVALID, "search window too large");
     if (wyp > 256) return fail(NRR_E_INVALID, "search window too large");
 
@@ -1682,12 +1689,12 @@ nrr_status launch_match_variant_l(const MatchLaunch &m, cudaStream_t stream)
     st = encode_volume_map(&mapI, m.preop, m.dtype, m.dims, BTX, by, bz);
     if (st != NRR_OK) return st;
 
-    auto kern = match_kernel_ptr<T, B, P, LEV, ANI>();
+    auto kern = match_kernel_ptr<T, B, P, LEV, ANI, LPT>();
     MatchLayout L;
     bool single = false;
     int occ = 0;
     bool stage = false;
-    st = choose_layout<T, B, P, LEV, ANI>(m, &L, &single, &stage, &occ);
+    st = choose_layout<T, B, P, LEV, ANI, LPT>(m, &L, &single, &stage, &occ);
     if (st != NRR_OK) return st;
     if (occ < 1) return fail(NRR_E_INVALID, "match kernel does not fit on an SM (%d B shared)", L.total);
     if (m.ctas_per_sm > 0 && m.ctas_per_sm < occ) occ = m.ctas_per_sm;
@@ -1711,7 +1718,7 @@ nrr_status launch_match_variant_l(const MatchLaunch &m, cudaStream_t stream)
     p.n_jobs = m.n_jobs;
     p.single_window = single ? 1 : 0;
     p.stage = stage ? 1 : 0;
-    match_unit_order(py, pz, wyp, BX * (int)sizeof(T) / 16, match_lpt<T, ANI>(), threads, p.unit_of);
+    match_unit_order(py, pz, wyp, BX * (int)sizeof(T) / 16, LPT, threads, p.unit_of);
     p.by = by;
     p.bz = bz;
     for (int j = 0; j < MATCH_MAX_JOBS; ++j) {
@@ -1750,43 +1757,64 @@ nrr_status launch_match_variant_l(const MatchLaunch &m, cudaStream_t stream)
     return NRR_OK;
 }
 
+// Search lines per thread of a launch (sub-windows planned): two only for
+// uint16 cubic blocks, as the launch's shape asks, else by the window's
+// x-shift count.
+inline int match_lines(const MatchLaunch &m)
+{
+    if (m.dtype != NRR_U16 || launch_by(m) != m.block || launch_bz(m) != m.block) return 1;
+    if (m.lines == 1 || m.lines == 2) return m.lines;
+    return match_default_lines(2 * m.sub_r[0] + 1);
+}
+
 // Launches whose jobs report extra radius levels use the level-aware kernel
 // (uint16 only: the batched search runs on uint16 volumes).
 // Launches whose blocks have other edges along y or z than along x use the
-// variant with those edges at run time.
-template <typename T, int B, int P>
+// variant with those edges at run time (one line per thread).
+template <typename T, int B, int P, int LPT>
 nrr_status launch_match_variant(const MatchLaunch &m, cudaStream_t stream)
 {
     bool lev = false;
     for (int j = 0; j < m.n_jobs; ++j) lev |= m.jobs[j].n_levels > 0;
     const bool ani = launch_by(m) != B || launch_bz(m) != B;
-    if (ani) {
-        if (lev) return fail(NRR_E_INTERNAL, "extra radius levels are not supported for anisotropic blocks");
-        return launch_match_variant_l<T, B, P, false, true>(m, stream);
+    if constexpr (LPT == 2) {
+        if (ani) return fail(NRR_E_INTERNAL, "two lines per thread need a cubic block");
+        return lev ? launch_match_variant_l<T, B, P, true, false, 2>(m, stream)
+                   : launch_match_variant_l<T, B, P, false, false, 2>(m, stream);
+    } else {
+        if (ani) {
+            if (lev) return fail(NRR_E_INTERNAL, "extra radius levels are not supported for anisotropic blocks");
+            return launch_match_variant_l<T, B, P, false, true, 1>(m, stream);
+        }
+        if (!lev) return launch_match_variant_l<T, B, P, false, false, 1>(m, stream);
+        if constexpr (std::is_same<T, float>::value)
+            return fail(NRR_E_INTERNAL, "extra radius levels are not supported for float32 volumes");
+        else
+            return launch_match_variant_l<T, B, P, true, false, 1>(m, stream);
     }
-    if (!lev) return launch_match_variant_l<T, B, P, false, false>(m, stream);
-    if constexpr (std::is_same<T, float>::value)
-        return fail(NRR_E_INTERNAL, "extra radius levels are not supported for float32 volumes");
-    else
-        return launch_match_variant_l<T, B, P, true, false>(m, stream);
 }
 
-template <typename T, int B, int P>
+template <typename T, int B, int P, int LPT>
 nrr_status occupancy_variant(const MatchLaunch &m, int *occ)
 {
     MatchLayout L;
     bool single = false;
     bool stage = false;
-    if (launch_by(m) != B || launch_bz(m) != B) return choose_layout<T, B, P, false, true>(m, &L, &single, &stage, occ);
-    return choose_layout<T, B, P, false, false>(m, &L, &single, &stage, occ);
+    if constexpr (LPT == 2) {
+        return choose_layout<T, B, P, false, false, 2>(m, &L, &single, &stage, occ);
+    } else {
+        if (launch_by(m) != B || launch_bz(m) != B)
+            return choose_layout<T, B, P, false, true, 1>(m, &L, &single, &stage, occ);
+        return choose_layout<T, B, P, false, false, 1>(m, &L, &single, &stage, occ);
+    }
 }
 
-template <typename T, int B>
+template <typename T, int B, int LPT>
 nrr_status launch_match_b(const MatchLaunch &m, cudaStream_t stream, int *occ)
 {
     switch (m.sub_r[0]) {
 #define NRR_CASE(r, p) \
-    case r: return occ ? occupancy_variant<T, B, p>(m, occ) : launch_match_variant<T, B, p>(m, stream);
+    case r: return occ ? occupancy_variant<T, B, p, LPT>(m, occ) : launch_match_variant<T, B, p, LPT>(m, stream);
         NRR_CASE(0, 1)
         NRR_CASE(1, 3)
         NRR_CASE(2, 5)
@@ -1800,13 +1828,18 @@ nrr_status launch_match_b(const MatchLaunch &m, cudaStream_t stream, int *occ)
     return fail(NRR_E_INVALID, "sub-window radius x %d outside 0..%d", m.sub_r[0], MATCH_WINDOW_R);
 }
 
-// One entry per (element type, block size); defined in the instantiation
-// translation units.
-nrr_status launch_match_u16_b3(const MatchLaunch &, cudaStream_t, int *);
-nrr_status launch_match_u16_b5(const MatchLaunch &, cudaStream_t, int *);
-nrr_status launch_match_u16_b7(const MatchLaunch &, cudaStream_t, int *);
-nrr_status launch_match_u16_b9(const MatchLaunch &, cudaStream_t, int *);
-nrr_status launch_match_u16_b11(const MatchLaunch &, cudaStream_t, int *);
+// One entry per (element type, block size, lines per thread); defined in the
+// instantiation translation units.  Float32 variants take one line per
+// thread.
+#define NRR_DECL_U16(b)                                                        \
+    nrr_status launch_match_u16_b##b##_l1(const MatchLaunch &, cudaStream_t, int *); \
+    nrr_status launch_match_u16_b##b##_l2(const MatchLaunch &, cudaStream_t, int *);
+NRR_DECL_U16(3)
+NRR_DECL_U16(5)
+NRR_DECL_U16(7)
+NRR_DECL_U16(9)
+NRR_DECL_U16(11)
+#undef NRR_DECL_U16
 nrr_status launch_match_f32_b3(const MatchLaunch &, cudaStream_t, int *);
 nrr_status launch_match_f32_b5(const MatchLaunch &, cudaStream_t, int *);
 nrr_status launch_match_f32_b7(const MatchLaunch &, cudaStream_t, int *);

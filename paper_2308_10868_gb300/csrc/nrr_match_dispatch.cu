@@ -1,17 +1,31 @@
-// Chooses the match-kernel variant for a call's element type and block size.
+// Chooses the match-kernel variant for a call's element type, block size and
+// search lines per thread.
 #include "nrr_match.cuh"
 
 namespace nrr {
 
 static nrr_status dispatch(const MatchLaunch &m, cudaStream_t stream, int *occ)
 {
-    const bool f = m.dtype == NRR_F32;
+    if (m.dtype == NRR_F32) {
+        switch (m.block) {
+        case 3: return launch_match_f32_b3(m, stream, occ);
+        case 5: return launch_match_f32_b5(m, stream, occ);
+        case 7: return launch_match_f32_b7(m, stream, occ);
+        case 9: return launch_match_f32_b9(m, stream, occ);
+        case 11: return launch_match_f32_b11(m, stream, occ);
+        }
+        return fail(NRR_E_INVALID, "block %d not supported", m.block);
+    }
+    const bool two = match_lines(m) == 2;
     switch (m.block) {
-    case 3: return f ? launch_match_f32_b3(m, stream, occ) : launch_match_u16_b3(m, stream, occ);
-    case 5: return f ? launch_match_f32_b5(m, stream, occ) : launch_match_u16_b5(m, stream, occ);
-    case 7: return f ? launch_match_f32_b7(m, stream, occ) : launch_match_u16_b7(m, stream, occ);
-    case 9: return f ? launch_match_f32_b9(m, stream, occ) : launch_match_u16_b9(m, stream, occ);
-    case 11: return f ? launch_match_f32_b11(m, stream, occ) : launch_match_u16_b11(m, stream, occ);
+#define NRR_U16(b) \
+    case b: return two ? launch_match_u16_b##b##_l2(m, stream, occ) : launch_match_u16_b##b##_l1(m, stream, occ);
+        NRR_U16(3)
+        NRR_U16(5)
+        NRR_U16(7)
+        NRR_U16(9)
+        NRR_U16(11)
+#undef NRR_U16
     }
     return fail(NRR_E_INVALID, "block %d not supported", m.block);
 }

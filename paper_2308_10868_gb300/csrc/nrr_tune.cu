@@ -2,9 +2,10 @@
 //
 // The paper tunes its GPU block-matching kernel by an empirical search over
 // the thread configuration (Sec. 4.3, GADAPT), reporting ~30x between tuned
-// and untuned.  Here the per-block tile (two search lines per thread) is
-// fixed by the block size and search radius; the free parameters of a
-// launch's shape are
+// and untuned.  Here the free parameters of a launch's shape are
+//   - the search lines each thread owns (uint16 cubic blocks: one, or two
+//     sharing each converted window row; which is faster depends on how the
+//     line units fill the CTA's last warp),
 //   - how many persistent CTAs share an SM (fewer leave more shared-memory
 //     bandwidth and L1 to each; more hide more latency),
 //   - the window buffers, i.e. blocks in flight per CTA (two: the next
@@ -42,7 +43,7 @@ static nrr_match_shape tuned_shape(nrr_dtype dtype, int block, const int32_t *ra
 {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(make_key(dtype, block, radius));
-    return it == g_tune.end() ? nrr_match_shape{0, 0, 0} : it->second;
+    return it == g_tune.end() ? nrr_match_shape{0, 0, 0, 0} : it->second;
 }
 
 void apply_tuning(MatchLaunch &a, nrr_dtype dtype, int block, const int32_t *radius)
@@ -51,12 +52,13 @@ void apply_tuning(MatchLaunch &a, nrr_dtype dtype, int block, const int32_t *rad
     a.ctas_per_sm = sh.ctas_per_sm;
     a.windows = sh.windows;
     a.stage_boxsums = sh.stage;
+    a.lines = sh.lines;
 }
 
 static bool shape_ok(const nrr_match_shape &s)
 {
     return s.ctas_per_sm >= 0 && s.ctas_per_sm <= 64 && s.windows >= 0 && s.windows <= 2 && s.stage >= 0 &&
-           s.stage <= 2;
+           s.stage <= 2 && s.lines >= 0 && s.lines <= 2;
 }
 
 static void set_tuned(nrr_dtype dtype, int block, const int32_t *radius, const nrr_match_shape &v)
@@ -83,7 +85,7 @@ nrr_status nrr_tuning_set(nrr_dtype dtype, int32_t block, const int32_t radius[3
 {
     clear_error();
     if (!radius || ctas_per_sm < 0 || ctas_per_sm > 64) return fail(NRR_E_INVALID, "bad tuning entry");
-    set_tuned(dtype, block, radius, nrr_match_shape{ctas_per_sm, 0, 0});
+    set_tuned(dtype, block, radius, nrr_match_shape{ctas_per_sm, 0, 0, 0});
     return NRR_OK;
 }
 
@@ -110,11 +112,11 @@ nrr_status nrr_tuning_save(const char *path)
     if (!f) return fail(NRR_E_INVALID, "cannot open tuning file for writing");
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        fprintf(f, "# device dtype block rx ry rz ctas_per_sm windows stage\n");
+        fprintf(f, "# device dtype block rx ry rz ctas_per_sm windows stage lines\n");
         for (auto &kv : g_tune)
-            fprintf(f, "%d %d %d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
+            fprintf(f, "%d %d %d %d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
                     std::get<2>(kv.first), std::get<3>(kv.first), std::get<4>(kv.first), std::get<5>(kv.first),
-                    kv.second.ctas_per_sm, kv.second.windows, kv.second.stage);
+                    kv.second.ctas_per_sm, kv.second.windows, kv.second.stage, kv.second.lines);
     }
     fclose(f);
     return NRR_OK;
@@ -129,12 +131,13 @@ nrr_status nrr_tuning_load(const char *path)
     int n = 0;
     while (fgets(line, sizeof line, f)) {
         int d, t, b, x, y, z;
-        nrr_match_shape v{0, 0, 0};
+        nrr_match_shape v{0, 0, 0, 0};
         if (line[0] == '#') continue;
-        // a line without the last two fields (ctas per SM only) leaves them by occupancy
-        const int k = sscanf(line, "%d %d %d %d %d %d %d %d %d", &d, &t, &b, &x, &y, &z, &v.ctas_per_sm, &v.windows,
-                             &v.stage);
-        if ((k == 7 || k == 9) && shape_ok(v)) {
+        // a line of 7 fields (ctas per SM only) or 9 (no lines per thread)
+        // leaves the missing ones at their defaults
+        const int k = sscanf(line, "%d %d %d %d %d %d %d %d %d %d", &d, &t, &b, &x, &y, &z, &v.ctas_per_sm,
+                             &v.windows, &v.stage, &v.lines);
+        if ((k == 7 || k == 9 || k == 10) && shape_ok(v)) {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             g_tune[TuneKey(d, t, b, x, y, z)] = v;
             ++n;
@@ -173,34 +176,38 @@ nrr_status nrr_autotune_match(const void *d_preop, const void *d_intraop, const 
     cudaEvent_t e0, e1;
     NRR_CUDA_TRY(cudaEventCreate(&e0));
     NRR_CUDA_TRY(cudaEventCreate(&e1));
-    nrr_match_shape best{0, 0, 0};
+    nrr_match_shape best{0, 0, 0, 0};
     float best_t = 1e30f;
-    for (int stage = 1; stage <= 2 && st == NRR_OK; ++stage)
-        for (int windows = 2; windows >= 1 && st == NRR_OK; --windows) {
-            a.stage_boxsums = stage;
-            a.windows = windows;
-            a.ctas_per_sm = 0;
-            int occ = 0;
-            st = match_occupancy(a, &occ);
-            for (int k = occ; k >= 1 && st == NRR_OK; --k) {
-                a.ctas_per_sm = k;
-                st = launch_match(a, s);  // warm-up
-                float tot = 0.f;
-                for (int rep = 0; rep < 3 && st == NRR_OK; ++rep) {
-                    cudaEventRecord(e0, s);
-                    st = launch_match(a, s);
-                    cudaEventRecord(e1, s);
-                    if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(NRR_E_CUDA, "event sync during tuning");
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    tot += ms;
-                }
-                if (st == NRR_OK && tot / 3 < best_t) {
-                    best_t = tot / 3;
-                    best = nrr_match_shape{k, windows, stage};
+    // two lines per thread exist for uint16 cubic blocks only
+    const int max_lines = dtype == NRR_U16 ? 2 : 1;
+    for (int lines = 1; lines <= max_lines && st == NRR_OK; ++lines)
+        for (int stage = 1; stage <= 2 && st == NRR_OK; ++stage)
+            for (int windows = 2; windows >= 1 && st == NRR_OK; --windows) {
+                a.lines = lines;
+                a.stage_boxsums = stage;
+                a.windows = windows;
+                a.ctas_per_sm = 0;
+                int occ = 0;
+                st = match_occupancy(a, &occ);
+                for (int k = occ; k >= 1 && st == NRR_OK; --k) {
+                    a.ctas_per_sm = k;
+                    st = launch_match(a, s);  // warm-up
+                    float tot = 0.f;
+                    for (int rep = 0; rep < 3 && st == NRR_OK; ++rep) {
+                        cudaEventRecord(e0, s);
+                        st = launch_match(a, s);
+                        cudaEventRecord(e1, s);
+                        if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(NRR_E_CUDA, "event sync during tuning");
+                        float ms = 0.f;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        tot += ms;
+                    }
+                    if (st == NRR_OK && tot / 3 < best_t) {
+                        best_t = tot / 3;
+                        best = nrr_match_shape{k, windows, stage, max_lines > 1 ? lines : 0};
+                    }
                 }
             }
-        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != NRR_OK) return st;

@@ -38,7 +38,7 @@ class BatchView(C.Structure):
 
 
 class MatchShape(C.Structure):
-    _fields_ = [("ctas_per_sm", C.c_int32), ("windows", C.c_int32), ("stage", C.c_int32)]
+    _fields_ = [("ctas_per_sm", C.c_int32), ("windows", C.c_int32), ("stage", C.c_int32), ("lines", C.c_int32)]
 
 
 class Pair(C.Structure):
@@ -350,16 +350,17 @@ def tuning_set(dtype_code: int, block: int, radius, ctas_per_sm: int):
 
 
 def tuning_get_shape(dtype_code: int, block: int, radius):
-    """The tuned launch shape (ctas_per_sm, windows, stage) of a variant."""
+    """The tuned launch shape (ctas_per_sm, windows, stage, lines) of a variant."""
     r = (C.c_int32 * 3)(*radius3(radius))
     v = MatchShape()
     _check(lib().nrr_tuning_get_shape(dtype_code, block, r, C.byref(v)), "nrr_tuning_get_shape")
-    return int(v.ctas_per_sm), int(v.windows), int(v.stage)
+    return int(v.ctas_per_sm), int(v.windows), int(v.stage), int(v.lines)
 
 
-def tuning_set_shape(dtype_code: int, block: int, radius, ctas_per_sm: int, windows: int = 0, stage: int = 0):
+def tuning_set_shape(dtype_code: int, block: int, radius, ctas_per_sm: int, windows: int = 0, stage: int = 0,
+                     lines: int = 0):
     r = (C.c_int32 * 3)(*radius3(radius))
-    v = MatchShape(ctas_per_sm, windows, stage)
+    v = MatchShape(ctas_per_sm, windows, stage, lines)
     _check(lib().nrr_tuning_set_shape(dtype_code, block, r, C.byref(v)), "nrr_tuning_set_shape")
 
 

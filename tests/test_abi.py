@@ -136,21 +136,21 @@ def test_tuning_shape_entries_need_no_device(L):
     from paper_2308_10868_gb300 import nrr
 
     r = (C.c_int32 * 3)(3, 3, 3)
-    for bad in ((65, 0, 0), (-1, 0, 0), (1, 3, 0), (1, 0, 3), (1, -1, 0)):
+    for bad in ((65, 0, 0), (-1, 0, 0), (1, 3, 0), (1, 0, 3), (1, -1, 0), (1, 0, 0, 3), (1, 0, 0, -1)):
         sh = nrr.MatchShape(*bad)
         assert L.nrr_tuning_set_shape(0, 7, r, C.byref(sh)) == -1
     assert L.nrr_tuning_set_shape(0, 7, r, None) == -1
     assert L.nrr_tuning_get_shape(0, 7, r, None) == -1
-    sh = nrr.MatchShape(3, 1, 2)
+    sh = nrr.MatchShape(3, 1, 2, 1)
     assert L.nrr_tuning_set_shape(0, 7, r, C.byref(sh)) == 0
     got = nrr.MatchShape()
     assert L.nrr_tuning_get_shape(0, 7, r, C.byref(got)) == 0
-    assert (got.ctas_per_sm, got.windows, got.stage) == (3, 1, 2)
+    assert (got.ctas_per_sm, got.windows, got.stage, got.lines) == (3, 1, 2, 1)
     k = C.c_int32(0)
     assert L.nrr_tuning_get(0, 7, r, C.byref(k)) == 0 and k.value == 3
     assert L.nrr_tuning_set(0, 7, r, 0) == 0  # ctas only: the other fields back to "by occupancy"
     assert L.nrr_tuning_get_shape(0, 7, r, C.byref(got)) == 0
-    assert (got.ctas_per_sm, got.windows, got.stage) == (0, 0, 0)
+    assert (got.ctas_per_sm, got.windows, got.stage, got.lines) == (0, 0, 0, 0)
 
 
 def test_tuning_table_save_and_load(L, tmp_path):
@@ -159,21 +159,26 @@ def test_tuning_table_save_and_load(L, tmp_path):
     from paper_2308_10868_gb300 import nrr
 
     r = (C.c_int32 * 3)(5, 4, 3)
-    assert L.nrr_tuning_set_shape(0, 9, r, C.byref(nrr.MatchShape(2, 2, 1))) == 0
+    assert L.nrr_tuning_set_shape(0, 9, r, C.byref(nrr.MatchShape(2, 2, 1, 2))) == 0
     path = str(tmp_path / "tune.txt")
     assert L.nrr_tuning_save(path.encode()) == 0
     text = open(path).read()
-    assert "ctas_per_sm windows stage" in text
+    assert "ctas_per_sm windows stage lines" in text
     assert L.nrr_tuning_set_shape(0, 9, r, C.byref(nrr.MatchShape(0, 0, 0))) == 0
     assert L.nrr_tuning_load(path.encode()) == 0
     got = nrr.MatchShape()
     assert L.nrr_tuning_get_shape(0, 9, r, C.byref(got)) == 0
-    assert (got.ctas_per_sm, got.windows, got.stage) == (2, 2, 1)
+    assert (got.ctas_per_sm, got.windows, got.stage, got.lines) == (2, 2, 1, 2)
     # a line of the older form (CTAs per SM only) leaves the other fields by occupancy
     old = tmp_path / "old.txt"
     dev = text.splitlines()[1].split()[0]
     old.write_text(f"# device dtype block rx ry rz ctas_per_sm\n{dev} 0 9 5 4 3 4\n")
     assert L.nrr_tuning_load(str(old).encode()) == 0
     assert L.nrr_tuning_get_shape(0, 9, r, C.byref(got)) == 0
-    assert (got.ctas_per_sm, got.windows, got.stage) == (4, 0, 0)
+    assert (got.ctas_per_sm, got.windows, got.stage, got.lines) == (4, 0, 0, 0)
+    # and a line without the lines per thread leaves them by x-shift count
+    old.write_text(f"# device dtype block rx ry rz ctas_per_sm windows stage\n{dev} 0 9 5 4 3 3 1 2\n")
+    assert L.nrr_tuning_load(str(old).encode()) == 0
+    assert L.nrr_tuning_get_shape(0, 9, r, C.byref(got)) == 0
+    assert (got.ctas_per_sm, got.windows, got.stage, got.lines) == (3, 1, 2, 0)
     assert L.nrr_tuning_set_shape(0, 9, r, C.byref(nrr.MatchShape(0, 0, 0))) == 0

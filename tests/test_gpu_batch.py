@@ -232,8 +232,9 @@ def test_plain_launches_and_work_queue_agree(nrr, uneven_pairs):
 @pytest.mark.parametrize("dtype", ["u16", "f32"])
 def test_every_launch_shape_gives_the_same_bits(nrr, pair, dtype):
     # CTAs per SM, one or two window buffers, box sums loaded at the bound
-    # or staged into shared memory by asynchronous copies: no shape may
-    # change a result bit (the autotuner picks among them)
+    # or staged into shared memory by asynchronous copies, one or two search
+    # lines per thread (float32 ignores the field): no shape may change a
+    # result bit (the autotuner picks among them)
     pre, intra, mask, dpre, dintra, dmask = pair
     p, i = (dpre, dintra) if dtype == "u16" else (torch.from_numpy(synth.as_f32(pre)).cuda(),
                                                    torch.from_numpy(synth.as_f32(intra)).cuda())
@@ -241,13 +242,32 @@ def test_every_launch_shape_gives_the_same_bits(nrr, pair, dtype):
     c = nrr.select_blocks(dpre, dmask, 7, 2, 0.1)
     for b, r in ((7, 4), (5, (3, 2, 5)), (7, 9)):
         ref = [t.cpu().numpy() for t in nrr.block_match(p, i, c, b, r)]
-        for k, windows, stage in ((1, 1, 1), (2, 2, 1), (1, 1, 2), (0, 2, 2), (3, 1, 2), (0, 0, 0)):
-            nrr.tuning_set_shape(code, b, r, k, windows, stage)
+        for k, windows, stage, lines in ((1, 1, 1, 2), (2, 2, 1, 1), (1, 1, 2, 1), (0, 2, 2, 2), (3, 1, 2, 2),
+                                         (0, 0, 0, 1), (0, 0, 0, 2), (0, 0, 0, 0)):
+            nrr.tuning_set_shape(code, b, r, k, windows, stage, lines)
             try:
                 got = [t.cpu().numpy() for t in nrr.block_match(p, i, c, b, r)]
             except nrr.NrrError as e:  # a layout that does not fit is refused, never run
                 assert e.status == -1 and "does not fit" in str(e), str(e)
                 continue
             nrr.device_status()
-            assert _same(got, ref), (dtype, b, r, k, windows, stage)
+            assert _same(got, ref), (dtype, b, r, k, windows, stage, lines)
         nrr.tuning_set_shape(code, b, r, 0, 0, 0)
+
+
+def test_one_and_two_lines_per_thread_agree_at_every_window_width(nrr, pair):
+    # uint16 cubic blocks: every x-shift count 1..15 of one window (radius
+    # 0..7) and every block size, searched with one and with two lines per
+    # thread, gives the same bits (the default picks one of the two by the
+    # x-shift count)
+    pre, intra, mask, dpre, dintra, dmask = pair
+    for b, r in ((3, 0), (5, 1), (7, 2), (9, 3), (11, 4), (5, 5), (7, 6), (3, 7), (9, (2, 5, 3))):
+        c = nrr.select_blocks(dpre, dmask, b, 2, 0.02)
+        outs = []
+        for lines in (1, 2):
+            nrr.tuning_set_shape(0, b, r, 0, 0, 0, lines)
+            outs.append([t.cpu().numpy() for t in nrr.block_match(dpre, dintra, c, b, r)])
+            nrr.device_status()
+        nrr.tuning_set_shape(0, b, r, 0, 0, 0)
+        assert _same(outs[0], outs[1]), (b, r)
+        assert outs[0][2].any(), (b, r)  # some blocks found a valid match
