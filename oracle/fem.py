@@ -34,7 +34,10 @@ references; the readings taken here are:
   lower block index, never a block whose residual is at most R2_MIN =
   1e-6 voxel^2, i.e. a thousandth of a voxel: such a block agrees with the
   field and its rank would be set by rounding), which get s_k = 0;
-  then N_int interpolation steps (solves without rejection).
+  then N_int interpolation steps (solves without rejection); a step with
+  no block left with s_k > 0 keeps U_{i+1} = U_i (the system is then K U =
+  K U_i, whose solutions differ by rigid motions; U_i is the one with the
+  least correction).
 
 Every function names the step of the method it computes; the linear solve is
 scipy's sparse direct solver (a library primitive).
@@ -278,6 +281,10 @@ class Model:
     def step(self, U: np.ndarray, s: np.ndarray, disp: np.ndarray) -> np.ndarray:
         """U_{i+1} = [K + H^T S H]^{-1} [H^T S D + K U_i] over the model's
         unknowns (the other vertices stay at 0)."""
+        if not (s > 0).any():
+            # no trusted block: K U = K U_i, and U_i is the solution (the
+            # correction of least norm), since K alone fixes no rigid motion
+            return U.copy()
         S3 = sp.diags(np.repeat(s, 3))
         A = (self.K + self.H.T @ S3 @ self.H).tocsr()
         rhs = self.H.T @ (S3 @ disp.reshape(-1).astype(np.float64)) + self.K @ U

@@ -258,3 +258,18 @@ def test_direct_solve_equals_dense_solve():
     A = np.asarray(A)
     rhs = (m.H.T @ (np.repeat(s, 3) * disp.ravel()) + m.K @ U0)[on]
     assert np.allclose(U[on], np.linalg.solve(A, rhs), rtol=1e-10, atol=1e-10)
+
+
+def test_step_without_trusted_blocks_keeps_the_field():
+    rng = np.random.default_rng(15)
+    mask = _mask(16, 16, 12)
+    c = _blocks(mask, G, 20, rng)
+    m = fem.Model(mask, c, G, E, NU)
+    U0 = rng.standard_normal(m.K.shape[0]) * m.dof_on
+    assert np.array_equal(m.step(U0, np.zeros(len(c)), np.ones((len(c), 3))), U0)
+    # F_r = 1 rejects every block with a residual: the next step keeps U
+    disp = rng.integers(-3, 4, size=(len(c), 3))
+    U, s, rej, when = fem.update(mask, c, disp, np.ones(len(c)), np.ones(len(c)), G, E, NU, 2, 0, 1.0)
+    assert (s == 0).all() and (when == 0).all()
+    U1, *_ = fem.update(mask, c, disp, np.ones(len(c)), np.ones(len(c)), G, E, NU, 1, 0, 1.0)
+    assert np.array_equal(U, U1)
