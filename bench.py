@@ -57,6 +57,7 @@ def _args():
     p.add_argument("--no-spacing", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-small", action="store_true")
+    p.add_argument("--no-fem", action="store_true")
     p.add_argument("--serve-open-requests", type=int, default=1000)  # 50 s at 20 req/s
     p.add_argument("--serve-sweep-requests", type=int, default=300)
     p.add_argument("--serve-closed-requests", type=int, default=1000)
@@ -213,6 +214,19 @@ def _cpu_baseline(w, pre, intra, mask):
     return {"value": ev / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"whole workload: selection of {n} blocks + matching all of them ({ev} evals), "
                       f"{dt:.2f} s, FP64 C oracle, OpenMP over blocks"}
+
+
+def _cpu_baseline_fem(d_mask, centers, n_sel, out):
+    """The FEM oracle (scipy sparse direct solves, FP64) on the bench's FEM
+    leg inputs at vertex spacing 8, timed once on the host."""
+    from oracle import fem as ofem
+
+    n = int(n_sel.item())
+    args = [t.cpu().numpy() for t in (d_mask, centers[:n], out[0][:n], out[1][:n], out[2][:n])]
+    t0 = time.perf_counter()
+    ofem.update(*args, 8, 1.0, 0.45, 2, 1, 0.05)
+    return {"kind": "oracle", "grid": 8, "update_s": time.perf_counter() - t0,
+            "sample": "the whole update (2 approximation steps + 1 interpolation step), numpy/scipy, one process"}
 
 
 def run_reference(a):
@@ -700,6 +714,40 @@ def _spacing(a, nrr, synth, d_pre, d_mask, w, flush):
     return out
 
 
+def _fem(a, nrr, d_mask, centers, n_sel, out, w, flush):
+    """The robust finite-element update (nrr_fem_update) on the step's block
+    matches: device time per update (CUDA events, best of 3, L2 flushed
+    before each) at vertex spacings 8 and 4 voxels, with each solve's
+    conjugate-gradient iterations; E = 1, nu = 0.45, two approximation steps
+    rejecting 5 % each and one interpolation step, tolerance 1e-10 on the
+    warm start's residual.  (The oracle's time for the same update is part
+    of the CPU-baseline leg.)"""
+    import torch
+
+    stream = torch.cuda.current_stream()
+    n = int(n_sel.item())
+    c, disp, ncc, valid = centers[:n], out[0][:n], out[1][:n], out[2][:n]
+    kw = dict(young=1.0, poisson=0.45, n_rej=2, n_int=1, reject_frac=0.05, cg_tol=1e-10)
+    res = {"workload": w.name + " block matches", "n_blocks": n, "params": kw,
+           "timing": "CUDA events around one nrr_fem_update call (which waits once for its stream), best of 3"}
+    for g in (8, 4):
+        ts, iters = [], None
+        for _ in range(4):
+            flush.fill_(5)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            U, sk, step, iters = nrr.fem_update(d_mask, c, disp, ncc, valid, grid=g, **kw)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        nrr.device_status()
+        nv = U.shape[0] * U.shape[1] * U.shape[2]
+        res[f"grid{g}"] = {"update_ms": min(ts[1:]), "vertices": nv, "cg_iterations": iters,
+                           "ms_per_cg_iteration": min(ts[1:]) / max(1, sum(iters)),
+                           "rejected": int((step >= 0).sum().item()), "max_abs_U": float(U.abs().max().item())}
+    return res
+
+
 def _phases(w, select_ms, box_ms, match_ms, peaks):
     """Device time of the three phases of a step (CUDA events on the launching
     stream, averaged over the timed steps) and, for the two HBM-type phases,
@@ -1051,8 +1099,12 @@ def run_ours(a):
         line["spacing"] = _spacing(a, nrr, synth, d_pre, d_mask, w, flush)
     if not a.no_aniso:
         line["aniso"] = _aniso(a, nrr, synth, d_pre, d_intra, d_mask, w, flush)
+    if not a.no_fem:
+        line["fem"] = _fem(a, nrr, d_mask, centers, n_sel, out, w, flush)
     if world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(w, pre, intra, mask)
+        if not a.no_fem:
+            line["cpu_baseline"]["fem"] = _cpu_baseline_fem(d_mask, centers, n_sel, out)
     print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()

@@ -510,6 +510,81 @@ nrr_status nrr_submit(const nrr_request *req, uint64_t *ticket);
 nrr_status nrr_poll(uint64_t ticket, nrr_result *out);
 nrr_status nrr_release(uint64_t ticket);
 
+/* ---- Robust finite-element update (Sec. 3 equation; Sec. 5 N_rej, N_int,
+ * F_r) ------------------------------------------------------------------------
+ * The step that consumes the block matches: mesh vertex displacements U
+ * balance a linear elastic model against the matched displacements D,
+ *     F_i = K U_i,   U_{i+1} = [K + H^T S H]^{-1} [H^T S D + F_i],
+ * K the stiffness matrix, H the interpolation from mesh vertices to the
+ * block centres, S the diagonal confidence of the matches.  The paper
+ * leaves mesh, material, S and the rejection rule to its references; this
+ * library reads them as:
+ *   mesh      8-node hexahedra on a grid of vertices every `grid` voxels
+ *             from the origin (Nx = ceil((nx - 1) / grid) + 1 per axis, the
+ *             last vertex at or past the last voxel); an element is in the
+ *             model when d_mask is set at its centre voxel (e * grid +
+ *             grid / 2 per axis, clamped into the volume); vertices of no
+ *             such element stay at U = 0;
+ *   material  homogeneous isotropic linear elasticity (young, poisson),
+ *             lengths in voxels, element stiffness by 2x2x2 Gauss points;
+ *   H         trilinear interpolation in the element floor(c / grid)
+ *             (clamped to the grid) of block centre c;
+ *   S         s_k = ncc_k for a valid match with ncc_k > 0 whose element is
+ *             in the model, else 0;
+ *   steps     U_0 = 0; n_rej approximation steps, each a solve followed by
+ *             the rejection (s_k = 0) of floor(0.5 + reject_frac * n) of
+ *             the n blocks with s_k > 0: those with the largest squared
+ *             residual |D_k - H_k U|^2, ties to the lower block index,
+ *             never one at or below 1e-6 voxel^2; then n_int interpolation
+ *             steps (solves without rejection); with no block left with
+ *             s_k > 0 a step keeps U_i.
+ * Each solve is Jacobi-preconditioned conjugate gradients in FP64, warm-
+ * started from U_i, run until |r| <= cg_tol |r_0| (r_0 = H^T S D + F_i -
+ * [K + H^T S H] U_i, the warm start's residual), as one cooperative launch.  The sums of H^T S H and H^T S D are accumulated in
+ * 64-bit fixed point (terms rounded to 2^-44 and 2^-40), so results do not
+ * depend on the order of the device's atomics.
+ *
+ * nrr_fem_update arguments:
+ *   d_mask [nz][ny][nx] u8, dims: the brain mask and the volume size;
+ *   d_centers int32 [n][3] (x, y, z), d_disp int32 [n][3], d_ncc f64 [n],
+ *     d_valid u8 [n]: the block matches (the outputs of nrr_block_match);
+ *     n = n_blocks, 0 .. 2^19;
+ *   params: grid >= 2, young > 0, 0 <= poisson < 0.5, n_rej >= 0,
+ *     n_int >= 0, 0 <= reject_frac <= 1, cg_tol > 0, cg_max_iter >= 1;
+ *   d_U f64 [Nz][Ny][Nx][3] (vertex (i, j, k) at x = i grid, ...): out;
+ *   d_s f64 [n]: the confidence after the rejections (out);
+ *   d_rejected_step int32 [n]: the approximation step that rejected each
+ *     block, -1 if none (out);
+ *   h_cg_iters: NULL, or a host array of n_rej + n_int ints receiving each
+ *     solve's iteration count;
+ *   stream: a cudaStream_t (NULL = legacy default stream).
+ * Device buffers are the caller's; scratch (about 0.6 KB per vertex plus
+ * 8 B per block) is allocated and freed on the stream.  The call waits for
+ * the stream once at the end to read the solves' records.
+ * Errors: NRR_E_INVALID for an argument out of range or a NULL pointer
+ * (n_blocks > 0); NRR_E_INTERNAL if a solve stops short of cg_tol within
+ * cg_max_iter iterations or meets a direction of non-positive curvature (a
+ * model part no block pins); NRR_E_TIMEOUT if a grid barrier of the solve
+ * gave up; NRR_E_CUDA / NRR_E_NOMEM from the runtime.
+ *
+ * nrr_fem_grid writes the vertex counts (Nx, Ny, Nz) of a volume and grid
+ * spacing; no device work. */
+typedef struct {
+    int32_t grid;
+    double young;
+    double poisson;
+    int32_t n_rej;
+    int32_t n_int;
+    double reject_frac;
+    double cg_tol;
+    int32_t cg_max_iter;
+} nrr_fem_params;
+
+nrr_status nrr_fem_grid(nrr_dims dims, int32_t grid, int32_t n_vertices[3]);
+nrr_status nrr_fem_update(const uint8_t *d_mask, nrr_dims dims, const int32_t *d_centers, const int32_t *d_disp,
+                          const double *d_ncc, const uint8_t *d_valid, int32_t n_blocks, const nrr_fem_params *params,
+                          double *d_U, double *d_s, int32_t *d_rejected_step, int32_t *h_cg_iters, void *stream);
+
 /* Waits for `stream`, then reports and clears the device error word that
  * the kernels set when a bounded wait gives up (NRR_E_TIMEOUT) or an
  * internal check fails (NRR_E_INTERNAL).  NRR_OK if neither happened. */

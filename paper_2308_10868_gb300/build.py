@@ -26,7 +26,7 @@ LIB = os.path.join(OUT_DIR, "libnrr.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 
-PLAIN_UNITS = ["nrr_api.cu", "nrr_select.cu", "nrr_spacing.cu", "nrr_boxsum.cu", "nrr_boxsum3.cu", "nrr_match_dispatch.cu", "nrr_tune.cu", "nrr_batch.cu", "nrr_serve.cu"]
+PLAIN_UNITS = ["nrr_api.cu", "nrr_select.cu", "nrr_spacing.cu", "nrr_boxsum.cu", "nrr_boxsum3.cu", "nrr_match_dispatch.cu", "nrr_tune.cu", "nrr_batch.cu", "nrr_serve.cu", "nrr_fem.cu"]
 # (float32?, block edge, search lines per thread): uint16 cubic blocks come
 # with one or two lines per thread, float32 with one
 MATCH_VARIANTS = [(0, b, l) for b in (3, 5, 7, 9, 11) for l in (1, 2)] + [(1, b, 1) for b in (3, 5, 7, 9, 11)]

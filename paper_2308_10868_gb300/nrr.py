@@ -48,6 +48,11 @@ class Pair(C.Structure):
 NRR_BATCH_GRAPH, NRR_BATCH_AUTOTUNE, NRR_BATCH_NO_DEDUP, NRR_BATCH_PLAIN_LAUNCH = 1, 2, 4, 8
 
 
+class FemParams(C.Structure):
+    _fields_ = [("grid", C.c_int32), ("young", C.c_double), ("poisson", C.c_double), ("n_rej", C.c_int32),
+                ("n_int", C.c_int32), ("reject_frac", C.c_double), ("cg_tol", C.c_double), ("cg_max_iter", C.c_int32)]
+
+
 class Request(C.Structure):
     _fields_ = [("d_preop", C.c_void_p), ("d_intraop", C.c_void_p), ("d_select", C.c_void_p),
                 ("d_mask", C.c_void_p), ("dims", Dims), ("dtype", C.c_int), ("block", C.c_int32),
@@ -76,6 +81,8 @@ SIGNATURES = {
     "nrr_block_match_aniso": (C.c_int, [_P, _P, C.c_int, Dims, _P, _I32, _P, _P, _P, _P, _P, _P, _P]),
     "nrr_block_match_bs_aniso": (C.c_int, [_P, _P, _P, C.c_int, Dims, _P, _I32, _P, _P, _P, _P, _P, _P, _P]),
     "nrr_device_status": (C.c_int, [_P]),
+    "nrr_fem_grid": (C.c_int, [Dims, _I32, _P]),
+    "nrr_fem_update": (C.c_int, [_P, Dims, _P, _P, _P, _P, _I32, _P, _P, _P, _P, _P, _P]),
     "nrr_test_set_wait": (C.c_int, [C.c_uint64, _I32]),
     "nrr_autotune_match": (C.c_int, [_P, _P, _P, C.c_int, Dims, _P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P]),
     "nrr_tuning_get": (C.c_int, [C.c_int, _I32, _P, _P]),
@@ -477,6 +484,45 @@ class Server:
     def stop(self):
         lib().nrr_server_stop()
         self._live.clear()
+
+
+def fem_grid(dims, grid: int):
+    """Vertex counts (Nx, Ny, Nz) of the finite-element grid of a volume of
+    dims (nx, ny, nz) with vertices every ``grid`` voxels."""
+    out = (C.c_int32 * 3)()
+    _check(lib().nrr_fem_grid(Dims(*dims), int(grid), out), "nrr_fem_grid")
+    return tuple(int(v) for v in out)
+
+
+def fem_update(mask: torch.Tensor, centers: torch.Tensor, disp: torch.Tensor, ncc: torch.Tensor,
+               valid: torch.Tensor, grid: int = 4, young: float = 1.0, poisson: float = 0.45, n_rej: int = 2,
+               n_int: int = 1, reject_frac: float = 0.05, cg_tol: float = 1e-10, cg_max_iter: int = 20000,
+               stream=None):
+    """The robust finite-element update on the block matches
+    (nrr_fem_update).  ``mask`` uint8 (nz, ny, nx); ``centers`` int32 (n, 3),
+    ``disp`` int32 (n, 3), ``ncc`` float64 (n,), ``valid`` uint8 (n,), all on
+    the device.  Returns (U float64 (Nz, Ny, Nx, 3), s float64 (n,),
+    rejected_step int32 (n,), the solves' iteration counts)."""
+    _cuda_contig(mask, "mask")
+    if mask.dtype != torch.uint8 or mask.dim() != 3:
+        raise ValueError("mask must be uint8 (nz, ny, nx)")
+    n = centers.shape[0]
+    for t, nm, dt in ((centers, "centers", torch.int32), (disp, "disp", torch.int32), (ncc, "ncc", torch.float64),
+                      (valid, "valid", torch.uint8)):
+        _cuda_contig(t, nm)
+        if t.dtype != dt or t.shape[0] != n:
+            raise ValueError(f"{nm} must be {dt} with {n} rows")
+    nz, ny, nx = mask.shape
+    Nx, Ny, Nz = fem_grid((nx, ny, nz), grid)
+    dev = mask.device
+    U = torch.empty((Nz, Ny, Nx, 3), dtype=torch.float64, device=dev)
+    s = torch.empty(n, dtype=torch.float64, device=dev)
+    step = torch.empty(n, dtype=torch.int32, device=dev)
+    iters = (C.c_int32 * max(1, n_rej + n_int))()
+    P = FemParams(grid, young, poisson, n_rej, n_int, reject_frac, cg_tol, cg_max_iter)
+    _check(lib().nrr_fem_update(_ptr(mask), Dims(nx, ny, nz), _ptr(centers), _ptr(disp), _ptr(ncc), _ptr(valid), n,
+                                C.byref(P), _ptr(U), _ptr(s), _ptr(step), iters, _stream(stream)), "nrr_fem_update")
+    return U, s, step, [int(v) for v in iters][: n_rej + n_int]
 
 
 def device_status(stream=None) -> int:

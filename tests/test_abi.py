@@ -182,3 +182,32 @@ def test_tuning_table_save_and_load(L, tmp_path):
     assert L.nrr_tuning_get_shape(0, 9, r, C.byref(got)) == 0
     assert (got.ctas_per_sm, got.windows, got.stage, got.lines) == (3, 1, 2, 0)
     assert L.nrr_tuning_set_shape(0, 9, r, C.byref(nrr.MatchShape(0, 0, 0))) == 0
+
+
+def test_fem_entries_need_no_device(L):
+    # vertex counts of the finite-element grid, and the update's argument
+    # checks, which return before any device work
+    from paper_2308_10868_gb300 import nrr
+
+    out = (C.c_int32 * 3)()
+    assert L.nrr_fem_grid(nrr.Dims(256, 256, 124), 4, out) == 0 and tuple(out) == (65, 65, 32)
+    assert L.nrr_fem_grid(nrr.Dims(30, 26, 19), 4, out) == 0 and tuple(out) == (9, 8, 6)
+    assert L.nrr_fem_grid(nrr.Dims(30, 26, 19), 1, out) == -1
+    assert L.nrr_fem_grid(nrr.Dims(1, 26, 19), 4, out) == -1
+    assert L.nrr_fem_grid(nrr.Dims(30, 26, 19), 4, None) == -1
+    good = dict(grid=4, young=1.0, poisson=0.45, n_rej=1, n_int=1, reject_frac=0.05, cg_tol=1e-10, cg_max_iter=100)
+    fake = C.c_void_p(0x1000)  # never dereferenced: every call below fails its checks first
+    d = nrr.Dims(32, 32, 32)
+    for bad in (dict(grid=1), dict(young=0.0), dict(young=float("nan")), dict(poisson=0.5), dict(poisson=-0.1),
+                dict(n_rej=-1), dict(n_int=1001), dict(reject_frac=-0.01), dict(reject_frac=1.01),
+                dict(cg_tol=0.0), dict(cg_max_iter=0)):
+        P = nrr.FemParams(**{**good, **bad})
+        assert L.nrr_fem_update(fake, d, fake, fake, fake, fake, 10, C.byref(P), fake, fake, fake, None, None) == -1, bad
+    P = nrr.FemParams(**good)
+    assert L.nrr_fem_update(fake, d, fake, fake, fake, fake, 10, None, fake, fake, fake, None, None) == -1
+    assert L.nrr_fem_update(fake, d, fake, fake, fake, fake, -1, C.byref(P), fake, fake, fake, None, None) == -1
+    assert L.nrr_fem_update(fake, d, fake, fake, fake, fake, (1 << 19) + 1, C.byref(P), fake, fake, fake, None, None) == -1
+    assert L.nrr_fem_update(fake, d, None, fake, fake, fake, 10, C.byref(P), fake, fake, fake, None, None) == -1
+    assert L.nrr_fem_update(None, d, fake, fake, fake, fake, 10, C.byref(P), fake, fake, fake, None, None) == -1
+    assert L.nrr_fem_update(fake, nrr.Dims(32, 1, 32), fake, fake, fake, fake, 10, C.byref(P), fake, fake, fake, None,
+                            None) == -1

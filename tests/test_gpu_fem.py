@@ -1,0 +1,155 @@
+"""GPU parity of the robust finite-element update (nrr_fem_update, through
+the C ABI) against the FP64 oracle (oracle/fem.py): vertex displacements
+within the solver tolerance, the confidence after the rejections exactly,
+and the step in which each block was rejected exactly (checked to be an
+ordering decision the oracle's residuals make clearly, not a near tie)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import fem
+from paper_2308_10868_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12     # relative residual of each solve in the tests
+U_ATOL = 1e-6   # voxels: the solves' error at that residual on these meshes stays far below
+
+
+@pytest.fixture(scope="module")
+def nrr():
+    from paper_2308_10868_gb300 import nrr as m
+    m.lib()
+    return m
+
+
+def _mask(nx, ny, nz, frac=0.45):
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    r = ((x - (nx - 1) / 2) / (frac * nx)) ** 2 + ((y - (ny - 1) / 2) / (frac * ny)) ** 2 + \
+        ((z - (nz - 1) / 2) / (frac * nz)) ** 2
+    return (r <= 1.0).astype(np.uint8)
+
+
+def _blocks(mask, g, n, rng):
+    nz, ny, nx = mask.shape
+    N = fem.grid_nodes((nx, ny, nz), g)
+    act = fem.active_elements(mask, g)
+    pts = np.argwhere(mask != 0)[:, ::-1]
+    ok = [p for p in pts if act[fem.block_cell(p, g, *N)[0][::-1]]]
+    pick = rng.choice(len(ok), size=n, replace=False)
+    return np.ascontiguousarray(np.array(ok)[pick]).astype(np.int32)
+
+
+def _run_both(nrr, mask, c, disp, ncc, valid, g=4, E=2.0, nu=0.3, n_rej=2, n_int=1, fr=0.05):
+    dev = torch.device("cuda:0")
+    t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(dev)
+    U, s, step, iters = nrr.fem_update(t(mask, np.uint8), t(c, np.int32).reshape(-1, 3), t(disp, np.int32).reshape(-1, 3),
+                                       t(ncc, np.float64), t(valid, np.uint8), grid=g, young=E, poisson=nu,
+                                       n_rej=n_rej, n_int=n_int, reject_frac=fr, cg_tol=TOL)
+    nrr.device_status()
+    Uo, so, rejo, wheno = fem.update(mask, c, disp, ncc, valid, g, E, nu, n_rej, n_int, fr)
+    return (U.cpu().numpy().reshape(-1, 3), s.cpu().numpy(), step.cpu().numpy(), iters), (Uo, so, wheno)
+
+
+def _check(gpu, ora, n_steps):
+    U, s, step, iters = gpu
+    Uo, so, wheno = ora
+    assert len(iters) == n_steps and all(i >= 0 for i in iters), iters
+    err = np.abs(U - Uo).max() if U.size else 0.0
+    print(f"max |U_gpu - U_oracle| = {err:.3e} voxels, CG iterations {iters}")
+    assert err <= U_ATOL
+    assert np.array_equal(step, wheno)
+    assert np.array_equal(s, so)
+
+
+def test_planted_outliers_match_oracle(nrr):
+    rng = np.random.default_rng(21)
+    mask = _mask(40, 36, 24)
+    c = _blocks(mask, 4, 400, rng)
+    disp = np.tile([2, -1, 1], (len(c), 1)).astype(np.int32)
+    disp += rng.integers(-1, 2, size=disp.shape).astype(np.int32)  # matching noise
+    bad = rng.choice(len(c), size=20, replace=False)
+    disp[bad] += rng.choice([-1, 1], size=(20, 3)) * 8
+    ncc = rng.uniform(0.4, 1.0, len(c))
+    valid = (rng.random(len(c)) > 0.05).astype(np.uint8)
+    gpu, ora = _run_both(nrr, mask, c, disp, ncc, valid, n_rej=3, n_int=2, fr=0.04)
+    _check(gpu, ora, 5)
+    assert (gpu[2] >= 0).sum() > 0
+
+
+def test_translation_recovered_nothing_rejected(nrr):
+    rng = np.random.default_rng(22)
+    mask = _mask(32, 32, 20)
+    c = _blocks(mask, 4, 150, rng)
+    disp = np.tile([3, 1, -2], (len(c), 1)).astype(np.int32)
+    ncc = rng.uniform(0.2, 1.0, len(c))
+    valid = np.ones(len(c), dtype=np.uint8)
+    gpu, ora = _run_both(nrr, mask, c, disp, ncc, valid, n_rej=2, n_int=1, fr=0.2)
+    _check(gpu, ora, 3)
+    m = fem.Model(mask, c, 4, 2.0, 0.3)
+    assert np.abs(gpu[0][m.node_on] - [3, 1, -2]).max() < 1e-9
+    assert (gpu[2] == -1).all()
+
+
+@pytest.mark.parametrize("g", [2, 3, 5])
+def test_ragged_grids_and_parameters(nrr, g):
+    # volume sizes no grid spacing divides (the last elements reach past the
+    # volume), other materials, no rejection step, and every fraction
+    rng = np.random.default_rng(23 + g)
+    mask = _mask(29, 23, 17, 0.48)
+    c = _blocks(mask, g, 120, rng)
+    disp = rng.integers(-4, 5, size=(len(c), 3)).astype(np.int32)
+    ncc = rng.uniform(-0.2, 1.0, len(c))
+    valid = (rng.random(len(c)) > 0.1).astype(np.uint8)
+    for E, nu, n_rej, n_int, fr in ((1.0, 0.45, 1, 1, 0.1), (5.0, 0.0, 0, 2, 0.5), (0.5, 0.3, 2, 0, 1.0)):
+        gpu, ora = _run_both(nrr, mask, c, disp, ncc, valid, g=g, E=E, nu=nu, n_rej=n_rej, n_int=n_int, fr=fr)
+        _check(gpu, ora, n_rej + n_int)
+
+
+def test_degenerate_inputs(nrr):
+    dev = torch.device("cuda:0")
+    mask = torch.from_numpy(_mask(24, 20, 16)).to(dev)
+    e3 = torch.empty((0, 3), dtype=torch.int32, device=dev)
+    U, s, step, iters = nrr.fem_update(mask, e3, e3, torch.empty(0, dtype=torch.float64, device=dev),
+                                       torch.empty(0, dtype=torch.uint8, device=dev), n_rej=1, n_int=1)
+    assert U.abs().max().item() == 0.0 and iters == [0, 0]  # no blocks: U stays 0
+    # every match invalid: nothing pins the mesh, U stays 0
+    rng = np.random.default_rng(24)
+    c = _blocks(_mask(24, 20, 16), 4, 30, rng)
+    ct = torch.from_numpy(c).to(dev)
+    U, s, step, iters = nrr.fem_update(mask, ct, ct.clone(), torch.ones(30, dtype=torch.float64, device=dev),
+                                       torch.zeros(30, dtype=torch.uint8, device=dev), n_rej=1, n_int=0)
+    assert U.abs().max().item() == 0.0 and (s == 0).all() and (step == -1).all()
+    # an empty mask: no element, no unknown
+    z = torch.zeros_like(mask)
+    U, s, step, iters = nrr.fem_update(z, ct, ct.clone(), torch.ones(30, dtype=torch.float64, device=dev),
+                                       torch.ones(30, dtype=torch.uint8, device=dev), n_rej=1, n_int=1)
+    assert U.abs().max().item() == 0.0 and (s == 0).all()
+    nrr.device_status()
+
+
+def test_argument_checks(nrr):
+    dev = torch.device("cuda:0")
+    mask = torch.from_numpy(_mask(16, 16, 16)).to(dev)
+    e3 = torch.empty((0, 3), dtype=torch.int32, device=dev)
+    ef = torch.empty(0, dtype=torch.float64, device=dev)
+    eu = torch.empty(0, dtype=torch.uint8, device=dev)
+    for kw in (dict(grid=1), dict(young=0.0), dict(poisson=0.5), dict(n_rej=-1), dict(reject_frac=1.5),
+               dict(cg_tol=0.0), dict(cg_max_iter=0)):
+        with pytest.raises(nrr.NrrError) as e:
+            nrr.fem_update(mask, e3, e3, ef, eu, **kw)
+        assert e.value.status == -1
+
+
+def test_matching_output_small_workload(nrr):
+    # the path as used: selection and block matching on the small phantom,
+    # then the update on their results
+    w = synth.WORKLOADS["small"]
+    pre, intra, mask = synth.workload_pair("small")
+    dev = torch.device("cuda:0")
+    dp, di, dm = nrr.to_device_u16(pre, dev), nrr.to_device_u16(intra, dev), torch.from_numpy(mask).to(dev)
+    c = nrr.select_blocks(dp, dm, w.block, w.stride, w.frac)
+    disp, ncc, valid = nrr.block_match(dp, di, c, w.block, w.radius)
+    gpu, ora = _run_both(nrr, mask, c.cpu().numpy(), disp.cpu().numpy(), ncc.cpu().numpy(), valid.cpu().numpy(),
+                         g=4, E=1.0, nu=0.45, n_rej=2, n_int=1, fr=0.05)
+    _check(gpu, ora, 3)
