@@ -45,6 +45,7 @@ namespace nrr {
 namespace {
 
 constexpr int FEM_THREADS = 256;
+constexpr int SOLVE_THREADS = 128;  // small CTAs spread a small mesh over every SM
 constexpr int REJ_THREADS = 1024;
 constexpr double FIX_M = 17592186044416.0;  // 2^44: fixed-point scale of the H^T S H terms (each in [0, 1])
 constexpr double FIX_B = 1099511627776.0;   // 2^40: fixed-point scale of the H^T S D terms (|D| < 2^15)
@@ -60,10 +61,13 @@ struct FemGrid {
 };
 
 // The element stiffness, row 3 a + c, column 3 b + d (local nodes a, b;
-// components c, d), kept in kernel-parameter space: every thread of a warp
-// reads the same entry.
+// components c, d), and the stiffness stencil of a vertex whose 8 elements
+// all belong to the model (the 3x3 block coupling it to neighbour o, summed
+// over the elements holding both), kept in kernel-parameter space: every
+// thread of a warp reads the same entry.
 struct FemKe {
     double k[24 * 24];
+    double st[27 * 9];
 };
 
 __host__ __device__ inline long long vidx(const FemGrid &G, int i, int j, int k)
@@ -178,6 +182,49 @@ __global__ void fem_assemble_kernel(FemGrid G, const int32_t *__restrict__ cente
     }
 }
 
+// The model's vertices in increasing order (one CTA: a block-wide scan per
+// round of REJ_THREADS x 8 vertices), so that the solve deals them out
+// evenly and in the same order on every run.
+__global__ void __launch_bounds__(REJ_THREADS) fem_active_list_kernel(const uint8_t *__restrict__ nact, long long nv,
+                                                                      int32_t *__restrict__ alist,
+                                                                      int32_t *__restrict__ acount)
+{
+    constexpr int CH = 8;
+    __shared__ int wsum[REJ_THREADS / 32];
+    __shared__ int s_base;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    if (tid == 0) s_base = 0;
+    __syncthreads();
+    for (long long start = 0; start < nv; start += (long long)blockDim.x * CH) {
+        const long long v0 = start + (long long)tid * CH;
+        int c = 0;
+        for (int q = 0; q < CH; ++q) c += (v0 + q < nv && nact[v0 + q]) ? 1 : 0;
+        int inc = c;  // inclusive scan over the CTA
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += u;
+        }
+        if (lane == 31) wsum[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            int w = lane < nw ? wsum[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += u;
+            }
+            if (lane < nw) wsum[lane] = w;  // inclusive over warps
+        }
+        __syncthreads();
+        int pos = s_base + (warp ? wsum[warp - 1] : 0) + inc - c;
+        for (int q = 0; q < CH; ++q)
+            if (v0 + q < nv && nact[v0 + q]) alist[pos++] = (int32_t)(v0 + q);
+        __syncthreads();
+        if (tid == 0) s_base += wsum[nw - 1];
+        __syncthreads();
+    }
+    if (tid == 0) *acount = s_base;
+}
+
 // ---- the solve ------------------------------------------------------------
 
 struct FemSolveArgs {
@@ -189,6 +236,8 @@ struct FemSolveArgs {
     double *x;     // [nv][3] in: U_i, out: U_{i+1}
     double *r, *p0, *p1, *q;  // [nv][3]
     double *part;             // [4][gridDim.x] per-CTA partial dot products
+    const int32_t *alist;     // the model's vertices in increasing order
+    const int32_t *acount;    // their number
     unsigned int *arrive;     // grid-barrier arrivals (zero at launch)
     int32_t *iters;           // iterations taken (-1: a grid barrier gave up, -2: breakdown)
     double *relres;           // final |r| / |r_0|
@@ -230,6 +279,21 @@ __device__ __forceinline__ void apply_A(const FemGrid &G, const FemKe &Ke, const
                                         int k, Get get, double (&y)[3])
 {
     y[0] = y[1] = y[2] = 0.0;
+    if (em == 0xFFu) {  // interior of the model: the precomputed stencil
+#pragma unroll
+        for (int o = 0; o < 27; ++o) {
+            double v[3];
+            get(vidx(G, i + o % 3 - 1, j + (o / 3) % 3 - 1, k + o / 9 - 1), v);
+            const double mo = mrow[o];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) y[c] = fma(Ke.st[o * 9 + 3 * c + d], v[d], y[c]);
+                y[c] = fma(mo, v[c], y[c]);
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int o = 0; o < 27; ++o) {
         const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
@@ -282,10 +346,10 @@ __device__ double grid_total(const double *part, int slot, double *sh)
     return sh[0];
 }
 
-__global__ void __launch_bounds__(FEM_THREADS) fem_solve_kernel(const __grid_constant__ FemSolveArgs a,
-                                                                const __grid_constant__ FemKe Ke)
+__global__ void __launch_bounds__(SOLVE_THREADS) fem_solve_kernel(const __grid_constant__ FemSolveArgs a,
+                                                                  const __grid_constant__ FemKe Ke)
 {
-    __shared__ double sh[FEM_THREADS / 32];
+    __shared__ double sh[SOLVE_THREADS / 32];
     const FemGrid &G = a.G;
     const long long T = (long long)gridDim.x * blockDim.x, t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     unsigned int bi = 0;  // grid barriers passed
@@ -339,6 +403,9 @@ __global__ void __launch_bounds__(FEM_THREADS) fem_solve_kernel(const __grid_con
         // stop once |r| <= tol |r_0|: the warm start's residual is what the
         // solve has to remove (|b| holds K U_i, which can dwarf it)
         const double rr0 = rr, thr = a.tol * a.tol * rr0;
+        // the model's vertices, dealt round-robin over the CTAs first so that
+        // every CTA gets the same share
+        const long long na = *a.acount, q0 = blockIdx.x + (long long)gridDim.x * threadIdx.x;
         double rz_prev = 1.0;
         int it = 0;
         bool broke = false;
@@ -353,8 +420,8 @@ __global__ void __launch_bounds__(FEM_THREADS) fem_solve_kernel(const __grid_con
                     v[c] = fma(__ldcg(a.dinv + 3 * nb + c), __ldcg(a.r + 3 * nb + c), beta * __ldcg(pold + 3 * nb + c));
             };
             double pq = 0.0;
-            for (long long n = t0; n < G.nv; n += T) {
-                if (!a.nact[n]) continue;
+            for (long long q = q0; q < na; q += T) {
+                const long long n = a.alist[q];
                 const int i = (int)(n % G.Nx), j = (int)((n / G.Nx) % G.Ny), k = (int)(n / ((long long)G.Nx * G.Ny));
                 const unsigned em = elem_mask(G, a.eact, i, j, k);
                 double y[3], pn[3];
@@ -376,8 +443,8 @@ __global__ void __launch_bounds__(FEM_THREADS) fem_solve_kernel(const __grid_con
             }
             const double alpha = rz / pq;
             double rz_l = 0.0, rr_l = 0.0;
-            for (long long n = t0; n < G.nv; n += T) {
-                if (!a.nact[n]) continue;
+            for (long long q = q0; q < na; q += T) {
+                const long long n = a.alist[q];
                 for (int c = 0; c < 3; ++c) {
                     a.x[3 * n + c] = fma(alpha, pcur[3 * n + c], a.x[3 * n + c]);
                     const double rc = fma(-alpha, a.q[3 * n + c], a.r[3 * n + c]);
@@ -585,6 +652,24 @@ void element_stiffness(double g, double E, double nu, double *K)
     }
 }
 
+// The stiffness stencil of a vertex with all 8 elements in the model: the
+// block coupling it (local node a of the element at offset -a) to neighbour
+// o = (dx, dy, dz), summed over the elements holding both.
+void interior_stencil(const double *K, double *st)
+{
+    for (int o = 0; o < 27; ++o) {
+        const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+        for (int e = 0; e < 9; ++e) st[o * 9 + e] = 0.0;
+        for (int a = 0; a < 8; ++a) {
+            const int bx = (a & 1) + dx, by = ((a >> 1) & 1) + dy, bz = ((a >> 2) & 1) + dz;
+            if (bx < 0 || bx > 1 || by < 0 || by > 1 || bz < 0 || bz > 1) continue;
+            const int b = bx + 2 * by + 4 * bz;
+            for (int c = 0; c < 3; ++c)
+                for (int d = 0; d < 3; ++d) st[o * 9 + 3 * c + d] += K[(3 * a + c) * 24 + 3 * b + d];
+        }
+    }
+}
+
 FemGrid make_grid(nrr_dims d, int g)
 {
     FemGrid G;
@@ -658,10 +743,13 @@ extern "C" nrr_status nrr_fem_update(const uint8_t *d_mask, nrr_dims dims, const
 
     auto kern = fem_solve_kernel;
     int occ = 0;
-    NRR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, FEM_THREADS, 0));
+    NRR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, SOLVE_THREADS, 0));
     if (occ < 1) return fail(NRR_E_INTERNAL, "solve kernel does not fit on an SM");
-    long long cg_blocks = ((long long)nv + FEM_THREADS - 1) / FEM_THREADS;
-    if (cg_blocks > (long long)occ * sm_count()) cg_blocks = (long long)occ * sm_count();
+    // at most two CTAs per SM: the solve's time per iteration is its two grid
+    // barriers plus an even share of the model's vertices per CTA
+    long long cg_blocks = ((long long)nv + SOLVE_THREADS - 1) / SOLVE_THREADS;
+    const long long cap_blocks = (long long)(occ < 2 ? occ : 2) * sm_count();
+    if (cg_blocks > cap_blocks) cg_blocks = cap_blocks;
     if (cg_blocks < 1) cg_blocks = 1;
 
     // scratch, one allocation: offsets in bytes, each 256-aligned
@@ -675,7 +763,7 @@ extern "C" nrr_status nrr_fem_update(const uint8_t *d_mask, nrr_dims dims, const
                  o_m = take(nv * 27 * 8), o_dinv = take(nv * 3 * 8), o_r = take(nv * 3 * 8), o_p0 = take(nv * 3 * 8),
                  o_p1 = take(nv * 3 * 8), o_q = take(nv * 3 * 8), o_part = take(4 * (size_t)cg_blocks * 8),
                  o_arr = take(8), o_keys = take(nb * 8), o_cnt = take(16), o_it = take((size_t)(steps + 1) * 4),
-                 o_rel = take((size_t)(steps + 1) * 8);
+                 o_rel = take((size_t)(steps + 1) * 8), o_alist = take(nv * 4), o_acnt = take(4);
     unsigned char *scr = nullptr;
     {
         const cudaError_t e = cudaMallocAsync((void **)&scr, off, st);
@@ -698,7 +786,9 @@ extern "C" nrr_status nrr_fem_update(const uint8_t *d_mask, nrr_dims dims, const
         if (s2 != NRR_OK) return s2;
         fem_elements_kernel<<<grid_for((long long)ne, FEM_THREADS), FEM_THREADS, 0, st>>>(d_mask, G, eact);
         fem_nodes_kernel<<<grid_for((long long)nv, FEM_THREADS), FEM_THREADS, 0, st>>>(G, eact, nact);
-        count_launches(2);
+        fem_active_list_kernel<<<1, REJ_THREADS, 0, st>>>(nact, (long long)nv, (int32_t *)(scr + o_alist),
+                                                          (int32_t *)(scr + o_acnt));
+        count_launches(3);
         if (n_blocks > 0) {
             fem_init_blocks_kernel<<<grid_for(n_blocks, FEM_THREADS), FEM_THREADS, 0, st>>>(G, eact, d_centers, d_ncc,
                                                                                          d_valid, n_blocks, d_s,
@@ -708,6 +798,7 @@ extern "C" nrr_status nrr_fem_update(const uint8_t *d_mask, nrr_dims dims, const
         NRR_CUDA_TRY(cudaGetLastError());
         FemKe Ke;
         element_stiffness((double)P.grid, P.young, P.poisson, Ke.k);
+        interior_stencil(Ke.k, Ke.st);
         FemSolveArgs A;
         A.G = G;
         A.eact = eact;
@@ -722,6 +813,8 @@ extern "C" nrr_status nrr_fem_update(const uint8_t *d_mask, nrr_dims dims, const
         A.p1 = (double *)(scr + o_p1);
         A.q = (double *)(scr + o_q);
         A.part = (double *)(scr + o_part);
+        A.alist = (const int32_t *)(scr + o_alist);
+        A.acount = (const int32_t *)(scr + o_acnt);
         A.arrive = (unsigned int *)(scr + o_arr);
         A.tol = P.cg_tol;
         A.max_iter = P.cg_max_iter;
@@ -740,7 +833,7 @@ extern "C" nrr_status nrr_fem_update(const uint8_t *d_mask, nrr_dims dims, const
             A.iters = iters + it;
             A.relres = relres + it;
             void *args[] = {(void *)&A, (void *)&Ke};
-            NRR_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)cg_blocks), dim3(FEM_THREADS),
+            NRR_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)cg_blocks), dim3(SOLVE_THREADS),
                                                      args, 0, st));
             count_launches(1);
             if (it < P.n_rej && n_blocks > 0) {
