@@ -235,6 +235,7 @@ struct FemSolveArgs {
     double *dinv;  // [nv][3] inverse diagonal of K + H^T S H (0 off the model)
     double *x;     // [nv][3] in: U_i, out: U_{i+1}
     double *r, *p0, *p1, *q;  // [nv][3]
+    double *z;                // [nv][3] D^-1 r, written with r
     double *part;             // [4][gridDim.x] per-CTA partial dot products
     const int32_t *alist;     // the model's vertices in increasing order
     const int32_t *acount;    // their number
@@ -346,7 +347,7 @@ __device__ double grid_total(const double *part, int slot, double *sh)
     return sh[0];
 }
 
-__global__ void __launch_bounds__(SOLVE_THREADS) fem_solve_kernel(const __grid_constant__ FemSolveArgs a,
+__global__ void __launch_bounds__(SOLVE_THREADS, 1) fem_solve_kernel(const __grid_constant__ FemSolveArgs a,
                                                                   const __grid_constant__ FemKe Ke)
 {
     __shared__ double sh[SOLVE_THREADS / 32];
@@ -364,6 +365,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) fem_solve_kernel(const __grid_c
             for (int c = 0; c < 3; ++c) {
                 a.dinv[3 * n + c] = 0.0;
                 a.r[3 * n + c] = 0.0;
+                a.z[3 * n + c] = 0.0;
                 a.x[3 * n + c] = 0.0;
             }
             continue;
@@ -386,6 +388,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) fem_solve_kernel(const __grid_c
             const double rc = bd - Mx[c];
             a.dinv[3 * n + c] = di;
             a.r[3 * n + c] = rc;
+            a.z[3 * n + c] = rc * di;
             rr += rc * rc;
             rz += rc * rc * di;
         }
@@ -413,11 +416,10 @@ __global__ void __launch_bounds__(SOLVE_THREADS) fem_solve_kernel(const __grid_c
             const double beta = it == 0 ? 0.0 : rz / rz_prev;
             const double *pold = (it & 1) ? a.p1 : a.p0;
             double *pcur = (it & 1) ? a.p0 : a.p1;
-            // p = z + beta p_old (z = D^-1 r) is formed where it is read
+            // p = z + beta p_old is formed where it is read
             auto getp = [&](long long nb, double(&v)[3]) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    v[c] = fma(__ldcg(a.dinv + 3 * nb + c), __ldcg(a.r + 3 * nb + c), beta * __ldcg(pold + 3 * nb + c));
+                for (int c = 0; c < 3; ++c) v[c] = fma(beta, __ldcg(pold + 3 * nb + c), __ldcg(a.z + 3 * nb + c));
             };
             double pq = 0.0;
             for (long long q = q0; q < na; q += T) {
@@ -448,9 +450,11 @@ __global__ void __launch_bounds__(SOLVE_THREADS) fem_solve_kernel(const __grid_c
                 for (int c = 0; c < 3; ++c) {
                     a.x[3 * n + c] = fma(alpha, pcur[3 * n + c], a.x[3 * n + c]);
                     const double rc = fma(-alpha, a.q[3 * n + c], a.r[3 * n + c]);
+                    const double zc = rc * a.dinv[3 * n + c];
                     a.r[3 * n + c] = rc;
+                    a.z[3 * n + c] = zc;
                     rr_l += rc * rc;
-                    rz_l += rc * rc * a.dinv[3 * n + c];
+                    rz_l += rc * zc;
                 }
             }
             rz_l = cta_sum(rz_l, sh);
@@ -763,7 +767,8 @@ extern "C" nrr_status nrr_fem_update(const uint8_t *d_mask, nrr_dims dims, const
                  o_m = take(nv * 27 * 8), o_dinv = take(nv * 3 * 8), o_r = take(nv * 3 * 8), o_p0 = take(nv * 3 * 8),
                  o_p1 = take(nv * 3 * 8), o_q = take(nv * 3 * 8), o_part = take(4 * (size_t)cg_blocks * 8),
                  o_arr = take(8), o_keys = take(nb * 8), o_cnt = take(16), o_it = take((size_t)(steps + 1) * 4),
-                 o_rel = take((size_t)(steps + 1) * 8), o_alist = take(nv * 4), o_acnt = take(4);
+                 o_rel = take((size_t)(steps + 1) * 8), o_alist = take(nv * 4), o_acnt = take(4),
+                 o_z = take(nv * 3 * 8);
     unsigned char *scr = nullptr;
     {
         const cudaError_t e = cudaMallocAsync((void **)&scr, off, st);
@@ -812,6 +817,7 @@ extern "C" nrr_status nrr_fem_update(const uint8_t *d_mask, nrr_dims dims, const
         A.p0 = (double *)(scr + o_p0);
         A.p1 = (double *)(scr + o_p1);
         A.q = (double *)(scr + o_q);
+        A.z = (double *)(scr + o_z);
         A.part = (double *)(scr + o_part);
         A.alist = (const int32_t *)(scr + o_alist);
         A.acount = (const int32_t *)(scr + o_acnt);
