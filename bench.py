@@ -58,6 +58,9 @@ def _args():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-small", action="store_true")
     p.add_argument("--no-fem", action="store_true")
+    p.add_argument("--fem-only", action="store_true",
+                   help="select and match the workload once, then run only the FEM leg (for profiling)")
+    p.add_argument("--fem-grids", default="8,4", help="vertex spacings of the FEM leg")
     p.add_argument("--serve-open-requests", type=int, default=1000)  # 50 s at 20 req/s
     p.add_argument("--serve-sweep-requests", type=int, default=300)
     p.add_argument("--serve-closed-requests", type=int, default=1000)
@@ -730,7 +733,7 @@ def _fem(a, nrr, d_mask, centers, n_sel, out, w, flush):
     kw = dict(young=1.0, poisson=0.45, n_rej=2, n_int=1, reject_frac=0.05, cg_tol=1e-10)
     res = {"workload": w.name + " block matches", "n_blocks": n, "params": kw,
            "timing": "CUDA events around one nrr_fem_update call (which waits once for its stream), best of 3"}
-    for g in (8, 4):
+    for g in (int(v) for v in a.fem_grids.split(",")):
         ts, iters = [], None
         for _ in range(4):
             flush.fill_(5)
@@ -867,6 +870,12 @@ def run_ours(a):
         nrr.block_match(p, i, centers, w.block, w.radius, n_blocks=n_sel, box=box, out=out)
         ev_phase[2].record(stream)
 
+    if a.fem_only:
+        step(d_pre, d_intra, d_mask)
+        nrr.device_status()
+        if rank == 0:
+            print(json.dumps({"fem": _fem(a, nrr, d_mask, centers, n_sel, out, w, flush)}), flush=True)
+        return 0
     for _ in range(max(3, a.warmup)):
         flush.fill_(1)
         step(d_pre, d_intra, d_mask)

@@ -279,7 +279,10 @@ template <class Get>
 __device__ __forceinline__ void apply_A(const FemGrid &G, const FemKe &Ke, const double *mrow, unsigned em, int i, int j,
                                         int k, Get get, double (&y)[3])
 {
-    y[0] = y[1] = y[2] = 0.0;
+    // one partial sum per neighbour plane dz and component: three short
+    // chains of dependent FP64 FMAs instead of one long one, added in a
+    // fixed order at the end
+    double yp[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
     if (em == 0xFFu) {  // interior of the model: the precomputed stencil
 #pragma unroll
         for (int o = 0; o < 27; ++o) {
@@ -289,33 +292,36 @@ __device__ __forceinline__ void apply_A(const FemGrid &G, const FemKe &Ke, const
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
 #pragma unroll
-                for (int d = 0; d < 3; ++d) y[c] = fma(Ke.st[o * 9 + 3 * c + d], v[d], y[c]);
-                y[c] = fma(mo, v[c], y[c]);
+                for (int d = 0; d < 3; ++d) yp[o / 9][c] = fma(Ke.st[o * 9 + 3 * c + d], v[d], yp[o / 9][c]);
+                yp[o / 9][c] = fma(mo, v[c], yp[o / 9][c]);
             }
         }
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int o = 0; o < 27; ++o) {
-        const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
-        const unsigned cm = couple_mask(dx, dy, dz);
-        if (!(em & cm)) continue;
-        double v[3];
-        get(vidx(G, i + dx, j + dy, k + dz), v);
+        for (int o = 0; o < 27; ++o) {
+            const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+            const unsigned cm = couple_mask(dx, dy, dz);
+            if (!(em & cm)) continue;
+            double v[3];
+            get(vidx(G, i + dx, j + dy, k + dz), v);
 #pragma unroll
-        for (int a = 0; a < 8; ++a) {
-            if (!((cm >> a) & 1u)) continue;
-            if (!((em >> a) & 1u)) continue;
-            const int b = ((a & 1) + dx) + 2 * (((a >> 1) & 1) + dy) + 4 * (((a >> 2) & 1) + dz);
+            for (int a = 0; a < 8; ++a) {
+                if (!((cm >> a) & 1u)) continue;
+                if (!((em >> a) & 1u)) continue;
+                const int b = ((a & 1) + dx) + 2 * (((a >> 1) & 1) + dy) + 4 * (((a >> 2) & 1) + dz);
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
+                for (int c = 0; c < 3; ++c)
 #pragma unroll
-                for (int d = 0; d < 3; ++d) y[c] = fma(Ke.k[(3 * a + c) * 24 + 3 * b + d], v[d], y[c]);
+                    for (int d = 0; d < 3; ++d)
+                        yp[o / 9][c] = fma(Ke.k[(3 * a + c) * 24 + 3 * b + d], v[d], yp[o / 9][c]);
+            }
+            const double mo = mrow[o];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) yp[o / 9][c] = fma(mo, v[c], yp[o / 9][c]);
         }
-        const double mo = mrow[o];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) y[c] = fma(mo, v[c], y[c]);
     }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y[c] = (yp[0][c] + yp[1][c]) + yp[2][c];
 }
 
 // Sum of v over the CTA, in a fixed order; every thread gets the result.

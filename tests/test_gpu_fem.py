@@ -153,3 +153,50 @@ def test_matching_output_small_workload(nrr):
     gpu, ora = _run_both(nrr, mask, c.cpu().numpy(), disp.cpu().numpy(), ncc.cpu().numpy(), valid.cpu().numpy(),
                          g=4, E=1.0, nu=0.45, n_rej=2, n_int=1, fr=0.05)
     _check(gpu, ora, 3)
+
+
+def test_full_size_clinical_properties(nrr):
+    # the bench's configuration (clinical matches, vertex spacing 4, 135,200
+    # vertices): too large for the oracle's direct solves, so the GPU's U
+    # is checked against the oracle's own assembled system, and its
+    # rejection against the oracle's rule applied to the residuals of that U
+    import scipy.sparse as sp
+
+    w = synth.WORKLOADS["clinical"]
+    pre, intra, mask = synth.workload_pair("clinical")
+    dev = torch.device("cuda:0")
+    dp, di, dm = nrr.to_device_u16(pre, dev), nrr.to_device_u16(intra, dev), torch.from_numpy(mask).to(dev)
+    c = nrr.select_blocks(dp, dm, w.block, w.stride, w.frac)
+    disp, ncc, valid = nrr.block_match(dp, di, c, w.block, w.radius)
+    g, E, nu, fr = 4, 1.0, 0.45, 0.05
+    cn, dn, nn, vn = (t.cpu().numpy() for t in (c, disp, ncc, valid))
+    m = fem.Model(mask, cn, g, E, nu)
+    s0 = fem.confidence(nn, vn, m.inside)
+    # one solve from U_0 = 0: [K + H^T S H] U = H^T S D on the model's unknowns
+    U, s, step, iters = nrr.fem_update(dm, c, disp, ncc, valid, grid=g, young=E, poisson=nu, n_rej=0, n_int=1,
+                                       cg_tol=1e-10)
+    nrr.device_status()
+    Un = U.cpu().numpy().reshape(-1)
+    S3 = sp.diags(np.repeat(s0, 3))
+    A = (m.K + m.H.T @ S3 @ m.H).tocsr()
+    b = m.H.T @ (S3 @ dn.reshape(-1).astype(np.float64))
+    on = m.dof_on
+    res = np.linalg.norm((A @ Un - b)[on]) / np.linalg.norm(b[on])
+    print(f"full size: relative residual of the GPU solution in the oracle's system {res:.2e}, {iters} iterations")
+    assert res <= 1e-9
+    assert np.all(Un[~on] == 0)
+    assert np.array_equal(s.cpu().numpy(), s0)
+    # one approximation step: the rejected blocks are the oracle's rule on
+    # the residuals of the GPU's U (same U, so the same order)
+    U1, s1, step1, _ = nrr.fem_update(dm, c, disp, ncc, valid, grid=g, young=E, poisson=nu, n_rej=1, n_int=0,
+                                      reject_frac=fr, cg_tol=1e-10)
+    nrr.device_status()
+    r2 = fem.residuals(m.H, U1.cpu().numpy().reshape(-1), dn)
+    want = fem.reject(s0, r2, fr)
+    got = np.nonzero(step1.cpu().numpy() == 0)[0]
+    assert len(got) == fem.n_reject(int((s0 > 0).sum()), fr)
+    diff = set(got.tolist()) ^ set(want.tolist())
+    if diff:  # only where two residuals agree to rounding at the threshold
+        thr = np.sort(r2[want])[0]
+        assert all(abs(r2[b] - thr) <= 1e-12 * thr for b in diff), sorted(diff)
+    assert np.array_equal(s1.cpu().numpy(), np.where(step1.cpu().numpy() == 0, 0.0, s0))
