@@ -538,11 +538,12 @@ nrr_status nrr_release(uint64_t ticket);
  *             never one at or below 1e-6 voxel^2; then n_int interpolation
  *             steps (solves without rejection); with no block left with
  *             s_k > 0 a step keeps U_i.
- * Each solve is Jacobi-preconditioned conjugate gradients in FP64, warm-
- * started from U_i, run until |r| <= cg_tol |r_0| (r_0 = H^T S D + F_i -
- * [K + H^T S H] U_i, the warm start's residual), as one cooperative launch.  The sums of H^T S H and H^T S D are accumulated in
- * 64-bit fixed point (terms rounded to 2^-44 and 2^-40), so results do not
- * depend on the order of the device's atomics.
+ * Each solve is conjugate gradients in FP64 preconditioned by the inverse of
+ * each vertex's 3x3 diagonal block, warm-started from U_i, run until
+ * |r| <= cg_tol |r_0| (r_0 = H^T S D + F_i - [K + H^T S H] U_i, the warm
+ * start's residual), as one cooperative launch.  The sums of H^T S H and
+ * H^T S D are accumulated in 64-bit fixed point (terms rounded to 2^-44 and
+ * 2^-40), so results do not depend on the order of the device's atomics.
  *
  * nrr_fem_update arguments:
  *   d_mask [nz][ny][nx] u8, dims: the brain mask and the volume size;

@@ -21,7 +21,8 @@
 //                              vertex and H^T S D, accumulated as 64-bit
 //                              fixed-point integers so that the sums do not
 //                              depend on the order of the atomics;
-//   fem_solve                  Jacobi-preconditioned conjugate gradients in
+//   fem_solve                  conjugate gradients preconditioned by the
+//                              inverse 3x3 diagonal block of each vertex, in
 //                              FP64 on K + H^T S H, matrix-free (K element by
 //                              element around each vertex, the stencil for
 //                              H^T S H), warm-started from U_i until the
@@ -232,7 +233,7 @@ struct FemSolveArgs {
     const uint8_t *eact, *nact;
     const unsigned long long *mfix, *bfix;
     double *m;     // [nv][27] H^T S H stencil
-    double *dinv;  // [nv][3] inverse diagonal of K + H^T S H (0 off the model)
+    double *binv;  // [nv][9] inverse of each vertex's 3x3 diagonal block of K + H^T S H (0 off the model)
     double *x;     // [nv][3] in: U_i, out: U_{i+1}
     double *r, *p0, *p1, *q;  // [nv][3]
     double *z;                // [nv][3] D^-1 r, written with r
@@ -324,6 +325,25 @@ __device__ __forceinline__ void apply_A(const FemGrid &G, const FemKe &Ke, const
     for (int c = 0; c < 3; ++c) y[c] = (yp[0][c] + yp[1][c]) + yp[2][c];
 }
 
+// Inverse of a symmetric positive definite 3x3 matrix (cofactors over the
+// determinant), row-major.
+__device__ __forceinline__ void inverse3(const double (&B)[3][3], double (&I)[9])
+{
+    const double c00 = B[1][1] * B[2][2] - B[1][2] * B[2][1], c01 = B[1][2] * B[2][0] - B[1][0] * B[2][2],
+                 c02 = B[1][0] * B[2][1] - B[1][1] * B[2][0];
+    const double det = B[0][0] * c00 + B[0][1] * c01 + B[0][2] * c02;
+    const double id = det > 0.0 ? 1.0 / det : 0.0;
+    I[0] = c00 * id;
+    I[1] = (B[0][2] * B[2][1] - B[0][1] * B[2][2]) * id;
+    I[2] = (B[0][1] * B[1][2] - B[0][2] * B[1][1]) * id;
+    I[3] = c01 * id;
+    I[4] = (B[0][0] * B[2][2] - B[0][2] * B[2][0]) * id;
+    I[5] = (B[0][2] * B[1][0] - B[0][0] * B[1][2]) * id;
+    I[6] = c02 * id;
+    I[7] = (B[0][1] * B[2][0] - B[0][0] * B[2][1]) * id;
+    I[8] = (B[0][0] * B[1][1] - B[0][1] * B[1][0]) * id;
+}
+
 // Sum of v over the CTA, in a fixed order; every thread gets the result.
 __device__ double cta_sum(double v, double *sh)
 {
@@ -368,8 +388,8 @@ __global__ void __launch_bounds__(SOLVE_THREADS, 1) fem_solve_kernel(const __gri
         for (int o = 0; o < 27; ++o) mrow[o] = (double)(long long)a.mfix[27 * n + o] / FIX_M;
         a.p0[3 * n] = a.p0[3 * n + 1] = a.p0[3 * n + 2] = 0.0;
         if (!a.nact[n]) {
+            for (int e = 0; e < 9; ++e) a.binv[9 * n + e] = 0.0;
             for (int c = 0; c < 3; ++c) {
-                a.dinv[3 * n + c] = 0.0;
                 a.r[3 * n + c] = 0.0;
                 a.z[3 * n + c] = 0.0;
                 a.x[3 * n + c] = 0.0;
@@ -384,20 +404,31 @@ __global__ void __launch_bounds__(SOLVE_THREADS, 1) fem_solve_kernel(const __gri
             const long long nb = vidx(G, i + o % 3 - 1, j + (o / 3) % 3 - 1, k + o / 9 - 1);
             for (int c = 0; c < 3; ++c) Mx[c] = fma(mrow[o], a.x[3 * nb + c], Mx[c]);
         }
+        // the vertex's 3x3 diagonal block of K + H^T S H and its inverse
+        // (the block preconditioner: it couples the three components,
+        // which a nearly incompressible material ties closely)
+        double Bd[3][3], Bi[9];
+        for (int c = 0; c < 3; ++c)
+            for (int d = 0; d < 3; ++d) {
+                double v = c == d ? mrow[13] : 0.0;
+                for (int q = 0; q < 8; ++q)
+                    if ((em >> q) & 1u) v += Ke.k[(3 * q + c) * 24 + 3 * q + d];
+                Bd[c][d] = v;
+            }
+        inverse3(Bd, Bi);
+        double rc[3];
         for (int c = 0; c < 3; ++c) {
-            double dg = mrow[13];
-            for (int q = 0; q < 8; ++q)
-                if ((em >> q) & 1u) dg += Ke.k[(3 * q + c) * 24 + 3 * q + c];
-            const double di = dg > 0.0 ? 1.0 / dg : 0.0;
-            const double bd = (double)(long long)a.bfix[3 * n + c] / FIX_B;
             // r_0 = H^T S D + K U_i - (K + H^T S H) U_i
-            const double rc = bd - Mx[c];
-            a.dinv[3 * n + c] = di;
-            a.r[3 * n + c] = rc;
-            a.z[3 * n + c] = rc * di;
-            rr += rc * rc;
-            rz += rc * rc * di;
+            rc[c] = (double)(long long)a.bfix[3 * n + c] / FIX_B - Mx[c];
+            a.r[3 * n + c] = rc[c];
+            rr += rc[c] * rc[c];
         }
+        for (int c = 0; c < 3; ++c) {
+            const double zc = Bi[3 * c] * rc[0] + Bi[3 * c + 1] * rc[1] + Bi[3 * c + 2] * rc[2];
+            a.z[3 * n + c] = zc;
+            rz += rc[c] * zc;
+        }
+        for (int e = 0; e < 9; ++e) a.binv[9 * n + e] = Bi[e];
     }
     rr = cta_sum(rr, sh);
     rz = cta_sum(rz, sh);
@@ -453,14 +484,18 @@ __global__ void __launch_bounds__(SOLVE_THREADS, 1) fem_solve_kernel(const __gri
             double rz_l = 0.0, rr_l = 0.0;
             for (long long q = q0; q < na; q += T) {
                 const long long n = a.alist[q];
+                double rc[3];
                 for (int c = 0; c < 3; ++c) {
                     a.x[3 * n + c] = fma(alpha, pcur[3 * n + c], a.x[3 * n + c]);
-                    const double rc = fma(-alpha, a.q[3 * n + c], a.r[3 * n + c]);
-                    const double zc = rc * a.dinv[3 * n + c];
-                    a.r[3 * n + c] = rc;
+                    rc[c] = fma(-alpha, a.q[3 * n + c], a.r[3 * n + c]);
+                    a.r[3 * n + c] = rc[c];
+                    rr_l += rc[c] * rc[c];
+                }
+                const double *Bi = a.binv + 9 * n;
+                for (int c = 0; c < 3; ++c) {
+                    const double zc = Bi[3 * c] * rc[0] + Bi[3 * c + 1] * rc[1] + Bi[3 * c + 2] * rc[2];
                     a.z[3 * n + c] = zc;
-                    rr_l += rc * rc;
-                    rz_l += rc * zc;
+                    rz_l += rc[c] * zc;
                 }
             }
             rz_l = cta_sum(rz_l, sh);
@@ -770,7 +805,7 @@ extern "C" nrr_status nrr_fem_update(const uint8_t *d_mask, nrr_dims dims, const
         return o;
     };
     const size_t o_eact = take(ne), o_nact = take(nv), o_mfix = take(nv * 27 * 8), o_bfix = take(nv * 3 * 8),
-                 o_m = take(nv * 27 * 8), o_dinv = take(nv * 3 * 8), o_r = take(nv * 3 * 8), o_p0 = take(nv * 3 * 8),
+                 o_m = take(nv * 27 * 8), o_binv = take(nv * 9 * 8), o_r = take(nv * 3 * 8), o_p0 = take(nv * 3 * 8),
                  o_p1 = take(nv * 3 * 8), o_q = take(nv * 3 * 8), o_part = take(4 * (size_t)cg_blocks * 8),
                  o_arr = take(8), o_keys = take(nb * 8), o_cnt = take(16), o_it = take((size_t)(steps + 1) * 4),
                  o_rel = take((size_t)(steps + 1) * 8), o_alist = take(nv * 4), o_acnt = take(4),
@@ -817,7 +852,7 @@ extern "C" nrr_status nrr_fem_update(const uint8_t *d_mask, nrr_dims dims, const
         A.mfix = mfix;
         A.bfix = bfix;
         A.m = (double *)(scr + o_m);
-        A.dinv = (double *)(scr + o_dinv);
+        A.binv = (double *)(scr + o_binv);
         A.x = d_U;
         A.r = (double *)(scr + o_r);
         A.p0 = (double *)(scr + o_p0);
