@@ -25,7 +25,8 @@
 //                              inverse 3x3 diagonal block of each vertex, in
 //                              FP64 on K + H^T S H, matrix-free (K element by
 //                              element around each vertex, the stencil for
-//                              H^T S H), warm-started from U_i until the
+//                              H^T S H; three lanes per vertex, one per
+//                              neighbour plane), warm-started from U_i until the
 //                              residual falls to tol times its start, as ONE
 //                              cooperative launch with two bounded grid
 //                              barriers per iteration; every CTA sums the
@@ -272,57 +273,52 @@ __host__ __device__ constexpr unsigned couple_mask(int dx, int dy, int dz)
     return cm;
 }
 
-// y = (K + H^T S H) v at vertex (i, j, k): for each of the 27 neighbours
-// whose coupling is not empty, its value v (from `get`) times the sum of the
-// element blocks K_e[a][b] over the model's elements holding both vertices,
-// plus the stencil coefficient of H^T S H times v.
+// The part of y = (K + H^T S H) v at vertex (i, j, k) that comes from the
+// 9 neighbours in plane dz = pl - 1, with the stiffness stencil `st` (27 x 9)
+// and the element stiffness `ke` (24 x 24) in shared memory (the three lanes
+// of a vertex read different planes of them).
 template <class Get>
-__device__ __forceinline__ void apply_A(const FemGrid &G, const FemKe &Ke, const double *mrow, unsigned em, int i, int j,
-                                        int k, Get get, double (&y)[3])
+__device__ __forceinline__ void apply_A_plane(const FemGrid &G, const double *st, const double *ke, const double *mrow,
+                                              unsigned em, int i, int j, int k, int pl, Get get, double (&y)[3])
 {
-    // one partial sum per neighbour plane dz and component: three short
-    // chains of dependent FP64 FMAs instead of one long one, added in a
-    // fixed order at the end
-    double yp[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+    y[0] = y[1] = y[2] = 0.0;
+    const int dz = pl - 1;
     if (em == 0xFFu) {  // interior of the model: the precomputed stencil
+        const double *sp = st + 81 * pl;
 #pragma unroll
-        for (int o = 0; o < 27; ++o) {
+        for (int oo = 0; oo < 9; ++oo) {
             double v[3];
-            get(vidx(G, i + o % 3 - 1, j + (o / 3) % 3 - 1, k + o / 9 - 1), v);
-            const double mo = mrow[o];
+            get(vidx(G, i + oo % 3 - 1, j + oo / 3 - 1, k + dz), v);
+            const double mo = mrow[oo + 9 * pl];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
 #pragma unroll
-                for (int d = 0; d < 3; ++d) yp[o / 9][c] = fma(Ke.st[o * 9 + 3 * c + d], v[d], yp[o / 9][c]);
-                yp[o / 9][c] = fma(mo, v[c], yp[o / 9][c]);
+                for (int d = 0; d < 3; ++d) y[c] = fma(sp[oo * 9 + 3 * c + d], v[d], y[c]);
+                y[c] = fma(mo, v[c], y[c]);
             }
         }
-    } else {
-#pragma unroll
-        for (int o = 0; o < 27; ++o) {
-            const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
-            const unsigned cm = couple_mask(dx, dy, dz);
-            if (!(em & cm)) continue;
-            double v[3];
-            get(vidx(G, i + dx, j + dy, k + dz), v);
-#pragma unroll
-            for (int a = 0; a < 8; ++a) {
-                if (!((cm >> a) & 1u)) continue;
-                if (!((em >> a) & 1u)) continue;
-                const int b = ((a & 1) + dx) + 2 * (((a >> 1) & 1) + dy) + 4 * (((a >> 2) & 1) + dz);
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-#pragma unroll
-                    for (int d = 0; d < 3; ++d)
-                        yp[o / 9][c] = fma(Ke.k[(3 * a + c) * 24 + 3 * b + d], v[d], yp[o / 9][c]);
-            }
-            const double mo = mrow[o];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) yp[o / 9][c] = fma(mo, v[c], yp[o / 9][c]);
-        }
+        return;
     }
 #pragma unroll
-    for (int c = 0; c < 3; ++c) y[c] = (yp[0][c] + yp[1][c]) + yp[2][c];
+    for (int oo = 0; oo < 9; ++oo) {
+        const int dx = oo % 3 - 1, dy = oo / 3 - 1;
+        const unsigned on = couple_mask(dx, dy, dz) & em;
+        if (!on) continue;
+        double v[3];
+        get(vidx(G, i + dx, j + dy, k + dz), v);
+        for (int a = 0; a < 8; ++a) {
+            if (!((on >> a) & 1u)) continue;
+            const int b = ((a & 1) + dx) + 2 * (((a >> 1) & 1) + dy) + 4 * (((a >> 2) & 1) + dz);
+            const double *kr = ke + 3 * a * 24 + 3 * b;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) y[c] = fma(kr[c * 24 + d], v[d], y[c]);
+        }
+        const double mo = mrow[oo + 9 * pl];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) y[c] = fma(mo, v[c], y[c]);
+    }
 }
 
 // Inverse of a symmetric positive definite 3x3 matrix (cofactors over the
@@ -377,6 +373,10 @@ __global__ void __launch_bounds__(SOLVE_THREADS, 1) fem_solve_kernel(const __gri
                                                                   const __grid_constant__ FemKe Ke)
 {
     __shared__ double sh[SOLVE_THREADS / 32];
+    __shared__ double s_st[27 * 9], s_ke[24 * 24];
+    for (int e = threadIdx.x; e < 24 * 24; e += blockDim.x) s_ke[e] = Ke.k[e];
+    for (int e = threadIdx.x; e < 27 * 9; e += blockDim.x) s_st[e] = Ke.st[e];
+    __syncthreads();
     const FemGrid &G = a.G;
     const long long T = (long long)gridDim.x * blockDim.x, t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     unsigned int bi = 0;  // grid barriers passed
@@ -443,9 +443,14 @@ __global__ void __launch_bounds__(SOLVE_THREADS, 1) fem_solve_kernel(const __gri
         // stop once |r| <= tol |r_0|: the warm start's residual is what the
         // solve has to remove (|b| holds K U_i, which can dwarf it)
         const double rr0 = rr, thr = a.tol * a.tol * rr0;
-        // the model's vertices, dealt round-robin over the CTAs first so that
-        // every CTA gets the same share
-        const long long na = *a.acount, q0 = blockIdx.x + (long long)gridDim.x * threadIdx.x;
+        const long long na = *a.acount;  // the model's vertices
+        // three lanes per vertex: lane 3 g + pl of a warp's first 30 serves
+        // vertex slot g, with the neighbours of plane dz = pl - 1 in the
+        // product and component pl in the updates; slot s of round rep is
+        // list entry blockIdx + gridDim (s + slots rep), so that every CTA
+        // gets the same share
+        const int lane = threadIdx.x & 31, grp = lane / 3, pl = lane - 3 * (lane / 3), base = 3 * grp;
+        const long long wslot0 = 10LL * (threadIdx.x >> 5), slots = 10LL * (blockDim.x >> 5);
         double rz_prev = 1.0;
         int it = 0;
         bool broke = false;
@@ -459,17 +464,32 @@ __global__ void __launch_bounds__(SOLVE_THREADS, 1) fem_solve_kernel(const __gri
                 for (int c = 0; c < 3; ++c) v[c] = fma(beta, __ldcg(pold + 3 * nb + c), __ldcg(a.z + 3 * nb + c));
             };
             double pq = 0.0;
-            for (long long q = q0; q < na; q += T) {
-                const long long n = a.alist[q];
-                const int i = (int)(n % G.Nx), j = (int)((n / G.Nx) % G.Ny), k = (int)(n / ((long long)G.Nx * G.Ny));
-                const unsigned em = elem_mask(G, a.eact, i, j, k);
-                double y[3], pn[3];
-                apply_A(G, Ke, a.m + 27 * n, em, i, j, k, getp, y);
-                getp(n, pn);
+            for (long long rep = 0;; ++rep) {
+                const long long qw = blockIdx.x + (long long)gridDim.x * (wslot0 + slots * rep);
+                if (qw >= na) break;  // the warp's first slot holds its smallest entry
+                const long long q = qw + (long long)gridDim.x * grp;
+                const bool act = grp < 10 && q < na;
+                double y[3] = {0.0, 0.0, 0.0};
+                long long n = 0;
+                if (act) {
+                    n = a.alist[q];
+                    const int i = (int)(n % G.Nx), j = (int)((n / G.Nx) % G.Ny), k = (int)(n / ((long long)G.Nx * G.Ny));
+                    const unsigned em = elem_mask(G, a.eact, i, j, k);
+                    apply_A_plane(G, s_st, s_ke, a.m + 27 * n, em, i, j, k, pl, getp, y);
+                }
+                double tot[3];
+#pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    pcur[3 * n + c] = pn[c];
-                    a.q[3 * n + c] = y[c];
-                    pq += pn[c] * y[c];
+                    const double t0 = __shfl_sync(0xffffffffu, y[c], base), t1 = __shfl_sync(0xffffffffu, y[c], base + 1),
+                                 t2 = __shfl_sync(0xffffffffu, y[c], base + 2);
+                    tot[c] = (t0 + t1) + t2;
+                }
+                if (act) {
+                    const double yc = pl == 0 ? tot[0] : (pl == 1 ? tot[1] : tot[2]);
+                    const double pn = fma(beta, __ldcg(pold + 3 * n + pl), __ldcg(a.z + 3 * n + pl));
+                    pcur[3 * n + pl] = pn;
+                    a.q[3 * n + pl] = yc;
+                    pq += pn * yc;
                 }
             }
             pq = cta_sum(pq, sh);
@@ -482,20 +502,27 @@ __global__ void __launch_bounds__(SOLVE_THREADS, 1) fem_solve_kernel(const __gri
             }
             const double alpha = rz / pq;
             double rz_l = 0.0, rr_l = 0.0;
-            for (long long q = q0; q < na; q += T) {
-                const long long n = a.alist[q];
-                double rc[3];
-                for (int c = 0; c < 3; ++c) {
-                    a.x[3 * n + c] = fma(alpha, pcur[3 * n + c], a.x[3 * n + c]);
-                    rc[c] = fma(-alpha, a.q[3 * n + c], a.r[3 * n + c]);
-                    a.r[3 * n + c] = rc[c];
-                    rr_l += rc[c] * rc[c];
+            for (long long rep = 0;; ++rep) {
+                const long long qw = blockIdx.x + (long long)gridDim.x * (wslot0 + slots * rep);
+                if (qw >= na) break;
+                const long long q = qw + (long long)gridDim.x * grp;
+                const bool act = grp < 10 && q < na;
+                double rp = 0.0;
+                long long n = 0;
+                if (act) {
+                    n = a.alist[q];
+                    a.x[3 * n + pl] = fma(alpha, pcur[3 * n + pl], a.x[3 * n + pl]);
+                    rp = fma(-alpha, a.q[3 * n + pl], a.r[3 * n + pl]);
+                    a.r[3 * n + pl] = rp;
+                    rr_l += rp * rp;
                 }
-                const double *Bi = a.binv + 9 * n;
-                for (int c = 0; c < 3; ++c) {
-                    const double zc = Bi[3 * c] * rc[0] + Bi[3 * c + 1] * rc[1] + Bi[3 * c + 2] * rc[2];
-                    a.z[3 * n + c] = zc;
-                    rz_l += rc[c] * zc;
+                const double r0 = __shfl_sync(0xffffffffu, rp, base), r1 = __shfl_sync(0xffffffffu, rp, base + 1),
+                             r2 = __shfl_sync(0xffffffffu, rp, base + 2);
+                if (act) {
+                    const double *Bi = a.binv + 9 * n + 3 * pl;
+                    const double zp = Bi[0] * r0 + Bi[1] * r1 + Bi[2] * r2;
+                    a.z[3 * n + pl] = zp;
+                    rz_l += rp * zp;
                 }
             }
             rz_l = cta_sum(rz_l, sh);
@@ -792,7 +819,8 @@ extern "C" nrr_status nrr_fem_update(const uint8_t *d_mask, nrr_dims dims, const
     if (occ < 1) return fail(NRR_E_INTERNAL, "solve kernel does not fit on an SM");
     // at most two CTAs per SM: the solve's time per iteration is its two grid
     // barriers plus an even share of the model's vertices per CTA
-    long long cg_blocks = ((long long)nv + SOLVE_THREADS - 1) / SOLVE_THREADS;
+    // three lanes per vertex, 30 of each warp's 32 lanes in use
+    long long cg_blocks = (3LL * (long long)nv + SOLVE_THREADS / 32 * 30 - 1) / (SOLVE_THREADS / 32 * 30);
     const long long cap_blocks = (long long)(occ < 2 ? occ : 2) * sm_count();
     if (cg_blocks > cap_blocks) cg_blocks = cap_blocks;
     if (cg_blocks < 1) cg_blocks = 1;
