@@ -65,8 +65,9 @@ struct FemGrid {
 // The element stiffness, row 3 a + c, column 3 b + d (local nodes a, b;
 // components c, d), and the stiffness stencil of a vertex whose 8 elements
 // all belong to the model (the 3x3 block coupling it to neighbour o, summed
-// over the elements holding both), kept in kernel-parameter space: every
-// thread of a warp reads the same entry.
+// over the elements holding both), passed as a kernel parameter and copied
+// into shared memory at the start of the solve (the three lanes of a vertex
+// read different planes of them).
 struct FemKe {
     double k[24 * 24];
     double st[27 * 9];
@@ -237,7 +238,7 @@ struct FemSolveArgs {
     double *binv;  // [nv][9] inverse of each vertex's 3x3 diagonal block of K + H^T S H (0 off the model)
     double *x;     // [nv][3] in: U_i, out: U_{i+1}
     double *r, *p0, *p1, *q;  // [nv][3]
-    double *z;                // [nv][3] D^-1 r, written with r
+    double *z;                // [nv][3] the preconditioned residual B^-1 r, written with r
     double *part;             // [4][gridDim.x] per-CTA partial dot products
     const int32_t *alist;     // the model's vertices in increasing order
     const int32_t *acount;    // their number
